@@ -1,0 +1,532 @@
+/*
+ * vsr_oracle.c -- plain CPU reference for custom-intersector ray traversal.
+ *
+ * TEST INFRASTRUCTURE.  This file is the oracle that the GPU library is
+ * checked against.  Only the test-suite, the smoke check and the benchmark's
+ * CPU-baseline leg may load it.  It shares no code, header, table or helper
+ * with the CUDA path; it reads the scene arrays, the rays and the serialised
+ * BVH blob (whose byte layout it parses itself) and nothing else.
+ *
+ * What it computes (Zellmann, "Adding Custom Intersectors to the C++ Ray
+ * Tracing Template Library Visionaray"):
+ *   - intersect(ray, triangle): the paper's FP32 triangle test
+ *     (basic_triangle<3, float>, Section 4), taken as Moller-Trumbore (1997)
+ *     with the rounding order fixed below;
+ *   - intersect(ray, aabb) with the inverse ray direction (Section 4, the
+ *     remark after the bvh_costs listing);
+ *   - the custom intersector operator() that wraps either test (Section 3.1)
+ *     and may clear hr.hit: default (forwards unchanged), alpha texture
+ *     (Section 4, alpha-mask listing), procedural alpha (Section 4) and the
+ *     bvh_costs counters (Section 4);
+ *   - the closest-hit and any-hit queries (Section 3.1) over a linear list of
+ *     primitives (brute force) and over a BVH with the while-while traversal
+ *     (Section 3.2, after Aila and Laine 2009) in which both calls to
+ *     intersect are replaced by the intersector.
+ *
+ * Rounding: compiled with -ffp-contract=off.  Every fused multiply-add is an
+ * explicit fmaf(); every other product or sum is a separately rounded FP32
+ * operation.  Readings of points the paper leaves open:
+ *   - triangle test: e1 = v1 - v0, e2 = v2 - v0, p = d x e2, det = e1.p;
+ *     det == 0 is a miss; inv = 1/det; s = o - v0; u = (s.p) inv;
+ *     q = s x e1; v = (d.q) inv; t = (e2.q) inv.  Geometric hit iff
+ *     u >= 0, v >= 0, u + v <= 1 (closed triangle, both faces);
+ *   - dot(a,b) = fmaf(a.x,b.x, fmaf(a.y,b.y, a.z*b.z));
+ *     cross(a,b).x = fmaf(a.y,b.z, -(a.z*b.y)) and cyclically;
+ *   - a candidate lies strictly inside (tmin, tmax); closest-hit replaces the
+ *     current best iff t < t_best or (t == t_best and prim < best prim),
+ *     comparing original primitive ids, which makes the answer unique;
+ *   - the intersector is consulted only for geometric candidates inside the
+ *     t interval (and, for closest-hit, that would improve the best), which
+ *     leaves every hit decision unchanged;
+ *   - direction components with |d| < 2^-80 are replaced by +-2^-80 when the
+ *     inverse direction is formed; the triangle test uses the original d;
+ *   - slab test: t0 = fmaf(lo, invd, -ood), t1 = fmaf(hi, invd, -ood) with
+ *     ood = o*invd; tn = max(min(t0,t1) over axes, tmin), tf = min(max(t0,t1)
+ *     over axes, t_far); the box is hit iff tn <= tf; t_far is t_best for
+ *     closest-hit and tmax for any-hit;
+ *   - traversal order: the root box is tested once; at an inner node both
+ *     children are tested; if both are hit the child on the side of the ray
+ *     direction's sign along the node's split axis is visited first
+ *     (left iff the sign bit of d[axis] is clear) and the other is pushed;
+ *     stack pops are LIFO with no re-test;
+ *   - bvh_costs counts every box test (root included) and every triangle
+ *     test, hit or not;
+ *   - texture lookup for the alpha decision: nearest texel, clamp to edge,
+ *     u -> column, v -> row; 8-bit alpha compared as integers against an
+ *     8-bit cutoff, float alpha compared against a float cutoff; primitives
+ *     whose texture id is 0xFFFFFFFF are opaque for both alpha intersectors;
+ *   - tex-coord interpolation: w0 = (1 - u) - v,
+ *     uv = fmaf(v, tc2, fmaf(u, tc1, w0*tc0)) per component;
+ *   - procedural alpha: accept iff sinf(f*uv.x) * sinf(f*uv.y) > 0.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_NONE 0xFFFFFFFFu
+
+/* intersector kinds */
+enum { ORC_ISECT_NONE = 0, ORC_ISECT_DEFAULT = 1, ORC_ISECT_ALPHA_TEX = 2,
+       ORC_ISECT_PROC_ALPHA = 3, ORC_ISECT_COUNT = 4 };
+/* queries */
+enum { ORC_CLOSEST = 0, ORC_ANY = 1 };
+/* texture formats */
+enum { ORC_TEX_U8 = 0, ORC_TEX_RGBA8 = 1, ORC_TEX_RGBA32F = 2 };
+/* near-tie flags */
+enum { ORC_TIE_EDGE = 1, ORC_TIE_ALPHA = 2 };
+
+typedef struct {
+    int32_t fmt;
+    uint32_t w, h, pad;
+    const void* texels;
+} orc_texture;
+
+typedef struct {
+    const float* verts;      /* [nverts*3] */
+    uint64_t nverts;
+    const uint32_t* idx;     /* [ntri*3] */
+    const float* uvs;        /* [ntri*6]: corner k of prim p at (3p+k)*2 */
+    const uint32_t* geom_id; /* [ntri] texture index or ORC_NONE */
+    uint32_t ntri, ntex;
+    const orc_texture* tex;  /* [ntex] */
+} orc_scene;
+
+typedef struct {
+    int32_t kind;
+    uint32_t cutoff_u8;
+    float cutoff_f;
+    float freq;
+} orc_isect;
+
+typedef struct {
+    float o[3], tmin, d[3], tmax;
+} orc_ray;
+
+typedef struct {
+    float t, u, v;
+    uint32_t prim;
+} orc_hit;
+
+/* per-ray statistics: box tests, triangle tests, intersector consultations,
+ * near-tie flags */
+typedef struct {
+    uint32_t boxes, tris, cands, flags;
+} orc_stats;
+
+/* ------------------------------------------------------------------ */
+/* vector helpers with the rounding order fixed                        */
+
+static float dot3(const float a[3], const float b[3]) {
+    return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
+}
+
+static void cross3(const float a[3], const float b[3], float r[3]) {
+    r[0] = fmaf(a[1], b[2], -(a[2] * b[1]));
+    r[1] = fmaf(a[2], b[0], -(a[0] * b[2]));
+    r[2] = fmaf(a[0], b[1], -(a[1] * b[0]));
+}
+
+/* ------------------------------------------------------------------ */
+/* intersect(ray, basic_triangle<3,float>) -- geometric test only.    */
+/* Returns 1 on a geometric hit; t, u, v are written whenever det!=0. */
+
+static int intersect_triangle(const orc_ray* r, const float v0[3], const float e1[3],
+                              const float e2[3], float* t, float* u, float* v) {
+    float p[3], s[3], q[3];
+    cross3(r->d, e2, p);
+    const float det = dot3(e1, p);
+    if (det == 0.0f) return -1; /* parallel: no t, u, v */
+    const float inv = 1.0f / det;
+    s[0] = r->o[0] - v0[0];
+    s[1] = r->o[1] - v0[1];
+    s[2] = r->o[2] - v0[2];
+    *u = dot3(s, p) * inv;
+    cross3(s, e1, q);
+    *v = dot3(r->d, q) * inv;
+    *t = dot3(e2, q) * inv;
+    return (*u >= 0.0f && *v >= 0.0f && (*u + *v) <= 1.0f) ? 1 : 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Ray set-up shared by the box test: guarded inverse direction.       */
+
+typedef struct {
+    orc_ray r;
+    float invd[3], ood[3];
+} orc_ray_ctx;
+
+static void ray_setup(const orc_ray* in, orc_ray_ctx* c) {
+    const float tiny = 0x1p-80f;
+    c->r = *in;
+    for (int a = 0; a < 3; ++a) {
+        float d = in->d[a];
+        if (fabsf(d) < tiny) d = copysignf(tiny, d);
+        c->invd[a] = 1.0f / d;
+        c->ood[a] = in->o[a] * c->invd[a];
+    }
+}
+
+/* intersect(ray, aabb, inv_dir): slab test against [tmin, t_far]. */
+static int intersect_aabb(const orc_ray_ctx* c, const float lo[3], const float hi[3],
+                          float t_far) {
+    float tn = c->r.tmin, tf = t_far;
+    for (int a = 0; a < 3; ++a) {
+        const float t0 = fmaf(lo[a], c->invd[a], -c->ood[a]);
+        const float t1 = fmaf(hi[a], c->invd[a], -c->ood[a]);
+        tn = fmaxf(tn, fminf(t0, t1));
+        tf = fminf(tf, fmaxf(t0, t1));
+    }
+    return tn <= tf;
+}
+
+/* ------------------------------------------------------------------ */
+/* Texture lookup (nearest, clamp to edge).                            */
+
+static uint32_t texel_index(float c, uint32_t n) {
+    const float cl = fminf(fmaxf(c, 0.0f), 1.0f);
+    int i = (int)floorf(cl * (float)n);
+    if (i > (int)n - 1) i = (int)n - 1;
+    return (uint32_t)i;
+}
+
+/* alpha decision for texture tx at uv; writes 1 if accepted */
+static int alpha_accept(const orc_texture* tx, float x, float y, const orc_isect* is) {
+    const uint32_t i = texel_index(x, tx->w), j = texel_index(y, tx->h);
+    const uint64_t k = (uint64_t)j * tx->w + i;
+    switch (tx->fmt) {
+        case ORC_TEX_U8:
+            return ((const uint8_t*)tx->texels)[k] >= is->cutoff_u8;
+        case ORC_TEX_RGBA8:
+            return ((const uint8_t*)tx->texels)[4 * k + 3] >= is->cutoff_u8;
+        default:
+            return ((const float*)tx->texels)[4 * k + 3] >= is->cutoff_f;
+    }
+}
+
+/* Interpolated texture coordinate of prim at barycentrics (u, v). */
+static void lerp_texcoord(const orc_scene* s, uint32_t prim, float u, float v, float* x,
+                          float* y) {
+    const float* tc = s->uvs + 6ull * prim;
+    const float w0 = (1.0f - u) - v;
+    *x = fmaf(v, tc[4], fmaf(u, tc[2], w0 * tc[0]));
+    *y = fmaf(v, tc[5], fmaf(u, tc[3], w0 * tc[1]));
+}
+
+/* The intersector's verdict on a geometric candidate (the line
+ * "hr.hit &= ..." of the user operator()).  Sets near-tie flags. */
+static int intersector_accepts(const orc_scene* s, const orc_isect* is, uint32_t prim,
+                               float u, float v, uint32_t* flags) {
+    if (is->kind != ORC_ISECT_ALPHA_TEX && is->kind != ORC_ISECT_PROC_ALPHA) return 1;
+    const uint32_t g = s->geom_id[prim];
+    if (g == ORC_NONE) return 1;
+    float x, y;
+    lerp_texcoord(s, prim, u, v, &x, &y);
+    if (is->kind == ORC_ISECT_ALPHA_TEX) {
+        const orc_texture* tx = &s->tex[g];
+        const int a = alpha_accept(tx, x, y, is);
+        /* near-tie: the decision changes within 1e-6 of uv */
+        const double e = 1e-6;
+        const float xs[2] = {(float)((double)x - e), (float)((double)x + e)};
+        const float ys[2] = {(float)((double)y - e), (float)((double)y + e)};
+        for (int m = 0; m < 2; ++m)
+            for (int n = 0; n < 2; ++n)
+                if (alpha_accept(tx, xs[m], ys[n], is) != a) *flags |= ORC_TIE_ALPHA;
+        return a;
+    }
+    const float sa = sinf(is->freq * x), sb = sinf(is->freq * y);
+    const double exact = sin((double)is->freq * (double)x) * sin((double)is->freq * (double)y);
+    if (fabs(exact) < 1e-6) *flags |= ORC_TIE_ALPHA;
+    return sa * sb > 0.0f;
+}
+
+/* ------------------------------------------------------------------ */
+/* Triangle access                                                     */
+
+static void tri_verts(const orc_scene* s, uint32_t prim, float v0[3], float e1[3],
+                      float e2[3]) {
+    const float* a = s->verts + 3ull * s->idx[3ull * prim];
+    const float* b = s->verts + 3ull * s->idx[3ull * prim + 1];
+    const float* c = s->verts + 3ull * s->idx[3ull * prim + 2];
+    for (int k = 0; k < 3; ++k) {
+        v0[k] = a[k];
+        e1[k] = b[k] - a[k];
+        e2[k] = c[k] - a[k];
+    }
+}
+
+static void note_edge_tie(float u, float v, uint32_t* flags) {
+    double m = (double)u;
+    if ((double)v < m) m = v;
+    double w = 1.0 - (double)u - (double)v;
+    if (w < m) m = w;
+    if (fabs(m) < 1e-6) *flags |= ORC_TIE_EDGE;
+}
+
+/* One primitive tested by the intersector under a query.  Returns 1 when an
+ * any-hit query terminates.  `best` holds the running result. */
+static int visit_prim(const orc_scene* s, const orc_isect* is, int query,
+                      const orc_ray_ctx* c, uint32_t prim, orc_hit* best, orc_stats* st) {
+    float v0[3], e1[3], e2[3], t, u, v;
+    tri_verts(s, prim, v0, e1, e2);
+    st->tris++;
+    const int g = intersect_triangle(&c->r, v0, e1, e2, &t, &u, &v);
+    if (g < 0) return 0;
+    const int in_range = t > c->r.tmin && t < c->r.tmax;
+    if (in_range) {
+        if (query == ORC_ANY || t <= best->t) note_edge_tie(u, v, &st->flags);
+    }
+    if (g == 0 || !in_range) return 0;
+    if (query == ORC_CLOSEST) {
+        if (!(t < best->t || (t == best->t && prim < best->prim))) return 0;
+        st->cands++;
+        if (!intersector_accepts(s, is, prim, u, v, &st->flags)) return 0;
+        best->t = t;
+        best->u = u;
+        best->v = v;
+        best->prim = prim;
+        return 0;
+    }
+    st->cands++;
+    if (!intersector_accepts(s, is, prim, u, v, &st->flags)) return 0;
+    best->t = t;
+    best->u = u;
+    best->v = v;
+    best->prim = prim;
+    return 1;
+}
+
+static void miss_record(const orc_ray* r, orc_hit* h) {
+    h->t = INFINITY;
+    h->u = 0.0f;
+    h->v = 0.0f;
+    h->prim = ORC_NONE;
+    (void)r;
+}
+
+/* ------------------------------------------------------------------ */
+/* Query over a linear primitive list (no BVH): the intersector        */
+/* replaces intersect inside the loop over primitives (Section 3.2).   */
+
+static void list_query(const orc_scene* s, const orc_isect* is, int query,
+                       const orc_ray* ray, orc_hit* out, orc_stats* st) {
+    orc_ray_ctx c;
+    ray_setup(ray, &c);
+    orc_hit best;
+    best.t = ray->tmax;
+    best.u = best.v = 0.0f;
+    best.prim = ORC_NONE;
+    memset(st, 0, sizeof(*st));
+    for (uint32_t p = 0; p < s->ntri; ++p)
+        if (visit_prim(s, is, query, &c, p, &best, st)) break;
+    if (best.prim == ORC_NONE) miss_record(ray, &best);
+    *out = best;
+}
+
+/* ------------------------------------------------------------------ */
+/* BVH blob parsing (own reader of the documented byte layout)         */
+
+typedef struct {
+    float lo[3];
+    uint32_t left_or_first;
+    float hi[3];
+    uint32_t count_axis;
+} orc_node;
+
+typedef struct {
+    const orc_node* nodes;
+    const uint32_t* order;
+    uint32_t num_nodes, num_prims, max_depth;
+} orc_bvh;
+
+static int parse_blob(const uint8_t* blob, uint64_t bytes, orc_bvh* b) {
+    if (!blob || bytes < 64) return -1;
+    if (memcmp(blob, "VSRBVH01", 8) != 0) return -2;
+    uint32_t hdr[8];
+    memcpy(hdr, blob + 8, sizeof(hdr));
+    /* hdr: version, header_bytes, num_nodes, num_prims, max_depth, leaf_max,
+     * num_leaves, flags */
+    if (hdr[0] != 1 || hdr[1] != 64) return -3;
+    b->num_nodes = hdr[2];
+    b->num_prims = hdr[3];
+    b->max_depth = hdr[4];
+    if (bytes != 64ull + 32ull * b->num_nodes + 4ull * b->num_prims) return -4;
+    if (b->max_depth > 64 || b->num_nodes < 2) return -5;
+    b->nodes = (const orc_node*)(blob + 64);
+    b->order = (const uint32_t*)(blob + 64 + 32ull * b->num_nodes);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* intersect(ray, BVH): the while-while traversal                      */
+
+static void bvh_query(const orc_scene* s, const orc_bvh* b, const orc_isect* is, int query,
+                      const orc_ray* ray, orc_hit* out, orc_stats* st) {
+    orc_ray_ctx c;
+    ray_setup(ray, &c);
+    orc_hit best;
+    best.t = ray->tmax;
+    best.u = best.v = 0.0f;
+    best.prim = ORC_NONE;
+    memset(st, 0, sizeof(*st));
+    uint32_t stack[72];
+    int sp = 0;
+    if (b->num_prims == 0) goto done;
+    st->boxes++;
+    if (!intersect_aabb(&c, b->nodes[0].lo, b->nodes[0].hi, best.t)) goto done;
+    uint32_t node = 0;
+    for (;;) { /* while ray not terminated */
+        while ((b->nodes[node].count_axis >> 2) == 0) { /* while node is inner */
+            const orc_node* nd = &b->nodes[node];
+            const uint32_t l = nd->left_or_first, r = l + 1;
+            const float far_t = (query == ORC_CLOSEST) ? best.t : ray->tmax;
+            st->boxes += 2;
+            const int hl = intersect_aabb(&c, b->nodes[l].lo, b->nodes[l].hi, far_t);
+            const int hr = intersect_aabb(&c, b->nodes[r].lo, b->nodes[r].hi, far_t);
+            if (hl && hr) {
+                const int axis = (int)(nd->count_axis & 3u);
+                const int neg = signbit(ray->d[axis]) ? 1 : 0;
+                stack[sp++] = neg ? l : r;
+                node = neg ? r : l;
+            } else if (hl) {
+                node = l;
+            } else if (hr) {
+                node = r;
+            } else {
+                if (sp == 0) goto done;
+                node = stack[--sp];
+            }
+        }
+        /* found a leaf: test its primitives */
+        const orc_node* lf = &b->nodes[node];
+        const uint32_t first = lf->left_or_first, cnt = lf->count_axis >> 2;
+        for (uint32_t k = 0; k < cnt; ++k)
+            if (visit_prim(s, is, query, &c, b->order[first + k], &best, st)) goto done;
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+done:
+    if (best.prim == ORC_NONE) miss_record(ray, &best);
+    *out = best;
+}
+
+/* ------------------------------------------------------------------ */
+/* Threaded drivers                                                    */
+
+typedef struct {
+    const orc_scene* s;
+    const orc_bvh* b; /* NULL: linear list */
+    const orc_isect* is;
+    int query;
+    const orc_ray* rays;
+    orc_hit* hits;
+    orc_stats* stats;
+    uint64_t begin, end;
+} orc_job;
+
+static void* run_job(void* arg) {
+    orc_job* j = (orc_job*)arg;
+    orc_stats tmp;
+    for (uint64_t i = j->begin; i < j->end; ++i) {
+        orc_stats* st = j->stats ? &j->stats[i] : &tmp;
+        if (j->b)
+            bvh_query(j->s, j->b, j->is, j->query, &j->rays[i], &j->hits[i], st);
+        else
+            list_query(j->s, j->is, j->query, &j->rays[i], &j->hits[i], st);
+    }
+    return NULL;
+}
+
+static int run_threads(orc_job base, uint64_t n, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if ((uint64_t)nthreads > n) nthreads = n > 0 ? (int)n : 1;
+    pthread_t th[256];
+    orc_job jobs[256];
+    for (int k = 0; k < nthreads; ++k) {
+        jobs[k] = base;
+        jobs[k].begin = n * (uint64_t)k / (uint64_t)nthreads;
+        jobs[k].end = n * (uint64_t)(k + 1) / (uint64_t)nthreads;
+    }
+    if (nthreads == 1) {
+        run_job(&jobs[0]);
+        return 0;
+    }
+    int started = 0;
+    for (int k = 0; k < nthreads; ++k) {
+        if (pthread_create(&th[k], NULL, run_job, &jobs[k]) != 0) break;
+        ++started;
+    }
+    for (int k = started; k < nthreads; ++k) run_job(&jobs[k]);
+    for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exported entry points                                               */
+
+/* Linear-list query (brute force over every triangle). */
+int orc_trace_list(const orc_scene* s, const orc_isect* is, int query, const float* rays,
+                   uint64_t n, float* hits, uint32_t* stats, int nthreads) {
+    if (!s || !is || (n && (!rays || !hits))) return -1;
+    orc_job j = {s, NULL, is, query, (const orc_ray*)rays, (orc_hit*)hits,
+                 (orc_stats*)stats, 0, 0};
+    return run_threads(j, n, nthreads);
+}
+
+/* BVH query with the while-while traversal. */
+int orc_trace_bvh(const orc_scene* s, const uint8_t* blob, uint64_t bytes,
+                  const orc_isect* is, int query, const float* rays, uint64_t n, float* hits,
+                  uint32_t* stats, int nthreads) {
+    orc_bvh b;
+    int rc = parse_blob(blob, bytes, &b);
+    if (rc) return rc;
+    if (b.num_prims != s->ntri) return -6;
+    orc_job j = {s, &b, is, query, (const orc_ray*)rays, (orc_hit*)hits,
+                 (orc_stats*)stats, 0, 0};
+    return run_threads(j, n, nthreads);
+}
+
+/* Single triangle test, exposed for worked-example checks.  out: t,u,v;
+ * returns 1 (hit), 0 (miss) or -1 (parallel). */
+int orc_intersect_triangle(const float* ray, const float* v0, const float* v1,
+                           const float* v2, float* out) {
+    float e1[3], e2[3];
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = v1[k] - v0[k];
+        e2[k] = v2[k] - v0[k];
+    }
+    return intersect_triangle((const orc_ray*)ray, v0, e1, e2, &out[0], &out[1], &out[2]);
+}
+
+/* Single box test with the guarded inverse direction. */
+int orc_intersect_aabb(const float* ray, const float* lo, const float* hi, float t_far) {
+    orc_ray_ctx c;
+    ray_setup((const orc_ray*)ray, &c);
+    return intersect_aabb(&c, lo, hi, t_far);
+}
+
+/* Shadow rays toward a directional light from primary hit points: origin
+ * p = fmaf(t, d, o) per component, direction l, t interval (eps, +inf).  A
+ * primary miss gives an inactive ray (tmin 0, tmax -1). */
+void orc_shadow_rays(const float* prim_rays, const float* prim_hits, uint64_t n,
+                     const float* l, float eps, float* out) {
+    for (uint64_t i = 0; i < n; ++i) {
+        const orc_ray* r = (const orc_ray*)prim_rays + i;
+        const orc_hit* h = (const orc_hit*)prim_hits + i;
+        orc_ray* s = (orc_ray*)out + i;
+        s->d[0] = l[0];
+        s->d[1] = l[1];
+        s->d[2] = l[2];
+        if (h->prim == ORC_NONE) {
+            s->o[0] = s->o[1] = s->o[2] = 0.0f;
+            s->tmin = 0.0f;
+            s->tmax = -1.0f;
+        } else {
+            for (int k = 0; k < 3; ++k) s->o[k] = fmaf(h->t, r->d[k], r->o[k]);
+            s->tmin = eps;
+            s->tmax = INFINITY;
+        }
+    }
+}

@@ -1,0 +1,284 @@
+"""Seeded synthetic scenes, textures and camera rays.
+
+These generators are the only code shared by the GPU path and the oracle.  They
+produce plain arrays (geometry, per-corner texture coordinates, texture ids,
+texels, rays); none of the traversal, intersection or intersector arithmetic
+lives here.  The workloads stand in for the paper's Fig. 1 use cases
+(billboards with alpha masks, procedural alpha, heat maps), whose scenes are
+not published.
+
+Layouts:
+  verts    float32 [V, 3]
+  idx      uint32  [T, 3]      vertex indices per triangle
+  uvs      float32 [T, 3, 2]   texture coordinate of corner k of triangle p
+  geom_id  uint32  [T]         texture index, 0xFFFFFFFF = untextured/opaque
+  rays     float32 [N, 8]      (ox, oy, oz, tmin, dx, dy, dz, tmax)
+Textures: fmt "u8" ([H, W] alpha), "rgba8" ([H, W, 4] uint8) or "rgba32f"
+([H, W, 4] float32); row j covers v in [j/H, (j+1)/H), column i covers u in
+[i/W, (i+1)/W).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _lib
+
+NONE = 0xFFFFFFFF
+SEED_BASE = 0x191212786
+
+
+@dataclass
+class Texture:
+    fmt: str
+    w: int
+    h: int
+    texels: np.ndarray
+
+
+@dataclass
+class Scene:
+    name: str
+    verts: np.ndarray
+    idx: np.ndarray
+    uvs: np.ndarray
+    geom_id: np.ndarray
+    textures: list = field(default_factory=list)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def ntri(self) -> int:
+        return int(self.idx.shape[0])
+
+    def extent(self) -> float:
+        if self.verts.shape[0] == 0:
+            return 1.0
+        lo = self.verts.min(axis=0).astype(np.float64)
+        hi = self.verts.max(axis=0).astype(np.float64)
+        return float(np.linalg.norm(hi - lo))
+
+    def bvh(self, leaf_max: int = 4, bins: int = 32) -> np.ndarray:
+        return _lib.bvh_build(self.verts, self.idx, leaf_max=leaf_max, bins=bins)
+
+
+# ---------------------------------------------------------------------------
+# cameras
+
+
+def pinhole_rays(eye, target, up, fovy_deg: float, width: int, height: int,
+                 tmin: float = 0.0, tmax: float = math.inf) -> np.ndarray:
+    """Pixel-centre rays of a pinhole camera, row-major from the top row;
+    directions normalised in float64 and rounded to float32."""
+    eye = np.asarray(eye, np.float64)
+    f = np.asarray(target, np.float64) - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(np.asarray(up, np.float64), f)
+    r /= np.linalg.norm(r)
+    u = np.cross(f, r)
+    th = math.tan(math.radians(fovy_deg) * 0.5)
+    aspect = width / height
+    sx = (2.0 * (np.arange(width) + 0.5) / width - 1.0) * th * aspect
+    sy = (1.0 - 2.0 * (np.arange(height) + 0.5) / height) * th
+    d = f[None, None, :] + sx[None, :, None] * r[None, None, :] + sy[:, None, None] * u[None, None, :]
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    rays = np.empty((height * width, 8), np.float32)
+    rays[:, 0:3] = eye.astype(np.float32)
+    rays[:, 3] = np.float32(tmin)
+    rays[:, 4:7] = d.reshape(-1, 3).astype(np.float32)
+    rays[:, 7] = np.float32(tmax)
+    return rays
+
+
+def orthographic_rays(lo_xy, hi_xy, z: float, n: int) -> np.ndarray:
+    """n x n rays along +z through cell centres of [lo, hi]^2 at depth z."""
+    xs = lo_xy[0] + (np.arange(n) + 0.5) / n * (hi_xy[0] - lo_xy[0])
+    ys = lo_xy[1] + (np.arange(n) + 0.5) / n * (hi_xy[1] - lo_xy[1])
+    X, Y = np.meshgrid(xs, ys)
+    rays = np.zeros((n * n, 8), np.float32)
+    rays[:, 0] = X.ravel()
+    rays[:, 1] = Y.ravel()
+    rays[:, 2] = z
+    rays[:, 3] = 0.0
+    rays[:, 6] = 1.0
+    rays[:, 7] = np.inf
+    return rays
+
+
+# ---------------------------------------------------------------------------
+# textures
+
+
+def disc_alpha_u8(size: int = 256, radius: float = 0.4) -> Texture:
+    """8-bit alpha: 255 where the texel centre lies within `radius` of the
+    UV centre (0.5, 0.5), else 0."""
+    c = (np.arange(size) + 0.5) / size
+    X, Y = np.meshgrid(c, c)
+    a = np.where((X - 0.5) ** 2 + (Y - 0.5) ** 2 <= radius * radius, 255, 0).astype(np.uint8)
+    return Texture("u8", size, size, a)
+
+
+def value_noise(rng: np.random.Generator, w: int, h: int, base: int = 16,
+                octaves: int = 3) -> np.ndarray:
+    """Lattice value noise (smoothstep-interpolated), base lattice plus
+    `octaves` finer octaves with halving amplitude, normalised to [0, 1]."""
+    out = np.zeros((h, w), np.float64)
+    amp, total = 1.0, 0.0
+    for o in range(octaves + 1):
+        L = base * (2 ** o)
+        lat = rng.uniform(0.0, 1.0, (L + 1, L + 1))
+        x = (np.arange(w) + 0.5) / w * L
+        y = (np.arange(h) + 0.5) / h * L
+        i0 = np.minimum(np.floor(x).astype(np.int64), L - 1)
+        j0 = np.minimum(np.floor(y).astype(np.int64), L - 1)
+        fx = x - i0
+        fy = y - j0
+        fx = fx * fx * (3 - 2 * fx)
+        fy = fy * fy * (3 - 2 * fy)
+        a = lat[j0[:, None], i0[None, :]]
+        b = lat[j0[:, None], i0[None, :] + 1]
+        c = lat[j0[:, None] + 1, i0[None, :]]
+        d = lat[j0[:, None] + 1, i0[None, :] + 1]
+        top = a + (b - a) * fx[None, :]
+        bot = c + (d - c) * fx[None, :]
+        out += amp * (top + (bot - top) * fy[:, None])
+        total += amp
+        amp *= 0.5
+    return out / total
+
+
+def foliage_rgba8(rng: np.random.Generator, size: int = 1024, coverage: float = 0.45) -> Texture:
+    """RGBA8 foliage: alpha 255 where value noise exceeds its (1-coverage)
+    quantile, green-ramp colour from a second noise field."""
+    n = value_noise(rng, size, size)
+    thr = np.quantile(n, 1.0 - coverage)
+    col = value_noise(rng, size, size)
+    tex = np.empty((size, size, 4), np.uint8)
+    tex[..., 0] = np.clip(30 + 70 * col, 0, 255).astype(np.uint8)
+    tex[..., 1] = np.clip(90 + 150 * col, 0, 255).astype(np.uint8)
+    tex[..., 2] = np.clip(20 + 50 * col, 0, 255).astype(np.uint8)
+    tex[..., 3] = np.where(n > thr, 255, 0).astype(np.uint8)
+    return Texture("rgba8", size, size, tex)
+
+
+# ---------------------------------------------------------------------------
+# geometry helpers
+
+_QUAD_UV = np.array([[[0, 0], [1, 0], [1, 1]], [[0, 0], [1, 1], [0, 1]]], np.float32)
+
+
+def _quads_to_tris(corners: np.ndarray):
+    """corners [Q,4,3] (counter-clockwise, UV (0,0),(1,0),(1,1),(0,1)) ->
+    verts [4Q,3], idx [2Q,3], uvs [2Q,3,2]."""
+    q = corners.shape[0]
+    verts = corners.reshape(-1, 3).astype(np.float32)
+    base = (np.arange(q, dtype=np.uint32) * 4)[:, None]
+    idx = np.empty((q, 2, 3), np.uint32)
+    idx[:, 0, :] = base + np.array([0, 1, 2], np.uint32)
+    idx[:, 1, :] = base + np.array([0, 2, 3], np.uint32)
+    uvs = np.broadcast_to(_QUAD_UV, (q, 2, 3, 2)).reshape(-1, 3, 2).copy()
+    return verts, idx.reshape(-1, 3), uvs
+
+
+def _random_rotations(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Uniform rotations on SO(3) from normalised Gaussian quaternions."""
+    q = rng.standard_normal((n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.empty((n, 3, 3))
+    R[:, 0, 0] = 1 - 2 * (y * y + z * z)
+    R[:, 0, 1] = 2 * (x * y - z * w)
+    R[:, 0, 2] = 2 * (x * z + y * w)
+    R[:, 1, 0] = 2 * (x * y + z * w)
+    R[:, 1, 1] = 1 - 2 * (x * x + z * z)
+    R[:, 1, 2] = 2 * (y * z - x * w)
+    R[:, 2, 0] = 2 * (x * z - y * w)
+    R[:, 2, 1] = 2 * (y * z + x * w)
+    R[:, 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+def random_quads(rng: np.random.Generator, n_quads: int, lo: float, hi: float,
+                 side_lo: float, side_hi: float) -> np.ndarray:
+    """Squares with centres U[lo,hi]^3, side U[side_lo,side_hi], uniform
+    orientation.  Returns corners [Q,4,3] float64."""
+    centres = rng.uniform(lo, hi, (n_quads, 3))
+    side = rng.uniform(side_lo, side_hi, n_quads)
+    R = _random_rotations(rng, n_quads)
+    local = np.array([[-0.5, -0.5, 0], [0.5, -0.5, 0], [0.5, 0.5, 0], [-0.5, 0.5, 0]])
+    pts = np.einsum("qij,kj->qki", R, local) * side[:, None, None]
+    return centres[:, None, :] + pts
+
+
+# ---------------------------------------------------------------------------
+# workloads
+
+
+def small_quads(seed: int = SEED_BASE + 0, n_quads: int = 2048, res: int = 256):
+    """2,048 random quads (4,096 triangles) in the unit cube with one 256x256
+    u8 disc alpha texture, and res x res pinhole primary rays from
+    (0.5, 0.5, -1) towards the cube centre (fovy 60 degrees)."""
+    rng = np.random.default_rng(seed)
+    corners = random_quads(rng, n_quads, 0.0, 1.0, 0.02, 0.1)
+    verts, idx, uvs = _quads_to_tris(corners)
+    geom = np.zeros(idx.shape[0], np.uint32)
+    scene = Scene("small_quads", verts, idx, uvs, geom, [disc_alpha_u8(256, 0.4)],
+                  {"n_quads": n_quads})
+    rays = pinhole_rays((0.5, 0.5, -1.0), (0.5, 0.5, 0.5), (0, 1, 0), 60.0, res, res)
+    return scene, rays
+
+
+def billboard_forest(seed: int = SEED_BASE + 1, n_quads: int = 500_000,
+                     width: int = 1920, height: int = 1080, tex_size: int = 1024,
+                     extent: float = 100.0):
+    """Vertical alpha-masked billboards scattered over an extent x extent
+    ground plane with Poisson-disc spacing (r = 0.1 at the full size), height
+    U[0.5, 3], width height*U[0.5, 1], yaw U[0, 2 pi); two opaque ground
+    triangles first; texture id = quad index mod 4 over four RGBA8 foliage
+    textures (about 45 % opaque).  Camera at (50, 1.7, -2) looking at
+    (50, 1, 50) scaled with the extent, fovy 60 degrees."""
+    rng = np.random.default_rng(seed)
+    # Poisson-disc radius keeps the full-size density (500k per 100x100).
+    r = 0.1 * math.sqrt((extent * extent / 1e4) / (n_quads / 5e5))
+    pts = _lib.poisson_disc(extent, extent, r, n_quads, seed).astype(np.float64)
+    q = pts.shape[0]
+    h = rng.uniform(0.5, 3.0, q)
+    w = h * rng.uniform(0.5, 1.0, q)
+    yaw = rng.uniform(0.0, 2 * math.pi, q)
+    ax = np.stack([np.cos(yaw), np.zeros(q), np.sin(yaw)], 1) * (0.5 * w)[:, None]
+    base = np.stack([pts[:, 0], np.zeros(q), pts[:, 1]], 1)
+    up = np.zeros((q, 3))
+    up[:, 1] = h
+    corners = np.stack([base - ax, base + ax, base + ax + up, base - ax + up], 1)
+    ground = np.array([[[0, 0, 0], [extent, 0, 0], [extent, 0, extent], [0, 0, extent]]], np.float64)
+    verts, idx, uvs = _quads_to_tris(np.concatenate([ground, corners], 0))
+    geom = np.empty(idx.shape[0], np.uint32)
+    geom[:2] = NONE
+    geom[2:] = (np.arange(q, dtype=np.uint32) % 4).repeat(2)
+    texs = [foliage_rgba8(np.random.default_rng(seed * 7 + k), tex_size) for k in range(4)]
+    s = extent / 100.0
+    scene = Scene("billboard_forest", verts, idx, uvs, geom, texs,
+                  {"n_quads": q, "poisson_r": r})
+    rays = pinhole_rays((50 * s, 1.7, -2 * s), (50 * s, 1.0, 50 * s), (0, 1, 0), 60.0,
+                        width, height)
+    return scene, rays
+
+
+LIGHT_DIR = np.array([0.3, 1.0, 0.2], np.float64) / np.linalg.norm([0.3, 1.0, 0.2])
+
+
+def light_dir_f32() -> np.ndarray:
+    return LIGHT_DIR.astype(np.float32)
+
+
+def shadow_eps(scene: Scene) -> float:
+    """Offset of secondary-ray origins: 1e-4 of the scene's bounding diagonal."""
+    return float(np.float32(1e-4 * scene.extent()))
+
+
+def quad_grid_scene(texture: Texture, geom: int = 0) -> Scene:
+    """One quad spanning [0,1]^2 at z = 0 with UVs equal to (x, y)."""
+    corners = np.array([[[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]]], np.float64)
+    verts, idx, uvs = _quads_to_tris(corners)
+    return Scene("unit_quad", verts, idx, uvs, np.full(2, geom, np.uint32), [texture])
