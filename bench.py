@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Throughput benchmark of custom-intersector BVH traversal on one GB300.
+
+Workload (one step): the billboard forest -- 500,000 vertical alpha-masked
+billboards (1,000,002 triangles with the two ground triangles), four RGBA8
+1024x1024 foliage textures, seeded synthetic data standing in for the paper's
+Fig. 1 scenes -- traced with the alpha-texture intersector: 1920x1080 primary
+closest-hit rays, secondary-ray generation toward a directional light, and
+1920x1080 shadow any-hit rays.  The value is whole-job Mrays/s (primary plus
+shadow rays) over the device-timed steps, inputs resident in HBM; L2 is
+flushed between steps.
+
+Also reported: a per-intersector breakdown (default, alpha texture,
+procedural alpha, counting; static and dynamic dispatch), the roofline of the
+dominant kernel from exact algorithmic bytes, an end-to-end number with host
+buffers, clocks sampled during the timed region and the CPU oracle timed on a
+bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s alpha any-hit vs default intersector; fwd+bwd Mrays/s; % of L2/HBM roofline"
+WORKLOAD = ("billboard forest: 500,000 alpha-masked billboards (1,000,002 triangles, "
+            "4 RGBA8 1024^2 textures), 1920x1080 primary closest-hit + 1920x1080 shadow "
+            "any-hit rays, alpha-texture intersector (cutoff 128)")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_traffic.json")
+FLUSH_BYTES = 256 << 20
+
+
+def default_params(V):
+    """Launch configuration used for the timed steps (and the full-size test)."""
+    return V.trace_params(block_size=128, persistent=0, refill_threshold=16)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1912_12786_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    mx = max(mx, float(c[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, c[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# byte model (algorithmic bytes of one trace launch)
+
+
+def trace_bytes(n_rays: int, stats: np.ndarray, texel_bytes: int, texcoords: bool) -> int:
+    """32 B ray + 16 B hit per ray, 32 B per box test (one node), 48 B per
+    triangle test, and for alpha intersectors 4 B geom id per intersector call
+    plus 24 B texture coordinates and one texel per textured call."""
+    s = stats.astype(np.int64).sum(axis=0)
+    b = n_rays * (32 + 16) + 32 * int(s[0]) + 48 * int(s[1])
+    if texcoords:
+        b += 4 * int(s[2]) + (24 + texel_bytes) * int(s[3])
+    return b
+
+
+# --------------------------------------------------------------------------
+# distributed set-up (one process per GPU; every rank traces its own frame)
+
+
+def dist_setup(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def dist_max(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------
+# CPU oracle leg
+
+
+def oracle_sample(sc, rays, blob, stride: int, repeats: int = 1):
+    """Time the oracle on every `stride`-th pixel: primary closest-hit and
+    shadow any-hit with the alpha-texture intersector, all host cores."""
+    from oracle import oracle as O
+    from paper_1912_12786_gb300.inputs import scenes
+    sel = rays[::stride]
+    cores = len(os.sched_getaffinity(0))
+    light, eps = scenes.light_dir_f32(), scenes.shadow_eps(sc)
+    elapsed, traced = 0.0, 0
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        h, _ = O.trace_bvh(sc, blob, sel, "alpha_tex", "closest", nthreads=cores)
+        t1 = time.perf_counter()
+        srays = O.shadow_rays(sel, O.hits_raw(h), light, eps)
+        t2 = time.perf_counter()
+        O.trace_bvh(sc, blob, srays, "alpha_tex", "any", nthreads=cores)
+        t3 = time.perf_counter()
+        elapsed += (t1 - t0) + (t3 - t2)
+        traced += 2 * len(sel)
+    return traced / elapsed / 1e6, cores, len(sel), elapsed
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup("gloo")
+    if rank != 0:
+        return 0
+    from paper_1912_12786_gb300.inputs import scenes
+    sc, rays = scenes.billboard_forest()
+    blob = sc.bvh()
+    stride = args.ref_stride
+    for _ in range(args.warmup):
+        oracle_sample(sc, rays, blob, stride * 4)
+    times, traced = [], 0
+    cores = len(os.sched_getaffinity(0))
+    for _ in range(args.steps):
+        _, cores, nsel, el = oracle_sample(sc, rays, blob, stride)
+        times.append(el)
+        traced += 2 * nsel
+    total = sum(times)
+    value = traced / total / 1e6
+    sample = (f"every {stride}th pixel of the 1920x1080 frame ({len(rays[::stride])} primary + "
+              f"as many shadow rays per step), alpha-texture closest + any hit")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mrays/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_stride": stride},
+        "cpu_baseline": {"value": round(value, 4), "unit": "Mrays/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU leg
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1912_12786_gb300 import vsr as V
+    from paper_1912_12786_gb300.inputs import scenes
+
+    V.lib()  # fails loudly if the library is missing
+    sc, rays = scenes.billboard_forest()
+    blob = sc.bvh()
+    s = V.scene_from_inputs(sc, blob)
+    n = len(rays)
+    d_rays = torch.from_numpy(rays).to(dev)
+    hits_p = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    rays_s = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    hits_s = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    alpha = V.intersector("alpha_tex", cutoff_u8=128)
+    light, eps = scenes.light_dir_f32(), scenes.shadow_eps(sc)
+    p = default_params(V)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        V.vsr_trace(s, d_rays, alpha, "closest", hits_p, None, p, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        V.vsr_make_shadow_rays(d_rays, hits_p, light, eps, rays_s, stream)
+        if ev is not None:
+            ev[2].record(stream)
+        V.vsr_trace(s, rays_s, alpha, "any", hits_s, None, p, stream)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        step(evs[k])
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    prim_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    gen_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    shad_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    total_ms = dist_max(sum(step_ms), world, dev)
+    rays_per_step = 2 * n
+    value = world * rays_per_step * args.steps / (total_ms / 1e3) / 1e6
+
+    # exact per-launch byte counts from the measurement variant (untimed)
+    st_p = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    st_s = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    tmp = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    V.vsr_trace_stats(s, d_rays, alpha, "closest", tmp, st_p)
+    V.vsr_trace_stats(s, rays_s, alpha, "any", tmp, st_s)
+    torch.cuda.synchronize(dev)
+    assert torch.equal(tmp.view(torch.int32), hits_s.view(torch.int32))
+    b_prim = trace_bytes(n, st_p.cpu().numpy().view(np.uint32), 4, True)
+    b_shad = trace_bytes(n, st_s.cpu().numpy().view(np.uint32), 4, True)
+    kernels = {
+        "trace closest alpha (primary)": (statistics.mean(prim_ms), b_prim),
+        "trace any alpha (shadow)": (statistics.mean(shad_ms), b_shad),
+    }
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    dom_ms, dom_bytes = kernels[dom]
+    peak, peak_src = peaks()
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        if tr.get("kernel_source_hash") == kernel_source_hash() and tr.get("kernel") == dom:
+            traffic = tr.get("traffic_bytes_per_launch")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
+                "algorithmic_bytes_per_launch": dom_bytes, "peak_source": peak_src,
+                "launch_ms": round(dom_ms, 4)}
+
+    out = {"metric": METRIC, "value": round(value, 2), "unit": "Mrays/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "rays_per_step": rays_per_step,
+                      "triangles": sc.ntri, "block_size": p.block_size,
+                      "persistent": p.persistent, "l2": "flushed between steps (256 MiB write)",
+                      "parallelism": f"replicas x{world} (each rank traces its own frame)"},
+           "roofline": roofline, "gpu_launches": 3 * args.steps,
+           "wall_s_timed_region": round(wall, 3),
+           "kernel_ms": {"trace_primary": round(statistics.mean(prim_ms), 4),
+                         "shadow_rays": round(statistics.mean(gen_ms), 4),
+                         "trace_shadow": round(statistics.mean(shad_ms), 4)},
+           "clocks": clk}
+
+    # end to end through the public API: pinned host rays in, host hits out
+    h_rays = torch.from_numpy(rays).pin_memory()
+    h_hp = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+    h_hs = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        d_rays.copy_(h_rays, non_blocking=True)
+        step()
+        h_hp.copy_(hits_p, non_blocking=True)
+        h_hs.copy_(hits_s, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        d_rays.copy_(h_rays, non_blocking=True)
+        step()
+        h_hp.copy_(hits_p, non_blocking=True)
+        h_hs.copy_(hits_s, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms = dist_max(e2e_ms, world, dev)
+    out["e2e"] = {"value": round(world * rays_per_step * args.steps / (e2e_ms / 1e3) / 1e6, 2),
+                  "unit": "Mrays/s", "h2d_bytes_per_step": int(h_rays.numel() * 4),
+                  "d2h_bytes_per_step": int((h_hp.numel() + h_hs.numel()) * 4)}
+
+    if not args.no_breakdown:
+        out["breakdown"] = breakdown(V, s, d_rays, rays_s, n, flush, stream, torch)
+
+    if rank == 0 and not args.no_cpu:
+        mr, cores, nsel, el = oracle_sample(sc, rays, blob, args.ref_stride)
+        out["cpu_baseline"] = {"value": round(mr, 4), "unit": "Mrays/s", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"every {args.ref_stride}th pixel ({nsel} primary + "
+                                         f"{nsel} shadow rays, {el:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    s.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def breakdown(V, s, d_rays, rays_s, n, flush, stream, torch, reps=5):
+    """Mrays/s per intersector x dispatch for the primary (closest) and shadow
+    (any) passes, each launch timed alone with L2 flushed before it."""
+    res = {}
+    hits = torch.empty((n, 4), dtype=torch.float32, device=d_rays.device)
+    cnt = torch.empty((n, 2), dtype=torch.int32, device=d_rays.device)
+    cfgs = [(k, d) for k in ("default", "alpha_tex", "proc_alpha", "count")
+            for d in ("static", "dynamic")]
+    for q, rr in (("closest", d_rays), ("any", rays_s)):
+        for kind, disp in cfgs + [("alpha_tex", "persistent")]:
+            p = V.trace_params(persistent=1) if disp == "persistent" else None
+            isect = V.intersector(kind, "static" if disp == "persistent" else disp)
+            c = cnt if kind == "count" else None
+            ms = []
+            for r in range(reps + 2):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                V.vsr_trace(s, rr, isect, q, hits, c, p, stream)
+                e1.record(stream)
+                e1.synchronize()
+                if r >= 2:
+                    ms.append(e0.elapsed_time(e1))
+            res[f"{q}/{kind}/{disp}"] = round(n / (statistics.median(ms) / 1e3) / 1e6, 1)
+    for q in ("closest", "any"):
+        base = res[f"{q}/default/static"]
+        for kind in ("alpha_tex", "proc_alpha", "count"):
+            res[f"{q}/{kind}/overhead_vs_default"] = round(base / res[f"{q}/{kind}/static"] - 1, 4)
+            res[f"{q}/{kind}/dynamic_vs_static"] = round(
+                res[f"{q}/{kind}/static"] / res[f"{q}/{kind}/dynamic"], 4)
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-stride", type=int, default=8)
+    ap.add_argument("--no-breakdown", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,239 @@
+/*
+ * vsr.h -- C ABI of the GB300 custom-intersector ray traversal library.
+ *
+ * Method (Zellmann, "Adding Custom Intersectors to the C++ Ray Tracing
+ * Template Library Visionaray"):
+ *   - Section 3.1: a custom intersector wraps intersect(ray, primitive); it
+ *     calls the built-in test, may inspect the hit record (barycentrics,
+ *     primitive id) and clears hr.hit to reject a candidate, which makes the
+ *     traversal continue.  The default intersector forwards the built-in
+ *     result unchanged.  Queries: closest hit and any hit over a BVH.
+ *   - Section 3.2: the BVH traversal (while-while, after Aila and Laine 2009)
+ *     calls intersect for node boxes and for primitives; both calls are
+ *     replaced by the intersector, statically at compile time.
+ *   - Section 1: callback libraries instead check at run time whether a
+ *     callback is registered and call it through a function pointer.
+ *   - Section 4: intersectors for an alpha-mask texture, a procedural alpha
+ *     function of the texture coordinate, and bvh_costs, which counts box and
+ *     triangle tests for a heat map.
+ *
+ * Here the intersectors are compiled in as template instantiations
+ * (VSR_DISPATCH_STATIC) and, for comparison, reached through a device
+ * function-pointer table checked at run time (VSR_DISPATCH_DYNAMIC).
+ *
+ * Conventions for every entry point:
+ *   - returns vsr_status; no C++ exception crosses the ABI;
+ *   - invalid arguments are rejected before any launch (VSR_ERR_ARG) and
+ *     vsr_last_error() gives a message for the calling thread;
+ *   - "device" pointers must be CUDA device (or managed) memory on the
+ *     scene's device; they are checked with cudaPointerGetAttributes and a
+ *     host pointer is rejected, never dereferenced by a kernel;
+ *   - work is enqueued on the given stream and is asynchronous unless stated;
+ *   - CUDA failures map to VSR_ERR_CUDA, allocation failures to VSR_ERR_OOM.
+ *
+ * Floating point: the triangle and box tests use FP32 with a fixed rounding
+ * order (explicit fused multiply-adds, IEEE division, no flush to zero) so
+ * that results are reproducible bit for bit by an independent CPU program.
+ */
+#ifndef VSR_H
+#define VSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "vsr_bvh.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* vsr_stream; /* == cudaStream_t; NULL = legacy default */
+
+typedef enum vsr_status {
+    VSR_OK = 0,
+    VSR_ERR_ARG = 1,     /* invalid argument, nothing launched */
+    VSR_ERR_CUDA = 2,    /* a CUDA runtime call or launch failed */
+    VSR_ERR_OOM = 3,     /* device or host allocation failed */
+    VSR_ERR_BLOB = 4,    /* BVH blob failed validation */
+    VSR_ERR_STACK = 5,   /* a traversal stack overflowed (device error word) */
+    VSR_ERR_TIMEOUT = 6, /* a bounded device wait gave up */
+    VSR_ERR_STATE = 7    /* call order violated (e.g. trace before bvh_load) */
+} vsr_status;
+
+/* ---------------------------------------------------------------- data */
+
+#define VSR_NO_TEXTURE 0xFFFFFFFFu /* geom_id of an untextured, opaque triangle */
+#define VSR_MISS 0xFFFFFFFFu       /* prim_id of a miss */
+
+typedef enum vsr_tex_format {
+    VSR_TEX_U8 = 0,     /* 1 byte per texel: alpha */
+    VSR_TEX_RGBA8 = 1,  /* 4 bytes per texel, alpha in byte 3 */
+    VSR_TEX_RGBA32F = 2 /* 16 bytes per texel, alpha in component 3 */
+} vsr_tex_format;
+
+/* A 2-D texture, row-major: texel (i, j) at index j*w + i; row j covers
+ * v in [j/h, (j+1)/h), column i covers u in [i/w, (i+1)/w). */
+typedef struct vsr_texture_desc {
+    int32_t fmt;         /* vsr_tex_format */
+    uint32_t w, h;       /* 1 .. 16384 */
+    uint32_t reserved;   /* 0 */
+    const void* texels;  /* host pointer, w*h texels, copied by the library */
+} vsr_texture_desc;
+
+/* A ray: origin, direction and the open parametric interval (tmin, tmax).
+ * 32 bytes, 16-byte aligned.  tmax < tmin marks an inactive ray (a miss). */
+typedef struct vsr_ray {
+    float ox, oy, oz, tmin;
+    float dx, dy, dz, tmax;
+} vsr_ray;
+
+/* A hit record (the paper's hit_record): distance, barycentrics (u weights
+ * the second vertex, v the third) and the original triangle index.  A miss
+ * has prim_id = VSR_MISS, t = +inf, u = v = 0.  16 bytes, 16-byte aligned. */
+typedef struct vsr_hit {
+    float t, u, v;
+    uint32_t prim_id;
+} vsr_hit;
+
+typedef enum vsr_isect_kind {
+    VSR_ISECT_NONE = 0,       /* no intersector: the default query overload */
+    VSR_ISECT_DEFAULT = 1,    /* basic_intersector: forwards intersect() */
+    VSR_ISECT_ALPHA_TEX = 2,  /* alpha mask: nearest texel alpha >= cutoff */
+    VSR_ISECT_PROC_ALPHA = 3, /* sinf(f*uv.x) * sinf(f*uv.y) > 0 */
+    VSR_ISECT_COUNT = 4       /* bvh_costs: counts box and triangle tests */
+} vsr_isect_kind;
+
+typedef enum vsr_dispatch {
+    VSR_DISPATCH_STATIC = 0, /* intersector compiled into the kernel */
+    VSR_DISPATCH_DYNAMIC = 1 /* run-time checked device function pointers */
+} vsr_dispatch;
+
+/* Intersector description.  Alpha intersectors read the triangle's texture
+ * (geom_id) and interpolate its three texture coordinates with the hit's
+ * barycentrics: uv = (1-u-v)*tc0 + u*tc1 + v*tc2.  Triangles whose geom_id is
+ * VSR_NO_TEXTURE are opaque for both alpha intersectors. */
+typedef struct vsr_intersector {
+    int32_t kind;             /* vsr_isect_kind */
+    int32_t dispatch;         /* vsr_dispatch */
+    uint32_t alpha_cutoff_u8; /* 8-bit textures: accept iff alpha >= this */
+    float alpha_cutoff_f;     /* float textures: accept iff alpha >= this */
+    float proc_freq;          /* procedural frequency f (40 in the tests) */
+    uint32_t reserved[3];     /* 0 */
+} vsr_intersector;
+
+typedef enum vsr_query {
+    VSR_CLOSEST = 0, /* nearest accepted candidate; equal t: lower prim id */
+    VSR_ANY = 1      /* first accepted candidate in traversal order */
+} vsr_query;
+
+/* Launch configuration; pass NULL for the tuned defaults. */
+typedef struct vsr_trace_params {
+    uint32_t block_size;       /* threads per block, multiple of 32, 32..512 */
+    uint32_t persistent;       /* 0: one ray per thread; 1: persistent warps */
+    uint32_t refill_threshold; /* persistent: refill idle lanes when fewer
+                                  than this many of 32 are still active */
+    uint32_t blocks_per_sm;    /* persistent: resident blocks per SM (0=auto) */
+} vsr_trace_params;
+
+typedef struct vsr_scene vsr_scene;
+
+/* ---------------------------------------------------------------- scene */
+
+/*
+ * Create a scene from indexed triangles (Section 3.1: basic_triangle<3,float>
+ * primitives, texture coordinate lists and textures as in the alpha-mask
+ * listing of Section 4).  All inputs are host pointers and are copied into
+ * device memory owned by the scene, on the current CUDA device.
+ *   verts   float32 [nverts*3]
+ *   idx     uint32 [ntri*3]; every index < nverts
+ *   uvs     float32 [ntri*6]: (u,v) of corner k of triangle p at 6p + 2k
+ *   geom_id uint32 [ntri]: texture index < ntex, or VSR_NO_TEXTURE
+ *   tex     [ntex] descriptors (may be NULL when ntex == 0)
+ * Errors: VSR_ERR_ARG (null pointer, index or geom_id out of range, bad
+ * texture), VSR_ERR_OOM, VSR_ERR_CUDA.  *out is NULL on failure.
+ */
+vsr_status vsr_scene_create_indexed(const float* verts, uint32_t nverts, const uint32_t* idx,
+                                    const float* uvs, const uint32_t* geom_id, uint32_t ntri,
+                                    const vsr_texture_desc* tex, uint32_t ntex,
+                                    vsr_scene** out);
+
+/* Same with three vertices per triangle: verts_xyz float32 [ntri*9]. */
+vsr_status vsr_scene_create(const float* verts_xyz, const float* uvs, const uint32_t* geom_id,
+                            uint32_t ntri, const vsr_texture_desc* tex, uint32_t ntex,
+                            vsr_scene** out);
+
+/* Free the scene and all device memory it owns (synchronises the device
+ * first).  NULL is accepted. */
+vsr_status vsr_scene_destroy(vsr_scene* scene);
+
+/*
+ * Load a serialised BVH (format in vsr_bvh.h) built over this scene's
+ * triangles.  The blob is validated (magic, version, sizes, checksum, index
+ * ranges, depth) and converted to the device layout: 32-byte nodes with
+ * sibling pairs adjacent and 48-byte triangles (v0, e1 = v1 - v0,
+ * e2 = v2 - v0) in leaf order.  Synchronous.  Errors: VSR_ERR_BLOB (invalid,
+ * or num_prims != ntri), VSR_ERR_ARG, VSR_ERR_OOM, VSR_ERR_CUDA.
+ */
+vsr_status vsr_bvh_load(vsr_scene* scene, const void* blob, size_t bytes);
+
+/* The library also exports the host builder and validator declared in
+ * vsr_bvh.h (vsr_bvh_build, vsr_bvh_free, vsr_bvh_validate); vsr_bvh_load
+ * runs vsr_bvh_validate before uploading. */
+
+/* ---------------------------------------------------------------- trace */
+
+/*
+ * Trace n rays (Section 3.1 queries through the Section 3.2 traversal with
+ * the intersector injected statically or dynamically).
+ *   rays     device, vsr_ray [n], 16-byte aligned
+ *   hits     device, vsr_hit [n], 16-byte aligned, caller-owned, written
+ *   counters device uint32 [n*2] or NULL; only for VSR_ISECT_COUNT, which
+ *            writes (box tests, triangle tests) per ray (bvh_costs)
+ *   params   NULL for the defaults
+ * Traversal order is fixed (root box tested once; at an inner node both
+ * children are tested and, if both are hit, the child on the side of the
+ * sign of the direction along the node's split axis is visited first; LIFO
+ * stack), so any-hit results and counts are deterministic.
+ * Errors: VSR_ERR_ARG, VSR_ERR_STATE (no BVH loaded), VSR_ERR_CUDA.
+ */
+vsr_status vsr_trace(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
+                     const vsr_intersector* isect, int32_t query, vsr_hit* hits,
+                     uint32_t* counters, const vsr_trace_params* params, vsr_stream stream);
+
+/*
+ * Measurement variant of vsr_trace with the static intersector: identical
+ * hits, plus per-ray statistics stats device uint32 [n*4] = (box tests,
+ * triangle tests, intersector consultations, 0).  Used to count the bytes
+ * the traversal must fetch.  Errors as vsr_trace.
+ */
+vsr_status vsr_trace_stats(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
+                           const vsr_intersector* isect, int32_t query, vsr_hit* hits,
+                           uint32_t* stats, vsr_stream stream);
+
+/*
+ * Secondary rays toward a directional light from primary hit points: origin
+ * o + t*d evaluated as fmaf(t, d, o) per component, direction light[3],
+ * interval (eps, +inf).  A primary miss gives an inactive ray (tmin 0,
+ * tmax -1, origin 0).  prim_rays/prim_hits/out: device [n].
+ */
+vsr_status vsr_make_shadow_rays(const vsr_ray* prim_rays, const vsr_hit* prim_hits, uint64_t n,
+                                const float light[3], float eps, vsr_ray* out,
+                                vsr_stream stream);
+
+/* ---------------------------------------------------------------- errors */
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* vsr_last_error(void);
+
+/* Read and clear the scene's device error word (bit 0: a traversal stack
+ * overflowed and the ray was terminated as a miss).  Synchronous. */
+vsr_status vsr_get_device_error(vsr_scene* scene, uint32_t* word);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int32_t vsr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VSR_H */

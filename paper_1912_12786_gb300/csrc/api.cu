@@ -1,0 +1,503 @@
+// C ABI of the GPU library: scene upload, BVH load, trace dispatch, secondary
+// ray generation and error reporting.  Every entry point validates its
+// arguments on the host before anything is launched, so an invalid call
+// returns an error instead of reaching a kernel.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "vsr.h"
+#include "vsr_internal.h"
+
+using namespace vsr;
+
+struct vsr_scene {
+    int device = 0;
+    uint32_t ntri = 0, nverts = 0, ntex = 0;
+    float* d_verts = nullptr;
+    uint32_t* d_idx = nullptr;
+    float2* d_uvs = nullptr;
+    uint32_t* d_geom = nullptr;
+    TexDesc* d_tex = nullptr;
+    uint8_t* d_texels = nullptr;
+    float4* d_nodes = nullptr;
+    float4* d_tris = nullptr;
+    uint32_t num_nodes = 0, max_depth = 0;
+    bool has_bvh = false;
+    DevScene dev{};
+    DevScene* d_user = nullptr;
+    uint32_t* d_err = nullptr;
+    unsigned long long* d_work = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+vsr_status fail(vsr_status s, const std::string& m) {
+    g_err = m;
+    return s;
+}
+
+vsr_status cuda_fail(cudaError_t e, const std::string& what) {
+    g_err = what + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? VSR_ERR_OOM : VSR_ERR_CUDA;
+}
+
+#define VSR_CUDA(call, what)                        \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            prev = -1;
+            ok = false;
+            return;
+        }
+        if (prev != d) ok = cudaSetDevice(d) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+cudaError_t dmalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+typedef int (*AddressRangeFn)(unsigned long long*, size_t*, unsigned long long);
+
+AddressRangeFn address_range_fn() {
+    static AddressRangeFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (AddressRangeFn) nullptr;
+        }
+        return reinterpret_cast<AddressRangeFn>(f);
+    }();
+    return fn;
+}
+
+// A device pointer on `device`, aligned, with `bytes` inside its allocation.
+vsr_status check_dev(const void* p, int device, const char* name, size_t align, size_t bytes) {
+    if (!p) return fail(VSR_ERR_ARG, std::string(name) + " is null");
+    if (reinterpret_cast<uintptr_t>(p) % align)
+        return fail(VSR_ERR_ARG, std::string(name) + " is not " + std::to_string(align) +
+                                     "-byte aligned");
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(VSR_ERR_ARG, std::string(name) + " is not a CUDA pointer");
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(VSR_ERR_ARG, std::string(name) + " is not device memory");
+    if (at.type == cudaMemoryTypeDevice && at.device != device)
+        return fail(VSR_ERR_ARG, std::string(name) + " lives on another device");
+    if (at.type == cudaMemoryTypeDevice) {
+        if (AddressRangeFn fn = address_range_fn()) {
+            unsigned long long base = 0;
+            size_t size = 0;
+            if (fn(&base, &size, (unsigned long long)reinterpret_cast<uintptr_t>(p)) == 0) {
+                const unsigned long long end = base + size;
+                const unsigned long long addr = reinterpret_cast<uintptr_t>(p);
+                if (addr + bytes > end || addr + bytes < addr)
+                    return fail(VSR_ERR_ARG, std::string(name) + " is smaller than " +
+                                                 std::to_string(bytes) + " bytes");
+            }
+        }
+    }
+    return VSR_OK;
+}
+
+uint32_t texel_size(int32_t fmt) {
+    return fmt == VSR_TEX_U8 ? 1u : (fmt == VSR_TEX_RGBA8 ? 4u : 16u);
+}
+
+// Convert one blob node to the packed device reference.
+uint32_t node_ref(const vsr_bvh_node& n) {
+    const uint32_t count = n.count_axis >> 2;
+    if (count == 0) return ((n.left_or_first >> 1) << 2) | (n.count_axis & 3u);
+    return kLeafBit | (n.left_or_first << 3) | (count - 1u);
+}
+
+__global__ void k_build_tris(const float* __restrict__ verts, const uint32_t* __restrict__ idx,
+                             const uint32_t* __restrict__ order, uint32_t n,
+                             float4* __restrict__ tris) {
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const uint32_t p = order[s];
+    const float* a = verts + 3ull * idx[3ull * p];
+    const float* b = verts + 3ull * idx[3ull * p + 1];
+    const float* c = verts + 3ull * idx[3ull * p + 2];
+    tris[3ull * s] = make_float4(a[0], a[1], a[2], __uint_as_float(p));
+    tris[3ull * s + 1] =
+        make_float4(__fsub_rn(b[0], a[0]), __fsub_rn(b[1], a[1]), __fsub_rn(b[2], a[2]), 0.0f);
+    tris[3ull * s + 2] =
+        make_float4(__fsub_rn(c[0], a[0]), __fsub_rn(c[1], a[1]), __fsub_rn(c[2], a[2]), 0.0f);
+}
+
+__global__ void k_shadow_rays(const float4* __restrict__ rays, const float4* __restrict__ hits,
+                              unsigned long long n, float lx, float ly, float lz, float eps,
+                              float4* __restrict__ out) {
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 h = hits[i];
+    if (__float_as_uint(h.w) == kMiss) {
+        out[2 * i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        out[2 * i + 1] = make_float4(lx, ly, lz, -1.0f);
+        return;
+    }
+    const float4 a = rays[2 * i], b = rays[2 * i + 1];
+    out[2 * i] = make_float4(__fmaf_rn(h.x, b.x, a.x), __fmaf_rn(h.x, b.y, a.y),
+                             __fmaf_rn(h.x, b.z, a.z), eps);
+    out[2 * i + 1] = make_float4(lx, ly, lz, __int_as_float(0x7f800000));
+}
+
+void free_bvh(vsr_scene* s) {
+    dfree(s->d_nodes);
+    dfree(s->d_tris);
+    s->has_bvh = false;
+}
+
+vsr_status validate_isect(const vsr_intersector* is, int32_t query) {
+    if (!is) return fail(VSR_ERR_ARG, "intersector is null");
+    if (is->kind < VSR_ISECT_NONE || is->kind > VSR_ISECT_COUNT)
+        return fail(VSR_ERR_ARG, "unknown intersector kind");
+    if (is->dispatch != VSR_DISPATCH_STATIC && is->dispatch != VSR_DISPATCH_DYNAMIC)
+        return fail(VSR_ERR_ARG, "unknown dispatch mode");
+    if (is->alpha_cutoff_u8 > 256) return fail(VSR_ERR_ARG, "alpha_cutoff_u8 above 256");
+    if (std::isnan(is->alpha_cutoff_f) || !std::isfinite(is->proc_freq))
+        return fail(VSR_ERR_ARG, "non-finite intersector parameter");
+    if (query != VSR_CLOSEST && query != VSR_ANY) return fail(VSR_ERR_ARG, "unknown query");
+    return VSR_OK;
+}
+
+vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
+                          const vsr_intersector* is, int32_t query, vsr_hit* hits,
+                          const vsr_trace_params* p, LaunchArgs& a) {
+    if (!s) return fail(VSR_ERR_ARG, "scene is null");
+    if (!s->has_bvh) return fail(VSR_ERR_STATE, "no BVH loaded into the scene");
+    vsr_status st = validate_isect(is, query);
+    if (st != VSR_OK) return st;
+    vsr_trace_params prm{128u, 0u, 16u, 0u};
+    if (p) prm = *p;
+    if (prm.block_size < 32 || prm.block_size > 256 || prm.block_size % 32)
+        return fail(VSR_ERR_ARG, "block_size must be a multiple of 32 in 32..256");
+    if (prm.persistent > 1) return fail(VSR_ERR_ARG, "persistent must be 0 or 1");
+    if (prm.refill_threshold < 1 || prm.refill_threshold > 32)
+        return fail(VSR_ERR_ARG, "refill_threshold must be in 1..32");
+    if (prm.blocks_per_sm > 32) return fail(VSR_ERR_ARG, "blocks_per_sm above 32");
+    if (prm.persistent && is->dispatch == VSR_DISPATCH_DYNAMIC)
+        return fail(VSR_ERR_ARG, "persistent launches use static dispatch only");
+    if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull)
+        return fail(VSR_ERR_ARG, "too many rays for one launch");
+    if (n > 0) {
+        st = check_dev(rays, s->device, "rays", 16, n * sizeof(vsr_ray));
+        if (st != VSR_OK) return st;
+        st = check_dev(hits, s->device, "hits", 16, n * sizeof(vsr_hit));
+        if (st != VSR_OK) return st;
+    }
+    a = LaunchArgs{};
+    a.sc = s->dev;
+    a.ip.cutoff_u8 = is->alpha_cutoff_u8;
+    a.ip.cutoff_f = is->alpha_cutoff_f;
+    a.ip.freq = is->proc_freq;
+    a.ip.kind = (uint32_t)is->kind;
+    a.rays = reinterpret_cast<const float4*>(rays);
+    a.n = n;
+    a.hits = reinterpret_cast<float4*>(hits);
+    a.query = query;
+    a.block = prm.block_size;
+    a.persistent = prm.persistent;
+    a.refill = prm.refill_threshold;
+    a.blocks_per_sm = prm.blocks_per_sm;
+    a.work = s->d_work;
+    a.dyn_user = s->d_user;
+    return VSR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t vsr_version(void) { return 100; }
+
+const char* vsr_last_error(void) { return g_err.c_str(); }
+
+vsr_status vsr_scene_create_indexed(const float* verts, uint32_t nverts, const uint32_t* idx,
+                                    const float* uvs, const uint32_t* geom_id, uint32_t ntri,
+                                    const vsr_texture_desc* tex, uint32_t ntex,
+                                    vsr_scene** out) {
+    g_err.clear();
+    if (!out) return fail(VSR_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (ntri > (1u << 28)) return fail(VSR_ERR_ARG, "more than 2^28 triangles");
+    if (ntri > 0 && (!verts || !idx || !uvs || !geom_id))
+        return fail(VSR_ERR_ARG, "null geometry pointer");
+    if (ntex > 0 && !tex) return fail(VSR_ERR_ARG, "null texture array");
+    for (uint64_t k = 0; k < 3ull * ntri; ++k)
+        if (idx[k] >= nverts) return fail(VSR_ERR_ARG, "vertex index out of range");
+    for (uint32_t p = 0; p < ntri; ++p)
+        if (geom_id[p] != VSR_NO_TEXTURE && geom_id[p] >= ntex)
+            return fail(VSR_ERR_ARG, "geom_id references a missing texture");
+    std::vector<TexDesc> td(ntex);
+    unsigned long long texel_bytes = 0;
+    for (uint32_t k = 0; k < ntex; ++k) {
+        const vsr_texture_desc& t = tex[k];
+        if (t.fmt < VSR_TEX_U8 || t.fmt > VSR_TEX_RGBA32F)
+            return fail(VSR_ERR_ARG, "unknown texture format");
+        if (t.w < 1 || t.h < 1 || t.w > 16384 || t.h > 16384)
+            return fail(VSR_ERR_ARG, "texture size outside 1..16384");
+        if (!t.texels) return fail(VSR_ERR_ARG, "null texels");
+        td[k] = TexDesc{(uint32_t)t.fmt, t.w, t.h, 0u, texel_bytes, 0ull};
+        texel_bytes += ((unsigned long long)t.w * t.h * texel_size(t.fmt) + 15ull) & ~15ull;
+    }
+    vsr_scene* s = new (std::nothrow) vsr_scene();
+    if (!s) return fail(VSR_ERR_OOM, "host allocation failed");
+    cudaGetDevice(&s->device);
+    s->ntri = ntri;
+    s->nverts = nverts;
+    s->ntex = ntex;
+    auto bail = [&](vsr_status st) {
+        vsr_scene_destroy(s);
+        return st;
+    };
+    cudaError_t e = cudaSuccess;
+    if ((e = dmalloc(&s->d_verts, 3ull * nverts)) != cudaSuccess ||
+        (e = dmalloc(&s->d_idx, 3ull * ntri)) != cudaSuccess ||
+        (e = dmalloc(&s->d_uvs, 3ull * ntri)) != cudaSuccess ||
+        (e = dmalloc(&s->d_geom, (size_t)ntri)) != cudaSuccess ||
+        (e = dmalloc(&s->d_tex, (size_t)ntex)) != cudaSuccess ||
+        (e = dmalloc(&s->d_texels, (size_t)texel_bytes)) != cudaSuccess ||
+        (e = dmalloc(&s->d_user, 1)) != cudaSuccess || (e = dmalloc(&s->d_err, 1)) != cudaSuccess ||
+        (e = dmalloc(&s->d_work, 1)) != cudaSuccess)
+        return bail(cuda_fail(e, "scene allocation"));
+    if ((nverts && (e = cudaMemcpy(s->d_verts, verts, 12ull * nverts, cudaMemcpyHostToDevice))) ||
+        (ntri && (e = cudaMemcpy(s->d_idx, idx, 12ull * ntri, cudaMemcpyHostToDevice))) ||
+        (ntri && (e = cudaMemcpy(s->d_uvs, uvs, 24ull * ntri, cudaMemcpyHostToDevice))) ||
+        (ntri && (e = cudaMemcpy(s->d_geom, geom_id, 4ull * ntri, cudaMemcpyHostToDevice))) ||
+        (ntex && (e = cudaMemcpy(s->d_tex, td.data(), sizeof(TexDesc) * ntex,
+                                 cudaMemcpyHostToDevice))) ||
+        (e = cudaMemset(s->d_err, 0, sizeof(uint32_t))))
+        return bail(cuda_fail(e, "scene upload"));
+    for (uint32_t k = 0; k < ntex; ++k) {
+        const size_t b = (size_t)tex[k].w * tex[k].h * texel_size(tex[k].fmt);
+        if ((e = cudaMemcpy(s->d_texels + td[k].offset, tex[k].texels, b,
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(cuda_fail(e, "texture upload"));
+    }
+    *out = s;
+    return VSR_OK;
+}
+
+vsr_status vsr_scene_create(const float* verts_xyz, const float* uvs, const uint32_t* geom_id,
+                            uint32_t ntri, const vsr_texture_desc* tex, uint32_t ntex,
+                            vsr_scene** out) {
+    g_err.clear();
+    if (ntri > (1u << 28)) return fail(VSR_ERR_ARG, "more than 2^28 triangles");
+    std::vector<uint32_t> idx(3ull * ntri);
+    for (uint64_t k = 0; k < idx.size(); ++k) idx[k] = (uint32_t)k;
+    return vsr_scene_create_indexed(verts_xyz, 3u * ntri, idx.data(), uvs, geom_id, ntri, tex,
+                                    ntex, out);
+}
+
+vsr_status vsr_scene_destroy(vsr_scene* s) {
+    if (!s) return VSR_OK;
+    DeviceGuard g(s->device);
+    cudaDeviceSynchronize();
+    free_bvh(s);
+    dfree(s->d_verts);
+    dfree(s->d_idx);
+    dfree(s->d_uvs);
+    dfree(s->d_geom);
+    dfree(s->d_tex);
+    dfree(s->d_texels);
+    dfree(s->d_user);
+    dfree(s->d_err);
+    dfree(s->d_work);
+    delete s;
+    return VSR_OK;
+}
+
+vsr_status vsr_bvh_load(vsr_scene* s, const void* blob, size_t bytes) {
+    g_err.clear();
+    if (!s) return fail(VSR_ERR_ARG, "scene is null");
+    if (vsr_bvh_validate(blob, bytes) != 0)
+        return fail(VSR_ERR_BLOB, std::string("invalid BVH blob: ") + vsr_bvh_last_error());
+    DeviceGuard g(s->device);
+    if (!g.ok) return fail(VSR_ERR_CUDA, "cannot select the scene's device");
+    uint32_t hdr[8];
+    std::memcpy(hdr, static_cast<const uint8_t*>(blob) + 8, sizeof(hdr));
+    const uint32_t num_nodes = hdr[2], num_prims = hdr[3], max_depth = hdr[4];
+    if (num_prims != s->ntri)
+        return fail(VSR_ERR_BLOB, "BVH was built over a different number of triangles");
+    const vsr_bvh_node* nodes =
+        reinterpret_cast<const vsr_bvh_node*>(static_cast<const uint8_t*>(blob) + 64);
+    const uint32_t* order = reinterpret_cast<const uint32_t*>(
+        static_cast<const uint8_t*>(blob) + 64 + 32ull * num_nodes);
+    free_bvh(s);
+    std::vector<float4> hn(2ull * num_nodes);
+    for (uint32_t i = 0; i < num_nodes; ++i) {
+        const vsr_bvh_node& nd = nodes[i];
+        const uint32_t ref = (i == 1) ? 0u : node_ref(nd);
+        float ref_bits;
+        std::memcpy(&ref_bits, &ref, sizeof(ref_bits));
+        hn[2ull * i] = make_float4(nd.lo[0], nd.lo[1], nd.lo[2], ref_bits);
+        hn[2ull * i + 1] = make_float4(nd.hi[0], nd.hi[1], nd.hi[2], 0.0f);
+    }
+    cudaError_t e;
+    if ((e = dmalloc(&s->d_nodes, hn.size())) != cudaSuccess)
+        return cuda_fail(e, "node allocation");
+    if ((e = cudaMemcpy(s->d_nodes, hn.data(), sizeof(float4) * hn.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess) {
+        free_bvh(s);
+        return cuda_fail(e, "node upload");
+    }
+    if ((e = dmalloc(&s->d_tris, 3ull * num_prims)) != cudaSuccess) {
+        free_bvh(s);
+        return cuda_fail(e, "triangle allocation");
+    }
+    if (num_prims) {
+        uint32_t* d_order = nullptr;
+        if ((e = dmalloc(&d_order, (size_t)num_prims)) != cudaSuccess) {
+            free_bvh(s);
+            return cuda_fail(e, "order allocation");
+        }
+        e = cudaMemcpy(d_order, order, 4ull * num_prims, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            k_build_tris<<<(num_prims + 255) / 256, 256>>>(s->d_verts, s->d_idx, d_order,
+                                                            num_prims, s->d_tris);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        }
+        cudaFree(d_order);
+        if (e != cudaSuccess) {
+            free_bvh(s);
+            return cuda_fail(e, "triangle layout");
+        }
+    }
+    s->num_nodes = num_nodes;
+    s->max_depth = max_depth;
+    DevScene& d = s->dev;
+    d.nodes = s->d_nodes;
+    d.tris = s->d_tris;
+    d.uvs = s->d_uvs;
+    d.geom = s->d_geom;
+    d.tex = s->d_tex;
+    d.texels = s->d_texels;
+    d.err = s->d_err;
+    d.nprims = num_prims;
+    d.ntex = s->ntex;
+    d.root_ref = node_ref(nodes[0]);
+    d.stack_depth = max_depth > 0 ? max_depth : 1u;
+    d.root_a = make_float4(nodes[0].lo[0], nodes[0].lo[1], nodes[0].lo[2], 0.0f);
+    d.root_b = make_float4(nodes[0].hi[0], nodes[0].hi[1], nodes[0].hi[2], 0.0f);
+    if ((e = cudaMemcpy(s->d_user, &d, sizeof(DevScene), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        free_bvh(s);
+        return cuda_fail(e, "scene descriptor upload");
+    }
+    s->has_bvh = true;
+    return VSR_OK;
+}
+
+vsr_status vsr_trace(vsr_scene* s, const vsr_ray* rays, uint64_t n, const vsr_intersector* is,
+                     int32_t query, vsr_hit* hits, uint32_t* counters,
+                     const vsr_trace_params* p, vsr_stream stream) {
+    g_err.clear();
+    LaunchArgs a;
+    vsr_status st = prepare_launch(s, rays, n, is, query, hits, p, a);
+    if (st != VSR_OK) return st;
+    if (counters) {
+        if (is->kind != VSR_ISECT_COUNT)
+            return fail(VSR_ERR_ARG, "counters are written by the COUNT intersector only");
+        if (n) {
+            st = check_dev(counters, s->device, "counters", 8, n * 8);
+            if (st != VSR_OK) return st;
+        }
+        a.counters = reinterpret_cast<uint2*>(counters);
+    }
+    if (n == 0) return VSR_OK;
+    a.stream = reinterpret_cast<cudaStream_t>(stream);
+    DeviceGuard g(s->device);
+    cudaError_t e = is->dispatch == VSR_DISPATCH_STATIC ? launch_static(a, is->kind, false)
+                                                        : launch_dynamic(a, is->kind);
+    if (e != cudaSuccess) return cuda_fail(e, "trace launch");
+    return VSR_OK;
+}
+
+vsr_status vsr_trace_stats(vsr_scene* s, const vsr_ray* rays, uint64_t n,
+                           const vsr_intersector* is, int32_t query, vsr_hit* hits,
+                           uint32_t* stats, vsr_stream stream) {
+    g_err.clear();
+    LaunchArgs a;
+    vsr_status st = prepare_launch(s, rays, n, is, query, hits, nullptr, a);
+    if (st != VSR_OK) return st;
+    if (n == 0) return VSR_OK;
+    st = check_dev(stats, s->device, "stats", 16, n * 16);
+    if (st != VSR_OK) return st;
+    a.stats = reinterpret_cast<uint4*>(stats);
+    a.stream = reinterpret_cast<cudaStream_t>(stream);
+    DeviceGuard g(s->device);
+    cudaError_t e = launch_static(a, is->kind, true);
+    if (e != cudaSuccess) return cuda_fail(e, "trace_stats launch");
+    return VSR_OK;
+}
+
+vsr_status vsr_make_shadow_rays(const vsr_ray* prim_rays, const vsr_hit* prim_hits, uint64_t n,
+                                const float light[3], float eps, vsr_ray* out,
+                                vsr_stream stream) {
+    g_err.clear();
+    if (!light) return fail(VSR_ERR_ARG, "light is null");
+    if (!std::isfinite(eps) || !std::isfinite(light[0]) || !std::isfinite(light[1]) ||
+        !std::isfinite(light[2]))
+        return fail(VSR_ERR_ARG, "non-finite light or eps");
+    if (n == 0) return VSR_OK;
+    if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 256ull)
+        return fail(VSR_ERR_ARG, "too many rays");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    vsr_status st = check_dev(prim_rays, dev, "prim_rays", 16, n * 32);
+    if (st == VSR_OK) st = check_dev(prim_hits, dev, "prim_hits", 16, n * 16);
+    if (st == VSR_OK) st = check_dev(out, dev, "out", 16, n * 32);
+    if (st != VSR_OK) return st;
+    k_shadow_rays<<<(unsigned)((n + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const float4*>(prim_rays), reinterpret_cast<const float4*>(prim_hits), n,
+        light[0], light[1], light[2], eps, reinterpret_cast<float4*>(out));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "shadow ray launch");
+    return VSR_OK;
+}
+
+vsr_status vsr_get_device_error(vsr_scene* s, uint32_t* word) {
+    g_err.clear();
+    if (!s || !word) return fail(VSR_ERR_ARG, "null argument");
+    DeviceGuard g(s->device);
+    VSR_CUDA(cudaDeviceSynchronize(), "synchronise");
+    VSR_CUDA(cudaMemcpy(word, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read error word");
+    VSR_CUDA(cudaMemset(s->d_err, 0, sizeof(uint32_t)), "clear error word");
+    return VSR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// Trace kernels with the intersector reached at run time through device
+// function pointers, the "usual function pointer approach" of callback
+// libraries that the paper contrasts with static injection (Sections 1 and
+// 5): the library checks whether a callback is registered and, if so, calls
+// it indirectly for every box test, triangle test and candidate.  The
+// traversal itself is the same template as the static kernels, so the two
+// variants differ only in how the intersector is reached.
+#include "vsr_internal.h"
+
+namespace vsr {
+
+struct DynCounters {
+    uint32_t boxes, tris;
+};
+
+typedef bool (*AcceptFn)(const DevScene*, IsectParams, uint32_t, float, float);
+typedef void (*HookFn)(DynCounters*);
+
+__device__ __noinline__ bool dyn_accept_default(const DevScene*, IsectParams, uint32_t, float,
+                                                float) {
+    return true;
+}
+__device__ __noinline__ bool dyn_accept_alpha(const DevScene* sc, IsectParams ip, uint32_t prim,
+                                              float u, float v) {
+    return alpha_tex_accept(*sc, ip, prim, u, v);
+}
+__device__ __noinline__ bool dyn_accept_proc(const DevScene* sc, IsectParams ip, uint32_t prim,
+                                             float u, float v) {
+    return proc_alpha_accept(*sc, ip, prim, u, v);
+}
+__device__ __noinline__ void dyn_count_box(DynCounters* c) { c->boxes++; }
+__device__ __noinline__ void dyn_count_tri(DynCounters* c) { c->tris++; }
+
+// Registration tables indexed by vsr_isect_kind; a null entry means "no
+// callback registered" and is skipped after the run-time check.
+__device__ AcceptFn g_accept[5] = {nullptr, dyn_accept_default, dyn_accept_alpha,
+                                   dyn_accept_proc, nullptr};
+__device__ HookFn g_on_box[5] = {nullptr, nullptr, nullptr, nullptr, dyn_count_box};
+__device__ HookFn g_on_tri[5] = {nullptr, nullptr, nullptr, nullptr, dyn_count_tri};
+
+struct IsectDynamic {
+    static constexpr bool kCounts = true;
+    static constexpr bool kTexcoords = false;
+    AcceptFn acc = nullptr;
+    HookFn on_box = nullptr, on_tri = nullptr;
+    const DevScene* user = nullptr;
+    DynCounters c{0u, 0u};
+    __device__ __forceinline__ void box() {
+        if (on_box) on_box(&c);
+    }
+    __device__ __forceinline__ void tri() {
+        if (on_tri) on_tri(&c);
+    }
+    __device__ __forceinline__ bool accept(const DevScene&, const IsectParams& ip, uint32_t prim,
+                                           float u, float v) {
+        return acc ? acc(user, ip, prim, u, v) : true;
+    }
+    __device__ __forceinline__ uint2 counters() const { return make_uint2(c.boxes, c.tris); }
+};
+
+template <int Q>
+__global__ void __launch_bounds__(256) k_trace_dyn(DevScene sc, IsectParams ip,
+                                                   const DevScene* __restrict__ user,
+                                                   const float4* __restrict__ rays,
+                                                   unsigned long long n,
+                                                   float4* __restrict__ hits,
+                                                   uint2* __restrict__ counters) {
+    extern __shared__ uint32_t s_stack[];
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Ray r = make_ray(__ldg(rays + 2 * i), __ldg(rays + 2 * i + 1));
+    IsectDynamic h;
+    const uint32_t kind = ip.kind < 5u ? ip.kind : 0u;
+    h.acc = g_accept[kind];
+    h.on_box = g_on_box[kind];
+    h.on_tri = g_on_tri[kind];
+    h.user = user;
+    Best best;
+    Stats st;
+    traverse<Q, IsectDynamic, false>(sc, ip, r, h, best, st, s_stack + threadIdx.x, blockDim.x);
+    hits[i] = hit_record(best);
+    if (counters) counters[i] = h.counters();
+}
+
+cudaError_t launch_dynamic(const LaunchArgs& a, int kind) {
+    (void)kind;
+    const size_t smem = (size_t)a.sc.stack_depth * a.block * sizeof(uint32_t);
+    const unsigned long long grid = (a.n + a.block - 1) / a.block;
+    auto k = (a.query == kClosest) ? k_trace_dyn<kClosest> : k_trace_dyn<kAny>;
+    if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.dyn_user, a.rays, a.n, a.hits,
+                                                     a.counters);
+    return cudaGetLastError();
+}
+
+}  // namespace vsr

@@ -1,0 +1,316 @@
+// Device-side layout, FP32 tests and the while-while traversal with an
+// injected intersector (Zellmann, Section 3.2).
+//
+// Device layout (built by vsr_bvh_load):
+//   nodes  2 x float4 per node: {lo.xyz, ref}, {hi.xyz, 0}.  Siblings are
+//          adjacent and start at an even index, so the two children of an
+//          inner node are one 64-byte aligned pair (4 x 128-bit loads).
+//   ref    packed node reference: inner = (left/2) << 2 | split axis,
+//          leaf = 1 << 31 | first << 3 | (count - 1).
+//   tris   3 x float4 per leaf slot: {v0.xyz, prim id}, {e1.xyz, 0},
+//          {e2.xyz, 0} with e1 = v1 - v0, e2 = v2 - v0, in leaf order.
+//   uvs    3 x float2 per original triangle id; geom: texture id per id.
+//
+// Rounding: the file is compiled with -fmad=false and every product, sum and
+// fused multiply-add below is an explicit __fmul_rn / __fadd_rn / __fmaf_rn,
+// divisions are IEEE (__fdiv_rn) and denormals are kept, so hit distances,
+// barycentrics, box decisions and counts are reproducible bit for bit.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vsr {
+
+constexpr uint32_t kMiss = 0xFFFFFFFFu;
+constexpr uint32_t kLeafBit = 0x80000000u;
+constexpr int kClosest = 0;
+constexpr int kAny = 1;
+
+enum : uint32_t { kTexU8 = 0, kTexRGBA8 = 1, kTexRGBA32F = 2 };
+enum : uint32_t { kErrStack = 1u };
+
+struct TexDesc {
+    uint32_t fmt, w, h, pad;
+    unsigned long long offset;  // byte offset into texels
+    unsigned long long pad2;
+};
+
+// Everything a kernel needs to know about a scene (passed by value).
+struct DevScene {
+    const float4* nodes;
+    const float4* tris;
+    const float2* uvs;
+    const uint32_t* geom;
+    const TexDesc* tex;
+    const uint8_t* texels;
+    uint32_t* err;
+    uint32_t nprims, ntex, root_ref, stack_depth;
+    float4 root_a, root_b;  // root box (lo, hi) in .xyz
+};
+
+struct IsectParams {
+    uint32_t cutoff_u8;
+    float cutoff_f;
+    float freq;
+    uint32_t kind;
+};
+
+// --------------------------------------------------------------------------
+// exact FP32 helpers
+
+__device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by,
+                                      float bz) {
+    return __fmaf_rn(ax, bx, __fmaf_rn(ay, by, __fmul_rn(az, bz)));
+}
+
+struct Ray {
+    float ox, oy, oz, tmin, dx, dy, dz, tmax;
+    float ix, iy, iz;     // guarded inverse direction
+    float nox, noy, noz;  // -(o * inv)
+};
+
+__device__ __forceinline__ float guard_dir(float d) {
+    return fabsf(d) < 0x1p-80f ? copysignf(0x1p-80f, d) : d;
+}
+
+__device__ __forceinline__ Ray make_ray(float4 a, float4 b) {
+    Ray r;
+    r.ox = a.x; r.oy = a.y; r.oz = a.z; r.tmin = a.w;
+    r.dx = b.x; r.dy = b.y; r.dz = b.z; r.tmax = b.w;
+    r.ix = __fdiv_rn(1.0f, guard_dir(b.x));
+    r.iy = __fdiv_rn(1.0f, guard_dir(b.y));
+    r.iz = __fdiv_rn(1.0f, guard_dir(b.z));
+    r.nox = -__fmul_rn(a.x, r.ix);
+    r.noy = -__fmul_rn(a.y, r.iy);
+    r.noz = -__fmul_rn(a.z, r.iz);
+    return r;
+}
+
+// intersect(ray, aabb, inv_dir): slab test over [tmin, tfar].
+__device__ __forceinline__ bool box_hit(const Ray& r, float4 lo, float4 hi, float tfar) {
+    const float t0x = __fmaf_rn(lo.x, r.ix, r.nox), t1x = __fmaf_rn(hi.x, r.ix, r.nox);
+    const float t0y = __fmaf_rn(lo.y, r.iy, r.noy), t1y = __fmaf_rn(hi.y, r.iy, r.noy);
+    const float t0z = __fmaf_rn(lo.z, r.iz, r.noz), t1z = __fmaf_rn(hi.z, r.iz, r.noz);
+    const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), r.tmin));
+    const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tfar));
+    return tn <= tf;
+}
+
+// intersect(ray, basic_triangle<3,float>): Moller-Trumbore with the fixed
+// rounding order.  Returns false when det == 0 (no t, u, v).
+__device__ __forceinline__ bool tri_test(const Ray& r, float4 a, float4 e1, float4 e2,
+                                         float& t, float& u, float& v) {
+    const float px = __fmaf_rn(r.dy, e2.z, -__fmul_rn(r.dz, e2.y));
+    const float py = __fmaf_rn(r.dz, e2.x, -__fmul_rn(r.dx, e2.z));
+    const float pz = __fmaf_rn(r.dx, e2.y, -__fmul_rn(r.dy, e2.x));
+    const float det = dot3(e1.x, e1.y, e1.z, px, py, pz);
+    if (det == 0.0f) return false;
+    const float inv = __fdiv_rn(1.0f, det);
+    const float sx = __fsub_rn(r.ox, a.x), sy = __fsub_rn(r.oy, a.y), sz = __fsub_rn(r.oz, a.z);
+    u = __fmul_rn(dot3(sx, sy, sz, px, py, pz), inv);
+    const float qx = __fmaf_rn(sy, e1.z, -__fmul_rn(sz, e1.y));
+    const float qy = __fmaf_rn(sz, e1.x, -__fmul_rn(sx, e1.z));
+    const float qz = __fmaf_rn(sx, e1.y, -__fmul_rn(sy, e1.x));
+    v = __fmul_rn(dot3(r.dx, r.dy, r.dz, qx, qy, qz), inv);
+    t = __fmul_rn(dot3(e2.x, e2.y, e2.z, qx, qy, qz), inv);
+    return true;
+}
+
+// --------------------------------------------------------------------------
+// intersector arithmetic (Section 4 use cases)
+
+// Interpolated texture coordinate: w0 = (1-u)-v, uv = v*tc2 + (u*tc1 + w0*tc0).
+__device__ __forceinline__ float2 lerp_uv(const float2* __restrict__ uvs, uint32_t prim, float u,
+                                          float v) {
+    const float2 c0 = __ldg(uvs + 3ull * prim), c1 = __ldg(uvs + 3ull * prim + 1),
+                 c2 = __ldg(uvs + 3ull * prim + 2);
+    const float w0 = __fsub_rn(__fsub_rn(1.0f, u), v);
+    float2 r;
+    r.x = __fmaf_rn(v, c2.x, __fmaf_rn(u, c1.x, __fmul_rn(w0, c0.x)));
+    r.y = __fmaf_rn(v, c2.y, __fmaf_rn(u, c1.y, __fmul_rn(w0, c0.y)));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t texel_coord(float c, uint32_t n) {
+    const float cl = fminf(fmaxf(c, 0.0f), 1.0f);
+    const int i = (int)floorf(__fmul_rn(cl, (float)n));
+    return (uint32_t)min(i, (int)n - 1);
+}
+
+// Alpha-mask decision: nearest texel, clamp to edge.
+__device__ __forceinline__ bool alpha_tex_accept(const DevScene& sc, const IsectParams& ip,
+                                                 uint32_t prim, float u, float v) {
+    const uint32_t g = __ldg(sc.geom + prim);
+    if (g == kMiss) return true;
+    const float2 uv = lerp_uv(sc.uvs, prim, u, v);
+    const uint4 d = __ldg(reinterpret_cast<const uint4*>(sc.tex + g));
+    const unsigned long long off = __ldg(&sc.tex[g].offset);
+    const uint32_t i = texel_coord(uv.x, d.y), j = texel_coord(uv.y, d.z);
+    const unsigned long long k = (unsigned long long)j * d.y + i;
+    if (d.x == kTexU8) return __ldg(sc.texels + off + k) >= ip.cutoff_u8;
+    if (d.x == kTexRGBA8) return __ldg(sc.texels + off + 4 * k + 3) >= ip.cutoff_u8;
+    const float a = __ldg(reinterpret_cast<const float*>(sc.texels + off) + 4 * k + 3);
+    return a >= ip.cutoff_f;
+}
+
+// Procedural alpha: accept iff sin(f u) sin(f v) > 0 at the texture coordinate.
+__device__ __forceinline__ bool proc_alpha_accept(const DevScene& sc, const IsectParams& ip,
+                                                  uint32_t prim, float u, float v) {
+    const uint32_t g = __ldg(sc.geom + prim);
+    if (g == kMiss) return true;
+    const float2 uv = lerp_uv(sc.uvs, prim, u, v);
+    const float sa = sinf(__fmul_rn(ip.freq, uv.x));
+    const float sb = sinf(__fmul_rn(ip.freq, uv.y));
+    return __fmul_rn(sa, sb) > 0.0f;
+}
+
+// --------------------------------------------------------------------------
+// statically injected intersectors: hooks on every box test and triangle
+// test, and a verdict on each geometric candidate ("hr.hit &= ...").
+
+struct IsectNone {
+    static constexpr bool kCounts = false;
+    static constexpr bool kTexcoords = false;  // reads geom id and texcoords
+    __device__ __forceinline__ void box() {}
+    __device__ __forceinline__ void tri() {}
+    __device__ __forceinline__ bool accept(const DevScene&, const IsectParams&, uint32_t, float,
+                                           float) {
+        return true;
+    }
+    __device__ __forceinline__ uint2 counters() const { return make_uint2(0, 0); }
+};
+
+// basic_intersector: forwards intersect() unchanged.
+struct IsectDefault : IsectNone {};
+
+struct IsectAlphaTex : IsectNone {
+    static constexpr bool kTexcoords = true;
+    __device__ __forceinline__ bool accept(const DevScene& sc, const IsectParams& ip,
+                                           uint32_t prim, float u, float v) {
+        return alpha_tex_accept(sc, ip, prim, u, v);
+    }
+};
+
+struct IsectProcAlpha : IsectNone {
+    static constexpr bool kTexcoords = true;
+    __device__ __forceinline__ bool accept(const DevScene& sc, const IsectParams& ip,
+                                           uint32_t prim, float u, float v) {
+        return proc_alpha_accept(sc, ip, prim, u, v);
+    }
+};
+
+// bvh_costs: ++num_boxes per box test, ++num_tris per triangle test.
+struct IsectCount : IsectNone {
+    static constexpr bool kCounts = true;
+    uint32_t num_boxes = 0, num_tris = 0;
+    __device__ __forceinline__ void box() { ++num_boxes; }
+    __device__ __forceinline__ void tri() { ++num_tris; }
+    __device__ __forceinline__ uint2 counters() const { return make_uint2(num_boxes, num_tris); }
+};
+
+// Measurement counters: box tests, triangle tests, intersector
+// consultations, and consultations that fetched texture coordinates.
+struct Stats {
+    uint32_t boxes = 0, tris = 0, cands = 0, texs = 0;
+};
+
+struct Best {
+    float t, u, v;
+    uint32_t prim;
+};
+
+// --------------------------------------------------------------------------
+// The while-while traversal.  `stack` points at this thread's column of a
+// shared-memory stack with `stride` words between levels.
+
+template <int Q, class H, bool STATS>
+__device__ __forceinline__ void traverse(const DevScene& sc, const IsectParams& ip, const Ray& r,
+                                         H& h, Best& best, Stats& st, uint32_t* stack,
+                                         uint32_t stride) {
+    best.t = r.tmax;
+    best.u = 0.0f;
+    best.v = 0.0f;
+    best.prim = kMiss;
+    if (sc.nprims == 0) return;
+    h.box();
+    if (STATS) st.boxes++;
+    if (!box_hit(r, sc.root_a, sc.root_b, best.t)) return;
+    uint32_t ref = sc.root_ref;
+    uint32_t sp = 0;
+    for (;;) {  // while ray not terminated
+        while (!(ref & kLeafBit)) {  // while node is inner
+            const float4* p = sc.nodes + 4ull * (ref >> 2);
+            const float4 la = __ldg(p), lb = __ldg(p + 1), ra = __ldg(p + 2), rb = __ldg(p + 3);
+            const float tfar = (Q == kClosest) ? best.t : r.tmax;
+            h.box();
+            h.box();
+            if (STATS) st.boxes += 2;
+            const bool hl = box_hit(r, la, lb, tfar);
+            const bool hr = box_hit(r, ra, rb, tfar);
+            const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(ra.w);
+            if (hl && hr) {
+                const uint32_t axis = ref & 3u;
+                const float da = axis == 0 ? r.dx : (axis == 1 ? r.dy : r.dz);
+                const bool neg = signbit(da);
+                if (sp >= sc.stack_depth) {  // unreachable for a validated blob
+                    atomicOr(sc.err, kErrStack);
+                    best.t = __int_as_float(0x7f800000);
+                    best.prim = kMiss;
+                    return;
+                }
+                stack[sp * stride] = neg ? rl : rr;
+                ++sp;
+                ref = neg ? rr : rl;
+            } else if (hl) {
+                ref = rl;
+            } else if (hr) {
+                ref = rr;
+            } else {
+                if (sp == 0) goto done;
+                --sp;
+                ref = stack[sp * stride];
+            }
+        }
+        {  // found a leaf: test its primitives
+            const uint32_t first = (ref >> 3) & 0x0FFFFFFFu;
+            const uint32_t cnt = (ref & 7u) + 1u;
+            const float4* tp = sc.tris + 3ull * first;
+            for (uint32_t k = 0; k < cnt; ++k) {
+                const float4 a = __ldg(tp + 3 * k), e1 = __ldg(tp + 3 * k + 1),
+                             e2 = __ldg(tp + 3 * k + 2);
+                h.tri();
+                if (STATS) st.tris++;
+                float t, u, v;
+                if (!tri_test(r, a, e1, e2, t, u, v)) continue;
+                const bool geo = u >= 0.0f && v >= 0.0f && __fadd_rn(u, v) <= 1.0f;
+                if (!geo || !(t > r.tmin) || !(t < r.tmax)) continue;
+                const uint32_t prim = __float_as_uint(a.w);
+                if (Q == kClosest) {
+                    if (!(t < best.t || (t == best.t && prim < best.prim))) continue;
+                }
+                if (STATS) {
+                    st.cands++;
+                    if (H::kTexcoords && __ldg(sc.geom + prim) != kMiss) st.texs++;
+                }
+                if (!h.accept(sc, ip, prim, u, v)) continue;
+                best.t = t;
+                best.u = u;
+                best.v = v;
+                best.prim = prim;
+                if (Q == kAny) goto done;
+            }
+        }
+        if (sp == 0) break;
+        --sp;
+        ref = stack[sp * stride];
+    }
+done:
+    if (best.prim == kMiss) best.t = __int_as_float(0x7f800000);
+}
+
+__device__ __forceinline__ float4 hit_record(const Best& b) {
+    return make_float4(b.t, b.u, b.v, __uint_as_float(b.prim));
+}
+
+}  // namespace vsr

@@ -1,0 +1,258 @@
+"""Thin ctypes binding of the GPU library (names as in ``include/vsr.h``).
+
+Argument marshalling only: every step of the traversal runs in the library's
+CUDA kernels.  Device buffers are torch CUDA tensors (PyTorch provides device
+memory and streams).  There is no CPU fallback: if ``libvsr.so`` has not been
+built, loading fails with an error.
+
+Tensor layouts:
+  rays      float32 [n, 8]  (ox, oy, oz, tmin, dx, dy, dz, tmax)
+  hits      float32 [n, 4]  (t, u, v, prim id bits); ``prim_ids(hits)`` gives
+            the uint32 ids as int64 (miss = 0xFFFFFFFF)
+  counters  int32   [n, 2]  (box tests, triangle tests) for the COUNT intersector
+  stats     int32   [n, 4]  (box tests, triangle tests, intersector calls, 0)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+VSR_OK, VSR_ERR_ARG, VSR_ERR_CUDA, VSR_ERR_OOM, VSR_ERR_BLOB, VSR_ERR_STACK, \
+    VSR_ERR_TIMEOUT, VSR_ERR_STATE = range(8)
+STATUS_NAMES = ["VSR_OK", "VSR_ERR_ARG", "VSR_ERR_CUDA", "VSR_ERR_OOM", "VSR_ERR_BLOB",
+                "VSR_ERR_STACK", "VSR_ERR_TIMEOUT", "VSR_ERR_STATE"]
+MISS = 0xFFFFFFFF
+NO_TEXTURE = 0xFFFFFFFF
+ISECT = {"none": 0, "default": 1, "alpha_tex": 2, "proc_alpha": 3, "count": 4}
+DISPATCH = {"static": 0, "dynamic": 1}
+QUERY = {"closest": 0, "any": 1}
+TEX_FMT = {"u8": 0, "rgba8": 1, "rgba32f": 2}
+
+
+class VsrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class vsr_texture_desc(ctypes.Structure):
+    _fields_ = [("fmt", ctypes.c_int32), ("w", ctypes.c_uint32), ("h", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("texels", ctypes.c_void_p)]
+
+
+class vsr_intersector(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dispatch", ctypes.c_int32),
+                ("alpha_cutoff_u8", ctypes.c_uint32), ("alpha_cutoff_f", ctypes.c_float),
+                ("proc_freq", ctypes.c_float), ("reserved", ctypes.c_uint32 * 3)]
+
+
+class vsr_trace_params(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_uint32), ("persistent", ctypes.c_uint32),
+                ("refill_threshold", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+
+
+_lib = None
+P = ctypes.c_void_p
+_SIGS = {
+    "vsr_version": ([], ctypes.c_int32),
+    "vsr_last_error": ([], ctypes.c_char_p),
+    "vsr_scene_create_indexed": ([P, ctypes.c_uint32, P, P, P, ctypes.c_uint32, P,
+                                  ctypes.c_uint32, ctypes.POINTER(P)], ctypes.c_int),
+    "vsr_scene_create": ([P, P, P, ctypes.c_uint32, P, ctypes.c_uint32, ctypes.POINTER(P)],
+                         ctypes.c_int),
+    "vsr_scene_destroy": ([P], ctypes.c_int),
+    "vsr_bvh_load": ([P, P, ctypes.c_size_t], ctypes.c_int),
+    "vsr_trace": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P], ctypes.c_int),
+    "vsr_trace_stats": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P], ctypes.c_int),
+    "vsr_make_shadow_rays": ([P, P, ctypes.c_uint64, P, ctypes.c_float, P, P], ctypes.c_int),
+    "vsr_get_device_error": ([P, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "vsr_bvh_build": ([P, ctypes.c_uint64, P, ctypes.c_uint32, P, ctypes.POINTER(P),
+                       ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "vsr_bvh_free": ([P], None),
+    "vsr_bvh_validate": ([P, ctypes.c_size_t], ctypes.c_int),
+    "vsr_bvh_last_error": ([], ctypes.c_char_p),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libvsr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"GPU library not built: {path} is missing "
+                               "(run __graft_entry__.build())")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != VSR_OK:
+        raise VsrError(status, lib().vsr_last_error().decode())
+
+
+def vsr_last_error() -> str:
+    return lib().vsr_last_error().decode()
+
+
+def vsr_version() -> int:
+    return lib().vsr_version()
+
+
+def intersector(kind="default", dispatch="static", cutoff_u8=128, cutoff_f=0.01,
+                freq=40.0) -> vsr_intersector:
+    return vsr_intersector(ISECT[kind], DISPATCH[dispatch], cutoff_u8, cutoff_f, freq)
+
+
+def trace_params(block_size=128, persistent=0, refill_threshold=16, blocks_per_sm=0):
+    return vsr_trace_params(block_size, persistent, refill_threshold, blocks_per_sm)
+
+
+class Scene:
+    """Owns a ``vsr_scene*``; destroyed with the object or ``close()``."""
+
+    def __init__(self, handle: int, ntri: int):
+        self.handle = handle
+        self.ntri = ntri
+
+    def close(self):
+        if self.handle:
+            lib().vsr_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _tex_array(textures):
+    keep = []
+    arr = (vsr_texture_desc * max(len(textures), 1))()
+    for k, t in enumerate(textures):
+        tx = np.ascontiguousarray(t.texels)
+        keep.append(tx)
+        arr[k] = vsr_texture_desc(TEX_FMT[t.fmt], t.w, t.h, 0, tx.ctypes.data)
+    return arr, keep
+
+
+def vsr_scene_create_indexed(verts, idx, uvs, geom_id, textures) -> Scene:
+    """Copy indexed host geometry, texture coordinates and textures to the
+    current CUDA device."""
+    v = np.ascontiguousarray(verts, np.float32).reshape(-1, 3)
+    i = np.ascontiguousarray(idx, np.uint32).reshape(-1, 3)
+    uv = np.ascontiguousarray(uvs, np.float32).reshape(-1, 3, 2)
+    g = np.ascontiguousarray(geom_id, np.uint32).reshape(-1)
+    tarr, keep = _tex_array(textures)
+    out = P()
+    st = lib().vsr_scene_create_indexed(v.ctypes.data, v.shape[0], i.ctypes.data, uv.ctypes.data,
+                                        g.ctypes.data, i.shape[0], tarr, len(textures),
+                                        ctypes.byref(out))
+    del keep
+    _check(st)
+    return Scene(out.value, i.shape[0])
+
+
+def vsr_scene_create(verts_xyz, uvs, geom_id, textures) -> Scene:
+    v = np.ascontiguousarray(verts_xyz, np.float32).reshape(-1, 9)
+    uv = np.ascontiguousarray(uvs, np.float32).reshape(-1, 3, 2)
+    g = np.ascontiguousarray(geom_id, np.uint32).reshape(-1)
+    tarr, keep = _tex_array(textures)
+    out = P()
+    st = lib().vsr_scene_create(v.ctypes.data, uv.ctypes.data, g.ctypes.data, v.shape[0], tarr,
+                                len(textures), ctypes.byref(out))
+    del keep
+    _check(st)
+    return Scene(out.value, v.shape[0])
+
+
+def vsr_scene_destroy(scene: Scene):
+    scene.close()
+
+
+def vsr_bvh_load(scene: Scene, blob: np.ndarray):
+    b = np.ascontiguousarray(blob, np.uint8)
+    _check(lib().vsr_bvh_load(scene.handle, b.ctypes.data if b.size else None, b.size))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def vsr_trace(scene: Scene, rays, isect: vsr_intersector, query, hits, counters=None,
+              params: vsr_trace_params | None = None, stream=None):
+    """Trace ``rays`` (cuda float32 [n,8]) into ``hits`` (cuda float32 [n,4])."""
+    q = QUERY[query] if isinstance(query, str) else int(query)
+    n = int(rays.shape[0])
+    _check(lib().vsr_trace(scene.handle, _ptr(rays), n, ctypes.byref(isect), q, _ptr(hits),
+                           _ptr(counters), ctypes.byref(params) if params else None,
+                           _stream(stream)))
+
+
+def vsr_trace_stats(scene: Scene, rays, isect: vsr_intersector, query, hits, stats,
+                    stream=None):
+    q = QUERY[query] if isinstance(query, str) else int(query)
+    _check(lib().vsr_trace_stats(scene.handle, _ptr(rays), int(rays.shape[0]),
+                                 ctypes.byref(isect), q, _ptr(hits), _ptr(stats),
+                                 _stream(stream)))
+
+
+def vsr_make_shadow_rays(prim_rays, prim_hits, light, eps: float, out, stream=None):
+    l = (ctypes.c_float * 3)(*[float(x) for x in light])
+    _check(lib().vsr_make_shadow_rays(_ptr(prim_rays), _ptr(prim_hits), int(prim_rays.shape[0]),
+                                      l, float(eps), _ptr(out), _stream(stream)))
+
+
+def vsr_get_device_error(scene: Scene) -> int:
+    w = ctypes.c_uint32()
+    _check(lib().vsr_get_device_error(scene.handle, ctypes.byref(w)))
+    return int(w.value)
+
+
+# ---------------------------------------------------------------- helpers
+
+
+def prim_ids(hits):
+    """uint32 primitive ids of a float32 [n,4] hit tensor, as int64."""
+    import torch
+    return hits.contiguous().view(torch.int32)[:, 3].to(torch.int64) & 0xFFFFFFFF
+
+
+def scene_from_inputs(sc, blob: np.ndarray) -> Scene:
+    """Upload a generated scene (``inputs.scenes.Scene``) and its BVH blob."""
+    s = vsr_scene_create_indexed(sc.verts, sc.idx, sc.uvs, sc.geom_id, sc.textures)
+    vsr_bvh_load(s, blob)
+    return s
+
+
+def trace(scene: Scene, rays, kind="default", query="closest", dispatch="static",
+          counters=False, params=None, stream=None, **kw):
+    """Allocate hits (and counters for COUNT) and trace; returns (hits, counters)."""
+    import torch
+    n = rays.shape[0]
+    hits = torch.empty((n, 4), dtype=torch.float32, device=rays.device)
+    cnt = torch.empty((n, 2), dtype=torch.int32, device=rays.device) if counters else None
+    vsr_trace(scene, rays, intersector(kind, dispatch, **kw), query, hits, cnt, params, stream)
+    return hits, cnt
