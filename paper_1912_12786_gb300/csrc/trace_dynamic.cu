@@ -5,16 +5,17 @@
 // it indirectly for every box test, triangle test and candidate.  The
 // traversal itself is the same template as the static kernels, so the two
 // variants differ only in how the intersector is reached.
+#include <mutex>
+
 #include "vsr_internal.h"
 
 namespace vsr {
 
-struct DynCounters {
-    uint32_t boxes, tris;
-};
-
 typedef bool (*AcceptFn)(const DevScene*, IsectParams, uint32_t, float, float);
-typedef void (*HookFn)(DynCounters*);
+// Counting callbacks take the running count by value and return it
+// incremented, so no callback ever receives a pointer into the caller's
+// local memory.
+typedef uint32_t (*CountFn)(uint32_t);
 
 __device__ __noinline__ bool dyn_accept_default(const DevScene*, IsectParams, uint32_t, float,
                                                 float) {
@@ -28,34 +29,48 @@ __device__ __noinline__ bool dyn_accept_proc(const DevScene* sc, IsectParams ip,
                                              float u, float v) {
     return proc_alpha_accept(*sc, ip, prim, u, v);
 }
-__device__ __noinline__ void dyn_count_box(DynCounters* c) { c->boxes++; }
-__device__ __noinline__ void dyn_count_tri(DynCounters* c) { c->tris++; }
+__device__ __noinline__ uint32_t dyn_count_box(uint32_t n) { return n + 1u; }
+__device__ __noinline__ uint32_t dyn_count_tri(uint32_t n) { return n + 1u; }
 
 // Registration tables indexed by vsr_isect_kind; a null entry means "no
-// callback registered" and is skipped after the run-time check.
-__device__ AcceptFn g_accept[5] = {nullptr, dyn_accept_default, dyn_accept_alpha,
-                                   dyn_accept_proc, nullptr};
-__device__ HookFn g_on_box[5] = {nullptr, nullptr, nullptr, nullptr, dyn_count_box};
-__device__ HookFn g_on_tri[5] = {nullptr, nullptr, nullptr, nullptr, dyn_count_tri};
+// callback registered" and is skipped after the run-time check.  They are
+// filled on the device by k_dyn_register before the first dynamic trace.
+__device__ AcceptFn g_accept[5];
+__device__ CountFn g_on_box[5];
+__device__ CountFn g_on_tri[5];
+
+__global__ void k_dyn_register() {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int k = 0; k < 5; ++k) {
+        g_accept[k] = nullptr;
+        g_on_box[k] = nullptr;
+        g_on_tri[k] = nullptr;
+    }
+    g_accept[1] = dyn_accept_default;
+    g_accept[2] = dyn_accept_alpha;
+    g_accept[3] = dyn_accept_proc;
+    g_on_box[4] = dyn_count_box;
+    g_on_tri[4] = dyn_count_tri;
+}
 
 struct IsectDynamic {
     static constexpr bool kCounts = true;
     static constexpr bool kTexcoords = false;
     AcceptFn acc = nullptr;
-    HookFn on_box = nullptr, on_tri = nullptr;
+    CountFn on_box = nullptr, on_tri = nullptr;
     const DevScene* user = nullptr;
-    DynCounters c{0u, 0u};
+    uint32_t boxes = 0, tris = 0;
     __device__ __forceinline__ void box() {
-        if (on_box) on_box(&c);
+        if (on_box) boxes = on_box(boxes);
     }
     __device__ __forceinline__ void tri() {
-        if (on_tri) on_tri(&c);
+        if (on_tri) tris = on_tri(tris);
     }
     __device__ __forceinline__ bool accept(const DevScene&, const IsectParams& ip, uint32_t prim,
                                            float u, float v) {
         return acc ? acc(user, ip, prim, u, v) : true;
     }
-    __device__ __forceinline__ uint2 counters() const { return make_uint2(c.boxes, c.tris); }
+    __device__ __forceinline__ uint2 counters() const { return make_uint2(boxes, tris); }
 };
 
 template <int Q>
@@ -82,8 +97,27 @@ __global__ void __launch_bounds__(256) k_trace_dyn(DevScene sc, IsectParams ip,
     if (counters) counters[i] = h.counters();
 }
 
+namespace {
+std::mutex g_reg_mutex;
+bool g_registered[64] = {};
+}  // namespace
+
 cudaError_t launch_dynamic(const LaunchArgs& a, int kind) {
     (void)kind;
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(g_reg_mutex);
+        if (!g_registered[dev]) {
+            k_dyn_register<<<1, 1>>>();
+            e0 = cudaGetLastError();
+            if (e0 == cudaSuccess) e0 = cudaDeviceSynchronize();
+            if (e0 != cudaSuccess) return e0;
+            g_registered[dev] = true;
+        }
+    }
     const size_t smem = (size_t)a.sc.stack_depth * a.block * sizeof(uint32_t);
     const unsigned long long grid = (a.n + a.block - 1) / a.block;
     auto k = (a.query == kClosest) ? k_trace_dyn<kClosest> : k_trace_dyn<kAny>;
