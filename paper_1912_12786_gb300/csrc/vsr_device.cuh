@@ -225,9 +225,9 @@ struct Best {
 // shared-memory stack with `stride` words between levels.
 
 template <int Q, class H, bool STATS>
-__device__ __forceinline__ void traverse(const DevScene& sc, const IsectParams& ip, const Ray& r,
-                                         H& h, Best& best, Stats& st, uint32_t* stack,
-                                         uint32_t stride) {
+__device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectParams& ip,
+                                              const Ray& r, H& h, Best& best, Stats& st,
+                                              uint32_t* stack, uint32_t stride) {
     best.t = r.tmax;
     best.u = 0.0f;
     best.v = 0.0f;
@@ -255,7 +255,6 @@ __device__ __forceinline__ void traverse(const DevScene& sc, const IsectParams& 
                 const bool neg = signbit(da);
                 if (sp >= sc.stack_depth) {  // unreachable for a validated blob
                     atomicOr(sc.err, kErrStack);
-                    best.t = __int_as_float(0x7f800000);
                     best.prim = kMiss;
                     return;
                 }
@@ -267,7 +266,7 @@ __device__ __forceinline__ void traverse(const DevScene& sc, const IsectParams& 
             } else if (hr) {
                 ref = rr;
             } else {
-                if (sp == 0) goto done;
+                if (sp == 0) return;
                 --sp;
                 ref = stack[sp * stride];
             }
@@ -298,15 +297,27 @@ __device__ __forceinline__ void traverse(const DevScene& sc, const IsectParams& 
                 best.u = u;
                 best.v = v;
                 best.prim = prim;
-                if (Q == kAny) goto done;
+                if (Q == kAny) return;
             }
         }
-        if (sp == 0) break;
+        if (sp == 0) return;
         --sp;
         ref = stack[sp * stride];
     }
-done:
-    if (best.prim == kMiss) best.t = __int_as_float(0x7f800000);
+}
+
+// Full query: traversal, then every miss (root missed, empty or inactive
+// interval, nothing accepted) is reported as t = +inf, u = v = 0.
+template <int Q, class H, bool STATS>
+__device__ __forceinline__ void traverse(const DevScene& sc, const IsectParams& ip, const Ray& r,
+                                         H& h, Best& best, Stats& st, uint32_t* stack,
+                                         uint32_t stride) {
+    traverse_body<Q, H, STATS>(sc, ip, r, h, best, st, stack, stride);
+    if (best.prim == kMiss) {
+        best.t = __int_as_float(0x7f800000);
+        best.u = 0.0f;
+        best.v = 0.0f;
+    }
 }
 
 __device__ __forceinline__ float4 hit_record(const Best& b) {
