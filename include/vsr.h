@@ -27,7 +27,10 @@
  *     vsr_last_error() gives a message for the calling thread;
  *   - "device" pointers must be CUDA device (or managed) memory on the
  *     scene's device; they are checked with cudaPointerGetAttributes and a
- *     host pointer is rejected, never dereferenced by a kernel;
+ *     host pointer is rejected, never dereferenced by a kernel; a buffer
+ *     that ends past its CUDA allocation is rejected (the check sees whole
+ *     allocations: a buffer carved from a larger allocation, as caching
+ *     allocators do, is only checked against the enclosing allocation);
  *   - work is enqueued on the given stream and is asynchronous unless stated;
  *   - CUDA failures map to VSR_ERR_CUDA, allocation failures to VSR_ERR_OOM.
  *

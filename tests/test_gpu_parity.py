@@ -8,7 +8,9 @@ boundary) may differ in primitive id and are reported; every other ray must
 match exactly, and t must in any case agree within 1e-5 relative when the ids
 agree.
 """
+import ctypes
 import math
+import os
 
 import numpy as np
 import pytest
@@ -30,6 +32,25 @@ def V():
     from paper_1912_12786_gb300 import _build, vsr
     _build.build()
     return vsr
+
+
+def _cudart():
+    import ctypes.util
+    import glob
+    cands = [ctypes.util.find_library("cudart"), "/usr/local/cuda/lib64/libcudart.so"]
+    cands += glob.glob(os.path.join(os.path.dirname(torch.__file__), "..", "nvidia", "*",
+                                    "lib", "libcudart.so*"))
+    for c in cands:
+        if not c:
+            continue
+        try:
+            lib = ctypes.CDLL(c)
+        except OSError:
+            continue
+        lib.cudaMalloc.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t]
+        lib.cudaFree.argtypes = [ctypes.c_void_p]
+        return lib
+    return None
 
 
 def _to_dev(a):
@@ -186,14 +207,23 @@ def test_invalid_arguments_rejected_before_launch(V, small):
     hits = torch.empty((len(rays), 4), dtype=torch.float32, device="cuda")
     isect = V.intersector("alpha_tex")
     host = np.zeros((len(rays), 8), np.float32)
-    import ctypes
     L = V.lib()
     st = L.vsr_trace(s.handle, host.ctypes.data, len(rays), ctypes.byref(isect), 0,
                      hits.data_ptr(), None, None, None)
     assert st == V.VSR_ERR_ARG and "device memory" in V.vsr_last_error()
-    small_hits = torch.empty((16, 4), dtype=torch.float32, device="cuda")
-    with pytest.raises(V.VsrError, match="smaller"):
-        V.vsr_trace(s, r, isect, "closest", small_hits)
+    # A buffer from cudaMalloc that is too small for n hits is rejected.  (The
+    # check sees whole allocations, so it is made with a raw allocation rather
+    # than a tensor carved from the caching allocator's larger blocks.)
+    rt = _cudart()
+    if rt is not None:
+        raw = ctypes.c_void_p()
+        assert rt.cudaMalloc(ctypes.byref(raw), ctypes.c_size_t(256)) == 0
+        try:
+            st = L.vsr_trace(s.handle, r.data_ptr(), len(rays), ctypes.byref(isect), 0,
+                             raw.value, None, None, None)
+            assert st == V.VSR_ERR_ARG and "smaller" in V.vsr_last_error()
+        finally:
+            rt.cudaFree(raw)
     cnt = torch.empty((len(rays), 2), dtype=torch.int32, device="cuda")
     with pytest.raises(V.VsrError, match="COUNT"):
         V.vsr_trace(s, r, isect, "closest", hits, cnt)
