@@ -41,7 +41,8 @@ METRIC = "Mrays/s alpha any-hit vs default intersector; fwd+bwd Mrays/s; % of L2
 WORKLOAD = ("billboard forest: 500,000 alpha-masked billboards (1,000,002 triangles, "
             "4 RGBA8 1024^2 textures), 1920x1080 primary closest-hit + 1920x1080 shadow "
             "any-hit rays, alpha-texture intersector (cutoff 128)")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_traffic.json")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "trace_closest_alpha_billboard_forest.md")
+ALU_LANES_PER_SM = 64  # ALU pipe (min/max, compares, integer): 16 lanes per SMSP
 FLUSH_BYTES = 256 << 20
 
 
@@ -140,6 +141,39 @@ def trace_bytes(n_rays: int, stats: np.ndarray, texel_bytes: int, texcoords: boo
     return b
 
 
+def trace_alu_ops(n_rays: int, stats: np.ndarray, texcoords: bool) -> int:
+    """Algorithmic operations of one launch on the ALU pipe (the busiest unit):
+    13 per box test (12 min/max of the slab test + 1 compare), 7 per triangle
+    test (det == 0, u >= 0, v >= 0, u + v <= 1, t > tmin, t < tmax, t < best),
+    1 per intersector call, 6 per ray set-up (direction guards), and for alpha
+    intersectors 8 per texture fetch (clamps, index bounds, alpha compare)."""
+    s = stats.astype(np.int64).sum(axis=0)
+    ops = 6 * n_rays + 13 * int(s[0]) + 7 * int(s[1]) + int(s[2])
+    if texcoords:
+        ops += 8 * int(s[3])
+    return ops
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    vals = {}
+    with open(PROFILE_SUMMARY) as f:
+        for line in f:
+            if ":" in line and line.startswith("    "):
+                k, v = line.strip().split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel") != kernel or vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return int(vals["traffic_bytes_per_launch"])
+
+
+def sm_count(torch, dev) -> int:
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
 # --------------------------------------------------------------------------
 # distributed set-up (one process per GPU; every rank traces its own frame)
 
@@ -174,16 +208,17 @@ def barrier(world):
 # CPU oracle leg
 
 
-def oracle_sample(sc, rays, blob, stride: int, repeats: int = 1):
-    """Time the oracle on every `stride`-th pixel: primary closest-hit and
-    shadow any-hit with the alpha-texture intersector, all host cores."""
+def oracle_sample(sc, rays, blob, stride: int, min_seconds: float = 0.0, max_repeats: int = 64):
+    """Time the oracle on every `stride`-th pixel -- primary closest-hit and
+    shadow any-hit with the alpha-texture intersector, all host cores --
+    repeating the sample until at least `min_seconds` of traversal time."""
     from oracle import oracle as O
     from paper_1912_12786_gb300.inputs import scenes
     sel = rays[::stride]
     cores = len(os.sched_getaffinity(0))
     light, eps = scenes.light_dir_f32(), scenes.shadow_eps(sc)
-    elapsed, traced = 0.0, 0
-    for _ in range(repeats):
+    elapsed, traced, reps = 0.0, 0, 0
+    while reps < max_repeats and (reps == 0 or elapsed < min_seconds):
         t0 = time.perf_counter()
         h, _ = O.trace_bvh(sc, blob, sel, "alpha_tex", "closest", nthreads=cores)
         t1 = time.perf_counter()
@@ -193,7 +228,8 @@ def oracle_sample(sc, rays, blob, stride: int, repeats: int = 1):
         t3 = time.perf_counter()
         elapsed += (t1 - t0) + (t3 - t2)
         traced += 2 * len(sel)
-    return traced / elapsed / 1e6, cores, len(sel), elapsed
+        reps += 1
+    return traced / elapsed / 1e6, cores, len(sel), elapsed, reps
 
 
 def run_reference(args):
@@ -209,13 +245,14 @@ def run_reference(args):
     times, traced = [], 0
     cores = len(os.sched_getaffinity(0))
     for _ in range(args.steps):
-        _, cores, nsel, el = oracle_sample(sc, rays, blob, stride)
+        _, cores, nsel, el, _ = oracle_sample(sc, rays, blob, stride)
         times.append(el)
         traced += 2 * nsel
     total = sum(times)
     value = traced / total / 1e6
     sample = (f"every {stride}th pixel of the 1920x1080 frame ({len(rays[::stride])} primary + "
-              f"as many shadow rays per step), alpha-texture closest + any hit")
+              f"as many shadow rays per step), alpha-texture closest + any hit, "
+              f"{total:.1f} s of traversal over {args.steps} steps")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mrays/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -303,26 +340,34 @@ def run_ours(args):
     V.vsr_trace_stats(s, rays_s, alpha, "any", tmp, st_s)
     torch.cuda.synchronize(dev)
     assert torch.equal(tmp.view(torch.int32), hits_s.view(torch.int32))
-    b_prim = trace_bytes(n, st_p.cpu().numpy().view(np.uint32), 4, True)
-    b_shad = trace_bytes(n, st_s.cpu().numpy().view(np.uint32), 4, True)
+    sp_np = st_p.cpu().numpy().view(np.uint32)
+    ss_np = st_s.cpu().numpy().view(np.uint32)
     kernels = {
-        "trace closest alpha (primary)": (statistics.mean(prim_ms), b_prim),
-        "trace any alpha (shadow)": (statistics.mean(shad_ms), b_shad),
+        "trace closest alpha (primary)": (statistics.mean(prim_ms), trace_bytes(n, sp_np, 4, True),
+                                          trace_alu_ops(n, sp_np, True)),
+        "trace any alpha (shadow)": (statistics.mean(shad_ms), trace_bytes(n, ss_np, 4, True),
+                                     trace_alu_ops(n, ss_np, True)),
     }
     dom = max(kernels, key=lambda k: kernels[k][0])
-    dom_ms, dom_bytes = kernels[dom]
-    peak, peak_src = peaks()
-    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
-    traffic = None
-    if os.path.exists(TRAFFIC_FILE):
-        with open(TRAFFIC_FILE) as f:
-            tr = json.load(f)
-        if tr.get("kernel_source_hash") == kernel_source_hash() and tr.get("kernel") == dom:
-            traffic = tr.get("traffic_bytes_per_launch")
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
-                "algorithmic_bytes_per_launch": dom_bytes, "peak_source": peak_src,
+    dom_ms, dom_bytes, dom_ops = kernels[dom]
+    hbm_peak, peak_src = peaks()
+    clk_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    alu_peak = sm_count(torch, dev) * ALU_LANES_PER_SM * clk_mhz * 1e6 / 1e12
+    alu_achieved = dom_ops / (dom_ms / 1e3) / 1e12
+    traffic = profiled_traffic(dom)
+    roofline = {"bound": "alu", "achieved": round(alu_achieved, 3), "peak": round(alu_peak, 3),
+                "unit": "Top/s", "frac": round(alu_achieved / alu_peak, 4), "traffic": traffic,
+                "kernel": dom, "algorithmic_ops_per_launch": dom_ops,
+                "peak_source": f"{sm_count(torch, dev)} SMs x {ALU_LANES_PER_SM} ALU lanes x "
+                               f"{clk_mhz:.0f} MHz",
                 "launch_ms": round(dom_ms, 4)}
+    mem = {"algorithmic_bytes_per_launch": dom_bytes,
+           "algorithmic_GBs": round(dom_bytes / (dom_ms / 1e3) / 1e9, 1),
+           "hbm_peak_GBs": hbm_peak, "hbm_peak_source": peak_src}
+    if traffic is not None:
+        hbm = traffic / (dom_ms / 1e3) / 1e9
+        mem.update({"hbm_traffic_bytes_per_launch": traffic, "hbm_achieved_GBs": round(hbm, 1),
+                    "hbm_frac": round(hbm / hbm_peak, 4)})
 
     out = {"metric": METRIC, "value": round(value, 2), "unit": "Mrays/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
@@ -332,7 +377,7 @@ def run_ours(args):
                       "triangles": sc.ntri, "block_size": p.block_size,
                       "persistent": p.persistent, "l2": "flushed between steps (256 MiB write)",
                       "parallelism": f"replicas x{world} (each rank traces its own frame)"},
-           "roofline": roofline, "gpu_launches": 3 * args.steps,
+           "roofline": roofline, "roofline_memory": mem, "gpu_launches": 3 * args.steps,
            "wall_s_timed_region": round(wall, 3),
            "kernel_ms": {"trace_primary": round(statistics.mean(prim_ms), 4),
                          "shadow_rays": round(statistics.mean(gen_ms), 4),
@@ -370,11 +415,13 @@ def run_ours(args):
         out["breakdown"] = breakdown(V, s, d_rays, rays_s, n, flush, stream, torch)
 
     if rank == 0 and not args.no_cpu:
-        mr, cores, nsel, el = oracle_sample(sc, rays, blob, args.ref_stride)
+        mr, cores, nsel, el, reps = oracle_sample(sc, rays, blob, args.ref_stride,
+                                                  min_seconds=10.0)
         out["cpu_baseline"] = {"value": round(mr, 4), "unit": "Mrays/s", "cores": cores,
                                "kind": "oracle",
-                               "sample": f"every {args.ref_stride}th pixel ({nsel} primary + "
-                                         f"{nsel} shadow rays, {el:.1f} s)"}
+                               "sample": f"every {args.ref_stride}th pixel of the frame ({nsel} "
+                                         f"primary + {nsel} shadow rays) x {reps} repeats, "
+                                         f"{el:.1f} s of traversal"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     s.close()
@@ -423,7 +470,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--ref-stride", type=int, default=8)
+    ap.add_argument("--ref-stride", type=int, default=1)
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
