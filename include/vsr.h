@@ -228,8 +228,12 @@ vsr_status vsr_make_shadow_rays(const vsr_ray* prim_rays, const vsr_hit* prim_hi
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* vsr_last_error(void);
 
-/* Read and clear the scene's device error word (bit 0: a traversal stack
- * overflowed and the ray was terminated as a miss).  Synchronous. */
+/* Read and clear the scene's device error word.  Bit 0: a traversal stack
+ * overflowed; bit 1: a ray visited more nodes than the BVH holds.  Either
+ * ends that ray as a miss; neither can happen with a validated blob (each
+ * node is visited at most once per ray), the checks exist so that a
+ * corrupted structure gives an error instead of a fault or an endless loop.
+ * Synchronous. */
 vsr_status vsr_get_device_error(vsr_scene* scene, uint32_t* word);
 
 /* Library version, e.g. 100 for 0.1.0. */

@@ -412,6 +412,7 @@ vsr_status vsr_bvh_load(vsr_scene* s, const void* blob, size_t bytes) {
     d.ntex = s->ntex;
     d.root_ref = node_ref(nodes[0]);
     d.stack_depth = max_depth > 0 ? max_depth : 1u;
+    d.max_steps = num_nodes + 2u;
     d.root_a = make_float4(nodes[0].lo[0], nodes[0].lo[1], nodes[0].lo[2], 0.0f);
     d.root_b = make_float4(nodes[0].hi[0], nodes[0].hi[1], nodes[0].hi[2], 0.0f);
     if ((e = cudaMemcpy(s->d_user, &d, sizeof(DevScene), cudaMemcpyHostToDevice)) != cudaSuccess) {

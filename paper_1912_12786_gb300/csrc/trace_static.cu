@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
     Best best;
     Stats st;
     H h;
-    uint32_t ref = 0, sp = 0;
+    uint32_t ref = 0, sp = 0, steps = 0;
 
     for (;;) {
         const uint32_t busy = __ballot_sync(0xFFFFFFFFu, has);
@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
                     best.u = best.v = 0.0f;
                     best.prim = kMiss;
                     sp = 0;
+                    steps = 0;
                     has = true;
                     if (sc.nprims == 0) {
                         ref = kLeafBit;  // finishes below with no work
@@ -106,6 +107,12 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
         // test it, pop the next node.
         bool done = false;
         while (!(ref & kLeafBit)) {
+            if (++steps > sc.max_steps) {
+                atomicOr(sc.err, kErrSteps);
+                best.prim = kMiss;
+                done = true;
+                break;
+            }
             const float4* p = sc.nodes + 4ull * (ref >> 2);
             const float4 la = __ldg(p), lb = __ldg(p + 1), ra = __ldg(p + 2), rb = __ldg(p + 3);
             const float tfar = (Q == kClosest) ? best.t : r.tmax;
@@ -140,6 +147,11 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
                 --sp;
                 ref = stack[sp * stride];
             }
+        }
+        if (!done && ++steps > sc.max_steps) {
+            atomicOr(sc.err, kErrSteps);
+            best.prim = kMiss;
+            done = true;
         }
         if (!done) {
             const uint32_t first = (ref >> 3) & 0x0FFFFFFFu;

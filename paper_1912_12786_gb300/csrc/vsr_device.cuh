@@ -28,7 +28,10 @@ constexpr int kClosest = 0;
 constexpr int kAny = 1;
 
 enum : uint32_t { kTexU8 = 0, kTexRGBA8 = 1, kTexRGBA32F = 2 };
-enum : uint32_t { kErrStack = 1u };
+// Device error word bits.  Neither can happen for a validated blob; the
+// checks turn a corrupted structure into an error instead of a fault or an
+// endless loop.
+enum : uint32_t { kErrStack = 1u, kErrSteps = 2u };
 
 struct TexDesc {
     uint32_t fmt, w, h, pad;
@@ -46,6 +49,8 @@ struct DevScene {
     const uint8_t* texels;
     uint32_t* err;
     uint32_t nprims, ntex, root_ref, stack_depth;
+    uint32_t max_steps;     // node visits per ray never exceed the node count
+    uint32_t pad[3];
     float4 root_a, root_b;  // root box (lo, hi) in .xyz
 };
 
@@ -238,8 +243,14 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
     if (!box_hit(r, sc.root_a, sc.root_b, best.t)) return;
     uint32_t ref = sc.root_ref;
     uint32_t sp = 0;
+    uint32_t steps = 0;
     for (;;) {  // while ray not terminated
         while (!(ref & kLeafBit)) {  // while node is inner
+            if (++steps > sc.max_steps) {
+                atomicOr(sc.err, kErrSteps);
+                best.prim = kMiss;
+                return;
+            }
             const float4* p = sc.nodes + 4ull * (ref >> 2);
             const float4 la = __ldg(p), lb = __ldg(p + 1), ra = __ldg(p + 2), rb = __ldg(p + 3);
             const float tfar = (Q == kClosest) ? best.t : r.tmax;
@@ -272,6 +283,11 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
             }
         }
         {  // found a leaf: test its primitives
+            if (++steps > sc.max_steps) {
+                atomicOr(sc.err, kErrSteps);
+                best.prim = kMiss;
+                return;
+            }
             const uint32_t first = (ref >> 3) & 0x0FFFFFFFu;
             const uint32_t cnt = (ref & 7u) + 1u;
             const float4* tp = sc.tris + 3ull * first;
