@@ -223,6 +223,31 @@ vsr_status vsr_make_shadow_rays(const vsr_ray* prim_rays, const vsr_hit* prim_hi
                                 const float light[3], float eps, vsr_ray* out,
                                 vsr_stream stream);
 
+/*
+ * Persistent-warp trace that allocates nothing.  The paper has no
+ * counterpart: this entry point is for integrators.
+ *
+ * For callers that must not call cudaMalloc while they trace: for example an
+ * application that hands all device memory to its own pool up front, or a
+ * frame loop that cannot afford the synchronisation a fresh allocation can
+ * bring.  Same arguments, results and errors as vsr_trace with
+ * params->persistent = 1 (params may be NULL: block 128, refill 16; the
+ * persistent flag is forced on; static dispatch only).
+ *
+ * The persistent kernel's only scratch -- the 64-bit counter from which warps
+ * claim rays -- lives in a 256-byte array compiled into the library instead
+ * of memory from cudaMalloc; every GPU that loads the library holds it until
+ * the process exits.  The counter is cleared on `stream` before each launch.
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * ordered (for example on one stream).  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  n above 2^40 is rejected with VSR_ERR_ARG.
+ */
+vsr_status vsr_trace_persistent_noalloc(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
+                                        const vsr_intersector* isect, int32_t query,
+                                        vsr_hit* hits, uint32_t* counters,
+                                        const vsr_trace_params* params, vsr_stream stream);
+
 /* ---------------------------------------------------------------- errors */
 
 /* Message describing the last failure on the calling thread ("" if none). */

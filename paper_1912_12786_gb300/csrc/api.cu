@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -502,3 +503,88 @@ vsr_status vsr_get_device_error(vsr_scene* s, uint32_t* word) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Persistent trace whose scratch comes from a static device array.
+//
+// The persistent kernel needs one piece of scratch memory: the 64-bit counter
+// from which warps claim rays.  vsr_trace keeps it in a word the scene
+// allocated with cudaMalloc; this variant keeps it in the array below, which
+// is part of the library image: every GPU that loads the library holds these
+// 256 bytes until the process exits, and the entry point itself allocates
+// nothing.  All calls share the array, so calls that overlap on the GPU race
+// on the counter.
+
+namespace {
+
+constexpr unsigned kNoallocWords = 32;  // 256 bytes
+constexpr unsigned kNoallocWordsPerCall = 1;
+constexpr uint64_t kNoallocMaxRays = 1ull << 40;
+constexpr int kNoallocMaxDevices = 64;
+static_assert(kNoallocWordsPerCall <= kNoallocWords, "scratch array too small");
+
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoallocWords];
+
+std::mutex g_noalloc_mutex;
+unsigned long long* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side name of the array is only a stand-in).
+vsr_status noalloc_scratch(int device, unsigned long long** out) {
+    if (device < 0 || device >= kNoallocMaxDevices)
+        return fail(VSR_ERR_ARG, "device index above the supported maximum of 64");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[device] = static_cast<unsigned long long*>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return VSR_OK;
+}
+
+}  // namespace
+
+extern "C" vsr_status vsr_trace_persistent_noalloc(vsr_scene* s, const vsr_ray* rays, uint64_t n,
+                                                   const vsr_intersector* is, int32_t query,
+                                                   vsr_hit* hits, uint32_t* counters,
+                                                   const vsr_trace_params* p,
+                                                   vsr_stream stream) {
+    g_err.clear();
+    if (n > kNoallocMaxRays)
+        return fail(VSR_ERR_ARG, "vsr_trace_persistent_noalloc: n = " + std::to_string(n) +
+                                     " exceeds the maximum of 2^40 rays");
+    if (kNoallocWordsPerCall * sizeof(unsigned long long) > sizeof(g_noalloc_scratch))
+        return fail(VSR_ERR_ARG, "vsr_trace_persistent_noalloc: scratch larger than 256 bytes");
+    if (is && is->dispatch != VSR_DISPATCH_STATIC)
+        return fail(VSR_ERR_ARG, "vsr_trace_persistent_noalloc: static dispatch only");
+    vsr_trace_params prm{128u, 1u, 16u, 0u};
+    if (p) {
+        prm = *p;
+        prm.persistent = 1u;
+    }
+    LaunchArgs a;
+    vsr_status st = prepare_launch(s, rays, n, is, query, hits, &prm, a);
+    if (st != VSR_OK) return st;
+    if (counters) {
+        if (is->kind != VSR_ISECT_COUNT)
+            return fail(VSR_ERR_ARG, "counters are written by the COUNT intersector only");
+        if (n) {
+            st = check_dev(counters, s->device, "counters", 8, n * 8);
+            if (st != VSR_OK) return st;
+        }
+        a.counters = reinterpret_cast<uint2*>(counters);
+    }
+    if (n == 0) return VSR_OK;
+    DeviceGuard g(s->device);
+    if (!g.ok) return fail(VSR_ERR_CUDA, "cannot select the scene's device");
+    unsigned long long* scratch = nullptr;
+    st = noalloc_scratch(s->device, &scratch);
+    if (st != VSR_OK) return st;
+    a.work = scratch;  // zeroed on the stream by the launcher before the kernel
+    a.stream = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_static(a, is->kind, false);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent trace launch");
+    return VSR_OK;
+}

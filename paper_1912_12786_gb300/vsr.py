@@ -69,6 +69,8 @@ _SIGS = {
     "vsr_bvh_load": ([P, P, ctypes.c_size_t], ctypes.c_int),
     "vsr_trace": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P], ctypes.c_int),
     "vsr_trace_stats": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P], ctypes.c_int),
+    "vsr_trace_persistent_noalloc": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P],
+                                     ctypes.c_int),
     "vsr_make_shadow_rays": ([P, P, ctypes.c_uint64, P, ctypes.c_float, P, P], ctypes.c_int),
     "vsr_get_device_error": ([P, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "vsr_bvh_build": ([P, ctypes.c_uint64, P, ctypes.c_uint32, P, ctypes.POINTER(P),
@@ -209,6 +211,18 @@ def vsr_trace(scene: Scene, rays, isect: vsr_intersector, query, hits, counters=
     _check(lib().vsr_trace(scene.handle, _ptr(rays), n, ctypes.byref(isect), q, _ptr(hits),
                            _ptr(counters), ctypes.byref(params) if params else None,
                            _stream(stream)))
+
+
+def vsr_trace_persistent_noalloc(scene: Scene, rays, isect: vsr_intersector, query, hits,
+                                 counters=None, params: vsr_trace_params | None = None,
+                                 stream=None, n=None):
+    """Persistent trace whose ray counter lives in the library's static device
+    array (no allocation by the library).  Calls that overlap on the GPU race."""
+    q = QUERY[query] if isinstance(query, str) else int(query)
+    count = int(rays.shape[0]) if n is None else int(n)
+    _check(lib().vsr_trace_persistent_noalloc(
+        scene.handle, _ptr(rays), count, ctypes.byref(isect), q, _ptr(hits), _ptr(counters),
+        ctypes.byref(params) if params else None, _stream(stream)))
 
 
 def vsr_trace_stats(scene: Scene, rays, isect: vsr_intersector, query, hits, stats,
