@@ -282,3 +282,110 @@ def quad_grid_scene(texture: Texture, geom: int = 0) -> Scene:
     corners = np.array([[[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]]], np.float64)
     verts, idx, uvs = _quads_to_tris(corners)
     return Scene("unit_quad", verts, idx, uvs, np.full(2, geom, np.uint32), [texture])
+
+
+# ---------------------------------------------------------------------------
+# differentiation workload
+
+
+def _icosahedron():
+    t = (1.0 + 5 ** 0.5) / 2.0
+    v = np.array([[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0],
+                  [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+                  [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]], np.float64)
+    f = np.array([[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11],
+                  [1, 5, 9], [5, 11, 4], [11, 10, 2], [10, 7, 6], [7, 1, 8],
+                  [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9],
+                  [4, 9, 5], [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]], np.int64)
+    return v / np.linalg.norm(v, axis=1, keepdims=True), f
+
+
+def geodesic_sphere(freq: int):
+    """Unit geodesic sphere: every icosahedron edge split into `freq` parts
+    (20 freq^2 triangles, 10 freq^2 + 2 vertices).  Shared vertices are merged
+    exactly through their integer barycentric keys."""
+    base, faces = _icosahedron()
+    keys, pts = {}, []
+    tris = []
+
+    def vid(a, b, c, wa, wb, wc):
+        key = tuple(sorted((x, w) for x, w in ((a, wa), (b, wb), (c, wc)) if w))
+        k = keys.get(key)
+        if k is None:
+            k = len(pts)
+            keys[key] = k
+            p = sum(base[x] * w for x, w in key) / freq
+            pts.append(p / np.linalg.norm(p))
+        return k
+
+    for a, b, c in faces:
+        grid = {}
+        for i in range(freq + 1):
+            for j in range(freq + 1 - i):
+                grid[i, j] = vid(a, b, c, freq - i - j, i, j)
+        for i in range(freq):
+            for j in range(freq - i):
+                tris.append((grid[i, j], grid[i + 1, j], grid[i, j + 1]))
+                if i + j < freq - 1:
+                    tris.append((grid[i + 1, j], grid[i + 1, j + 1], grid[i, j + 1]))
+    return np.array(pts), np.array(tris, np.int64)
+
+
+def _spherical_uvs(verts: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """Equirectangular per-corner texture coordinates; triangles across the
+    seam get u shifted by one on their small-u corners, and pole corners take
+    the mean u of the other two corners."""
+    p = verts[idx]  # [T,3,3]
+    r = np.linalg.norm(p, axis=-1)
+    u = 0.5 + np.arctan2(p[..., 2], p[..., 0]) / (2 * np.pi)
+    v = 0.5 - np.arcsin(np.clip(p[..., 1] / r, -1, 1)) / np.pi
+    seam = (u.max(1) - u.min(1)) > 0.5
+    u[seam] = np.where(u[seam] < 0.5, u[seam] + 1.0, u[seam])
+    pole = np.abs(p[..., 1] / r) > 1 - 1e-9
+    for k in range(3):
+        m = pole[:, k]
+        others = [x for x in range(3) if x != k]
+        u[m, k] = u[m][:, others].mean(1)
+    return np.stack([u, v], -1).astype(np.float32)
+
+
+def _vertex_neighbours(n: int, idx: np.ndarray):
+    e = np.concatenate([idx[:, [0, 1]], idx[:, [1, 2]], idx[:, [2, 0]]])
+    e = np.concatenate([e, e[:, ::-1]])
+    e = np.unique(e, axis=0)
+    return e
+
+
+def displaced_icosphere(seed: int = SEED_BASE + 2, freq: int = 57, res: int = 512,
+                        tex_size: int = 512, alpha_cut: float = 0.3):
+    """Displaced geodesic sphere (freq 57: 64,980 triangles, 32,492 vertices),
+    radius 1 plus 0.05 N(0,1) per vertex smoothed by three uniform-Laplacian
+    passes, along the normal.  RGBA32F albedo: smooth value-noise colour and
+    alpha from uniform noise (the intersector keeps alpha >= alpha_cut).
+    res x res primary rays from (0, 0, 3) toward the origin, fovy 45 degrees.
+    Also returns target parameters: vertices + 0.01 N(0,1), colour texels +
+    0.01 N(0,1) (alpha unchanged)."""
+    rng = np.random.default_rng(seed)
+    pts, idx = geodesic_sphere(freq)
+    disp = 0.05 * rng.standard_normal(len(pts))
+    e = _vertex_neighbours(len(pts), idx)
+    deg = np.bincount(e[:, 0], minlength=len(pts)).astype(np.float64)
+    for _ in range(3):
+        acc = np.zeros(len(pts))
+        np.add.at(acc, e[:, 0], disp[e[:, 1]])
+        disp = 0.5 * disp + 0.5 * acc / deg
+    verts = (pts * (1.0 + disp)[:, None]).astype(np.float32)
+    uvs = _spherical_uvs(pts, idx)
+    tex = np.empty((tex_size, tex_size, 4), np.float32)
+    for c in range(3):
+        tex[..., c] = value_noise(rng, tex_size, tex_size, base=8, octaves=2)
+    tex[..., 3] = rng.uniform(0.0, 1.0, (tex_size, tex_size))
+    geom = np.zeros(len(idx), np.uint32)
+    scene = Scene("displaced_icosphere", verts, idx.astype(np.uint32), uvs, geom,
+                  [Texture("rgba32f", tex_size, tex_size, tex)],
+                  {"freq": freq, "alpha_cut": alpha_cut})
+    rays = pinhole_rays((0.0, 0.0, 3.0), (0.0, 0.0, 0.0), (0, 1, 0), 45.0, res, res)
+    target_verts = (verts + 0.01 * rng.standard_normal(verts.shape)).astype(np.float32)
+    target_tex = tex.copy()
+    target_tex[..., :3] += (0.01 * rng.standard_normal((tex_size, tex_size, 3))).astype(np.float32)
+    return scene, rays, target_verts, target_tex
