@@ -413,6 +413,7 @@ def run_ours(args):
 
     if not args.no_breakdown:
         out["breakdown"] = breakdown(V, s, d_rays, rays_s, n, flush, stream, torch)
+        out["fwd_bwd"] = fwd_bwd(V, torch, dev, flush, stream, args.steps, args.warmup)
 
     if rank == 0 and not args.no_cpu:
         mr, cores, nsel, el, reps = oracle_sample(sc, rays, blob, args.ref_stride,
@@ -462,6 +463,65 @@ def breakdown(V, s, d_rays, rays_s, n, flush, stream, torch, reps=5):
             res[f"{q}/{kind}/dynamic_vs_static"] = round(
                 res[f"{q}/{kind}/static"] / res[f"{q}/{kind}/dynamic"], 4)
     return res
+
+
+def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):
+    """Forward render + adjoint on the displaced icosphere (64,980 triangles,
+    RGBA32F 512^2 albedo with alpha cutout 0.3, 512x512 rays, alpha-texture
+    closest hit, diffuse shading, L2 loss to an image rendered from perturbed
+    vertices and texels).  One step: render, loss gradient, zeroed gradient
+    buffers, backward (re-trace + adjoint).  Mrays/s counts primary rays."""
+    from paper_1912_12786_gb300.inputs import scenes
+    sc, rays, tv, tt = scenes.displaced_icosphere()
+    blob = sc.bvh()
+    s = V.scene_from_inputs(sc, blob)
+    n = len(rays)
+    d_rays = torch.from_numpy(rays).to(dev)
+    isect = V.intersector("alpha_tex", cutoff_f=0.3)
+    shade = V.shade_params(scenes.light_dir_f32())
+    target = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    V.vsr_scene_update(s, torch.from_numpy(tv).to(dev), 0, torch.from_numpy(tt).to(dev))
+    V.vsr_render(s, d_rays, isect, shade, target)
+    V.vsr_scene_update(s, torch.from_numpy(sc.verts).to(dev), 0,
+                       torch.from_numpy(sc.textures[0].texels).to(dev))
+    img = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    gv = torch.zeros((sc.verts.shape[0], 3), dtype=torch.float32, device=dev)
+    gt = torch.zeros(sc.textures[0].texels.shape, dtype=torch.float32, device=dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        V.vsr_render(s, d_rays, isect, shade, img, None, None, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        g = 2.0 * (img - target)
+        gv.zero_()
+        gt.zero_()
+        V.vsr_trace_backward(s, d_rays, isect, shade, g, gv, gt, None, stream)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    ms, fwd, bwd = [], [], []
+    for _ in range(steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        step(ev)
+        ev[2].synchronize()
+        ms.append(ev[0].elapsed_time(ev[2]))
+        fwd.append(ev[0].elapsed_time(ev[1]))
+        bwd.append(ev[1].elapsed_time(ev[2]))
+    s.close()
+    t = statistics.median(ms)
+    return {"value": round(n / (t / 1e3) / 1e6, 2), "unit": "Mrays/s", "ms_per_step": round(t, 4),
+            "forward_ms": round(statistics.median(fwd), 4),
+            "backward_ms": round(statistics.median(bwd), 4),
+            "workload": "displaced icosphere, 64,980 triangles, 512x512 rays, alpha-texture "
+                        "closest hit, gradients for 32,492 vertices and 512^2 texels",
+            "gpu_launches_per_step": 2}
 
 
 def main():

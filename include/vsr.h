@@ -248,17 +248,81 @@ vsr_status vsr_trace_persistent_noalloc(vsr_scene* scene, const vsr_ray* rays, u
                                         vsr_hit* hits, uint32_t* counters,
                                         const vsr_trace_params* params, vsr_stream stream);
 
+/* ---------------------------------------------------------------- gradients */
+
+/*
+ * Differentiable shading on the closest-hit query (an extension of the
+ * paper's Section 3.1 queries; the paper has no gradients).  For a hit,
+ *   c = albedo_rgb(uv) * max(0, n_f . light)
+ * with uv the interpolated texture coordinate (as the alpha intersector uses
+ * it), albedo the bilinear lookup of the triangle's texture (texel centres at
+ * ((i + 0.5)/W, (j + 0.5)/H), clamp-to-edge indices; RGBA32F as stored,
+ * RGBA8 divided by 255, u8 and untextured triangles albedo 1) and
+ * n_f = normalize((v1 - v0) x (v2 - v0)) flipped to face the ray.  A miss
+ * gives `background`.
+ */
+typedef struct vsr_shade_params {
+    float light[3];      /* unit vector toward a directional light */
+    float background[3]; /* colour of a miss */
+    uint32_t grad_tex;   /* texture receiving texel gradients (RGBA32F), or
+                            VSR_NO_TEXTURE */
+    uint32_t reserved;   /* 0 */
+} vsr_shade_params;
+
+/*
+ * Closest-hit trace with `isect` (static dispatch) and the shading above.
+ *   image device float32 [n*3], written; hits device vsr_hit [n] or NULL.
+ *   params NULL or a non-persistent configuration.
+ * Errors as vsr_trace.
+ */
+vsr_status vsr_render(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
+                      const vsr_intersector* isect, const vsr_shade_params* shade,
+                      float* image, vsr_hit* hits, const vsr_trace_params* params,
+                      vsr_stream stream);
+
+/*
+ * Adjoint of vsr_render at fixed visibility: every ray is traced again with
+ * the same traversal (the same hit; no forward state is stored) and dL/dc is
+ * propagated to the vertices -- through the barycentrics u, v of the
+ * Moller-Trumbore solve (dL/dv_k = -b_k M^-T (0, dL/du, dL/dv), M = [-d, e1,
+ * e2], b = (1-u-v, u, v)) and through the face normal -- and to the texels of
+ * texture shade->grad_tex through the bilinear weights.
+ *   dL_dimage   device float32 [n*3]
+ *   grad_verts  device float32 [nverts*3], accumulated (atomics: the
+ *               summation order, hence the last bits, may vary between runs)
+ *   grad_texels device float32 [w*h*4] of texture grad_tex (RGBA32F), or
+ *               NULL; accumulated into the r, g, b channels
+ * The scene must be unchanged since the forward render.  Errors as vsr_trace.
+ */
+vsr_status vsr_trace_backward(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
+                              const vsr_intersector* isect, const vsr_shade_params* shade,
+                              const float* dL_dimage, float* grad_verts, float* grad_texels,
+                              const vsr_trace_params* params, vsr_stream stream);
+
+/*
+ * Replace the scene's vertex positions and/or one texture's texels with
+ * device data (same sizes as at creation; NULL leaves them unchanged).  After
+ * a vertex update the triangle layout is rebuilt and the BVH boxes are refit
+ * bottom-up (topology kept), so traces stay exact; traversal order and
+ * bvh_costs counts then follow the refit boxes.  Synchronous.
+ */
+vsr_status vsr_scene_update(vsr_scene* scene, const float* verts, uint32_t tex_index,
+                            const void* texels, vsr_stream stream);
+
 /* ---------------------------------------------------------------- errors */
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* vsr_last_error(void);
 
-/* Read and clear the scene's device error word.  Bit 0: a traversal stack
- * overflowed; bit 1: a ray visited more nodes than the BVH holds.  Either
- * ends that ray as a miss; neither can happen with a validated blob (each
- * node is visited at most once per ray), the checks exist so that a
- * corrupted structure gives an error instead of a fault or an endless loop.
- * Synchronous. */
+/* Read and clear the scene's device error word (synchronous).
+ *   bit 0: a traversal stack overflowed;
+ *   bit 1: a ray visited more nodes than the BVH holds;
+ *   bit 2: a render or backward kernel found a load whose address did not
+ *          match its width and skipped it (vsr_last_error() names the line).
+ * Bits 0 and 1 end that ray as a miss; neither can happen with a validated
+ * blob (each node is visited at most once per ray).  All three checks exist
+ * so that a corrupted structure or a bad address gives an error instead of
+ * a fault or an endless loop. */
 vsr_status vsr_get_device_error(vsr_scene* scene, uint32_t* word);
 
 /* Library version, e.g. 100 for 0.1.0. */

@@ -32,6 +32,12 @@ struct vsr_scene {
     DevScene* d_user = nullptr;
     uint32_t* d_err = nullptr;
     unsigned long long* d_work = nullptr;
+    // kept for updates: leaf order, node ids by tree level (deepest first),
+    // host copies of the texture descriptors
+    uint32_t* d_order = nullptr;
+    uint32_t* d_levels = nullptr;
+    std::vector<uint32_t> level_offsets;
+    std::vector<TexDesc> h_tex;
 };
 
 namespace {
@@ -179,7 +185,33 @@ __global__ void k_shadow_rays(const float4* __restrict__ rays, const float4* __r
 void free_bvh(vsr_scene* s) {
     dfree(s->d_nodes);
     dfree(s->d_tris);
+    dfree(s->d_order);
+    dfree(s->d_levels);
+    s->level_offsets.clear();
     s->has_bvh = false;
+}
+
+// Node ids grouped by depth, deepest level first (for the bottom-up refit).
+void node_levels(const vsr_bvh_node* nodes, uint32_t num_nodes, uint32_t max_depth,
+                 std::vector<uint32_t>& ids, std::vector<uint32_t>& offsets) {
+    std::vector<std::vector<uint32_t>> by_depth(max_depth + 1);
+    std::vector<std::pair<uint32_t, uint32_t>> st{{0u, 0u}};
+    while (!st.empty()) {
+        auto [id, depth] = st.back();
+        st.pop_back();
+        by_depth[depth].push_back(id);
+        const uint32_t count = nodes[id].count_axis >> 2;
+        if (count == 0 && id < num_nodes) {
+            st.push_back({nodes[id].left_or_first, depth + 1});
+            st.push_back({nodes[id].left_or_first + 1, depth + 1});
+        }
+    }
+    ids.clear();
+    offsets.assign(1, 0u);
+    for (int dpt = (int)max_depth; dpt >= 0; --dpt) {
+        ids.insert(ids.end(), by_depth[dpt].begin(), by_depth[dpt].end());
+        offsets.push_back((uint32_t)ids.size());
+    }
 }
 
 vsr_status validate_isect(const vsr_intersector* is, int32_t query) {
@@ -309,6 +341,7 @@ vsr_status vsr_scene_create_indexed(const float* verts, uint32_t nverts, const u
                             cudaMemcpyHostToDevice)) != cudaSuccess)
             return bail(cuda_fail(e, "texture upload"));
     }
+    s->h_tex = td;
     *out = s;
     return VSR_OK;
 }
@@ -381,22 +414,28 @@ vsr_status vsr_bvh_load(vsr_scene* s, const void* blob, size_t bytes) {
         return cuda_fail(e, "triangle allocation");
     }
     if (num_prims) {
-        uint32_t* d_order = nullptr;
-        if ((e = dmalloc(&d_order, (size_t)num_prims)) != cudaSuccess) {
+        if ((e = dmalloc(&s->d_order, (size_t)num_prims)) != cudaSuccess) {
             free_bvh(s);
             return cuda_fail(e, "order allocation");
         }
-        e = cudaMemcpy(d_order, order, 4ull * num_prims, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(s->d_order, order, 4ull * num_prims, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) {
-            k_build_tris<<<(num_prims + 255) / 256, 256>>>(s->d_verts, s->d_idx, d_order,
+            k_build_tris<<<(num_prims + 255) / 256, 256>>>(s->d_verts, s->d_idx, s->d_order,
                                                             num_prims, s->d_tris);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
         }
-        cudaFree(d_order);
         if (e != cudaSuccess) {
             free_bvh(s);
             return cuda_fail(e, "triangle layout");
+        }
+        std::vector<uint32_t> ids;
+        node_levels(nodes, num_nodes, max_depth, ids, s->level_offsets);
+        if ((e = dmalloc(&s->d_levels, ids.size())) != cudaSuccess ||
+            (e = cudaMemcpy(s->d_levels, ids.data(), 4ull * ids.size(),
+                            cudaMemcpyHostToDevice)) != cudaSuccess) {
+            free_bvh(s);
+            return cuda_fail(e, "level list upload");
         }
     }
     s->num_nodes = num_nodes;
@@ -499,10 +538,157 @@ vsr_status vsr_get_device_error(vsr_scene* s, uint32_t* word) {
     VSR_CUDA(cudaDeviceSynchronize(), "synchronise");
     VSR_CUDA(cudaMemcpy(word, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read error word");
     VSR_CUDA(cudaMemset(s->d_err, 0, sizeof(uint32_t)), "clear error word");
+    unsigned line = 0;
+    VSR_CUDA(render_align_error(&line), "read alignment check");
+    if (line) {
+        *word |= kErrAlign;
+        g_err = "render kernel skipped a misaligned load at render.cu/vsr_device.cuh line " +
+                std::to_string(line);
+    }
     return VSR_OK;
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Differentiable shading (render.cu kernels)
+
+namespace {
+
+vsr_status prepare_shade(const vsr_scene* s, const vsr_shade_params* sh, ShadeDev& out) {
+    if (!sh) return fail(VSR_ERR_ARG, "shade params are null");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(sh->light[k]) || !std::isfinite(sh->background[k]))
+            return fail(VSR_ERR_ARG, "non-finite light or background");
+    if (sh->grad_tex != VSR_NO_TEXTURE && sh->grad_tex >= s->ntex)
+        return fail(VSR_ERR_ARG, "grad_tex references a missing texture");
+    out = ShadeDev{{sh->light[0], sh->light[1], sh->light[2]},
+                   {sh->background[0], sh->background[1], sh->background[2]},
+                   sh->grad_tex,
+                   0u};
+    return VSR_OK;
+}
+
+vsr_status prepare_render(vsr_scene* s, const vsr_ray* rays, uint64_t n,
+                          const vsr_intersector* is, const vsr_shade_params* sh,
+                          const vsr_trace_params* p, LaunchArgs& a, ShadeDev& shd) {
+    if (is && is->dispatch != VSR_DISPATCH_STATIC)
+        return fail(VSR_ERR_ARG, "rendering uses static dispatch only");
+    if (p && p->persistent) return fail(VSR_ERR_ARG, "rendering uses non-persistent launches");
+    // hits are checked by the callers; a placeholder keeps prepare_launch's
+    // hit check out of the way when n == 0
+    vsr_status st = prepare_launch(s, rays, 0, is, VSR_CLOSEST, nullptr, p, a);
+    if (st != VSR_OK) return st;
+    if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull)
+        return fail(VSR_ERR_ARG, "too many rays for one launch");
+    if (n) {
+        st = check_dev(rays, s->device, "rays", 16, n * sizeof(vsr_ray));
+        if (st != VSR_OK) return st;
+    }
+    a.n = n;
+    a.rays = reinterpret_cast<const float4*>(rays);
+    return prepare_shade(s, sh, shd);
+}
+
+}  // namespace
+
+extern "C" vsr_status vsr_render(vsr_scene* s, const vsr_ray* rays, uint64_t n,
+                                 const vsr_intersector* is, const vsr_shade_params* sh,
+                                 float* image, vsr_hit* hits, const vsr_trace_params* p,
+                                 vsr_stream stream) {
+    g_err.clear();
+    LaunchArgs a;
+    ShadeDev shd;
+    vsr_status st = prepare_render(s, rays, n, is, sh, p, a, shd);
+    if (st != VSR_OK) return st;
+    if (n == 0) return VSR_OK;
+    st = check_dev(image, s->device, "image", 4, n * 12);
+    if (st == VSR_OK && hits) st = check_dev(hits, s->device, "hits", 16, n * 16);
+    if (st != VSR_OK) return st;
+    a.stream = reinterpret_cast<cudaStream_t>(stream);
+    DeviceGuard g(s->device);
+    cudaError_t e = launch_render(a, is->kind, shd, s->d_verts, s->d_idx, image,
+                                  reinterpret_cast<float4*>(hits));
+    if (e != cudaSuccess) return cuda_fail(e, "render launch");
+    return VSR_OK;
+}
+
+extern "C" vsr_status vsr_trace_backward(vsr_scene* s, const vsr_ray* rays, uint64_t n,
+                                         const vsr_intersector* is,
+                                         const vsr_shade_params* sh, const float* dL_dimage,
+                                         float* grad_verts, float* grad_texels,
+                                         const vsr_trace_params* p, vsr_stream stream) {
+    g_err.clear();
+    LaunchArgs a;
+    ShadeDev shd;
+    vsr_status st = prepare_render(s, rays, n, is, sh, p, a, shd);
+    if (st != VSR_OK) return st;
+    if (grad_texels) {
+        if (shd.grad_tex == VSR_NO_TEXTURE || s->h_tex[shd.grad_tex].fmt != VSR_TEX_RGBA32F)
+            return fail(VSR_ERR_ARG, "texel gradients need an RGBA32F grad_tex");
+    }
+    if (n == 0) return VSR_OK;
+    st = check_dev(dL_dimage, s->device, "dL_dimage", 4, n * 12);
+    if (st == VSR_OK) st = check_dev(grad_verts, s->device, "grad_verts", 4, 12ull * s->nverts);
+    if (st == VSR_OK && grad_texels) {
+        const TexDesc& t = s->h_tex[shd.grad_tex];
+        st = check_dev(grad_texels, s->device, "grad_texels", 4, 16ull * t.w * t.h);
+    }
+    if (st != VSR_OK) return st;
+    a.stream = reinterpret_cast<cudaStream_t>(stream);
+    DeviceGuard g(s->device);
+    cudaError_t e = launch_render_backward(a, is->kind, shd, s->d_verts, s->d_idx, dL_dimage,
+                                           grad_verts, grad_texels);
+    if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+    return VSR_OK;
+}
+
+extern "C" vsr_status vsr_scene_update(vsr_scene* s, const float* verts, uint32_t tex_index,
+                                       const void* texels, vsr_stream stream) {
+    g_err.clear();
+    if (!s) return fail(VSR_ERR_ARG, "scene is null");
+    vsr_status st = VSR_OK;
+    if (verts && s->nverts) st = check_dev(verts, s->device, "verts", 4, 12ull * s->nverts);
+    if (st != VSR_OK) return st;
+    size_t tex_bytes = 0;
+    if (texels) {
+        if (tex_index >= s->ntex) return fail(VSR_ERR_ARG, "tex_index references a missing texture");
+        const TexDesc& t = s->h_tex[tex_index];
+        tex_bytes = (size_t)t.w * t.h * texel_size((int32_t)t.fmt);
+        st = check_dev(texels, s->device, "texels", 4, tex_bytes);
+        if (st != VSR_OK) return st;
+    }
+    DeviceGuard g(s->device);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (texels)
+        VSR_CUDA(cudaMemcpyAsync(s->d_texels + s->h_tex[tex_index].offset, texels, tex_bytes,
+                                 cudaMemcpyDeviceToDevice, cs),
+                 "texel update");
+    if (verts && s->nverts) {
+        VSR_CUDA(cudaMemcpyAsync(s->d_verts, verts, 12ull * s->nverts, cudaMemcpyDeviceToDevice, cs),
+                 "vertex update");
+        if (s->has_bvh && s->dev.nprims) {
+            k_build_tris<<<(s->dev.nprims + 255) / 256, 256, 0, cs>>>(s->d_verts, s->d_idx,
+                                                                    s->d_order, s->dev.nprims,
+                                                                    s->d_tris);
+            VSR_CUDA(cudaGetLastError(), "triangle layout");
+            VSR_CUDA(launch_refit(s->d_nodes, s->d_levels, s->level_offsets.data(),
+                                  (uint32_t)s->level_offsets.size() - 1u, s->d_verts, s->d_idx,
+                                  s->d_order, cs),
+                     "refit");
+        }
+    }
+    VSR_CUDA(cudaStreamSynchronize(cs), "update");
+    if (verts && s->has_bvh && s->dev.nprims) {
+        float4 root[2];
+        VSR_CUDA(cudaMemcpy(root, s->d_nodes, sizeof(root), cudaMemcpyDeviceToHost), "root box");
+        s->dev.root_a = make_float4(root[0].x, root[0].y, root[0].z, 0.0f);
+        s->dev.root_b = make_float4(root[1].x, root[1].y, root[1].z, 0.0f);
+        VSR_CUDA(cudaMemcpy(s->d_user, &s->dev, sizeof(DevScene), cudaMemcpyHostToDevice),
+                 "scene descriptor upload");
+    }
+    return VSR_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Persistent trace whose scratch comes from a static device array.

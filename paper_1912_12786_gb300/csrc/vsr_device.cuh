@@ -20,6 +20,26 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+// Loads through the read-only path.  A translation unit that defines
+// VSR_CHECKED_LOADS before including this header gets loads that first check
+// the address against the access width, record the source line of a
+// misaligned one in g_vsr_align_line (see render.cu) and skip it, so that such
+// an access becomes an error code instead of a fault.
+#ifdef VSR_CHECKED_LOADS
+__device__ unsigned int g_vsr_align_line;
+template <class T>
+__device__ __forceinline__ T vsr_checked_ldg(const T* p, unsigned line) {
+    if (reinterpret_cast<unsigned long long>(p) % sizeof(T)) {
+        atomicCAS(&g_vsr_align_line, 0u, line);
+        return T{};
+    }
+    return __ldg(p);
+}
+#define VSR_LDG(p) ::vsr_checked_ldg((p), __LINE__)
+#else
+#define VSR_LDG(p) __ldg(p)
+#endif
+
 namespace vsr {
 
 constexpr uint32_t kMiss = 0xFFFFFFFFu;
@@ -31,7 +51,7 @@ enum : uint32_t { kTexU8 = 0, kTexRGBA8 = 1, kTexRGBA32F = 2 };
 // Device error word bits.  Neither can happen for a validated blob; the
 // checks turn a corrupted structure into an error instead of a fault or an
 // endless loop.
-enum : uint32_t { kErrStack = 1u, kErrSteps = 2u };
+enum : uint32_t { kErrStack = 1u, kErrSteps = 2u, kErrAlign = 4u };
 
 struct TexDesc {
     uint32_t fmt, w, h, pad;
@@ -128,8 +148,8 @@ __device__ __forceinline__ bool tri_test(const Ray& r, float4 a, float4 e1, floa
 // Interpolated texture coordinate: w0 = (1-u)-v, uv = v*tc2 + (u*tc1 + w0*tc0).
 __device__ __forceinline__ float2 lerp_uv(const float2* __restrict__ uvs, uint32_t prim, float u,
                                           float v) {
-    const float2 c0 = __ldg(uvs + 3ull * prim), c1 = __ldg(uvs + 3ull * prim + 1),
-                 c2 = __ldg(uvs + 3ull * prim + 2);
+    const float2 c0 = VSR_LDG(uvs + 3ull * prim), c1 = VSR_LDG(uvs + 3ull * prim + 1),
+                 c2 = VSR_LDG(uvs + 3ull * prim + 2);
     const float w0 = __fsub_rn(__fsub_rn(1.0f, u), v);
     float2 r;
     r.x = __fmaf_rn(v, c2.x, __fmaf_rn(u, c1.x, __fmul_rn(w0, c0.x)));
@@ -146,23 +166,23 @@ __device__ __forceinline__ uint32_t texel_coord(float c, uint32_t n) {
 // Alpha-mask decision: nearest texel, clamp to edge.
 __device__ __forceinline__ bool alpha_tex_accept(const DevScene& sc, const IsectParams& ip,
                                                  uint32_t prim, float u, float v) {
-    const uint32_t g = __ldg(sc.geom + prim);
+    const uint32_t g = VSR_LDG(sc.geom + prim);
     if (g == kMiss) return true;
     const float2 uv = lerp_uv(sc.uvs, prim, u, v);
-    const uint4 d = __ldg(reinterpret_cast<const uint4*>(sc.tex + g));
-    const unsigned long long off = __ldg(&sc.tex[g].offset);
+    const uint4 d = VSR_LDG(reinterpret_cast<const uint4*>(sc.tex + g));
+    const unsigned long long off = VSR_LDG(&sc.tex[g].offset);
     const uint32_t i = texel_coord(uv.x, d.y), j = texel_coord(uv.y, d.z);
     const unsigned long long k = (unsigned long long)j * d.y + i;
-    if (d.x == kTexU8) return __ldg(sc.texels + off + k) >= ip.cutoff_u8;
-    if (d.x == kTexRGBA8) return __ldg(sc.texels + off + 4 * k + 3) >= ip.cutoff_u8;
-    const float a = __ldg(reinterpret_cast<const float*>(sc.texels + off) + 4 * k + 3);
+    if (d.x == kTexU8) return VSR_LDG(sc.texels + off + k) >= ip.cutoff_u8;
+    if (d.x == kTexRGBA8) return VSR_LDG(sc.texels + off + 4 * k + 3) >= ip.cutoff_u8;
+    const float a = VSR_LDG(reinterpret_cast<const float*>(sc.texels + off) + 4 * k + 3);
     return a >= ip.cutoff_f;
 }
 
 // Procedural alpha: accept iff sin(f u) sin(f v) > 0 at the texture coordinate.
 __device__ __forceinline__ bool proc_alpha_accept(const DevScene& sc, const IsectParams& ip,
                                                   uint32_t prim, float u, float v) {
-    const uint32_t g = __ldg(sc.geom + prim);
+    const uint32_t g = VSR_LDG(sc.geom + prim);
     if (g == kMiss) return true;
     const float2 uv = lerp_uv(sc.uvs, prim, u, v);
     const float sa = sinf(__fmul_rn(ip.freq, uv.x));
@@ -252,7 +272,7 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
                 return;
             }
             const float4* p = sc.nodes + 4ull * (ref >> 2);
-            const float4 la = __ldg(p), lb = __ldg(p + 1), ra = __ldg(p + 2), rb = __ldg(p + 3);
+            const float4 la = VSR_LDG(p), lb = VSR_LDG(p + 1), ra = VSR_LDG(p + 2), rb = VSR_LDG(p + 3);
             const float tfar = (Q == kClosest) ? best.t : r.tmax;
             h.box();
             h.box();
@@ -292,8 +312,8 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
             const uint32_t cnt = (ref & 7u) + 1u;
             const float4* tp = sc.tris + 3ull * first;
             for (uint32_t k = 0; k < cnt; ++k) {
-                const float4 a = __ldg(tp + 3 * k), e1 = __ldg(tp + 3 * k + 1),
-                             e2 = __ldg(tp + 3 * k + 2);
+                const float4 a = VSR_LDG(tp + 3 * k), e1 = VSR_LDG(tp + 3 * k + 1),
+                             e2 = VSR_LDG(tp + 3 * k + 2);
                 h.tri();
                 if (STATS) st.tris++;
                 float t, u, v;
@@ -306,7 +326,7 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
                 }
                 if (STATS) {
                     st.cands++;
-                    if (H::kTexcoords && __ldg(sc.geom + prim) != kMiss) st.texs++;
+                    if (H::kTexcoords && VSR_LDG(sc.geom + prim) != kMiss) st.texs++;
                 }
                 if (!h.accept(sc, ip, prim, u, v)) continue;
                 best.t = t;

@@ -26,11 +26,34 @@ struct LaunchArgs {
     cudaStream_t stream;
 };
 
+// Shading parameters of the differentiable render (device copy).
+struct ShadeDev {
+    float light[3];  // unit vector toward a directional light
+    float bg[3];     // colour of a miss
+    uint32_t grad_tex;
+    uint32_t pad;
+};
+
 // Static injection: one instantiation per (query, intersector, stats).
 cudaError_t launch_static(const LaunchArgs& a, int kind, bool stats);
 // Dynamic injection: run-time checked function-pointer table.
 cudaError_t launch_dynamic(const LaunchArgs& a, int kind);
 // Resident blocks per SM for the given kernel configuration (0 on error).
 int persistent_grid(const LaunchArgs& a, const void* kernel, size_t smem);
+
+// Closest-hit render with diffuse shading, and its adjoint (render.cu).
+cudaError_t launch_render(const LaunchArgs& a, int kind, const ShadeDev& sh, const float* verts,
+                          const uint32_t* idx, float* image, float4* hits);
+cudaError_t launch_render_backward(const LaunchArgs& a, int kind, const ShadeDev& sh,
+                                   const float* verts, const uint32_t* idx, const float* g,
+                                   float* gv, float* gt);
+// Source line of the first misaligned load a render kernel skipped (0 if
+// none), cleared after reading.
+cudaError_t render_align_error(unsigned* line);
+// Bottom-up refit over node lists grouped by level, deepest first
+// (level_offsets is a host array of levels + 1 entries).
+cudaError_t launch_refit(float4* nodes, const uint32_t* level_nodes,
+                         const uint32_t* level_offsets, uint32_t levels, const float* verts,
+                         const uint32_t* idx, const uint32_t* order, cudaStream_t stream);
 
 }  // namespace vsr

@@ -56,6 +56,11 @@ class vsr_trace_params(ctypes.Structure):
                 ("refill_threshold", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
 
 
+class vsr_shade_params(ctypes.Structure):
+    _fields_ = [("light", ctypes.c_float * 3), ("background", ctypes.c_float * 3),
+                ("grad_tex", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
 _lib = None
 P = ctypes.c_void_p
 _SIGS = {
@@ -71,6 +76,9 @@ _SIGS = {
     "vsr_trace_stats": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "vsr_trace_persistent_noalloc": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P],
                                      ctypes.c_int),
+    "vsr_render": ([P, P, ctypes.c_uint64, P, P, P, P, P, P], ctypes.c_int),
+    "vsr_trace_backward": ([P, P, ctypes.c_uint64, P, P, P, P, P, P, P], ctypes.c_int),
+    "vsr_scene_update": ([P, P, ctypes.c_uint32, P, P], ctypes.c_int),
     "vsr_make_shadow_rays": ([P, P, ctypes.c_uint64, P, ctypes.c_float, P, P], ctypes.c_int),
     "vsr_get_device_error": ([P, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "vsr_bvh_build": ([P, ctypes.c_uint64, P, ctypes.c_uint32, P, ctypes.POINTER(P),
@@ -231,6 +239,36 @@ def vsr_trace_stats(scene: Scene, rays, isect: vsr_intersector, query, hits, sta
     _check(lib().vsr_trace_stats(scene.handle, _ptr(rays), int(rays.shape[0]),
                                  ctypes.byref(isect), q, _ptr(hits), _ptr(stats),
                                  _stream(stream)))
+
+
+def shade_params(light, background=(0.0, 0.0, 0.0), grad_tex=0) -> vsr_shade_params:
+    return vsr_shade_params((ctypes.c_float * 3)(*[float(x) for x in light]),
+                            (ctypes.c_float * 3)(*[float(x) for x in background]),
+                            grad_tex, 0)
+
+
+def vsr_render(scene: Scene, rays, isect: vsr_intersector, shade: vsr_shade_params, image,
+               hits=None, params: vsr_trace_params | None = None, stream=None):
+    """Closest-hit trace plus diffuse textured shading into image (float32 [n,3])."""
+    _check(lib().vsr_render(scene.handle, _ptr(rays), int(rays.shape[0]), ctypes.byref(isect),
+                            ctypes.byref(shade), _ptr(image), _ptr(hits),
+                            ctypes.byref(params) if params else None, _stream(stream)))
+
+
+def vsr_trace_backward(scene: Scene, rays, isect: vsr_intersector, shade: vsr_shade_params,
+                       dL_dimage, grad_verts, grad_texels=None,
+                       params: vsr_trace_params | None = None, stream=None):
+    """Accumulate dL/dverts and dL/dtexels (texture shade.grad_tex) at fixed visibility."""
+    _check(lib().vsr_trace_backward(scene.handle, _ptr(rays), int(rays.shape[0]),
+                                    ctypes.byref(isect), ctypes.byref(shade), _ptr(dL_dimage),
+                                    _ptr(grad_verts), _ptr(grad_texels),
+                                    ctypes.byref(params) if params else None, _stream(stream)))
+
+
+def vsr_scene_update(scene: Scene, verts=None, tex_index=0, texels=None, stream=None):
+    """Replace vertex positions and/or one texture's texels (device tensors)."""
+    _check(lib().vsr_scene_update(scene.handle, _ptr(verts), tex_index, _ptr(texels),
+                                  _stream(stream)))
 
 
 def vsr_make_shadow_rays(prim_rays, prim_hits, light, eps: float, out, stream=None):
