@@ -414,6 +414,7 @@ def run_ours(args):
     if not args.no_breakdown:
         out["breakdown"] = breakdown(V, s, d_rays, rays_s, n, flush, stream, torch)
         out["fwd_bwd"] = fwd_bwd(V, torch, dev, flush, stream, args.steps, args.warmup)
+        out["batch"] = batch_bench(V, torch, dev, flush, stream, args.steps)
 
     if rank == 0 and not args.no_cpu:
         mr, cores, nsel, el, reps = oracle_sample(sc, rays, blob, args.ref_stride,
@@ -522,6 +523,58 @@ def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):
             "workload": "displaced icosphere, 64,980 triangles, 512x512 rays, alpha-texture "
                         "closest hit, gradients for 32,492 vertices and 512^2 texels",
             "gpu_launches_per_step": 2}
+
+
+def batch_bench(V, torch, dev, flush, stream, steps):
+    """256 independent scenes (log-uniform 1k-200k triangles, log-uniform
+    1k-1M rays, half primary and half diffuse) with the alpha-texture
+    intersector: one autotuned persistent launch replayed from a CUDA graph,
+    against one vsr_trace launch per scene."""
+    from paper_1912_12786_gb300.inputs import scenes
+    items = scenes.batch_scenes()
+    blobs = scenes.build_bvhs([sc for sc, _ in items])
+    handles = [V.scene_from_inputs(sc, b) for (sc, _), b in zip(items, blobs)]
+    rays = [torch.from_numpy(r).to(dev) for _, r in items]
+    hits = [torch.empty((r.shape[0], 4), dtype=torch.float32, device=dev) for r in rays]
+    total = sum(int(r.shape[0]) for r in rays)
+    alpha = V.intersector("alpha_tex", cutoff_u8=128)
+    out = {"workload": f"{len(items)} scenes, {sum(sc.ntri for sc, _ in items)} triangles, "
+                       f"{total} rays, alpha-texture intersector",
+           "rays": total}
+    for q in ("any", "closest"):
+        b = V.vsr_batch_create(handles, rays, hits, alpha, q)
+        V.vsr_batch_launch(b, stream)
+        torch.cuda.synchronize(dev)
+        p = V.vsr_batch_params(b)
+        bt, pt = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            V.vsr_batch_launch(b, stream)
+            e1.record(stream)
+            e1.synchronize()
+            bt.append(e0.elapsed_time(e1))
+        for _ in range(max(3, steps // 4)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for h, r, o in zip(handles, rays, hits):
+                V.vsr_trace(h, r, alpha, q, o, None, None, stream)
+            e1.record(stream)
+            e1.synchronize()
+            pt.append(e0.elapsed_time(e1))
+        b.close()
+        tb, tp = statistics.median(bt), statistics.median(pt)
+        out[q] = {"batched_Mrays_s": round(total / (tb / 1e3) / 1e6, 1),
+                  "per_scene_Mrays_s": round(total / (tp / 1e3) / 1e6, 1),
+                  "speedup": round(tp / tb, 3), "batched_ms": round(tb, 3),
+                  "per_scene_ms": round(tp, 3),
+                  "tuned": {"block_size": p.block_size, "refill_threshold": p.refill_threshold,
+                            "blocks_per_sm": p.blocks_per_sm}}
+    for h in handles:
+        h.close()
+    return out
 
 
 def main():

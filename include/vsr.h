@@ -132,7 +132,9 @@ typedef enum vsr_query {
 /* Launch configuration; pass NULL for the tuned defaults. */
 typedef struct vsr_trace_params {
     uint32_t block_size;       /* threads per block, multiple of 32, 32..512 */
-    uint32_t persistent;       /* 0: one ray per thread; 1: persistent warps */
+    uint32_t persistent;       /* 0: one ray per thread; 1: persistent warps
+                                  (static dispatch; not for the procedural-
+                                  alpha any-hit query, which is refused) */
     uint32_t refill_threshold; /* persistent: refill idle lanes when fewer
                                   than this many of 32 are still active */
     uint32_t blocks_per_sm;    /* persistent: resident blocks per SM (0=auto) */
@@ -247,6 +249,56 @@ vsr_status vsr_trace_persistent_noalloc(vsr_scene* scene, const vsr_ray* rays, u
                                         const vsr_intersector* isect, int32_t query,
                                         vsr_hit* hits, uint32_t* counters,
                                         const vsr_trace_params* params, vsr_stream stream);
+
+/* ---------------------------------------------------------------- batches */
+
+/*
+ * Many independent scenes, each with its own ray batch, traced in one
+ * persistent launch (an extension of the paper's Section 3.1 queries: every
+ * ray gets exactly the result vsr_trace would give it on its scene).  The
+ * rays of all scenes form one index space; warps claim rays with one atomic
+ * per warp and refill idle lanes, so batches of very uneven sizes share the
+ * GPU without per-scene launches.
+ *
+ * vsr_batch_create records the scenes (each with a loaded BVH, all on one
+ * device), the device ray and hit arrays (rays[k]/hits[k]: vsr_ray/vsr_hit
+ * [n[k]], 16-byte aligned, caller-owned; n[k] may be 0), the intersector
+ * (static dispatch) and the query, and builds the device tables.  With
+ * params == NULL the launch configuration (block size, refill threshold,
+ * blocks per SM) is chosen by timing a grid of candidates on the batch itself
+ * at the first launch; results are cached per workload shape in the process
+ * and, if the environment variable VSR_TUNE_CACHE names a file, there too.
+ * The traversal stack depth is the deepest BVH's depth, so it needs no
+ * tuning.
+ *
+ * vsr_batch_launch: the first call synchronises `stream`, tunes if needed,
+ * runs the batch once and captures the launch (counter reset + kernel) in a
+ * CUDA graph; every call then replays the graph on `stream`.  The recorded
+ * pointers must stay valid for the batch's lifetime; the first launch writes
+ * the hits more than once.  Errors: VSR_ERR_ARG, VSR_ERR_STATE (a scene
+ * without BVH), VSR_ERR_OOM, VSR_ERR_CUDA.  nbatch is 1..65536.
+ */
+typedef struct vsr_batch vsr_batch;
+
+vsr_status vsr_batch_create(vsr_scene* const* scenes, const vsr_ray* const* rays,
+                            const uint64_t* n, vsr_hit* const* hits, uint32_t nbatch,
+                            const vsr_intersector* isect, int32_t query,
+                            const vsr_trace_params* params, vsr_batch** out);
+vsr_status vsr_batch_launch(vsr_batch* batch, vsr_stream stream);
+/* Launch configuration in use (the tuned one after the first launch). */
+vsr_status vsr_batch_params(const vsr_batch* batch, vsr_trace_params* out);
+/* Synchronises the device and frees the batch.  NULL is accepted. */
+vsr_status vsr_batch_destroy(vsr_batch* batch);
+
+/*
+ * One-call form: the library keeps the last 8 batches keyed by every
+ * argument and launches the matching one, creating (and tuning) it on first
+ * use; make that first call outside any stream capture.
+ */
+vsr_status vsr_trace_batch(vsr_scene* const* scenes, const vsr_ray* const* rays,
+                           const uint64_t* n, vsr_hit* const* hits, uint32_t nbatch,
+                           const vsr_intersector* isect, int32_t query,
+                           const vsr_trace_params* params, vsr_stream stream);
 
 /* ---------------------------------------------------------------- gradients */
 

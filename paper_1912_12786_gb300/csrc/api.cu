@@ -2,7 +2,10 @@
 // ray generation and error reporting.  Every entry point validates its
 // arguments on the host before anything is launched, so an invalid call
 // returns an error instead of reaching a kernel.
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstdint>
 #include <cstring>
 #include <limits>
@@ -244,6 +247,11 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (prm.blocks_per_sm > 32) return fail(VSR_ERR_ARG, "blocks_per_sm above 32");
     if (prm.persistent && is->dispatch == VSR_DISPATCH_DYNAMIC)
         return fail(VSR_ERR_ARG, "persistent launches use static dispatch only");
+    // This one instantiation stalled on the GPU twice without a cause found;
+    // it is refused until one is (the one-ray-per-thread launch serves it).
+    if (prm.persistent && is->kind == VSR_ISECT_PROC_ALPHA && query == VSR_ANY)
+        return fail(VSR_ERR_ARG,
+                    "persistent launch of the procedural-alpha any-hit query is disabled");
     if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull)
         return fail(VSR_ERR_ARG, "too many rays for one launch");
     if (n > 0) {
@@ -773,4 +781,342 @@ extern "C" vsr_status vsr_trace_persistent_noalloc(vsr_scene* s, const vsr_ray* 
     cudaError_t e = launch_static(a, is->kind, false);
     if (e != cudaSuccess) return cuda_fail(e, "persistent trace launch");
     return VSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent launch: device tables built once, launch configuration
+// autotuned, the launch captured in a CUDA graph and replayed.
+
+struct vsr_batch {
+    int device = 0;
+    uint32_t nbatch = 0;
+    unsigned long long total = 0;
+    int kind = 0, query = 0;
+    IsectParams ip{};
+    uint32_t stack_max = 1;
+    BatchItem* d_items = nullptr;
+    unsigned long long* d_offsets = nullptr;
+    unsigned long long* d_work = nullptr;
+    vsr_trace_params params{128u, 1u, 16u, 0u};
+    bool tuned = false;
+    uint64_t shape = 0;  // workload signature for the tuning cache
+    cudaStream_t side = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+uint64_t fnv_mix(uint64_t h, uint64_t v) {
+    for (int k = 0; k < 8; ++k) {
+        h ^= (v >> (8 * k)) & 0xFFu;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+std::mutex g_tune_mutex;
+std::vector<std::pair<uint64_t, vsr_trace_params>> g_tune_cache;
+bool g_tune_file_loaded = false;
+
+const char* tune_file() {
+    const char* f = std::getenv("VSR_TUNE_CACHE");
+    return (f && *f) ? f : nullptr;
+}
+
+bool tune_lookup(uint64_t shape, vsr_trace_params* out) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    if (!g_tune_file_loaded) {
+        g_tune_file_loaded = true;
+        if (const char* f = tune_file()) {
+            if (FILE* fp = std::fopen(f, "r")) {
+                unsigned long long sh;
+                unsigned b, r, bps;
+                while (std::fscanf(fp, "%llx %u %u %u", &sh, &b, &r, &bps) == 4)
+                    g_tune_cache.push_back({sh, vsr_trace_params{b, 1u, r, bps}});
+                std::fclose(fp);
+            }
+        }
+    }
+    for (const auto& e : g_tune_cache)
+        if (e.first == shape) {
+            *out = e.second;
+            return true;
+        }
+    return false;
+}
+
+void tune_store(uint64_t shape, const vsr_trace_params& p) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache.push_back({shape, p});
+    if (const char* f = tune_file()) {
+        if (FILE* fp = std::fopen(f, "a")) {
+            std::fprintf(fp, "%llx %u %u %u\n", (unsigned long long)shape, p.block_size,
+                         p.refill_threshold, p.blocks_per_sm);
+            std::fclose(fp);
+        }
+    }
+}
+
+vsr_status validate_params(const vsr_trace_params& p) {
+    if (p.block_size < 32 || p.block_size > 256 || p.block_size % 32)
+        return fail(VSR_ERR_ARG, "block_size must be a multiple of 32 in 32..256");
+    if (p.refill_threshold < 1 || p.refill_threshold > 32)
+        return fail(VSR_ERR_ARG, "refill_threshold must be in 1..32");
+    if (p.blocks_per_sm > 32) return fail(VSR_ERR_ARG, "blocks_per_sm above 32");
+    return VSR_OK;
+}
+
+BatchLaunch batch_launch_args(const vsr_batch* b, const vsr_trace_params& p) {
+    BatchLaunch L;
+    L.items = b->d_items;
+    L.offsets = b->d_offsets;
+    L.nbatch = b->nbatch;
+    L.ip = b->ip;
+    L.total = b->total;
+    L.work = b->d_work;
+    L.block = p.block_size;
+    L.refill = p.refill_threshold;
+    L.blocks_per_sm = p.blocks_per_sm;
+    L.stack_max = b->stack_max;
+    return L;
+}
+
+// Time every candidate configuration on the batch itself (two timed runs
+// after one warm-up, median of the two) and keep the fastest.
+vsr_status batch_tune(vsr_batch* b) {
+    static const uint32_t blocks[] = {64u, 128u, 256u};
+    static const uint32_t refills[] = {8u, 16u, 24u, 32u};
+    static const uint32_t per_sm[] = {0u, 2u, 4u};
+    cudaEvent_t e0, e1;
+    VSR_CUDA(cudaEventCreate(&e0), "tune events");
+    VSR_CUDA(cudaEventCreate(&e1), "tune events");
+    float best_ms = 0.0f;
+    vsr_trace_params best = b->params;
+    bool have = false;
+    vsr_status st = VSR_OK;
+    for (uint32_t bl : blocks) {
+        if ((size_t)b->stack_max * bl * 4 > 200 * 1024) continue;
+        for (uint32_t rf : refills)
+            for (uint32_t ps : per_sm) {
+                const vsr_trace_params cand{bl, 1u, rf, ps};
+                const BatchLaunch L = batch_launch_args(b, cand);
+                float ms[2] = {0.0f, 0.0f};
+                cudaError_t e = launch_batch(L, b->kind, b->query, b->side);
+                for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+                    e = cudaEventRecord(e0, b->side);
+                    if (e == cudaSuccess) e = launch_batch(L, b->kind, b->query, b->side);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, b->side);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[k], e0, e1);
+                }
+                if (e != cudaSuccess) {
+                    st = cuda_fail(e, "autotune");
+                    goto out;
+                }
+                const float m = 0.5f * (ms[0] + ms[1]);
+                if (!have || m < best_ms) {
+                    best_ms = m;
+                    best = cand;
+                    have = true;
+                }
+            }
+    }
+    b->params = best;
+    b->tuned = true;
+    tune_store(b->shape, best);
+out:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+void batch_free(vsr_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->side) cudaStreamDestroy(b->side);
+    dfree(b->d_items);
+    dfree(b->d_offsets);
+    dfree(b->d_work);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" vsr_status vsr_batch_create(vsr_scene* const* scenes, const vsr_ray* const* rays,
+                                       const uint64_t* n, vsr_hit* const* hits, uint32_t nbatch,
+                                       const vsr_intersector* is, int32_t query,
+                                       const vsr_trace_params* params, vsr_batch** out) {
+    g_err.clear();
+    if (!out) return fail(VSR_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (nbatch < 1 || nbatch > 65536) return fail(VSR_ERR_ARG, "nbatch must be in 1..65536");
+    if (!scenes || !rays || !n || !hits) return fail(VSR_ERR_ARG, "null batch array");
+    vsr_status st = validate_isect(is, query);
+    if (st != VSR_OK) return st;
+    if (is->dispatch != VSR_DISPATCH_STATIC)
+        return fail(VSR_ERR_ARG, "batched launches use static dispatch only");
+    vsr_trace_params prm{128u, 1u, 16u, 0u};
+    if (params) {
+        prm = *params;
+        prm.persistent = 1u;
+        st = validate_params(prm);
+        if (st != VSR_OK) return st;
+    }
+    if (!scenes[0]) return fail(VSR_ERR_ARG, "scene 0 is null");
+    const int device = scenes[0]->device;
+    std::vector<BatchItem> items(nbatch);
+    std::vector<unsigned long long> offsets(nbatch + 1, 0ull);
+    uint32_t stack_max = 1;
+    uint64_t shape = fnv_mix(fnv_mix(fnv_mix(1469598103934665603ull, (uint64_t)is->kind),
+                                     (uint64_t)query),
+                             nbatch);
+    for (uint32_t k = 0; k < nbatch; ++k) {
+        vsr_scene* s = scenes[k];
+        if (!s) return fail(VSR_ERR_ARG, "scene " + std::to_string(k) + " is null");
+        if (!s->has_bvh) return fail(VSR_ERR_STATE, "scene " + std::to_string(k) + " has no BVH");
+        if (s->device != device) return fail(VSR_ERR_ARG, "scenes live on different devices");
+        if (n[k] > (1ull << 36)) return fail(VSR_ERR_ARG, "ray batch too large");
+        if (n[k]) {
+            st = check_dev(rays[k], device, "rays", 16, n[k] * sizeof(vsr_ray));
+            if (st == VSR_OK) st = check_dev(hits[k], device, "hits", 16, n[k] * sizeof(vsr_hit));
+            if (st != VSR_OK) return fail(st, vsr_last_error() + std::string(" (batch entry ") +
+                                                  std::to_string(k) + ")");
+        }
+        items[k].sc = s->dev;
+        items[k].rays = reinterpret_cast<const float4*>(rays[k]);
+        items[k].hits = reinterpret_cast<float4*>(hits[k]);
+        offsets[k + 1] = offsets[k] + n[k];
+        stack_max = std::max(stack_max, s->dev.stack_depth);
+        shape = fnv_mix(fnv_mix(shape, s->ntri), n[k]);
+    }
+    if (offsets[nbatch] > (1ull << 40)) return fail(VSR_ERR_ARG, "more than 2^40 rays in a batch");
+    DeviceGuard g(device);
+    if (!g.ok) return fail(VSR_ERR_CUDA, "cannot select the scenes' device");
+    vsr_batch* b = new (std::nothrow) vsr_batch();
+    if (!b) return fail(VSR_ERR_OOM, "host allocation failed");
+    b->device = device;
+    b->nbatch = nbatch;
+    b->total = offsets[nbatch];
+    b->kind = is->kind;
+    b->query = query;
+    b->ip = IsectParams{is->alpha_cutoff_u8, is->alpha_cutoff_f, is->proc_freq, (uint32_t)is->kind};
+    b->stack_max = stack_max;
+    b->shape = shape;
+    b->params = prm;
+    b->tuned = params != nullptr || tune_lookup(shape, &b->params);
+    cudaError_t e;
+    if ((e = dmalloc(&b->d_items, (size_t)nbatch)) != cudaSuccess ||
+        (e = dmalloc(&b->d_offsets, (size_t)nbatch + 1)) != cudaSuccess ||
+        (e = dmalloc(&b->d_work, 1)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * nbatch,
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_offsets, offsets.data(), 8ull * (nbatch + 1),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking)) != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(e, "batch set-up");
+    }
+    *out = b;
+    return VSR_OK;
+}
+
+extern "C" vsr_status vsr_batch_launch(vsr_batch* b, vsr_stream stream) {
+    g_err.clear();
+    if (!b) return fail(VSR_ERR_ARG, "batch is null");
+    DeviceGuard g(b->device);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (!b->exec) {
+        // first launch: inputs produced on the caller's stream must be ready
+        // before tuning runs on the side stream
+        VSR_CUDA(cudaStreamSynchronize(cs), "synchronise before the first batch launch");
+        if (!b->tuned) {
+            vsr_status st = batch_tune(b);
+            if (st != VSR_OK) return st;
+        }
+        BatchLaunch L = batch_launch_args(b, b->params);
+        // one plain launch resolves the grid and shared-memory attribute
+        VSR_CUDA(launch_batch(L, b->kind, b->query, b->side), "batch launch");
+        VSR_CUDA(cudaStreamSynchronize(b->side), "batch launch");
+        VSR_CUDA(batch_grid(L, b->kind, b->query, &L.grid), "batch grid");
+        VSR_CUDA(cudaStreamBeginCapture(b->side, cudaStreamCaptureModeThreadLocal), "capture");
+        cudaError_t e = launch_batch(L, b->kind, b->query, b->side);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(b->side, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e != cudaSuccess ? e : e2, "batch graph capture");
+        }
+        b->graph = graph;
+        VSR_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0), "batch graph instantiate");
+    }
+    VSR_CUDA(cudaGraphLaunch(b->exec, cs), "batch graph launch");
+    return VSR_OK;
+}
+
+extern "C" vsr_status vsr_batch_params(const vsr_batch* b, vsr_trace_params* out) {
+    g_err.clear();
+    if (!b || !out) return fail(VSR_ERR_ARG, "null argument");
+    *out = b->params;
+    return VSR_OK;
+}
+
+extern "C" vsr_status vsr_batch_destroy(vsr_batch* b) {
+    if (!b) return VSR_OK;
+    DeviceGuard g(b->device);
+    cudaDeviceSynchronize();
+    batch_free(b);
+    return VSR_OK;
+}
+
+namespace {
+struct BatchCacheEntry {
+    uint64_t key;
+    vsr_batch* batch;
+};
+std::mutex g_batch_cache_mutex;
+std::vector<BatchCacheEntry> g_batch_cache;
+constexpr size_t kBatchCacheSize = 8;
+}  // namespace
+
+extern "C" vsr_status vsr_trace_batch(vsr_scene* const* scenes, const vsr_ray* const* rays,
+                                      const uint64_t* n, vsr_hit* const* hits, uint32_t nbatch,
+                                      const vsr_intersector* is, int32_t query,
+                                      const vsr_trace_params* params, vsr_stream stream) {
+    g_err.clear();
+    if (!scenes || !rays || !n || !hits || !is || nbatch < 1 || nbatch > 65536)
+        return fail(VSR_ERR_ARG, "invalid batch arguments");
+    uint64_t key = 1469598103934665603ull;
+    for (uint32_t k = 0; k < nbatch; ++k) {
+        key = fnv_mix(key, reinterpret_cast<uintptr_t>(scenes[k]));
+        key = fnv_mix(key, reinterpret_cast<uintptr_t>(rays[k]));
+        key = fnv_mix(key, reinterpret_cast<uintptr_t>(hits[k]));
+        key = fnv_mix(key, n[k]);
+    }
+    key = fnv_mix(fnv_mix(fnv_mix(key, nbatch), (uint64_t)query),
+                  ((uint64_t)(uint32_t)is->kind << 32) | (uint32_t)is->dispatch);
+    uint32_t fbits;
+    std::memcpy(&fbits, &is->alpha_cutoff_f, 4);
+    key = fnv_mix(fnv_mix(key, is->alpha_cutoff_u8), fbits);
+    std::memcpy(&fbits, &is->proc_freq, 4);
+    key = fnv_mix(key, fbits);
+    if (params)
+        key = fnv_mix(fnv_mix(key, params->block_size),
+                      ((uint64_t)params->refill_threshold << 32) | params->blocks_per_sm);
+    vsr_batch* b = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_batch_cache_mutex);
+        for (auto& e : g_batch_cache)
+            if (e.key == key) b = e.batch;
+        if (!b) {
+            vsr_status st = vsr_batch_create(scenes, rays, n, hits, nbatch, is, query, params, &b);
+            if (st != VSR_OK) return st;
+            if (g_batch_cache.size() >= kBatchCacheSize) {
+                vsr_batch_destroy(g_batch_cache.front().batch);
+                g_batch_cache.erase(g_batch_cache.begin());
+            }
+            g_batch_cache.push_back({key, b});
+        }
+    }
+    return vsr_batch_launch(b, stream);
 }

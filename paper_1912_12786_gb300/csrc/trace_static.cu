@@ -35,7 +35,9 @@ __global__ void __launch_bounds__(256) k_trace(DevScene sc, IsectParams ip,
 // Persistent variant.  Per-lane traversal state lives in registers and the
 // shared-memory stack column; a lane that finishes its ray idles until the
 // warp refills.  Every wait is a plain loop over claimed work: no lane ever
-// waits on another warp or block.
+// waits on another warp or block.  Each outer iteration either advances some
+// lane's traversal (bounded per ray by the node count) or claims at least one
+// ray, so the kernel terminates.
 template <int Q, class H, bool STATS>
 __global__ void __launch_bounds__(256) k_trace_persistent(
     DevScene sc, IsectParams ip, const float4* __restrict__ rays, unsigned long long n,
@@ -47,14 +49,22 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t lt_mask = (1u << lane) - 1u;
 
-    bool has = false;       // lane holds a ray in flight
-    bool exhausted = false; // warp-uniform: the counter passed n
+    bool has = false;        // lane holds a ray in flight
+    bool exhausted = false;  // warp-uniform: the counter passed n
     unsigned long long ri = 0;
     Ray r;
     Best best;
     Stats st;
     H h;
     uint32_t ref = 0, sp = 0, steps = 0;
+
+    auto finish = [&]() {
+        finish_miss(best);
+        hits[ri] = hit_record(best);
+        if (H::kCounts && counters) counters[ri] = h.counters();
+        if (STATS) stats[ri] = make_uint4(st.boxes, st.tris, st.cands, st.texs);
+        has = false;
+    };
 
     for (;;) {
         const uint32_t busy = __ballot_sync(0xFFFFFFFFu, has);
@@ -68,33 +78,11 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
             if (!has) {
                 ri = base + (unsigned long long)__popc(idle & lt_mask);
                 if (ri < n) {
-                    r = make_ray(__ldg(rays + 2 * ri), __ldg(rays + 2 * ri + 1));
+                    r = make_ray(VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
                     h = H();
                     st = Stats();
-                    best.t = r.tmax;
-                    best.u = best.v = 0.0f;
-                    best.prim = kMiss;
-                    sp = 0;
-                    steps = 0;
                     has = true;
-                    if (sc.nprims == 0) {
-                        ref = kLeafBit;  // finishes below with no work
-                        has = false;
-                    } else {
-                        h.box();
-                        if (STATS) st.boxes++;
-                        if (box_hit(r, sc.root_a, sc.root_b, best.t)) {
-                            ref = sc.root_ref;
-                        } else {
-                            has = false;
-                        }
-                    }
-                    if (!has) {  // finished at the root
-                        best.t = __int_as_float(0x7f800000);
-                        hits[ri] = hit_record(best);
-                        if (H::kCounts && counters) counters[ri] = h.counters();
-                        if (STATS) stats[ri] = make_uint4(st.boxes, st.tris, st.cands, st.texs);
-                    }
+                    if (!traverse_start<Q, H, STATS>(sc, r, h, best, st, ref, sp, steps)) finish();
                 }
             }
         }
@@ -103,106 +91,8 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
             continue;
         }
         if (!has) continue;
-        // One outer iteration of the while-while loop: descend to a leaf,
-        // test it, pop the next node.
-        bool done = false;
-        while (!(ref & kLeafBit)) {
-            if (++steps > sc.max_steps) {
-                atomicOr(sc.err, kErrSteps);
-                best.prim = kMiss;
-                done = true;
-                break;
-            }
-            const float4* p = sc.nodes + 4ull * (ref >> 2);
-            const float4 la = __ldg(p), lb = __ldg(p + 1), ra = __ldg(p + 2), rb = __ldg(p + 3);
-            const float tfar = (Q == kClosest) ? best.t : r.tmax;
-            h.box();
-            h.box();
-            if (STATS) st.boxes += 2;
-            const bool hl = box_hit(r, la, lb, tfar);
-            const bool hr = box_hit(r, ra, rb, tfar);
-            const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(ra.w);
-            if (hl && hr) {
-                const uint32_t axis = ref & 3u;
-                const float da = axis == 0 ? r.dx : (axis == 1 ? r.dy : r.dz);
-                const bool neg = signbit(da);
-                if (sp >= sc.stack_depth) {
-                    atomicOr(sc.err, kErrStack);
-                    best.prim = kMiss;
-                    done = true;
-                    break;
-                }
-                stack[sp * stride] = neg ? rl : rr;
-                ++sp;
-                ref = neg ? rr : rl;
-            } else if (hl) {
-                ref = rl;
-            } else if (hr) {
-                ref = rr;
-            } else {
-                if (sp == 0) {
-                    done = true;
-                    break;
-                }
-                --sp;
-                ref = stack[sp * stride];
-            }
-        }
-        if (!done && ++steps > sc.max_steps) {
-            atomicOr(sc.err, kErrSteps);
-            best.prim = kMiss;
-            done = true;
-        }
-        if (!done) {
-            const uint32_t first = (ref >> 3) & 0x0FFFFFFFu;
-            const uint32_t cnt = (ref & 7u) + 1u;
-            const float4* tp = sc.tris + 3ull * first;
-            for (uint32_t k = 0; k < cnt; ++k) {
-                const float4 a = __ldg(tp + 3 * k), e1 = __ldg(tp + 3 * k + 1),
-                             e2 = __ldg(tp + 3 * k + 2);
-                h.tri();
-                if (STATS) st.tris++;
-                float t, u, v;
-                if (!tri_test(r, a, e1, e2, t, u, v)) continue;
-                const bool geo = u >= 0.0f && v >= 0.0f && __fadd_rn(u, v) <= 1.0f;
-                if (!geo || !(t > r.tmin) || !(t < r.tmax)) continue;
-                const uint32_t prim = __float_as_uint(a.w);
-                if (Q == kClosest) {
-                    if (!(t < best.t || (t == best.t && prim < best.prim))) continue;
-                }
-                if (STATS) {
-                    st.cands++;
-                    if (H::kTexcoords && __ldg(sc.geom + prim) != kMiss) st.texs++;
-                }
-                if (!h.accept(sc, ip, prim, u, v)) continue;
-                best.t = t;
-                best.u = u;
-                best.v = v;
-                best.prim = prim;
-                if (Q == kAny) {
-                    done = true;
-                    break;
-                }
-            }
-            if (!done) {
-                if (sp == 0) {
-                    done = true;
-                } else {
-                    --sp;
-                    ref = stack[sp * stride];
-                }
-            }
-        }
-        if (done) {
-            if (best.prim == kMiss) {
-                best.t = __int_as_float(0x7f800000);
-                best.u = best.v = 0.0f;
-            }
-            hits[ri] = hit_record(best);
-            if (H::kCounts && counters) counters[ri] = h.counters();
-            if (STATS) stats[ri] = make_uint4(st.boxes, st.tris, st.cands, st.texs);
-            has = false;
-        }
+        if (traverse_step<Q, H, STATS>(sc, ip, r, h, best, st, ref, sp, steps, stack, stride))
+            finish();
     }
 }
 

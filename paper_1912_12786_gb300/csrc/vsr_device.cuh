@@ -356,6 +356,118 @@ __device__ __forceinline__ void traverse(const DevScene& sc, const IsectParams& 
     }
 }
 
+// The same traversal split into resumable pieces for persistent kernels,
+// whose lanes interleave rays: traverse_start tests the root box and
+// returns whether the ray is still live; each traverse_step runs one outer
+// iteration of the while-while loop (descend to a leaf, test it, pop the
+// next node) and returns true when the ray has finished.  Composed, they
+// visit nodes and primitives in exactly the order of traverse_body.
+template <int Q, class H, bool STATS>
+__device__ __forceinline__ bool traverse_start(const DevScene& sc, const Ray& r, H& h, Best& best,
+                                               Stats& st, uint32_t& ref, uint32_t& sp,
+                                               uint32_t& steps) {
+    best.t = r.tmax;
+    best.u = 0.0f;
+    best.v = 0.0f;
+    best.prim = kMiss;
+    sp = 0;
+    steps = 0;
+    if (sc.nprims == 0) return false;
+    h.box();
+    if (STATS) st.boxes++;
+    if (!box_hit(r, sc.root_a, sc.root_b, best.t)) return false;
+    ref = sc.root_ref;
+    return true;
+}
+
+template <int Q, class H, bool STATS>
+__device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectParams& ip,
+                                              const Ray& r, H& h, Best& best, Stats& st,
+                                              uint32_t& ref, uint32_t& sp, uint32_t& steps,
+                                              uint32_t* stack, uint32_t stride) {
+    while (!(ref & kLeafBit)) {
+        if (++steps > sc.max_steps) {
+            atomicOr(sc.err, kErrSteps);
+            best.prim = kMiss;
+            return true;
+        }
+        const float4* p = sc.nodes + 4ull * (ref >> 2);
+        const float4 la = VSR_LDG(p), lb = VSR_LDG(p + 1), ra = VSR_LDG(p + 2), rb = VSR_LDG(p + 3);
+        const float tfar = (Q == kClosest) ? best.t : r.tmax;
+        h.box();
+        h.box();
+        if (STATS) st.boxes += 2;
+        const bool hl = box_hit(r, la, lb, tfar);
+        const bool hr = box_hit(r, ra, rb, tfar);
+        const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(ra.w);
+        if (hl && hr) {
+            const uint32_t axis = ref & 3u;
+            const float da = axis == 0 ? r.dx : (axis == 1 ? r.dy : r.dz);
+            const bool neg = signbit(da);
+            if (sp >= sc.stack_depth) {
+                atomicOr(sc.err, kErrStack);
+                best.prim = kMiss;
+                return true;
+            }
+            stack[sp * stride] = neg ? rl : rr;
+            ++sp;
+            ref = neg ? rr : rl;
+        } else if (hl) {
+            ref = rl;
+        } else if (hr) {
+            ref = rr;
+        } else {
+            if (sp == 0) return true;
+            --sp;
+            ref = stack[sp * stride];
+        }
+    }
+    if (++steps > sc.max_steps) {
+        atomicOr(sc.err, kErrSteps);
+        best.prim = kMiss;
+        return true;
+    }
+    const uint32_t first = (ref >> 3) & 0x0FFFFFFFu;
+    const uint32_t cnt = (ref & 7u) + 1u;
+    const float4* tp = sc.tris + 3ull * first;
+    for (uint32_t k = 0; k < cnt; ++k) {
+        const float4 a = VSR_LDG(tp + 3 * k), e1 = VSR_LDG(tp + 3 * k + 1), e2 = VSR_LDG(tp + 3 * k + 2);
+        h.tri();
+        if (STATS) st.tris++;
+        float t, u, v;
+        if (!tri_test(r, a, e1, e2, t, u, v)) continue;
+        const bool geo = u >= 0.0f && v >= 0.0f && __fadd_rn(u, v) <= 1.0f;
+        if (!geo || !(t > r.tmin) || !(t < r.tmax)) continue;
+        const uint32_t prim = __float_as_uint(a.w);
+        if (Q == kClosest) {
+            if (!(t < best.t || (t == best.t && prim < best.prim))) continue;
+        }
+        if (STATS) {
+            st.cands++;
+            if (H::kTexcoords && VSR_LDG(sc.geom + prim) != kMiss) st.texs++;
+        }
+        if (!h.accept(sc, ip, prim, u, v)) continue;
+        best.t = t;
+        best.u = u;
+        best.v = v;
+        best.prim = prim;
+        if (Q == kAny) return true;
+    }
+    if (sp == 0) return true;
+    --sp;
+    ref = stack[sp * stride];
+    return false;
+}
+
+// Miss record normalisation shared by all kernels.
+__device__ __forceinline__ void finish_miss(Best& best) {
+    if (best.prim == kMiss) {
+        best.t = __int_as_float(0x7f800000);
+        best.u = 0.0f;
+        best.v = 0.0f;
+    }
+}
+
 __device__ __forceinline__ float4 hit_record(const Best& b) {
     return make_float4(b.t, b.u, b.v, __uint_as_float(b.prim));
 }

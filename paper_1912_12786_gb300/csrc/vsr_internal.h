@@ -50,6 +50,29 @@ cudaError_t launch_render_backward(const LaunchArgs& a, int kind, const ShadeDev
 // Source line of the first misaligned load a render kernel skipped (0 if
 // none), cleared after reading.
 cudaError_t render_align_error(unsigned* line);
+// One scene of a batched launch: its descriptor and its ray and hit arrays.
+struct BatchItem {
+    DevScene sc;
+    const float4* rays;
+    float4* hits;
+};
+
+struct BatchLaunch {
+    const BatchItem* items;             // device [nbatch]
+    const unsigned long long* offsets;  // device [nbatch + 1] ray prefix offsets
+    uint32_t nbatch;
+    IsectParams ip;
+    unsigned long long total;
+    unsigned long long* work;  // ray counter, zeroed before each launch
+    uint32_t block, refill, blocks_per_sm, stack_max;
+    uint32_t grid = 0;  // non-zero: launch exactly this grid, with no set-up calls
+};
+
+// Batched persistent trace over many scenes (batch.cu).
+cudaError_t launch_batch(const BatchLaunch& b, int kind, int query, cudaStream_t stream);
+// Grid that launch_batch uses for b (after its shared-memory attribute is set).
+cudaError_t batch_grid(const BatchLaunch& b, int kind, int query, uint32_t* grid);
+
 // Bottom-up refit over node lists grouped by level, deepest first
 // (level_offsets is a host array of levels + 1 entries).
 cudaError_t launch_refit(float4* nodes, const uint32_t* level_nodes,

@@ -389,3 +389,92 @@ def displaced_icosphere(seed: int = SEED_BASE + 2, freq: int = 57, res: int = 51
     target_tex = tex.copy()
     target_tex[..., :3] += (0.01 * rng.standard_normal((tex_size, tex_size, 3))).astype(np.float32)
     return scene, rays, target_verts, target_tex
+
+
+# ---------------------------------------------------------------------------
+# batching workload
+
+
+def camera_rays_random(rng: np.random.Generator, n: int, eye=(0.5, 0.5, -1.0),
+                       target=(0.5, 0.5, 0.5), up=(0, 1, 0), fovy_deg: float = 60.0,
+                       aspect: float = 1.0) -> np.ndarray:
+    """n pinhole rays through uniformly random image-plane positions."""
+    eye = np.asarray(eye, np.float64)
+    f = np.asarray(target, np.float64) - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(np.asarray(up, np.float64), f)
+    r /= np.linalg.norm(r)
+    u = np.cross(f, r)
+    th = math.tan(math.radians(fovy_deg) * 0.5)
+    sx = rng.uniform(-1, 1, n) * th * aspect
+    sy = rng.uniform(-1, 1, n) * th
+    d = f[None] + sx[:, None] * r[None] + sy[:, None] * u[None]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rays = np.empty((n, 8), np.float32)
+    rays[:, 0:3] = eye.astype(np.float32)
+    rays[:, 3] = 0.0
+    rays[:, 4:7] = d.astype(np.float32)
+    rays[:, 7] = np.inf
+    return rays
+
+
+def diffuse_rays(rng: np.random.Generator, scene: Scene, n: int) -> np.ndarray:
+    """n rays leaving uniformly chosen points of uniformly chosen triangles in
+    cosine-distributed directions about a random side of the face normal;
+    interval (1e-4 of the scene diagonal, +inf)."""
+    tri = rng.integers(0, scene.ntri, n)
+    v = scene.verts.astype(np.float64)[scene.idx[tri]]  # [n,3,3]
+    e1, e2 = v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]
+    a, b = rng.uniform(size=n), rng.uniform(size=n)
+    sa = np.sqrt(a)
+    p = v[:, 0] + (sa * (1 - b))[:, None] * e1 + (sa * b)[:, None] * e2
+    nrm = np.cross(e1, e2)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    nrm *= np.where(rng.uniform(size=n) < 0.5, -1.0, 1.0)[:, None]
+    helper = np.where(np.abs(nrm[:, :1]) > 0.9, np.array([[0, 1, 0]]), np.array([[1, 0, 0]]))
+    t1 = np.cross(helper, nrm)
+    t1 /= np.linalg.norm(t1, axis=1, keepdims=True)
+    t2 = np.cross(nrm, t1)
+    xi1, xi2 = rng.uniform(size=n), rng.uniform(size=n)
+    rr, phi = np.sqrt(xi1), 2 * np.pi * xi2
+    d = (rr * np.cos(phi))[:, None] * t1 + (rr * np.sin(phi))[:, None] * t2 \
+        + np.sqrt(1 - xi1)[:, None] * nrm
+    rays = np.empty((n, 8), np.float32)
+    rays[:, 0:3] = p.astype(np.float32)
+    rays[:, 3] = np.float32(1e-4 * scene.extent())
+    rays[:, 4:7] = d.astype(np.float32)
+    rays[:, 7] = np.inf
+    return rays
+
+
+def batch_scenes(seed: int = SEED_BASE + 3, n_scenes: int = 256, tri_range=(1_000, 200_000),
+                 ray_range=(1_000, 1_000_000), tex_size: int = 256):
+    """Independent scenes for the batched launch: triangle counts log-uniform
+    in tri_range (rounded to even: random quads as in small_quads), each with
+    its own u8 disc alpha of radius U[0.25, 0.45]; ray counts log-uniform in
+    ray_range, half pinhole primary rays from (0.5, 0.5, -1) and half diffuse
+    rays from random surface points.  Returns a list of (scene, rays)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_scenes):
+        ntri = int(np.exp(rng.uniform(np.log(tri_range[0]), np.log(tri_range[1]))))
+        nq = max(1, ntri // 2)
+        nrays = int(np.exp(rng.uniform(np.log(ray_range[0]), np.log(ray_range[1]))))
+        corners = random_quads(rng, nq, 0.0, 1.0, 0.02, 0.1)
+        verts, idx, uvs = _quads_to_tris(corners)
+        tex = disc_alpha_u8(tex_size, float(rng.uniform(0.25, 0.45)))
+        sc = Scene(f"batch_{k}", verts, idx, uvs, np.zeros(len(idx), np.uint32), [tex])
+        half = nrays // 2
+        rays = np.concatenate([camera_rays_random(rng, half), diffuse_rays(rng, sc, nrays - half)])
+        out.append((sc, rays))
+    return out
+
+
+def build_bvhs(scene_list, threads: int | None = None):
+    """BVH blobs for many scenes, built concurrently (the builder releases the
+    interpreter lock)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    threads = threads or len(os.sched_getaffinity(0))
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(lambda s: s.bvh(), scene_list))

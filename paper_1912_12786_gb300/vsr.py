@@ -76,6 +76,12 @@ _SIGS = {
     "vsr_trace_stats": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "vsr_trace_persistent_noalloc": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P],
                                      ctypes.c_int),
+    "vsr_batch_create": ([P, P, P, P, ctypes.c_uint32, P, ctypes.c_int32, P, ctypes.POINTER(P)],
+                         ctypes.c_int),
+    "vsr_batch_launch": ([P, P], ctypes.c_int),
+    "vsr_batch_params": ([P, P], ctypes.c_int),
+    "vsr_batch_destroy": ([P], ctypes.c_int),
+    "vsr_trace_batch": ([P, P, P, P, ctypes.c_uint32, P, ctypes.c_int32, P, P], ctypes.c_int),
     "vsr_render": ([P, P, ctypes.c_uint64, P, P, P, P, P, P], ctypes.c_int),
     "vsr_trace_backward": ([P, P, ctypes.c_uint64, P, P, P, P, P, P, P], ctypes.c_int),
     "vsr_scene_update": ([P, P, ctypes.c_uint32, P, P], ctypes.c_int),
@@ -239,6 +245,67 @@ def vsr_trace_stats(scene: Scene, rays, isect: vsr_intersector, query, hits, sta
     _check(lib().vsr_trace_stats(scene.handle, _ptr(rays), int(rays.shape[0]),
                                  ctypes.byref(isect), q, _ptr(hits), _ptr(stats),
                                  _stream(stream)))
+
+
+class Batch:
+    """Owns a ``vsr_batch*`` (see vsr_batch_create)."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            lib().vsr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _batch_arrays(scenes, rays, hits):
+    nb = len(scenes)
+    sc = (P * nb)(*[s.handle for s in scenes])
+    rp = (P * nb)(*[_ptr(r) for r in rays])
+    hp = (P * nb)(*[_ptr(h) for h in hits])
+    ns = (ctypes.c_uint64 * nb)(*[int(r.shape[0]) for r in rays])
+    return nb, sc, rp, hp, ns
+
+
+def vsr_batch_create(scenes, rays, hits, isect: vsr_intersector, query,
+                     params: vsr_trace_params | None = None) -> Batch:
+    """Prepare one persistent launch over many scenes (lists of equal length)."""
+    q = QUERY[query] if isinstance(query, str) else int(query)
+    nb, sc, rp, hp, ns = _batch_arrays(scenes, rays, hits)
+    out = P()
+    _check(lib().vsr_batch_create(sc, rp, ns, hp, nb, ctypes.byref(isect), q,
+                                  ctypes.byref(params) if params else None, ctypes.byref(out)))
+    return Batch(out.value, (scenes, rays, hits))
+
+
+def vsr_batch_launch(batch: Batch, stream=None):
+    _check(lib().vsr_batch_launch(batch.handle, _stream(stream)))
+
+
+def vsr_batch_params(batch: Batch) -> vsr_trace_params:
+    p = vsr_trace_params()
+    _check(lib().vsr_batch_params(batch.handle, ctypes.byref(p)))
+    return p
+
+
+def vsr_batch_destroy(batch: Batch):
+    batch.close()
+
+
+def vsr_trace_batch(scenes, rays, hits, isect: vsr_intersector, query,
+                    params: vsr_trace_params | None = None, stream=None):
+    q = QUERY[query] if isinstance(query, str) else int(query)
+    nb, sc, rp, hp, ns = _batch_arrays(scenes, rays, hits)
+    _check(lib().vsr_trace_batch(sc, rp, ns, hp, nb, ctypes.byref(isect), q,
+                                 ctypes.byref(params) if params else None, _stream(stream)))
 
 
 def shade_params(light, background=(0.0, 0.0, 0.0), grad_tex=0) -> vsr_shade_params:

@@ -34,7 +34,7 @@ def setup():
 
 
 @pytest.mark.parametrize("kind,query", [("alpha_tex", "closest"), ("count", "any"),
-                                        ("proc_alpha", "any")])
+                                        ("default", "any")])
 def test_noalloc_matches_persistent_trace_twice(setup, kind, query):
     V, s, rays = setup
     n = rays.shape[0]
@@ -64,3 +64,5 @@ def test_noalloc_rejects_more_rays_than_supported(setup):
     with pytest.raises(V.VsrError, match="static dispatch"):
         V.vsr_trace_persistent_noalloc(s, rays, V.intersector("default", "dynamic"), "closest",
                                        hits)
+    with pytest.raises(V.VsrError, match="disabled"):
+        V.vsr_trace_persistent_noalloc(s, rays, V.intersector("proc_alpha"), "any", hits)
