@@ -93,7 +93,22 @@ struct Ray {
     float ox, oy, oz, tmin, dx, dy, dz, tmax;
     float ix, iy, iz;     // guarded inverse direction
     float nox, noy, noz;  // -(o * inv)
+    uint32_t negmask;     // bit a set iff the sign bit of d[a] is set
 };
+
+// Three-input minimum / maximum (one ALU instruction on sm_100-family GPUs).
+// Like fminf/fmaxf they ignore a NaN operand; min and max are exact, so any
+// grouping of the operands gives the same value.
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 
 __device__ __forceinline__ float guard_dir(float d) {
     return fabsf(d) < 0x1p-80f ? copysignf(0x1p-80f, d) : d;
@@ -109,6 +124,7 @@ __device__ __forceinline__ Ray make_ray(float4 a, float4 b) {
     r.nox = -__fmul_rn(a.x, r.ix);
     r.noy = -__fmul_rn(a.y, r.iy);
     r.noz = -__fmul_rn(a.z, r.iz);
+    r.negmask = (signbit(b.x) ? 1u : 0u) | (signbit(b.y) ? 2u : 0u) | (signbit(b.z) ? 4u : 0u);
     return r;
 }
 
@@ -117,13 +133,15 @@ __device__ __forceinline__ bool box_hit(const Ray& r, float4 lo, float4 hi, floa
     const float t0x = __fmaf_rn(lo.x, r.ix, r.nox), t1x = __fmaf_rn(hi.x, r.ix, r.nox);
     const float t0y = __fmaf_rn(lo.y, r.iy, r.noy), t1y = __fmaf_rn(hi.y, r.iy, r.noy);
     const float t0z = __fmaf_rn(lo.z, r.iz, r.noz), t1z = __fmaf_rn(hi.z, r.iz, r.noz);
-    const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), r.tmin));
-    const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tfar));
+    const float tn = fmax3(fminf(t0x, t1x), fminf(t0y, t1y), fmaxf(fminf(t0z, t1z), r.tmin));
+    const float tf = fmin3(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fminf(fmaxf(t0z, t1z), tfar));
     return tn <= tf;
 }
 
 // intersect(ray, basic_triangle<3,float>): Moller-Trumbore with the fixed
-// rounding order.  Returns false when det == 0 (no t, u, v).
+// rounding order.  Returns false when det == 0 (no t, u, v) and, as a shortcut
+// that changes no decision, when u alone already rules out a geometric hit
+// (u < 0, u > 1 or NaN: with v >= 0 the rounded u + v is at least u).
 __device__ __forceinline__ bool tri_test(const Ray& r, float4 a, float4 e1, float4 e2,
                                          float& t, float& u, float& v) {
     const float px = __fmaf_rn(r.dy, e2.z, -__fmul_rn(r.dz, e2.y));
@@ -134,6 +152,7 @@ __device__ __forceinline__ bool tri_test(const Ray& r, float4 a, float4 e1, floa
     const float inv = __fdiv_rn(1.0f, det);
     const float sx = __fsub_rn(r.ox, a.x), sy = __fsub_rn(r.oy, a.y), sz = __fsub_rn(r.oz, a.z);
     u = __fmul_rn(dot3(sx, sy, sz, px, py, pz), inv);
+    if (!(u >= 0.0f && u <= 1.0f)) return false;
     const float qx = __fmaf_rn(sy, e1.z, -__fmul_rn(sz, e1.y));
     const float qy = __fmaf_rn(sz, e1.x, -__fmul_rn(sx, e1.z));
     const float qz = __fmaf_rn(sx, e1.y, -__fmul_rn(sy, e1.x));
@@ -281,9 +300,7 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
             const bool hr = box_hit(r, ra, rb, tfar);
             const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(ra.w);
             if (hl && hr) {
-                const uint32_t axis = ref & 3u;
-                const float da = axis == 0 ? r.dx : (axis == 1 ? r.dy : r.dz);
-                const bool neg = signbit(da);
+                const bool neg = (r.negmask >> (ref & 3u)) & 1u;
                 if (sp >= sc.stack_depth) {  // unreachable for a validated blob
                     atomicOr(sc.err, kErrStack);
                     best.prim = kMiss;
@@ -401,9 +418,7 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
         const bool hr = box_hit(r, ra, rb, tfar);
         const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(ra.w);
         if (hl && hr) {
-            const uint32_t axis = ref & 3u;
-            const float da = axis == 0 ? r.dx : (axis == 1 ? r.dy : r.dz);
-            const bool neg = signbit(da);
+            const bool neg = (r.negmask >> (ref & 3u)) & 1u;
             if (sp >= sc.stack_depth) {
                 atomicOr(sc.err, kErrStack);
                 best.prim = kMiss;
