@@ -12,12 +12,14 @@
 #include "vsr_bvh.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <string>
+#include <thread>
 #include <vector>
 
 namespace {
@@ -83,13 +85,64 @@ class Builder {
     Builder(std::vector<Ref>&& refs, const vsr_build_params& p)
         : refs_(std::move(refs)), p_(p) {}
 
+    // Build the whole tree.  The top of the tree is built serially until a
+    // subtree holds at most `defer` references; those subtrees are built on
+    // threads, each into its own node array over its own (disjoint) range of
+    // references, and appended in creation order.  The result does not depend
+    // on the number of threads or their timing.
     void run() {
         nodes_.reserve(refs_.size() * 2 + 2);
         nodes_.resize(2);
         std::memset(nodes_.data(), 0, sizeof(vsr_bvh_node) * 2);
         if (refs_.empty()) return;
-        std::vector<Task> stack;
-        stack.push_back({0, 0, (uint32_t)refs_.size(), 0});
+        const uint32_t n = (uint32_t)refs_.size();
+        const uint32_t defer = std::max<uint32_t>(n / 256u, 4096u);
+        std::vector<Task> deferred;
+        process({{0, 0, n, 0}}, nodes_, max_depth_, num_leaves_, defer, &deferred);
+        if (deferred.empty()) return;
+        struct Sub {
+            std::vector<vsr_bvh_node> nodes;
+            uint32_t depth = 0, leaves = 0;
+        };
+        std::vector<Sub> subs(deferred.size());
+        std::atomic<size_t> next{0};
+        auto worker = [&]() {
+            for (size_t k = next++; k < deferred.size(); k = next++) {
+                const Task& t = deferred[k];
+                Sub& sb = subs[k];
+                sb.nodes.resize(1);
+                std::memset(sb.nodes.data(), 0, sizeof(vsr_bvh_node));
+                process({{0, t.begin, t.end, t.depth}}, sb.nodes, sb.depth, sb.leaves, 0u,
+                        nullptr);
+            }
+        };
+        unsigned nt = std::thread::hardware_concurrency();
+        if (const char* e = std::getenv("VSR_BUILD_THREADS")) nt = (unsigned)std::atoi(e);
+        nt = std::max(1u, std::min<unsigned>(nt, (unsigned)deferred.size()));
+        std::vector<std::thread> pool;
+        for (unsigned k = 1; k < nt; ++k) pool.emplace_back(worker);
+        worker();
+        for (auto& th : pool) th.join();
+        for (size_t k = 0; k < deferred.size(); ++k) {
+            Sub& sb = subs[k];
+            const uint32_t base = (uint32_t)nodes_.size();  // even: pairs only
+            auto remap = [&](vsr_bvh_node nd) {
+                if ((nd.count_axis >> 2) == 0) nd.left_or_first = base + nd.left_or_first - 1u;
+                return nd;
+            };
+            nodes_[deferred[k].node] = remap(sb.nodes[0]);
+            for (size_t j = 1; j < sb.nodes.size(); ++j) nodes_.push_back(remap(sb.nodes[j]));
+            max_depth_ = std::max(max_depth_, sb.depth);
+            num_leaves_ += sb.leaves;
+        }
+    }
+
+    // Binned-SAH construction of the subtrees on `stack` into `nodes`.  A
+    // task whose node is nodes[t.node] covers refs_[t.begin, t.end); child
+    // pairs are appended to `nodes`.  With `deferred`, tasks of at most
+    // `defer` references (and more than a leaf) are set aside instead.
+    void process(std::vector<Task> stack, std::vector<vsr_bvh_node>& nodes, uint32_t& max_depth,
+                 uint32_t& leaves, uint32_t defer, std::vector<Task>* deferred) {
         std::vector<uint32_t> cnt(p_.bins);
         std::vector<Box> bbox(p_.bins);
         std::vector<double> right_area(p_.bins);
@@ -97,20 +150,24 @@ class Builder {
         while (!stack.empty()) {
             Task t = stack.back();
             stack.pop_back();
+            if (deferred && t.end - t.begin <= defer && t.end - t.begin > p_.leaf_max) {
+                deferred->push_back(t);
+                continue;
+            }
             Box nb, cb;
             for (uint32_t i = t.begin; i < t.end; ++i) {
                 nb.grow(refs_[i].lo, refs_[i].hi);
                 cb.grow_point(refs_[i].c);
             }
-            vsr_bvh_node& nd = nodes_[t.node];
+            vsr_bvh_node& nd = nodes[t.node];
             for (int a = 0; a < 3; ++a) {
                 nd.lo[a] = nb.lo[a];
                 nd.hi[a] = nb.hi[a];
             }
             const uint32_t n = t.end - t.begin;
-            max_depth_ = std::max(max_depth_, t.depth);
+            max_depth = std::max(max_depth, t.depth);
             if (n == 1) {
-                make_leaf(t);
+                make_leaf(t, nodes, leaves);
                 continue;
             }
             int axis = -1;
@@ -159,7 +216,7 @@ class Builder {
                     const double split_cost =
                         p_.traversal_cost + (na > 0.0 ? best / na : (double)n);
                     if (n <= p_.leaf_max && (double)n <= split_cost) {
-                        make_leaf(t);
+                        make_leaf(t, nodes, leaves);
                         continue;
                     }
                     const int a = best_axis;
@@ -179,7 +236,7 @@ class Builder {
             }
             if (!sah_ok) {
                 if (n <= p_.leaf_max) {
-                    make_leaf(t);
+                    make_leaf(t, nodes, leaves);
                     continue;
                 }
                 // Object median along the widest centroid axis (index split
@@ -202,9 +259,9 @@ class Builder {
                 }
                 axis = a;
             }
-            const uint32_t left = (uint32_t)nodes_.size();
-            nodes_.resize(nodes_.size() + 2);
-            vsr_bvh_node& nd2 = nodes_[t.node];  // resize may move storage
+            const uint32_t left = (uint32_t)nodes.size();
+            nodes.resize(nodes.size() + 2);
+            vsr_bvh_node& nd2 = nodes[t.node];  // resize may move storage
             nd2.left_or_first = left;
             nd2.count_axis = (uint32_t)axis;
             stack.push_back({left + 1, mid, t.end, t.depth + 1});
@@ -252,11 +309,11 @@ class Builder {
     uint32_t bin_of(float c, float lo, float scale) const {
         return bin_of_n(c, lo, scale, p_.bins);
     }
-    void make_leaf(const Task& t) {
-        vsr_bvh_node& nd = nodes_[t.node];
+    static void make_leaf(const Task& t, std::vector<vsr_bvh_node>& nodes, uint32_t& leaves) {
+        vsr_bvh_node& nd = nodes[t.node];
         nd.left_or_first = t.begin;
         nd.count_axis = (t.end - t.begin) << 2;
-        ++num_leaves_;
+        ++leaves;
     }
 
     std::vector<Ref> refs_;

@@ -478,3 +478,60 @@ def build_bvhs(scene_list, threads: int | None = None):
     threads = threads or len(os.sched_getaffinity(0))
     with ThreadPoolExecutor(max_workers=threads) as ex:
         return list(ex.map(lambda s: s.bvh(), scene_list))
+
+
+# ---------------------------------------------------------------------------
+# large incoherent workload
+
+
+def heightfield(n_cells: int, extent: float, amplitude: float, rng: np.random.Generator):
+    """n_cells x n_cells grid over [0, extent]^2 (two triangles per cell) with
+    height amplitude * value noise; returns verts, idx, uvs."""
+    h = amplitude * value_noise(rng, n_cells + 1, n_cells + 1, base=8, octaves=3)
+    xs = np.linspace(0.0, extent, n_cells + 1)
+    X, Z = np.meshgrid(xs, xs)
+    verts = np.stack([X, h, Z], -1).reshape(-1, 3).astype(np.float32)
+    i = np.arange(n_cells)
+    a = (i[:, None] * (n_cells + 1) + i[None, :]).ravel()
+    b, c, d = a + 1, a + n_cells + 1, a + n_cells + 2
+    idx = np.empty((len(a), 2, 3), np.uint32)
+    idx[:, 0] = np.stack([a, b, d], 1)
+    idx[:, 1] = np.stack([a, d, c], 1)
+    uv = verts[:, [0, 2]] / extent
+    idx = idx.reshape(-1, 3)
+    return verts, idx, uv[idx].astype(np.float32)
+
+
+def large_incoherent(seed: int = SEED_BASE + 4, n_quads: int = 7_000_000, ground_cells: int = 1000,
+                     width: int = 1920, height: int = 1080, tex_size: int = 1024):
+    """7 M random quads (14 M triangles, side U[0.005, 0.05], uniform
+    orientation, UVs over [0, 1]^2, textured) in [0, 10]^3 plus a 1000 x 1000
+    cell heightfield (2 M opaque triangles, height 0.5 * value noise) over
+    [0, 10]^2: 16 M triangles.  One RGBA32F tex_size^2 colour texture (value
+    noise, alpha 1).  Primary rays from (5, 8, -5) toward (5, 2, 5), fovy 60
+    degrees."""
+    rng = np.random.default_rng(seed)
+    corners = random_quads(rng, n_quads, 0.0, 10.0, 0.005, 0.05)
+    qv, qi, quv = _quads_to_tris(corners)
+    del corners
+    gv, gi, guv = heightfield(ground_cells, 10.0, 0.5, rng)
+    verts = np.concatenate([qv, gv])
+    idx = np.concatenate([qi, gi + np.uint32(len(qv))])
+    uvs = np.concatenate([quv, guv])
+    geom = np.full(len(idx), NONE, np.uint32)
+    geom[: len(qi)] = 0
+    tex = np.empty((tex_size, tex_size, 4), np.float32)
+    for c in range(3):
+        tex[..., c] = value_noise(rng, tex_size, tex_size, base=16, octaves=3)
+    tex[..., 3] = 1.0
+    scene = Scene("large_incoherent", verts, idx, uvs, geom,
+                  [Texture("rgba32f", tex_size, tex_size, tex)], {"n_quads": n_quads})
+    rays = pinhole_rays((5.0, 8.0, -5.0), (5.0, 2.0, 5.0), (0, 1, 0), 60.0, width, height)
+    return scene, rays
+
+
+def ao_random(n_rays: int, spp: int, seed: int = SEED_BASE + 5) -> np.ndarray:
+    """Uniform random numbers in [0, 1) for ambient-occlusion sampling,
+    float32 [n_rays * spp, 2]; passed to both the GPU and the oracle."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.0, 1.0, (n_rays * spp, 2)).astype(np.float32)
