@@ -415,6 +415,7 @@ def run_ours(args):
         out["breakdown"] = breakdown(V, s, d_rays, rays_s, n, flush, stream, torch)
         out["fwd_bwd"] = fwd_bwd(V, torch, dev, flush, stream, args.steps, args.warmup)
         out["batch"] = batch_bench(V, torch, dev, flush, stream, args.steps)
+        out["large"] = large_bench(V, torch, dev, flush, stream, args.steps)
 
     if rank == 0 and not args.no_cpu:
         mr, cores, nsel, el, reps = oracle_sample(sc, rays, blob, args.ref_stride,
@@ -574,6 +575,65 @@ def batch_bench(V, torch, dev, flush, stream, steps):
                             "blocks_per_sm": p.blocks_per_sm}}
     for h in handles:
         h.close()
+    return out
+
+
+def large_bench(V, torch, dev, flush, stream, steps):
+    """16 M triangles (7 M procedurally alpha-masked quads + 2 M-triangle
+    heightfield): 1920x1080 primary closest hits (procedural alpha), then 4
+    ambient-occlusion rays per pixel (tmax 0.5) traced any-hit with the
+    procedural-alpha and counting intersectors, static and dynamic."""
+    from paper_1912_12786_gb300.inputs import scenes
+    sc, rays = scenes.large_incoherent()
+    blob = sc.bvh()
+    s = V.scene_from_inputs(sc, blob)
+    n, spp = len(rays), 4
+    d_rays = torch.from_numpy(rays).to(dev)
+    hits = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    ao = torch.empty((n * spp, 8), dtype=torch.float32, device=dev)
+    ao_hits = torch.empty((n * spp, 4), dtype=torch.float32, device=dev)
+    cnt = torch.empty((n * spp, 2), dtype=torch.int32, device=dev)
+    xi = torch.from_numpy(scenes.ao_random(n, spp)).to(dev)
+    proc = V.intersector("proc_alpha")
+
+    def timed(fn, reps):
+        ms = []
+        for k in range(reps + 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 2:
+                ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    reps = max(3, steps // 2)
+    out = {"workload": f"{sc.ntri} triangles, {n} primary + {n * spp} ambient-occlusion rays",
+           "triangles": sc.ntri}
+    t = timed(lambda: V.vsr_trace(s, d_rays, proc, "closest", hits, None, None, stream), reps)
+    out["primary_closest_proc_alpha_Mrays_s"] = round(n / (t / 1e3) / 1e6, 1)
+    V.vsr_make_ao_rays(s, d_rays, hits, spp, xi, 0.5, scenes.shadow_eps(sc), ao, stream)
+    m = n * spp
+    for kind in ("proc_alpha", "count", "default"):
+        for disp in ("static", "dynamic"):
+            isect = V.intersector(kind, disp)
+            c = cnt if kind == "count" else None
+            t = timed(lambda: V.vsr_trace(s, ao, isect, "any", ao_hits, c, None, stream), reps)
+            out[f"ao_any/{kind}/{disp}_Mrays_s"] = round(m / (t / 1e3) / 1e6, 1)
+            out[f"ao_any/{kind}/{disp}_ms"] = round(t, 3)
+    for kind in ("proc_alpha", "count"):
+        out[f"ao_any/{kind}/dynamic_vs_static"] = round(
+            out[f"ao_any/{kind}/static_Mrays_s"] / out[f"ao_any/{kind}/dynamic_Mrays_s"], 4)
+    st = torch.empty((m, 4), dtype=torch.int32, device=dev)
+    V.vsr_trace_stats(s, ao, proc, "any", ao_hits, st, stream)
+    torch.cuda.synchronize(dev)
+    b = trace_bytes(m, st.cpu().numpy().view(np.uint32), 16, True)
+    t = out["ao_any/proc_alpha/static_ms"]
+    out["ao_any/proc_alpha/static_algorithmic_bytes"] = b
+    out["ao_any/proc_alpha/static_algorithmic_GBs"] = round(b / (t / 1e3) / 1e9, 1)
+    s.close()
     return out
 
 

@@ -361,6 +361,22 @@ vsr_status vsr_trace_backward(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
 vsr_status vsr_scene_update(vsr_scene* scene, const float* verts, uint32_t tex_index,
                             const void* texels, vsr_stream stream);
 
+/*
+ * Ambient-occlusion rays from primary hits (a workload step; the paper has
+ * no ray generation): spp rays per primary ray i, written at i*spp + k.
+ * Origin fmaf(t, d, o); direction cosine-distributed about the face normal
+ * turned against the primary direction, for the uniforms xi[i*spp + k] =
+ * (x1, x2): sqrt(x1) cos(2 pi x2) t1 + sqrt(x1) sin(2 pi x2) t2 +
+ * sqrt(1 - x1) n, with the tangent frame (t1, t2) of Duff et al. (2017,
+ * "Building an orthonormal basis, revisited"); interval (eps, tmax).  A
+ * primary miss gives inactive rays.  FP32.
+ *   prim_rays/prim_hits device [n]; xi device float32 [n*spp*2];
+ *   out device vsr_ray [n*spp].  spp 1..64.
+ */
+vsr_status vsr_make_ao_rays(vsr_scene* scene, const vsr_ray* prim_rays, const vsr_hit* prim_hits,
+                            uint64_t n, uint32_t spp, const float* xi, float tmax, float eps,
+                            vsr_ray* out, vsr_stream stream);
+
 /* ---------------------------------------------------------------- errors */
 
 /* Message describing the last failure on the calling thread ("" if none). */

@@ -83,6 +83,9 @@ def _load():
         lib.orc_intersect_aabb.argtypes = [P, P, P, ctypes.c_float]
         lib.orc_shadow_rays.argtypes = [P, P, ctypes.c_uint64, P, ctypes.c_float, P]
         lib.orc_shadow_rays.restype = None
+        lib.orc_ao_rays.argtypes = [P, P, P, ctypes.c_uint64, ctypes.c_uint32, P, ctypes.c_float,
+                                    ctypes.c_float, P]
+        lib.orc_ao_rays.restype = None
         _lib = lib
     return _lib
 
@@ -185,6 +188,20 @@ def shadow_rays(prim_rays, prim_hits_raw, light, eps):
     l = np.ascontiguousarray(light, np.float32)
     out = np.zeros_like(r)
     lib.orc_shadow_rays(_ptr(r), _ptr(h), r.shape[0], _ptr(l), float(eps), _ptr(out))
+    return out
+
+
+def ao_rays(scene, prim_rays, prim_hits_raw, spp, xi, tmax, eps):
+    """Ambient-occlusion rays from primary hits (spp per pixel, FP64 frame)."""
+    lib = _load()
+    sh = _SceneHandle(scene)
+    r = np.ascontiguousarray(prim_rays, np.float32).reshape(-1, 8)
+    h = np.ascontiguousarray(prim_hits_raw, np.float32).reshape(-1, 4)
+    x = np.ascontiguousarray(xi, np.float32).reshape(-1, 2)
+    assert x.shape[0] == r.shape[0] * spp
+    out = np.zeros((r.shape[0] * spp, 8), np.float32)
+    lib.orc_ao_rays(ctypes.byref(sh.c), _ptr(r), _ptr(h), r.shape[0], spp, _ptr(x),
+                    float(tmax), float(eps), _ptr(out))
     return out
 
 

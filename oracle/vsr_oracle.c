@@ -530,3 +530,59 @@ void orc_shadow_rays(const float* prim_rays, const float* prim_hits, uint64_t n,
         }
     }
 }
+
+/* Ambient-occlusion rays (a workload step, not in the paper): spp rays per
+ * primary hit.  Origin fmaf(t, d, o) per component; normal n = normalize of
+ * (v1 - v0) x (v2 - v0) turned against the primary direction; tangent frame
+ * by the branchless construction of Duff et al. (2017, "Building an
+ * orthonormal basis, revisited"); direction for uniforms (x1, x2):
+ * sqrt(x1) cos(2 pi x2) t1 + sqrt(x1) sin(2 pi x2) t2 + sqrt(1 - x1) n.  The
+ * frame and direction are evaluated in FP64 and rounded to FP32; interval
+ * (eps, tmax).  Primary misses give inactive rays (origin 0, direction
+ * (0, 0, 1), tmin 0, tmax -1).  Output ray i*spp + k. */
+void orc_ao_rays(const orc_scene* s, const float* prim_rays, const float* prim_hits, uint64_t n,
+                 uint32_t spp, const float* xi, float tmax, float eps, float* out) {
+    for (uint64_t i = 0; i < n; ++i) {
+        const orc_ray* r = (const orc_ray*)prim_rays + i;
+        const orc_hit* h = (const orc_hit*)prim_hits + i;
+        float o[3] = {0.0f, 0.0f, 0.0f};
+        double nn[3] = {0.0, 0.0, 1.0};
+        const int hit = h->prim != ORC_NONE;
+        if (hit) {
+            float v0[3], e1[3], e2[3];
+            tri_verts(s, h->prim, v0, e1, e2);
+            for (int k = 0; k < 3; ++k) o[k] = fmaf(h->t, r->d[k], r->o[k]);
+            nn[0] = (double)e1[1] * e2[2] - (double)e1[2] * e2[1];
+            nn[1] = (double)e1[2] * e2[0] - (double)e1[0] * e2[2];
+            nn[2] = (double)e1[0] * e2[1] - (double)e1[1] * e2[0];
+            const double len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+            for (int k = 0; k < 3; ++k) nn[k] = len > 0 ? nn[k] / len : (k == 2 ? 1.0 : 0.0);
+            if (nn[0] * r->d[0] + nn[1] * r->d[1] + nn[2] * r->d[2] > 0)
+                for (int k = 0; k < 3; ++k) nn[k] = -nn[k];
+        }
+        const double sg = copysign(1.0, nn[2]);
+        const double a = -1.0 / (sg + nn[2]);
+        const double b = nn[0] * nn[1] * a;
+        const double t1[3] = {1.0 + sg * nn[0] * nn[0] * a, sg * b, -sg * nn[0]};
+        const double t2[3] = {b, sg + nn[1] * nn[1] * a, -nn[1]};
+        for (uint32_t k = 0; k < spp; ++k) {
+            orc_ray* q = (orc_ray*)out + (i * spp + k);
+            if (!hit) {
+                q->o[0] = q->o[1] = q->o[2] = 0.0f;
+                q->d[0] = q->d[1] = 0.0f;
+                q->d[2] = 1.0f;
+                q->tmin = 0.0f;
+                q->tmax = -1.0f;
+                continue;
+            }
+            const double x1 = xi[2 * (i * spp + k)], x2 = xi[2 * (i * spp + k) + 1];
+            const double rr = sqrt(x1), ph = 6.283185307179586 * x2, z = sqrt(1.0 - x1);
+            for (int c = 0; c < 3; ++c) {
+                q->o[c] = o[c];
+                q->d[c] = (float)(rr * cos(ph) * t1[c] + rr * sin(ph) * t2[c] + z * nn[c]);
+            }
+            q->tmin = eps;
+            q->tmax = tmax;
+        }
+    }
+}

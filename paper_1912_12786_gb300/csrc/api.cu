@@ -185,6 +185,65 @@ __global__ void k_shadow_rays(const float4* __restrict__ rays, const float4* __r
     out[2 * i + 1] = make_float4(lx, ly, lz, __int_as_float(0x7f800000));
 }
 
+// Ambient-occlusion rays: spp per primary hit, cosine-distributed about the
+// face normal turned against the primary direction, tangent frame of Duff et
+// al. (2017), FP32.  Output ray i*spp + k.
+__global__ void k_ao_rays(const float* __restrict__ verts, const uint32_t* __restrict__ idx,
+                          const float4* __restrict__ rays, const float4* __restrict__ hits,
+                          unsigned long long n, uint32_t spp, const float2* __restrict__ xi,
+                          float tmax, float eps, float4* __restrict__ out) {
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 h = hits[i];
+    if (__float_as_uint(h.w) == kMiss) {
+        for (uint32_t k = 0; k < spp; ++k) {
+            out[2 * (i * spp + k)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            out[2 * (i * spp + k) + 1] = make_float4(0.0f, 0.0f, 1.0f, -1.0f);
+        }
+        return;
+    }
+    const float4 a = rays[2 * i], b = rays[2 * i + 1];
+    const uint32_t p = __float_as_uint(h.w);
+    const float* v0 = verts + 3ull * idx[3ull * p];
+    const float* v1 = verts + 3ull * idx[3ull * p + 1];
+    const float* v2 = verts + 3ull * idx[3ull * p + 2];
+    const float e1x = v1[0] - v0[0], e1y = v1[1] - v0[1], e1z = v1[2] - v0[2];
+    const float e2x = v2[0] - v0[0], e2y = v2[1] - v0[1], e2z = v2[2] - v0[2];
+    float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    const float len = sqrtf(nx * nx + ny * ny + nz * nz);
+    if (len > 0.0f) {
+        nx /= len;
+        ny /= len;
+        nz /= len;
+    } else {
+        nx = 0.0f;
+        ny = 0.0f;
+        nz = 1.0f;
+    }
+    if (nx * b.x + ny * b.y + nz * b.z > 0.0f) {
+        nx = -nx;
+        ny = -ny;
+        nz = -nz;
+    }
+    const float sg = copysignf(1.0f, nz);
+    const float ca = -1.0f / (sg + nz);
+    const float cb = nx * ny * ca;
+    const float t1x = 1.0f + sg * nx * nx * ca, t1y = sg * cb, t1z = -sg * nx;
+    const float t2x = cb, t2y = sg + ny * ny * ca, t2z = -ny;
+    const float ox = __fmaf_rn(h.x, b.x, a.x), oy = __fmaf_rn(h.x, b.y, a.y),
+                oz = __fmaf_rn(h.x, b.z, a.z);
+    for (uint32_t k = 0; k < spp; ++k) {
+        const float2 x = xi[i * spp + k];
+        const float rr = sqrtf(x.x), z = sqrtf(1.0f - x.x);
+        float sp, cp;
+        sincospif(2.0f * x.y, &sp, &cp);
+        out[2 * (i * spp + k)] = make_float4(ox, oy, oz, eps);
+        out[2 * (i * spp + k) + 1] =
+            make_float4(rr * cp * t1x + rr * sp * t2x + z * nx, rr * cp * t1y + rr * sp * t2y + z * ny,
+                        rr * cp * t1z + rr * sp * t2z + z * nz, tmax);
+    }
+}
+
 void free_bvh(vsr_scene* s) {
     dfree(s->d_nodes);
     dfree(s->d_tris);
@@ -536,6 +595,31 @@ vsr_status vsr_make_shadow_rays(const vsr_ray* prim_rays, const vsr_hit* prim_hi
         light[0], light[1], light[2], eps, reinterpret_cast<float4*>(out));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "shadow ray launch");
+    return VSR_OK;
+}
+
+vsr_status vsr_make_ao_rays(vsr_scene* s, const vsr_ray* prim_rays, const vsr_hit* prim_hits,
+                            uint64_t n, uint32_t spp, const float* xi, float tmax, float eps,
+                            vsr_ray* out, vsr_stream stream) {
+    g_err.clear();
+    if (!s) return fail(VSR_ERR_ARG, "scene is null");
+    if (spp < 1 || spp > 64) return fail(VSR_ERR_ARG, "spp must be in 1..64");
+    if (!std::isfinite(eps) || std::isnan(tmax)) return fail(VSR_ERR_ARG, "bad eps or tmax");
+    if (n == 0) return VSR_OK;
+    if (n * spp > (uint64_t)(std::numeric_limits<int>::max() - 1) * 256ull)
+        return fail(VSR_ERR_ARG, "too many rays");
+    vsr_status st = check_dev(prim_rays, s->device, "prim_rays", 16, n * 32);
+    if (st == VSR_OK) st = check_dev(prim_hits, s->device, "prim_hits", 16, n * 16);
+    if (st == VSR_OK) st = check_dev(xi, s->device, "xi", 8, n * spp * 8);
+    if (st == VSR_OK) st = check_dev(out, s->device, "out", 16, n * spp * 32);
+    if (st != VSR_OK) return st;
+    DeviceGuard g(s->device);
+    k_ao_rays<<<(unsigned)((n + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        s->d_verts, s->d_idx, reinterpret_cast<const float4*>(prim_rays),
+        reinterpret_cast<const float4*>(prim_hits), n, spp, reinterpret_cast<const float2*>(xi),
+        tmax, eps, reinterpret_cast<float4*>(out));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ao ray launch");
     return VSR_OK;
 }
 

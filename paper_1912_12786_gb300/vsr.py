@@ -85,6 +85,8 @@ _SIGS = {
     "vsr_render": ([P, P, ctypes.c_uint64, P, P, P, P, P, P], ctypes.c_int),
     "vsr_trace_backward": ([P, P, ctypes.c_uint64, P, P, P, P, P, P, P], ctypes.c_int),
     "vsr_scene_update": ([P, P, ctypes.c_uint32, P, P], ctypes.c_int),
+    "vsr_make_ao_rays": ([P, P, P, ctypes.c_uint64, ctypes.c_uint32, P, ctypes.c_float,
+                          ctypes.c_float, P, P], ctypes.c_int),
     "vsr_make_shadow_rays": ([P, P, ctypes.c_uint64, P, ctypes.c_float, P, P], ctypes.c_int),
     "vsr_get_device_error": ([P, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "vsr_bvh_build": ([P, ctypes.c_uint64, P, ctypes.c_uint32, P, ctypes.POINTER(P),
@@ -336,6 +338,14 @@ def vsr_scene_update(scene: Scene, verts=None, tex_index=0, texels=None, stream=
     """Replace vertex positions and/or one texture's texels (device tensors)."""
     _check(lib().vsr_scene_update(scene.handle, _ptr(verts), tex_index, _ptr(texels),
                                   _stream(stream)))
+
+
+def vsr_make_ao_rays(scene: Scene, prim_rays, prim_hits, spp: int, xi, tmax: float, eps: float,
+                     out, stream=None):
+    """Ambient-occlusion rays (spp per primary ray) into out (float32 [n*spp, 8])."""
+    _check(lib().vsr_make_ao_rays(scene.handle, _ptr(prim_rays), _ptr(prim_hits),
+                                  int(prim_rays.shape[0]), spp, _ptr(xi), float(tmax),
+                                  float(eps), _ptr(out), _stream(stream)))
 
 
 def vsr_make_shadow_rays(prim_rays, prim_hits, light, eps: float, out, stream=None):
