@@ -646,12 +646,35 @@ def main():
     ap.add_argument("--ref-stride", type=int, default=1)
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--leg", choices=["all", "large", "batch", "fwd_bwd"], default="all",
+                    help="run one auxiliary measurement alone (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg != "all":
+        return run_leg(args)
     return run_ours(args)
+
+
+def run_leg(args):
+    """One auxiliary measurement alone (for profiling): prints its JSON."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    from paper_1912_12786_gb300 import vsr as V
+    V.lib()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    if args.leg == "large":
+        res = large_bench(V, torch, dev, flush, stream, args.steps)
+    elif args.leg == "batch":
+        res = batch_bench(V, torch, dev, flush, stream, args.steps)
+    else:
+        res = fwd_bwd(V, torch, dev, flush, stream, args.steps, args.warmup)
+    print(json.dumps({"leg": args.leg, **res}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":
