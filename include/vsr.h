@@ -352,6 +352,31 @@ vsr_status vsr_trace_backward(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
                               const vsr_trace_params* params, vsr_stream stream);
 
 /*
+ * Ambient-occlusion shading on the closest-hit query:
+ *   c = albedo_rgb(uv) * (1 - occluded / spp)      (background for a miss)
+ * where the spp occlusion rays of pixel i are built exactly as
+ * vsr_make_ao_rays builds them from the uniforms xi[i*spp + k] and traced
+ * any-hit with the same intersector (static dispatch).
+ *   image device float32 [n*3]; occlusion device float32 [n] (occluded
+ *   fraction) or NULL; xi device float32 [n*spp*2]; spp 1..64.
+ */
+vsr_status vsr_render_ao(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
+                         const vsr_intersector* isect, uint32_t spp, const float* xi,
+                         float ao_tmax, float eps, const vsr_shade_params* shade, float* image,
+                         float* occlusion, vsr_stream stream);
+
+/*
+ * Adjoint of vsr_render_ao with respect to the colour texels of texture
+ * shade->grad_tex (RGBA32F) at fixed visibility: the primary hit and the
+ * occlusion rays are traced again and dL/dc * (1 - occluded/spp) * bilinear
+ * weight is accumulated into grad_texels [w*h*4] (r, g, b channels, atomics).
+ */
+vsr_status vsr_render_ao_backward(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
+                                  const vsr_intersector* isect, uint32_t spp, const float* xi,
+                                  float ao_tmax, float eps, const vsr_shade_params* shade,
+                                  const float* dL_dimage, float* grad_texels, vsr_stream stream);
+
+/*
  * Replace the scene's vertex positions and/or one texture's texels with
  * device data (same sizes as at creation; NULL leaves them unchanged).  After
  * a vertex update the triangle layout is rebuilt and the BVH boxes are refit

@@ -66,8 +66,8 @@ class FrozenShading:
 
     # -- forward ---------------------------------------------------------
 
-    def colours(self, verts, texels, sel=None):
-        """FP64 colours of the hit pixels (or of the subset `sel` of them)."""
+    def _surface(self, verts, sel):
+        """FP64 (uv, e1, e2, d, textured) of the frozen triangles."""
         idx = self.idx if sel is None else self.idx[sel]
         o = self.o if sel is None else self.o[sel]
         d = self.d if sel is None else self.d[sel]
@@ -83,6 +83,11 @@ class FrozenShading:
         tuv = torch.linalg.solve(M, (o - a).unsqueeze(-1)).squeeze(-1)
         u, v = tuv[:, 1], tuv[:, 2]
         uv = (1 - u - v)[:, None] * tc[:, 0] + u[:, None] * tc[:, 1] + v[:, None] * tc[:, 2]
+        return uv, e1, e2, d, textured
+
+    def colours(self, verts, texels, sel=None):
+        """FP64 colours of the hit pixels (or of the subset `sel` of them)."""
+        uv, e1, e2, d, textured = self._surface(verts, sel)
         alb = self.bilinear(texels, uv)
         alb = torch.where(textured[:, None], alb, torch.ones_like(alb))
         m = torch.linalg.cross(e1, e2)
@@ -207,3 +212,21 @@ class FrozenShading:
                 self._corners = (ii.numpy(), jj.numpy(), self.textured.numpy())
         ii, jj, tex = self._corners
         return np.flatnonzero((ii == i).any(1) & (jj == j).any(1) & tex)
+
+
+class FrozenAO(FrozenShading):
+    """Ambient-occlusion shading at fixed visibility:
+    c = albedo_rgb(uv) * visibility, visibility = 1 - occluded fraction of the
+    pixel's occlusion rays (given, from the oracle's own traversal)."""
+
+    def __init__(self, scene, rays, prims, visibility, background=(0.0, 0.0, 0.0), tex=0):
+        super().__init__(scene, rays, prims, light=(0.0, 0.0, 1.0), background=background,
+                         tex=tex)
+        self.vis = _t(np.asarray(visibility, np.float64)[self.hit])
+
+    def colours(self, verts, texels, sel=None):
+        uv, _, _, _, textured = self._surface(verts, sel)
+        alb = self.bilinear(texels, uv)
+        alb = torch.where(textured[:, None], alb, torch.ones_like(alb))
+        vis = self.vis if sel is None else self.vis[sel]
+        return alb * vis[:, None]

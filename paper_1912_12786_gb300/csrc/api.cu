@@ -203,44 +203,12 @@ __global__ void k_ao_rays(const float* __restrict__ verts, const uint32_t* __res
         return;
     }
     const float4 a = rays[2 * i], b = rays[2 * i + 1];
-    const uint32_t p = __float_as_uint(h.w);
-    const float* v0 = verts + 3ull * idx[3ull * p];
-    const float* v1 = verts + 3ull * idx[3ull * p + 1];
-    const float* v2 = verts + 3ull * idx[3ull * p + 2];
-    const float e1x = v1[0] - v0[0], e1y = v1[1] - v0[1], e1z = v1[2] - v0[2];
-    const float e2x = v2[0] - v0[0], e2y = v2[1] - v0[1], e2z = v2[2] - v0[2];
-    float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-    const float len = sqrtf(nx * nx + ny * ny + nz * nz);
-    if (len > 0.0f) {
-        nx /= len;
-        ny /= len;
-        nz /= len;
-    } else {
-        nx = 0.0f;
-        ny = 0.0f;
-        nz = 1.0f;
-    }
-    if (nx * b.x + ny * b.y + nz * b.z > 0.0f) {
-        nx = -nx;
-        ny = -ny;
-        nz = -nz;
-    }
-    const float sg = copysignf(1.0f, nz);
-    const float ca = -1.0f / (sg + nz);
-    const float cb = nx * ny * ca;
-    const float t1x = 1.0f + sg * nx * nx * ca, t1y = sg * cb, t1z = -sg * nx;
-    const float t2x = cb, t2y = sg + ny * ny * ca, t2z = -ny;
+    const AoFrame f = ao_frame(verts, idx, __float_as_uint(h.w), b.x, b.y, b.z);
     const float ox = __fmaf_rn(h.x, b.x, a.x), oy = __fmaf_rn(h.x, b.y, a.y),
                 oz = __fmaf_rn(h.x, b.z, a.z);
     for (uint32_t k = 0; k < spp; ++k) {
-        const float2 x = xi[i * spp + k];
-        const float rr = sqrtf(x.x), z = sqrtf(1.0f - x.x);
-        float sp, cp;
-        sincospif(2.0f * x.y, &sp, &cp);
         out[2 * (i * spp + k)] = make_float4(ox, oy, oz, eps);
-        out[2 * (i * spp + k) + 1] =
-            make_float4(rr * cp * t1x + rr * sp * t2x + z * nx, rr * cp * t1y + rr * sp * t2y + z * ny,
-                        rr * cp * t1z + rr * sp * t2z + z * nz, tmax);
+        out[2 * (i * spp + k) + 1] = ao_direction(f, xi[i * spp + k], tmax);
     }
 }
 
@@ -732,6 +700,68 @@ extern "C" vsr_status vsr_trace_backward(vsr_scene* s, const vsr_ray* rays, uint
     cudaError_t e = launch_render_backward(a, is->kind, shd, s->d_verts, s->d_idx, dL_dimage,
                                            grad_verts, grad_texels);
     if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+    return VSR_OK;
+}
+
+namespace {
+
+vsr_status prepare_ao(vsr_scene* s, uint64_t n, uint32_t spp, const float* xi, float tmax,
+                      float eps) {
+    if (spp < 1 || spp > 64) return fail(VSR_ERR_ARG, "spp must be in 1..64");
+    if (!std::isfinite(eps) || std::isnan(tmax)) return fail(VSR_ERR_ARG, "bad eps or tmax");
+    if (n) return check_dev(xi, s->device, "xi", 8, n * spp * 8);
+    return VSR_OK;
+}
+
+}  // namespace
+
+extern "C" vsr_status vsr_render_ao(vsr_scene* s, const vsr_ray* rays, uint64_t n,
+                                    const vsr_intersector* is, uint32_t spp, const float* xi,
+                                    float ao_tmax, float eps, const vsr_shade_params* sh,
+                                    float* image, float* occlusion, vsr_stream stream) {
+    g_err.clear();
+    LaunchArgs a;
+    ShadeDev shd;
+    vsr_status st = prepare_render(s, rays, n, is, sh, nullptr, a, shd);
+    if (st == VSR_OK) st = prepare_ao(s, n, spp, xi, ao_tmax, eps);
+    if (st != VSR_OK) return st;
+    if (n == 0) return VSR_OK;
+    st = check_dev(image, s->device, "image", 4, n * 12);
+    if (st == VSR_OK && occlusion) st = check_dev(occlusion, s->device, "occlusion", 4, n * 4);
+    if (st != VSR_OK) return st;
+    AoArgs ao{shd, s->d_verts, s->d_idx, spp, reinterpret_cast<const float2*>(xi), ao_tmax, eps,
+              image, occlusion, nullptr, nullptr};
+    a.stream = reinterpret_cast<cudaStream_t>(stream);
+    DeviceGuard g(s->device);
+    cudaError_t e = launch_render_ao(a, is->kind, ao, false);
+    if (e != cudaSuccess) return cuda_fail(e, "ao render launch");
+    return VSR_OK;
+}
+
+extern "C" vsr_status vsr_render_ao_backward(vsr_scene* s, const vsr_ray* rays, uint64_t n,
+                                             const vsr_intersector* is, uint32_t spp,
+                                             const float* xi, float ao_tmax, float eps,
+                                             const vsr_shade_params* sh, const float* dL_dimage,
+                                             float* grad_texels, vsr_stream stream) {
+    g_err.clear();
+    LaunchArgs a;
+    ShadeDev shd;
+    vsr_status st = prepare_render(s, rays, n, is, sh, nullptr, a, shd);
+    if (st == VSR_OK) st = prepare_ao(s, n, spp, xi, ao_tmax, eps);
+    if (st != VSR_OK) return st;
+    if (shd.grad_tex == VSR_NO_TEXTURE || s->h_tex[shd.grad_tex].fmt != VSR_TEX_RGBA32F)
+        return fail(VSR_ERR_ARG, "texel gradients need an RGBA32F grad_tex");
+    if (n == 0) return VSR_OK;
+    const TexDesc& t = s->h_tex[shd.grad_tex];
+    st = check_dev(dL_dimage, s->device, "dL_dimage", 4, n * 12);
+    if (st == VSR_OK) st = check_dev(grad_texels, s->device, "grad_texels", 4, 16ull * t.w * t.h);
+    if (st != VSR_OK) return st;
+    AoArgs ao{shd, s->d_verts, s->d_idx, spp, reinterpret_cast<const float2*>(xi), ao_tmax, eps,
+              nullptr, nullptr, dL_dimage, grad_texels};
+    a.stream = reinterpret_cast<cudaStream_t>(stream);
+    DeviceGuard g(s->device);
+    cudaError_t e = launch_render_ao(a, is->kind, ao, true);
+    if (e != cudaSuccess) return cuda_fail(e, "ao backward launch");
     return VSR_OK;
 }
 

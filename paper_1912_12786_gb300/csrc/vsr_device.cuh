@@ -474,6 +474,54 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
     return false;
 }
 
+// Ambient-occlusion sampling frame at a hit: face normal of the triangle
+// (v1 - v0) x (v2 - v0) turned against the ray direction d, tangent frame of
+// Duff et al. (2017, "Building an orthonormal basis, revisited").  FP32.
+struct AoFrame {
+    float nx, ny, nz, t1x, t1y, t1z, t2x, t2y, t2z;
+};
+
+__device__ __forceinline__ AoFrame ao_frame(const float* __restrict__ verts,
+                                            const uint32_t* __restrict__ idx, uint32_t prim,
+                                            float dx, float dy, float dz) {
+    const float* v0 = verts + 3ull * idx[3ull * prim];
+    const float* v1 = verts + 3ull * idx[3ull * prim + 1];
+    const float* v2 = verts + 3ull * idx[3ull * prim + 2];
+    const float e1x = v1[0] - v0[0], e1y = v1[1] - v0[1], e1z = v1[2] - v0[2];
+    const float e2x = v2[0] - v0[0], e2y = v2[1] - v0[1], e2z = v2[2] - v0[2];
+    float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    const float len = sqrtf(nx * nx + ny * ny + nz * nz);
+    if (len > 0.0f) {
+        nx /= len;
+        ny /= len;
+        nz /= len;
+    } else {
+        nx = 0.0f;
+        ny = 0.0f;
+        nz = 1.0f;
+    }
+    if (nx * dx + ny * dy + nz * dz > 0.0f) {
+        nx = -nx;
+        ny = -ny;
+        nz = -nz;
+    }
+    const float sg = copysignf(1.0f, nz);
+    const float ca = -1.0f / (sg + nz);
+    const float cb = nx * ny * ca;
+    return AoFrame{nx, ny, nz, 1.0f + sg * nx * nx * ca, sg * cb, -sg * nx,
+                   cb, sg + ny * ny * ca, -ny};
+}
+
+// Cosine-distributed direction for the uniforms (x1, x2).
+__device__ __forceinline__ float4 ao_direction(const AoFrame& f, float2 x, float tmax) {
+    const float rr = sqrtf(x.x), z = sqrtf(1.0f - x.x);
+    float sp, cp;
+    sincospif(2.0f * x.y, &sp, &cp);
+    return make_float4(rr * cp * f.t1x + rr * sp * f.t2x + z * f.nx,
+                       rr * cp * f.t1y + rr * sp * f.t2y + z * f.ny,
+                       rr * cp * f.t1z + rr * sp * f.t2z + z * f.nz, tmax);
+}
+
 // Miss record normalisation shared by all kernels.
 __device__ __forceinline__ void finish_miss(Best& best) {
     if (best.prim == kMiss) {

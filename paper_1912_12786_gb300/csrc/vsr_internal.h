@@ -73,6 +73,21 @@ cudaError_t launch_batch(const BatchLaunch& b, int kind, int query, cudaStream_t
 // Grid that launch_batch uses for b (after its shared-memory attribute is set).
 cudaError_t batch_grid(const BatchLaunch& b, int kind, int query, uint32_t* grid);
 
+// Ambient-occlusion render and its texel adjoint (render.cu).
+struct AoArgs {
+    ShadeDev sh;
+    const float* verts;
+    const uint32_t* idx;
+    uint32_t spp;
+    const float2* xi;
+    float tmax, eps;
+    float* image;        // forward
+    float* occ;          // forward, optional
+    const float* g;      // backward
+    float* grad_texels;  // backward
+};
+cudaError_t launch_render_ao(const LaunchArgs& a, int kind, const AoArgs& ao, bool backward);
+
 // Bottom-up refit over node lists grouped by level, deepest first
 // (level_offsets is a host array of levels + 1 entries).
 cudaError_t launch_refit(float4* nodes, const uint32_t* level_nodes,

@@ -127,3 +127,18 @@ def test_gradient_matches_central_differences(small_sphere):
     reft = gt[tj, ti, tc]
     assert np.linalg.norm(reft) > 0
     np.testing.assert_allclose(fdt, reft, rtol=1e-6, atol=1e-9 * np.abs(reft).max())
+
+
+def test_ao_shading_closed_form():
+    """c = albedo * visibility; with a 1x1 texture a and target 0,
+    dL/dT = sum over pixels of 2 * a * vis^2; untextured pixels have albedo 1."""
+    sc = _tri_scene()
+    pts = np.array([[0.1, 0.1], [0.3, 0.2], [0.05, 0.6]], np.float32)
+    rays = _ortho(pts)
+    vis = np.array([0.25, 1.0, 0.5])
+    fa = A.FrozenAO(sc, rays, np.zeros(3, np.uint32), vis)
+    a = sc.textures[0].texels[0, 0, :3].astype(np.float64)
+    img = fa.image(A._t(sc.verts), A._t(sc.textures[0].texels)).numpy()
+    np.testing.assert_allclose(img, vis[:, None] * a[None], rtol=1e-12)
+    _, _, gt, _ = fa.loss_grad(sc.verts, sc.textures[0].texels, np.zeros((3, 3)))
+    np.testing.assert_allclose(gt[0, 0, :3], 2 * a * float((vis ** 2).sum()), rtol=1e-12)

@@ -6,7 +6,8 @@ Checks: primary closest hits on a seeded sample against the oracle; the GPU
 ambient-occlusion ray construction against the oracle's (origins bit-exact,
 directions within 2e-6); any-hit parity on oracle-made AO rays for the
 procedural-alpha and counting intersectors in static and dynamic dispatch;
-whole-launch invariants over all 8.3 M AO rays.
+whole-launch invariants over all 8.3 M AO rays; the ambient-occlusion render
+and its texel adjoint against the FP64 reference.
 """
 import numpy as np
 import pytest
@@ -97,3 +98,64 @@ def test_full_ao_pass_invariants(large):
     active = (ao[:, 7] > 0).float().mean().item()
     assert 0.3 < active < 0.99
     assert V.vsr_get_device_error(s) == 0
+
+
+def test_ao_render_and_texel_gradients(large):
+    """c = albedo(uv) * (1 - occluded fraction of 4 AO rays) and its gradient
+    with respect to the colour texels at fixed visibility, against the FP64
+    reference, whose occlusion comes from the oracle's own AO rays and
+    traversal.  Pixels whose primary primitive or occluded count differs
+    (primary near-ties; AO directions agree only to 2e-6) are counted and
+    bounded, and left out of the comparison by zeroing their adjoint on both
+    sides."""
+    from oracle import adjoint as A
+    V, sc, rays, blob, s, xi, eps = large
+    ref, st = O.trace_bvh(sc, blob, rays, "proc_alpha", "closest")
+    ao = O.ao_rays(sc, rays, O.hits_raw(ref), SPP, xi, TMAX, eps)
+    aoh, _ = O.trace_bvh(sc, blob, ao, "proc_alpha", "any")
+    occ = (aoh["prim"] != O.NONE).reshape(-1, SPP).mean(1)
+    fa = A.FrozenAO(sc, rays, ref["prim"], 1.0 - occ)
+    tex = sc.textures[0].texels
+    proc = V.intersector("proc_alpha")
+    shade = V.shade_params((0.0, 0.0, 1.0), grad_tex=0)
+    d_rays = torch.from_numpy(rays).cuda()
+    d_xi = torch.from_numpy(xi).cuda()
+    hits = torch.empty((len(rays), 4), dtype=torch.float32, device="cuda")
+    V.vsr_trace(s, d_rays, proc, "closest", hits)
+    img = torch.empty((len(rays), 3), dtype=torch.float32, device="cuda")
+    gocc = torch.empty(len(rays), dtype=torch.float32, device="cuda")
+    V.vsr_render_ao(s, d_rays, proc, SPP, d_xi, TMAX, eps, shade, img, gocc)
+    torch.cuda.synchronize()
+    gprim = hits.cpu().numpy()[:, 3].view(np.uint32)
+    same = (gprim == ref["prim"]) & (np.abs(gocc.cpu().numpy() - occ) < 1e-6)
+    assert (~same).sum() <= 1e-3 * len(rays), int((~same).sum())
+    assert np.all(same[(gprim == O.NONE) & (ref["prim"] == O.NONE)])
+    ref_img = fa.image(A._t(sc.verts), A._t(tex)).numpy()
+    err = np.abs(img.cpu().numpy()[same] - ref_img[same]).max(1)
+    assert np.quantile(err, 0.999) < 2e-5 and err.max() < 1e-3, (np.quantile(err, 0.999), err.max())
+    rng = np.random.default_rng(31)
+    tt = tex.copy()
+    tt[..., :3] += (0.01 * rng.standard_normal(tex[..., :3].shape)).astype(np.float32)
+    target = fa.image(A._t(sc.verts), A._t(tt)).numpy()
+    _, _, _, g = fa.loss_grad(sc.verts, tex, target)
+    g[~same] = 0.0
+    _, gt_ref = fa.vjp(sc.verts, tex, g)
+    gt = torch.zeros(tex.shape, dtype=torch.float32, device="cuda")
+    V.vsr_render_ao_backward(s, d_rays, proc, SPP, d_xi, TMAX, eps, shade,
+                             torch.from_numpy(g.astype(np.float32)).cuda(), gt)
+    torch.cuda.synchronize()
+    gt = gt.cpu().numpy()
+    rel = np.linalg.norm(gt - gt_ref) / np.linalg.norm(gt_ref)
+    assert rel < 1e-3, rel
+    assert np.all(gt[..., 3] == 0)
+    # central differences of the loss over the agreeing pixels: exact up to
+    # rounding, since the loss is quadratic in the texels at fixed visibility
+    fa_same = A.FrozenAO(sc, rays, np.where(same, ref["prim"], O.NONE), 1.0 - occ)
+    tj = rng.integers(0, tex.shape[0], 256)
+    ti = rng.integers(0, tex.shape[1], 256)
+    tc = rng.integers(0, 3, 256)
+    fd = np.array([fa_same.fd_texel(sc.verts, tex, target, j, i, c)
+                   for j, i, c in zip(tj, ti, tc)])
+    assert np.count_nonzero(fd) > 128
+    assert np.linalg.norm(gt[tj, ti, tc] - fd) <= 1e-3 * np.linalg.norm(fd)
+    assert V.vsr_get_device_error(s) == 0, V.vsr_last_error()
