@@ -125,7 +125,8 @@ class FrozenShading:
         tx = _t(texels).requires_grad_(True)
         col = self.colours(v, tx)
         (col * _t(g)[self.hit]).sum().backward()
-        return v.grad.numpy(), tx.grad.numpy()
+        gv = torch.zeros_like(v) if v.grad is None else v.grad
+        return gv.numpy(), tx.grad.numpy()
 
     def loss_grad(self, verts, texels, target):
         """L = sum |image - target|^2 and its gradients (FP64)."""
@@ -205,28 +206,60 @@ class FrozenShading:
                 u, v = tuv[:, 1], tuv[:, 2]
                 uv = (1 - u - v)[:, None] * tc[:, 0] + u[:, None] * tc[:, 1] \
                     + v[:, None] * tc[:, 2]
-                x0 = torch.floor(uv[:, 0] * self.W - 0.5).long()
-                y0 = torch.floor(uv[:, 1] * self.H - 0.5).long()
-                ii = torch.stack([x0.clamp(0, self.W - 1), (x0 + 1).clamp(0, self.W - 1)], 1)
-                jj = torch.stack([y0.clamp(0, self.H - 1), (y0 + 1).clamp(0, self.H - 1)], 1)
-                self._corners = (ii.numpy(), jj.numpy(), self.textured.numpy())
+                self._corners = self._footprint(uv)
         ii, jj, tex = self._corners
         return np.flatnonzero((ii == i).any(1) & (jj == j).any(1) & tex)
+
+    def _footprint(self, uv):
+        """Clamped column and row indices of the 2x2 texels each uv reads."""
+        with torch.no_grad():
+            x0 = torch.floor(uv[:, 0] * self.W - 0.5).long()
+            y0 = torch.floor(uv[:, 1] * self.H - 0.5).long()
+            ii = torch.stack([x0.clamp(0, self.W - 1), (x0 + 1).clamp(0, self.W - 1)], 1)
+            jj = torch.stack([y0.clamp(0, self.H - 1), (y0 + 1).clamp(0, self.H - 1)], 1)
+        return ii.numpy(), jj.numpy(), self.textured.numpy()
 
 
 class FrozenAO(FrozenShading):
     """Ambient-occlusion shading at fixed visibility:
     c = albedo_rgb(uv) * visibility, visibility = 1 - occluded fraction of the
-    pixel's occlusion rays (given, from the oracle's own traversal)."""
+    pixel's occlusion rays (given, from the oracle's own traversal).
 
-    def __init__(self, scene, rays, prims, visibility, background=(0.0, 0.0, 0.0), tex=0):
+    bary  optional float32 [n, 2]: the (u, v) the closest-hit traversal
+          returned for each pixel.  When given, uv is interpolated in FP64 at
+          those barycentrics instead of at the FP64 ray-plane solution, so the
+          image is the one defined by the traversal's own hit record (on small
+          triangles with a texture stretched over each, the FP32 hit point
+          moves uv by a sizable part of a texel).  uv is then constant in the
+          vertices: only texel gradients are defined.
+    """
+
+    def __init__(self, scene, rays, prims, visibility, background=(0.0, 0.0, 0.0), tex=0,
+                 bary=None):
         super().__init__(scene, rays, prims, light=(0.0, 0.0, 1.0), background=background,
                          tex=tex)
         self.vis = _t(np.asarray(visibility, np.float64)[self.hit])
+        self.bary = None if bary is None else _t(np.asarray(bary, np.float32)[self.hit])
+
+    def _uv_at_bary(self, sel):
+        b = self.bary if sel is None else self.bary[sel]
+        tc = self.tc if sel is None else self.tc[sel]
+        u, v = b[:, 0], b[:, 1]
+        return (1 - u - v)[:, None] * tc[:, 0] + u[:, None] * tc[:, 1] + v[:, None] * tc[:, 2]
 
     def colours(self, verts, texels, sel=None):
-        uv, _, _, _, textured = self._surface(verts, sel)
+        if self.bary is None:
+            uv, _, _, _, textured = self._surface(verts, sel)
+        else:
+            uv = self._uv_at_bary(sel)
+            textured = self.textured if sel is None else self.textured[sel]
         alb = self.bilinear(texels, uv)
         alb = torch.where(textured[:, None], alb, torch.ones_like(alb))
         vis = self.vis if sel is None else self.vis[sel]
         return alb * vis[:, None]
+
+    def pixels_of_texel(self, verts, j, i):
+        if self.bary is not None and getattr(self, "_corners", None) is None:
+            uv = self._uv_at_bary(None)
+            self._corners = self._footprint(uv)
+        return super().pixels_of_texel(verts, j, i)

@@ -142,3 +142,36 @@ def test_ao_shading_closed_form():
     np.testing.assert_allclose(img, vis[:, None] * a[None], rtol=1e-12)
     _, _, gt, _ = fa.loss_grad(sc.verts, sc.textures[0].texels, np.zeros((3, 3)))
     np.testing.assert_allclose(gt[0, 0, :3], 2 * a * float((vis ** 2).sum()), rtol=1e-12)
+
+
+def test_ao_bary_option_matches_the_solved_uv():
+    """On a well-conditioned triangle the oracle's FP32 (u, v) agree with the
+    FP64 ray-plane solution to float32 rounding, so FrozenAO gives the same
+    image and texel gradients with and without `bary` (to ~1e-6 relative),
+    and differs from them when the barycentrics are shifted by half a texel."""
+    rng = np.random.default_rng(5)
+    tex = rng.uniform(0, 1, (16, 16, 4)).astype(np.float32)
+    sc = _tri_scene(tex=tex)
+    pts = rng.uniform(0.02, 0.45, (64, 2)).astype(np.float32)
+    rays = _ortho(pts)
+    hits, _ = O.trace_list(sc, rays, "default", "closest")
+    assert np.all(hits["prim"] == 0)
+    bary = np.stack([hits["u"], hits["v"]], 1)
+    vis = rng.choice([0.25, 0.5, 1.0], len(pts))
+    target = np.zeros((len(pts), 3))
+    fa = A.FrozenAO(sc, rays, hits["prim"], vis)
+    fb = A.FrozenAO(sc, rays, hits["prim"], vis, bary=bary)
+    ia = fa.image(A._t(sc.verts), A._t(tex)).numpy()
+    ib = fb.image(A._t(sc.verts), A._t(tex)).numpy()
+    np.testing.assert_allclose(ib, ia, rtol=1e-5, atol=1e-6)
+    _, _, ga, _ = fa.loss_grad(sc.verts, tex, target)
+    _, _, gb, _ = fb.loss_grad(sc.verts, tex, target)
+    assert np.linalg.norm(gb - ga) <= 1e-5 * np.linalg.norm(ga)
+    for k in range(8):
+        j, i, c = rng.integers(0, 16), rng.integers(0, 16), rng.integers(0, 3)
+        assert np.array_equal(fb.pixels_of_texel(sc.verts, j, i),
+                              fa.pixels_of_texel(sc.verts, j, i))
+        assert math.isclose(fb.fd_texel(sc.verts, tex, target, j, i, c), gb[j, i, c],
+                            rel_tol=1e-7, abs_tol=1e-12)
+    shifted = A.FrozenAO(sc, rays, hits["prim"], vis, bary=bary + np.float32(0.5 / 16))
+    assert np.abs(shifted.image(A._t(sc.verts), A._t(tex)).numpy() - ia).max() > 1e-2
