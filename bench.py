@@ -583,8 +583,8 @@ def large_bench(V, torch, dev, flush, stream, steps):
     heightfield): 1920x1080 primary closest hits (procedural alpha), then 4
     ambient-occlusion rays per pixel (tmax 0.5) traced any-hit with the
     procedural-alpha and counting intersectors, static and dynamic; then the
-    fused ambient-occlusion render and its texel adjoint (forward + backward
-    per frame)."""
+    ambient-occlusion render and its texel adjoint (forward + backward per
+    frame)."""
     from paper_1912_12786_gb300.inputs import scenes
     sc, rays = scenes.large_incoherent()
     blob = sc.bvh()
@@ -635,17 +635,18 @@ def large_bench(V, torch, dev, flush, stream, steps):
     t = out["ao_any/proc_alpha/static_ms"]
     out["ao_any/proc_alpha/static_algorithmic_bytes"] = b
     out["ao_any/proc_alpha/static_algorithmic_GBs"] = round(b / (t / 1e3) / 1e9, 1)
-    # ambient-occlusion render (primary + 4 AO rays per pixel, shading fused)
-    # and its adjoint with respect to the colour texels (both traced again)
+    # ambient-occlusion render (primary trace, occlusion count with one thread
+    # per AO ray, shading) and its texel adjoint from the saved hits
     eps = scenes.shadow_eps(sc)
     shade = V.shade_params((0.0, 0.0, 1.0), grad_tex=0)
     img = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    occ = torch.empty(n, dtype=torch.float32, device=dev)
     g_img = torch.ones((n, 3), dtype=torch.float32, device=dev)
     tx = sc.textures[0]
     g_tex = torch.zeros((tx.h, tx.w, 4), dtype=torch.float32, device=dev)
-    fwd = lambda: V.vsr_render_ao(s, d_rays, proc, spp, xi, 0.5, eps, shade, img, None, stream)
-    bwd = lambda: V.vsr_render_ao_backward(s, d_rays, proc, spp, xi, 0.5, eps, shade, g_img,
-                                           g_tex, stream)
+    fwd = lambda: V.vsr_render_ao(s, d_rays, proc, spp, xi, 0.5, eps, shade, img, hits, occ,
+                                  stream)
+    bwd = lambda: V.vsr_render_ao_backward(s, hits, occ, shade, g_img, g_tex, stream)
     tf = timed(fwd, reps)
     tb = timed(bwd, reps)
     tfb = timed(lambda: (fwd(), bwd()), reps)

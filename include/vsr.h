@@ -356,24 +356,32 @@ vsr_status vsr_trace_backward(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
  *   c = albedo_rgb(uv) * (1 - occluded / spp)      (background for a miss)
  * where the spp occlusion rays of pixel i are built exactly as
  * vsr_make_ao_rays builds them from the uniforms xi[i*spp + k] and traced
- * any-hit with the same intersector (static dispatch).
- *   image device float32 [n*3]; occlusion device float32 [n] (occluded
- *   fraction) or NULL; xi device float32 [n*spp*2]; spp 1..64.
+ * any-hit with the same intersector (static dispatch).  Three launches on
+ * `stream`: the closest-hit trace into `hits`, the occlusion count (one
+ * thread per occlusion ray) and the shading.
+ *   image     device float32 [n*3], written
+ *   hits      device vsr_hit [n], written: the primary closest hits
+ *   occlusion device float32 [n], written: occluded fraction (0 for a miss)
+ *   xi        device float32 [n*spp*2]; spp 1..64
+ * hits and occlusion are the state vsr_render_ao_backward needs.  Errors as
+ * vsr_trace.
  */
 vsr_status vsr_render_ao(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
                          const vsr_intersector* isect, uint32_t spp, const float* xi,
                          float ao_tmax, float eps, const vsr_shade_params* shade, float* image,
-                         float* occlusion, vsr_stream stream);
+                         vsr_hit* hits, float* occlusion, vsr_stream stream);
 
 /*
  * Adjoint of vsr_render_ao with respect to the colour texels of texture
- * shade->grad_tex (RGBA32F) at fixed visibility: the primary hit and the
- * occlusion rays are traced again and dL/dc * (1 - occluded/spp) * bilinear
- * weight is accumulated into grad_texels [w*h*4] (r, g, b channels, atomics).
+ * shade->grad_tex (RGBA32F) at fixed visibility, from the forward's hits and
+ * occlusion (no traversal): dL/dc * (1 - occlusion) * bilinear weight is
+ * accumulated into grad_texels [w*h*4] (r, g, b channels; atomics, so the
+ * last bits may vary between runs).  The scene must be unchanged since the
+ * forward.  A hit record whose primitive index is out of range is skipped
+ * and sets bit 3 of the device error word.
  */
-vsr_status vsr_render_ao_backward(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
-                                  const vsr_intersector* isect, uint32_t spp, const float* xi,
-                                  float ao_tmax, float eps, const vsr_shade_params* shade,
+vsr_status vsr_render_ao_backward(vsr_scene* scene, const vsr_hit* hits, const float* occlusion,
+                                  uint64_t n, const vsr_shade_params* shade,
                                   const float* dL_dimage, float* grad_texels, vsr_stream stream);
 
 /*
@@ -394,7 +402,8 @@ vsr_status vsr_scene_update(vsr_scene* scene, const float* verts, uint32_t tex_i
  * (x1, x2): sqrt(x1) cos(2 pi x2) t1 + sqrt(x1) sin(2 pi x2) t2 +
  * sqrt(1 - x1) n, with the tangent frame (t1, t2) of Duff et al. (2017,
  * "Building an orthonormal basis, revisited"); interval (eps, tmax).  A
- * primary miss gives inactive rays.  FP32.
+ * primary miss gives inactive rays, and so does a hit record whose primitive
+ * is out of range (device error bit 3).  FP32.
  *   prim_rays/prim_hits device [n]; xi device float32 [n*spp*2];
  *   out device vsr_ray [n*spp].  spp 1..64.
  */
@@ -411,9 +420,11 @@ const char* vsr_last_error(void);
  *   bit 0: a traversal stack overflowed;
  *   bit 1: a ray visited more nodes than the BVH holds;
  *   bit 2: a render or backward kernel found a load whose address did not
- *          match its width and skipped it (vsr_last_error() names the line).
+ *          match its width and skipped it (vsr_last_error() names the line);
+ *   bit 3: a caller-supplied hit record named a primitive out of range
+ *          (skipped; vsr_make_ao_rays gives its rays inactive).
  * Bits 0 and 1 end that ray as a miss; neither can happen with a validated
- * blob (each node is visited at most once per ray).  All three checks exist
+ * blob (each node is visited at most once per ray).  All four checks exist
  * so that a corrupted structure or a bad address gives an error instead of
  * a fault or an endless loop. */
 vsr_status vsr_get_device_error(vsr_scene* scene, uint32_t* word);

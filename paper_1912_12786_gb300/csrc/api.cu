@@ -191,11 +191,14 @@ __global__ void k_shadow_rays(const float4* __restrict__ rays, const float4* __r
 __global__ void k_ao_rays(const float* __restrict__ verts, const uint32_t* __restrict__ idx,
                           const float4* __restrict__ rays, const float4* __restrict__ hits,
                           unsigned long long n, uint32_t spp, const float2* __restrict__ xi,
-                          float tmax, float eps, float4* __restrict__ out) {
+                          float tmax, float eps, uint32_t nprims, uint32_t* __restrict__ err,
+                          float4* __restrict__ out) {
     const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 h = hits[i];
-    if (__float_as_uint(h.w) == kMiss) {
+    const bool bad = __float_as_uint(h.w) != kMiss && __float_as_uint(h.w) >= nprims;
+    if (bad) atomicOr(err, kErrHit);
+    if (__float_as_uint(h.w) == kMiss || bad) {
         for (uint32_t k = 0; k < spp; ++k) {
             out[2 * (i * spp + k)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             out[2 * (i * spp + k) + 1] = make_float4(0.0f, 0.0f, 1.0f, -1.0f);
@@ -585,7 +588,7 @@ vsr_status vsr_make_ao_rays(vsr_scene* s, const vsr_ray* prim_rays, const vsr_hi
     k_ao_rays<<<(unsigned)((n + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
         s->d_verts, s->d_idx, reinterpret_cast<const float4*>(prim_rays),
         reinterpret_cast<const float4*>(prim_hits), n, spp, reinterpret_cast<const float2*>(xi),
-        tmax, eps, reinterpret_cast<float4*>(out));
+        tmax, eps, s->dev.nprims, s->dev.err, reinterpret_cast<float4*>(out));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "ao ray launch");
     return VSR_OK;
@@ -709,6 +712,9 @@ vsr_status prepare_ao(vsr_scene* s, uint64_t n, uint32_t spp, const float* xi, f
                       float eps) {
     if (spp < 1 || spp > 64) return fail(VSR_ERR_ARG, "spp must be in 1..64");
     if (!std::isfinite(eps) || std::isnan(tmax)) return fail(VSR_ERR_ARG, "bad eps or tmax");
+    // one thread per occlusion ray, blocks of at least 32 threads
+    if (n * spp > (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull)
+        return fail(VSR_ERR_ARG, "too many occlusion rays for one launch");
     if (n) return check_dev(xi, s->device, "xi", 8, n * spp * 8);
     return VSR_OK;
 }
@@ -718,7 +724,8 @@ vsr_status prepare_ao(vsr_scene* s, uint64_t n, uint32_t spp, const float* xi, f
 extern "C" vsr_status vsr_render_ao(vsr_scene* s, const vsr_ray* rays, uint64_t n,
                                     const vsr_intersector* is, uint32_t spp, const float* xi,
                                     float ao_tmax, float eps, const vsr_shade_params* sh,
-                                    float* image, float* occlusion, vsr_stream stream) {
+                                    float* image, vsr_hit* hits, float* occlusion,
+                                    vsr_stream stream) {
     g_err.clear();
     LaunchArgs a;
     ShadeDev shd;
@@ -727,40 +734,49 @@ extern "C" vsr_status vsr_render_ao(vsr_scene* s, const vsr_ray* rays, uint64_t 
     if (st != VSR_OK) return st;
     if (n == 0) return VSR_OK;
     st = check_dev(image, s->device, "image", 4, n * 12);
-    if (st == VSR_OK && occlusion) st = check_dev(occlusion, s->device, "occlusion", 4, n * 4);
+    if (st == VSR_OK) st = check_dev(hits, s->device, "hits", 16, n * sizeof(vsr_hit));
+    if (st == VSR_OK) st = check_dev(occlusion, s->device, "occlusion", 4, n * 4);
     if (st != VSR_OK) return st;
     AoArgs ao{shd, s->d_verts, s->d_idx, spp, reinterpret_cast<const float2*>(xi), ao_tmax, eps,
-              image, occlusion, nullptr, nullptr};
+              reinterpret_cast<float4*>(hits), occlusion, image, nullptr, nullptr};
     a.stream = reinterpret_cast<cudaStream_t>(stream);
+    a.hits = ao.hits;
     DeviceGuard g(s->device);
-    cudaError_t e = launch_render_ao(a, is->kind, ao, false);
-    if (e != cudaSuccess) return cuda_fail(e, "ao render launch");
+    cudaError_t e = launch_static(a, is->kind, false);
+    if (e != cudaSuccess) return cuda_fail(e, "ao primary trace launch");
+    VSR_CUDA(cudaMemsetAsync(occlusion, 0, n * 4, a.stream), "occlusion counts");
+    e = launch_ao_occlusion(a, is->kind, ao);
+    if (e != cudaSuccess) return cuda_fail(e, "ao occlusion launch");
+    e = launch_ao_shade(a.sc, ao, n, a.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ao shade launch");
     return VSR_OK;
 }
 
-extern "C" vsr_status vsr_render_ao_backward(vsr_scene* s, const vsr_ray* rays, uint64_t n,
-                                             const vsr_intersector* is, uint32_t spp,
-                                             const float* xi, float ao_tmax, float eps,
+extern "C" vsr_status vsr_render_ao_backward(vsr_scene* s, const vsr_hit* hits,
+                                             const float* occlusion, uint64_t n,
                                              const vsr_shade_params* sh, const float* dL_dimage,
                                              float* grad_texels, vsr_stream stream) {
     g_err.clear();
-    LaunchArgs a;
+    if (!s) return fail(VSR_ERR_ARG, "scene is null");
     ShadeDev shd;
-    vsr_status st = prepare_render(s, rays, n, is, sh, nullptr, a, shd);
-    if (st == VSR_OK) st = prepare_ao(s, n, spp, xi, ao_tmax, eps);
+    vsr_status st = prepare_shade(s, sh, shd);
     if (st != VSR_OK) return st;
     if (shd.grad_tex == VSR_NO_TEXTURE || s->h_tex[shd.grad_tex].fmt != VSR_TEX_RGBA32F)
         return fail(VSR_ERR_ARG, "texel gradients need an RGBA32F grad_tex");
+    if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 256ull)
+        return fail(VSR_ERR_ARG, "too many pixels for one launch");
     if (n == 0) return VSR_OK;
     const TexDesc& t = s->h_tex[shd.grad_tex];
-    st = check_dev(dL_dimage, s->device, "dL_dimage", 4, n * 12);
+    st = check_dev(hits, s->device, "hits", 16, n * sizeof(vsr_hit));
+    if (st == VSR_OK) st = check_dev(occlusion, s->device, "occlusion", 4, n * 4);
+    if (st == VSR_OK) st = check_dev(dL_dimage, s->device, "dL_dimage", 4, n * 12);
     if (st == VSR_OK) st = check_dev(grad_texels, s->device, "grad_texels", 4, 16ull * t.w * t.h);
     if (st != VSR_OK) return st;
-    AoArgs ao{shd, s->d_verts, s->d_idx, spp, reinterpret_cast<const float2*>(xi), ao_tmax, eps,
-              nullptr, nullptr, dL_dimage, grad_texels};
-    a.stream = reinterpret_cast<cudaStream_t>(stream);
+    AoArgs ao{shd, nullptr, nullptr, 0, nullptr, 0.0f, 0.0f,
+              reinterpret_cast<float4*>(const_cast<vsr_hit*>(hits)),
+              const_cast<float*>(occlusion), nullptr, dL_dimage, grad_texels};
     DeviceGuard g(s->device);
-    cudaError_t e = launch_render_ao(a, is->kind, ao, true);
+    cudaError_t e = launch_ao_backward(s->dev, ao, n, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "ao backward launch");
     return VSR_OK;
 }

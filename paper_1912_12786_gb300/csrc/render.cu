@@ -247,96 +247,99 @@ __global__ void __launch_bounds__(256) k_render_backward(
     }
 }
 
-// Ambient-occlusion shading: c = albedo_rgb(uv) * (1 - occluded / spp) for a
-// primary hit (background for a miss), where each of the spp occlusion rays
-// is built exactly as vsr_make_ao_rays builds it and traced any-hit with the
-// same intersector.  `occ` (optional) receives the occluded fraction.
-template <class H>
-__device__ __forceinline__ float ao_visibility(const DevScene& sc, const IsectParams& ip,
-                                               const float* __restrict__ verts,
-                                               const uint32_t* __restrict__ idx,
-                                               const float4 ra, const float4 rb, const Best& best,
-                                               uint32_t spp, const float2* __restrict__ xi,
-                                               unsigned long long i, float ao_tmax, float eps,
-                                               uint32_t* stack, uint32_t stride) {
-    const AoFrame f = ao_frame(verts, idx, best.prim, rb.x, rb.y, rb.z);
-    const float4 o = make_float4(__fmaf_rn(best.t, rb.x, ra.x), __fmaf_rn(best.t, rb.y, ra.y),
-                                 __fmaf_rn(best.t, rb.z, ra.z), eps);
-    uint32_t occluded = 0;
-    for (uint32_t k = 0; k < spp; ++k) {
-        const Ray ar = make_ray(o, ao_direction(f, VSR_LDG(xi + i * spp + k), ao_tmax));
-        H h;
-        Best b;
-        Stats st;
-        traverse<kAny, H, false>(sc, ip, ar, h, b, st, stack, stride);
-        occluded += b.prim != kMiss ? 1u : 0u;
-    }
-    return 1.0f - (float)occluded / (float)spp;
-}
+// Ambient-occlusion render: c = albedo_rgb(uv) * (1 - occluded / spp) for a
+// primary hit, background for a miss.  Three passes over the saved primary
+// hits: the closest-hit trace (the trace kernels), the occlusion count (one
+// thread per occlusion ray) and the shading.
 
+// Occlusion ray j = i * spp + k of pixel i, built from the pixel's closest
+// hit exactly as vsr_make_ao_rays builds it and traced any-hit with the same
+// intersector; an occluded ray adds 1 to cnt[i].  The counts are integers,
+// so the totals do not depend on the order of the atomics.
 template <class H>
-__global__ void __launch_bounds__(256) k_render_ao(DevScene sc, IsectParams ip, ShadeDev sh,
-                                                   const float* __restrict__ verts,
-                                                   const uint32_t* __restrict__ idx,
-                                                   const float4* __restrict__ rays,
-                                                   unsigned long long n, uint32_t spp,
-                                                   const float2* __restrict__ xi, float ao_tmax,
-                                                   float eps, float* __restrict__ image,
-                                                   float* __restrict__ occ) {
+__global__ void __launch_bounds__(256) k_ao_occlusion(DevScene sc, IsectParams ip,
+                                                      const float* __restrict__ verts,
+                                                      const uint32_t* __restrict__ idx,
+                                                      const float4* __restrict__ rays,
+                                                      const float4* __restrict__ hits,
+                                                      unsigned long long n, uint32_t spp,
+                                                      const float2* __restrict__ xi,
+                                                      float ao_tmax, float eps,
+                                                      uint32_t* __restrict__ cnt) {
     extern __shared__ uint32_t s_stack[];
-    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float4 ra = VSR_LDG(rays + 2 * i), rb = VSR_LDG(rays + 2 * i + 1);
-    H h;
+    const unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n * spp) return;
+    const unsigned long long i = j / spp;
+    const float4 h = VSR_LDG(hits + i);
+    const uint32_t prim = __float_as_uint(h.w);
+    if (prim == kMiss) return;
+    const float4 rb = VSR_LDG(rays + 2 * i + 1);
+    const float4 ra = VSR_LDG(rays + 2 * i);
+    const AoFrame f = ao_frame(verts, idx, prim, rb.x, rb.y, rb.z);
+    const float4 o = make_float4(__fmaf_rn(h.x, rb.x, ra.x), __fmaf_rn(h.x, rb.y, ra.y),
+                                 __fmaf_rn(h.x, rb.z, ra.z), eps);
+    const Ray ar = make_ray(o, ao_direction(f, VSR_LDG(xi + j), ao_tmax));
+    H hk;
     Best best;
     Stats st;
-    traverse<kClosest, H, false>(sc, ip, make_ray(ra, rb), h, best, st, s_stack + threadIdx.x,
-                                 blockDim.x);
+    traverse<kAny, H, false>(sc, ip, ar, hk, best, st, s_stack + threadIdx.x, blockDim.x);
+    if (best.prim != kMiss) atomicAdd(cnt + i, 1u);
+}
+
+// Shading of the saved hits; occ enters as the integer counts of
+// k_ao_occlusion and leaves as the occluded fraction (0 for a miss).
+__global__ void __launch_bounds__(256) k_ao_shade(DevScene sc, ShadeDev sh,
+                                                  const float4* __restrict__ hits,
+                                                  unsigned long long n, uint32_t spp,
+                                                  float* __restrict__ occ,
+                                                  float* __restrict__ image) {
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 h = VSR_LDG(hits + i);
+    const uint32_t prim = __float_as_uint(h.w);
     float c[3] = {sh.bg[0], sh.bg[1], sh.bg[2]};
     float o = 0.0f;
-    if (best.prim != kMiss) {
-        const float vis = ao_visibility<H>(sc, ip, verts, idx, ra, rb, best, spp, xi, i, ao_tmax,
-                                           eps, s_stack + threadIdx.x, blockDim.x);
-        o = 1.0f - vis;
+    if (prim != kMiss) {
+        o = (float)reinterpret_cast<const uint32_t*>(occ)[i] / (float)spp;
+        const float vis = 1.0f - o;
         Bilinear b;
-        albedo(sc, VSR_LDG(sc.geom + best.prim), lerp_uv(sc.uvs, best.prim, best.u, best.v), b);
+        albedo(sc, VSR_LDG(sc.geom + prim), lerp_uv(sc.uvs, prim, h.y, h.z), b);
         for (int ch = 0; ch < 3; ++ch) c[ch] = b.rgb[ch] * vis;
     }
     image[3 * i] = c[0];
     image[3 * i + 1] = c[1];
     image[3 * i + 2] = c[2];
-    if (occ) occ[i] = o;
+    occ[i] = o;
 }
 
 // Adjoint with respect to the colour texels of texture sh.grad_tex at fixed
-// visibility: dc/dT(corner) = (1 - occluded/spp) * w(corner); the primary hit
-// and the occlusion rays are traced again.
-template <class H>
-__global__ void __launch_bounds__(256) k_render_ao_backward(
-    DevScene sc, IsectParams ip, ShadeDev sh, const float* __restrict__ verts,
-    const uint32_t* __restrict__ idx, const float4* __restrict__ rays, unsigned long long n,
-    uint32_t spp, const float2* __restrict__ xi, float ao_tmax, float eps,
-    const float* __restrict__ dL_dimage, float* __restrict__ grad_texels) {
-    extern __shared__ uint32_t s_stack[];
+// visibility, from the forward's saved hits and occluded fractions (no
+// traversal): dc/dT(corner) = (1 - occ) * w(corner).  A hit record whose
+// primitive is out of range is skipped and flagged (kErrHit).
+__global__ void __launch_bounds__(256) k_ao_backward(DevScene sc, ShadeDev sh,
+                                                     const float4* __restrict__ hits,
+                                                     const float* __restrict__ occ,
+                                                     unsigned long long n,
+                                                     const float* __restrict__ dL_dimage,
+                                                     float* __restrict__ grad_texels) {
     const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float g[3] = {VSR_LDG(dL_dimage + 3 * i), VSR_LDG(dL_dimage + 3 * i + 1),
                         VSR_LDG(dL_dimage + 3 * i + 2)};
     if (g[0] == 0.0f && g[1] == 0.0f && g[2] == 0.0f) return;
-    const float4 ra = VSR_LDG(rays + 2 * i), rb = VSR_LDG(rays + 2 * i + 1);
-    H h;
-    Best best;
-    Stats st;
-    traverse<kClosest, H, false>(sc, ip, make_ray(ra, rb), h, best, st, s_stack + threadIdx.x,
-                                 blockDim.x);
-    if (best.prim == kMiss) return;
-    const uint32_t geom = VSR_LDG(sc.geom + best.prim);
+    const float4 h = VSR_LDG(hits + i);
+    const uint32_t prim = __float_as_uint(h.w);
+    if (prim == kMiss) return;
+    if (prim >= sc.nprims) {
+        atomicOr(sc.err, kErrHit);
+        return;
+    }
+    const uint32_t geom = VSR_LDG(sc.geom + prim);
     if (geom != sh.grad_tex) return;
     Bilinear b;
-    albedo(sc, geom, lerp_uv(sc.uvs, best.prim, best.u, best.v), b);
+    albedo(sc, geom, lerp_uv(sc.uvs, prim, h.y, h.z), b);
     if (!b.rgba32f) return;
-    const float vis = ao_visibility<H>(sc, ip, verts, idx, ra, rb, best, spp, xi, i, ao_tmax, eps,
-                                       s_stack + threadIdx.x, blockDim.x);
+    const float vis = 1.0f - VSR_LDG(occ + i);
     if (vis == 0.0f) return;
     const float w[4] = {(1.0f - b.fx) * (1.0f - b.fy), b.fx * (1.0f - b.fy),
                         (1.0f - b.fx) * b.fy, b.fx * b.fy};
@@ -473,38 +476,43 @@ cudaError_t launch_refit(float4* nodes, const uint32_t* level_nodes,
 namespace {
 
 template <class H>
-cudaError_t render_ao_one(const LaunchArgs& a, const AoArgs& ao, bool backward) {
+cudaError_t occlusion_one(const LaunchArgs& a, const AoArgs& ao) {
     const size_t smem = (size_t)a.sc.stack_depth * a.block * sizeof(uint32_t);
-    const unsigned long long grid = (a.n + a.block - 1) / a.block;
-    if (!backward) {
-        auto k = k_render_ao<H>;
-        cudaError_t e = prep_smem(k, smem);
-        if (e != cudaSuccess) return e;
-        k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, ao.sh, ao.verts, ao.idx, a.rays,
-                                                         a.n, ao.spp, ao.xi, ao.tmax, ao.eps,
-                                                         ao.image, ao.occ);
-    } else {
-        auto k = k_render_ao_backward<H>;
-        cudaError_t e = prep_smem(k, smem);
-        if (e != cudaSuccess) return e;
-        k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, ao.sh, ao.verts, ao.idx, a.rays,
-                                                         a.n, ao.spp, ao.xi, ao.tmax, ao.eps, ao.g,
-                                                         ao.grad_texels);
-    }
+    const unsigned long long m = a.n * ao.spp;
+    auto k = k_ao_occlusion<H>;
+    cudaError_t e = prep_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)((m + a.block - 1) / a.block), a.block, smem, a.stream>>>(
+        a.sc, a.ip, ao.verts, ao.idx, a.rays, ao.hits, a.n, ao.spp, ao.xi, ao.tmax, ao.eps,
+        reinterpret_cast<uint32_t*>(ao.occ));
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_render_ao(const LaunchArgs& a, int kind, const AoArgs& ao, bool backward) {
+cudaError_t launch_ao_occlusion(const LaunchArgs& a, int kind, const AoArgs& ao) {
     switch (kind) {
-        case 0: return render_ao_one<IsectNone>(a, ao, backward);
-        case 1: return render_ao_one<IsectDefault>(a, ao, backward);
-        case 2: return render_ao_one<IsectAlphaTex>(a, ao, backward);
-        case 3: return render_ao_one<IsectProcAlpha>(a, ao, backward);
-        case 4: return render_ao_one<IsectCount>(a, ao, backward);
+        case 0: return occlusion_one<IsectNone>(a, ao);
+        case 1: return occlusion_one<IsectDefault>(a, ao);
+        case 2: return occlusion_one<IsectAlphaTex>(a, ao);
+        case 3: return occlusion_one<IsectProcAlpha>(a, ao);
+        case 4: return occlusion_one<IsectCount>(a, ao);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_ao_shade(const DevScene& sc, const AoArgs& ao, unsigned long long n,
+                            cudaStream_t stream) {
+    k_ao_shade<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(sc, ao.sh, ao.hits, n, ao.spp,
+                                                                ao.occ, ao.image);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ao_backward(const DevScene& sc, const AoArgs& ao, unsigned long long n,
+                               cudaStream_t stream) {
+    k_ao_backward<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(sc, ao.sh, ao.hits, ao.occ, n,
+                                                                   ao.g, ao.grad_texels);
+    return cudaGetLastError();
 }
 
 }  // namespace vsr

@@ -48,10 +48,11 @@ constexpr int kClosest = 0;
 constexpr int kAny = 1;
 
 enum : uint32_t { kTexU8 = 0, kTexRGBA8 = 1, kTexRGBA32F = 2 };
-// Device error word bits.  Neither can happen for a validated blob; the
-// checks turn a corrupted structure into an error instead of a fault or an
-// endless loop.
-enum : uint32_t { kErrStack = 1u, kErrSteps = 2u, kErrAlign = 4u };
+// Device error word bits: stack overflow and step limit (neither can happen
+// for a validated blob), a misaligned load skipped, a caller-supplied hit
+// record out of range.  The checks turn a corrupted structure or input into
+// an error instead of a fault or an endless loop.
+enum : uint32_t { kErrStack = 1u, kErrSteps = 2u, kErrAlign = 4u, kErrHit = 8u };
 
 struct TexDesc {
     uint32_t fmt, w, h, pad;

@@ -81,12 +81,20 @@ struct AoArgs {
     uint32_t spp;
     const float2* xi;
     float tmax, eps;
+    float4* hits;        // primary closest hits (written by the trace, read after)
+    float* occ;          // occlusion counts (zeroed uint32), then occluded fractions
     float* image;        // forward
-    float* occ;          // forward, optional
     const float* g;      // backward
     float* grad_texels;  // backward
 };
-cudaError_t launch_render_ao(const LaunchArgs& a, int kind, const AoArgs& ao, bool backward);
+// Occlusion counts for a.n pixels (a.rays, ao.hits) into ao.occ as uint32.
+cudaError_t launch_ao_occlusion(const LaunchArgs& a, int kind, const AoArgs& ao);
+// Image and occluded fractions from the hits and counts.
+cudaError_t launch_ao_shade(const DevScene& sc, const AoArgs& ao, unsigned long long n,
+                            cudaStream_t stream);
+// Texel gradients from the saved hits and occluded fractions.
+cudaError_t launch_ao_backward(const DevScene& sc, const AoArgs& ao, unsigned long long n,
+                               cudaStream_t stream);
 
 // Bottom-up refit over node lists grouped by level, deepest first
 // (level_offsets is a host array of levels + 1 entries).

@@ -85,9 +85,8 @@ _SIGS = {
     "vsr_render": ([P, P, ctypes.c_uint64, P, P, P, P, P, P], ctypes.c_int),
     "vsr_trace_backward": ([P, P, ctypes.c_uint64, P, P, P, P, P, P, P], ctypes.c_int),
     "vsr_render_ao": ([P, P, ctypes.c_uint64, P, ctypes.c_uint32, P, ctypes.c_float,
-                       ctypes.c_float, P, P, P, P], ctypes.c_int),
-    "vsr_render_ao_backward": ([P, P, ctypes.c_uint64, P, ctypes.c_uint32, P, ctypes.c_float,
-                                ctypes.c_float, P, P, P, P], ctypes.c_int),
+                       ctypes.c_float, P, P, P, P, P], ctypes.c_int),
+    "vsr_render_ao_backward": ([P, P, P, ctypes.c_uint64, P, P, P, P], ctypes.c_int),
     "vsr_scene_update": ([P, P, ctypes.c_uint32, P, P], ctypes.c_int),
     "vsr_make_ao_rays": ([P, P, P, ctypes.c_uint64, ctypes.c_uint32, P, ctypes.c_float,
                           ctypes.c_float, P, P], ctypes.c_int),
@@ -339,21 +338,21 @@ def vsr_trace_backward(scene: Scene, rays, isect: vsr_intersector, shade: vsr_sh
 
 
 def vsr_render_ao(scene: Scene, rays, isect: vsr_intersector, spp: int, xi, ao_tmax: float,
-                  eps: float, shade: vsr_shade_params, image, occlusion=None, stream=None):
-    """albedo(uv) * (1 - occluded fraction of spp AO rays) into image [n,3]."""
+                  eps: float, shade: vsr_shade_params, image, hits, occlusion, stream=None):
+    """albedo(uv) * (1 - occluded fraction of spp AO rays) into image [n,3];
+    the primary hits [n,4] and occluded fractions [n] are written too."""
     _check(lib().vsr_render_ao(scene.handle, _ptr(rays), int(rays.shape[0]), ctypes.byref(isect),
                                spp, _ptr(xi), float(ao_tmax), float(eps), ctypes.byref(shade),
-                               _ptr(image), _ptr(occlusion), _stream(stream)))
+                               _ptr(image), _ptr(hits), _ptr(occlusion), _stream(stream)))
 
 
-def vsr_render_ao_backward(scene: Scene, rays, isect: vsr_intersector, spp: int, xi,
-                           ao_tmax: float, eps: float, shade: vsr_shade_params, dL_dimage,
+def vsr_render_ao_backward(scene: Scene, hits, occlusion, shade: vsr_shade_params, dL_dimage,
                            grad_texels, stream=None):
-    """Accumulate dL/dtexels of shade.grad_tex for vsr_render_ao (fixed visibility)."""
-    _check(lib().vsr_render_ao_backward(scene.handle, _ptr(rays), int(rays.shape[0]),
-                                        ctypes.byref(isect), spp, _ptr(xi), float(ao_tmax),
-                                        float(eps), ctypes.byref(shade), _ptr(dL_dimage),
-                                        _ptr(grad_texels), _stream(stream)))
+    """Accumulate dL/dtexels of shade.grad_tex for vsr_render_ao from its saved
+    hits and occlusion (fixed visibility)."""
+    _check(lib().vsr_render_ao_backward(scene.handle, _ptr(hits), _ptr(occlusion),
+                                        int(hits.shape[0]), ctypes.byref(shade),
+                                        _ptr(dL_dimage), _ptr(grad_texels), _stream(stream)))
 
 
 def vsr_scene_update(scene: Scene, verts=None, tex_index=0, texels=None, stream=None):

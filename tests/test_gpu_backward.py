@@ -149,3 +149,75 @@ def test_autograd_function_and_scene_update(sphere):
     assert np.array_equal(gh[~ties, 3], O.hits_raw(ref).view(np.uint32)[~ties, 3])
     V.vsr_scene_update(d["s"], torch.from_numpy(sc.verts).cuda())
     assert V.vsr_get_device_error(d["s"]) == 0
+
+
+def test_ao_render_autograd_and_bad_hit_records(sphere):
+    """Ambient-occlusion render on the icosphere (4 occlusion rays per pixel,
+    tmax 0.5): hits bit-exact with the oracle, occlusion equal to the oracle's
+    on all but a few pixels, texel gradients of AORenderFunction equal to the
+    direct backward call and within 1e-3 of the FP64 reference on the pixels
+    whose occlusion agrees.  A hit record naming a primitive out of range is
+    skipped by the backward and by vsr_make_ao_rays, and sets error bit 3."""
+    from paper_1912_12786_gb300.autograd import render_ao
+    d = sphere
+    V, sc, s = d["V"], d["sc"], d["s"]
+    spp, tmax, eps = 4, 0.5, scenes.shadow_eps(sc)
+    n = len(d["rays"])
+    xi_h = scenes.ao_random(n, spp)
+    rays, xi = torch.from_numpy(d["rays"]).cuda(), torch.from_numpy(xi_h).cuda()
+    isect = V.intersector("alpha_tex", cutoff_f=0.3)
+    shade = V.shade_params((0.0, 0.0, 1.0), grad_tex=0)
+    tex0 = sc.textures[0].texels
+    img = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    hits = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    occ = torch.empty(n, dtype=torch.float32, device="cuda")
+    V.vsr_render_ao(s, rays, isect, spp, xi, tmax, eps, shade, img, hits, occ)
+    torch.cuda.synchronize()
+    ref, st = d["ref_hits"], d["st"]
+    gh = hits.cpu().numpy().view(np.uint32)
+    ties = st[:, 3] != 0
+    assert np.array_equal(gh[~ties], O.hits_raw(ref).view(np.uint32)[~ties])
+    ao = O.ao_rays(sc, d["rays"], O.hits_raw(ref), spp, xi_h, tmax, eps)
+    aoh, _ = O.trace_bvh(sc, d["blob"], ao, "alpha_tex", "any", cutoff_f=0.3)
+    occ_ref = (aoh["prim"] != O.NONE).reshape(-1, spp).mean(1)
+    same = (gh[:, 3] == ref["prim"]) & (np.abs(occ.cpu().numpy() - occ_ref) < 1e-6)
+    assert (~same).sum() <= 1e-3 * n and 0.05 < occ_ref[ref["prim"] != O.NONE].mean() < 0.95
+    fa = A.FrozenAO(sc, d["rays"], ref["prim"], 1.0 - occ_ref,
+                    bary=np.stack([ref["u"], ref["v"]], 1))
+    ref_img = fa.image(A._t(sc.verts), A._t(tex0)).numpy()
+    assert np.abs(img.cpu().numpy()[same] - ref_img[same]).max() < 2e-5
+    # upstream gradient from the oracle's image, zero where occlusion differs
+    g_ref = np.where(same[:, None], 2.0 * (ref_img - 0.5), 0.0)
+    g = torch.from_numpy(g_ref.astype(np.float32)).cuda()
+    # autograd against the direct calls (same hits and occlusion, same kernels)
+    tex = torch.from_numpy(tex0.copy()).cuda().requires_grad_(True)
+    img2 = render_ao(s, rays, tex, isect, spp, xi, tmax, eps, shade)
+    assert torch.equal(img2, img)
+    img2.backward(g)
+    gt = torch.zeros_like(tex)
+    V.vsr_render_ao_backward(s, hits, occ, shade, g, gt)
+    torch.cuda.synchronize()
+    gt = gt.cpu().numpy()
+    assert np.allclose(tex.grad.cpu().numpy(), gt, rtol=1e-4, atol=1e-6 * np.abs(gt).max())
+    # FP64 reference at the oracle's barycentrics and occlusion
+    _, gt_ref = fa.vjp(sc.verts, tex0, g_ref)
+    assert _rel(gt, gt_ref) < 1e-3
+    assert np.all(gt[..., 3] == 0)
+    assert V.vsr_get_device_error(s) == 0, V.vsr_last_error()
+    # hit records out of range: skipped and flagged, never dereferenced
+    k = int(np.flatnonzero(gh[:, 3] != O.NONE)[0])
+    bad = hits.clone()
+    bad[k, 3] = torch.tensor([sc.ntri + 5], dtype=torch.int32).view(torch.float32)[0]
+    gt2 = torch.zeros_like(tex)
+    gk = torch.zeros_like(g)
+    gk[k] = 1.0
+    V.vsr_render_ao_backward(s, bad, occ, shade, gk, gt2)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(gt2) == 0
+    assert V.vsr_get_device_error(s) & 8
+    out = torch.empty((n * spp, 8), dtype=torch.float32, device="cuda")
+    V.vsr_make_ao_rays(s, rays, bad, spp, xi, tmax, eps, out)
+    torch.cuda.synchronize()
+    assert torch.all(out[k * spp:(k + 1) * spp, 7] < 0)
+    assert V.vsr_get_device_error(s) & 8
+    assert V.vsr_get_device_error(s) == 0

@@ -122,11 +122,11 @@ def test_ao_render_and_texel_gradients(large):
     d_rays = torch.from_numpy(rays).cuda()
     d_xi = torch.from_numpy(xi).cuda()
     hits = torch.empty((len(rays), 4), dtype=torch.float32, device="cuda")
-    V.vsr_trace(s, d_rays, proc, "closest", hits)
     img = torch.empty((len(rays), 3), dtype=torch.float32, device="cuda")
     gocc = torch.empty(len(rays), dtype=torch.float32, device="cuda")
-    V.vsr_render_ao(s, d_rays, proc, SPP, d_xi, TMAX, eps, shade, img, gocc)
+    V.vsr_render_ao(s, d_rays, proc, SPP, d_xi, TMAX, eps, shade, img, hits, gocc)
     torch.cuda.synchronize()
+    _cmp(hits.cpu().numpy(), ref, st, "ao render primary")
     gprim = hits.cpu().numpy()[:, 3].view(np.uint32)
     same = (gprim == ref["prim"]) & (np.abs(gocc.cpu().numpy() - occ) < 1e-6)
     assert (~same).sum() <= 1e-3 * len(rays), int((~same).sum())
@@ -146,8 +146,8 @@ def test_ao_render_and_texel_gradients(large):
     g[~same] = 0.0
     _, gt_ref = fa.vjp(sc.verts, tex, g)
     gt = torch.zeros(tex.shape, dtype=torch.float32, device="cuda")
-    V.vsr_render_ao_backward(s, d_rays, proc, SPP, d_xi, TMAX, eps, shade,
-                             torch.from_numpy(g.astype(np.float32)).cuda(), gt)
+    V.vsr_render_ao_backward(s, hits, gocc, shade, torch.from_numpy(g.astype(np.float32)).cuda(),
+                             gt)
     torch.cuda.synchronize()
     gt = gt.cpu().numpy()
     rel = np.linalg.norm(gt - gt_ref) / np.linalg.norm(gt_ref)
