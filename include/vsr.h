@@ -131,13 +131,22 @@ typedef enum vsr_query {
 
 /* Launch configuration; pass NULL for the tuned defaults. */
 typedef struct vsr_trace_params {
-    uint32_t block_size;       /* threads per block, multiple of 32, 32..512 */
+    uint32_t block_size;       /* threads per block, multiple of 32, 32..256 */
     uint32_t persistent;       /* 0: one ray per thread; 1: persistent warps
                                   (static dispatch; not for the procedural-
                                   alpha any-hit query, which is refused) */
     uint32_t refill_threshold; /* persistent: refill idle lanes when fewer
                                   than this many of 32 are still active */
     uint32_t blocks_per_sm;    /* persistent: resident blocks per SM (0=auto) */
+    uint32_t image_width;      /* 0: threads take rays in buffer order.  w > 0:
+                                  the rays are a row-major image w pixels wide
+                                  (the last row may be partial; widths above
+                                  n act as n) and each warp
+                                  takes a 4 x 8 pixel tile, so its rays are
+                                  neighbours in both directions; rays and hits
+                                  keep their layout.  Results are identical;
+                                  coherent (camera) rays trace faster.  Not for
+                                  batched launches. */
 } vsr_trace_params;
 
 typedef struct vsr_scene vsr_scene;
@@ -418,15 +427,16 @@ const char* vsr_last_error(void);
 
 /* Read and clear the scene's device error word (synchronous).
  *   bit 0: a traversal stack overflowed;
- *   bit 1: a ray visited more nodes than the BVH holds;
+ *   bit 1: a ray visited more leaves than the BVH has nodes;
  *   bit 2: a render or backward kernel found a load whose address did not
  *          match its width and skipped it (vsr_last_error() names the line);
  *   bit 3: a caller-supplied hit record named a primitive out of range
  *          (skipped; vsr_make_ao_rays gives its rays inactive).
  * Bits 0 and 1 end that ray as a miss; neither can happen with a validated
- * blob (each node is visited at most once per ray).  All four checks exist
- * so that a corrupted structure or a bad address gives an error instead of
- * a fault or an endless loop. */
+ * blob (each node is visited at most once per ray, and descent strictly
+ * increases the node index).  All four checks exist so that a corrupted
+ * structure or a bad address gives an error instead of a fault or an
+ * endless loop. */
 vsr_status vsr_get_device_error(vsr_scene* scene, uint32_t* word);
 
 /* Library version, e.g. 100 for 0.1.0. */

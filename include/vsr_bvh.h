@@ -31,8 +31,9 @@
  *
  * Node semantics: node 0 is the root.  count = count_axis >> 2,
  * axis = count_axis & 3.  count == 0: inner node whose children are the two
- * adjacent nodes left_or_first (even, >= 2) and left_or_first + 1, split along
- * `axis` (0, 1, 2).  count > 0: leaf holding prim_order[left_or_first ..
+ * adjacent nodes left_or_first (even, >= 2, and above the node's own index:
+ * children follow their parent) and left_or_first + 1, split along `axis`
+ * (0, 1, 2).  count > 0: leaf holding prim_order[left_or_first ..
  * left_or_first + count).  Every triangle appears in exactly one leaf.  A blob
  * with num_prims == 0 has num_nodes == 2, an all-zero root and is traced as
  * "every ray misses".

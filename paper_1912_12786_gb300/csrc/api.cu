@@ -260,6 +260,24 @@ vsr_status validate_isect(const vsr_intersector* is, int32_t query) {
     return VSR_OK;
 }
 
+// Thread -> ray map for n rays laid out as a row-major image `width` pixels
+// wide (0: buffer order).  The padded thread count is at most 8n; layouts
+// whose count would not fit one launch are refused.
+vsr_status make_map(uint64_t n, uint32_t width, RayMap& m) {
+    constexpr uint64_t kMaxThreads = (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull;
+    m = RayMap{n, n, 0u, 0u};
+    if (width == 0 || n == 0) return VSR_OK;
+    if (width > n) width = (uint32_t)n;  // one partial row: the same rays
+    const uint64_t rows = (n + width - 1) / width;
+    const uint64_t tiles_x = (width + 3ull) / 4ull, tiles_y = (rows + 7ull) / 8ull;
+    if (tiles_y > kMaxThreads / 32ull / tiles_x)
+        return fail(VSR_ERR_ARG, "image_width gives too many threads for one launch");
+    m.threads = tiles_x * tiles_y * 32ull;
+    m.width = width;
+    m.tiles_x = (uint32_t)tiles_x;
+    return VSR_OK;
+}
+
 vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
                           const vsr_intersector* is, int32_t query, vsr_hit* hits,
                           const vsr_trace_params* p, LaunchArgs& a) {
@@ -267,7 +285,7 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (!s->has_bvh) return fail(VSR_ERR_STATE, "no BVH loaded into the scene");
     vsr_status st = validate_isect(is, query);
     if (st != VSR_OK) return st;
-    vsr_trace_params prm{128u, 0u, 16u, 0u};
+    vsr_trace_params prm{128u, 0u, 16u, 0u, 0u};
     if (p) prm = *p;
     if (prm.block_size < 32 || prm.block_size > 256 || prm.block_size % 32)
         return fail(VSR_ERR_ARG, "block_size must be a multiple of 32 in 32..256");
@@ -291,6 +309,8 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
         if (st != VSR_OK) return st;
     }
     a = LaunchArgs{};
+    st = make_map(n, prm.image_width, a.map);
+    if (st != VSR_OK) return st;
     a.sc = s->dev;
     a.ip.cutoff_u8 = is->alpha_cutoff_u8;
     a.ip.cutoff_f = is->alpha_cutoff_f;
@@ -649,6 +669,8 @@ vsr_status prepare_render(vsr_scene* s, const vsr_ray* rays, uint64_t n,
         if (st != VSR_OK) return st;
     }
     a.n = n;
+    st = make_map(n, p ? p->image_width : 0u, a.map);
+    if (st != VSR_OK) return st;
     a.rays = reinterpret_cast<const float4*>(rays);
     return prepare_shade(s, sh, shd);
 }
@@ -994,6 +1016,8 @@ vsr_status validate_params(const vsr_trace_params& p) {
     if (p.refill_threshold < 1 || p.refill_threshold > 32)
         return fail(VSR_ERR_ARG, "refill_threshold must be in 1..32");
     if (p.blocks_per_sm > 32) return fail(VSR_ERR_ARG, "blocks_per_sm above 32");
+    if (p.image_width != 0)
+        return fail(VSR_ERR_ARG, "batched launches take rays in buffer order (image_width 0)");
     return VSR_OK;
 }
 

@@ -125,11 +125,13 @@ __global__ void __launch_bounds__(256) k_render(DevScene sc, IsectParams ip, Sha
                                                 const float* __restrict__ verts,
                                                 const uint32_t* __restrict__ idx,
                                                 const float4* __restrict__ rays,
-                                                unsigned long long n, float* __restrict__ image,
+                                                RayMap map, float* __restrict__ image,
                                                 float4* __restrict__ hits) {
     extern __shared__ uint32_t s_stack[];
-    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= map.threads) return;
+    const unsigned long long i = ray_of_thread(g, map);
+    if (i >= map.n) return;
     const float4 ra = VSR_LDG(rays + 2 * i), rb = VSR_LDG(rays + 2 * i + 1);
     const Ray r = make_ray(ra, rb);
     H h;
@@ -168,12 +170,14 @@ __global__ void __launch_bounds__(256) k_render(DevScene sc, IsectParams ip, Sha
 template <class H>
 __global__ void __launch_bounds__(256) k_render_backward(
     DevScene sc, IsectParams ip, ShadeDev sh, const float* __restrict__ verts,
-    const uint32_t* __restrict__ idx, const float4* __restrict__ rays, unsigned long long n,
+    const uint32_t* __restrict__ idx, const float4* __restrict__ rays, RayMap map,
     const float* __restrict__ dL_dimage, float* __restrict__ grad_verts,
     float* __restrict__ grad_texels) {
     extern __shared__ uint32_t s_stack[];
-    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const unsigned long long gi = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= map.threads) return;
+    const unsigned long long i = ray_of_thread(gi, map);
+    if (i >= map.n) return;
     const float4 ra = VSR_LDG(rays + 2 * i), rb = VSR_LDG(rays + 2 * i + 1);
     const Ray r = make_ray(ra, rb);
     H h;
@@ -406,8 +410,8 @@ cudaError_t render_one(const LaunchArgs& a, const ShadeDev& sh, const float* ver
     auto k = k_render<H>;
     cudaError_t e = prep_smem(k, smem);
     if (e != cudaSuccess) return e;
-    const unsigned long long grid = (a.n + a.block - 1) / a.block;
-    k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, sh, verts, idx, a.rays, a.n, image,
+    const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
+    k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, sh, verts, idx, a.rays, a.map, image,
                                                      hits);
     return cudaGetLastError();
 }
@@ -419,8 +423,8 @@ cudaError_t backward_one(const LaunchArgs& a, const ShadeDev& sh, const float* v
     auto k = k_render_backward<H>;
     cudaError_t e = prep_smem(k, smem);
     if (e != cudaSuccess) return e;
-    const unsigned long long grid = (a.n + a.block - 1) / a.block;
-    k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, sh, verts, idx, a.rays, a.n, g, gv,
+    const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
+    k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, sh, verts, idx, a.rays, a.map, g, gv,
                                                      gt);
     return cudaGetLastError();
 }

@@ -77,12 +77,14 @@ template <int Q>
 __global__ void __launch_bounds__(256) k_trace_dyn(DevScene sc, IsectParams ip,
                                                    const DevScene* __restrict__ user,
                                                    const float4* __restrict__ rays,
-                                                   unsigned long long n,
+                                                   RayMap map,
                                                    float4* __restrict__ hits,
                                                    uint2* __restrict__ counters) {
     extern __shared__ uint32_t s_stack[];
-    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= map.threads) return;
+    const unsigned long long i = ray_of_thread(g, map);
+    if (i >= map.n) return;
     const Ray r = make_ray(__ldg(rays + 2 * i), __ldg(rays + 2 * i + 1));
     IsectDynamic h;
     const uint32_t kind = ip.kind < 5u ? ip.kind : 0u;
@@ -119,14 +121,14 @@ cudaError_t launch_dynamic(const LaunchArgs& a, int kind) {
         }
     }
     const size_t smem = (size_t)a.sc.stack_depth * a.block * sizeof(uint32_t);
-    const unsigned long long grid = (a.n + a.block - 1) / a.block;
+    const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
     auto k = (a.query == kClosest) ? k_trace_dyn<kClosest> : k_trace_dyn<kAny>;
     if (smem > 48 * 1024) {
         cudaError_t e =
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.dyn_user, a.rays, a.n, a.hits,
+    k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.dyn_user, a.rays, a.map, a.hits,
                                                      a.counters);
     return cudaGetLastError();
 }

@@ -16,12 +16,14 @@ namespace vsr {
 template <int Q, class H, bool STATS>
 __global__ void __launch_bounds__(256) k_trace(DevScene sc, IsectParams ip,
                                                const float4* __restrict__ rays,
-                                               unsigned long long n, float4* __restrict__ hits,
+                                               RayMap map, float4* __restrict__ hits,
                                                uint2* __restrict__ counters,
                                                uint4* __restrict__ stats) {
     extern __shared__ uint32_t s_stack[];
-    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= map.threads) return;
+    const unsigned long long i = ray_of_thread(g, map);
+    if (i >= map.n) return;
     const Ray r = make_ray(__ldg(rays + 2 * i), __ldg(rays + 2 * i + 1));
     H h;
     Best best;
@@ -34,13 +36,14 @@ __global__ void __launch_bounds__(256) k_trace(DevScene sc, IsectParams ip,
 
 // Persistent variant.  Per-lane traversal state lives in registers and the
 // shared-memory stack column; a lane that finishes its ray idles until the
-// warp refills.  Every wait is a plain loop over claimed work: no lane ever
+// warp refills.  The counter hands out thread slots of the ray map; a slot
+// past the image edge takes no ray.  Every wait is a plain loop over claimed work: no lane ever
 // waits on another warp or block.  Each outer iteration either advances some
 // lane's traversal (bounded per ray by the node count) or claims at least one
 // ray, so the kernel terminates.
 template <int Q, class H, bool STATS>
 __global__ void __launch_bounds__(256) k_trace_persistent(
-    DevScene sc, IsectParams ip, const float4* __restrict__ rays, unsigned long long n,
+    DevScene sc, IsectParams ip, const float4* __restrict__ rays, RayMap map,
     float4* __restrict__ hits, uint2* __restrict__ counters, uint4* __restrict__ stats,
     unsigned long long* __restrict__ work, uint32_t refill) {
     extern __shared__ uint32_t s_stack[];
@@ -74,10 +77,11 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(work, (unsigned long long)nidle);
             base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            if (base + nidle >= n) exhausted = true;
+            if (base + nidle >= map.threads) exhausted = true;
             if (!has) {
-                ri = base + (unsigned long long)__popc(idle & lt_mask);
-                if (ri < n) {
+                const unsigned long long slot = base + (unsigned long long)__popc(idle & lt_mask);
+                ri = slot < map.threads ? ray_of_thread(slot, map) : map.n;
+                if (ri < map.n) {
                     r = make_ray(VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
                     h = H();
                     st = Stats();
@@ -125,8 +129,8 @@ cudaError_t launch_one(const LaunchArgs& a) {
         auto k = k_trace<Q, H, STATS>;
         cudaError_t e = ensure_smem(k, smem);
         if (e != cudaSuccess) return e;
-        const unsigned long long grid = (a.n + a.block - 1) / a.block;
-        k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.n, a.hits,
+        const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
+        k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits,
                                                          a.counters, a.stats);
         return cudaGetLastError();
     }
@@ -137,7 +141,7 @@ cudaError_t launch_one(const LaunchArgs& a) {
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), a.stream);
     if (e != cudaSuccess) return e;
-    k<<<grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.n, a.hits, a.counters, a.stats,
+    k<<<grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits, a.counters, a.stats,
                                          a.work, a.refill);
     return cudaGetLastError();
 }

@@ -48,9 +48,9 @@ constexpr int kClosest = 0;
 constexpr int kAny = 1;
 
 enum : uint32_t { kTexU8 = 0, kTexRGBA8 = 1, kTexRGBA32F = 2 };
-// Device error word bits: stack overflow and step limit (neither can happen
-// for a validated blob), a misaligned load skipped, a caller-supplied hit
-// record out of range.  The checks turn a corrupted structure or input into
+// Device error word bits: stack overflow and more leaf visits than nodes
+// (neither can happen for a validated blob), a misaligned load skipped, a
+// caller-supplied hit record out of range.  The checks turn a corrupted structure or input into
 // an error instead of a fault or an endless loop.
 enum : uint32_t { kErrStack = 1u, kErrSteps = 2u, kErrAlign = 4u, kErrHit = 8u };
 
@@ -74,6 +74,32 @@ struct DevScene {
     uint32_t pad[3];
     float4 root_a, root_b;  // root box (lo, hi) in .xyz
 };
+
+// Which ray each thread traces.  width == 0: thread g takes ray g.  width >
+// 0: the rays form a row-major image `width` pixels wide and each warp takes
+// a 4 x 8 pixel tile (tiles in row-major order, lanes row-major inside the
+// tile), so a warp's rays are neighbours in both image directions.  The
+// grid then covers `threads` = tiles_x * tiles_y * 32 threads; threads past
+// the image's right or bottom edge take no ray.  Rays and hits keep the
+// caller's layout either way.
+struct RayMap {
+    unsigned long long n;        // rays
+    unsigned long long threads;  // threads the grid covers
+    uint32_t width, tiles_x;
+};
+
+// Ray of thread g (< map.threads), or map.n when the thread takes none.
+__device__ __forceinline__ unsigned long long ray_of_thread(unsigned long long g,
+                                                            const RayMap& m) {
+    if (m.width == 0) return g;
+    const uint32_t tile = (uint32_t)(g >> 5), lane = (uint32_t)g & 31u;
+    const uint32_t ty = tile / m.tiles_x, tx = tile - ty * m.tiles_x;
+    const uint32_t px = tx * 4u + (lane & 3u);
+    if (px >= m.width) return m.n;
+    const unsigned long long i =
+        ((unsigned long long)ty * 8u + (lane >> 2)) * m.width + px;
+    return i < m.n ? i : m.n;
+}
 
 struct IsectParams {
     uint32_t cutoff_u8;
@@ -285,12 +311,11 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
     uint32_t sp = 0;
     uint32_t steps = 0;
     for (;;) {  // while ray not terminated
-        while (!(ref & kLeafBit)) {  // while node is inner
-            if (++steps > sc.max_steps) {
-                atomicOr(sc.err, kErrSteps);
-                best.prim = kMiss;
-                return;
-            }
+        // While the node is inner.  Descent ends by construction: a loaded
+        // blob is a tree whose children sit at higher node indices than
+        // their parent, so no counter is needed here (leaf visits are
+        // counted below).
+        while (!(ref & kLeafBit)) {
             const float4* p = sc.nodes + 4ull * (ref >> 2);
             const float4 la = VSR_LDG(p), lb = VSR_LDG(p + 1), ra = VSR_LDG(p + 2), rb = VSR_LDG(p + 3);
             const float tfar = (Q == kClosest) ? best.t : r.tmax;
@@ -403,12 +428,7 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
                                               const Ray& r, H& h, Best& best, Stats& st,
                                               uint32_t& ref, uint32_t& sp, uint32_t& steps,
                                               uint32_t* stack, uint32_t stride) {
-    while (!(ref & kLeafBit)) {
-        if (++steps > sc.max_steps) {
-            atomicOr(sc.err, kErrSteps);
-            best.prim = kMiss;
-            return true;
-        }
+    while (!(ref & kLeafBit)) {  // bounded as in traverse_body
         const float4* p = sc.nodes + 4ull * (ref >> 2);
         const float4 la = VSR_LDG(p), lb = VSR_LDG(p + 1), ra = VSR_LDG(p + 2), rb = VSR_LDG(p + 3);
         const float tfar = (Q == kClosest) ? best.t : r.tmax;

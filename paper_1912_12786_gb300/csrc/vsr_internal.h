@@ -13,6 +13,7 @@ struct LaunchArgs {
     IsectParams ip;
     const float4* rays;
     unsigned long long n;
+    RayMap map;  // thread -> ray (map.n == n)
     float4* hits;
     uint2* counters;  // COUNT intersector: (boxes, tris) per ray, may be null
     uint4* stats;     // measurement variant: (boxes, tris, cands, 0), may be null

@@ -439,6 +439,9 @@ int vsr_bvh_validate(const void* blob, size_t bytes) {
             if (axis > 2) return bvh_fail("blob: bad split axis");
             if (l < 2 || (l & 1u) || (uint64_t)l + 1 >= h.num_nodes)
                 return bvh_fail("blob: child index out of range");
+            // descent then strictly increases the node index, which bounds
+            // every traversal loop without a per-step counter
+            if (l <= it.node) return bvh_fail("blob: children must follow their parent");
             for (uint32_t c = l; c <= l + 1; ++c) {
                 if (seen_node[c]) return bvh_fail("blob: node reached twice");
                 seen_node[c] = 1;

@@ -53,7 +53,8 @@ class vsr_intersector(ctypes.Structure):
 
 class vsr_trace_params(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_uint32), ("persistent", ctypes.c_uint32),
-                ("refill_threshold", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+                ("refill_threshold", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("image_width", ctypes.c_uint32)]
 
 
 class vsr_shade_params(ctypes.Structure):
@@ -139,8 +140,9 @@ def intersector(kind="default", dispatch="static", cutoff_u8=128, cutoff_f=0.01,
     return vsr_intersector(ISECT[kind], DISPATCH[dispatch], cutoff_u8, cutoff_f, freq)
 
 
-def trace_params(block_size=128, persistent=0, refill_threshold=16, blocks_per_sm=0):
-    return vsr_trace_params(block_size, persistent, refill_threshold, blocks_per_sm)
+def trace_params(block_size=128, persistent=0, refill_threshold=16, blocks_per_sm=0,
+                 image_width=0):
+    return vsr_trace_params(block_size, persistent, refill_threshold, blocks_per_sm, image_width)
 
 
 class Scene:

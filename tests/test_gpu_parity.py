@@ -142,6 +142,39 @@ def test_ragged_sizes(V, small, n, persistent):
     compare(hits, ref, st, f"n={n}")
 
 
+@pytest.mark.parametrize("width", [1, 3, 4, 5, 37, 256, 1000])
+@pytest.mark.parametrize("n", [1, 31, 33, 4097, 65536])
+def test_image_width_tiles(V, small, width, n):
+    """Pixel-tile thread mapping: every ray traced exactly once, results
+    identical to buffer order (and so to the oracle) for static, dynamic and
+    persistent launches, COUNT counters included, at ragged sizes and widths
+    that leave partial tiles and a partial last row."""
+    sc, rays, blob, s = small
+    sel = _to_dev(np.resize(rays, (n, 8)))
+    for disp, pers, kind, q in [("static", 0, "alpha_tex", "closest"),
+                                ("static", 0, "count", "any"),
+                                ("dynamic", 0, "proc_alpha", "closest"),
+                                ("static", 1, "alpha_tex", "any"),
+                                ("static", 1, "count", "closest")]:
+        cnt = kind == "count"
+        base = V.trace_params(block_size=96, persistent=pers)
+        tiled = V.trace_params(block_size=96, persistent=pers, image_width=width)
+        h0, c0 = V.trace(s, sel, kind, q, disp, counters=cnt, params=base)
+        h1 = torch.full_like(h0, float("nan"))
+        c1 = torch.full_like(c0, -1) if cnt else None
+        V.vsr_trace(s, sel, V.intersector(kind, disp), q, h1, c1, tiled)
+        torch.cuda.synchronize()
+        assert torch.equal(h0.view(torch.int32), h1.view(torch.int32)), (disp, pers, kind, q)
+        if cnt:
+            assert torch.equal(c0, c1)
+    if n == 65536:
+        ref, st = O.trace_bvh(sc, blob, rays, "alpha_tex", "closest")
+        p = V.trace_params(image_width=width)
+        hits, _ = V.trace(s, sel, "alpha_tex", "closest", params=p)
+        compare(hits, ref, st, f"width={width}")
+    assert V.vsr_get_device_error(s) == 0
+
+
 def test_shadow_rays_and_any_hit(V, small):
     sc, rays, blob, s = small
     href, _ = O.trace_bvh(sc, blob, rays, "alpha_tex", "closest")

@@ -415,6 +415,23 @@ def test_blob_corruptions_rejected(small):
     assert bvh_validate(blob[:10]) != ""
 
 
+def test_children_must_follow_their_parent():
+    """The GPU traversal bounds its descent by the node index, so the
+    validator rejects an inner node whose children sit at a lower index; the
+    same tree laid out top-down is accepted."""
+    def leaf(first):
+        return ([-1, -1, 0], first, [1, 1, 3], 1 << 2)
+
+    def inner(left):
+        return ([-1, -1, 0], left, [1, 1, 3], 2)   # count 0, split on z
+
+    pad = ([0, 0, 0], 0, [0, 0, 0], 0)
+    back = [inner(4), pad, leaf(0), leaf(1), inner(2), leaf(2)]
+    down = [inner(2), pad, inner(4), leaf(2), leaf(0), leaf(1)]
+    assert "follow their parent" in bvh_validate(make_blob(back, [0, 1, 2], 2))
+    assert bvh_validate(make_blob(down, [0, 1, 2], 2)) == ""
+
+
 def test_empty_and_single_triangle_blobs():
     b0 = bvh_build(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.uint32))
     assert bvh_validate(b0) == ""
