@@ -13,6 +13,10 @@ Intersectors to the C++ Ray Tracing Template Library Visionaray"):
   paragraph on linear lists; query definitions Section 3.1).
 * ``trace_bvh``   -- the same queries through the while-while BVH traversal
   with both ``intersect`` calls replaced by the intersector (Section 3.2).
+* ``trace_multi`` -- the multi-hit query (the third visibility query of the
+  library the paper extends, Section 1): the first N accepted hits in
+  ascending (t, prim) order, over the list as the plain definition (collect,
+  sort, keep N) or through the BVH traversal with an N-entry buffer.
 * intersector kinds follow Section 3.1 (default forwarding), Section 4
   (alpha-mask listing, procedural alpha, ``bvh_costs``).
 """
@@ -79,6 +83,8 @@ def _load():
         lib.orc_trace_list.argtypes = [P, P, ctypes.c_int, P, ctypes.c_uint64, P, P, ctypes.c_int]
         lib.orc_trace_bvh.argtypes = [P, P, ctypes.c_uint64, P, ctypes.c_int, P,
                                       ctypes.c_uint64, P, P, ctypes.c_int]
+        lib.orc_trace_multi.argtypes = [P, P, ctypes.c_uint64, P, ctypes.c_uint32, P,
+                                        ctypes.c_uint64, P, P, ctypes.c_int]
         lib.orc_intersect_triangle.argtypes = [P, P, P, P, P]
         lib.orc_intersect_aabb.argtypes = [P, P, P, ctypes.c_float]
         lib.orc_shadow_rays.argtypes = [P, P, ctypes.c_uint64, P, ctypes.c_float, P]
@@ -159,6 +165,33 @@ def trace_bvh(scene, blob: np.ndarray, rays, kind="default", query="closest",
     columns are (box tests, triangle tests, intersector calls, near-tie flags)."""
     blob = np.frombuffer(blob, np.uint8) if not isinstance(blob, np.ndarray) else blob
     return _run("bvh", scene, rays, kind, query, nthreads, np.ascontiguousarray(blob), **kw)
+
+
+def trace_multi(scene, rays, nh: int, kind="default", blob=None, nthreads=None, **kw):
+    """Multi-hit query: the first ``nh`` accepted hits of each ray in
+    ascending (t, prim) order, misses after them.  ``blob`` None: sorted brute
+    force over every triangle; otherwise the BVH traversal.  Returns (hits,
+    stats): hits is a dict of [n, nh] arrays (t, u, v, prim); stats as in
+    trace_bvh (for the brute force: triangle tests and consultations)."""
+    lib = _load()
+    sh = _SceneHandle(scene)
+    rays = np.ascontiguousarray(rays, np.float32).reshape(-1, 8)
+    n = rays.shape[0]
+    hits = np.zeros((n * nh, 4), np.float32)
+    stats = np.zeros((n, 4), np.uint32)
+    isect = _isect(kind, **kw)
+    if nthreads is None:
+        nthreads = len(os.sched_getaffinity(0))
+    if blob is not None:
+        blob = np.frombuffer(blob, np.uint8) if not isinstance(blob, np.ndarray) else blob
+        blob = np.ascontiguousarray(blob)
+    rc = lib.orc_trace_multi(ctypes.byref(sh.c), None if blob is None else _ptr(blob),
+                             0 if blob is None else blob.nbytes, ctypes.byref(isect), nh,
+                             _ptr(rays), n, _ptr(hits), _ptr(stats), nthreads)
+    if rc != 0:
+        raise ValueError(f"oracle rejected its inputs (code {rc})")
+    h = split_hits(hits)
+    return {k: v.reshape(n, nh) for k, v in h.items()}, stats
 
 
 def intersect_triangle(ray, v0, v1, v2):

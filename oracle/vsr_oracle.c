@@ -21,7 +21,14 @@
  *   - the closest-hit and any-hit queries (Section 3.1) over a linear list of
  *     primitives (brute force) and over a BVH with the while-while traversal
  *     (Section 3.2, after Aila and Laine 2009) in which both calls to
- *     intersect are replaced by the intersector.
+ *     intersect are replaced by the intersector;
+ *   - the multi-hit query (the third visibility query of the library the
+ *     paper extends, Section 1 and its citation of Zellmann et al. 2017): the
+ *     first N accepted hits in ascending order.  Over a list it is the plain
+ *     definition (collect every accepted candidate, sort, keep N); over the
+ *     BVH it is the closest-hit traversal with a sorted buffer of N entries
+ *     whose last entry plays the role of the closest hit (closest-hit is the
+ *     multi-hit query with N = 1).
  *
  * Rounding: compiled with -ffp-contract=off.  Every fused multiply-add is an
  * explicit fmaf(); every other product or sum is a separately rounded FP32
@@ -34,7 +41,8 @@
  *     cross(a,b).x = fmaf(a.y,b.z, -(a.z*b.y)) and cyclically;
  *   - a candidate lies strictly inside (tmin, tmax); closest-hit replaces the
  *     current best iff t < t_best or (t == t_best and prim < best prim),
- *     comparing original primitive ids, which makes the answer unique;
+ *     comparing original primitive ids, which makes the answer unique; the
+ *     multi-hit order is the same (t, prim) order;
  *   - the intersector is consulted only for geometric candidates inside the
  *     t interval (and, for closest-hit, that would improve the best), which
  *     leaves every hit decision unchanged;
@@ -71,7 +79,7 @@
 enum { ORC_ISECT_NONE = 0, ORC_ISECT_DEFAULT = 1, ORC_ISECT_ALPHA_TEX = 2,
        ORC_ISECT_PROC_ALPHA = 3, ORC_ISECT_COUNT = 4 };
 /* queries */
-enum { ORC_CLOSEST = 0, ORC_ANY = 1 };
+enum { ORC_CLOSEST = 0, ORC_ANY = 1, ORC_MULTI = 2 };
 /* texture formats */
 enum { ORC_TEX_U8 = 0, ORC_TEX_RGBA8 = 1, ORC_TEX_RGBA32F = 2 };
 /* near-tie flags */
@@ -264,28 +272,48 @@ static void note_edge_tie(float u, float v, uint32_t* flags) {
     if (fabs(m) < 1e-6) *flags |= ORC_TIE_EDGE;
 }
 
+/* (t, prim) comes before hit e in the closest-hit / multi-hit order. */
+static int hit_before(float t, uint32_t prim, const orc_hit* e) {
+    return t < e->t || (t == e->t && prim < e->prim);
+}
+
+/* Insert a hit into the ascending buffer buf[0..nh), dropping its last
+ * entry; the caller has checked that the hit comes before that entry. */
+static void insert_hit(orc_hit* buf, uint32_t nh, float t, float u, float v, uint32_t prim) {
+    uint32_t k = nh - 1;
+    while (k > 0 && hit_before(t, prim, &buf[k - 1])) {
+        buf[k] = buf[k - 1];
+        --k;
+    }
+    buf[k].t = t;
+    buf[k].u = u;
+    buf[k].v = v;
+    buf[k].prim = prim;
+}
+
 /* One primitive tested by the intersector under a query.  Returns 1 when an
- * any-hit query terminates.  `best` holds the running result. */
+ * any-hit query terminates.  `best` holds the running result: one hit for
+ * closest-hit and any-hit, the ascending buffer of nh hits for multi-hit
+ * (whose last entry bounds the search as the closest hit does). */
 static int visit_prim(const orc_scene* s, const orc_isect* is, int query,
-                      const orc_ray_ctx* c, uint32_t prim, orc_hit* best, orc_stats* st) {
+                      const orc_ray_ctx* c, uint32_t prim, orc_hit* best, uint32_t nh,
+                      orc_stats* st) {
     float v0[3], e1[3], e2[3], t, u, v;
     tri_verts(s, prim, v0, e1, e2);
     st->tris++;
     const int g = intersect_triangle(&c->r, v0, e1, e2, &t, &u, &v);
     if (g < 0) return 0;
     const int in_range = t > c->r.tmin && t < c->r.tmax;
+    const orc_hit* last = &best[nh - 1];
     if (in_range) {
-        if (query == ORC_ANY || t <= best->t) note_edge_tie(u, v, &st->flags);
+        if (query == ORC_ANY || t <= last->t) note_edge_tie(u, v, &st->flags);
     }
     if (g == 0 || !in_range) return 0;
-    if (query == ORC_CLOSEST) {
-        if (!(t < best->t || (t == best->t && prim < best->prim))) return 0;
+    if (query != ORC_ANY) {
+        if (!hit_before(t, prim, last)) return 0;
         st->cands++;
         if (!intersector_accepts(s, is, prim, u, v, &st->flags)) return 0;
-        best->t = t;
-        best->u = u;
-        best->v = v;
-        best->prim = prim;
+        insert_hit(best, nh, t, u, v, prim);
         return 0;
     }
     st->cands++;
@@ -319,9 +347,51 @@ static void list_query(const orc_scene* s, const orc_isect* is, int query,
     best.prim = ORC_NONE;
     memset(st, 0, sizeof(*st));
     for (uint32_t p = 0; p < s->ntri; ++p)
-        if (visit_prim(s, is, query, &c, p, &best, st)) break;
+        if (visit_prim(s, is, query, &c, p, &best, 1, st)) break;
     if (best.prim == ORC_NONE) miss_record(ray, &best);
     *out = best;
+}
+
+static int cmp_hit(const void* a, const void* b) {
+    const orc_hit* x = (const orc_hit*)a;
+    const orc_hit* y = (const orc_hit*)b;
+    if (hit_before(x->t, x->prim, y)) return -1;
+    if (hit_before(y->t, y->prim, x)) return 1;
+    return 0;
+}
+
+/* Multi-hit over the list, as defined: every triangle tested, every
+ * geometric candidate inside (tmin, tmax) put to the intersector, the
+ * accepted ones sorted by (t, prim) and the first nh kept; missing entries
+ * are miss records.  `scratch` holds room for ntri hits. */
+static void list_multi(const orc_scene* s, const orc_isect* is, uint32_t nh, const orc_ray* ray,
+                       orc_hit* out, orc_hit* scratch, orc_stats* st) {
+    orc_ray_ctx c;
+    ray_setup(ray, &c);
+    memset(st, 0, sizeof(*st));
+    uint32_t m = 0;
+    for (uint32_t p = 0; p < s->ntri; ++p) {
+        float v0[3], e1[3], e2[3], t, u, v;
+        tri_verts(s, p, v0, e1, e2);
+        st->tris++;
+        if (intersect_triangle(&c.r, v0, e1, e2, &t, &u, &v) != 1) continue;
+        if (!(t > c.r.tmin && t < c.r.tmax)) continue;
+        note_edge_tie(u, v, &st->flags);
+        st->cands++;
+        if (!intersector_accepts(s, is, p, u, v, &st->flags)) continue;
+        scratch[m].t = t;
+        scratch[m].u = u;
+        scratch[m].v = v;
+        scratch[m].prim = p;
+        ++m;
+    }
+    qsort(scratch, m, sizeof(orc_hit), cmp_hit);
+    for (uint32_t k = 0; k < nh; ++k) {
+        if (k < m)
+            out[k] = scratch[k];
+        else
+            miss_record(ray, &out[k]);
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -361,26 +431,31 @@ static int parse_blob(const uint8_t* blob, uint64_t bytes, orc_bvh* b) {
 /* ------------------------------------------------------------------ */
 /* intersect(ray, BVH): the while-while traversal                      */
 
+/* out: one hit (closest, any) or nh hits in ascending order (multi). */
 static void bvh_query(const orc_scene* s, const orc_bvh* b, const orc_isect* is, int query,
-                      const orc_ray* ray, orc_hit* out, orc_stats* st) {
+                      uint32_t nh, const orc_ray* ray, orc_hit* out, orc_stats* st) {
     orc_ray_ctx c;
     ray_setup(ray, &c);
-    orc_hit best;
-    best.t = ray->tmax;
-    best.u = best.v = 0.0f;
-    best.prim = ORC_NONE;
+    orc_hit* best = out;
+    if (query != ORC_MULTI) nh = 1;
+    for (uint32_t k = 0; k < nh; ++k) {
+        best[k].t = ray->tmax;
+        best[k].u = best[k].v = 0.0f;
+        best[k].prim = ORC_NONE;
+    }
+    const orc_hit* last = &best[nh - 1];
     memset(st, 0, sizeof(*st));
     uint32_t stack[72];
     int sp = 0;
     if (b->num_prims == 0) goto done;
     st->boxes++;
-    if (!intersect_aabb(&c, b->nodes[0].lo, b->nodes[0].hi, best.t)) goto done;
+    if (!intersect_aabb(&c, b->nodes[0].lo, b->nodes[0].hi, last->t)) goto done;
     uint32_t node = 0;
     for (;;) { /* while ray not terminated */
         while ((b->nodes[node].count_axis >> 2) == 0) { /* while node is inner */
             const orc_node* nd = &b->nodes[node];
             const uint32_t l = nd->left_or_first, r = l + 1;
-            const float far_t = (query == ORC_CLOSEST) ? best.t : ray->tmax;
+            const float far_t = (query != ORC_ANY) ? last->t : ray->tmax;
             st->boxes += 2;
             const int hl = intersect_aabb(&c, b->nodes[l].lo, b->nodes[l].hi, far_t);
             const int hr = intersect_aabb(&c, b->nodes[r].lo, b->nodes[r].hi, far_t);
@@ -402,13 +477,13 @@ static void bvh_query(const orc_scene* s, const orc_bvh* b, const orc_isect* is,
         const orc_node* lf = &b->nodes[node];
         const uint32_t first = lf->left_or_first, cnt = lf->count_axis >> 2;
         for (uint32_t k = 0; k < cnt; ++k)
-            if (visit_prim(s, is, query, &c, b->order[first + k], &best, st)) goto done;
+            if (visit_prim(s, is, query, &c, b->order[first + k], best, nh, st)) goto done;
         if (sp == 0) break;
         node = stack[--sp];
     }
 done:
-    if (best.prim == ORC_NONE) miss_record(ray, &best);
-    *out = best;
+    for (uint32_t k = 0; k < nh; ++k)
+        if (best[k].prim == ORC_NONE) miss_record(ray, &best[k]);
 }
 
 /* ------------------------------------------------------------------ */
@@ -419,6 +494,7 @@ typedef struct {
     const orc_bvh* b; /* NULL: linear list */
     const orc_isect* is;
     int query;
+    uint32_t nh; /* hits per ray (multi-hit), else 1 */
     const orc_ray* rays;
     orc_hit* hits;
     orc_stats* stats;
@@ -428,13 +504,22 @@ typedef struct {
 static void* run_job(void* arg) {
     orc_job* j = (orc_job*)arg;
     orc_stats tmp;
+    orc_hit* scratch = NULL;
+    if (!j->b && j->query == ORC_MULTI) {
+        scratch = (orc_hit*)malloc(sizeof(orc_hit) * (j->s->ntri ? j->s->ntri : 1));
+        if (!scratch) return (void*)1;
+    }
     for (uint64_t i = j->begin; i < j->end; ++i) {
         orc_stats* st = j->stats ? &j->stats[i] : &tmp;
+        orc_hit* out = &j->hits[i * j->nh];
         if (j->b)
-            bvh_query(j->s, j->b, j->is, j->query, &j->rays[i], &j->hits[i], st);
+            bvh_query(j->s, j->b, j->is, j->query, j->nh, &j->rays[i], out, st);
+        else if (j->query == ORC_MULTI)
+            list_multi(j->s, j->is, j->nh, &j->rays[i], out, scratch, st);
         else
-            list_query(j->s, j->is, j->query, &j->rays[i], &j->hits[i], st);
+            list_query(j->s, j->is, j->query, &j->rays[i], out, st);
     }
+    free(scratch);
     return NULL;
 }
 
@@ -449,18 +534,19 @@ static int run_threads(orc_job base, uint64_t n, int nthreads) {
         jobs[k].begin = n * (uint64_t)k / (uint64_t)nthreads;
         jobs[k].end = n * (uint64_t)(k + 1) / (uint64_t)nthreads;
     }
-    if (nthreads == 1) {
-        run_job(&jobs[0]);
-        return 0;
-    }
-    int started = 0;
+    if (nthreads == 1) return run_job(&jobs[0]) ? -7 : 0;
+    int started = 0, failed = 0;
     for (int k = 0; k < nthreads; ++k) {
         if (pthread_create(&th[k], NULL, run_job, &jobs[k]) != 0) break;
         ++started;
     }
-    for (int k = started; k < nthreads; ++k) run_job(&jobs[k]);
-    for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
-    return 0;
+    for (int k = started; k < nthreads; ++k) failed |= run_job(&jobs[k]) != NULL;
+    for (int k = 0; k < started; ++k) {
+        void* r = NULL;
+        pthread_join(th[k], &r);
+        failed |= r != NULL;
+    }
+    return failed ? -7 : 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -470,7 +556,8 @@ static int run_threads(orc_job base, uint64_t n, int nthreads) {
 int orc_trace_list(const orc_scene* s, const orc_isect* is, int query, const float* rays,
                    uint64_t n, float* hits, uint32_t* stats, int nthreads) {
     if (!s || !is || (n && (!rays || !hits))) return -1;
-    orc_job j = {s, NULL, is, query, (const orc_ray*)rays, (orc_hit*)hits,
+    if (query != ORC_CLOSEST && query != ORC_ANY) return -1;
+    orc_job j = {s, NULL, is, query, 1, (const orc_ray*)rays, (orc_hit*)hits,
                  (orc_stats*)stats, 0, 0};
     return run_threads(j, n, nthreads);
 }
@@ -483,7 +570,25 @@ int orc_trace_bvh(const orc_scene* s, const uint8_t* blob, uint64_t bytes,
     int rc = parse_blob(blob, bytes, &b);
     if (rc) return rc;
     if (b.num_prims != s->ntri) return -6;
-    orc_job j = {s, &b, is, query, (const orc_ray*)rays, (orc_hit*)hits,
+    if (query != ORC_CLOSEST && query != ORC_ANY) return -1;
+    orc_job j = {s, &b, is, query, 1, (const orc_ray*)rays, (orc_hit*)hits,
+                 (orc_stats*)stats, 0, 0};
+    return run_threads(j, n, nthreads);
+}
+
+/* Multi-hit query: hits [n * nh] (nh per ray, ascending).  blob == NULL:
+ * the sorted brute force over the list; otherwise the BVH traversal. */
+int orc_trace_multi(const orc_scene* s, const uint8_t* blob, uint64_t bytes,
+                    const orc_isect* is, uint32_t nh, const float* rays, uint64_t n,
+                    float* hits, uint32_t* stats, int nthreads) {
+    if (!s || !is || nh < 1 || (n && (!rays || !hits))) return -1;
+    orc_bvh b;
+    if (blob) {
+        int rc = parse_blob(blob, bytes, &b);
+        if (rc) return rc;
+        if (b.num_prims != s->ntri) return -6;
+    }
+    orc_job j = {s, blob ? &b : NULL, is, ORC_MULTI, nh, (const orc_ray*)rays, (orc_hit*)hits,
                  (orc_stats*)stats, 0, 0};
     return run_threads(j, n, nthreads);
 }
