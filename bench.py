@@ -426,6 +426,7 @@ def run_ours(args):
 
     if not args.no_breakdown:
         out["breakdown"] = breakdown(V, s, d_rays, rays_s, n, flush, stream, torch)
+        out["multi_hit"] = multi_hit(V, s, d_rays, n, flush, stream, torch)
         out["fwd_bwd"] = fwd_bwd(V, torch, dev, flush, stream, args.steps, args.warmup)
         out["batch"] = batch_bench(V, torch, dev, flush, stream, args.steps)
         out["large"] = large_bench(V, torch, dev, flush, stream, args.steps)
@@ -480,6 +481,33 @@ def breakdown(V, s, d_rays, rays_s, n, flush, stream, torch, reps=5):
             res[f"{q}/{kind}/overhead_vs_default"] = round(base / res[f"{q}/{kind}/static"] - 1, 4)
             res[f"{q}/{kind}/dynamic_vs_static"] = round(
                 res[f"{q}/{kind}/static"] / res[f"{q}/{kind}/dynamic"], 4)
+    return res
+
+
+def multi_hit(V, s, d_rays, n, flush, stream, torch, reps=5):
+    """Multi-hit query on the forest's primary rays: the first N accepted
+    hits through the alpha-masked billboards (N = 1 is the closest-hit
+    query), same launch configuration as the timed step."""
+    res = {}
+    p = default_params(V)
+    alpha = V.intersector("alpha_tex")
+    for nh in (1, 4, 8, 16):
+        hits = torch.empty((n, nh, 4), dtype=torch.float32, device=d_rays.device)
+        ms = []
+        for r in range(reps + 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            V.vsr_trace_multi(s, d_rays, alpha, nh, hits, None, p, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if r >= 2:
+                ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        found = int((hits[:, :, 3].view(torch.int32) != -1).sum().item())
+        res[f"n{nh}_Mrays_s"] = round(n / (t / 1e3) / 1e6, 1)
+        res[f"n{nh}_ms"] = round(t, 4)
+        res[f"n{nh}_hits_per_ray"] = round(found / n, 3)
     return res
 
 

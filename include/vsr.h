@@ -215,6 +215,26 @@ vsr_status vsr_trace(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
                      uint32_t* counters, const vsr_trace_params* params, vsr_stream stream);
 
 /*
+ * Multi-hit query: the first max_hits accepted hits of each ray in ascending
+ * (t, prim) order -- the third visibility query of the library the paper
+ * extends (Section 1), with the custom intersector injected exactly as for
+ * closest-hit (Section 3.2).  The traversal is the closest-hit traversal whose
+ * bound is the max_hits-th entry of a sorted buffer, so the intersector is
+ * consulted for the candidates that would enter the buffer; max_hits == 1 is
+ * the closest-hit query.
+ *   hits      device vsr_hit [n * max_hits]: ray i's hits at i*max_hits + k,
+ *             nearest first, then miss records (t = +inf, u = v = 0,
+ *             prim = VSR_MISS)
+ *   counters  as vsr_trace (COUNT intersector only), or NULL
+ *   max_hits  1..16; static dispatch; params->persistent must be 0
+ * Errors as vsr_trace.
+ */
+vsr_status vsr_trace_multi(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
+                           const vsr_intersector* isect, uint32_t max_hits, vsr_hit* hits,
+                           uint32_t* counters, const vsr_trace_params* params,
+                           vsr_stream stream);
+
+/*
  * Measurement variant of vsr_trace with the static intersector: identical
  * hits, plus per-ray statistics stats device uint32 [n*4] = (box tests,
  * triangle tests, intersector consultations, 0).  Used to count the bytes

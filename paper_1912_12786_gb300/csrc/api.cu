@@ -546,6 +546,38 @@ vsr_status vsr_trace(vsr_scene* s, const vsr_ray* rays, uint64_t n, const vsr_in
     return VSR_OK;
 }
 
+vsr_status vsr_trace_multi(vsr_scene* s, const vsr_ray* rays, uint64_t n,
+                           const vsr_intersector* is, uint32_t max_hits, vsr_hit* hits,
+                           uint32_t* counters, const vsr_trace_params* p, vsr_stream stream) {
+    g_err.clear();
+    if (max_hits < 1 || max_hits > 16) return fail(VSR_ERR_ARG, "max_hits must be in 1..16");
+    if (is && is->dispatch != VSR_DISPATCH_STATIC)
+        return fail(VSR_ERR_ARG, "the multi-hit query uses static dispatch only");
+    if (p && p->persistent) return fail(VSR_ERR_ARG, "the multi-hit query uses one ray per thread");
+    LaunchArgs a;
+    vsr_status st = prepare_launch(s, rays, n, is, VSR_CLOSEST, hits, p, a);
+    if (st != VSR_OK) return st;
+    if (n) {
+        st = check_dev(hits, s->device, "hits", 16, n * max_hits * sizeof(vsr_hit));
+        if (st != VSR_OK) return st;
+    }
+    if (counters) {
+        if (is->kind != VSR_ISECT_COUNT)
+            return fail(VSR_ERR_ARG, "counters are written by the COUNT intersector only");
+        if (n) {
+            st = check_dev(counters, s->device, "counters", 8, n * 8);
+            if (st != VSR_OK) return st;
+        }
+        a.counters = reinterpret_cast<uint2*>(counters);
+    }
+    if (n == 0) return VSR_OK;
+    a.stream = reinterpret_cast<cudaStream_t>(stream);
+    DeviceGuard g(s->device);
+    cudaError_t e = launch_multi(a, is->kind, s->d_verts, s->d_idx, max_hits);
+    if (e != cudaSuccess) return cuda_fail(e, "multi-hit launch");
+    return VSR_OK;
+}
+
 vsr_status vsr_trace_stats(vsr_scene* s, const vsr_ray* rays, uint64_t n,
                            const vsr_intersector* is, int32_t query, vsr_hit* hits,
                            uint32_t* stats, vsr_stream stream) {

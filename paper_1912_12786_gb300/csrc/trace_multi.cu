@@ -1,0 +1,98 @@
+// Multi-hit query with the intersector injected at compile time: the first
+// n accepted hits of each ray in ascending (t, prim) order.  This is the third
+// visibility query of the library the paper extends (Section 1, next to
+// closest-hit and any-hit), and the custom intersector reaches it the same
+// way (Section 3.2).  The traversal is the closest-hit traversal with the n-th
+// entry of a sorted buffer as its bound (MultiBest), so the intersector is
+// consulted for exactly the candidates that would enter the buffer; with
+// n == 1 it is the closest-hit query.
+#include "vsr_internal.h"
+
+namespace vsr {
+
+namespace {
+
+// Hit record of a kept entry: the triangle test again on the original
+// vertices, with the edges formed as the device triangle layout forms them
+// (k_build_tris), which reproduces t, u and v bit for bit.  A kept entry
+// passed this test during the traversal, so it passes it again.
+__device__ __forceinline__ float4 multi_record(const Ray& r, const float* __restrict__ verts,
+                                               const uint32_t* __restrict__ idx, uint32_t p) {
+    if (p == kMiss) return make_float4(__int_as_float(0x7f800000), 0.0f, 0.0f, __uint_as_float(p));
+    const float* a = verts + 3ull * VSR_LDG(idx + 3ull * p);
+    const float* b = verts + 3ull * VSR_LDG(idx + 3ull * p + 1);
+    const float* c = verts + 3ull * VSR_LDG(idx + 3ull * p + 2);
+    const float4 v0 = make_float4(VSR_LDG(a), VSR_LDG(a + 1), VSR_LDG(a + 2), 0.0f);
+    const float4 e1 = make_float4(__fsub_rn(VSR_LDG(b), v0.x), __fsub_rn(VSR_LDG(b + 1), v0.y),
+                                  __fsub_rn(VSR_LDG(b + 2), v0.z), 0.0f);
+    const float4 e2 = make_float4(__fsub_rn(VSR_LDG(c), v0.x), __fsub_rn(VSR_LDG(c + 1), v0.y),
+                                  __fsub_rn(VSR_LDG(c + 2), v0.z), 0.0f);
+    float t = 0.0f, u = 0.0f, v = 0.0f;
+    tri_test(r, v0, e1, e2, t, u, v);
+    return make_float4(t, u, v, __uint_as_float(p));
+}
+
+template <class H, int NT>
+__global__ void __launch_bounds__(256) k_trace_multi(DevScene sc, IsectParams ip,
+                                                     const float* __restrict__ verts,
+                                                     const uint32_t* __restrict__ idx,
+                                                     const float4* __restrict__ rays, RayMap map,
+                                                     uint32_t nh, float4* __restrict__ hits,
+                                                     uint2* __restrict__ counters) {
+    extern __shared__ uint32_t s_stack[];
+    const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= map.threads) return;
+    const unsigned long long i = ray_of_thread(g, map);
+    if (i >= map.n) return;
+    const Ray r = make_ray(__ldg(rays + 2 * i), __ldg(rays + 2 * i + 1));
+    H h;
+    MultiBest<NT> mb;
+    mb.n = nh;
+    Stats st;
+    traverse_body<kClosest, H, false>(sc, ip, r, h, mb, st, s_stack + threadIdx.x, blockDim.x);
+    float4* out = hits + i * nh;
+#pragma unroll
+    for (int k = 0; k < NT; ++k)
+        if ((uint32_t)k < nh) out[k] = multi_record(r, verts, idx, mb.pk[k]);
+    if (H::kCounts && counters) counters[i] = h.counters();
+}
+
+template <class H, int NT>
+cudaError_t multi_one(const LaunchArgs& a, const float* verts, const uint32_t* idx, uint32_t nh) {
+    const size_t smem = (size_t)a.sc.stack_depth * a.block * sizeof(uint32_t);
+    auto k = k_trace_multi<H, NT>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
+    k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, verts, idx, a.rays, a.map, nh,
+                                                     a.hits, a.counters);
+    return cudaGetLastError();
+}
+
+// Buffers of 4, 8 or 16 entries; n up to the buffer size.
+template <class H>
+cudaError_t multi_sized(const LaunchArgs& a, const float* verts, const uint32_t* idx,
+                        uint32_t nh) {
+    if (nh <= 4) return multi_one<H, 4>(a, verts, idx, nh);
+    if (nh <= 8) return multi_one<H, 8>(a, verts, idx, nh);
+    return multi_one<H, 16>(a, verts, idx, nh);
+}
+
+}  // namespace
+
+cudaError_t launch_multi(const LaunchArgs& a, int kind, const float* verts, const uint32_t* idx,
+                         uint32_t nh) {
+    if (nh < 1 || nh > 16) return cudaErrorInvalidValue;
+    switch (kind) {
+        case 0: return multi_sized<IsectNone>(a, verts, idx, nh);
+        case 1: return multi_sized<IsectDefault>(a, verts, idx, nh);
+        case 2: return multi_sized<IsectAlphaTex>(a, verts, idx, nh);
+        case 3: return multi_sized<IsectProcAlpha>(a, verts, idx, nh);
+        case 4: return multi_sized<IsectCount>(a, verts, idx, nh);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace vsr

@@ -286,23 +286,92 @@ struct Stats {
     uint32_t boxes = 0, tris = 0, cands = 0, texs = 0;
 };
 
+// The running result of the closest-hit and any-hit queries.  The traversal
+// bounds its search by (t, prim) and hands every accepted candidate to take().
 struct Best {
     float t, u, v;
     uint32_t prim;
+    __device__ __forceinline__ void init(float tmax) {
+        t = tmax;
+        u = 0.0f;
+        v = 0.0f;
+        prim = kMiss;
+    }
+    __device__ __forceinline__ void take(float tc, float uc, float vc, uint32_t pc) {
+        t = tc;
+        u = uc;
+        v = vc;
+        prim = pc;
+    }
+    __device__ __forceinline__ void fail() { prim = kMiss; }
+};
+
+// (t, prim) comes before (t2, prim2) in the closest-hit / multi-hit order.
+__device__ __forceinline__ bool hit_before(float t, uint32_t p, float t2, uint32_t p2) {
+    return t < t2 || (t == t2 && p < p2);
+}
+
+// The running result of the multi-hit query: the first n (<= NT) accepted
+// hits in ascending (t, prim) order, kept as (t, prim) in registers (the
+// barycentrics are recomputed for the final entries).  (t, prim) mirror entry
+// n - 1, so the traversal's closest-hit bound is the multi-hit bound; with
+// n == 1 the query is the closest-hit query.  Entries at n and beyond are
+// scratch that take() may overwrite and nothing reads.
+template <int NT>
+struct MultiBest {
+    float tk[NT];
+    uint32_t pk[NT];
+    float t;
+    uint32_t prim;
+    uint32_t n;
+    __device__ __forceinline__ void init(float tmax) {
+#pragma unroll
+        for (int k = 0; k < NT; ++k) {
+            tk[k] = tmax;
+            pk[k] = kMiss;
+        }
+        t = tmax;
+        prim = kMiss;
+    }
+    // Insert a candidate that comes before entry n - 1 (the caller checked).
+    __device__ __forceinline__ void take(float tc, float, float, uint32_t pc) {
+#pragma unroll
+        for (int k = NT - 1; k > 0; --k) {
+            if (hit_before(tc, pc, tk[k - 1], pk[k - 1])) {
+                tk[k] = tk[k - 1];
+                pk[k] = pk[k - 1];
+            } else if (hit_before(tc, pc, tk[k], pk[k])) {
+                tk[k] = tc;
+                pk[k] = pc;
+            }
+        }
+        if (hit_before(tc, pc, tk[0], pk[0])) {
+            tk[0] = tc;
+            pk[0] = pc;
+        }
+#pragma unroll
+        for (int k = 0; k < NT; ++k)
+            if ((uint32_t)k + 1u == n) {
+                t = tk[k];
+                prim = pk[k];
+            }
+    }
+    __device__ __forceinline__ void fail() {
+#pragma unroll
+        for (int k = 0; k < NT; ++k) pk[k] = kMiss;
+        prim = kMiss;
+    }
 };
 
 // --------------------------------------------------------------------------
 // The while-while traversal.  `stack` points at this thread's column of a
 // shared-memory stack with `stride` words between levels.
 
-template <int Q, class H, bool STATS>
+template <int Q, class H, bool STATS, class B = Best>
 __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectParams& ip,
-                                              const Ray& r, H& h, Best& best, Stats& st,
+                                              const Ray& r, H& h, B& best, Stats& st,
                                               uint32_t* stack, uint32_t stride) {
-    best.t = r.tmax;
-    best.u = 0.0f;
-    best.v = 0.0f;
-    best.prim = kMiss;
+    best.init(r.tmax);
     if (sc.nprims == 0) return;
     h.box();
     if (STATS) st.boxes++;
@@ -329,7 +398,7 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
                 const bool neg = (r.negmask >> (ref & 3u)) & 1u;
                 if (sp >= sc.stack_depth) {  // unreachable for a validated blob
                     atomicOr(sc.err, kErrStack);
-                    best.prim = kMiss;
+                    best.fail();
                     return;
                 }
                 stack[sp * stride] = neg ? rl : rr;
@@ -348,7 +417,7 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
         {  // found a leaf: test its primitives
             if (++steps > sc.max_steps) {
                 atomicOr(sc.err, kErrSteps);
-                best.prim = kMiss;
+                best.fail();
                 return;
             }
             const uint32_t first = (ref >> 3) & 0x0FFFFFFFu;
@@ -365,17 +434,14 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
                 if (!geo || !(t > r.tmin) || !(t < r.tmax)) continue;
                 const uint32_t prim = __float_as_uint(a.w);
                 if (Q == kClosest) {
-                    if (!(t < best.t || (t == best.t && prim < best.prim))) continue;
+                    if (!hit_before(t, prim, best.t, best.prim)) continue;
                 }
                 if (STATS) {
                     st.cands++;
                     if (H::kTexcoords && VSR_LDG(sc.geom + prim) != kMiss) st.texs++;
                 }
                 if (!h.accept(sc, ip, prim, u, v)) continue;
-                best.t = t;
-                best.u = u;
-                best.v = v;
-                best.prim = prim;
+                best.take(t, u, v, prim);
                 if (Q == kAny) return;
             }
         }
@@ -409,10 +475,7 @@ template <int Q, class H, bool STATS>
 __device__ __forceinline__ bool traverse_start(const DevScene& sc, const Ray& r, H& h, Best& best,
                                                Stats& st, uint32_t& ref, uint32_t& sp,
                                                uint32_t& steps) {
-    best.t = r.tmax;
-    best.u = 0.0f;
-    best.v = 0.0f;
-    best.prim = kMiss;
+    best.init(r.tmax);
     sp = 0;
     steps = 0;
     if (sc.nprims == 0) return false;
@@ -442,7 +505,7 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
             const bool neg = (r.negmask >> (ref & 3u)) & 1u;
             if (sp >= sc.stack_depth) {
                 atomicOr(sc.err, kErrStack);
-                best.prim = kMiss;
+                best.fail();
                 return true;
             }
             stack[sp * stride] = neg ? rl : rr;
@@ -460,7 +523,7 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
     }
     if (++steps > sc.max_steps) {
         atomicOr(sc.err, kErrSteps);
-        best.prim = kMiss;
+        best.fail();
         return true;
     }
     const uint32_t first = (ref >> 3) & 0x0FFFFFFFu;
@@ -476,17 +539,14 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
         if (!geo || !(t > r.tmin) || !(t < r.tmax)) continue;
         const uint32_t prim = __float_as_uint(a.w);
         if (Q == kClosest) {
-            if (!(t < best.t || (t == best.t && prim < best.prim))) continue;
+            if (!hit_before(t, prim, best.t, best.prim)) continue;
         }
         if (STATS) {
             st.cands++;
             if (H::kTexcoords && VSR_LDG(sc.geom + prim) != kMiss) st.texs++;
         }
         if (!h.accept(sc, ip, prim, u, v)) continue;
-        best.t = t;
-        best.u = u;
-        best.v = v;
-        best.prim = prim;
+        best.take(t, u, v, prim);
         if (Q == kAny) return true;
     }
     if (sp == 0) return true;

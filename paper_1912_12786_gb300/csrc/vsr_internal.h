@@ -42,6 +42,11 @@ cudaError_t launch_dynamic(const LaunchArgs& a, int kind);
 // Resident blocks per SM for the given kernel configuration (0 on error).
 int persistent_grid(const LaunchArgs& a, const void* kernel, size_t smem);
 
+// Multi-hit query (trace_multi.cu): the first nh (1..16) accepted hits per
+// ray in ascending (t, prim) order into a.hits [n * nh].
+cudaError_t launch_multi(const LaunchArgs& a, int kind, const float* verts, const uint32_t* idx,
+                         uint32_t nh);
+
 // Closest-hit render with diffuse shading, and its adjoint (render.cu).
 cudaError_t launch_render(const LaunchArgs& a, int kind, const ShadeDev& sh, const float* verts,
                           const uint32_t* idx, float* image, float4* hits);

@@ -75,6 +75,7 @@ _SIGS = {
     "vsr_bvh_load": ([P, P, ctypes.c_size_t], ctypes.c_int),
     "vsr_trace": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P], ctypes.c_int),
     "vsr_trace_stats": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P], ctypes.c_int),
+    "vsr_trace_multi": ([P, P, ctypes.c_uint64, P, ctypes.c_uint32, P, P, P, P], ctypes.c_int),
     "vsr_trace_persistent_noalloc": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P],
                                      ctypes.c_int),
     "vsr_batch_create": ([P, P, P, P, ctypes.c_uint32, P, ctypes.c_int32, P, ctypes.POINTER(P)],
@@ -222,6 +223,16 @@ def _stream(stream):
 
 def _ptr(t):
     return None if t is None else t.data_ptr()
+
+
+def vsr_trace_multi(scene: Scene, rays, isect: vsr_intersector, max_hits: int, hits,
+                    counters=None, params: vsr_trace_params | None = None, stream=None):
+    """First ``max_hits`` accepted hits per ray, nearest first, into ``hits``
+    (cuda float32 [n * max_hits, 4] or [n, max_hits, 4])."""
+    n = int(rays.shape[0])
+    _check(lib().vsr_trace_multi(scene.handle, _ptr(rays), n, ctypes.byref(isect), int(max_hits),
+                                 _ptr(hits), _ptr(counters),
+                                 ctypes.byref(params) if params else None, _stream(stream)))
 
 
 def vsr_trace(scene: Scene, rays, isect: vsr_intersector, query, hits, counters=None,

@@ -1,0 +1,134 @@
+"""Multi-hit query on the GPU vs the oracle, through the C ABI (needs a GB300).
+
+Bar: the first N accepted hits of each ray (t, u, v, prim, in ascending
+(t, prim) order, then miss records) are bit-identical to the oracle's
+multi-hit traversal, and bvh_costs counters too; rays the oracle flags as near
+ties may differ and are excluded, as for closest-hit.  N = 1 must reproduce
+vsr_trace's closest hit bit for bit.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1912_12786_gb300.inputs import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+KINDS = ["none", "default", "alpha_tex", "proc_alpha", "count"]
+
+
+@pytest.fixture(scope="module")
+def V():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_12786_gb300 import _build, vsr
+    _build.build()
+    return vsr
+
+
+@pytest.fixture(scope="module")
+def small(V):
+    sc, rays = scenes.small_quads()
+    blob = sc.bvh()
+    s = V.scene_from_inputs(sc, blob)
+    yield sc, rays, blob, s
+    s.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _multi(V, s, rays, kind, nh, params=None, counters=False):
+    n = rays.shape[0]
+    hits = torch.full((n, nh, 4), float("nan"), dtype=torch.float32, device="cuda")
+    cnt = torch.full((n, 2), -1, dtype=torch.int32, device="cuda") if counters else None
+    V.vsr_trace_multi(s, rays, V.intersector(kind), nh, hits, cnt, params)
+    torch.cuda.synchronize()
+    return hits.cpu().numpy(), (cnt.cpu().numpy().view(np.uint32) if counters else None)
+
+
+def _compare(got, ref, st, label):
+    """got [n, nh, 4] float32; ref dict of [n, nh]; st oracle stats."""
+    r = np.stack([ref["t"], ref["u"], ref["v"], ref["prim"].view(np.float32)], -1)
+    bad = np.any(got.view(np.uint32) != r.view(np.uint32), axis=(1, 2))
+    ties = st[:, 3] != 0
+    assert not (bad & ~ties).any(), f"{label}: {int((bad & ~ties).sum())} rays differ"
+    return int(ties.sum())
+
+
+@pytest.mark.parametrize("nh", [1, 3, 4, 5, 8, 9, 16])
+@pytest.mark.parametrize("kind", KINDS)
+def test_small_all_intersectors(V, small, kind, nh):
+    sc, rays, blob, s = small
+    ref, st = O.trace_multi(sc, rays, nh, kind, blob)
+    got, cnt = _multi(V, s, _dev(rays), kind, nh, counters=(kind == "count"))
+    _compare(got, ref, st, f"{kind} nh={nh}")
+    if kind == "count":
+        ok = st[:, 3] == 0
+        assert np.array_equal(cnt[ok], st[ok, :2])
+    assert V.vsr_get_device_error(s) == 0
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_one_hit_is_vsr_trace(V, small, kind):
+    sc, rays, blob, s = small
+    d = _dev(rays)
+    got, _ = _multi(V, s, d, kind, 1)
+    h, _ = V.trace(s, d, kind, "closest")
+    torch.cuda.synchronize()
+    assert np.array_equal(got[:, 0].view(np.uint32), h.cpu().numpy().view(np.uint32))
+
+
+@pytest.mark.parametrize("n,width", [(1, 0), (33, 0), (4097, 0), (4097, 37), (65536, 256)])
+def test_ragged_and_pixel_tiles(V, small, n, width):
+    sc, rays, blob, s = small
+    sel = np.resize(rays[::-1], (n, 8))
+    ref, st = O.trace_multi(sc, sel, 6, "alpha_tex", blob)
+    got, _ = _multi(V, s, _dev(sel), "alpha_tex", 6, V.trace_params(image_width=width))
+    _compare(got, ref, st, f"n={n} width={width}")
+
+
+def test_argument_checks(V, small):
+    sc, rays, blob, s = small
+    d = _dev(rays[:64])
+    hits = torch.empty((64, 16, 4), dtype=torch.float32, device="cuda")
+    for nh in (0, 17):
+        with pytest.raises(V.VsrError):
+            V.vsr_trace_multi(s, d, V.intersector("default"), nh, hits)
+    with pytest.raises(V.VsrError, match="static dispatch"):
+        V.vsr_trace_multi(s, d, V.intersector("default", "dynamic"), 4, hits)
+    with pytest.raises(V.VsrError, match="one ray per thread"):
+        V.vsr_trace_multi(s, d, V.intersector("default"), 4, hits, None,
+                          V.trace_params(persistent=1))
+    small_hits = torch.empty((64, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(V.VsrError, match="hits"):
+        V.vsr_trace_multi(s, _dev(np.resize(rays, (1 << 16, 8))), V.intersector("default"), 16,
+                          small_hits)
+
+
+def test_forest_full_frame_sample(V):
+    """1920x1080 primary rays through the alpha-masked forest, 8 hits per
+    ray in the bench's launch configuration: a seeded sample against the
+    oracle, and the first column against vsr_trace over the whole frame."""
+    import bench
+    sc, rays = scenes.billboard_forest()
+    blob = sc.bvh()
+    s = V.scene_from_inputs(sc, blob)
+    try:
+        d = _dev(rays)
+        p = bench.default_params(V)
+        got, _ = _multi(V, s, d, "alpha_tex", 8, p)
+        h, _ = V.trace(s, d, "alpha_tex", "closest", params=p)
+        torch.cuda.synchronize()
+        assert np.array_equal(got[:, 0].view(np.uint32), h.cpu().numpy().view(np.uint32))
+        rng = np.random.default_rng(11)
+        sel = np.sort(rng.choice(len(rays), 4000, replace=False))
+        ref, st = O.trace_multi(sc, rays[sel], 8, "alpha_tex", blob)
+        assert _compare(got[sel], ref, st, "forest") <= 0.01 * len(sel)
+        depth = (got[:, :, 3].view(np.uint32) != O.NONE).sum(1)
+        assert depth.mean() > 2.0  # looking through several layers of foliage
+        assert V.vsr_get_device_error(s) == 0
+    finally:
+        s.close()
