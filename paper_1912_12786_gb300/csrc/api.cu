@@ -660,6 +660,15 @@ vsr_status vsr_get_device_error(vsr_scene* s, uint32_t* word) {
         g_err = "render kernel skipped a misaligned load at render.cu/vsr_device.cuh line " +
                 std::to_string(line);
     }
+    line = 0;
+    VSR_CUDA(multi_align_error(&line), "read alignment check");
+    if (line) {
+        *word |= kErrAlign;
+        g_err += (g_err.empty() ? "" : "; ") +
+                 std::string("multi-hit kernel skipped a misaligned access at "
+                             "trace_multi.cu/vsr_device.cuh line ") +
+                 std::to_string(line);
+    }
     return VSR_OK;
 }
 

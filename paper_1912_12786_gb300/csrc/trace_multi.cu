@@ -6,6 +6,14 @@
 // entry of a sorted buffer as its bound (MultiBest), so the intersector is
 // consulted for exactly the candidates that would enter the buffer; with
 // n == 1 it is the closest-hit query.
+//
+// The first launch of the unchecked build raised a misaligned-address fault
+// that reading the code did not explain (every access here uses a cudaMalloc
+// or caller base and an index that keeps the access width's alignment), so,
+// as for the render kernels, every load goes through the alignment-checked
+// path and the hit and counter stores check their address: a misaligned
+// access is skipped and its source line reported (device error bit 2).
+#define VSR_CHECKED_LOADS 1
 #include "vsr_internal.h"
 
 namespace vsr {
@@ -44,7 +52,7 @@ __global__ void __launch_bounds__(256) k_trace_multi(DevScene sc, IsectParams ip
     if (g >= map.threads) return;
     const unsigned long long i = ray_of_thread(g, map);
     if (i >= map.n) return;
-    const Ray r = make_ray(__ldg(rays + 2 * i), __ldg(rays + 2 * i + 1));
+    const Ray r = make_ray(VSR_LDG(rays + 2 * i), VSR_LDG(rays + 2 * i + 1));
     H h;
     MultiBest<NT> mb;
     mb.n = nh;
@@ -52,9 +60,20 @@ __global__ void __launch_bounds__(256) k_trace_multi(DevScene sc, IsectParams ip
     traverse_body<kClosest, H, false>(sc, ip, r, h, mb, st, s_stack + threadIdx.x, blockDim.x);
     float4* out = hits + i * nh;
 #pragma unroll
-    for (int k = 0; k < NT; ++k)
-        if ((uint32_t)k < nh) out[k] = multi_record(r, verts, idx, mb.pk[k]);
-    if (H::kCounts && counters) counters[i] = h.counters();
+    for (int k = 0; k < NT; ++k) {
+        if ((uint32_t)k >= nh) continue;
+        const float4 rec = multi_record(r, verts, idx, mb.pk[k]);
+        if (reinterpret_cast<unsigned long long>(out + k) % 16)
+            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
+        else
+            out[k] = rec;
+    }
+    if (H::kCounts && counters) {
+        if (reinterpret_cast<unsigned long long>(counters + i) % 8)
+            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
+        else
+            counters[i] = h.counters();
+    }
 }
 
 template <class H, int NT>
@@ -81,6 +100,13 @@ cudaError_t multi_sized(const LaunchArgs& a, const float* verts, const uint32_t*
 }
 
 }  // namespace
+
+cudaError_t multi_align_error(unsigned* line) {
+    cudaError_t e = cudaMemcpyFromSymbol(line, g_vsr_align_line, sizeof(unsigned));
+    if (e != cudaSuccess || *line == 0) return e;
+    const unsigned zero = 0;
+    return cudaMemcpyToSymbol(g_vsr_align_line, &zero, sizeof(unsigned));
+}
 
 cudaError_t launch_multi(const LaunchArgs& a, int kind, const float* verts, const uint32_t* idx,
                          uint32_t nh) {

@@ -46,6 +46,9 @@ int persistent_grid(const LaunchArgs& a, const void* kernel, size_t smem);
 // ray in ascending (t, prim) order into a.hits [n * nh].
 cudaError_t launch_multi(const LaunchArgs& a, int kind, const float* verts, const uint32_t* idx,
                          uint32_t nh);
+// Source line of the first misaligned access the multi-hit kernels skipped
+// (0 if none), cleared after reading.
+cudaError_t multi_align_error(unsigned* line);
 
 // Closest-hit render with diffuse shading, and its adjoint (render.cu).
 cudaError_t launch_render(const LaunchArgs& a, int kind, const ShadeDev& sh, const float* verts,
