@@ -3,9 +3,10 @@
 // visibility query of the library the paper extends (Section 1, next to
 // closest-hit and any-hit), and the custom intersector reaches it the same
 // way (Section 3.2).  The traversal is the closest-hit traversal with the n-th
-// entry of a sorted buffer as its bound (MultiBest), so the intersector is
-// consulted for exactly the candidates that would enter the buffer; with
-// n == 1 it is the closest-hit query.
+// entry of a sorted buffer as its bound (MultiBest, in shared memory after
+// the traversal stack), so the intersector is consulted for exactly the
+// candidates that would enter the buffer; with n == 1 it is the closest-hit
+// query.
 //
 // The first launch of the unchecked build raised a misaligned-address fault
 // that reading the code did not explain (every access here uses a cudaMalloc
@@ -40,7 +41,7 @@ __device__ __forceinline__ float4 multi_record(const Ray& r, const float* __rest
     return make_float4(t, u, v, __uint_as_float(p));
 }
 
-template <class H, int NT>
+template <class H>
 __global__ void __launch_bounds__(256) k_trace_multi(DevScene sc, IsectParams ip,
                                                      const float* __restrict__ verts,
                                                      const uint32_t* __restrict__ idx,
@@ -54,15 +55,20 @@ __global__ void __launch_bounds__(256) k_trace_multi(DevScene sc, IsectParams ip
     if (i >= map.n) return;
     const Ray r = make_ray(VSR_LDG(rays + 2 * i), VSR_LDG(rays + 2 * i + 1));
     H h;
-    MultiBest<NT> mb;
+    // shared memory: stack (depth x block words), then the buffer's t and
+    // prim columns (nh x block words each)
+    const uint32_t stride = blockDim.x;
+    uint32_t* buf = s_stack + sc.stack_depth * stride;
+    MultiBest mb;
+    mb.tk = reinterpret_cast<float*>(buf) + threadIdx.x;
+    mb.pk = buf + nh * stride + threadIdx.x;
+    mb.stride = stride;
     mb.n = nh;
     Stats st;
-    traverse_body<kClosest, H, false>(sc, ip, r, h, mb, st, s_stack + threadIdx.x, blockDim.x);
+    traverse_body<kClosest, H, false>(sc, ip, r, h, mb, st, s_stack + threadIdx.x, stride);
     float4* out = hits + i * nh;
-#pragma unroll
-    for (int k = 0; k < NT; ++k) {
-        if ((uint32_t)k >= nh) continue;
-        const float4 rec = multi_record(r, verts, idx, mb.pk[k]);
+    for (uint32_t k = 0; k < nh; ++k) {
+        const float4 rec = multi_record(r, verts, idx, mb.pk[k * stride]);
         if (reinterpret_cast<unsigned long long>(out + k) % 16)
             atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
         else
@@ -76,10 +82,10 @@ __global__ void __launch_bounds__(256) k_trace_multi(DevScene sc, IsectParams ip
     }
 }
 
-template <class H, int NT>
+template <class H>
 cudaError_t multi_one(const LaunchArgs& a, const float* verts, const uint32_t* idx, uint32_t nh) {
-    const size_t smem = (size_t)a.sc.stack_depth * a.block * sizeof(uint32_t);
-    auto k = k_trace_multi<H, NT>;
+    const size_t smem = ((size_t)a.sc.stack_depth + 2u * nh) * a.block * sizeof(uint32_t);
+    auto k = k_trace_multi<H>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -88,15 +94,6 @@ cudaError_t multi_one(const LaunchArgs& a, const float* verts, const uint32_t* i
     k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, verts, idx, a.rays, a.map, nh,
                                                      a.hits, a.counters);
     return cudaGetLastError();
-}
-
-// Buffers of 4, 8 or 16 entries; n up to the buffer size.
-template <class H>
-cudaError_t multi_sized(const LaunchArgs& a, const float* verts, const uint32_t* idx,
-                        uint32_t nh) {
-    if (nh <= 4) return multi_one<H, 4>(a, verts, idx, nh);
-    if (nh <= 8) return multi_one<H, 8>(a, verts, idx, nh);
-    return multi_one<H, 16>(a, verts, idx, nh);
 }
 
 }  // namespace
@@ -112,11 +109,11 @@ cudaError_t launch_multi(const LaunchArgs& a, int kind, const float* verts, cons
                          uint32_t nh) {
     if (nh < 1 || nh > 16) return cudaErrorInvalidValue;
     switch (kind) {
-        case 0: return multi_sized<IsectNone>(a, verts, idx, nh);
-        case 1: return multi_sized<IsectDefault>(a, verts, idx, nh);
-        case 2: return multi_sized<IsectAlphaTex>(a, verts, idx, nh);
-        case 3: return multi_sized<IsectProcAlpha>(a, verts, idx, nh);
-        case 4: return multi_sized<IsectCount>(a, verts, idx, nh);
+        case 0: return multi_one<IsectNone>(a, verts, idx, nh);
+        case 1: return multi_one<IsectDefault>(a, verts, idx, nh);
+        case 2: return multi_one<IsectAlphaTex>(a, verts, idx, nh);
+        case 3: return multi_one<IsectProcAlpha>(a, verts, idx, nh);
+        case 4: return multi_one<IsectCount>(a, verts, idx, nh);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -311,54 +311,45 @@ __device__ __forceinline__ bool hit_before(float t, uint32_t p, float t2, uint32
     return t < t2 || (t == t2 && p < p2);
 }
 
-// The running result of the multi-hit query: the first n (<= NT) accepted
-// hits in ascending (t, prim) order, kept as (t, prim) in registers (the
+// The running result of the multi-hit query: the first n accepted hits in
+// ascending (t, prim) order, kept as (t, prim) in this thread's columns of
+// shared memory (stride words apart, like the traversal stack; the
 // barycentrics are recomputed for the final entries).  (t, prim) mirror entry
 // n - 1, so the traversal's closest-hit bound is the multi-hit bound; with
-// n == 1 the query is the closest-hit query.  Entries at n and beyond are
-// scratch that take() may overwrite and nothing reads.
-template <int NT>
+// n == 1 the query is the closest-hit query.  An insertion shifts only the
+// entries the new hit passes, and hits tend to arrive front to back.
 struct MultiBest {
-    float tk[NT];
-    uint32_t pk[NT];
+    float* tk;
+    uint32_t* pk;
+    uint32_t stride, n;
     float t;
     uint32_t prim;
-    uint32_t n;
     __device__ __forceinline__ void init(float tmax) {
-#pragma unroll
-        for (int k = 0; k < NT; ++k) {
-            tk[k] = tmax;
-            pk[k] = kMiss;
+        for (uint32_t k = 0; k < n; ++k) {
+            tk[k * stride] = tmax;
+            pk[k * stride] = kMiss;
         }
         t = tmax;
         prim = kMiss;
     }
     // Insert a candidate that comes before entry n - 1 (the caller checked).
     __device__ __forceinline__ void take(float tc, float, float, uint32_t pc) {
-#pragma unroll
-        for (int k = NT - 1; k > 0; --k) {
-            if (hit_before(tc, pc, tk[k - 1], pk[k - 1])) {
-                tk[k] = tk[k - 1];
-                pk[k] = pk[k - 1];
-            } else if (hit_before(tc, pc, tk[k], pk[k])) {
-                tk[k] = tc;
-                pk[k] = pc;
-            }
+        uint32_t k = n - 1;
+        while (k > 0) {
+            const float tp = tk[(k - 1) * stride];
+            const uint32_t pp = pk[(k - 1) * stride];
+            if (!hit_before(tc, pc, tp, pp)) break;
+            tk[k * stride] = tp;
+            pk[k * stride] = pp;
+            --k;
         }
-        if (hit_before(tc, pc, tk[0], pk[0])) {
-            tk[0] = tc;
-            pk[0] = pc;
-        }
-#pragma unroll
-        for (int k = 0; k < NT; ++k)
-            if ((uint32_t)k + 1u == n) {
-                t = tk[k];
-                prim = pk[k];
-            }
+        tk[k * stride] = tc;
+        pk[k * stride] = pc;
+        t = tk[(n - 1) * stride];
+        prim = pk[(n - 1) * stride];
     }
     __device__ __forceinline__ void fail() {
-#pragma unroll
-        for (int k = 0; k < NT; ++k) pk[k] = kMiss;
+        for (uint32_t k = 0; k < n; ++k) pk[k * stride] = kMiss;
         prim = kMiss;
     }
 };
