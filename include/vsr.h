@@ -234,6 +234,59 @@ vsr_status vsr_trace_multi(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
                            uint32_t* counters, const vsr_trace_params* params,
                            vsr_stream stream);
 
+/* ------------------------------------------------------------- instancing */
+
+/*
+ * Instancing (Section 3.2: BVHs acting as compound primitives, where the
+ * BVH stores BVHs as primitives and the custom intersector is passed on to
+ * each BVH's own intersect).  An instance set is a top-level BVH whose leaves
+ * hold instances; instance i shows mesh inst_mesh[i] (a scene with its BVH
+ * loaded) through the world-to-object affine map W_i = world_to_object[12i ..
+ * 12i+12) (row-major 3 x 4: rows (r0 r1 r2 | t)).  Rays are taken to object
+ * space as o'_r = fmaf(W_r0, o.x, fmaf(W_r1, o.y, fmaf(W_r2, o.z, W_r3))),
+ * d'_r = fmaf(W_r0, d.x, fmaf(W_r1, d.y, W_r2 * d.z)) with (tmin, tmax)
+ * unchanged, so hit distances are in world units of the ray parameter.
+ *   meshes      host array [nmeshes] of scenes with BVHs, on one device
+ *   top_blob    a BVH blob over the instances' world-space boxes (primitive i
+ *               is instance i; see vsr_bvh_build_boxes).  Each box must
+ *               contain every world point whose object-space image lies in
+ *               the mesh, or rays through the uncovered part miss.
+ * The set copies the transforms and the meshes' device descriptors: the
+ * meshes must outlive it, and neither vsr_bvh_load nor vsr_scene_update may
+ * be called on them while it exists.
+ * Errors: VSR_ERR_ARG (null, out of range, non-finite transform), VSR_ERR_BLOB
+ * (invalid top-level blob or wrong instance count), VSR_ERR_STATE (a mesh
+ * without BVH), VSR_ERR_OOM, VSR_ERR_CUDA.
+ */
+typedef struct vsr_instances vsr_instances;
+vsr_status vsr_instances_create(vsr_scene* const* meshes, uint32_t nmeshes,
+                                const uint32_t* inst_mesh, const float* world_to_object,
+                                uint32_t ninst, const void* top_blob, size_t top_bytes,
+                                vsr_instances** out);
+vsr_status vsr_instances_destroy(vsr_instances* instances);
+
+/*
+ * Closest-hit or any-hit over an instance set with a static intersector: the
+ * top-level BVH is traversed while-while with the world-space ray (the same
+ * order rule as a mesh), and at each instance the mesh's own traversal runs
+ * with the object-space ray, continuing the running result.  Closest-hit
+ * ties go to the lower instance id, then the lower primitive id.  Counters
+ * (COUNT) include the top-level box tests.
+ *   hits      device vsr_hit [n]: prim_id is the mesh's primitive id
+ *   inst_ids  device uint32 [n] (VSR_MISS on a miss) or NULL
+ *   params    one ray per thread (persistent 0); image_width allowed
+ * Errors as vsr_trace.  Traversal errors of the top level go to the set's
+ * error word (vsr_instances_device_error), those inside a mesh to the mesh's.
+ */
+vsr_status vsr_trace_instances(vsr_instances* instances, const vsr_ray* rays, uint64_t n,
+                               const vsr_intersector* isect, int32_t query, vsr_hit* hits,
+                               uint32_t* inst_ids, uint32_t* counters,
+                               const vsr_trace_params* params, vsr_stream stream);
+
+/* Read and clear the instance set's device error word (synchronous; bits as
+ * vsr_get_device_error's 0 and 1). */
+vsr_status vsr_instances_device_error(vsr_instances* instances, uint32_t* word);
+
 /*
  * Measurement variant of vsr_trace with the static intersector: identical
  * hits, plus per-ray statistics stats device uint32 [n*4] = (box tests,

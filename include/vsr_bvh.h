@@ -85,7 +85,18 @@ int vsr_bvh_build(const float* verts, uint64_t nverts, const uint32_t* idx,
                   uint32_t ntri, const vsr_build_params* params, void** blob,
                   size_t* bytes);
 
-/* Release a blob returned by vsr_bvh_build. NULL is ignored. */
+/*
+ * The same builder over axis-aligned boxes (the primitives of a top-level
+ * BVH whose leaves hold instances, each a BVH of its own; Section 3.2 on
+ * BVHs acting as compound primitives).  Primitive i of the blob is box i.
+ *   boxes  host, float32 [n*6]: lo.xyz, hi.xyz per box, finite, lo <= hi
+ * Returns and ownership as vsr_bvh_build.
+ */
+int vsr_bvh_build_boxes(const float* boxes, uint32_t n, const vsr_build_params* params,
+                        void** blob, size_t* bytes);
+
+/* Release a blob returned by vsr_bvh_build or vsr_bvh_build_boxes. NULL is
+ * ignored. */
 void vsr_bvh_free(void* blob);
 
 /* Structural validation of a blob (magic, version, sizes, checksum, child and

@@ -17,6 +17,9 @@ Intersectors to the C++ Ray Tracing Template Library Visionaray"):
   library the paper extends, Section 1): the first N accepted hits in
   ascending (t, prim) order, over the list as the plain definition (collect,
   sort, keep N) or through the BVH traversal with an N-entry buffer.
+* ``trace_instances`` -- instancing (Section 3.2: BVHs as compound primitives
+  of a list or of a top-level BVH, the intersector passed on to each BVH's
+  own intersect), rays taken to object space by a world-to-object map.
 * intersector kinds follow Section 3.1 (default forwarding), Section 4
   (alpha-mask listing, procedural alpha, ``bvh_costs``).
 """
@@ -85,6 +88,9 @@ def _load():
                                       ctypes.c_uint64, P, P, ctypes.c_int]
         lib.orc_trace_multi.argtypes = [P, P, ctypes.c_uint64, P, ctypes.c_uint32, P,
                                         ctypes.c_uint64, P, P, ctypes.c_int]
+        lib.orc_trace_instances.argtypes = [P, P, P, ctypes.c_uint32, P, P, ctypes.c_uint32, P,
+                                            ctypes.c_uint64, P, ctypes.c_int, P, ctypes.c_uint64,
+                                            P, P, P, ctypes.c_int]
         lib.orc_intersect_triangle.argtypes = [P, P, P, P, P]
         lib.orc_intersect_aabb.argtypes = [P, P, P, ctypes.c_float]
         lib.orc_shadow_rays.argtypes = [P, P, ctypes.c_uint64, P, ctypes.c_float, P]
@@ -192,6 +198,46 @@ def trace_multi(scene, rays, nh: int, kind="default", blob=None, nthreads=None, 
         raise ValueError(f"oracle rejected its inputs (code {rc})")
     h = split_hits(hits)
     return {k: v.reshape(n, nh) for k, v in h.items()}, stats
+
+
+def trace_instances(meshes, inst_mesh, w2o, rays, kind="default", query="closest",
+                    top_blob=None, nthreads=None, **kw):
+    """Closest-hit / any-hit over instances.  meshes: list of (scene, blob);
+    inst_mesh uint32 [m]; w2o float32 [m, 12] world-to-object maps (row-major
+    3 x 4); top_blob None: the instances as a linear list, else the top-level
+    BVH over them.  Returns (hits, inst_ids, stats)."""
+    lib = _load()
+    handles = [_SceneHandle(sc) for sc, _ in meshes]
+    blobs = [np.ascontiguousarray(np.frombuffer(b, np.uint8) if not isinstance(b, np.ndarray)
+                                  else b) for _, b in meshes]
+    nm = len(meshes)
+    scene_ptrs = (ctypes.c_void_p * max(nm, 1))(*[ctypes.addressof(h.c) for h in handles])
+    blob_ptrs = (ctypes.c_void_p * max(nm, 1))(*[_ptr(b) for b in blobs])
+    blob_sizes = (ctypes.c_uint64 * max(nm, 1))(*[b.nbytes for b in blobs])
+    im = np.ascontiguousarray(inst_mesh, np.uint32).reshape(-1)
+    w = np.ascontiguousarray(w2o, np.float32).reshape(-1, 12)
+    assert w.shape[0] == im.shape[0]
+    rays = np.ascontiguousarray(rays, np.float32).reshape(-1, 8)
+    n = rays.shape[0]
+    hits = np.zeros((n, 4), np.float32)
+    ids = np.zeros(n, np.uint32)
+    stats = np.zeros((n, 4), np.uint32)
+    isect = _isect(kind, **kw)
+    if nthreads is None:
+        nthreads = len(os.sched_getaffinity(0))
+    top = None
+    if top_blob is not None:
+        top = np.ascontiguousarray(np.frombuffer(top_blob, np.uint8)
+                                   if not isinstance(top_blob, np.ndarray) else top_blob)
+    rc = lib.orc_trace_instances(scene_ptrs, blob_ptrs, blob_sizes, nm,
+                                 _ptr(im) if im.size else None, _ptr(w) if w.size else None,
+                                 im.shape[0], None if top is None else _ptr(top),
+                                 0 if top is None else top.nbytes, ctypes.byref(isect),
+                                 QUERY[query], _ptr(rays), n, _ptr(hits), _ptr(ids), _ptr(stats),
+                                 nthreads)
+    if rc != 0:
+        raise ValueError(f"oracle rejected its inputs (code {rc})")
+    return split_hits(hits), ids, stats
 
 
 def intersect_triangle(ray, v0, v1, v2):

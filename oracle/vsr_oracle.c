@@ -28,7 +28,15 @@
  *     definition (collect every accepted candidate, sort, keep N); over the
  *     BVH it is the closest-hit traversal with a sorted buffer of N entries
  *     whose last entry plays the role of the closest hit (closest-hit is the
- *     multi-hit query with N = 1).
+ *     multi-hit query with N = 1);
+ *   - instancing (Section 3.2: BVHs acting as compound primitives of a list
+ *     or of a top-level BVH, with the intersector passed on to each BVH's own
+ *     intersect): an instance is a mesh seen through a world-to-object affine
+ *     map W (row-major 3 x 4); the ray is taken to object space as
+ *     o'_r = fmaf(W_r0, o.x, fmaf(W_r1, o.y, fmaf(W_r2, o.z, W_r3))),
+ *     d'_r = fmaf(W_r0, d.x, fmaf(W_r1, d.y, W_r2 * d.z)), same (tmin, tmax),
+ *     so t is the same parameter in both spaces; closest-hit ties between
+ *     instances go to the lower instance id, then the lower primitive id.
  *
  * Rounding: compiled with -ffp-contract=off.  Every fused multiply-add is an
  * explicit fmaf(); every other product or sum is a separately rounded FP32
@@ -487,6 +495,176 @@ done:
 }
 
 /* ------------------------------------------------------------------ */
+/* Instancing: BVHs as compound primitives (Section 3.2)              */
+
+typedef struct {
+    float t, u, v;
+    uint32_t prim, inst;
+} orc_ihit;
+
+typedef struct {
+    const orc_scene* scene;
+    orc_bvh bvh;
+} orc_mesh;
+
+typedef struct {
+    const orc_mesh* meshes;
+    const uint32_t* inst_mesh; /* [ninst] */
+    const float* inst_w2o;     /* [ninst * 12] */
+    uint32_t ninst;
+    const orc_bvh* top;        /* NULL: the instances form a linear list */
+} orc_inst_set;
+
+/* (t, inst, prim) comes before hit e. */
+static int ihit_before(float t, uint32_t inst, uint32_t prim, const orc_ihit* e) {
+    if (t != e->t) return t < e->t;
+    return inst < e->inst || (inst == e->inst && prim < e->prim);
+}
+
+static void to_object(const float* w, const orc_ray* r, orc_ray* out) {
+    for (int k = 0; k < 3; ++k) {
+        const float* m = w + 4 * k;
+        out->o[k] = fmaf(m[0], r->o[0], fmaf(m[1], r->o[1], fmaf(m[2], r->o[2], m[3])));
+        out->d[k] = fmaf(m[0], r->d[0], fmaf(m[1], r->d[1], m[2] * r->d[2]));
+    }
+    out->tmin = r->tmin;
+    out->tmax = r->tmax;
+}
+
+/* One instance: its mesh's while-while traversal with the object-space ray,
+ * continuing the running result `best` (the intersector passed on to the
+ * mesh's own intersect).  Returns 1 when an any-hit query ends. */
+static int instance_query(const orc_mesh* m, const orc_isect* is, int query, uint32_t inst,
+                          const orc_ray* obj, orc_ihit* best, orc_stats* st) {
+    const orc_bvh* b = &m->bvh;
+    const orc_scene* s = m->scene;
+    if (b->num_prims == 0) return 0;
+    orc_ray_ctx c;
+    ray_setup(obj, &c);
+    st->boxes++;
+    if (!intersect_aabb(&c, b->nodes[0].lo, b->nodes[0].hi,
+                        query == ORC_CLOSEST ? best->t : obj->tmax))
+        return 0;
+    uint32_t stack[72];
+    int sp = 0;
+    uint32_t node = 0;
+    for (;;) {
+        while ((b->nodes[node].count_axis >> 2) == 0) {
+            const orc_node* nd = &b->nodes[node];
+            const uint32_t l = nd->left_or_first, r = l + 1;
+            const float far_t = (query == ORC_CLOSEST) ? best->t : obj->tmax;
+            st->boxes += 2;
+            const int hl = intersect_aabb(&c, b->nodes[l].lo, b->nodes[l].hi, far_t);
+            const int hr = intersect_aabb(&c, b->nodes[r].lo, b->nodes[r].hi, far_t);
+            if (hl && hr) {
+                const int neg = signbit(obj->d[nd->count_axis & 3u]) ? 1 : 0;
+                stack[sp++] = neg ? l : r;
+                node = neg ? r : l;
+            } else if (hl) {
+                node = l;
+            } else if (hr) {
+                node = r;
+            } else {
+                if (sp == 0) return 0;
+                node = stack[--sp];
+            }
+        }
+        const orc_node* lf = &b->nodes[node];
+        const uint32_t first = lf->left_or_first, cnt = lf->count_axis >> 2;
+        for (uint32_t k = 0; k < cnt; ++k) {
+            const uint32_t prim = b->order[first + k];
+            float v0[3], e1[3], e2[3], t, u, v;
+            tri_verts(s, prim, v0, e1, e2);
+            st->tris++;
+            const int g = intersect_triangle(&c.r, v0, e1, e2, &t, &u, &v);
+            if (g < 0) continue;
+            const int in_range = t > c.r.tmin && t < c.r.tmax;
+            if (in_range && (query == ORC_ANY || t <= best->t)) note_edge_tie(u, v, &st->flags);
+            if (g == 0 || !in_range) continue;
+            if (query == ORC_CLOSEST && !ihit_before(t, inst, prim, best)) continue;
+            st->cands++;
+            if (!intersector_accepts(s, is, prim, u, v, &st->flags)) continue;
+            best->t = t;
+            best->u = u;
+            best->v = v;
+            best->prim = prim;
+            best->inst = inst;
+            if (query == ORC_ANY) return 1;
+        }
+        if (sp == 0) return 0;
+        node = stack[--sp];
+    }
+}
+
+/* Closest-hit or any-hit over the instances: a linear list in id order, or
+ * the top-level BVH traversed while-while with the world-space ray (the same
+ * order rule; its leaves list instance ids). */
+static void inst_query(const orc_inst_set* set, const orc_isect* is, int query,
+                       const orc_ray* ray, orc_ihit* out, orc_stats* st) {
+    orc_ihit best = {ray->tmax, 0.0f, 0.0f, ORC_NONE, ORC_NONE};
+    memset(st, 0, sizeof(*st));
+    orc_ray obj;
+    if (!set->top) {
+        for (uint32_t i = 0; i < set->ninst; ++i) {
+            to_object(set->inst_w2o + 12ull * i, ray, &obj);
+            if (instance_query(&set->meshes[set->inst_mesh[i]], is, query, i, &obj, &best, st))
+                break;
+        }
+    } else if (set->top->num_prims > 0) {
+        const orc_bvh* b = set->top;
+        orc_ray_ctx c;
+        ray_setup(ray, &c);
+        st->boxes++;
+        if (!intersect_aabb(&c, b->nodes[0].lo, b->nodes[0].hi,
+                            query == ORC_CLOSEST ? best.t : ray->tmax))
+            goto done;
+        uint32_t stack[72];
+        int sp = 0;
+        uint32_t node = 0;
+        for (;;) {
+            while ((b->nodes[node].count_axis >> 2) == 0) {
+                const orc_node* nd = &b->nodes[node];
+                const uint32_t l = nd->left_or_first, r = l + 1;
+                const float far_t = (query == ORC_CLOSEST) ? best.t : ray->tmax;
+                st->boxes += 2;
+                const int hl = intersect_aabb(&c, b->nodes[l].lo, b->nodes[l].hi, far_t);
+                const int hr = intersect_aabb(&c, b->nodes[r].lo, b->nodes[r].hi, far_t);
+                if (hl && hr) {
+                    const int neg = signbit(ray->d[nd->count_axis & 3u]) ? 1 : 0;
+                    stack[sp++] = neg ? l : r;
+                    node = neg ? r : l;
+                } else if (hl) {
+                    node = l;
+                } else if (hr) {
+                    node = r;
+                } else {
+                    if (sp == 0) goto done;
+                    node = stack[--sp];
+                }
+            }
+            const orc_node* lf = &b->nodes[node];
+            const uint32_t first = lf->left_or_first, cnt = lf->count_axis >> 2;
+            for (uint32_t k = 0; k < cnt; ++k) {
+                const uint32_t inst = b->order[first + k];
+                to_object(set->inst_w2o + 12ull * inst, ray, &obj);
+                if (instance_query(&set->meshes[set->inst_mesh[inst]], is, query, inst, &obj,
+                                   &best, st))
+                    goto done;
+            }
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+done:
+    if (best.prim == ORC_NONE) {
+        best.t = INFINITY;
+        best.u = best.v = 0.0f;
+        best.inst = ORC_NONE;
+    }
+    *out = best;
+}
+
+/* ------------------------------------------------------------------ */
 /* Threaded drivers                                                    */
 
 typedef struct {
@@ -499,6 +677,8 @@ typedef struct {
     orc_hit* hits;
     orc_stats* stats;
     uint64_t begin, end;
+    const orc_inst_set* set; /* instance queries: hits [n], inst_ids [n] */
+    uint32_t* inst_ids;
 } orc_job;
 
 static void* run_job(void* arg) {
@@ -512,7 +692,15 @@ static void* run_job(void* arg) {
     for (uint64_t i = j->begin; i < j->end; ++i) {
         orc_stats* st = j->stats ? &j->stats[i] : &tmp;
         orc_hit* out = &j->hits[i * j->nh];
-        if (j->b)
+        if (j->set) {
+            orc_ihit h;
+            inst_query(j->set, j->is, j->query, &j->rays[i], &h, st);
+            out->t = h.t;
+            out->u = h.u;
+            out->v = h.v;
+            out->prim = h.prim;
+            if (j->inst_ids) j->inst_ids[i] = h.inst;
+        } else if (j->b)
             bvh_query(j->s, j->b, j->is, j->query, j->nh, &j->rays[i], out, st);
         else if (j->query == ORC_MULTI)
             list_multi(j->s, j->is, j->nh, &j->rays[i], out, scratch, st);
@@ -558,7 +746,7 @@ int orc_trace_list(const orc_scene* s, const orc_isect* is, int query, const flo
     if (!s || !is || (n && (!rays || !hits))) return -1;
     if (query != ORC_CLOSEST && query != ORC_ANY) return -1;
     orc_job j = {s, NULL, is, query, 1, (const orc_ray*)rays, (orc_hit*)hits,
-                 (orc_stats*)stats, 0, 0};
+                 (orc_stats*)stats, 0, 0, NULL, NULL};
     return run_threads(j, n, nthreads);
 }
 
@@ -572,7 +760,7 @@ int orc_trace_bvh(const orc_scene* s, const uint8_t* blob, uint64_t bytes,
     if (b.num_prims != s->ntri) return -6;
     if (query != ORC_CLOSEST && query != ORC_ANY) return -1;
     orc_job j = {s, &b, is, query, 1, (const orc_ray*)rays, (orc_hit*)hits,
-                 (orc_stats*)stats, 0, 0};
+                 (orc_stats*)stats, 0, 0, NULL, NULL};
     return run_threads(j, n, nthreads);
 }
 
@@ -589,8 +777,47 @@ int orc_trace_multi(const orc_scene* s, const uint8_t* blob, uint64_t bytes,
         if (b.num_prims != s->ntri) return -6;
     }
     orc_job j = {s, blob ? &b : NULL, is, ORC_MULTI, nh, (const orc_ray*)rays, (orc_hit*)hits,
-                 (orc_stats*)stats, 0, 0};
+                 (orc_stats*)stats, 0, 0, NULL, NULL};
     return run_threads(j, n, nthreads);
+}
+
+/* Closest-hit / any-hit over instances of meshes (each a scene with its own
+ * blob).  top_blob == NULL: the instances form a linear list; otherwise the
+ * top-level BVH over them (its primitive i is instance i).  hits [n*4],
+ * inst_ids [n] (0xFFFFFFFF on a miss), stats [n*4] or NULL. */
+int orc_trace_instances(const orc_scene* const* scenes, const uint8_t* const* blobs,
+                        const uint64_t* blob_bytes, uint32_t nmeshes, const uint32_t* inst_mesh,
+                        const float* inst_w2o, uint32_t ninst, const uint8_t* top_blob,
+                        uint64_t top_bytes, const orc_isect* is, int query, const float* rays,
+                        uint64_t n, float* hits, uint32_t* inst_ids, uint32_t* stats,
+                        int nthreads) {
+    if (!scenes || !blobs || !blob_bytes || !is || (ninst && (!inst_mesh || !inst_w2o)) ||
+        (n && (!rays || !hits)))
+        return -1;
+    if (query != ORC_CLOSEST && query != ORC_ANY) return -1;
+    orc_mesh* meshes = (orc_mesh*)calloc(nmeshes ? nmeshes : 1, sizeof(orc_mesh));
+    if (!meshes) return -7;
+    int rc = 0;
+    for (uint32_t m = 0; m < nmeshes && rc == 0; ++m) {
+        meshes[m].scene = scenes[m];
+        rc = parse_blob(blobs[m], blob_bytes[m], &meshes[m].bvh);
+        if (rc == 0 && meshes[m].bvh.num_prims != scenes[m]->ntri) rc = -6;
+    }
+    for (uint32_t i = 0; i < ninst && rc == 0; ++i)
+        if (inst_mesh[i] >= nmeshes) rc = -1;
+    orc_bvh top;
+    if (rc == 0 && top_blob) {
+        rc = parse_blob(top_blob, top_bytes, &top);
+        if (rc == 0 && top.num_prims != ninst) rc = -6;
+    }
+    if (rc == 0) {
+        orc_inst_set set = {meshes, inst_mesh, inst_w2o, ninst, top_blob ? &top : NULL};
+        orc_job j = {NULL, NULL, is, query, 1, (const orc_ray*)rays, (orc_hit*)hits,
+                     (orc_stats*)stats, 0, 0, &set, inst_ids};
+        rc = run_threads(j, n, nthreads);
+    }
+    free(meshes);
+    return rc;
 }
 
 /* Single triangle test, exposed for worked-example checks.  out: t,u,v;

@@ -1315,3 +1315,207 @@ extern "C" vsr_status vsr_trace_batch(vsr_scene* const* scenes, const vsr_ray* c
     }
     return vsr_batch_launch(b, stream);
 }
+
+// ---------------------------------------------------------------------------
+// Instancing: BVHs as compound primitives of a top-level BVH (Section 3.2).
+// The instance set snapshots the meshes' device descriptors; the meshes must
+// outlive it and keep their geometry and BVH while it exists.
+
+struct vsr_instances {
+    int device = 0;
+    uint32_t nmeshes = 0, ninst = 0;
+    DevScene* d_meshes = nullptr;
+    float4* d_inst = nullptr;
+    float4* d_nodes = nullptr;
+    uint32_t* d_order = nullptr;
+    uint32_t* d_err = nullptr;
+    InstDev dev{};
+    uint32_t stack_words = 1;
+};
+
+namespace {
+
+void free_instances(vsr_instances* x) {
+    dfree(x->d_meshes);
+    dfree(x->d_inst);
+    dfree(x->d_nodes);
+    dfree(x->d_order);
+    dfree(x->d_err);
+    delete x;
+}
+
+}  // namespace
+
+extern "C" vsr_status vsr_instances_create(vsr_scene* const* meshes, uint32_t nmeshes,
+                                           const uint32_t* inst_mesh,
+                                           const float* world_to_object, uint32_t ninst,
+                                           const void* top_blob, size_t top_bytes,
+                                           vsr_instances** out) {
+    g_err.clear();
+    if (!out) return fail(VSR_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!meshes || nmeshes < 1 || nmeshes > 65536)
+        return fail(VSR_ERR_ARG, "nmeshes must be in 1..65536 with a mesh array");
+    if (ninst > (1u << 28)) return fail(VSR_ERR_ARG, "more than 2^28 instances");
+    if (ninst && (!inst_mesh || !world_to_object))
+        return fail(VSR_ERR_ARG, "null instance arrays");
+    uint32_t mesh_depth = 1;
+    for (uint32_t m = 0; m < nmeshes; ++m) {
+        if (!meshes[m]) return fail(VSR_ERR_ARG, "mesh " + std::to_string(m) + " is null");
+        if (!meshes[m]->has_bvh)
+            return fail(VSR_ERR_STATE, "mesh " + std::to_string(m) + " has no BVH loaded");
+        if (meshes[m]->device != meshes[0]->device)
+            return fail(VSR_ERR_ARG, "meshes live on different devices");
+        mesh_depth = std::max(mesh_depth, meshes[m]->dev.stack_depth);
+    }
+    for (uint32_t i = 0; i < ninst; ++i) {
+        if (inst_mesh[i] >= nmeshes)
+            return fail(VSR_ERR_ARG, "instance " + std::to_string(i) + " names a missing mesh");
+        for (int k = 0; k < 12; ++k)
+            if (!std::isfinite(world_to_object[12ull * i + k]))
+                return fail(VSR_ERR_ARG, "instance " + std::to_string(i) +
+                                             " has a non-finite transform");
+    }
+    if (vsr_bvh_validate(top_blob, top_bytes) != 0)
+        return fail(VSR_ERR_BLOB, std::string("invalid top-level blob: ") + vsr_bvh_last_error());
+    uint32_t hdr[8];
+    std::memcpy(hdr, static_cast<const uint8_t*>(top_blob) + 8, sizeof(hdr));
+    const uint32_t num_nodes = hdr[2], num_prims = hdr[3], max_depth = hdr[4];
+    if (num_prims != ninst)
+        return fail(VSR_ERR_BLOB, "top-level BVH was built over a different number of instances");
+    const vsr_bvh_node* nodes =
+        reinterpret_cast<const vsr_bvh_node*>(static_cast<const uint8_t*>(top_blob) + 64);
+    const uint32_t* order = reinterpret_cast<const uint32_t*>(
+        static_cast<const uint8_t*>(top_blob) + 64 + 32ull * num_nodes);
+    DeviceGuard g(meshes[0]->device);
+    if (!g.ok) return fail(VSR_ERR_CUDA, "cannot select the meshes' device");
+    vsr_instances* x = new (std::nothrow) vsr_instances;
+    if (!x) return fail(VSR_ERR_OOM, "out of host memory");
+    x->device = meshes[0]->device;
+    x->nmeshes = nmeshes;
+    x->ninst = ninst;
+    std::vector<DevScene> descs(nmeshes);
+    for (uint32_t m = 0; m < nmeshes; ++m) descs[m] = meshes[m]->dev;
+    std::vector<float4> inst(4ull * std::max(ninst, 1u));
+    for (uint32_t i = 0; i < ninst; ++i) {
+        const float* w = world_to_object + 12ull * i;
+        for (int r = 0; r < 3; ++r)
+            inst[4ull * i + r] = make_float4(w[4 * r], w[4 * r + 1], w[4 * r + 2], w[4 * r + 3]);
+        float mesh_bits;
+        std::memcpy(&mesh_bits, &inst_mesh[i], sizeof(mesh_bits));
+        inst[4ull * i + 3] = make_float4(mesh_bits, 0.0f, 0.0f, 0.0f);
+    }
+    std::vector<float4> hn(2ull * num_nodes);
+    for (uint32_t i = 0; i < num_nodes; ++i) {
+        const vsr_bvh_node& nd = nodes[i];
+        const uint32_t ref = (i == 1) ? 0u : node_ref(nd);
+        float ref_bits;
+        std::memcpy(&ref_bits, &ref, sizeof(ref_bits));
+        hn[2ull * i] = make_float4(nd.lo[0], nd.lo[1], nd.lo[2], ref_bits);
+        hn[2ull * i + 1] = make_float4(nd.hi[0], nd.hi[1], nd.hi[2], 0.0f);
+    }
+    cudaError_t e;
+    if ((e = dmalloc(&x->d_meshes, (size_t)nmeshes)) != cudaSuccess ||
+        (e = dmalloc(&x->d_inst, inst.size())) != cudaSuccess ||
+        (e = dmalloc(&x->d_nodes, hn.size())) != cudaSuccess ||
+        (e = dmalloc(&x->d_order, (size_t)std::max(ninst, 1u))) != cudaSuccess ||
+        (e = dmalloc(&x->d_err, 1)) != cudaSuccess) {
+        free_instances(x);
+        return e == cudaErrorMemoryAllocation ? fail(VSR_ERR_OOM, "instance set allocation")
+                                              : cuda_fail(e, "instance set allocation");
+    }
+    if ((e = cudaMemcpy(x->d_meshes, descs.data(), sizeof(DevScene) * nmeshes,
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(x->d_inst, inst.data(), sizeof(float4) * inst.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(x->d_nodes, hn.data(), sizeof(float4) * hn.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ninst && (e = cudaMemcpy(x->d_order, order, 4ull * ninst, cudaMemcpyHostToDevice)) !=
+                      cudaSuccess) ||
+        (e = cudaMemset(x->d_err, 0, sizeof(uint32_t))) != cudaSuccess) {
+        free_instances(x);
+        return cuda_fail(e, "instance set upload");
+    }
+    InstDev& d = x->dev;
+    d.nodes = x->d_nodes;
+    d.order = x->d_order;
+    d.inst = x->d_inst;
+    d.meshes = x->d_meshes;
+    d.err = x->d_err;
+    d.ninst = ninst;
+    d.root_ref = node_ref(nodes[0]);
+    d.top_depth = max_depth > 0 ? max_depth : 1u;
+    d.max_leaves = num_nodes + 2u;
+    d.root_a = make_float4(nodes[0].lo[0], nodes[0].lo[1], nodes[0].lo[2], 0.0f);
+    d.root_b = make_float4(nodes[0].hi[0], nodes[0].hi[1], nodes[0].hi[2], 0.0f);
+    x->stack_words = d.top_depth + mesh_depth;
+    *out = x;
+    return VSR_OK;
+}
+
+extern "C" vsr_status vsr_instances_destroy(vsr_instances* x) {
+    g_err.clear();
+    if (!x) return VSR_OK;
+    DeviceGuard g(x->device);
+    free_instances(x);
+    return VSR_OK;
+}
+
+extern "C" vsr_status vsr_trace_instances(vsr_instances* x, const vsr_ray* rays, uint64_t n,
+                                          const vsr_intersector* is, int32_t query,
+                                          vsr_hit* hits, uint32_t* inst_ids, uint32_t* counters,
+                                          const vsr_trace_params* p, vsr_stream stream) {
+    g_err.clear();
+    if (!x) return fail(VSR_ERR_ARG, "instance set is null");
+    vsr_status st = validate_isect(is, query);
+    if (st != VSR_OK) return st;
+    if (is->dispatch != VSR_DISPATCH_STATIC)
+        return fail(VSR_ERR_ARG, "instanced traces use static dispatch only");
+    vsr_trace_params prm{128u, 0u, 16u, 0u, 0u};
+    if (p) prm = *p;
+    if (prm.block_size < 32 || prm.block_size > 256 || prm.block_size % 32)
+        return fail(VSR_ERR_ARG, "block_size must be a multiple of 32 in 32..256");
+    if (prm.persistent) return fail(VSR_ERR_ARG, "instanced traces use one ray per thread");
+    if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull)
+        return fail(VSR_ERR_ARG, "too many rays for one launch");
+    InstLaunch L{};
+    st = make_map(n, prm.image_width, L.map);
+    if (st != VSR_OK) return st;
+    if (n == 0) return VSR_OK;
+    if ((st = check_dev(rays, x->device, "rays", 16, n * sizeof(vsr_ray))) != VSR_OK ||
+        (st = check_dev(hits, x->device, "hits", 16, n * sizeof(vsr_hit))) != VSR_OK)
+        return st;
+    if (inst_ids && (st = check_dev(inst_ids, x->device, "inst_ids", 4, n * 4)) != VSR_OK)
+        return st;
+    if (counters) {
+        if (is->kind != VSR_ISECT_COUNT)
+            return fail(VSR_ERR_ARG, "counters are written by the COUNT intersector only");
+        if ((st = check_dev(counters, x->device, "counters", 8, n * 8)) != VSR_OK) return st;
+    }
+    L.is = x->dev;
+    L.ip.cutoff_u8 = is->alpha_cutoff_u8;
+    L.ip.cutoff_f = is->alpha_cutoff_f;
+    L.ip.freq = is->proc_freq;
+    L.ip.kind = (uint32_t)is->kind;
+    L.rays = reinterpret_cast<const float4*>(rays);
+    L.hits = reinterpret_cast<float4*>(hits);
+    L.inst_ids = inst_ids;
+    L.counters = reinterpret_cast<uint2*>(counters);
+    L.block = prm.block_size;
+    L.stack_words = x->stack_words;
+    L.stream = reinterpret_cast<cudaStream_t>(stream);
+    DeviceGuard g(x->device);
+    cudaError_t e = launch_instances(L, is->kind, query);
+    if (e != cudaSuccess) return cuda_fail(e, "instanced trace launch");
+    return VSR_OK;
+}
+
+extern "C" vsr_status vsr_instances_device_error(vsr_instances* x, uint32_t* word) {
+    g_err.clear();
+    if (!x || !word) return fail(VSR_ERR_ARG, "null argument");
+    DeviceGuard g(x->device);
+    VSR_CUDA(cudaDeviceSynchronize(), "synchronise");
+    VSR_CUDA(cudaMemcpy(word, x->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read error word");
+    VSR_CUDA(cudaMemset(x->d_err, 0, sizeof(uint32_t)), "clear error word");
+    return VSR_OK;
+}

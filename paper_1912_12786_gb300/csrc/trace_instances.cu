@@ -1,0 +1,190 @@
+// Instancing: BVHs acting as compound primitives (Section 3.2).  The
+// visibility query runs over a top-level BVH whose leaves hold instances; an
+// instance is a mesh (a scene with its own BVH) seen through a world-to-object
+// affine map, and the custom intersector is passed on to the mesh's own
+// traversal, where it replaces both calls to intersect exactly as for a
+// single mesh.  Closest-hit ties between instances go to the lower instance
+// id, then the lower primitive id.
+//
+// One ray per thread.  The top-level while-while loop uses the bottom of the
+// thread's shared-memory stack; a mesh traversal runs on the stack above the
+// top-level entries, continuing the running result.
+#include "vsr_internal.h"
+
+namespace vsr {
+
+namespace {
+
+// Running result across instances, in the interface the mesh traversal
+// expects (see Best): init() leaves the result alone because it spans
+// instances (reset() starts a ray), before() orders by (t, instance, prim) and
+// take() records the current instance.
+struct InstBest {
+    float t, u, v;
+    uint32_t prim, inst, cur;
+    bool failed;
+    __device__ __forceinline__ void reset(float tmax) {
+        t = tmax;
+        u = 0.0f;
+        v = 0.0f;
+        prim = kMiss;
+        inst = kMiss;
+        failed = false;
+    }
+    __device__ __forceinline__ void init(float) {}
+    __device__ __forceinline__ bool before(float tc, uint32_t pc) const {
+        return tc < t || (tc == t && (cur < inst || (cur == inst && pc < prim)));
+    }
+    __device__ __forceinline__ void take(float tc, float uc, float vc, uint32_t pc) {
+        t = tc;
+        u = uc;
+        v = vc;
+        prim = pc;
+        inst = cur;
+    }
+    __device__ __forceinline__ void fail() {
+        prim = kMiss;
+        failed = true;
+    }
+};
+
+// Ray in the instance's object space: o' = W (o, 1), d' = W (d, 0) with the
+// rounding order fixed (rows of W in w0..w2, translation in .w); the interval
+// is unchanged, so t is the same parameter in both spaces.
+__device__ __forceinline__ Ray to_object(const float4 ra, const float4 rb, const float4 w0,
+                                         const float4 w1, const float4 w2) {
+    const float4 o = make_float4(
+        __fmaf_rn(w0.x, ra.x, __fmaf_rn(w0.y, ra.y, __fmaf_rn(w0.z, ra.z, w0.w))),
+        __fmaf_rn(w1.x, ra.x, __fmaf_rn(w1.y, ra.y, __fmaf_rn(w1.z, ra.z, w1.w))),
+        __fmaf_rn(w2.x, ra.x, __fmaf_rn(w2.y, ra.y, __fmaf_rn(w2.z, ra.z, w2.w))), ra.w);
+    const float4 d = make_float4(
+        __fmaf_rn(w0.x, rb.x, __fmaf_rn(w0.y, rb.y, __fmul_rn(w0.z, rb.z))),
+        __fmaf_rn(w1.x, rb.x, __fmaf_rn(w1.y, rb.y, __fmul_rn(w1.z, rb.z))),
+        __fmaf_rn(w2.x, rb.x, __fmaf_rn(w2.y, rb.y, __fmul_rn(w2.z, rb.z))), rb.w);
+    return make_ray(o, d);
+}
+
+template <int Q, class H>
+__global__ void __launch_bounds__(256) k_trace_inst(InstDev is, IsectParams ip,
+                                                    const float4* __restrict__ rays, RayMap map,
+                                                    float4* __restrict__ hits,
+                                                    uint32_t* __restrict__ inst_ids,
+                                                    uint2* __restrict__ counters) {
+    extern __shared__ uint32_t s_stack[];
+    const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= map.threads) return;
+    const unsigned long long i = ray_of_thread(g, map);
+    if (i >= map.n) return;
+    const float4 ra = VSR_LDG(rays + 2 * i), rb = VSR_LDG(rays + 2 * i + 1);
+    const Ray r = make_ray(ra, rb);
+    uint32_t* stack = s_stack + threadIdx.x;
+    const uint32_t stride = blockDim.x;
+    H h;
+    InstBest best;
+    best.reset(r.tmax);
+    Stats st;
+    if (is.ninst > 0) {
+        h.box();
+        if (box_hit(r, is.root_a, is.root_b, Q == kClosest ? best.t : r.tmax)) {
+            uint32_t ref = is.root_ref, sp = 0, leaves = 0;
+            for (;;) {
+                // descent ends by construction (children follow their parent)
+                while (!(ref & kLeafBit)) {
+                    const float4* p = is.nodes + 4ull * (ref >> 2);
+                    const float4 la = VSR_LDG(p), lb = VSR_LDG(p + 1), qa = VSR_LDG(p + 2),
+                                 qb = VSR_LDG(p + 3);
+                    const float tfar = (Q == kClosest) ? best.t : r.tmax;
+                    h.box();
+                    h.box();
+                    const bool hl = box_hit(r, la, lb, tfar);
+                    const bool hr = box_hit(r, qa, qb, tfar);
+                    const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(qa.w);
+                    if (hl && hr) {
+                        const bool neg = (r.negmask >> (ref & 3u)) & 1u;
+                        if (sp >= is.top_depth) {  // unreachable for a validated blob
+                            atomicOr(is.err, kErrStack);
+                            best.fail();
+                            goto done;
+                        }
+                        stack[sp * stride] = neg ? rl : rr;
+                        ++sp;
+                        ref = neg ? rr : rl;
+                    } else if (hl) {
+                        ref = rl;
+                    } else if (hr) {
+                        ref = rr;
+                    } else {
+                        if (sp == 0) goto done;
+                        --sp;
+                        ref = stack[sp * stride];
+                    }
+                }
+                if (++leaves > is.max_leaves) {  // unreachable for a validated blob
+                    atomicOr(is.err, kErrSteps);
+                    best.fail();
+                    goto done;
+                }
+                {
+                    const uint32_t first = (ref >> 3) & 0x0FFFFFFFu, cnt = (ref & 7u) + 1u;
+                    for (uint32_t k = 0; k < cnt; ++k) {
+                        const uint32_t id = VSR_LDG(is.order + first + k);
+                        const float4* w = is.inst + 4ull * id;
+                        const Ray ro = to_object(ra, rb, VSR_LDG(w), VSR_LDG(w + 1), VSR_LDG(w + 2));
+                        const DevScene& msc = is.meshes[__float_as_uint(VSR_LDG(w + 3).x)];
+                        best.cur = id;
+                        traverse_body<Q, H, false>(msc, ip, ro, h, best, st, stack + sp * stride,
+                                                   stride);
+                        if (best.failed || (Q == kAny && best.prim != kMiss)) goto done;
+                    }
+                }
+                if (sp == 0) break;
+                --sp;
+                ref = stack[sp * stride];
+            }
+        }
+    }
+done:
+    if (best.prim == kMiss) {
+        best.t = __int_as_float(0x7f800000);
+        best.u = 0.0f;
+        best.v = 0.0f;
+        best.inst = kMiss;
+    }
+    hits[i] = make_float4(best.t, best.u, best.v, __uint_as_float(best.prim));
+    if (inst_ids) inst_ids[i] = best.inst;
+    if (H::kCounts && counters) counters[i] = h.counters();
+}
+
+template <int Q, class H>
+cudaError_t inst_one(const InstLaunch& L) {
+    const size_t smem = (size_t)L.stack_words * L.block * sizeof(uint32_t);
+    auto k = k_trace_inst<Q, H>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned long long grid = (L.map.threads + L.block - 1) / L.block;
+    k<<<(unsigned)grid, L.block, smem, L.stream>>>(L.is, L.ip, L.rays, L.map, L.hits, L.inst_ids,
+                                                   L.counters);
+    return cudaGetLastError();
+}
+
+template <int Q>
+cudaError_t inst_kind(const InstLaunch& L, int kind) {
+    switch (kind) {
+        case 0: return inst_one<Q, IsectNone>(L);
+        case 1: return inst_one<Q, IsectDefault>(L);
+        case 2: return inst_one<Q, IsectAlphaTex>(L);
+        case 3: return inst_one<Q, IsectProcAlpha>(L);
+        case 4: return inst_one<Q, IsectCount>(L);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_instances(const InstLaunch& L, int kind, int query) {
+    return query == kClosest ? inst_kind<kClosest>(L, kind) : inst_kind<kAny>(L, kind);
+}
+
+}  // namespace vsr

@@ -286,8 +286,14 @@ struct Stats {
     uint32_t boxes = 0, tris = 0, cands = 0, texs = 0;
 };
 
+// (t, prim) comes before (t2, prim2) in the closest-hit / multi-hit order.
+__device__ __forceinline__ bool hit_before(float t, uint32_t p, float t2, uint32_t p2) {
+    return t < t2 || (t == t2 && p < p2);
+}
+
 // The running result of the closest-hit and any-hit queries.  The traversal
-// bounds its search by (t, prim) and hands every accepted candidate to take().
+// bounds its search by t, asks before() whether a candidate would improve the
+// result and hands every accepted candidate to take().
 struct Best {
     float t, u, v;
     uint32_t prim;
@@ -303,13 +309,11 @@ struct Best {
         v = vc;
         prim = pc;
     }
+    __device__ __forceinline__ bool before(float tc, uint32_t pc) const {
+        return hit_before(tc, pc, t, prim);
+    }
     __device__ __forceinline__ void fail() { prim = kMiss; }
 };
-
-// (t, prim) comes before (t2, prim2) in the closest-hit / multi-hit order.
-__device__ __forceinline__ bool hit_before(float t, uint32_t p, float t2, uint32_t p2) {
-    return t < t2 || (t == t2 && p < p2);
-}
 
 // The running result of the multi-hit query: the first n accepted hits in
 // ascending (t, prim) order, kept as (t, prim) in this thread's columns of
@@ -347,6 +351,9 @@ struct MultiBest {
         pk[k * stride] = pc;
         t = tk[(n - 1) * stride];
         prim = pk[(n - 1) * stride];
+    }
+    __device__ __forceinline__ bool before(float tc, uint32_t pc) const {
+        return hit_before(tc, pc, t, prim);
     }
     __device__ __forceinline__ void fail() {
         for (uint32_t k = 0; k < n; ++k) pk[k * stride] = kMiss;
@@ -425,7 +432,7 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
                 if (!geo || !(t > r.tmin) || !(t < r.tmax)) continue;
                 const uint32_t prim = __float_as_uint(a.w);
                 if (Q == kClosest) {
-                    if (!hit_before(t, prim, best.t, best.prim)) continue;
+                    if (!best.before(t, prim)) continue;
                 }
                 if (STATS) {
                     st.cands++;
@@ -530,7 +537,7 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
         if (!geo || !(t > r.tmin) || !(t < r.tmax)) continue;
         const uint32_t prim = __float_as_uint(a.w);
         if (Q == kClosest) {
-            if (!hit_before(t, prim, best.t, best.prim)) continue;
+            if (!best.before(t, prim)) continue;
         }
         if (STATS) {
             st.cands++;

@@ -50,6 +50,32 @@ cudaError_t launch_multi(const LaunchArgs& a, int kind, const float* verts, cons
 // (0 if none), cleared after reading.
 cudaError_t multi_align_error(unsigned* line);
 
+// Instancing (trace_instances.cu): a top-level BVH whose leaves hold
+// instances of meshes, each seen through a world-to-object affine map.
+struct InstDev {
+    const float4* nodes;     // top-level nodes, device layout as a mesh's
+    const uint32_t* order;   // leaf slot -> instance id
+    const float4* inst;      // 4 x float4 per instance: rows of W, {mesh id bits, 0, 0, 0}
+    const DevScene* meshes;  // descriptors of the meshes (device copies)
+    uint32_t* err;           // the instance set's device error word
+    uint32_t ninst, root_ref, top_depth, max_leaves;
+    float4 root_a, root_b;   // top-level root box
+};
+
+struct InstLaunch {
+    InstDev is;
+    IsectParams ip;
+    const float4* rays;
+    RayMap map;
+    float4* hits;
+    uint32_t* inst_ids;  // may be null
+    uint2* counters;     // COUNT intersector, may be null
+    uint32_t block;
+    uint32_t stack_words;  // top-level depth + deepest mesh
+    cudaStream_t stream;
+};
+cudaError_t launch_instances(const InstLaunch& L, int kind, int query);
+
 // Closest-hit render with diffuse shading, and its adjoint (render.cu).
 cudaError_t launch_render(const LaunchArgs& a, int kind, const ShadeDev& sh, const float* verts,
                           const uint32_t* idx, float* image, float4* hits);

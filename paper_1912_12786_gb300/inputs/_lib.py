@@ -50,6 +50,8 @@ def lib():
         L.vsr_bvh_build.argtypes = [P, ctypes.c_uint64, P, ctypes.c_uint32, P,
                                     ctypes.POINTER(ctypes.c_void_p),
                                     ctypes.POINTER(ctypes.c_size_t)]
+        L.vsr_bvh_build_boxes.argtypes = [P, ctypes.c_uint32, P, ctypes.POINTER(ctypes.c_void_p),
+                                          ctypes.POINTER(ctypes.c_size_t)]
         L.vsr_bvh_free.argtypes = [P]
         L.vsr_bvh_free.restype = None
         L.vsr_bvh_validate.argtypes = [P, ctypes.c_size_t]
@@ -78,6 +80,26 @@ def bvh_build(verts: np.ndarray, idx: np.ndarray | None, leaf_max: int = 4,
     nbytes = ctypes.c_size_t()
     rc = L.vsr_bvh_build(verts.ctypes.data, verts.shape[0], ip, ntri, ctypes.byref(p),
                          ctypes.byref(out), ctypes.byref(nbytes))
+    if rc != 0:
+        raise ValueError(L.vsr_bvh_last_error().decode())
+    try:
+        blob = np.frombuffer(ctypes.string_at(out.value, nbytes.value), np.uint8).copy()
+    finally:
+        L.vsr_bvh_free(out)
+    return blob
+
+
+def bvh_build_boxes(boxes: np.ndarray, leaf_max: int = 4, bins: int = 32,
+                    traversal_cost: float = 1.0) -> np.ndarray:
+    """Binned-SAH BVH over boxes float32 [n, 6] (lo.xyz, hi.xyz); primitive i
+    of the returned blob is box i."""
+    L = lib()
+    boxes = np.ascontiguousarray(boxes, np.float32).reshape(-1, 6)
+    p = BuildParams(leaf_max, bins, traversal_cost)
+    out = ctypes.c_void_p()
+    nbytes = ctypes.c_size_t()
+    rc = L.vsr_bvh_build_boxes(boxes.ctypes.data if boxes.size else None, boxes.shape[0],
+                               ctypes.byref(p), ctypes.byref(out), ctypes.byref(nbytes))
     if rc != 0:
         raise ValueError(L.vsr_bvh_last_error().decode())
     try:

@@ -389,6 +389,41 @@ int vsr_bvh_build(const float* verts, uint64_t nverts, const uint32_t* idx,
     return b.serialise(blob, bytes);
 }
 
+int vsr_bvh_build_boxes(const float* boxes, uint32_t n, const vsr_build_params* params,
+                        void** blob, size_t* bytes) {
+    g_bvh_err.clear();
+    if (!blob || !bytes) return bvh_fail("vsr_bvh_build_boxes: null output pointer");
+    *blob = nullptr;
+    *bytes = 0;
+    if (n > 0 && !boxes) return bvh_fail("vsr_bvh_build_boxes: null boxes");
+    if (n > (1u << 28)) return bvh_fail("vsr_bvh_build_boxes: more than 2^28 boxes");
+    vsr_build_params p{4u, 32u, 1.0f};
+    if (params) p = *params;
+    if (p.leaf_max < 1 || p.leaf_max > VSR_BVH_MAX_LEAF)
+        return bvh_fail("vsr_bvh_build_boxes: leaf_max must be in 1..8");
+    if (p.bins < 4 || p.bins > 256) return bvh_fail("vsr_bvh_build_boxes: bins must be in 4..256");
+    if (!(p.traversal_cost >= 0.0f) || !std::isfinite(p.traversal_cost))
+        return bvh_fail("vsr_bvh_build_boxes: traversal_cost must be finite and >= 0");
+    std::vector<Ref> refs(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        Ref& r = refs[i];
+        for (int a = 0; a < 3; ++a) {
+            r.lo[a] = boxes[6ull * i + a];
+            r.hi[a] = boxes[6ull * i + 3 + a];
+            if (!std::isfinite(r.lo[a]) || !std::isfinite(r.hi[a]) || r.lo[a] > r.hi[a])
+                return bvh_fail("vsr_bvh_build_boxes: box " + std::to_string(i) +
+                                " is not finite with lo <= hi");
+            r.c[a] = 0.5f * r.lo[a] + 0.5f * r.hi[a];
+        }
+        r.prim = i;
+    }
+    Builder b(std::move(refs), p);
+    b.run();
+    if (b.max_depth() > VSR_BVH_MAX_DEPTH)
+        return bvh_fail("vsr_bvh_build_boxes: depth limit exceeded");
+    return b.serialise(blob, bytes);
+}
+
 int vsr_bvh_validate(const void* blob, size_t bytes) {
     g_bvh_err.clear();
     if (!blob) return bvh_fail("blob: null pointer");

@@ -265,6 +265,122 @@ def billboard_forest(seed: int = SEED_BASE + 1, n_quads: int = 500_000,
     return scene, rays
 
 
+# ---------------------------------------------------------------------------
+# instancing workloads: meshes placed by affine maps, a top-level BVH over
+# the instances' world boxes
+
+
+@dataclass
+class InstanceSet:
+    name: str
+    meshes: list          # Scene per mesh
+    blobs: list           # BVH blob per mesh
+    inst_mesh: np.ndarray  # uint32 [m]
+    o2w: np.ndarray       # float64 [m, 3, 4] object-to-world placement
+    w2o: np.ndarray       # float32 [m, 12] world-to-object map the traversal applies
+    boxes: np.ndarray     # float32 [m, 6] world boxes (lo.xyz, hi.xyz)
+    top: np.ndarray       # BVH blob over the boxes (primitive i = instance i)
+
+
+def _place(rot, scale, trans):
+    """Object-to-world map x -> scale * rot @ x + trans as a 3 x 4 matrix."""
+    m = np.zeros((3, 4))
+    m[:, :3] = scale * np.asarray(rot, np.float64)
+    m[:, 3] = trans
+    return m
+
+
+def _rot_y(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+def make_instance_set(name, meshes, inst_mesh, o2w) -> InstanceSet:
+    """Inverse maps (float64, rounded to float32) and world boxes: the mesh's
+    box corners mapped to world space, padded by 1e-5 of the box size (the
+    traversal applies the float32 inverse) and rounded outward to float32."""
+    inst_mesh = np.asarray(inst_mesh, np.uint32)
+    o2w = np.asarray(o2w, np.float64).reshape(-1, 3, 4)
+    blobs = [m.bvh() for m in meshes]
+    w2o = np.zeros((len(o2w), 12), np.float32)
+    boxes = np.zeros((len(o2w), 6), np.float32)
+    obox = []
+    for m in meshes:
+        v = m.verts[np.asarray(m.idx).reshape(-1)].astype(np.float64)
+        obox.append((v.min(0), v.max(0)))
+    for i, (mid, a) in enumerate(zip(inst_mesh, o2w)):
+        inv = np.linalg.inv(np.vstack([a, [0, 0, 0, 1]]))[:3]
+        w2o[i] = inv.reshape(-1).astype(np.float32)
+        lo, hi = obox[mid]
+        corners = np.array([[x, y, z] for x in (lo[0], hi[0]) for y in (lo[1], hi[1])
+                            for z in (lo[2], hi[2])])
+        wc = corners @ a[:, :3].T + a[:, 3]
+        wlo, whi = wc.min(0), wc.max(0)
+        pad = 1e-5 * max(float(np.linalg.norm(whi - wlo)), 1.0)
+        boxes[i, :3] = np.nextafter((wlo - pad).astype(np.float32), np.float32(-np.inf))
+        boxes[i, 3:] = np.nextafter((whi + pad).astype(np.float32), np.float32(np.inf))
+    return InstanceSet(name, list(meshes), blobs, inst_mesh, o2w, w2o, boxes,
+                       _lib.bvh_build_boxes(boxes))
+
+
+def instanced_small(seed: int = SEED_BASE + 7, n_inst: int = 7):
+    """The small quad scene and a unit quad (u8 disc alpha) placed n_inst
+    times by random rotations (uniform on SO(3)), scales U[0.5, 1.5] and
+    translations around (0.5, 0.5, 0.5); instance 0 is the small scene
+    unmoved.  Rays: the small scene's 256 x 256 camera."""
+    rng = np.random.default_rng(seed)
+    quads, rays = small_quads()
+    unit = quad_grid_scene(disc_alpha_u8(256, 0.4))
+    o2w = [_place(np.eye(3), 1.0, np.zeros(3))]
+    mesh = [0]
+    for k in range(1, n_inst):
+        q = rng.standard_normal(4)
+        q /= np.linalg.norm(q)
+        w, x, y, z = q
+        rot = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+        scale = rng.uniform(0.5, 1.5)
+        centre = np.array([0.5, 0.5, 0.5]) + rng.uniform(-0.7, 0.7, 3)
+        m = k % 2
+        ocentre = np.array([0.5, 0.5, 0.5]) if m == 0 else np.array([0.5, 0.5, 0.0])
+        o2w.append(_place(rot, scale, centre - scale * rot @ ocentre))
+        mesh.append(m)
+    return make_instance_set("instanced_small", [quads, unit], mesh, o2w), rays
+
+
+def instanced_forest(seed: int = SEED_BASE + 6, grid: int = 8, extent: float = 100.0,
+                     width: int = 1920, height: int = 1080, tex_size: int = 1024):
+    """The billboard forest built by instancing: one tile of extent/grid
+    squared with 500,000/grid^2 billboards (the forest's density and
+    textures, without ground) placed grid x grid times, each turned about its
+    vertical axis by U[0, 2 pi), plus the 100 x 100 ground as a mesh of its
+    own (instance 0, unmoved).  The same camera and frame as the forest."""
+    rng = np.random.default_rng(seed)
+    cell = extent / grid
+    tile, _ = billboard_forest(seed=seed, n_quads=int(500_000 / grid ** 2), extent=cell,
+                               width=8, height=8, tex_size=tex_size)
+    tile = Scene("forest_tile", tile.verts, tile.idx[2:], tile.uvs[2:], tile.geom_id[2:],
+                 tile.textures, tile.meta)
+    g = np.array([[[0, 0, 0], [extent, 0, 0], [extent, 0, extent], [0, 0, extent]]], np.float64)
+    gv, gi, guv = _quads_to_tris(g)
+    ground = Scene("ground", gv, gi, guv, np.full(2, NONE, np.uint32), [])
+    o2w = [_place(np.eye(3), 1.0, np.zeros(3))]
+    mesh = [1]
+    tc = np.array([0.5 * cell, 0.0, 0.5 * cell])
+    for a in range(grid):
+        for b in range(grid):
+            rot = _rot_y(rng.uniform(0.0, 2 * math.pi))
+            centre = np.array([(a + 0.5) * cell, 0.0, (b + 0.5) * cell])
+            o2w.append(_place(rot, 1.0, centre - rot @ tc))
+            mesh.append(0)
+    inst = make_instance_set("instanced_forest", [tile, ground], mesh, o2w)
+    s = extent / 100.0
+    rays = pinhole_rays((50 * s, 1.7, -2 * s), (50 * s, 1.0, 50 * s), (0, 1, 0), 60.0,
+                        width, height)
+    return inst, rays
+
+
 LIGHT_DIR = np.array([0.3, 1.0, 0.2], np.float64) / np.linalg.norm([0.3, 1.0, 0.2])
 
 

@@ -76,6 +76,12 @@ _SIGS = {
     "vsr_trace": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P], ctypes.c_int),
     "vsr_trace_stats": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "vsr_trace_multi": ([P, P, ctypes.c_uint64, P, ctypes.c_uint32, P, P, P, P], ctypes.c_int),
+    "vsr_instances_create": ([P, ctypes.c_uint32, P, P, ctypes.c_uint32, P, ctypes.c_size_t,
+                              ctypes.POINTER(P)], ctypes.c_int),
+    "vsr_instances_destroy": ([P], ctypes.c_int),
+    "vsr_trace_instances": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P, P],
+                            ctypes.c_int),
+    "vsr_instances_device_error": ([P, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "vsr_trace_persistent_noalloc": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P],
                                      ctypes.c_int),
     "vsr_batch_create": ([P, P, P, P, ctypes.c_uint32, P, ctypes.c_int32, P, ctypes.POINTER(P)],
@@ -233,6 +239,57 @@ def vsr_trace_multi(scene: Scene, rays, isect: vsr_intersector, max_hits: int, h
     _check(lib().vsr_trace_multi(scene.handle, _ptr(rays), n, ctypes.byref(isect), int(max_hits),
                                  _ptr(hits), _ptr(counters),
                                  ctypes.byref(params) if params else None, _stream(stream)))
+
+
+class Instances:
+    """Owns a ``vsr_instances*`` and keeps its meshes alive."""
+
+    def __init__(self, handle: int, meshes):
+        self.handle = handle
+        self.meshes = list(meshes)
+
+    def close(self):
+        if self.handle:
+            lib().vsr_instances_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vsr_instances_create(meshes, inst_mesh, world_to_object, top_blob) -> Instances:
+    """Instance set over ``meshes`` (Scene objects with BVHs): inst_mesh uint32
+    [m], world_to_object float32 [m, 12], top_blob over the instances' boxes."""
+    im = np.ascontiguousarray(inst_mesh, np.uint32).reshape(-1)
+    w = np.ascontiguousarray(world_to_object, np.float32).reshape(-1, 12)
+    tb = np.ascontiguousarray(top_blob, np.uint8)
+    arr = (P * len(meshes))(*[m.handle for m in meshes])
+    out = P()
+    _check(lib().vsr_instances_create(arr, len(meshes), im.ctypes.data if im.size else None,
+                                      w.ctypes.data if w.size else None, im.shape[0],
+                                      tb.ctypes.data, tb.nbytes, ctypes.byref(out)))
+    return Instances(out.value, meshes)
+
+
+def vsr_trace_instances(inst: Instances, rays, isect: vsr_intersector, query, hits,
+                        inst_ids=None, counters=None, params: vsr_trace_params | None = None,
+                        stream=None):
+    """Trace ``rays`` through an instance set into ``hits`` [n,4] (and the
+    instance ids [n])."""
+    q = QUERY[query] if isinstance(query, str) else int(query)
+    _check(lib().vsr_trace_instances(inst.handle, _ptr(rays), int(rays.shape[0]),
+                                     ctypes.byref(isect), q, _ptr(hits), _ptr(inst_ids),
+                                     _ptr(counters), ctypes.byref(params) if params else None,
+                                     _stream(stream)))
+
+
+def vsr_instances_device_error(inst: Instances) -> int:
+    w = ctypes.c_uint32()
+    _check(lib().vsr_instances_device_error(inst.handle, ctypes.byref(w)))
+    return int(w.value)
 
 
 def vsr_trace(scene: Scene, rays, isect: vsr_intersector, query, hits, counters=None,
