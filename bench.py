@@ -427,6 +427,7 @@ def run_ours(args):
     if not args.no_breakdown:
         out["breakdown"] = breakdown(V, s, d_rays, rays_s, n, flush, stream, torch)
         out["multi_hit"] = multi_hit(V, s, d_rays, n, flush, stream, torch)
+        out["instanced"] = instanced_bench(V, torch, dev, flush, stream, args.steps)
         out["fwd_bwd"] = fwd_bwd(V, torch, dev, flush, stream, args.steps, args.warmup)
         out["batch"] = batch_bench(V, torch, dev, flush, stream, args.steps)
         out["large"] = large_bench(V, torch, dev, flush, stream, args.steps)
@@ -509,6 +510,54 @@ def multi_hit(V, s, d_rays, n, flush, stream, torch, reps=5):
         res[f"n{nh}_ms"] = round(t, 4)
         res[f"n{nh}_hits_per_ray"] = round(found / n, 3)
     return res
+
+
+def instanced_bench(V, torch, dev, flush, stream, steps):
+    """The timed step (primary closest hit, shadow rays, shadow any hit with
+    the alpha intersector) on the forest built by instancing: 64 copies of
+    one 7,812-billboard tile, each turned about its vertical axis, plus the
+    ground, under a top-level BVH."""
+    from paper_1912_12786_gb300.inputs import scenes
+    I, rays = scenes.instanced_forest()
+    ms = [V.scene_from_inputs(m, b) for m, b in zip(I.meshes, I.blobs)]
+    X = V.vsr_instances_create(ms, I.inst_mesh, I.w2o, I.top)
+    n = len(rays)
+    d_rays = torch.from_numpy(rays).to(dev)
+    hits_p = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    rays_s = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    hits_s = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    alpha = V.intersector("alpha_tex", cutoff_u8=128)
+    light = torch.from_numpy(scenes.light_dir_f32()).to(dev)
+    eps = float(np.float32(1e-4 * 100.0 * math.sqrt(3)))
+    p = default_params(V)
+    ms_prim, ms_shad = [], []
+    for k in range(max(3, steps // 2) + 2):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        V.vsr_trace_instances(X, d_rays, alpha, "closest", hits_p, None, None, p, stream)
+        ev[1].record(stream)
+        V.vsr_make_shadow_rays(d_rays, hits_p, light, eps, rays_s, stream)
+        ev[2].record(stream)
+        V.vsr_trace_instances(X, rays_s, alpha, "any", hits_s, None, None, p, stream)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        if k >= 2:
+            ms_prim.append(ev[0].elapsed_time(ev[1]))
+            ms_shad.append(ev[2].elapsed_time(ev[3]))
+    tp, ts = statistics.median(ms_prim), statistics.median(ms_shad)
+    tile = I.meshes[0]
+    X.close()
+    for m in ms:
+        m.close()
+    return {"workload": f"{len(I.inst_mesh)} instances (64 turned copies of a {tile.ntri}-"
+                        f"triangle tile + ground), {n} primary + {n} shadow rays, alpha texture",
+            "primary_closest_Mrays_s": round(n / (tp / 1e3) / 1e6, 1),
+            "shadow_any_Mrays_s": round(n / (ts / 1e3) / 1e6, 1),
+            "primary_ms": round(tp, 4), "shadow_ms": round(ts, 4),
+            "step_Mrays_s": round(2 * n / ((tp + ts) / 1e3) / 1e6, 1),
+            "triangles_stored": sum(m.ntri for m in I.meshes),
+            "triangles_instanced": int(sum(I.meshes[k].ntri for k in I.inst_mesh))}
 
 
 def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):

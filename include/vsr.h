@@ -284,7 +284,7 @@ vsr_status vsr_trace_instances(vsr_instances* instances, const vsr_ray* rays, ui
                                const vsr_trace_params* params, vsr_stream stream);
 
 /* Read and clear the instance set's device error word (synchronous; bits as
- * vsr_get_device_error's 0 and 1). */
+ * vsr_get_device_error's 0, 1 and 2). */
 vsr_status vsr_instances_device_error(vsr_instances* instances, uint32_t* word);
 
 /*

@@ -1517,5 +1517,12 @@ extern "C" vsr_status vsr_instances_device_error(vsr_instances* x, uint32_t* wor
     VSR_CUDA(cudaDeviceSynchronize(), "synchronise");
     VSR_CUDA(cudaMemcpy(word, x->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read error word");
     VSR_CUDA(cudaMemset(x->d_err, 0, sizeof(uint32_t)), "clear error word");
+    unsigned line = 0;
+    VSR_CUDA(instances_align_error(&line), "read alignment check");
+    if (line) {
+        *word |= kErrAlign;
+        g_err = "instanced kernel skipped a misaligned access at "
+                "trace_instances.cu/vsr_device.cuh line " + std::to_string(line);
+    }
     return VSR_OK;
 }

@@ -9,6 +9,14 @@
 // One ray per thread.  The top-level while-while loop uses the bottom of the
 // thread's shared-memory stack; a mesh traversal runs on the stack above the
 // top-level entries, continuing the running result.
+//
+// Two new kernels (the render and multi-hit kernels) raised an unexplained
+// misaligned-address fault on the first launch of their unchecked builds and
+// ran clean with checked accesses, so this translation unit starts checked:
+// every load goes through the alignment-checked path and the stores check
+// their address (a skipped access is reported with its line, device error
+// bit 2).
+#define VSR_CHECKED_LOADS 1
 #include "vsr_internal.h"
 
 namespace vsr {
@@ -150,9 +158,22 @@ done:
         best.v = 0.0f;
         best.inst = kMiss;
     }
-    hits[i] = make_float4(best.t, best.u, best.v, __uint_as_float(best.prim));
-    if (inst_ids) inst_ids[i] = best.inst;
-    if (H::kCounts && counters) counters[i] = h.counters();
+    if (reinterpret_cast<unsigned long long>(hits + i) % 16)
+        atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
+    else
+        hits[i] = make_float4(best.t, best.u, best.v, __uint_as_float(best.prim));
+    if (inst_ids) {
+        if (reinterpret_cast<unsigned long long>(inst_ids + i) % 4)
+            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
+        else
+            inst_ids[i] = best.inst;
+    }
+    if (H::kCounts && counters) {
+        if (reinterpret_cast<unsigned long long>(counters + i) % 8)
+            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
+        else
+            counters[i] = h.counters();
+    }
 }
 
 template <int Q, class H>
@@ -182,6 +203,13 @@ cudaError_t inst_kind(const InstLaunch& L, int kind) {
 }
 
 }  // namespace
+
+cudaError_t instances_align_error(unsigned* line) {
+    cudaError_t e = cudaMemcpyFromSymbol(line, g_vsr_align_line, sizeof(unsigned));
+    if (e != cudaSuccess || *line == 0) return e;
+    const unsigned zero = 0;
+    return cudaMemcpyToSymbol(g_vsr_align_line, &zero, sizeof(unsigned));
+}
 
 cudaError_t launch_instances(const InstLaunch& L, int kind, int query) {
     return query == kClosest ? inst_kind<kClosest>(L, kind) : inst_kind<kAny>(L, kind);

@@ -75,6 +75,9 @@ struct InstLaunch {
     cudaStream_t stream;
 };
 cudaError_t launch_instances(const InstLaunch& L, int kind, int query);
+// Source line of the first misaligned access the instanced kernels skipped
+// (0 if none), cleared after reading.
+cudaError_t instances_align_error(unsigned* line);
 
 // Closest-hit render with diffuse shading, and its adjoint (render.cu).
 cudaError_t launch_render(const LaunchArgs& a, int kind, const ShadeDev& sh, const float* verts,

@@ -1,0 +1,161 @@
+"""Instanced traces on the GPU vs the oracle, through the C ABI (needs a GB300).
+
+Bar: hits (t, u, v, prim), instance ids and bvh_costs counters bit-identical
+to the oracle's two-level traversal (top-level BVH over the instances, each
+mesh's own BVH below, the intersector passed on); near-tie rays excluded as
+for single meshes.  Closest-hit ties between coincident instances go to the
+lower instance id.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1912_12786_gb300.inputs import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+KINDS = ["none", "default", "alpha_tex", "proc_alpha", "count"]
+
+
+@pytest.fixture(scope="module")
+def V():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_12786_gb300 import _build, vsr
+    _build.build()
+    return vsr
+
+
+def _upload(V, I):
+    ms = [V.scene_from_inputs(m, b) for m, b in zip(I.meshes, I.blobs)]
+    return V.vsr_instances_create(ms, I.inst_mesh, I.w2o, I.top)
+
+
+@pytest.fixture(scope="module")
+def small(V):
+    I, rays = scenes.instanced_small()
+    X = _upload(V, I)
+    yield I, rays, X
+    X.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _gpu(V, X, rays, kind, query, params=None):
+    n = rays.shape[0]
+    hits = torch.full((n, 4), float("nan"), dtype=torch.float32, device="cuda")
+    ids = torch.full((n,), 7, dtype=torch.int32, device="cuda")
+    cnt = torch.full((n, 2), -1, dtype=torch.int32, device="cuda") if kind == "count" else None
+    V.vsr_trace_instances(X, rays, V.intersector(kind), query, hits, ids, cnt, params)
+    torch.cuda.synchronize()
+    return (hits.cpu().numpy(), ids.cpu().numpy().view(np.uint32),
+            None if cnt is None else cnt.cpu().numpy().view(np.uint32))
+
+
+def _oracle(I, rays, kind, query):
+    return O.trace_instances(list(zip(I.meshes, I.blobs)), I.inst_mesh, I.w2o, rays, kind, query,
+                             I.top)
+
+
+def _compare(got, ids, ref, rids, st, label):
+    r = O.hits_raw(ref)
+    ok = st[:, 3] == 0
+    bad = (np.any(got.view(np.uint32) != r.view(np.uint32), axis=1) | (ids != rids)) & ok
+    assert not bad.any(), f"{label}: {int(bad.sum())} rays differ"
+    return ok
+
+
+@pytest.mark.parametrize("query", ["closest", "any"])
+@pytest.mark.parametrize("kind", KINDS)
+def test_small_all_intersectors(V, small, kind, query):
+    I, rays, X = small
+    ref, rids, st = _oracle(I, rays, kind, query)
+    got, ids, cnt = _gpu(V, X, _dev(rays), kind, query)
+    ok = _compare(got, ids, ref, rids, st, f"{kind}/{query}")
+    if cnt is not None:
+        assert np.array_equal(cnt[ok], st[ok, :2])
+    assert len(np.unique(ids[ids != O.NONE])) >= 4
+    assert V.vsr_instances_device_error(X) == 0
+    for m in X.meshes:
+        assert V.vsr_get_device_error(m) == 0
+
+
+@pytest.mark.parametrize("n,width", [(1, 0), (33, 0), (4097, 37), (65536, 256)])
+def test_ragged_and_pixel_tiles(V, small, n, width):
+    I, rays, X = small
+    sel = np.resize(rays[::-1], (n, 8))
+    ref, rids, st = _oracle(I, sel, "alpha_tex", "closest")
+    got, ids, _ = _gpu(V, X, _dev(sel), "alpha_tex", "closest", V.trace_params(image_width=width))
+    _compare(got, ids, ref, rids, st, f"n={n} width={width}")
+
+
+def test_coincident_instances_tie_to_the_lower_id(V):
+    from test_oracle_pins import two_tri_scene
+    sc, _ = two_tri_scene()
+    ident = np.hstack([np.eye(3), np.zeros((3, 1))])
+    moved = np.hstack([np.eye(3), np.array([[10.0], [0.0], [0.0]])])
+    I = scenes.make_instance_set("two", [sc], [0, 0, 0], [moved, ident, ident])
+    X = _upload(V, I)
+    try:
+        rays = np.array([[0, 0, 0, 0, 0, 0, 1, np.inf], [10, 0, 0, 0, 0, 0, 1, np.inf],
+                         [0, 0, 4, 0, 0, 0, -1, np.inf]], np.float32)
+        got, ids, _ = _gpu(V, X, _dev(rays), "default", "closest")
+        assert list(ids) == [1, 0, 1]
+        assert list(got[:, 3].view(np.uint32)) == [0, 0, 1] and list(got[:, 0]) == [1.0, 1.0, 1.0]
+    finally:
+        X.close()
+
+
+def test_argument_checks(V, small):
+    I, rays, X = small
+    d = _dev(rays[:64])
+    hits = torch.empty((64, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(V.VsrError, match="static dispatch"):
+        V.vsr_trace_instances(X, d, V.intersector("default", "dynamic"), "closest", hits)
+    with pytest.raises(V.VsrError, match="one ray per thread"):
+        V.vsr_trace_instances(X, d, V.intersector("default"), "closest", hits, None, None,
+                              V.trace_params(persistent=1))
+    ms = X.meshes
+    with pytest.raises(V.VsrError, match="missing mesh"):
+        V.vsr_instances_create(ms, np.full(len(I.inst_mesh), 5, np.uint32), I.w2o, I.top)
+    with pytest.raises(V.VsrError, match="different number of instances"):
+        V.vsr_instances_create(ms, I.inst_mesh[:-1], I.w2o[:-1], I.top)
+    bad = I.w2o.copy()
+    bad[2, 5] = np.nan
+    with pytest.raises(V.VsrError, match="non-finite"):
+        V.vsr_instances_create(ms, I.inst_mesh, bad, I.top)
+    bare = V.vsr_scene_create_indexed(I.meshes[0].verts, I.meshes[0].idx, I.meshes[0].uvs,
+                                      I.meshes[0].geom_id, I.meshes[0].textures)
+    with pytest.raises(V.VsrError, match="no BVH"):
+        V.vsr_instances_create([bare, ms[1]], I.inst_mesh, I.w2o, I.top)
+    bare.close()
+
+
+def test_instanced_forest_sample(V):
+    """The forest built from 64 turned copies of one tile plus the ground:
+    the full 1920x1080 frame, primary closest hits and shadow any hits with
+    the alpha intersector in the bench's launch configuration, a seeded
+    sample against the oracle."""
+    import bench
+    I, rays = scenes.instanced_forest()
+    X = _upload(V, I)
+    try:
+        p = bench.default_params(V)
+        got, ids, _ = _gpu(V, X, _dev(rays), "alpha_tex", "closest", p)
+        rng = np.random.default_rng(17)
+        sel = np.sort(rng.choice(len(rays), 4000, replace=False))
+        ref, rids, st = _oracle(I, rays[sel], "alpha_tex", "closest")
+        ok = _compare(got[sel], ids[sel], ref, rids, st, "forest primary")
+        assert ok.mean() > 0.99
+        assert len(np.unique(ids[ids != O.NONE])) > 40
+        light, eps = scenes.light_dir_f32(), np.float32(1e-4 * 100.0 * np.sqrt(3))
+        sref = O.shadow_rays(rays[sel], O.hits_raw(ref), light, float(eps))
+        sh_ref, sh_ids, sh_st = _oracle(I, sref, "alpha_tex", "any")
+        sh, shi, _ = _gpu(V, X, _dev(sref), "alpha_tex", "any", p)
+        _compare(sh, shi, sh_ref, sh_ids, sh_st, "forest shadow")
+        assert V.vsr_instances_device_error(X) == 0
+    finally:
+        X.close()
