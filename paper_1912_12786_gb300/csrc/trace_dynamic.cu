@@ -73,8 +73,12 @@ struct IsectDynamic {
     __device__ __forceinline__ uint2 counters() const { return make_uint2(boxes, tris); }
 };
 
+// Register cap per query: the indirect calls make the callback kernel
+// register-hungry (about 100 uncapped), and it runs faster at higher
+// occupancy despite a few spills -- 80 registers for closest-hit and 64 for
+// any-hit were the fastest of the caps measured (none, 80, 64).
 template <int Q>
-__global__ void __launch_bounds__(256) k_trace_dyn(DevScene sc, IsectParams ip,
+__global__ void __launch_bounds__(256, Q == kClosest ? 3 : 4) k_trace_dyn(DevScene sc, IsectParams ip,
                                                    const DevScene* __restrict__ user,
                                                    const float4* __restrict__ rays,
                                                    RayMap map,
