@@ -78,12 +78,10 @@ struct IsectDynamic {
 // occupancy despite a few spills -- 80 registers for closest-hit and 64 for
 // any-hit were the fastest of the caps measured (none, 80, 64).
 template <int Q>
-__global__ void __launch_bounds__(256, Q == kClosest ? 3 : 4) k_trace_dyn(DevScene sc, IsectParams ip,
-                                                   const DevScene* __restrict__ user,
-                                                   const float4* __restrict__ rays,
-                                                   RayMap map,
-                                                   float4* __restrict__ hits,
-                                                   uint2* __restrict__ counters) {
+__global__ void __launch_bounds__(256, Q == kClosest ? 3 : 4)
+    k_trace_dyn(DevScene sc, IsectParams ip, const DevScene* __restrict__ user,
+                const float4* __restrict__ rays, RayMap map, float4* __restrict__ hits,
+                uint2* __restrict__ counters) {
     extern __shared__ uint32_t s_stack[];
     const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= map.threads) return;
