@@ -153,13 +153,16 @@ def trace_bytes(n_rays: int, stats: np.ndarray, texel_bytes: int, texcoords: boo
 
 
 def trace_alu_ops(n_rays: int, stats: np.ndarray, texcoords: bool) -> int:
-    """Algorithmic operations of one launch on the ALU pipe (the busiest unit):
-    13 per box test (12 min/max of the slab test + 1 compare), 7 per triangle
-    test (det == 0, u >= 0, v >= 0, u + v <= 1, t > tmin, t < tmax, t < best),
-    1 per intersector call, 6 per ray set-up (direction guards), and for alpha
-    intersectors 8 per texture fetch (clamps, index bounds, alpha compare)."""
+    """Algorithmic work of one launch on the ALU pipe (the busiest unit), as
+    the fewest ALU-pipe instructions this GPU needs for it (a three-input
+    min/max is one instruction): 11 per box test (6 per-axis min/max, 2 each
+    for the entry and exit bounds with tmin and the far limit folded in, 1
+    compare), 7 per triangle test (det == 0, u >= 0, v >= 0, u + v <= 1,
+    t > tmin, t < tmax, t < best), 1 per intersector call, 6 per ray set-up
+    (direction guards), and for alpha intersectors 8 per texture fetch
+    (clamps, index bounds, alpha compare)."""
     s = stats.astype(np.int64).sum(axis=0)
-    ops = 6 * n_rays + 13 * int(s[0]) + 7 * int(s[1]) + int(s[2])
+    ops = 6 * n_rays + 11 * int(s[0]) + 7 * int(s[1]) + int(s[2])
     if texcoords:
         ops += 8 * int(s[3])
     return ops
