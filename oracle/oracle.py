@@ -21,7 +21,8 @@ Intersectors to the C++ Ray Tracing Template Library Visionaray"):
   of a list or of a top-level BVH, the intersector passed on to each BVH's
   own intersect), rays taken to object space by a world-to-object map.
 * intersector kinds follow Section 3.1 (default forwarding), Section 4
-  (alpha-mask listing, procedural alpha, ``bvh_costs``).
+  (alpha-mask listing, procedural alpha, ``bvh_costs``) and Section 3.2 (an
+  intersector that also replaces intersect(ray, aabb): the clip box).
 """
 from __future__ import annotations
 
@@ -40,10 +41,10 @@ _lock = threading.Lock()
 _lib = None
 
 NONE = 0xFFFFFFFF
-ISECT = {"none": 0, "default": 1, "alpha_tex": 2, "proc_alpha": 3, "count": 4}
+ISECT = {"none": 0, "default": 1, "alpha_tex": 2, "proc_alpha": 3, "count": 4, "clip": 5}
 QUERY = {"closest": 0, "any": 1}
 TEX_FMT = {"u8": 0, "rgba8": 1, "rgba32f": 2}
-TIE_EDGE, TIE_ALPHA = 1, 2
+TIE_EDGE, TIE_ALPHA, TIE_CLIP = 1, 2, 4
 
 
 class _Texture(ctypes.Structure):
@@ -60,7 +61,8 @@ class _Scene(ctypes.Structure):
 
 class _Isect(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("cutoff_u8", ctypes.c_uint32),
-                ("cutoff_f", ctypes.c_float), ("freq", ctypes.c_float)]
+                ("cutoff_f", ctypes.c_float), ("freq", ctypes.c_float),
+                ("clip_lo", ctypes.c_float * 3), ("clip_hi", ctypes.c_float * 3)]
 
 
 def build(force: bool = False) -> str:
@@ -124,8 +126,10 @@ class _SceneHandle:
                         ctypes.addressof(self.tex))
 
 
-def _isect(kind: str, cutoff_u8: int = 128, cutoff_f: float = 0.01, freq: float = 40.0):
-    return _Isect(ISECT[kind], cutoff_u8, cutoff_f, freq)
+def _isect(kind: str, cutoff_u8: int = 128, cutoff_f: float = 0.01, freq: float = 40.0,
+           clip_lo=(0.0, 0.0, 0.0), clip_hi=(0.0, 0.0, 0.0)):
+    return _Isect(ISECT[kind], cutoff_u8, cutoff_f, freq, (ctypes.c_float * 3)(*clip_lo),
+                  (ctypes.c_float * 3)(*clip_hi))
 
 
 def _run(fn, scene, rays, kind, query, nthreads, extra, **kw):

@@ -73,7 +73,12 @@
  *     whose texture id is 0xFFFFFFFF are opaque for both alpha intersectors;
  *   - tex-coord interpolation: w0 = (1 - u) - v,
  *     uv = fmaf(v, tc2, fmaf(u, tc1, w0*tc0)) per component;
- *   - procedural alpha: accept iff sinf(f*uv.x) * sinf(f*uv.y) > 0.
+ *   - procedural alpha: accept iff sinf(f*uv.x) * sinf(f*uv.y) > 0;
+ *   - clip box (Section 3.2: an intersector may also replace intersect(ray,
+ *     aabb) for the BVH's node boxes): a candidate is accepted iff its hit
+ *     point p = fmaf(t, d, o) (per component) lies in the closed clip box, and
+ *     a node box that does not overlap the clip box counts as missed, which
+ *     skips its subtree without changing any answer.
  */
 #include <math.h>
 #include <pthread.h>
@@ -85,13 +90,13 @@
 
 /* intersector kinds */
 enum { ORC_ISECT_NONE = 0, ORC_ISECT_DEFAULT = 1, ORC_ISECT_ALPHA_TEX = 2,
-       ORC_ISECT_PROC_ALPHA = 3, ORC_ISECT_COUNT = 4 };
+       ORC_ISECT_PROC_ALPHA = 3, ORC_ISECT_COUNT = 4, ORC_ISECT_CLIP = 5 };
 /* queries */
 enum { ORC_CLOSEST = 0, ORC_ANY = 1, ORC_MULTI = 2 };
 /* texture formats */
 enum { ORC_TEX_U8 = 0, ORC_TEX_RGBA8 = 1, ORC_TEX_RGBA32F = 2 };
 /* near-tie flags */
-enum { ORC_TIE_EDGE = 1, ORC_TIE_ALPHA = 2 };
+enum { ORC_TIE_EDGE = 1, ORC_TIE_ALPHA = 2, ORC_TIE_CLIP = 4 };
 
 typedef struct {
     int32_t fmt;
@@ -114,6 +119,7 @@ typedef struct {
     uint32_t cutoff_u8;
     float cutoff_f;
     float freq;
+    float clip_lo[3], clip_hi[3]; /* clip-box intersector */
 } orc_isect;
 
 typedef struct {
@@ -230,10 +236,31 @@ static void lerp_texcoord(const orc_scene* s, uint32_t prim, float u, float v, f
     *y = fmaf(v, tc[5], fmaf(u, tc[3], w0 * tc[1]));
 }
 
-/* The intersector's verdict on a geometric candidate (the line
- * "hr.hit &= ..." of the user operator()).  Sets near-tie flags. */
+/* The intersector's verdict on a node box (its intersect(ray, aabb)
+ * overload): 0 makes the box count as missed.  Only the clip box culls. */
+static int box_keep(const orc_isect* is, const float lo[3], const float hi[3]) {
+    if (is->kind != ORC_ISECT_CLIP) return 1;
+    for (int a = 0; a < 3; ++a)
+        if (lo[a] > is->clip_hi[a] || hi[a] < is->clip_lo[a]) return 0;
+    return 1;
+}
+
+/* The intersector's verdict on a geometric candidate at distance t along
+ * ray r (the line "hr.hit &= ..." of the user operator()).  Sets near-tie
+ * flags. */
 static int intersector_accepts(const orc_scene* s, const orc_isect* is, uint32_t prim,
-                               float u, float v, uint32_t* flags) {
+                               float u, float v, const orc_ray* r, float t, uint32_t* flags) {
+    if (is->kind == ORC_ISECT_CLIP) {
+        int in = 1;
+        for (int a = 0; a < 3; ++a) {
+            const float p = fmaf(t, r->d[a], r->o[a]);
+            in &= p >= is->clip_lo[a] && p <= is->clip_hi[a];
+            const double tol = 1e-6 * fmax(1.0, fabs((double)p));
+            if (fabs((double)p - is->clip_lo[a]) < tol || fabs((double)p - is->clip_hi[a]) < tol)
+                *flags |= ORC_TIE_CLIP;
+        }
+        return in;
+    }
     if (is->kind != ORC_ISECT_ALPHA_TEX && is->kind != ORC_ISECT_PROC_ALPHA) return 1;
     const uint32_t g = s->geom_id[prim];
     if (g == ORC_NONE) return 1;
@@ -320,12 +347,12 @@ static int visit_prim(const orc_scene* s, const orc_isect* is, int query,
     if (query != ORC_ANY) {
         if (!hit_before(t, prim, last)) return 0;
         st->cands++;
-        if (!intersector_accepts(s, is, prim, u, v, &st->flags)) return 0;
+        if (!intersector_accepts(s, is, prim, u, v, &c->r, t, &st->flags)) return 0;
         insert_hit(best, nh, t, u, v, prim);
         return 0;
     }
     st->cands++;
-    if (!intersector_accepts(s, is, prim, u, v, &st->flags)) return 0;
+    if (!intersector_accepts(s, is, prim, u, v, &c->r, t, &st->flags)) return 0;
     best->t = t;
     best->u = u;
     best->v = v;
@@ -386,7 +413,7 @@ static void list_multi(const orc_scene* s, const orc_isect* is, uint32_t nh, con
         if (!(t > c.r.tmin && t < c.r.tmax)) continue;
         note_edge_tie(u, v, &st->flags);
         st->cands++;
-        if (!intersector_accepts(s, is, p, u, v, &st->flags)) continue;
+        if (!intersector_accepts(s, is, p, u, v, &c.r, t, &st->flags)) continue;
         scratch[m].t = t;
         scratch[m].u = u;
         scratch[m].v = v;
@@ -457,7 +484,9 @@ static void bvh_query(const orc_scene* s, const orc_bvh* b, const orc_isect* is,
     int sp = 0;
     if (b->num_prims == 0) goto done;
     st->boxes++;
-    if (!intersect_aabb(&c, b->nodes[0].lo, b->nodes[0].hi, last->t)) goto done;
+    if (!intersect_aabb(&c, b->nodes[0].lo, b->nodes[0].hi, last->t) ||
+        !box_keep(is, b->nodes[0].lo, b->nodes[0].hi))
+        goto done;
     uint32_t node = 0;
     for (;;) { /* while ray not terminated */
         while ((b->nodes[node].count_axis >> 2) == 0) { /* while node is inner */
@@ -465,8 +494,10 @@ static void bvh_query(const orc_scene* s, const orc_bvh* b, const orc_isect* is,
             const uint32_t l = nd->left_or_first, r = l + 1;
             const float far_t = (query != ORC_ANY) ? last->t : ray->tmax;
             st->boxes += 2;
-            const int hl = intersect_aabb(&c, b->nodes[l].lo, b->nodes[l].hi, far_t);
-            const int hr = intersect_aabb(&c, b->nodes[r].lo, b->nodes[r].hi, far_t);
+            const int hl = intersect_aabb(&c, b->nodes[l].lo, b->nodes[l].hi, far_t) &&
+                           box_keep(is, b->nodes[l].lo, b->nodes[l].hi);
+            const int hr = intersect_aabb(&c, b->nodes[r].lo, b->nodes[r].hi, far_t) &&
+                           box_keep(is, b->nodes[r].lo, b->nodes[r].hi);
             if (hl && hr) {
                 const int axis = (int)(nd->count_axis & 3u);
                 const int neg = signbit(ray->d[axis]) ? 1 : 0;
@@ -583,7 +614,7 @@ static int instance_query(const orc_mesh* m, const orc_isect* is, int query, uin
             if (g == 0 || !in_range) continue;
             if (query == ORC_CLOSEST && !ihit_before(t, inst, prim, best)) continue;
             st->cands++;
-            if (!intersector_accepts(s, is, prim, u, v, &st->flags)) continue;
+            if (!intersector_accepts(s, is, prim, u, v, &c.r, t, &st->flags)) continue;
             best->t = t;
             best->u = u;
             best->v = v;
@@ -795,6 +826,7 @@ int orc_trace_instances(const orc_scene* const* scenes, const uint8_t* const* bl
         (n && (!rays || !hits)))
         return -1;
     if (query != ORC_CLOSEST && query != ORC_ANY) return -1;
+    if (is->kind == ORC_ISECT_CLIP) return -1; /* a world-space clip box is not supported */
     orc_mesh* meshes = (orc_mesh*)calloc(nmeshes ? nmeshes : 1, sizeof(orc_mesh));
     if (!meshes) return -7;
     int rc = 0;
