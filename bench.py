@@ -461,12 +461,15 @@ def breakdown(V, s, d_rays, rays_s, n, flush, stream, torch, reps=5):
     cnt = torch.empty((n, 2), dtype=torch.int32, device=d_rays.device)
     cfgs = [(k, d) for k in ("default", "alpha_tex", "proc_alpha", "count")
             for d in ("static", "dynamic")]
+    # the clip box keeps the left half of the forest (x <= 50) and culls the rest
+    clip = dict(clip_lo=(-1.0, -1.0, -1.0), clip_hi=(50.0, 10.0, 101.0))
     for q, rr in (("closest", d_rays), ("any", rays_s)):
-        for kind, disp in cfgs + [("alpha_tex", "persistent")]:
+        for kind, disp in cfgs + [("alpha_tex", "persistent"), ("clip", "static")]:
             p = default_params(V)
             if disp == "persistent":
                 p.persistent = 1
-            isect = V.intersector(kind, "static" if disp == "persistent" else disp)
+            isect = V.intersector(kind, "static" if disp == "persistent" else disp,
+                                  **(clip if kind == "clip" else {}))
             c = cnt if kind == "count" else None
             ms = []
             for r in range(reps + 2):

@@ -103,7 +103,8 @@ typedef enum vsr_isect_kind {
     VSR_ISECT_DEFAULT = 1,    /* basic_intersector: forwards intersect() */
     VSR_ISECT_ALPHA_TEX = 2,  /* alpha mask: nearest texel alpha >= cutoff */
     VSR_ISECT_PROC_ALPHA = 3, /* sinf(f*uv.x) * sinf(f*uv.y) > 0 */
-    VSR_ISECT_COUNT = 4       /* bvh_costs: counts box and triangle tests */
+    VSR_ISECT_COUNT = 4,      /* bvh_costs: counts box and triangle tests */
+    VSR_ISECT_CLIP = 5        /* clip box: intercepts node box tests too */
 } vsr_isect_kind;
 
 typedef enum vsr_dispatch {
@@ -114,14 +115,23 @@ typedef enum vsr_dispatch {
 /* Intersector description.  Alpha intersectors read the triangle's texture
  * (geom_id) and interpolate its three texture coordinates with the hit's
  * barycentrics: uv = (1-u-v)*tc0 + u*tc1 + v*tc2.  Triangles whose geom_id is
- * VSR_NO_TEXTURE are opaque for both alpha intersectors. */
+ * VSR_NO_TEXTURE are opaque for both alpha intersectors.
+ *
+ * The clip box replaces both calls to intersect (Section 3.2: an intersector
+ * may also overload intersect(ray, aabb) for the BVH's node boxes): a
+ * candidate is accepted iff its hit point fmaf(t, d, o) (per component) lies
+ * in the closed box [clip_lo, clip_hi], and a node box that does not overlap
+ * the clip box counts as missed, so its subtree is skipped.  The answer is the
+ * nearest hit inside the box.  Static dispatch; vsr_trace (one ray per thread
+ * or persistent), vsr_trace_stats and vsr_trace_multi only. */
 typedef struct vsr_intersector {
     int32_t kind;             /* vsr_isect_kind */
     int32_t dispatch;         /* vsr_dispatch */
     uint32_t alpha_cutoff_u8; /* 8-bit textures: accept iff alpha >= this */
     float alpha_cutoff_f;     /* float textures: accept iff alpha >= this */
     float proc_freq;          /* procedural frequency f (40 in the tests) */
-    uint32_t reserved[3];     /* 0 */
+    float clip_lo[3];         /* clip box (VSR_ISECT_CLIP), lo <= hi, finite */
+    float clip_hi[3];
 } vsr_intersector;
 
 typedef enum vsr_query {

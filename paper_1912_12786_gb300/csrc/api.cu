@@ -249,15 +249,36 @@ void node_levels(const vsr_bvh_node* nodes, uint32_t num_nodes, uint32_t max_dep
 
 vsr_status validate_isect(const vsr_intersector* is, int32_t query) {
     if (!is) return fail(VSR_ERR_ARG, "intersector is null");
-    if (is->kind < VSR_ISECT_NONE || is->kind > VSR_ISECT_COUNT)
+    if (is->kind < VSR_ISECT_NONE || is->kind > VSR_ISECT_CLIP)
         return fail(VSR_ERR_ARG, "unknown intersector kind");
     if (is->dispatch != VSR_DISPATCH_STATIC && is->dispatch != VSR_DISPATCH_DYNAMIC)
         return fail(VSR_ERR_ARG, "unknown dispatch mode");
     if (is->alpha_cutoff_u8 > 256) return fail(VSR_ERR_ARG, "alpha_cutoff_u8 above 256");
     if (std::isnan(is->alpha_cutoff_f) || !std::isfinite(is->proc_freq))
         return fail(VSR_ERR_ARG, "non-finite intersector parameter");
+    if (is->kind == VSR_ISECT_CLIP) {
+        if (is->dispatch != VSR_DISPATCH_STATIC)
+            return fail(VSR_ERR_ARG, "the clip-box intersector uses static dispatch only");
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(is->clip_lo[a]) || !std::isfinite(is->clip_hi[a]) ||
+                is->clip_lo[a] > is->clip_hi[a])
+                return fail(VSR_ERR_ARG, "clip box must be finite with clip_lo <= clip_hi");
+    }
     if (query != VSR_CLOSEST && query != VSR_ANY) return fail(VSR_ERR_ARG, "unknown query");
     return VSR_OK;
+}
+
+IsectParams isect_params(const vsr_intersector* is) {
+    IsectParams ip{};
+    ip.cutoff_u8 = is->alpha_cutoff_u8;
+    ip.cutoff_f = is->alpha_cutoff_f;
+    ip.freq = is->proc_freq;
+    ip.kind = (uint32_t)is->kind;
+    for (int a = 0; a < 3; ++a) {
+        ip.clip_lo[a] = is->clip_lo[a];
+        ip.clip_hi[a] = is->clip_hi[a];
+    }
+    return ip;
 }
 
 // Thread -> ray map for n rays laid out as a row-major image `width` pixels
@@ -312,10 +333,7 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     st = make_map(n, prm.image_width, a.map);
     if (st != VSR_OK) return st;
     a.sc = s->dev;
-    a.ip.cutoff_u8 = is->alpha_cutoff_u8;
-    a.ip.cutoff_f = is->alpha_cutoff_f;
-    a.ip.freq = is->proc_freq;
-    a.ip.kind = (uint32_t)is->kind;
+    a.ip = isect_params(is);
     a.rays = reinterpret_cast<const float4*>(rays);
     a.n = n;
     a.hits = reinterpret_cast<float4*>(hits);
@@ -698,6 +716,8 @@ vsr_status prepare_render(vsr_scene* s, const vsr_ray* rays, uint64_t n,
                           const vsr_trace_params* p, LaunchArgs& a, ShadeDev& shd) {
     if (is && is->dispatch != VSR_DISPATCH_STATIC)
         return fail(VSR_ERR_ARG, "rendering uses static dispatch only");
+    if (is && is->kind == VSR_ISECT_CLIP)
+        return fail(VSR_ERR_ARG, "the clip-box intersector is for vsr_trace and vsr_trace_multi");
     if (p && p->persistent) return fail(VSR_ERR_ARG, "rendering uses non-persistent launches");
     // hits are checked by the callers; a placeholder keeps prepare_launch's
     // hit check out of the way when n == 0
@@ -1151,6 +1171,8 @@ extern "C" vsr_status vsr_batch_create(vsr_scene* const* scenes, const vsr_ray* 
     if (st != VSR_OK) return st;
     if (is->dispatch != VSR_DISPATCH_STATIC)
         return fail(VSR_ERR_ARG, "batched launches use static dispatch only");
+    if (is->kind == VSR_ISECT_CLIP)
+        return fail(VSR_ERR_ARG, "the clip-box intersector is for vsr_trace and vsr_trace_multi");
     vsr_trace_params prm{128u, 1u, 16u, 0u};
     if (params) {
         prm = *params;
@@ -1195,7 +1217,7 @@ extern "C" vsr_status vsr_batch_create(vsr_scene* const* scenes, const vsr_ray* 
     b->total = offsets[nbatch];
     b->kind = is->kind;
     b->query = query;
-    b->ip = IsectParams{is->alpha_cutoff_u8, is->alpha_cutoff_f, is->proc_freq, (uint32_t)is->kind};
+    b->ip = isect_params(is);
     b->stack_max = stack_max;
     b->shape = shape;
     b->params = prm;
@@ -1471,6 +1493,8 @@ extern "C" vsr_status vsr_trace_instances(vsr_instances* x, const vsr_ray* rays,
     if (st != VSR_OK) return st;
     if (is->dispatch != VSR_DISPATCH_STATIC)
         return fail(VSR_ERR_ARG, "instanced traces use static dispatch only");
+    if (is->kind == VSR_ISECT_CLIP)
+        return fail(VSR_ERR_ARG, "the clip-box intersector is for vsr_trace and vsr_trace_multi");
     vsr_trace_params prm{128u, 0u, 16u, 0u, 0u};
     if (p) prm = *p;
     if (prm.block_size < 32 || prm.block_size > 256 || prm.block_size % 32)
@@ -1493,10 +1517,7 @@ extern "C" vsr_status vsr_trace_instances(vsr_instances* x, const vsr_ray* rays,
         if ((st = check_dev(counters, x->device, "counters", 8, n * 8)) != VSR_OK) return st;
     }
     L.is = x->dev;
-    L.ip.cutoff_u8 = is->alpha_cutoff_u8;
-    L.ip.cutoff_f = is->alpha_cutoff_f;
-    L.ip.freq = is->proc_freq;
-    L.ip.kind = (uint32_t)is->kind;
+    L.ip = isect_params(is);
     L.rays = reinterpret_cast<const float4*>(rays);
     L.hits = reinterpret_cast<float4*>(hits);
     L.inst_ids = inst_ids;

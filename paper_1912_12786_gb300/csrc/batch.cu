@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_trace_batch(const BatchItem* __restrict
                     r = make_ray(VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
                     h = H();
                     has = true;
-                    if (!traverse_start<Q, H, false>(sc, r, h, best, st, ref, sp, steps)) {
+                    if (!traverse_start<Q, H, false>(sc, ip, r, h, best, st, ref, sp, steps)) {
                         finish_miss(best);
                         hp[ri] = hit_record(best);
                         has = false;

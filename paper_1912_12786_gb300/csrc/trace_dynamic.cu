@@ -11,23 +11,39 @@
 
 namespace vsr {
 
-typedef bool (*AcceptFn)(const DevScene*, IsectParams, uint32_t, float, float);
+// The callbacks receive the intersector parameters they read by value, 16
+// bytes (the clip box of the static intersectors is not among them).
+struct DynParams {
+    uint32_t cutoff_u8;
+    float cutoff_f;
+    float freq;
+    uint32_t kind;
+};
+typedef bool (*AcceptFn)(const DevScene*, DynParams, uint32_t, float, float);
 // Counting callbacks take the running count by value and return it
 // incremented, so no callback ever receives a pointer into the caller's
 // local memory.
 typedef uint32_t (*CountFn)(uint32_t);
 
-__device__ __noinline__ bool dyn_accept_default(const DevScene*, IsectParams, uint32_t, float,
+__device__ __forceinline__ IsectParams from_dyn(DynParams d) {
+    IsectParams ip{};
+    ip.cutoff_u8 = d.cutoff_u8;
+    ip.cutoff_f = d.cutoff_f;
+    ip.freq = d.freq;
+    ip.kind = d.kind;
+    return ip;
+}
+__device__ __noinline__ bool dyn_accept_default(const DevScene*, DynParams, uint32_t, float,
                                                 float) {
     return true;
 }
-__device__ __noinline__ bool dyn_accept_alpha(const DevScene* sc, IsectParams ip, uint32_t prim,
+__device__ __noinline__ bool dyn_accept_alpha(const DevScene* sc, DynParams dp, uint32_t prim,
                                               float u, float v) {
-    return alpha_tex_accept(*sc, ip, prim, u, v);
+    return alpha_tex_accept(*sc, from_dyn(dp), prim, u, v);
 }
-__device__ __noinline__ bool dyn_accept_proc(const DevScene* sc, IsectParams ip, uint32_t prim,
+__device__ __noinline__ bool dyn_accept_proc(const DevScene* sc, DynParams dp, uint32_t prim,
                                              float u, float v) {
-    return proc_alpha_accept(*sc, ip, prim, u, v);
+    return proc_alpha_accept(*sc, from_dyn(dp), prim, u, v);
 }
 __device__ __noinline__ uint32_t dyn_count_box(uint32_t n) { return n + 1u; }
 __device__ __noinline__ uint32_t dyn_count_tri(uint32_t n) { return n + 1u; }
@@ -60,15 +76,18 @@ struct IsectDynamic {
     CountFn on_box = nullptr, on_tri = nullptr;
     const DevScene* user = nullptr;
     uint32_t boxes = 0, tris = 0;
+    __device__ __forceinline__ void begin(const Ray&) {}
     __device__ __forceinline__ void box() {
         if (on_box) boxes = on_box(boxes);
     }
     __device__ __forceinline__ void tri() {
         if (on_tri) tris = on_tri(tris);
     }
+    __device__ __forceinline__ bool keep(const IsectParams&, float4, float4) const { return true; }
     __device__ __forceinline__ bool accept(const DevScene&, const IsectParams& ip, uint32_t prim,
-                                           float u, float v) {
-        return acc ? acc(user, ip, prim, u, v) : true;
+                                           float u, float v, float) {
+        return acc ? acc(user, DynParams{ip.cutoff_u8, ip.cutoff_f, ip.freq, ip.kind}, prim, u, v)
+                   : true;
     }
     __device__ __forceinline__ uint2 counters() const { return make_uint2(boxes, tris); }
 };

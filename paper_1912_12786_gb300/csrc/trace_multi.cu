@@ -114,6 +114,7 @@ cudaError_t launch_multi(const LaunchArgs& a, int kind, const float* verts, cons
         case 2: return multi_one<IsectAlphaTex>(a, verts, idx, nh);
         case 3: return multi_one<IsectProcAlpha>(a, verts, idx, nh);
         case 4: return multi_one<IsectCount>(a, verts, idx, nh);
+        case 5: return multi_one<IsectClip>(a, verts, idx, nh);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
                     h = H();
                     st = Stats();
                     has = true;
-                    if (!traverse_start<Q, H, STATS>(sc, r, h, best, st, ref, sp, steps)) finish();
+                    if (!traverse_start<Q, H, STATS>(sc, ip, r, h, best, st, ref, sp, steps))
+                        finish();
                 }
             }
         }
@@ -154,6 +155,7 @@ cudaError_t launch_kind(const LaunchArgs& a, int kind) {
         case 2: return launch_one<Q, IsectAlphaTex, STATS>(a);
         case 3: return launch_one<Q, IsectProcAlpha, STATS>(a);
         case 4: return launch_one<Q, IsectCount, STATS>(a);
+        case 5: return launch_one<Q, IsectClip, STATS>(a);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -106,6 +106,7 @@ struct IsectParams {
     float cutoff_f;
     float freq;
     uint32_t kind;
+    float clip_lo[3], clip_hi[3];  // clip-box intersector
 };
 
 // --------------------------------------------------------------------------
@@ -240,13 +241,19 @@ __device__ __forceinline__ bool proc_alpha_accept(const DevScene& sc, const Isec
 // statically injected intersectors: hooks on every box test and triangle
 // test, and a verdict on each geometric candidate ("hr.hit &= ...").
 
+// Hooks: begin() sees the ray once; box() and tri() run on every box and
+// triangle test (bvh_costs); keep() may turn a box the ray hits into a miss
+// (the intersector's intersect(ray, aabb) overload, Section 3.2); accept()
+// gives the verdict on a candidate hit at distance t.
 struct IsectNone {
     static constexpr bool kCounts = false;
     static constexpr bool kTexcoords = false;  // reads geom id and texcoords
+    __device__ __forceinline__ void begin(const Ray&) {}
     __device__ __forceinline__ void box() {}
     __device__ __forceinline__ void tri() {}
+    __device__ __forceinline__ bool keep(const IsectParams&, float4, float4) const { return true; }
     __device__ __forceinline__ bool accept(const DevScene&, const IsectParams&, uint32_t, float,
-                                           float) {
+                                           float, float) {
         return true;
     }
     __device__ __forceinline__ uint2 counters() const { return make_uint2(0, 0); }
@@ -258,7 +265,7 @@ struct IsectDefault : IsectNone {};
 struct IsectAlphaTex : IsectNone {
     static constexpr bool kTexcoords = true;
     __device__ __forceinline__ bool accept(const DevScene& sc, const IsectParams& ip,
-                                           uint32_t prim, float u, float v) {
+                                           uint32_t prim, float u, float v, float) {
         return alpha_tex_accept(sc, ip, prim, u, v);
     }
 };
@@ -266,7 +273,7 @@ struct IsectAlphaTex : IsectNone {
 struct IsectProcAlpha : IsectNone {
     static constexpr bool kTexcoords = true;
     __device__ __forceinline__ bool accept(const DevScene& sc, const IsectParams& ip,
-                                           uint32_t prim, float u, float v) {
+                                           uint32_t prim, float u, float v, float) {
         return proc_alpha_accept(sc, ip, prim, u, v);
     }
 };
@@ -278,6 +285,32 @@ struct IsectCount : IsectNone {
     __device__ __forceinline__ void box() { ++num_boxes; }
     __device__ __forceinline__ void tri() { ++num_tris; }
     __device__ __forceinline__ uint2 counters() const { return make_uint2(num_boxes, num_tris); }
+};
+
+// Clip box: a node box that does not overlap [clip_lo, clip_hi] counts as
+// missed (its subtree is skipped), and a candidate is accepted iff its hit
+// point fmaf(t, d, o) lies in the closed box.
+struct IsectClip : IsectNone {
+    float ox, oy, oz, dx, dy, dz;
+    __device__ __forceinline__ void begin(const Ray& r) {
+        ox = r.ox;
+        oy = r.oy;
+        oz = r.oz;
+        dx = r.dx;
+        dy = r.dy;
+        dz = r.dz;
+    }
+    __device__ __forceinline__ bool keep(const IsectParams& ip, float4 lo, float4 hi) const {
+        return lo.x <= ip.clip_hi[0] && hi.x >= ip.clip_lo[0] && lo.y <= ip.clip_hi[1] &&
+               hi.y >= ip.clip_lo[1] && lo.z <= ip.clip_hi[2] && hi.z >= ip.clip_lo[2];
+    }
+    __device__ __forceinline__ bool accept(const DevScene&, const IsectParams& ip, uint32_t,
+                                           float, float, float t) {
+        const float px = __fmaf_rn(t, dx, ox), py = __fmaf_rn(t, dy, oy),
+                    pz = __fmaf_rn(t, dz, oz);
+        return px >= ip.clip_lo[0] && px <= ip.clip_hi[0] && py >= ip.clip_lo[1] &&
+               py <= ip.clip_hi[1] && pz >= ip.clip_lo[2] && pz <= ip.clip_hi[2];
+    }
 };
 
 // Measurement counters: box tests, triangle tests, intersector
@@ -371,9 +404,10 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
                                               uint32_t* stack, uint32_t stride) {
     best.init(r.tmax);
     if (sc.nprims == 0) return;
+    h.begin(r);
     h.box();
     if (STATS) st.boxes++;
-    if (!box_hit(r, sc.root_a, sc.root_b, best.t)) return;
+    if (!box_hit(r, sc.root_a, sc.root_b, best.t) || !h.keep(ip, sc.root_a, sc.root_b)) return;
     uint32_t ref = sc.root_ref;
     uint32_t sp = 0;
     uint32_t steps = 0;
@@ -389,8 +423,8 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
             h.box();
             h.box();
             if (STATS) st.boxes += 2;
-            const bool hl = box_hit(r, la, lb, tfar);
-            const bool hr = box_hit(r, ra, rb, tfar);
+            const bool hl = box_hit(r, la, lb, tfar) && h.keep(ip, la, lb);
+            const bool hr = box_hit(r, ra, rb, tfar) && h.keep(ip, ra, rb);
             const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(ra.w);
             if (hl && hr) {
                 const bool neg = (r.negmask >> (ref & 3u)) & 1u;
@@ -438,7 +472,7 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
                     st.cands++;
                     if (H::kTexcoords && VSR_LDG(sc.geom + prim) != kMiss) st.texs++;
                 }
-                if (!h.accept(sc, ip, prim, u, v)) continue;
+                if (!h.accept(sc, ip, prim, u, v, t)) continue;
                 best.take(t, u, v, prim);
                 if (Q == kAny) return;
             }
@@ -470,16 +504,18 @@ __device__ __forceinline__ void traverse(const DevScene& sc, const IsectParams& 
 // next node) and returns true when the ray has finished.  Composed, they
 // visit nodes and primitives in exactly the order of traverse_body.
 template <int Q, class H, bool STATS>
-__device__ __forceinline__ bool traverse_start(const DevScene& sc, const Ray& r, H& h, Best& best,
-                                               Stats& st, uint32_t& ref, uint32_t& sp,
-                                               uint32_t& steps) {
+__device__ __forceinline__ bool traverse_start(const DevScene& sc, const IsectParams& ip,
+                                               const Ray& r, H& h, Best& best, Stats& st,
+                                               uint32_t& ref, uint32_t& sp, uint32_t& steps) {
     best.init(r.tmax);
     sp = 0;
     steps = 0;
     if (sc.nprims == 0) return false;
+    h.begin(r);
     h.box();
     if (STATS) st.boxes++;
-    if (!box_hit(r, sc.root_a, sc.root_b, best.t)) return false;
+    if (!box_hit(r, sc.root_a, sc.root_b, best.t) || !h.keep(ip, sc.root_a, sc.root_b))
+        return false;
     ref = sc.root_ref;
     return true;
 }
@@ -496,8 +532,8 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
         h.box();
         h.box();
         if (STATS) st.boxes += 2;
-        const bool hl = box_hit(r, la, lb, tfar);
-        const bool hr = box_hit(r, ra, rb, tfar);
+        const bool hl = box_hit(r, la, lb, tfar) && h.keep(ip, la, lb);
+        const bool hr = box_hit(r, ra, rb, tfar) && h.keep(ip, ra, rb);
         const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(ra.w);
         if (hl && hr) {
             const bool neg = (r.negmask >> (ref & 3u)) & 1u;
@@ -543,7 +579,7 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
             st.cands++;
             if (H::kTexcoords && VSR_LDG(sc.geom + prim) != kMiss) st.texs++;
         }
-        if (!h.accept(sc, ip, prim, u, v)) continue;
+        if (!h.accept(sc, ip, prim, u, v, t)) continue;
         best.take(t, u, v, prim);
         if (Q == kAny) return true;
     }

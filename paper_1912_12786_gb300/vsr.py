@@ -27,7 +27,7 @@ STATUS_NAMES = ["VSR_OK", "VSR_ERR_ARG", "VSR_ERR_CUDA", "VSR_ERR_OOM", "VSR_ERR
                 "VSR_ERR_STACK", "VSR_ERR_TIMEOUT", "VSR_ERR_STATE"]
 MISS = 0xFFFFFFFF
 NO_TEXTURE = 0xFFFFFFFF
-ISECT = {"none": 0, "default": 1, "alpha_tex": 2, "proc_alpha": 3, "count": 4}
+ISECT = {"none": 0, "default": 1, "alpha_tex": 2, "proc_alpha": 3, "count": 4, "clip": 5}
 DISPATCH = {"static": 0, "dynamic": 1}
 QUERY = {"closest": 0, "any": 1}
 TEX_FMT = {"u8": 0, "rgba8": 1, "rgba32f": 2}
@@ -48,7 +48,8 @@ class vsr_texture_desc(ctypes.Structure):
 class vsr_intersector(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("dispatch", ctypes.c_int32),
                 ("alpha_cutoff_u8", ctypes.c_uint32), ("alpha_cutoff_f", ctypes.c_float),
-                ("proc_freq", ctypes.c_float), ("reserved", ctypes.c_uint32 * 3)]
+                ("proc_freq", ctypes.c_float), ("clip_lo", ctypes.c_float * 3),
+                ("clip_hi", ctypes.c_float * 3)]
 
 
 class vsr_trace_params(ctypes.Structure):
@@ -143,8 +144,9 @@ def vsr_version() -> int:
 
 
 def intersector(kind="default", dispatch="static", cutoff_u8=128, cutoff_f=0.01,
-                freq=40.0) -> vsr_intersector:
-    return vsr_intersector(ISECT[kind], DISPATCH[dispatch], cutoff_u8, cutoff_f, freq)
+                freq=40.0, clip_lo=(0.0, 0.0, 0.0), clip_hi=(0.0, 0.0, 0.0)) -> vsr_intersector:
+    return vsr_intersector(ISECT[kind], DISPATCH[dispatch], cutoff_u8, cutoff_f, freq,
+                           (ctypes.c_float * 3)(*clip_lo), (ctypes.c_float * 3)(*clip_hi))
 
 
 def trace_params(block_size=128, persistent=0, refill_threshold=16, blocks_per_sm=0,
