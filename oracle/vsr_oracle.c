@@ -76,9 +76,12 @@
  *   - procedural alpha: accept iff sinf(f*uv.x) * sinf(f*uv.y) > 0;
  *   - clip box (Section 3.2: an intersector may also replace intersect(ray,
  *     aabb) for the BVH's node boxes): a candidate is accepted iff its hit
- *     point p = fmaf(t, d, o) (per component) lies in the closed clip box, and
- *     a node box that does not overlap the clip box counts as missed, which
- *     skips its subtree without changing any answer.
+ *     point p = fmaf(t, d, o) (per component) lies in the closed clip box; a
+ *     node box that does not overlap the clip box counts as missed, and the
+ *     far limit of every node box test is also capped at the distance where
+ *     the ray leaves the clip box (the slab test above with the clip box, -inf
+ *     when the ray misses it).  Neither changes an answer away from hit
+ *     points within rounding of a clip face, which are flagged as near ties.
  */
 #include <math.h>
 #include <pthread.h>
@@ -243,6 +246,20 @@ static int box_keep(const orc_isect* is, const float lo[3], const float hi[3]) {
     for (int a = 0; a < 3; ++a)
         if (lo[a] > is->clip_hi[a] || hi[a] < is->clip_lo[a]) return 0;
     return 1;
+}
+
+/* Far limit of node box tests under the intersector: the clip box caps it at
+ * the ray's exit distance from the box. */
+static float clip_exit(const orc_ray_ctx* c, const orc_isect* is) {
+    if (is->kind != ORC_ISECT_CLIP) return INFINITY;
+    float tn = -INFINITY, tf = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        const float t0 = fmaf(is->clip_lo[a], c->invd[a], -c->ood[a]);
+        const float t1 = fmaf(is->clip_hi[a], c->invd[a], -c->ood[a]);
+        tn = fmaxf(tn, fminf(t0, t1));
+        tf = fminf(tf, fmaxf(t0, t1));
+    }
+    return tn <= tf ? tf : -INFINITY;
 }
 
 /* The intersector's verdict on a geometric candidate at distance t along
@@ -483,8 +500,9 @@ static void bvh_query(const orc_scene* s, const orc_bvh* b, const orc_isect* is,
     uint32_t stack[72];
     int sp = 0;
     if (b->num_prims == 0) goto done;
+    const float cap = clip_exit(&c, is);
     st->boxes++;
-    if (!intersect_aabb(&c, b->nodes[0].lo, b->nodes[0].hi, last->t) ||
+    if (!intersect_aabb(&c, b->nodes[0].lo, b->nodes[0].hi, fminf(last->t, cap)) ||
         !box_keep(is, b->nodes[0].lo, b->nodes[0].hi))
         goto done;
     uint32_t node = 0;
@@ -492,7 +510,7 @@ static void bvh_query(const orc_scene* s, const orc_bvh* b, const orc_isect* is,
         while ((b->nodes[node].count_axis >> 2) == 0) { /* while node is inner */
             const orc_node* nd = &b->nodes[node];
             const uint32_t l = nd->left_or_first, r = l + 1;
-            const float far_t = (query != ORC_ANY) ? last->t : ray->tmax;
+            const float far_t = fminf((query != ORC_ANY) ? last->t : ray->tmax, cap);
             st->boxes += 2;
             const int hl = intersect_aabb(&c, b->nodes[l].lo, b->nodes[l].hi, far_t) &&
                            box_keep(is, b->nodes[l].lo, b->nodes[l].hi);

@@ -76,7 +76,8 @@ struct IsectDynamic {
     CountFn on_box = nullptr, on_tri = nullptr;
     const DevScene* user = nullptr;
     uint32_t boxes = 0, tris = 0;
-    __device__ __forceinline__ void begin(const Ray&) {}
+    __device__ __forceinline__ void begin(const Ray&, const IsectParams&) {}
+    __device__ __forceinline__ float far(float tfar) const { return tfar; }
     __device__ __forceinline__ void box() {
         if (on_box) boxes = on_box(boxes);
     }

@@ -242,15 +242,17 @@ __device__ __forceinline__ bool proc_alpha_accept(const DevScene& sc, const Isec
 // test, and a verdict on each geometric candidate ("hr.hit &= ...").
 
 // Hooks: begin() sees the ray once; box() and tri() run on every box and
-// triangle test (bvh_costs); keep() may turn a box the ray hits into a miss
-// (the intersector's intersect(ray, aabb) overload, Section 3.2); accept()
-// gives the verdict on a candidate hit at distance t.
+// triangle test (bvh_costs); far() may lower the far limit of node box tests
+// and keep() may turn a box the ray hits into a miss (both part of the
+// intersector's intersect(ray, aabb) overload, Section 3.2); accept() gives
+// the verdict on a candidate hit at distance t.
 struct IsectNone {
     static constexpr bool kCounts = false;
     static constexpr bool kTexcoords = false;  // reads geom id and texcoords
-    __device__ __forceinline__ void begin(const Ray&) {}
+    __device__ __forceinline__ void begin(const Ray&, const IsectParams&) {}
     __device__ __forceinline__ void box() {}
     __device__ __forceinline__ void tri() {}
+    __device__ __forceinline__ float far(float tfar) const { return tfar; }
     __device__ __forceinline__ bool keep(const IsectParams&, float4, float4) const { return true; }
     __device__ __forceinline__ bool accept(const DevScene&, const IsectParams&, uint32_t, float,
                                            float, float) {
@@ -288,18 +290,29 @@ struct IsectCount : IsectNone {
 };
 
 // Clip box: a node box that does not overlap [clip_lo, clip_hi] counts as
-// missed (its subtree is skipped), and a candidate is accepted iff its hit
-// point fmaf(t, d, o) lies in the closed box.
+// missed (its subtree is skipped), node box tests stop where the ray leaves
+// the clip box, and a candidate is accepted iff its hit point fmaf(t, d, o)
+// lies in the closed box.
 struct IsectClip : IsectNone {
-    float ox, oy, oz, dx, dy, dz;
-    __device__ __forceinline__ void begin(const Ray& r) {
+    float ox, oy, oz, dx, dy, dz, t_exit;
+    __device__ __forceinline__ void begin(const Ray& r, const IsectParams& ip) {
         ox = r.ox;
         oy = r.oy;
         oz = r.oz;
         dx = r.dx;
         dy = r.dy;
         dz = r.dz;
+        const float t0x = __fmaf_rn(ip.clip_lo[0], r.ix, r.nox);
+        const float t1x = __fmaf_rn(ip.clip_hi[0], r.ix, r.nox);
+        const float t0y = __fmaf_rn(ip.clip_lo[1], r.iy, r.noy);
+        const float t1y = __fmaf_rn(ip.clip_hi[1], r.iy, r.noy);
+        const float t0z = __fmaf_rn(ip.clip_lo[2], r.iz, r.noz);
+        const float t1z = __fmaf_rn(ip.clip_hi[2], r.iz, r.noz);
+        const float tn = fmax3(fminf(t0x, t1x), fminf(t0y, t1y), fminf(t0z, t1z));
+        const float tf = fmin3(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fmaxf(t0z, t1z));
+        t_exit = tn <= tf ? tf : __int_as_float(0xff800000);
     }
+    __device__ __forceinline__ float far(float tfar) const { return fminf(tfar, t_exit); }
     __device__ __forceinline__ bool keep(const IsectParams& ip, float4 lo, float4 hi) const {
         return lo.x <= ip.clip_hi[0] && hi.x >= ip.clip_lo[0] && lo.y <= ip.clip_hi[1] &&
                hi.y >= ip.clip_lo[1] && lo.z <= ip.clip_hi[2] && hi.z >= ip.clip_lo[2];
@@ -404,10 +417,11 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
                                               uint32_t* stack, uint32_t stride) {
     best.init(r.tmax);
     if (sc.nprims == 0) return;
-    h.begin(r);
+    h.begin(r, ip);
     h.box();
     if (STATS) st.boxes++;
-    if (!box_hit(r, sc.root_a, sc.root_b, best.t) || !h.keep(ip, sc.root_a, sc.root_b)) return;
+    if (!box_hit(r, sc.root_a, sc.root_b, h.far(best.t)) || !h.keep(ip, sc.root_a, sc.root_b))
+        return;
     uint32_t ref = sc.root_ref;
     uint32_t sp = 0;
     uint32_t steps = 0;
@@ -419,7 +433,7 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
         while (!(ref & kLeafBit)) {
             const float4* p = sc.nodes + 4ull * (ref >> 2);
             const float4 la = VSR_LDG(p), lb = VSR_LDG(p + 1), ra = VSR_LDG(p + 2), rb = VSR_LDG(p + 3);
-            const float tfar = (Q == kClosest) ? best.t : r.tmax;
+            const float tfar = h.far((Q == kClosest) ? best.t : r.tmax);
             h.box();
             h.box();
             if (STATS) st.boxes += 2;
@@ -511,10 +525,10 @@ __device__ __forceinline__ bool traverse_start(const DevScene& sc, const IsectPa
     sp = 0;
     steps = 0;
     if (sc.nprims == 0) return false;
-    h.begin(r);
+    h.begin(r, ip);
     h.box();
     if (STATS) st.boxes++;
-    if (!box_hit(r, sc.root_a, sc.root_b, best.t) || !h.keep(ip, sc.root_a, sc.root_b))
+    if (!box_hit(r, sc.root_a, sc.root_b, h.far(best.t)) || !h.keep(ip, sc.root_a, sc.root_b))
         return false;
     ref = sc.root_ref;
     return true;
@@ -528,7 +542,7 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
     while (!(ref & kLeafBit)) {  // bounded as in traverse_body
         const float4* p = sc.nodes + 4ull * (ref >> 2);
         const float4 la = VSR_LDG(p), lb = VSR_LDG(p + 1), ra = VSR_LDG(p + 2), rb = VSR_LDG(p + 3);
-        const float tfar = (Q == kClosest) ? best.t : r.tmax;
+        const float tfar = h.far((Q == kClosest) ? best.t : r.tmax);
         h.box();
         h.box();
         if (STATS) st.boxes += 2;
