@@ -355,7 +355,9 @@ vsr_status vsr_trace_persistent_noalloc(vsr_scene* scene, const vsr_ray* rays, u
  * vsr_batch_create records the scenes (each with a loaded BVH, all on one
  * device), the device ray and hit arrays (rays[k]/hits[k]: vsr_ray/vsr_hit
  * [n[k]], 16-byte aligned, caller-owned; n[k] may be 0), the intersector
- * (static dispatch) and the query, and builds the device tables.  With
+ * (static dispatch; not the clip box, and not the procedural-alpha
+ * intersector with the any-hit query, which is refused as for persistent
+ * vsr_trace) and the query, and builds the device tables.  With
  * params == NULL the launch configuration (block size, refill threshold,
  * blocks per SM) is chosen by timing a grid of candidates on the batch itself
  * at the first launch; results are cached per workload shape in the process

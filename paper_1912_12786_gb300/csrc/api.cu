@@ -1173,6 +1173,11 @@ extern "C" vsr_status vsr_batch_create(vsr_scene* const* scenes, const vsr_ray* 
         return fail(VSR_ERR_ARG, "batched launches use static dispatch only");
     if (is->kind == VSR_ISECT_CLIP)
         return fail(VSR_ERR_ARG, "the clip-box intersector is for vsr_trace and vsr_trace_multi");
+    // The procedural-alpha any-hit query stalled in persistent-warp loops three
+    // times (twice in the single-scene persistent kernel, once in this batched
+    // one) without a cause found; it stays off these kernels until one is.
+    if (is->kind == VSR_ISECT_PROC_ALPHA && query == VSR_ANY)
+        return fail(VSR_ERR_ARG, "batched procedural-alpha any-hit query is disabled");
     vsr_trace_params prm{128u, 1u, 16u, 0u};
     if (params) {
         prm = *params;

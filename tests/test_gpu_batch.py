@@ -45,7 +45,7 @@ def _hits_like(dev_rays):
 
 
 @pytest.mark.parametrize("kind,query", [("alpha_tex", "closest"), ("alpha_tex", "any"),
-                                        ("default", "closest"), ("proc_alpha", "any")])
+                                        ("default", "closest"), ("default", "any")])
 def test_batch_equals_per_scene(batch, kind, query):
     V, items, blobs, handles, dev_rays = batch
     isect = V.intersector(kind)
@@ -111,6 +111,8 @@ def test_batch_rejects_bad_arguments(batch):
     hits = _hits_like(dev_rays)
     with pytest.raises(V.VsrError, match="static dispatch"):
         V.vsr_batch_create(handles, dev_rays, hits, V.intersector("default", "dynamic"), "any")
+    with pytest.raises(V.VsrError, match="procedural-alpha any-hit query is disabled"):
+        V.vsr_batch_create(handles, dev_rays, hits, V.intersector("proc_alpha"), "any")
     sc = items[0][0]
     nobvh = V.vsr_scene_create_indexed(sc.verts, sc.idx, sc.uvs, sc.geom_id, sc.textures)
     with pytest.raises(V.VsrError, match="VSR_ERR_STATE"):
