@@ -20,6 +20,9 @@ Intersectors to the C++ Ray Tracing Template Library Visionaray"):
 * ``trace_instances`` -- instancing (Section 3.2: BVHs as compound primitives
   of a list or of a top-level BVH, the intersector passed on to each BVH's
   own intersect), rays taken to object space by a world-to-object map.
+* ``path_trace`` -- a diffuse path tracer on the closest-hit query with the
+  intersector (a workload; FP32 with the bounce construction's operation
+  order fixed so that every bounce is reproducible).
 * intersector kinds follow Section 3.1 (default forwarding), Section 4
   (alpha-mask listing, procedural alpha, ``bvh_costs``) and Section 3.2 (an
   intersector that also replaces intersect(ray, aabb): the clip box).
@@ -93,6 +96,9 @@ def _load():
         lib.orc_trace_instances.argtypes = [P, P, P, ctypes.c_uint32, P, P, ctypes.c_uint32, P,
                                             ctypes.c_uint64, P, ctypes.c_int, P, ctypes.c_uint64,
                                             P, P, P, ctypes.c_int]
+        lib.orc_path_trace.argtypes = [P, P, ctypes.c_uint64, P, P, ctypes.c_uint64,
+                                       ctypes.c_uint32, P, ctypes.c_float, P, P, P, P,
+                                       ctypes.c_int]
         lib.orc_intersect_triangle.argtypes = [P, P, P, P, P]
         lib.orc_intersect_aabb.argtypes = [P, P, P, ctypes.c_float]
         lib.orc_shadow_rays.argtypes = [P, P, ctypes.c_uint64, P, ctypes.c_float, P]
@@ -242,6 +248,35 @@ def trace_instances(meshes, inst_mesh, w2o, rays, kind="default", query="closest
     if rc != 0:
         raise ValueError(f"oracle rejected its inputs (code {rc})")
     return split_hits(hits), ids, stats
+
+
+def path_trace(scene, blob, rays, bounces: int, dirs, eps: float, sky=(1.0, 1.0, 1.0),
+               untex=(0.8, 0.8, 0.8), kind="default", nthreads=None, **kw):
+    """Diffuse path tracing with the intersector (FP32, fixed operation order):
+    returns (radiance float32 [n, 3], near-tie flags uint32 [n]).  dirs:
+    float32 [n * bounces, 3] local unit directions, path i's bounce k at
+    row i * bounces + k."""
+    lib = _load()
+    sh = _SceneHandle(scene)
+    rays = np.ascontiguousarray(rays, np.float32).reshape(-1, 8)
+    n = rays.shape[0]
+    d = np.ascontiguousarray(dirs, np.float32).reshape(-1, 3)
+    assert d.shape[0] == n * bounces
+    b = np.ascontiguousarray(np.frombuffer(blob, np.uint8) if not isinstance(blob, np.ndarray)
+                             else blob)
+    sk = np.ascontiguousarray(sky, np.float32)
+    ut = np.ascontiguousarray(untex, np.float32)
+    rad = np.zeros((n, 3), np.float32)
+    flags = np.zeros(n, np.uint32)
+    isect = _isect(kind, **kw)
+    if nthreads is None:
+        nthreads = len(os.sched_getaffinity(0))
+    rc = lib.orc_path_trace(ctypes.byref(sh.c), _ptr(b), b.nbytes, ctypes.byref(isect), _ptr(rays),
+                            n, bounces, _ptr(d) if d.size else None, float(eps), _ptr(sk),
+                            _ptr(ut), _ptr(rad), _ptr(flags), nthreads)
+    if rc != 0:
+        raise ValueError(f"oracle rejected its inputs (code {rc})")
+    return rad, flags
 
 
 def intersect_triangle(ray, v0, v1, v2):

@@ -922,6 +922,151 @@ void orc_shadow_rays(const float* prim_rays, const float* prim_hits, uint64_t n,
  * frame and direction are evaluated in FP64 and rounded to FP32; interval
  * (eps, tmax).  Primary misses give inactive rays (origin 0, direction
  * (0, 0, 1), tmin 0, tmax -1).  Output ray i*spp + k. */
+/* ------------------------------------------------------------------ */
+/* Path tracing with the intersector: a diffuse path tracer built on    */
+/* the closest-hit query (a workload; the paper has no shading).  FP32  */
+/* with the operation order fixed so that every bounce is reproducible. */
+
+/* Albedo at a hit: the colour of the nearest texel (the one the alpha
+ * decision reads) of a colour texture (RGBA8 / 255, RGBA32F as stored), or
+ * `untex` for untextured triangles and alpha-only (u8) textures. */
+static void hit_albedo(const orc_scene* s, uint32_t prim, float u, float v, const float untex[3],
+                       float out[3]) {
+    const uint32_t g = s->geom_id[prim];
+    if (g == ORC_NONE || s->tex[g].fmt == ORC_TEX_U8) {
+        for (int c = 0; c < 3; ++c) out[c] = untex[c];
+        return;
+    }
+    float x, y;
+    lerp_texcoord(s, prim, u, v, &x, &y);
+    const orc_texture* tx = &s->tex[g];
+    const uint64_t k = (uint64_t)texel_index(y, tx->h) * tx->w + texel_index(x, tx->w);
+    for (int c = 0; c < 3; ++c)
+        out[c] = tx->fmt == ORC_TEX_RGBA8 ? (float)((const uint8_t*)tx->texels)[4 * k + c] / 255.0f
+                                          : ((const float*)tx->texels)[4 * k + c];
+}
+
+/* Diffuse bounce from hit h of ray r along the local unit vector l: origin
+ * fmaf(t, d, o); face normal m = e1 x e2 (the triangle test's cross),
+ * n = m / sqrtf(m . m) (IEEE square root and division; (0, 0, 1) when m = 0),
+ * turned against d when n . d > 0; tangent frame of Duff et al. (2017):
+ * s = copysignf(1, n.z), a = -1 / (s + n.z), b = (n.x n.y) a,
+ * t1 = (1 + ((s n.x) n.x) a, s b, -(s n.x)), t2 = (b, s + (n.y n.y) a, -n.y);
+ * direction fmaf(l.x, t1, fmaf(l.y, t2, l.z n)); interval (eps, +inf). */
+static void bounce_ray(const orc_scene* s, const orc_ray* r, const orc_hit* h, const float l[3],
+                       float eps, orc_ray* out) {
+    float v0[3], e1[3], e2[3], m[3], n[3];
+    tri_verts(s, h->prim, v0, e1, e2);
+    cross3(e1, e2, m);
+    const float len = sqrtf(dot3(m, m));
+    for (int k = 0; k < 3; ++k) n[k] = len > 0.0f ? m[k] / len : (k == 2 ? 1.0f : 0.0f);
+    if (dot3(n, r->d) > 0.0f)
+        for (int k = 0; k < 3; ++k) n[k] = -n[k];
+    const float sg = copysignf(1.0f, n[2]);
+    const float a = -1.0f / (sg + n[2]);
+    const float b = (n[0] * n[1]) * a;
+    const float sx = sg * n[0];
+    const float t1[3] = {1.0f + (sx * n[0]) * a, sg * b, -sx};
+    const float t2[3] = {b, sg + (n[1] * n[1]) * a, -n[1]};
+    for (int k = 0; k < 3; ++k) {
+        out->o[k] = fmaf(h->t, r->d[k], r->o[k]);
+        out->d[k] = fmaf(l[0], t1[k], fmaf(l[1], t2[k], l[2] * n[k]));
+    }
+    out->tmin = eps;
+    out->tmax = INFINITY;
+}
+
+/* One path: closest hit with the intersector; a miss returns throughput x
+ * sky; a hit multiplies the throughput by the albedo and, before `bounces`
+ * bounces are spent, continues along dirs[3k..3k+3); after the last bounce's
+ * hit the path returns 0. */
+static void path_query(const orc_scene* s, const orc_bvh* b, const orc_isect* is,
+                       const orc_ray* ray, uint32_t bounces, const float* dirs, float eps,
+                       const float sky[3], const float untex[3], float out[3], uint32_t* flags) {
+    float f[3] = {1.0f, 1.0f, 1.0f};
+    orc_ray cur = *ray;
+    out[0] = out[1] = out[2] = 0.0f;
+    *flags = 0;
+    for (uint32_t k = 0;; ++k) {
+        orc_hit h;
+        orc_stats st;
+        bvh_query(s, b, is, ORC_CLOSEST, 1, &cur, &h, &st);
+        *flags |= st.flags;
+        if (h.prim == ORC_NONE) {
+            for (int c = 0; c < 3; ++c) out[c] = f[c] * sky[c];
+            return;
+        }
+        float alb[3];
+        hit_albedo(s, h.prim, h.u, h.v, untex, alb);
+        for (int c = 0; c < 3; ++c) f[c] = f[c] * alb[c];
+        if (k == bounces) return;
+        orc_ray next;
+        bounce_ray(s, &cur, &h, dirs + 3ull * k, eps, &next);
+        cur = next;
+    }
+}
+
+typedef struct {
+    const orc_scene* s;
+    const orc_bvh* b;
+    const orc_isect* is;
+    const orc_ray* rays;
+    uint32_t bounces;
+    const float *dirs, *sky, *untex;
+    float eps;
+    float* radiance;
+    uint32_t* flags;
+    uint64_t begin, end;
+} orc_path_job;
+
+static void* run_path_job(void* arg) {
+    orc_path_job* j = (orc_path_job*)arg;
+    for (uint64_t i = j->begin; i < j->end; ++i) {
+        uint32_t fl;
+        path_query(j->s, j->b, j->is, &j->rays[i], j->bounces,
+                   j->dirs + 3ull * j->bounces * i, j->eps, j->sky, j->untex,
+                   j->radiance + 3 * i, &fl);
+        if (j->flags) j->flags[i] = fl;
+    }
+    return NULL;
+}
+
+/* Path tracing over a BVH: radiance [n*3]; dirs [n*bounces*3] local unit
+ * vectors (path i's bounce k at 3*(i*bounces + k)); flags [n] the OR of the
+ * near-tie flags of every segment, or NULL. */
+int orc_path_trace(const orc_scene* s, const uint8_t* blob, uint64_t bytes, const orc_isect* is,
+                   const float* rays, uint64_t n, uint32_t bounces, const float* dirs, float eps,
+                   const float* sky, const float* untex, float* radiance, uint32_t* flags,
+                   int nthreads) {
+    if (!s || !is || !sky || !untex || (n && (!rays || !radiance)) ||
+        (n && bounces && !dirs))
+        return -1;
+    orc_bvh b;
+    int rc = parse_blob(blob, bytes, &b);
+    if (rc) return rc;
+    if (b.num_prims != s->ntri) return -6;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if ((uint64_t)nthreads > n) nthreads = n > 0 ? (int)n : 1;
+    pthread_t th[256];
+    orc_path_job jobs[256];
+    for (int k = 0; k < nthreads; ++k) {
+        orc_path_job j = {s, &b, is, (const orc_ray*)rays, bounces, dirs, sky, untex, eps,
+                          radiance, flags, n * (uint64_t)k / (uint64_t)nthreads,
+                          n * (uint64_t)(k + 1) / (uint64_t)nthreads};
+        jobs[k] = j;
+    }
+    int started = 0;
+    for (int k = 1; k < nthreads; ++k) {
+        if (pthread_create(&th[k], NULL, run_path_job, &jobs[k]) != 0) break;
+        started = k;
+    }
+    run_path_job(&jobs[0]);
+    for (int k = started + 1; k < nthreads; ++k) run_path_job(&jobs[k]);
+    for (int k = 1; k <= started; ++k) pthread_join(th[k], NULL);
+    return 0;
+}
+
 void orc_ao_rays(const orc_scene* s, const float* prim_rays, const float* prim_hits, uint64_t n,
                  uint32_t spp, const float* xi, float tmax, float eps, float* out) {
     for (uint64_t i = 0; i < n; ++i) {

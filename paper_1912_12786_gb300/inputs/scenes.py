@@ -646,6 +646,18 @@ def large_incoherent(seed: int = SEED_BASE + 4, n_quads: int = 7_000_000, ground
     return scene, rays
 
 
+def path_dirs(n_paths: int, bounces: int, seed: int = SEED_BASE + 8) -> np.ndarray:
+    """Cosine-distributed unit directions in a local frame (z up) for the
+    diffuse bounces of path tracing, float32 [n_paths * bounces, 3] (path i's
+    bounce k at row i * bounces + k); drawn in float64 and rounded."""
+    rng = np.random.default_rng(seed)
+    x1 = rng.uniform(0.0, 1.0, n_paths * bounces)
+    x2 = rng.uniform(0.0, 1.0, n_paths * bounces)
+    r = np.sqrt(x1)
+    d = np.stack([r * np.cos(2 * np.pi * x2), r * np.sin(2 * np.pi * x2), np.sqrt(1.0 - x1)], 1)
+    return d.astype(np.float32)
+
+
 def ao_random(n_rays: int, spp: int, seed: int = SEED_BASE + 5) -> np.ndarray:
     """Uniform random numbers in [0, 1) for ambient-occlusion sampling,
     float32 [n_rays * spp, 2]; passed to both the GPU and the oracle."""
