@@ -431,6 +431,7 @@ def run_ours(args):
         out["breakdown"] = breakdown(V, s, d_rays, rays_s, n, flush, stream, torch)
         out["multi_hit"] = multi_hit(V, s, d_rays, n, flush, stream, torch)
         out["instanced"] = instanced_bench(V, torch, dev, flush, stream, args.steps)
+        out["path"] = path_bench(V, s, sc, d_rays, n, flush, stream, torch, args.steps)
         out["fwd_bwd"] = fwd_bwd(V, torch, dev, flush, stream, args.steps, args.warmup)
         out["batch"] = batch_bench(V, torch, dev, flush, stream, args.steps)
         out["large"] = large_bench(V, torch, dev, flush, stream, args.steps)
@@ -516,6 +517,34 @@ def multi_hit(V, s, d_rays, n, flush, stream, torch, reps=5):
         res[f"n{nh}_ms"] = round(t, 4)
         res[f"n{nh}_hits_per_ray"] = round(found / n, 3)
     return res
+
+
+def path_bench(V, s, sc, d_rays, n, flush, stream, torch, steps, bounces=3):
+    """Diffuse path tracing of the forest frame: every segment a closest-hit
+    query with the alpha intersector (pixel tiles), 3 bounces, sky light."""
+    from paper_1912_12786_gb300.inputs import scenes
+    dirs = torch.from_numpy(scenes.path_dirs(n, bounces)).to(d_rays.device)
+    rad = torch.empty((n, 3), dtype=torch.float32, device=d_rays.device)
+    seg = torch.empty(n, dtype=torch.int32, device=d_rays.device)
+    alpha = V.intersector("alpha_tex")
+    pp = V.path_params(bounces, scenes.shadow_eps(sc), (0.7, 0.8, 1.0), (0.8, 0.75, 0.6))
+    p = default_params(V)
+    ms = []
+    for k in range(max(3, steps // 2) + 2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        V.vsr_path_trace(s, d_rays, alpha, pp, dirs, rad, seg, p, stream)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 2:
+            ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    segments = int(seg.sum().item())
+    return {"workload": f"{n} paths, {bounces} diffuse bounces, alpha texture, forest",
+            "ms_per_frame": round(t, 4), "Mpaths_s": round(n / (t / 1e3) / 1e6, 1),
+            "segments": segments, "Msegments_s": round(segments / (t / 1e3) / 1e6, 1),
+            "gpu_launches_per_frame": 1 + 2 * (bounces + 1)}
 
 
 def instanced_bench(V, torch, dev, flush, stream, steps):

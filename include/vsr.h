@@ -227,7 +227,7 @@ vsr_status vsr_trace(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
 /*
  * Multi-hit query: the first max_hits accepted hits of each ray in ascending
  * (t, prim) order -- the third visibility query of the library the paper
- * extends (Section 1), with the custom intersector injected exactly as for
+ * extends (Section 3.1), with the custom intersector injected exactly as for
  * closest-hit (Section 3.2).  The traversal is the closest-hit traversal whose
  * bound is the max_hits-th entry of a sorted buffer, so the intersector is
  * consulted for the candidates that would enter the buffer; max_hits == 1 is
@@ -243,6 +243,42 @@ vsr_status vsr_trace_multi(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
                            const vsr_intersector* isect, uint32_t max_hits, vsr_hit* hits,
                            uint32_t* counters, const vsr_trace_params* params,
                            vsr_stream stream);
+
+/* ----------------------------------------------------------- path tracing */
+
+/*
+ * Diffuse path tracing on the closest-hit query with the intersector: a
+ * workload of many incoherent segments through the same traversal (the paper
+ * has no shading; its default kernels include a path tracer, Section 3.1).
+ * Per path: a segment that misses returns throughput x sky; a hit multiplies
+ * the throughput by the albedo (the colour of the nearest texel, the one the
+ * alpha decision reads: RGBA8 / 255 or RGBA32F; `untextured` for untextured
+ * triangles and u8 textures) and, while bounces remain, continues from
+ * fmaf(t, d, o) over (eps, +inf) along the given local unit vector in the
+ * face's tangent frame (face normal e1 x e2 turned against d; frame of Duff
+ * et al. 2017); after `bounces` bounces the path returns 0.  FP32 with the
+ * operation order of vsr_path_trace's kernels fixed (IEEE sqrt and division).
+ *   rays      device vsr_ray [n], the primary segments
+ *   dirs      device float32 [n * bounces * 3]: path i's bounce k at
+ *             3 * (i * bounces + k), cosine-distributed for a diffuse surface
+ *   radiance  device float32 [n * 3], written
+ *   segments  device uint32 [n] or NULL: closest-hit queries path i made
+ *   params    one ray per thread (persistent 0); image_width applies to every
+ *             segment's launch (bounce segments stay at their pixel)
+ * One closest-hit launch per segment depth plus one shading launch, on
+ * `stream`; scratch (n * 60 bytes) comes from the stream-ordered allocator.
+ * Errors as vsr_trace.
+ */
+typedef struct vsr_path_params {
+    uint32_t bounces;      /* 0..64 */
+    float eps;             /* tmin of bounce segments, finite, >= 0 */
+    float sky[3];          /* finite */
+    float untextured[3];   /* finite */
+} vsr_path_params;
+vsr_status vsr_path_trace(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
+                          const vsr_intersector* isect, const vsr_path_params* path,
+                          const float* dirs, float* radiance, uint32_t* segments,
+                          const vsr_trace_params* params, vsr_stream stream);
 
 /* ------------------------------------------------------------- instancing */
 

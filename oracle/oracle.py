@@ -14,7 +14,7 @@ Intersectors to the C++ Ray Tracing Template Library Visionaray"):
 * ``trace_bvh``   -- the same queries through the while-while BVH traversal
   with both ``intersect`` calls replaced by the intersector (Section 3.2).
 * ``trace_multi`` -- the multi-hit query (the third visibility query of the
-  library the paper extends, Section 1): the first N accepted hits in
+  library the paper extends, Section 3.1): the first N accepted hits in
   ascending (t, prim) order, over the list as the plain definition (collect,
   sort, keep N) or through the BVH traversal with an N-entry buffer.
 * ``trace_instances`` -- instancing (Section 3.2: BVHs as compound primitives

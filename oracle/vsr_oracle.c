@@ -23,7 +23,7 @@
  *     (Section 3.2, after Aila and Laine 2009) in which both calls to
  *     intersect are replaced by the intersector;
  *   - the multi-hit query (the third visibility query of the library the
- *     paper extends, Section 1 and its citation of Zellmann et al. 2017): the
+ *     paper extends, defined in Section 3.1 next to closest-hit and any-hit): the
  *     first N accepted hits in ascending order.  Over a list it is the plain
  *     definition (collect every accepted candidate, sort, keep N); over the
  *     BVH it is the closest-hit traversal with a sorted buffer of N entries

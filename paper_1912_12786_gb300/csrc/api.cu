@@ -679,6 +679,14 @@ vsr_status vsr_get_device_error(vsr_scene* s, uint32_t* word) {
                 std::to_string(line);
     }
     line = 0;
+    VSR_CUDA(path_align_error(&line), "read alignment check");
+    if (line) {
+        *word |= kErrAlign;
+        g_err += (g_err.empty() ? "" : "; ") +
+                 std::string("path kernel skipped a misaligned load at path.cu/vsr_device.cuh line ") +
+                 std::to_string(line);
+    }
+    line = 0;
     VSR_CUDA(multi_align_error(&line), "read alignment check");
     if (line) {
         *word |= kErrAlign;
@@ -1550,5 +1558,78 @@ extern "C" vsr_status vsr_instances_device_error(vsr_instances* x, uint32_t* wor
         g_err = "instanced kernel skipped a misaligned access at "
                 "trace_instances.cu/vsr_device.cuh line " + std::to_string(line);
     }
+    return VSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Diffuse path tracing on the closest-hit query (path.cu): one trace launch
+// per segment depth over every path, then the shading launch.
+
+extern "C" vsr_status vsr_path_trace(vsr_scene* s, const vsr_ray* rays, uint64_t n,
+                                     const vsr_intersector* is, const vsr_path_params* pp,
+                                     const float* dirs, float* radiance, uint32_t* segments,
+                                     const vsr_trace_params* p, vsr_stream stream) {
+    g_err.clear();
+    if (!pp) return fail(VSR_ERR_ARG, "path parameters are null");
+    if (pp->bounces > 64) return fail(VSR_ERR_ARG, "bounces must be in 0..64");
+    if (!std::isfinite(pp->eps) || pp->eps < 0.0f)
+        return fail(VSR_ERR_ARG, "eps must be finite and >= 0");
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(pp->sky[c]) || !std::isfinite(pp->untextured[c]))
+            return fail(VSR_ERR_ARG, "non-finite sky or albedo");
+    if (p && p->persistent) return fail(VSR_ERR_ARG, "path tracing uses one ray per thread");
+    LaunchArgs a;
+    // n == 0 keeps prepare_launch's ray and hit checks out of the way
+    vsr_status st = prepare_launch(s, rays, 0, is, VSR_CLOSEST, nullptr, p, a);
+    if (st != VSR_OK) return st;
+    if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull)
+        return fail(VSR_ERR_ARG, "too many rays for one launch");
+    if (n == 0) return VSR_OK;
+    if ((st = check_dev(rays, s->device, "rays", 16, n * sizeof(vsr_ray))) != VSR_OK ||
+        (st = check_dev(radiance, s->device, "radiance", 4, n * 12)) != VSR_OK)
+        return st;
+    if (pp->bounces &&
+        (st = check_dev(dirs, s->device, "dirs", 4, n * pp->bounces * 12ull)) != VSR_OK)
+        return st;
+    if (segments && (st = check_dev(segments, s->device, "segments", 4, n * 4)) != VSR_OK)
+        return st;
+    st = make_map(n, p ? p->image_width : 0u, a.map);
+    if (st != VSR_OK) return st;
+    a.n = n;
+    PathDev pd{};
+    pd.bounces = pp->bounces;
+    pd.eps = pp->eps;
+    for (int c = 0; c < 3; ++c) {
+        pd.sky[c] = pp->sky[c];
+        pd.untex[c] = pp->untextured[c];
+    }
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    DeviceGuard g(s->device);
+    if (!g.ok) return fail(VSR_ERR_CUDA, "cannot select the scene's device");
+    float4* work = nullptr;
+    float4* hits = nullptr;
+    float* f = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&work), n * 32, cs);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&hits), n * 16, cs);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&f), n * 12, cs);
+    if (e == cudaSuccess)
+        e = launch_path_init(reinterpret_cast<const float4*>(rays), n, work, f, radiance, segments,
+                             cs);
+    a.rays = work;
+    a.hits = hits;
+    a.stream = cs;
+    for (uint32_t k = 0; e == cudaSuccess && k <= pp->bounces; ++k) {
+        e = is->dispatch == VSR_DISPATCH_STATIC ? launch_static(a, is->kind, false)
+                                                : launch_dynamic(a, is->kind);
+        if (e == cudaSuccess)
+            e = launch_path_bounce(s->dev, pd, s->d_verts, s->d_idx, work, hits, f, dirs, k, n,
+                                   radiance, segments, cs);
+    }
+    if (f) cudaFreeAsync(f, cs);
+    if (hits) cudaFreeAsync(hits, cs);
+    if (work) cudaFreeAsync(work, cs);
+    if (e != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(VSR_ERR_OOM, "path scratch allocation")
+                                              : cuda_fail(e, "path tracing launch");
     return VSR_OK;
 }

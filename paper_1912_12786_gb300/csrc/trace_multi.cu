@@ -1,6 +1,6 @@
 // Multi-hit query with the intersector injected at compile time: the first
 // n accepted hits of each ray in ascending (t, prim) order.  This is the third
-// visibility query of the library the paper extends (Section 1, next to
+// visibility query of the library the paper extends (Section 3.1, next to
 // closest-hit and any-hit), and the custom intersector reaches it the same
 // way (Section 3.2).  The traversal is the closest-hit traversal with the n-th
 // entry of a sorted buffer as its bound (MultiBest, in shared memory after

@@ -79,6 +79,23 @@ cudaError_t launch_instances(const InstLaunch& L, int kind, int query);
 // (0 if none), cleared after reading.
 cudaError_t instances_align_error(unsigned* line);
 
+// Diffuse path tracing (path.cu): shading and the next segment per bounce.
+struct PathDev {
+    uint32_t bounces;
+    float eps;
+    float sky[3];
+    float untex[3];
+};
+cudaError_t launch_path_init(const float4* rays, unsigned long long n, float4* work, float* f,
+                             float* radiance, uint32_t* segments, cudaStream_t stream);
+cudaError_t launch_path_bounce(const DevScene& sc, const PathDev& pd, const float* verts,
+                               const uint32_t* idx, float4* work, const float4* hits, float* f,
+                               const float* dirs, uint32_t k, unsigned long long n,
+                               float* radiance, uint32_t* segments, cudaStream_t stream);
+// Source line of the first misaligned load the path kernels skipped (0 if
+// none), cleared after reading.
+cudaError_t path_align_error(unsigned* line);
+
 // Closest-hit render with diffuse shading, and its adjoint (render.cu).
 cudaError_t launch_render(const LaunchArgs& a, int kind, const ShadeDev& sh, const float* verts,
                           const uint32_t* idx, float* image, float4* hits);

@@ -58,6 +58,16 @@ class vsr_trace_params(ctypes.Structure):
                 ("image_width", ctypes.c_uint32)]
 
 
+class vsr_path_params(ctypes.Structure):
+    _fields_ = [("bounces", ctypes.c_uint32), ("eps", ctypes.c_float),
+                ("sky", ctypes.c_float * 3), ("untextured", ctypes.c_float * 3)]
+
+
+def path_params(bounces=3, eps=1e-4, sky=(1.0, 1.0, 1.0), untextured=(0.8, 0.8, 0.8)):
+    return vsr_path_params(bounces, eps, (ctypes.c_float * 3)(*sky),
+                           (ctypes.c_float * 3)(*untextured))
+
+
 class vsr_shade_params(ctypes.Structure):
     _fields_ = [("light", ctypes.c_float * 3), ("background", ctypes.c_float * 3),
                 ("grad_tex", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
@@ -83,6 +93,7 @@ _SIGS = {
     "vsr_trace_instances": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P, P],
                             ctypes.c_int),
     "vsr_instances_device_error": ([P, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "vsr_path_trace": ([P, P, ctypes.c_uint64, P, P, P, P, P, P, P], ctypes.c_int),
     "vsr_trace_persistent_noalloc": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P],
                                      ctypes.c_int),
     "vsr_batch_create": ([P, P, P, P, ctypes.c_uint32, P, ctypes.c_int32, P, ctypes.POINTER(P)],
@@ -292,6 +303,15 @@ def vsr_instances_device_error(inst: Instances) -> int:
     w = ctypes.c_uint32()
     _check(lib().vsr_instances_device_error(inst.handle, ctypes.byref(w)))
     return int(w.value)
+
+
+def vsr_path_trace(scene: Scene, rays, isect: vsr_intersector, path: vsr_path_params, dirs,
+                   radiance, segments=None, params: vsr_trace_params | None = None, stream=None):
+    """Diffuse path tracing of ``rays`` (cuda float32 [n,8]) into radiance [n,3];
+    dirs float32 [n * bounces, 3] local unit directions."""
+    _check(lib().vsr_path_trace(scene.handle, _ptr(rays), int(rays.shape[0]), ctypes.byref(isect),
+                                ctypes.byref(path), _ptr(dirs), _ptr(radiance), _ptr(segments),
+                                ctypes.byref(params) if params else None, _stream(stream)))
 
 
 def vsr_trace(scene: Scene, rays, isect: vsr_intersector, query, hits, counters=None,
