@@ -56,8 +56,10 @@ def default_params(V, image_width=FRAME_W):
                           image_width=image_width)
 
 
-# the translation unit of the static trace kernels (the dominant kernel)
-TRACE_SOURCES = ("trace_static.cu", "vsr_device.cuh", "vsr_internal.h")
+# the device code of the static trace kernels (the dominant kernel): the
+# kernels and the traversal they inline (vsr_internal.h adds host-side launch
+# structures only)
+TRACE_SOURCES = ("trace_static.cu", "vsr_device.cuh")
 
 
 def kernel_source_hash() -> str:
