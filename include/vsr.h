@@ -548,7 +548,8 @@ const char* vsr_last_error(void);
 
 /* Read and clear the scene's device error word (synchronous).
  *   bit 0: a traversal stack overflowed;
- *   bit 1: a ray visited more leaves than the BVH has nodes;
+ *   bit 1: a ray made more visits than the BVH has nodes (persistent and
+ *          batched launches count every node, the others count leaves);
  *   bit 2: a render or backward kernel found a load whose address did not
  *          match its width and skipped it (vsr_last_error() names the line);
  *   bit 3: a caller-supplied hit record named a primitive out of range

@@ -539,7 +539,15 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
                                               const Ray& r, H& h, Best& best, Stats& st,
                                               uint32_t& ref, uint32_t& sp, uint32_t& steps,
                                               uint32_t* stack, uint32_t stride) {
-    while (!(ref & kLeafBit)) {  // bounded as in traverse_body
+    // Descent ends by construction as in traverse_body; the persistent and
+    // batched kernels that run these steps keep the per-node visit bound as
+    // well, so their outer loops stay bounded whatever the node data.
+    while (!(ref & kLeafBit)) {
+        if (++steps > sc.max_steps) {
+            atomicOr(sc.err, kErrSteps);
+            best.fail();
+            return true;
+        }
         const float4* p = sc.nodes + 4ull * (ref >> 2);
         const float4 la = VSR_LDG(p), lb = VSR_LDG(p + 1), ra = VSR_LDG(p + 2), rb = VSR_LDG(p + 3);
         const float tfar = h.far((Q == kClosest) ? best.t : r.tmax);
