@@ -175,6 +175,32 @@ def test_image_width_tiles(V, small, width, n):
     assert V.vsr_get_device_error(s) == 0
 
 
+@pytest.mark.parametrize("leaf,bins,cost", [(1, 32, 1.0), (2, 8, 1.0), (8, 128, 1.0),
+                                            (4, 32, 0.0), (4, 32, 4.0)])
+def test_other_build_parameters(V, small, leaf, bins, cost):
+    """Trees of other shapes (leaf sizes 1..8, 8..128 bins, traversal costs
+    0..4): closest and any hits and counts still match the oracle's traversal
+    of the same tree, and closest hits equal the default tree's."""
+    from paper_1912_12786_gb300.inputs import _lib
+    sc, rays, blob0, s0 = small
+    blob = _lib.bvh_build(sc.verts, sc.idx, leaf_max=leaf, bins=bins, traversal_cost=cost)
+    s = V.scene_from_inputs(sc, blob)
+    try:
+        d = _to_dev(rays)
+        for q in ("closest", "any"):
+            ref, st = O.trace_bvh(sc, blob, rays, "count", q)
+            hits, cnt = V.trace(s, d, "count", q, counters=True)
+            compare(hits, ref, st, f"leaf={leaf} bins={bins} cost={cost} {q}")
+            ok = st[:, 3] == 0
+            assert np.array_equal(cnt.cpu().numpy().view(np.uint32)[ok], st[ok, :2])
+        h0, _ = V.trace(s0, d, "alpha_tex", "closest")
+        h1, _ = V.trace(s, d, "alpha_tex", "closest")
+        assert torch.equal(h0.view(torch.int32), h1.view(torch.int32))
+        assert V.vsr_get_device_error(s) == 0
+    finally:
+        s.close()
+
+
 def test_shadow_rays_and_any_hit(V, small):
     sc, rays, blob, s = small
     href, _ = O.trace_bvh(sc, blob, rays, "alpha_tex", "closest")
