@@ -138,6 +138,29 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
     return r;
 }
 
+// The two children of an inner node: a 64-byte aligned pair of 32-byte
+// records, read as two 256-bit loads (the address is 32-byte aligned by
+// construction: the node array comes from cudaMalloc and pair k sits at byte
+// 64 k).  Checked builds read them as four checked 128-bit loads.
+__device__ __forceinline__ void load_pair(const float4* p, float4& la, float4& lb, float4& ra,
+                                          float4& rb) {
+#ifdef VSR_CHECKED_LOADS
+    la = VSR_LDG(p);
+    lb = VSR_LDG(p + 1);
+    ra = VSR_LDG(p + 2);
+    rb = VSR_LDG(p + 3);
+#else
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(la.x), "=f"(la.y), "=f"(la.z), "=f"(la.w), "=f"(lb.x), "=f"(lb.y), "=f"(lb.z),
+          "=f"(lb.w)
+        : "l"(p));
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(ra.x), "=f"(ra.y), "=f"(ra.z), "=f"(ra.w), "=f"(rb.x), "=f"(rb.y), "=f"(rb.z),
+          "=f"(rb.w)
+        : "l"(p + 2));
+#endif
+}
+
 __device__ __forceinline__ float guard_dir(float d) {
     return fabsf(d) < 0x1p-80f ? copysignf(0x1p-80f, d) : d;
 }
@@ -432,7 +455,8 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
         // counted below).
         while (!(ref & kLeafBit)) {
             const float4* p = sc.nodes + 4ull * (ref >> 2);
-            const float4 la = VSR_LDG(p), lb = VSR_LDG(p + 1), ra = VSR_LDG(p + 2), rb = VSR_LDG(p + 3);
+            float4 la, lb, ra, rb;
+            load_pair(p, la, lb, ra, rb);
             const float tfar = h.far((Q == kClosest) ? best.t : r.tmax);
             h.box();
             h.box();
@@ -549,7 +573,8 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
             return true;
         }
         const float4* p = sc.nodes + 4ull * (ref >> 2);
-        const float4 la = VSR_LDG(p), lb = VSR_LDG(p + 1), ra = VSR_LDG(p + 2), rb = VSR_LDG(p + 3);
+        float4 la, lb, ra, rb;
+            load_pair(p, la, lb, ra, rb);
         const float tfar = h.far((Q == kClosest) ? best.t : r.tmax);
         h.box();
         h.box();
