@@ -81,3 +81,30 @@ def test_library_builder_matches_input_builder(lib):
     got = np.frombuffer(ctypes.string_at(out.value, nbytes.value), np.uint8)
     lib.vsr_bvh_free(out)
     assert np.array_equal(got, ref)
+
+
+def test_headers_are_plain_c_and_match_the_binding(tmp_path):
+    """The boundary headers compile as pedantic C99 (no C++ in the ABI), and
+    every struct the binding passes has the size ctypes gives it."""
+    import shutil
+    import subprocess
+    from paper_1912_12786_gb300 import vsr as V
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = ["vsr_ray", "vsr_hit", "vsr_intersector", "vsr_trace_params", "vsr_shade_params",
+               "vsr_path_params", "vsr_texture_desc", "vsr_build_params", "vsr_bvh_node"]
+    src = tmp_path / "abi.c"
+    src.write_text('#include <stdio.h>\n#include "vsr.h"\n#include "vsr_bvh.h"\nint main(void) {\n' +
+                   "".join(f'    printf("%zu\\n", sizeof({s}));\n' for s in structs) +
+                   "    return 0;\n}\n")
+    exe = tmp_path / "abi"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                    _build.INCLUDE, str(src), "-o", str(exe)], check=True)
+    sizes = dict(zip(structs, map(int, subprocess.run([str(exe)], check=True, capture_output=True,
+                                                      text=True).stdout.split())))
+    assert sizes["vsr_ray"] == 32 and sizes["vsr_hit"] == 16 and sizes["vsr_bvh_node"] == 32
+    for name in ("vsr_intersector", "vsr_trace_params", "vsr_shade_params", "vsr_path_params",
+                 "vsr_texture_desc"):
+        assert sizes[name] == ctypes.sizeof(getattr(V, name)), name
+    from paper_1912_12786_gb300.inputs import _lib
+    assert sizes["vsr_build_params"] == ctypes.sizeof(_lib.BuildParams)
