@@ -501,11 +501,16 @@ def breakdown(V, s, d_rays, rays_s, n, flush, stream, torch, reps=5):
     # the clip box keeps the left half of the forest (x <= 50) and culls the rest
     clip = dict(clip_lo=(-1.0, -1.0, -1.0), clip_hi=(50.0, 10.0, 101.0))
     for q, rr in (("closest", d_rays), ("any", rays_s)):
-        for kind, disp in cfgs + [("alpha_tex", "persistent"), ("clip", "static")]:
+        extra = [("alpha_tex", "persistent"), ("alpha_tex", "persistent_tile"), ("clip", "static")]
+        for kind, disp in cfgs + extra:
             p = default_params(V)
-            if disp == "persistent":
+            if disp.startswith("persistent"):
                 p.persistent = 1
-            isect = V.intersector(kind, "static" if disp == "persistent" else disp,
+            if disp == "persistent_tile":
+                # refill only when all 32 lanes are idle: every claim is one
+                # 32-slot pixel tile
+                p.refill_threshold = 1
+            isect = V.intersector(kind, "static" if disp.startswith("persistent") else disp,
                                   **(clip if kind == "clip" else {}))
             c = cnt if kind == "count" else None
             ms = []
