@@ -463,7 +463,9 @@ def run_ours(args):
                   "serial_value": round(world * rays_per_step * args.steps / (serial_ms / 1e3) / 1e6,
                                         2)}
 
-    if not args.no_breakdown:
+    # the auxiliary legs and the CPU baseline describe one GPU: a multi-GPU run
+    # (replicas) reports the step alone and releases the GPUs sooner
+    if not args.no_breakdown and world == 1:
         out["breakdown"] = breakdown(V, s, d_rays, rays_s, n, flush, stream, torch)
         out["multi_hit"] = multi_hit(V, s, d_rays, n, flush, stream, torch)
         out["instanced"] = instanced_bench(V, torch, dev, flush, stream, args.steps)
@@ -472,7 +474,7 @@ def run_ours(args):
         out["batch"] = batch_bench(V, torch, dev, flush, stream, args.steps)
         out["large"] = large_bench(V, torch, dev, flush, stream, args.steps)
 
-    if rank == 0 and not args.no_cpu:
+    if world == 1 and not args.no_cpu:
         mr, cores, nsel, el, reps = oracle_sample(sc, rays, blob, args.ref_stride,
                                                   min_seconds=10.0)
         out["cpu_baseline"] = {"value": round(mr, 4), "unit": "Mrays/s", "cores": cores,
