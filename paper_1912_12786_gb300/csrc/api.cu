@@ -669,7 +669,8 @@ vsr_status vsr_get_device_error(vsr_scene* s, uint32_t* word) {
     if (!s || !word) return fail(VSR_ERR_ARG, "null argument");
     DeviceGuard g(s->device);
     VSR_CUDA(cudaDeviceSynchronize(), "synchronise");
-    VSR_CUDA(cudaMemcpy(word, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read error word");
+    VSR_CUDA(cudaMemcpy(word, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost),
+             "read error word");
     VSR_CUDA(cudaMemset(s->d_err, 0, sizeof(uint32_t)), "clear error word");
     unsigned line = 0;
     VSR_CUDA(render_align_error(&line), "read alignment check");
@@ -683,7 +684,8 @@ vsr_status vsr_get_device_error(vsr_scene* s, uint32_t* word) {
     if (line) {
         *word |= kErrAlign;
         g_err += (g_err.empty() ? "" : "; ") +
-                 std::string("path kernel skipped a misaligned load at path.cu/vsr_device.cuh line ") +
+                 std::string("path kernel skipped a misaligned load at "
+                             "path.cu/vsr_device.cuh line ") +
                  std::to_string(line);
     }
     line = 0;
@@ -881,7 +883,8 @@ extern "C" vsr_status vsr_scene_update(vsr_scene* s, const float* verts, uint32_
     if (st != VSR_OK) return st;
     size_t tex_bytes = 0;
     if (texels) {
-        if (tex_index >= s->ntex) return fail(VSR_ERR_ARG, "tex_index references a missing texture");
+        if (tex_index >= s->ntex)
+            return fail(VSR_ERR_ARG, "tex_index references a missing texture");
         const TexDesc& t = s->h_tex[tex_index];
         tex_bytes = (size_t)t.w * t.h * texel_size((int32_t)t.fmt);
         st = check_dev(texels, s->device, "texels", 4, tex_bytes);
@@ -894,7 +897,8 @@ extern "C" vsr_status vsr_scene_update(vsr_scene* s, const float* verts, uint32_
                                  cudaMemcpyDeviceToDevice, cs),
                  "texel update");
     if (verts && s->nverts) {
-        VSR_CUDA(cudaMemcpyAsync(s->d_verts, verts, 12ull * s->nverts, cudaMemcpyDeviceToDevice, cs),
+        VSR_CUDA(cudaMemcpyAsync(s->d_verts, verts, 12ull * s->nverts, cudaMemcpyDeviceToDevice,
+                                 cs),
                  "vertex update");
         if (s->has_bvh && s->dev.nprims) {
             k_build_tris<<<(s->dev.nprims + 255) / 256, 256, 0, cs>>>(s->d_verts, s->d_idx,
@@ -1549,7 +1553,8 @@ extern "C" vsr_status vsr_instances_device_error(vsr_instances* x, uint32_t* wor
     if (!x || !word) return fail(VSR_ERR_ARG, "null argument");
     DeviceGuard g(x->device);
     VSR_CUDA(cudaDeviceSynchronize(), "synchronise");
-    VSR_CUDA(cudaMemcpy(word, x->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read error word");
+    VSR_CUDA(cudaMemcpy(word, x->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost),
+             "read error word");
     VSR_CUDA(cudaMemset(x->d_err, 0, sizeof(uint32_t)), "clear error word");
     unsigned line = 0;
     VSR_CUDA(instances_align_error(&line), "read alignment check");

@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(256) k_trace_inst(InstDev is, IsectParams ip,
                     for (uint32_t k = 0; k < cnt; ++k) {
                         const uint32_t id = VSR_LDG(is.order + first + k);
                         const float4* w = is.inst + 4ull * id;
-                        const Ray ro = to_object(ra, rb, VSR_LDG(w), VSR_LDG(w + 1), VSR_LDG(w + 2));
+                        const Ray ro =
+                            to_object(ra, rb, VSR_LDG(w), VSR_LDG(w + 1), VSR_LDG(w + 2));
                         const DevScene& msc = is.meshes[__float_as_uint(VSR_LDG(w + 3).x)];
                         best.cur = id;
                         traverse_body<Q, H, false>(msc, ip, ro, h, best, st, stack + sp * stride,
@@ -181,7 +182,8 @@ cudaError_t inst_one(const InstLaunch& L) {
     const size_t smem = (size_t)L.stack_words * L.block * sizeof(uint32_t);
     auto k = k_trace_inst<Q, H>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const unsigned long long grid = (L.map.threads + L.block - 1) / L.block;

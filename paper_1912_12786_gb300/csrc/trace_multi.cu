@@ -87,7 +87,8 @@ cudaError_t multi_one(const LaunchArgs& a, const float* verts, const uint32_t* i
     const size_t smem = ((size_t)a.sc.stack_depth + 2u * nh) * a.block * sizeof(uint32_t);
     auto k = k_trace_multi<H>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;

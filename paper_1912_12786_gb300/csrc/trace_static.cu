@@ -37,10 +37,10 @@ __global__ void __launch_bounds__(256) k_trace(DevScene sc, IsectParams ip,
 // Persistent variant.  Per-lane traversal state lives in registers and the
 // shared-memory stack column; a lane that finishes its ray idles until the
 // warp refills.  The counter hands out thread slots of the ray map; a slot
-// past the image edge takes no ray.  Every wait is a plain loop over claimed work: no lane ever
-// waits on another warp or block.  Each outer iteration either advances some
-// lane's traversal (bounded per ray by the node count) or claims at least one
-// ray, so the kernel terminates.
+// past the image edge takes no ray.  Every wait is a plain loop over claimed
+// work: no lane ever waits on another warp or block.  Each outer iteration
+// either advances some lane's traversal (bounded per ray by the node count)
+// or claims at least one ray, so the kernel terminates.
 template <int Q, class H, bool STATS>
 __global__ void __launch_bounds__(256) k_trace_persistent(
     DevScene sc, IsectParams ip, const float4* __restrict__ rays, RayMap map,
