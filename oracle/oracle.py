@@ -99,6 +99,8 @@ def _load():
         lib.orc_path_trace.argtypes = [P, P, ctypes.c_uint64, P, P, ctypes.c_uint64,
                                        ctypes.c_uint32, P, ctypes.c_float, P, P, P, P,
                                        ctypes.c_int]
+        lib.orc_bounce.argtypes = [P, P, P, P, ctypes.c_uint64, ctypes.c_float, P]
+        lib.orc_bounce.restype = None
         lib.orc_intersect_triangle.argtypes = [P, P, P, P, P]
         lib.orc_intersect_aabb.argtypes = [P, P, P, ctypes.c_float]
         lib.orc_shadow_rays.argtypes = [P, P, ctypes.c_uint64, P, ctypes.c_float, P]
@@ -277,6 +279,19 @@ def path_trace(scene, blob, rays, bounces: int, dirs, eps: float, sky=(1.0, 1.0,
     if rc != 0:
         raise ValueError(f"oracle rejected its inputs (code {rc})")
     return rad, flags
+
+
+def bounce(scene, rays, hits_raw, dirs, eps):
+    """The path tracer's next segment for each (ray, hit, local direction)."""
+    lib = _load()
+    sh = _SceneHandle(scene)
+    r = np.ascontiguousarray(rays, np.float32).reshape(-1, 8)
+    h = np.ascontiguousarray(hits_raw, np.float32).reshape(-1, 4)
+    d = np.ascontiguousarray(dirs, np.float32).reshape(-1, 3)
+    assert r.shape[0] == h.shape[0] == d.shape[0]
+    out = np.zeros_like(r)
+    lib.orc_bounce(ctypes.byref(sh.c), _ptr(r), _ptr(h), _ptr(d), r.shape[0], float(eps), _ptr(out))
+    return out
 
 
 def intersect_triangle(ray, v0, v1, v2):

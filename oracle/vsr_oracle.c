@@ -1067,6 +1067,16 @@ int orc_path_trace(const orc_scene* s, const uint8_t* blob, uint64_t bytes, cons
     return 0;
 }
 
+/* One bounce for each of n (ray, hit, local direction) triples: the next
+ * segment exactly as the path tracer builds it.  rays/out [n*8], hits [n*4],
+ * dirs [n*3]; every hit must name a primitive. */
+void orc_bounce(const orc_scene* s, const float* rays, const float* hits, const float* dirs,
+                uint64_t n, float eps, float* out) {
+    for (uint64_t i = 0; i < n; ++i)
+        bounce_ray(s, (const orc_ray*)rays + i, (const orc_hit*)hits + i, dirs + 3 * i, eps,
+                   (orc_ray*)out + i);
+}
+
 void orc_ao_rays(const orc_scene* s, const float* prim_rays, const float* prim_hits, uint64_t n,
                  uint32_t spp, const float* xi, float tmax, float eps, float* out) {
     for (uint64_t i = 0; i < n; ++i) {
