@@ -83,6 +83,32 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def read_peaks(V, torch, dev) -> dict:
+    """Read rates of this GPU from the library's read probe (16-byte loads
+    cached in L2 only, every thread of a full-occupancy grid): a buffer of half
+    the L2 read 20 times per launch gives the L2 read peak, one of four L2
+    sizes read twice the HBM read rate.  Best of 10 launches each, CUDA events
+    on the current stream; untimed with respect to the steps."""
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    out = {}
+    for key, size, reps in (("l2", l2 // 2, 20), ("hbm", 4 * l2, 2)):
+        buf = torch.ones(size // 16 * 16, dtype=torch.uint8, device=dev)
+        V.vsr_read_probe(buf, reps)
+        best = 0.0
+        for _ in range(10):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            V.vsr_read_probe(buf, reps)
+            b.record()
+            torch.cuda.synchronize(dev)
+            best = max(best, buf.numel() * reps / (a.elapsed_time(b) / 1e3) / 1e9)
+        out[key] = round(best, 1)
+        del buf
+    out["l2_bytes"] = l2
+    return out
+
+
 # --------------------------------------------------------------------------
 # clocks during the timed region
 
@@ -381,6 +407,12 @@ def run_ours(args):
     mem = {"algorithmic_bytes_per_launch": dom_bytes,
            "algorithmic_GBs": round(dom_bytes / (dom_ms / 1e3) / 1e9, 1),
            "hbm_peak_GBs": hbm_peak, "hbm_peak_source": peak_src}
+    rp = read_peaks(V, torch, dev)
+    mem.update({"l2_peak_GBs": rp["l2"],
+                "l2_peak_source": f"read probe: {rp['l2_bytes'] // 2} B (half the L2) read 20x "
+                                  "per launch, best of 10",
+                "l2_frac": round(dom_bytes / (dom_ms / 1e3) / 1e9 / rp["l2"], 4),
+                "hbm_read_probe_GBs": rp["hbm"]})
     if traffic is not None:
         hbm = traffic / (dom_ms / 1e3) / 1e9
         mem.update({"hbm_traffic_bytes_per_launch": traffic, "hbm_achieved_GBs": round(hbm, 1),

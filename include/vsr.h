@@ -541,6 +541,22 @@ vsr_status vsr_make_ao_rays(vsr_scene* scene, const vsr_ray* prim_rays, const vs
                             uint64_t n, uint32_t spp, const float* xi, float tmax, float eps,
                             vsr_ray* out, vsr_stream stream);
 
+/* ----------------------------------------------------------- measurement */
+
+/* Read-bandwidth probe, the denominator of the memory roofline of the trace
+ * kernels (whose node, triangle and texel fetches go through L1 and L2).  One
+ * kernel launch on `stream` in which every thread of a full-occupancy grid
+ * (SMs x resident 512-thread blocks) reads all of `buf` `reps` times with
+ * 16-byte loads cached in L2 only; it writes nothing.  A buffer well inside
+ * the L2 measures the L2 read rate, one far larger the HBM read rate: the
+ * caller times the launch (bytes x reps read).
+ *   buf    device memory of the current device, 16-byte aligned (not owned);
+ *   bytes  a nonzero multiple of 16, within buf's allocation;
+ *   reps   passes over the buffer, >= 1.
+ * VSR_ERR_ARG on a null, unaligned, host or too-small buffer or a bad size;
+ * VSR_ERR_CUDA if the launch fails.  Asynchronous. */
+vsr_status vsr_read_probe(const void* buf, uint64_t bytes, uint32_t reps, vsr_stream stream);
+
 /* ---------------------------------------------------------------- errors */
 
 /* Message describing the last failure on the calling thread ("" if none). */

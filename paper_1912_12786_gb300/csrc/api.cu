@@ -664,6 +664,20 @@ vsr_status vsr_make_ao_rays(vsr_scene* s, const vsr_ray* prim_rays, const vsr_hi
     return VSR_OK;
 }
 
+vsr_status vsr_read_probe(const void* buf, uint64_t bytes, uint32_t reps, vsr_stream stream) {
+    g_err.clear();
+    if (bytes == 0 || bytes % 16)
+        return fail(VSR_ERR_ARG, "bytes must be a nonzero multiple of 16");
+    if (reps == 0) return fail(VSR_ERR_ARG, "reps must be >= 1");
+    int dev = 0;
+    VSR_CUDA(cudaGetDevice(&dev), "current device");
+    vsr_status st = check_dev(buf, dev, "buf", 16, bytes);
+    if (st != VSR_OK) return st;
+    VSR_CUDA(launch_read_probe(buf, bytes, reps, reinterpret_cast<cudaStream_t>(stream)),
+             "read probe launch");
+    return VSR_OK;
+}
+
 vsr_status vsr_get_device_error(vsr_scene* s, uint32_t* word) {
     g_err.clear();
     if (!s || !word) return fail(VSR_ERR_ARG, "null argument");

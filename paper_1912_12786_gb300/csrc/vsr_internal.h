@@ -95,6 +95,8 @@ cudaError_t launch_path_bounce(const DevScene& sc, const PathDev& pd, const floa
 // Source line of the first misaligned load the path kernels skipped (0 if
 // none), cleared after reading.
 cudaError_t path_align_error(unsigned* line);
+cudaError_t launch_read_probe(const void* buf, unsigned long long bytes, uint32_t reps,
+                              cudaStream_t stream);
 
 // Closest-hit render with diffuse shading, and its adjoint (render.cu).
 cudaError_t launch_render(const LaunchArgs& a, int kind, const ShadeDev& sh, const float* verts,

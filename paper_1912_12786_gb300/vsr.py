@@ -112,6 +112,7 @@ _SIGS = {
                           ctypes.c_float, P, P], ctypes.c_int),
     "vsr_make_shadow_rays": ([P, P, ctypes.c_uint64, P, ctypes.c_float, P, P], ctypes.c_int),
     "vsr_get_device_error": ([P, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "vsr_read_probe": ([P, ctypes.c_uint64, ctypes.c_uint32, P], ctypes.c_int),
     "vsr_bvh_build": ([P, ctypes.c_uint64, P, ctypes.c_uint32, P, ctypes.POINTER(P),
                        ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "vsr_bvh_free": ([P], None),
@@ -465,6 +466,13 @@ def vsr_make_shadow_rays(prim_rays, prim_hits, light, eps: float, out, stream=No
     l = (ctypes.c_float * 3)(*[float(x) for x in light])
     _check(lib().vsr_make_shadow_rays(_ptr(prim_rays), _ptr(prim_hits), int(prim_rays.shape[0]),
                                       l, float(eps), _ptr(out), _stream(stream)))
+
+
+def vsr_read_probe(buf, reps: int = 1, stream=None):
+    """One launch reading all of ``buf`` (a 16-byte aligned cuda tensor whose
+    size is a multiple of 16 bytes) ``reps`` times with L2-cached loads."""
+    nbytes = int(buf.numel() * buf.element_size())
+    _check(lib().vsr_read_probe(_ptr(buf), nbytes, int(reps), _stream(stream)))
 
 
 def vsr_get_device_error(scene: Scene) -> int:
