@@ -47,7 +47,8 @@ FLUSH_BYTES = 256 << 20
 
 
 FRAME_W = 1920  # the forest and large frames are row-major 1920x1080 images
-E2E_BANDS = 6   # end-to-end step: bands of rows pipelined over three streams
+E2E_BANDS = 6   # end-to-end step: bands of rows pipelined over streams
+E2E_TRACE_STREAMS = 3  # streams the bands' traces go to, round robin
 
 
 def default_params(V, image_width=FRAME_W):
@@ -436,42 +437,64 @@ def run_ours(args):
            "clocks": clk}
 
     # end to end through the public API: pinned host rays in, host hits out.
-    # The frame goes as E2E_BANDS bands of whole rows through three streams:
-    # one copies rays in, one traces, one copies hits out, so the traces run
-    # back to back while the next band's rays arrive and the previous band's
-    # hits leave (each band is an image of the same width: the pixel-tile
-    # launch applies unchanged).  Events order each band across the streams.
+    # The frame goes as E2E_BANDS bands of whole rows (each band an image of
+    # the same width, so the pixel-tile launch applies unchanged).  One stream
+    # copies rays in; the bands' traces go round robin to E2E_TRACE_STREAMS
+    # streams, so one band's launch tail overlaps the next band's launch; each
+    # trace stream has its own stream for copying hits out.  Events order each
+    # band across the streams.  Issued eagerly, the 6 x 5 calls take about as
+    # long on the host as the GPU takes to run them, so the step is captured
+    # once into a CUDA graph (copies included) and replayed every step.
     h_rays = torch.from_numpy(rays).pin_memory()
     h_hp = torch.empty((n, 4), dtype=torch.float32).pin_memory()
     h_hs = torch.empty((n, 4), dtype=torch.float32).pin_memory()
-    s_in, s_cmp, s_out = (torch.cuda.Stream(dev) for _ in range(3))
+    s_in = torch.cuda.Stream(dev)
+    s_trace = [torch.cuda.Stream(dev) for _ in range(E2E_TRACE_STREAMS)]
+    s_out = [torch.cuda.Stream(dev) for _ in range(E2E_TRACE_STREAMS)]
     band_ev = [[torch.cuda.Event() for _ in range(3)] for _ in range(E2E_BANDS)]
     rows = (n + FRAME_W - 1) // FRAME_W
     cut = [min(n, FRAME_W * (rows * k // E2E_BANDS)) for k in range(E2E_BANDS + 1)]
 
-    def e2e_step(done):
-        for st in (s_in, s_cmp, s_out):
-            st.wait_stream(stream)
+    def e2e_issue(base):
+        for st in [s_in] + s_trace + s_out:
+            st.wait_stream(base)
         for b in range(E2E_BANDS):
             lo, hi = cut[b], cut[b + 1]
+            tr, out_st = s_trace[b % E2E_TRACE_STREAMS], s_out[b % E2E_TRACE_STREAMS]
             e_in, e_p, e_s = band_ev[b]
             with torch.cuda.stream(s_in):
                 d_rays[lo:hi].copy_(h_rays[lo:hi], non_blocking=True)
             e_in.record(s_in)
-            s_cmp.wait_event(e_in)
-            V.vsr_trace(s, d_rays[lo:hi], alpha, "closest", hits_p[lo:hi], None, p, s_cmp)
-            V.vsr_make_shadow_rays(d_rays[lo:hi], hits_p[lo:hi], light, eps, rays_s[lo:hi], s_cmp)
-            e_p.record(s_cmp)
-            V.vsr_trace(s, rays_s[lo:hi], alpha, "any", hits_s[lo:hi], None, p, s_cmp)
-            e_s.record(s_cmp)
-            s_out.wait_event(e_p)
-            with torch.cuda.stream(s_out):
+            tr.wait_event(e_in)
+            V.vsr_trace(s, d_rays[lo:hi], alpha, "closest", hits_p[lo:hi], None, p, tr)
+            V.vsr_make_shadow_rays(d_rays[lo:hi], hits_p[lo:hi], light, eps, rays_s[lo:hi], tr)
+            e_p.record(tr)
+            V.vsr_trace(s, rays_s[lo:hi], alpha, "any", hits_s[lo:hi], None, p, tr)
+            e_s.record(tr)
+            out_st.wait_event(e_p)
+            with torch.cuda.stream(out_st):
                 h_hp[lo:hi].copy_(hits_p[lo:hi], non_blocking=True)
-            s_out.wait_event(e_s)
-            with torch.cuda.stream(s_out):
+            out_st.wait_event(e_s)
+            with torch.cuda.stream(out_st):
                 h_hs[lo:hi].copy_(hits_s[lo:hi], non_blocking=True)
-        for st in (s_in, s_cmp, s_out):
-            stream.wait_stream(st)
+        for st in [s_in] + s_trace + s_out:
+            base.wait_stream(st)
+
+    def eager_step(done):
+        e2e_issue(stream)
+        done.record(stream)
+
+    e2e_issue(stream)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(stream)
+    with torch.cuda.graph(graph, stream=cap):
+        e2e_issue(torch.cuda.current_stream(dev))
+    torch.cuda.synchronize(dev)
+
+    def e2e_step(done):
+        graph.replay()
         done.record(stream)
 
     def serial_step(done):
@@ -497,16 +520,24 @@ def run_ours(args):
 
     e2e_ms = timed_e2e(e2e_step)
     banded = (h_hp.clone(), h_hs.clone())
+    eager_ms = timed_e2e(eager_step)
+    eager = (h_hp.clone(), h_hs.clone())
     serial_ms = timed_e2e(serial_step)
-    assert torch.equal(banded[0].view(torch.int32), h_hp.view(torch.int32))
-    assert torch.equal(banded[1].view(torch.int32), h_hs.view(torch.int32))
+    for got in (banded, eager):
+        assert torch.equal(got[0].view(torch.int32), h_hp.view(torch.int32))
+        assert torch.equal(got[1].view(torch.int32), h_hs.view(torch.int32))
+
     def mrays(ms):
         return round(world * rays_per_step * args.steps / (ms / 1e3) / 1e6, 2)
 
     out["e2e"] = {"value": mrays(e2e_ms), "unit": "Mrays/s",
                   "h2d_bytes_per_step": int(h_rays.numel() * 4),
                   "d2h_bytes_per_step": int((h_hp.numel() + h_hs.numel()) * 4),
-                  "bands": E2E_BANDS, "streams": 3, "serial_value": mrays(serial_ms)}
+                  "bands": E2E_BANDS, "trace_streams": E2E_TRACE_STREAMS,
+                  "schedule": "one CUDA graph per step: rays in on 1 stream, bands round robin "
+                              f"over {E2E_TRACE_STREAMS} trace streams, hits out on 1 stream "
+                              "per trace stream",
+                  "eager_value": mrays(eager_ms), "serial_value": mrays(serial_ms)}
 
     # the auxiliary legs and the CPU baseline describe one GPU: a multi-GPU run
     # (replicas) reports the step alone and releases the GPUs sooner
