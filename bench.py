@@ -47,8 +47,8 @@ FLUSH_BYTES = 256 << 20
 
 
 FRAME_W = 1920  # the forest and large frames are row-major 1920x1080 images
-E2E_BANDS = 6   # end-to-end step: bands of rows pipelined over streams
-E2E_TRACE_STREAMS = 3  # streams the bands' traces go to, round robin
+E2E_BANDS = 8   # end-to-end step: bands of rows pipelined over streams
+E2E_TRACE_STREAMS = 4  # streams the bands' traces go to, round robin
 
 
 def default_params(V, image_width=FRAME_W):
@@ -442,9 +442,9 @@ def run_ours(args):
     # copies rays in; the bands' traces go round robin to E2E_TRACE_STREAMS
     # streams, so one band's launch tail overlaps the next band's launch; each
     # trace stream has its own stream for copying hits out.  Events order each
-    # band across the streams.  Issued eagerly, the 6 x 5 calls take about as
-    # long on the host as the GPU takes to run them, so the step is captured
-    # once into a CUDA graph (copies included) and replayed every step.
+    # band across the streams.  Issued eagerly, the five calls per band take
+    # about as long on the host as the GPU takes to run them, so the step is
+    # captured once into a CUDA graph (copies included) and replayed every step.
     h_rays = torch.from_numpy(rays).pin_memory()
     h_hp = torch.empty((n, 4), dtype=torch.float32).pin_memory()
     h_hs = torch.empty((n, 4), dtype=torch.float32).pin_memory()
