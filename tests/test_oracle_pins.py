@@ -446,3 +446,56 @@ def test_empty_and_single_triangle_blobs():
                      np.zeros((0, 3, 2), np.float32), np.zeros(0, np.uint32), [])
     h, st = O.trace_bvh(e, b0, _ray((0, 0, 0), (0, 0, 1))[None], "count", "closest")
     assert h["prim"][0] == O.NONE and tuple(st[0, :2]) == (0, 0)
+
+
+def test_ao_rays_cosine_sampling_about_the_face_normal():
+    """Ambient-occlusion rays (4 per pixel): each leaves from the primary hit
+    point (within 1e-5 of o + t d in FP64), along a
+    unit vector on the side of the face that the primary ray came from; its
+    cosine to that normal is sqrt(1 - xi1) (cosine-weighted sampling), and two
+    samples of one pixel are turned about the normal by 2 pi (xi2' - xi2) in a
+    right-handed tangent frame.  A miss gives inactive rays (tmax < tmin)."""
+    rng = np.random.default_rng(21)
+    m, spp = 1500, 4
+    tri = rng.uniform(-1, 1, (m, 3, 3)).astype(np.float32)
+    sc = scenes.Scene("tris", tri.reshape(-1, 3), np.arange(3 * m, dtype=np.uint32).reshape(m, 3),
+                      np.zeros((m, 3, 2), np.float32), np.full(m, O.NONE, np.uint32), [])
+    rays = np.zeros((m, 8), np.float32)
+    rays[:, 0:3] = rng.uniform(-3, 3, (m, 3))
+    d = rng.standard_normal((m, 3))
+    rays[:, 4:7] = d / np.linalg.norm(d, axis=1, keepdims=True)
+    rays[:, 7] = np.inf
+    hits = np.zeros((m, 4), np.float32)
+    hits[:, 0] = rng.uniform(0.1, 5, m)
+    prim = np.arange(m, dtype=np.uint32)
+    prim[::7] = O.NONE
+    hits[:, 3] = prim.view(np.float32)
+    xi = rng.uniform(0, 1, (m * spp, 2)).astype(np.float32)
+    out = O.ao_rays(sc, rays, hits, spp, xi, 0.5, 1e-3).reshape(m, spp, 8)
+    miss = prim == O.NONE
+    assert np.all(out[miss][..., 7] < out[miss][..., 3])
+    h = ~miss
+    o, dd = rays[h, 0:3].astype(np.float64), rays[h, 4:7].astype(np.float64)
+    t = hits[h, 0].astype(np.float64)
+    q = out[h]
+    want_o = np.broadcast_to((o + t[:, None] * dd)[:, None, :], q[:, :, 0:3].shape)
+    np.testing.assert_allclose(q[:, :, 0:3], want_o, rtol=0, atol=1e-5)
+    assert np.all(q[:, :, 3] == np.float32(1e-3)) and np.all(q[:, :, 7] == np.float32(0.5))
+    tr = tri[h].astype(np.float64)
+    n = np.cross(tr[:, 1] - tr[:, 0], tr[:, 2] - tr[:, 0])
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    n[np.einsum("ij,ij->i", n, dd) > 0] *= -1
+    w = q[:, :, 4:7].astype(np.float64)
+    assert np.allclose(np.linalg.norm(w, axis=2), 1.0, atol=1e-6)
+    x = xi.reshape(m, spp, 2)[h].astype(np.float64)
+    cos = np.einsum("ikj,ij->ik", w, n)
+    np.testing.assert_allclose(cos, np.sqrt(1 - x[:, :, 0]), rtol=0, atol=2e-6)
+    p = w - cos[:, :, None] * n[:, None, :]
+    sin_ok = np.sqrt(x[:, 0, 0]) > 1e-2
+    for k in range(1, spp):
+        ok = sin_ok & (np.sqrt(x[:, k, 0]) > 1e-2)
+        a, b = p[ok, 0], p[ok, k]
+        ang = np.arctan2(np.einsum("ij,ij->i", np.cross(a, b), n[ok]), np.einsum("ij,ij->i", a, b))
+        want = 2 * np.pi * (x[ok, k, 1] - x[ok, 0, 1])
+        diff = np.angle(np.exp(1j * (ang - want)))
+        assert np.abs(diff).max() < 1e-3, np.abs(diff).max()
