@@ -486,16 +486,22 @@ def run_ours(args):
 
     e2e_issue(stream)
     torch.cuda.synchronize(dev)
-    graph = torch.cuda.CUDAGraph()
+    graph, capture_error = torch.cuda.CUDAGraph(), None
     cap = torch.cuda.Stream(dev)
     cap.wait_stream(stream)
-    with torch.cuda.graph(graph, stream=cap):
-        e2e_issue(torch.cuda.current_stream(dev))
+    try:
+        with torch.cuda.graph(graph, stream=cap):
+            e2e_issue(torch.cuda.current_stream(dev))
+    except RuntimeError as exc:  # the line then reports the eager schedule
+        capture_error = f"{type(exc).__name__}: {str(exc).splitlines()[0][:160]}"
     torch.cuda.synchronize(dev)
 
     def e2e_step(done):
-        graph.replay()
-        done.record(stream)
+        if capture_error is None:
+            graph.replay()
+            done.record(stream)
+        else:
+            eager_step(done)
 
     def serial_step(done):
         d_rays.copy_(h_rays, non_blocking=True)
@@ -534,9 +540,11 @@ def run_ours(args):
                   "h2d_bytes_per_step": int(h_rays.numel() * 4),
                   "d2h_bytes_per_step": int((h_hp.numel() + h_hs.numel()) * 4),
                   "bands": E2E_BANDS, "trace_streams": E2E_TRACE_STREAMS,
-                  "schedule": "one CUDA graph per step: rays in on 1 stream, bands round robin "
-                              f"over {E2E_TRACE_STREAMS} trace streams, hits out on 1 stream "
-                              "per trace stream",
+                  "schedule": ("one CUDA graph per step" if capture_error is None else
+                               f"eager (graph capture failed: {capture_error})") +
+                              f": rays in on 1 stream, bands round robin over "
+                              f"{E2E_TRACE_STREAMS} trace streams, hits out on 1 stream per "
+                              "trace stream",
                   "eager_value": mrays(eager_ms), "serial_value": mrays(serial_ms)}
 
     # the auxiliary legs and the CPU baseline describe one GPU: a multi-GPU run
