@@ -992,7 +992,7 @@ extern "C" vsr_status vsr_trace_persistent_noalloc(vsr_scene* s, const vsr_ray* 
         return fail(VSR_ERR_ARG, "vsr_trace_persistent_noalloc: scratch larger than 256 bytes");
     if (is && is->dispatch != VSR_DISPATCH_STATIC)
         return fail(VSR_ERR_ARG, "vsr_trace_persistent_noalloc: static dispatch only");
-    vsr_trace_params prm{128u, 1u, 16u, 0u};
+    vsr_trace_params prm{128u, 1u, 16u, 0u, 0u};
     if (p) {
         prm = *p;
         prm.persistent = 1u;
@@ -1036,7 +1036,7 @@ struct vsr_batch {
     BatchItem* d_items = nullptr;
     unsigned long long* d_offsets = nullptr;
     unsigned long long* d_work = nullptr;
-    vsr_trace_params params{128u, 1u, 16u, 0u};
+    vsr_trace_params params{128u, 1u, 16u, 0u, 0u};
     bool tuned = false;
     uint64_t shape = 0;  // workload signature for the tuning cache
     cudaStream_t side = nullptr;
@@ -1072,7 +1072,7 @@ bool tune_lookup(uint64_t shape, vsr_trace_params* out) {
                 unsigned long long sh;
                 unsigned b, r, bps;
                 while (std::fscanf(fp, "%llx %u %u %u", &sh, &b, &r, &bps) == 4)
-                    g_tune_cache.push_back({sh, vsr_trace_params{b, 1u, r, bps}});
+                    g_tune_cache.push_back({sh, vsr_trace_params{b, 1u, r, bps, 0u}});
                 std::fclose(fp);
             }
         }
@@ -1140,7 +1140,7 @@ vsr_status batch_tune(vsr_batch* b) {
         if ((size_t)b->stack_max * bl * 4 > 200 * 1024) continue;
         for (uint32_t rf : refills)
             for (uint32_t ps : per_sm) {
-                const vsr_trace_params cand{bl, 1u, rf, ps};
+                const vsr_trace_params cand{bl, 1u, rf, ps, 0u};
                 const BatchLaunch L = batch_launch_args(b, cand);
                 float ms[2] = {0.0f, 0.0f};
                 cudaError_t e = launch_batch(L, b->kind, b->query, b->side);
@@ -1204,7 +1204,7 @@ extern "C" vsr_status vsr_batch_create(vsr_scene* const* scenes, const vsr_ray* 
     // one) without a cause found; it stays off these kernels until one is.
     if (is->kind == VSR_ISECT_PROC_ALPHA && query == VSR_ANY)
         return fail(VSR_ERR_ARG, "batched procedural-alpha any-hit query is disabled");
-    vsr_trace_params prm{128u, 1u, 16u, 0u};
+    vsr_trace_params prm{128u, 1u, 16u, 0u, 0u};
     if (params) {
         prm = *params;
         prm.persistent = 1u;
