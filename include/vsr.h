@@ -336,8 +336,11 @@ vsr_status vsr_instances_device_error(vsr_instances* instances, uint32_t* word);
 /*
  * Measurement variant of vsr_trace with the static intersector: identical
  * hits, plus per-ray statistics stats device uint32 [n*4] = (box tests,
- * triangle tests, intersector consultations, 0).  Used to count the bytes
- * the traversal must fetch.  Errors as vsr_trace.
+ * triangle tests, intersector consultations, texture look-ups), the last
+ * being the consultations on triangles with a texture by an intersector that
+ * reads texture coordinates (alpha texture, procedural alpha; 0 for the
+ * others).  Used to count the bytes the traversal must fetch.  Errors as
+ * vsr_trace.
  */
 vsr_status vsr_trace_stats(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
                            const vsr_intersector* isect, int32_t query, vsr_hit* hits,

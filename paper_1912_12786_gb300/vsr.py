@@ -10,7 +10,8 @@ Tensor layouts:
   hits      float32 [n, 4]  (t, u, v, prim id bits); ``prim_ids(hits)`` gives
             the uint32 ids as int64 (miss = 0xFFFFFFFF)
   counters  int32   [n, 2]  (box tests, triangle tests) for the COUNT intersector
-  stats     int32   [n, 4]  (box tests, triangle tests, intersector calls, 0)
+  stats     int32   [n, 4]  (box tests, triangle tests, intersector calls,
+            texture look-ups)
 """
 from __future__ import annotations
 
@@ -34,6 +35,8 @@ TEX_FMT = {"u8": 0, "rgba8": 1, "rgba32f": 2}
 
 
 class VsrError(RuntimeError):
+    """A non-OK status from the library; ``status`` is the vsr_status code and
+    the message is vsr_last_error() at the time of the call."""
     def __init__(self, status: int, msg: str):
         self.status = status
         name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
@@ -41,11 +44,14 @@ class VsrError(RuntimeError):
 
 
 class vsr_texture_desc(ctypes.Structure):
+    """One texture (C layout of vsr_texture_desc): format, size, host texels."""
     _fields_ = [("fmt", ctypes.c_int32), ("w", ctypes.c_uint32), ("h", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("texels", ctypes.c_void_p)]
 
 
 class vsr_intersector(ctypes.Structure):
+    """The custom intersector (C layout of vsr_intersector): kind, static or
+    dynamic dispatch, alpha cutoffs, procedural frequency, clip box."""
     _fields_ = [("kind", ctypes.c_int32), ("dispatch", ctypes.c_int32),
                 ("alpha_cutoff_u8", ctypes.c_uint32), ("alpha_cutoff_f", ctypes.c_float),
                 ("proc_freq", ctypes.c_float), ("clip_lo", ctypes.c_float * 3),
@@ -53,22 +59,27 @@ class vsr_intersector(ctypes.Structure):
 
 
 class vsr_trace_params(ctypes.Structure):
+    """Launch configuration (C layout of vsr_trace_params)."""
     _fields_ = [("block_size", ctypes.c_uint32), ("persistent", ctypes.c_uint32),
                 ("refill_threshold", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("image_width", ctypes.c_uint32)]
 
 
 class vsr_path_params(ctypes.Structure):
+    """Path-tracing parameters (C layout of vsr_path_params)."""
     _fields_ = [("bounces", ctypes.c_uint32), ("eps", ctypes.c_float),
                 ("sky", ctypes.c_float * 3), ("untextured", ctypes.c_float * 3)]
 
 
 def path_params(bounces=3, eps=1e-4, sky=(1.0, 1.0, 1.0), untextured=(0.8, 0.8, 0.8)):
+    """vsr_path_params: bounces after the first segment, the interval start of
+    every bounce segment, the sky radiance and the albedo of untextured hits."""
     return vsr_path_params(bounces, eps, (ctypes.c_float * 3)(*sky),
                            (ctypes.c_float * 3)(*untextured))
 
 
 class vsr_shade_params(ctypes.Structure):
+    """Diffuse shading parameters (C layout of vsr_shade_params)."""
     _fields_ = [("light", ctypes.c_float * 3), ("background", ctypes.c_float * 3),
                 ("grad_tex", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
@@ -122,6 +133,7 @@ _SIGS = {
 
 
 def lib_path() -> str:
+    """Path of the in-tree libvsr.so."""
     return _build.LIB
 
 
@@ -148,21 +160,28 @@ def _check(status: int):
 
 
 def vsr_last_error() -> str:
+    """Message of the last failure on the calling thread ("" if none)."""
     return lib().vsr_last_error().decode()
 
 
 def vsr_version() -> int:
+    """Library version, e.g. 100 for 0.1.0."""
     return lib().vsr_version()
 
 
 def intersector(kind="default", dispatch="static", cutoff_u8=128, cutoff_f=0.01,
                 freq=40.0, clip_lo=(0.0, 0.0, 0.0), clip_hi=(0.0, 0.0, 0.0)) -> vsr_intersector:
+    """vsr_intersector by name: kind in ISECT, dispatch in DISPATCH; the
+    cutoffs apply to u8/RGBA8 and to float alpha, ``freq`` to procedural alpha,
+    ``clip_lo``/``clip_hi`` to the clip box."""
     return vsr_intersector(ISECT[kind], DISPATCH[dispatch], cutoff_u8, cutoff_f, freq,
                            (ctypes.c_float * 3)(*clip_lo), (ctypes.c_float * 3)(*clip_hi))
 
 
 def trace_params(block_size=128, persistent=0, refill_threshold=16, blocks_per_sm=0,
                  image_width=0):
+    """vsr_trace_params with the library's defaults; ``image_width`` > 0 maps
+    each warp to a 4 x 8 pixel tile of a row-major image of that width."""
     return vsr_trace_params(block_size, persistent, refill_threshold, blocks_per_sm, image_width)
 
 
@@ -213,6 +232,8 @@ def vsr_scene_create_indexed(verts, idx, uvs, geom_id, textures) -> Scene:
 
 
 def vsr_scene_create(verts_xyz, uvs, geom_id, textures) -> Scene:
+    """Copy non-indexed host triangles (float32 [m, 9]), per-corner texture
+    coordinates and textures to the current CUDA device."""
     v = np.ascontiguousarray(verts_xyz, np.float32).reshape(-1, 9)
     uv = np.ascontiguousarray(uvs, np.float32).reshape(-1, 3, 2)
     g = np.ascontiguousarray(geom_id, np.uint32).reshape(-1)
@@ -226,10 +247,12 @@ def vsr_scene_create(verts_xyz, uvs, geom_id, textures) -> Scene:
 
 
 def vsr_scene_destroy(scene: Scene):
+    """Free the scene's device memory."""
     scene.close()
 
 
 def vsr_bvh_load(scene: Scene, blob: np.ndarray):
+    """Validate a BVH blob (uint8) and convert it to the device layout."""
     b = np.ascontiguousarray(blob, np.uint8)
     _check(lib().vsr_bvh_load(scene.handle, b.ctypes.data if b.size else None, b.size))
 
@@ -301,6 +324,7 @@ def vsr_trace_instances(inst: Instances, rays, isect: vsr_intersector, query, hi
 
 
 def vsr_instances_device_error(inst: Instances) -> int:
+    """Read and clear the instance set's device error word (synchronous)."""
     w = ctypes.c_uint32()
     _check(lib().vsr_instances_device_error(inst.handle, ctypes.byref(w)))
     return int(w.value)
@@ -339,6 +363,8 @@ def vsr_trace_persistent_noalloc(scene: Scene, rays, isect: vsr_intersector, que
 
 def vsr_trace_stats(scene: Scene, rays, isect: vsr_intersector, query, hits, stats,
                     stream=None):
+    """Trace as vsr_trace and write per-ray (box tests, triangle tests,
+    intersector calls, texture fetches) into ``stats`` (int32 [n, 4])."""
     q = QUERY[query] if isinstance(query, str) else int(query)
     _check(lib().vsr_trace_stats(scene.handle, _ptr(rays), int(rays.shape[0]),
                                  ctypes.byref(isect), q, _ptr(hits), _ptr(stats),
@@ -385,21 +411,25 @@ def vsr_batch_create(scenes, rays, hits, isect: vsr_intersector, query,
 
 
 def vsr_batch_launch(batch: Batch, stream=None):
+    """Replay the batch's launch on ``stream``."""
     _check(lib().vsr_batch_launch(batch.handle, _stream(stream)))
 
 
 def vsr_batch_params(batch: Batch) -> vsr_trace_params:
+    """The launch configuration the batch was tuned to."""
     p = vsr_trace_params()
     _check(lib().vsr_batch_params(batch.handle, ctypes.byref(p)))
     return p
 
 
 def vsr_batch_destroy(batch: Batch):
+    """Free the batch (its scenes and buffers stay the caller's)."""
     batch.close()
 
 
 def vsr_trace_batch(scenes, rays, hits, isect: vsr_intersector, query,
                     params: vsr_trace_params | None = None, stream=None):
+    """Trace many scenes' ray batches in one persistent launch (untuned)."""
     q = QUERY[query] if isinstance(query, str) else int(query)
     nb, sc, rp, hp, ns = _batch_arrays(scenes, rays, hits)
     _check(lib().vsr_trace_batch(sc, rp, ns, hp, nb, ctypes.byref(isect), q,
@@ -407,6 +437,8 @@ def vsr_trace_batch(scenes, rays, hits, isect: vsr_intersector, query,
 
 
 def shade_params(light, background=(0.0, 0.0, 0.0), grad_tex=0) -> vsr_shade_params:
+    """vsr_shade_params: directional light, background colour and the texture
+    whose texels receive gradients."""
     return vsr_shade_params((ctypes.c_float * 3)(*[float(x) for x in light]),
                             (ctypes.c_float * 3)(*[float(x) for x in background]),
                             grad_tex, 0)
@@ -463,6 +495,8 @@ def vsr_make_ao_rays(scene: Scene, prim_rays, prim_hits, spp: int, xi, tmax: flo
 
 
 def vsr_make_shadow_rays(prim_rays, prim_hits, light, eps: float, out, stream=None):
+    """Rays from the primary hit points toward the directional light into
+    ``out`` (float32 [n, 8]); misses give inactive rays."""
     l = (ctypes.c_float * 3)(*[float(x) for x in light])
     _check(lib().vsr_make_shadow_rays(_ptr(prim_rays), _ptr(prim_hits), int(prim_rays.shape[0]),
                                       l, float(eps), _ptr(out), _stream(stream)))
@@ -476,6 +510,7 @@ def vsr_read_probe(buf, reps: int = 1, stream=None):
 
 
 def vsr_get_device_error(scene: Scene) -> int:
+    """Read and clear the scene's device error word (synchronous)."""
     w = ctypes.c_uint32()
     _check(lib().vsr_get_device_error(scene.handle, ctypes.byref(w)))
     return int(w.value)
