@@ -109,7 +109,12 @@ def test_stats_variant_counts(V, small, kind, query):
     stats = torch.empty((len(rays), 4), dtype=torch.int32, device="cuda")
     V.vsr_trace_stats(s, r, V.intersector(kind), query, hits, stats)
     compare(hits, ref, st, "stats")
-    assert np.array_equal(stats.cpu().numpy().view(np.uint32)[:, :3], st[:, :3])
+    got = stats.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got[:, :3], st[:, :3])
+    # texture look-ups: every triangle of this scene is textured, so the
+    # alpha intersectors look up once per consultation and the others never
+    want = st[:, 2] if kind in ("alpha_tex", "proc_alpha") else np.zeros_like(st[:, 2])
+    assert np.array_equal(got[:, 3], want)
 
 
 @pytest.mark.parametrize("block,refill", [(32, 1), (128, 16), (256, 32), (64, 24)])
