@@ -41,7 +41,13 @@ METRIC = "Mrays/s alpha any-hit vs default intersector; fwd+bwd Mrays/s; % of L2
 WORKLOAD = ("billboard forest: 500,000 alpha-masked billboards (1,000,002 triangles, "
             "4 RGBA8 1024^2 textures), 1920x1080 primary closest-hit + 1920x1080 shadow "
             "any-hit rays, alpha-texture intersector (cutoff 128)")
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "trace_closest_alpha_billboard_forest.md")
+# committed ncu summaries whose per-launch counters the roofline uses
+PROFILE_SUMMARIES = {
+    "trace closest alpha (primary)": os.path.join(
+        ROOT, "profiles", "trace_closest_alpha_billboard_forest.md"),
+    "trace any proc (ambient occlusion)": os.path.join(
+        ROOT, "profiles", "trace_ao_any_proc_large_incoherent.md"),
+}
 ALU_LANES_PER_SM = 64  # ALU pipe (min/max, compares, integer): 16 lanes per SMSP
 FLUSH_BYTES = 256 << 20
 
@@ -59,9 +65,9 @@ def default_params(V, image_width=FRAME_W):
 
 
 # the device code of the static trace kernels (the dominant kernel): the
-# kernels and the traversal they inline (vsr_internal.h adds host-side launch
-# structures only)
-TRACE_SOURCES = ("trace_static.cu", "vsr_device.cuh")
+# kernel templates and the traversal they inline (vsr_internal.h adds
+# host-side launch structures only; trace_k<K>.cu only instantiate)
+TRACE_SOURCES = ("trace_static.cuh", "vsr_device.cuh")
 
 
 def kernel_source_hash() -> str:
@@ -85,9 +91,10 @@ def peaks():
 
 
 def read_peaks(V, torch, dev) -> dict:
-    """Read rates of this GPU from the library's read probe (16-byte loads
-    cached in L2 only, every thread of a full-occupancy grid): a buffer of half
-    the L2 read 20 times per launch gives the L2 read peak, one of four L2
+    """Read rates of this GPU from the library's read probes (16-byte loads,
+    every thread of a full-occupancy grid): every block re-reading a 32 KB
+    buffer through L1 gives the L1 read peak; a buffer of half the L2 read
+    20 times per launch with L2-only loads the L2 read peak; one of four L2
     sizes read twice the HBM read rate.  Best of 10 launches each, CUDA events
     on the current stream; untimed with respect to the steps."""
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
@@ -106,6 +113,18 @@ def read_peaks(V, torch, dev) -> dict:
             best = max(best, buf.numel() * reps / (a.elapsed_time(b) / 1e3) / 1e9)
         out[key] = round(best, 1)
         del buf
+    buf = torch.ones(32 * 1024, dtype=torch.uint8, device=dev)
+    V.vsr_read_probe_l1(buf, 64)
+    best = 0.0
+    for _ in range(10):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        nbytes = V.vsr_read_probe_l1(buf, 64)
+        b.record()
+        torch.cuda.synchronize(dev)
+        best = max(best, nbytes / (a.elapsed_time(b) / 1e3) / 1e9)
+    out["l1"] = round(best, 1)
     out["l2_bytes"] = l2
     return out
 
@@ -172,9 +191,11 @@ class ClockSampler:
 
 
 def trace_bytes(n_rays: int, stats: np.ndarray, texel_bytes: int, texcoords: bool) -> int:
-    """32 B ray + 16 B hit per ray, 32 B per box test (one node), 48 B per
-    triangle test, and for alpha intersectors 4 B geom id per intersector call
-    plus 24 B texture coordinates and one texel per textured call."""
+    """Algorithmic bytes of one launch, counted per lane: 32 B ray + 16 B hit
+    per ray, 32 B per box test (one node), 48 B per triangle test, and for
+    intersectors that read texture coordinates 4 B geom id per intersector
+    call plus 24 B texture coordinates and `texel_bytes` per textured call
+    (the alpha texture reads one texel; procedural alpha reads none)."""
     s = stats.astype(np.int64).sum(axis=0)
     b = n_rays * (32 + 16) + 32 * int(s[0]) + 48 * int(s[1])
     if texcoords:
@@ -182,36 +203,134 @@ def trace_bytes(n_rays: int, stats: np.ndarray, texel_bytes: int, texcoords: boo
     return b
 
 
-def trace_alu_ops(n_rays: int, stats: np.ndarray, texcoords: bool) -> int:
+ALU_OPS_PER_LOOKUP = {"alpha_tex": 8, "proc_alpha": 11}
+
+
+def trace_alu_ops(n_rays: int, stats: np.ndarray, lookup_ops: int = 0) -> int:
     """Algorithmic work of one launch on the ALU pipe (the busiest unit), as
     the fewest ALU-pipe instructions this GPU needs for it (a three-input
     min/max is one instruction): 11 per box test (6 per-axis min/max, 2 each
     for the entry and exit bounds with tmin and the far limit folded in, 1
     compare), 7 per triangle test (det == 0, u >= 0, v >= 0, u + v <= 1,
     t > tmin, t < tmax, t < best), 1 per intersector call, 6 per ray set-up
-    (direction guards), and for alpha intersectors 8 per texture fetch
-    (clamps, index bounds, alpha compare)."""
+    (direction guards), and `lookup_ops` per textured consultation: 8 for
+    the alpha texture (clamps, index bounds, alpha compare), 11 for
+    procedural alpha (per coordinate: the two sign compares of the reduced
+    argument, the quotient's parity and the sign select; then the product's
+    sign)."""
     s = stats.astype(np.int64).sum(axis=0)
-    ops = 6 * n_rays + 11 * int(s[0]) + 7 * int(s[1]) + int(s[2])
-    if texcoords:
-        ops += 8 * int(s[3])
-    return ops
+    return 6 * n_rays + 11 * int(s[0]) + 7 * int(s[1]) + int(s[2]) + lookup_ops * int(s[3])
 
 
-def profiled_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
-    if not os.path.exists(PROFILE_SUMMARY):
+def render_backward_model(n_rays: int, stats: np.ndarray, grad: np.ndarray, lit: np.ndarray):
+    """Algorithmic bytes and atomics of one k_render_backward launch.  The
+    re-trace: trace_bytes with a 4-byte alpha read per textured consultation
+    (RGBA32F, alpha only), less the 16-byte hit record it does not write.
+    Then every ray with a hit and a nonzero image gradient (`grad`) reads
+    12 B of dL/dc, 12 B of vertex indices, 36 B of vertices, 4 B geom id,
+    24 B texture coordinates, 24 B texture descriptor and 48 B of the four
+    bilinear texels' colours (160 B), and adds 9 vertex gradient atomics
+    (36 B); a lit one (`lit`: nonzero shading) adds 12 texel gradient
+    atomics (48 B)."""
+    g = int(np.count_nonzero(grad))
+    gl = int(np.count_nonzero(grad & lit))
+    nbytes = trace_bytes(n_rays, stats, 4, True) - 16 * n_rays + 160 * g + 36 * g + 48 * gl
+    return nbytes, 9 * g + 12 * gl
+
+
+def ao_backward_model(hit: np.ndarray, textured: np.ndarray, visible: np.ndarray):
+    """Algorithmic bytes and atomics of one k_ao_backward launch (image
+    gradient nonzero everywhere): every pixel reads 12 B of dL/dc and its
+    16-byte hit record; a hit reads 4 B geom id; a hit on the gradient's
+    texture also reads 24 B texture coordinates, 24 B descriptor, 48 B of
+    the bilinear texels' colours and 4 B occlusion, and, if not fully
+    occluded (`visible`), adds 12 texel gradient atomics (48 B)."""
+    n = hit.size
+    h = int(np.count_nonzero(hit))
+    t = int(np.count_nonzero(hit & textured))
+    tv = int(np.count_nonzero(hit & textured & visible))
+    return 28 * n + 4 * h + 100 * t + 48 * tv, 12 * tv
+
+
+def launch_config(p) -> str:
+    """The launch configuration a profile summary is tied to."""
+    return (f"block={p.block_size} persistent={p.persistent} refill={p.refill_threshold} "
+            f"stack_regs={p.stack_regs} image_width={p.image_width}")
+
+
+def profiled_levels(kernel: str, config: str):
+    """Per-launch bytes at each memory level from the committed ncu summary
+    of `kernel` -- L1 (l1tex__t_sectors x 32), L2 (lts__t_sectors x 32) and
+    DRAM (dram__bytes_read + dram__bytes_write) -- if the summary was taken
+    on the current kernel sources and the same launch configuration."""
+    path = PROFILE_SUMMARIES.get(kernel)
+    if not path or not os.path.exists(path):
         return None
     vals = {}
-    with open(PROFILE_SUMMARY) as f:
+    with open(path) as f:
         for line in f:
             if ":" in line and line.startswith("    "):
                 k, v = line.strip().split(":", 1)
                 vals[k.strip()] = v.strip()
-    if vals.get("kernel") != kernel or vals.get("kernel_source_hash") != kernel_source_hash():
+    if (vals.get("kernel") != kernel or vals.get("kernel_source_hash") != kernel_source_hash()
+            or vals.get("launch_config") != config):
         return None
-    return int(vals["traffic_bytes_per_launch"])
+    try:
+        return {lvl: int(vals[f"{lvl}_bytes_per_launch"]) for lvl in ("l1", "l2", "dram")}
+    except (KeyError, ValueError):
+        return None
+
+
+def profile_params(V, kernel: str):
+    """The launch configuration the committed summary of `kernel` was taken
+    on, as vsr_trace_params (None without a summary)."""
+    path = PROFILE_SUMMARIES.get(kernel)
+    if not path or not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            if line.strip().startswith("launch_config:"):
+                kv = dict(x.split("=") for x in line.split(":", 1)[1].split())
+                return V.trace_params(block_size=int(kv["block"]),
+                                      persistent=int(kv["persistent"]),
+                                      refill_threshold=int(kv["refill"]),
+                                      stack_regs=int(kv["stack_regs"]),
+                                      image_width=int(kv["image_width"]))
+    return None
+
+
+def time_launch(torch, flush, stream, fn, reps=7):
+    """Median CUDA-event time (ms) of fn() on `stream`, L2 flushed before each
+    launch, after two untimed launches."""
+    ms = []
+    for k in range(reps + 2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 2:
+            ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def level_fractions(levels, ms: float, peaks_gbs: dict) -> dict:
+    """GB/s moved at each level over a launch of `ms` milliseconds, and the
+    fraction of that level's measured read peak."""
+    out = {}
+    for lvl in ("l1", "l2", "dram"):
+        gbs = levels[lvl] / (ms / 1e3) / 1e9
+        out[lvl] = {"bytes_per_launch": levels[lvl], "GBs": round(gbs, 1),
+                    "peak_GBs": peaks_gbs[lvl], "frac": round(gbs / peaks_gbs[lvl], 4)}
+    return out
+
+
+def tuned_or_default(V, s, isect, query):
+    """The configuration vsr_trace with params NULL uses for this scene,
+    intersector and query (tuned by an earlier call), else the defaults."""
+    p = V.vsr_trace_tuned_params(s, isect, query)
+    return p if p is not None else V.trace_params()
 
 
 def sm_count(torch, dev) -> int:
@@ -339,16 +458,25 @@ def run_ours(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # Launch configuration: vsr_trace_tune times its candidates on the frame
+    # (untimed, before the steps) and keeps the fastest in the scene for each
+    # query; the timed step then calls vsr_trace with params NULL.
+    tuned_p = V.vsr_trace_tune(s, d_rays, alpha, "closest", hits_p, FRAME_W, stream)
+    V.vsr_trace(s, d_rays, alpha, "closest", hits_p, None, None, stream)
+    V.vsr_make_shadow_rays(d_rays, hits_p, light, eps, rays_s, stream)
+    tuned_s = V.vsr_trace_tune(s, rays_s, alpha, "any", hits_s, FRAME_W, stream)
+    torch.cuda.synchronize(dev)
+
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        V.vsr_trace(s, d_rays, alpha, "closest", hits_p, None, p, stream)
+        V.vsr_trace(s, d_rays, alpha, "closest", hits_p, None, None, stream)
         if ev is not None:
             ev[1].record(stream)
         V.vsr_make_shadow_rays(d_rays, hits_p, light, eps, rays_s, stream)
         if ev is not None:
             ev[2].record(stream)
-        V.vsr_trace(s, rays_s, alpha, "any", hits_s, None, p, stream)
+        V.vsr_trace(s, rays_s, alpha, "any", hits_s, None, None, stream)
         if ev is not None:
             ev[3].record(stream)
 
@@ -388,44 +516,65 @@ def run_ours(args):
     ss_np = st_s.cpu().numpy().view(np.uint32)
     kernels = {
         "trace closest alpha (primary)": (statistics.mean(prim_ms), trace_bytes(n, sp_np, 4, True),
-                                          trace_alu_ops(n, sp_np, True)),
+                                          trace_alu_ops(n, sp_np, ALU_OPS_PER_LOOKUP["alpha_tex"]),
+                                          tuned_p),
         "trace any alpha (shadow)": (statistics.mean(shad_ms), trace_bytes(n, ss_np, 4, True),
-                                     trace_alu_ops(n, ss_np, True)),
+                                     trace_alu_ops(n, ss_np, ALU_OPS_PER_LOOKUP["alpha_tex"]),
+                                     tuned_s),
     }
     dom = max(kernels, key=lambda k: kernels[k][0])
-    dom_ms, dom_bytes, dom_ops = kernels[dom]
+    dom_ms, dom_bytes, dom_ops, dom_p = kernels[dom]
     hbm_peak, peak_src = peaks()
     clk_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     alu_peak = sm_count(torch, dev) * ALU_LANES_PER_SM * clk_mhz * 1e6 / 1e12
     alu_achieved = dom_ops / (dom_ms / 1e3) / 1e12
-    traffic = profiled_traffic(dom)
+    # per-level bytes come from the committed ncu summary of the dominant
+    # kernel; its launch is re-timed here on the configuration that summary
+    # was taken on (which the tuner may or may not have chosen in this run)
+    prof_p = profile_params(V, dom)
+    levels = profiled_levels(dom, launch_config(prof_p)) if prof_p is not None else None
+    traffic = levels["dram"] if levels and launch_config(prof_p) == launch_config(dom_p) else None
     roofline = {"bound": "alu", "achieved": round(alu_achieved, 3), "peak": round(alu_peak, 3),
                 "unit": "Top/s", "frac": round(alu_achieved / alu_peak, 4), "traffic": traffic,
                 "kernel": dom, "algorithmic_ops_per_launch": dom_ops,
                 "peak_source": f"{sm_count(torch, dev)} SMs x {ALU_LANES_PER_SM} ALU lanes x "
                                f"{clk_mhz:.0f} MHz",
-                "launch_ms": round(dom_ms, 4)}
+                "launch_ms": round(dom_ms, 4), "launch_config": launch_config(dom_p)}
+    rp = read_peaks(V, torch, dev)
+    level_peaks = {"l1": rp["l1"], "l2": rp["l2"], "dram": hbm_peak}
     mem = {"algorithmic_bytes_per_launch": dom_bytes,
            "algorithmic_GBs": round(dom_bytes / (dom_ms / 1e3) / 1e9, 1),
-           "hbm_peak_GBs": hbm_peak, "hbm_peak_source": peak_src}
-    rp = read_peaks(V, torch, dev)
-    mem.update({"l2_peak_GBs": rp["l2"],
-                "l2_peak_source": f"read probe: {rp['l2_bytes'] // 2} B (half the L2) read 20x "
-                                  "per launch, best of 10",
-                "l2_frac": round(dom_bytes / (dom_ms / 1e3) / 1e9 / rp["l2"], 4),
-                "hbm_read_probe_GBs": rp["hbm"]})
-    if traffic is not None:
-        hbm = traffic / (dom_ms / 1e3) / 1e9
-        mem.update({"hbm_traffic_bytes_per_launch": traffic, "hbm_achieved_GBs": round(hbm, 1),
-                    "hbm_frac": round(hbm / hbm_peak, 4)})
+           "algorithmic_note": "per-lane bytes of the scope table's model; lanes of a warp "
+                               "share sectors, so the levels below move fewer bytes",
+           "peaks": {"l1": f"{rp['l1']} GB/s, L1 read probe (every block re-reads 32 KB, "
+                           "best of 10)",
+                     "l2": f"{rp['l2']} GB/s, L2 read probe ({rp['l2_bytes'] // 2} B, half "
+                           "the L2, read 20x per launch, best of 10)",
+                     "dram": f"{hbm_peak} GB/s, {peak_src} HBM copy"},
+           "hbm_read_probe_GBs": rp["hbm"]}
+    if levels is not None:
+        dom_rays = d_rays if dom.startswith("trace closest") else rays_s
+        dom_q = "closest" if dom.startswith("trace closest") else "any"
+        prof_ms = time_launch(torch, flush, stream, lambda: V.vsr_trace(
+            s, dom_rays, alpha, dom_q, hits_p if dom_q == "closest" else hits_s, None, prof_p,
+            stream))
+        mem["levels"] = level_fractions(levels, prof_ms, level_peaks)
+        mem["levels_launch"] = {"config": launch_config(prof_p), "launch_ms": round(prof_ms, 4)}
+        mem["levels_source"] = os.path.relpath(PROFILE_SUMMARIES[dom], ROOT)
+    else:
+        mem["levels"] = None
+        mem["levels_source"] = "no ncu summary on the current sources and launch configuration"
 
     out = {"metric": METRIC, "value": round(value, 2), "unit": "Mrays/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "rays_per_step": rays_per_step,
-                      "triangles": sc.ntri, "block_size": p.block_size,
-                      "persistent": p.persistent, "image_width": p.image_width,
+                      "triangles": sc.ntri,
+                      "launch": "vsr_trace with params NULL: the configuration vsr_trace_tune "
+                                "chose on the frame (untimed, before the steps)",
+                      "tuned_primary": V.params_dict(tuned_p),
+                      "tuned_shadow": V.params_dict(tuned_s),
                       "ray_order": "row-major frame; each warp traces a 4x8 pixel tile",
                       "l2": "flushed between steps (256 MiB write)",
                       "parallelism": f"replicas x{world} (each rank traces its own frame)"},
@@ -466,10 +615,10 @@ def run_ours(args):
                 d_rays[lo:hi].copy_(h_rays[lo:hi], non_blocking=True)
             e_in.record(s_in)
             tr.wait_event(e_in)
-            V.vsr_trace(s, d_rays[lo:hi], alpha, "closest", hits_p[lo:hi], None, p, tr)
+            V.vsr_trace(s, d_rays[lo:hi], alpha, "closest", hits_p[lo:hi], None, None, tr)
             V.vsr_make_shadow_rays(d_rays[lo:hi], hits_p[lo:hi], light, eps, rays_s[lo:hi], tr)
             e_p.record(tr)
-            V.vsr_trace(s, rays_s[lo:hi], alpha, "any", hits_s[lo:hi], None, p, tr)
+            V.vsr_trace(s, rays_s[lo:hi], alpha, "any", hits_s[lo:hi], None, None, tr)
             e_s.record(tr)
             out_st.wait_event(e_p)
             with torch.cuda.stream(out_st):
@@ -587,7 +736,8 @@ def breakdown(V, s, d_rays, rays_s, n, flush, stream, torch, reps=5):
     # the clip box keeps the left half of the forest (x <= 50) and culls the rest
     clip = dict(clip_lo=(-1.0, -1.0, -1.0), clip_hi=(50.0, 10.0, 101.0))
     for q, rr in (("closest", d_rays), ("any", rays_s)):
-        extra = [("alpha_tex", "persistent"), ("alpha_tex", "persistent_tile"), ("clip", "static")]
+        extra = [("alpha_tex", "persistent"), ("alpha_tex", "persistent_tile"), ("clip", "static"),
+                 ("proc_alpha", "persistent")]
         for kind, disp in cfgs + extra:
             p = default_params(V)
             if disp.startswith("persistent"):
@@ -616,6 +766,53 @@ def breakdown(V, s, d_rays, rays_s, n, flush, stream, torch, reps=5):
             res[f"{q}/{kind}/overhead_vs_default"] = round(base / res[f"{q}/{kind}/static"] - 1, 4)
             res[f"{q}/{kind}/dynamic_vs_static"] = round(
                 res[f"{q}/{kind}/static"] / res[f"{q}/{kind}/dynamic"], 4)
+    # static vs dynamic injection at equal register budgets: both kernels
+    # compiled with __launch_bounds__(256, b) for b = 3 and 4, and both
+    # without a budget (b = 1); shared-memory stack, same tiles
+    for q, rr in (("closest", d_rays), ("any", rays_s)):
+        for kind in ("default", "alpha_tex", "proc_alpha", "count"):
+            c = cnt if kind == "count" else None
+            for cap in (1, 3, 4):
+                t = {}
+                for disp in ("static", "dynamic"):
+                    p = V.trace_params(block_size=128, image_width=FRAME_W, reg_cap_blocks=cap)
+                    isect = V.intersector(kind, disp)
+                    ms = []
+                    for r in range(reps + 2):
+                        flush.zero_()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        V.vsr_trace(s, rr, isect, q, hits, c, p, stream)
+                        e1.record(stream)
+                        e1.synchronize()
+                        if r >= 2:
+                            ms.append(e0.elapsed_time(e1))
+                    t[disp] = statistics.median(ms)
+                    res[f"equal_regs/{q}/{kind}/cap{cap}/{disp}_Mrays_s"] = round(
+                        n / (t[disp] / 1e3) / 1e6, 1)
+                res[f"equal_regs/{q}/{kind}/cap{cap}/dynamic_vs_static"] = round(
+                    t["dynamic"] / t["static"], 4)
+    # the register short stack: primary and shadow launch times per number of
+    # stack entries held in registers (the rest in shared memory), alpha
+    # texture, same tiles, at each block size
+    alpha = V.intersector("alpha_tex")
+    for block in (64, 128, 256):
+        for k in (0, 1, 2, 4, 8):
+            p = V.trace_params(block_size=block, image_width=FRAME_W, stack_regs=k)
+            for q, rr in (("closest", d_rays), ("any", rays_s)):
+                ms = []
+                for r in range(reps + 2):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    V.vsr_trace(s, rr, alpha, q, hits, None, p, stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if r >= 2:
+                        ms.append(e0.elapsed_time(e1))
+                res[f"stack_regs/{q}/block{block}/K{k}_ms"] = round(statistics.median(ms), 4)
     return res
 
 
@@ -625,24 +822,28 @@ def multi_hit(V, s, d_rays, n, flush, stream, torch, reps=5):
     query), same launch configuration as the timed step."""
     res = {}
     p = default_params(V)
-    alpha = V.intersector("alpha_tex")
     for nh in (1, 4, 8, 16):
         hits = torch.empty((n, nh, 4), dtype=torch.float32, device=d_rays.device)
-        ms = []
-        for r in range(reps + 2):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            V.vsr_trace_multi(s, d_rays, alpha, nh, hits, None, p, stream)
-            e1.record(stream)
-            e1.synchronize()
-            if r >= 2:
-                ms.append(e0.elapsed_time(e1))
-        t = statistics.median(ms)
-        found = int((hits[:, :, 3].view(torch.int32) != -1).sum().item())
-        res[f"n{nh}_Mrays_s"] = round(n / (t / 1e3) / 1e6, 1)
-        res[f"n{nh}_ms"] = round(t, 4)
-        res[f"n{nh}_hits_per_ray"] = round(found / n, 3)
+        for disp in ("static", "dynamic"):
+            alpha = V.intersector("alpha_tex", disp)
+            ms = []
+            for r in range(reps + 2):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                V.vsr_trace_multi(s, d_rays, alpha, nh, hits, None, p, stream)
+                e1.record(stream)
+                e1.synchronize()
+                if r >= 2:
+                    ms.append(e0.elapsed_time(e1))
+            t = statistics.median(ms)
+            tag = "" if disp == "static" else "dynamic_"
+            res[f"{tag}n{nh}_Mrays_s"] = round(n / (t / 1e3) / 1e6, 1)
+            res[f"{tag}n{nh}_ms"] = round(t, 4)
+            if disp == "static":
+                found = int((hits[:, :, 3].view(torch.int32) != -1).sum().item())
+                res[f"n{nh}_hits_per_ray"] = round(found / n, 3)
+        res[f"n{nh}_dynamic_vs_static"] = round(res[f"dynamic_n{nh}_ms"] / res[f"n{nh}_ms"], 4)
     return res
 
 
@@ -688,26 +889,30 @@ def instanced_bench(V, torch, dev, flush, stream, steps):
     hits_p = torch.empty((n, 4), dtype=torch.float32, device=dev)
     rays_s = torch.empty((n, 8), dtype=torch.float32, device=dev)
     hits_s = torch.empty((n, 4), dtype=torch.float32, device=dev)
-    alpha = V.intersector("alpha_tex", cutoff_u8=128)
     light = torch.from_numpy(scenes.light_dir_f32()).to(dev)
     eps = float(np.float32(1e-4 * 100.0 * math.sqrt(3)))
     p = default_params(V)
-    ms_prim, ms_shad = [], []
-    for k in range(max(3, steps // 2) + 2):
-        flush.zero_()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        ev[0].record(stream)
-        V.vsr_trace_instances(X, d_rays, alpha, "closest", hits_p, None, None, p, stream)
-        ev[1].record(stream)
-        V.vsr_make_shadow_rays(d_rays, hits_p, light, eps, rays_s, stream)
-        ev[2].record(stream)
-        V.vsr_trace_instances(X, rays_s, alpha, "any", hits_s, None, None, p, stream)
-        ev[3].record(stream)
-        ev[3].synchronize()
-        if k >= 2:
-            ms_prim.append(ev[0].elapsed_time(ev[1]))
-            ms_shad.append(ev[2].elapsed_time(ev[3]))
-    tp, ts = statistics.median(ms_prim), statistics.median(ms_shad)
+    times = {}
+    for disp in ("static", "dynamic"):
+        alpha = V.intersector("alpha_tex", disp, cutoff_u8=128)
+        ms_prim, ms_shad = [], []
+        for k in range(max(3, steps // 2) + 2):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            V.vsr_trace_instances(X, d_rays, alpha, "closest", hits_p, None, None, p, stream)
+            ev[1].record(stream)
+            V.vsr_make_shadow_rays(d_rays, hits_p, light, eps, rays_s, stream)
+            ev[2].record(stream)
+            V.vsr_trace_instances(X, rays_s, alpha, "any", hits_s, None, None, p, stream)
+            ev[3].record(stream)
+            ev[3].synchronize()
+            if k >= 2:
+                ms_prim.append(ev[0].elapsed_time(ev[1]))
+                ms_shad.append(ev[2].elapsed_time(ev[3]))
+        times[disp] = (statistics.median(ms_prim), statistics.median(ms_shad))
+    tp, ts = times["static"]
+    dp, ds = times["dynamic"]
     tile = I.meshes[0]
     X.close()
     for m in ms:
@@ -717,6 +922,9 @@ def instanced_bench(V, torch, dev, flush, stream, steps):
             "primary_closest_Mrays_s": round(n / (tp / 1e3) / 1e6, 1),
             "shadow_any_Mrays_s": round(n / (ts / 1e3) / 1e6, 1),
             "primary_ms": round(tp, 4), "shadow_ms": round(ts, 4),
+            "dynamic_primary_ms": round(dp, 4), "dynamic_shadow_ms": round(ds, 4),
+            "dynamic_vs_static_primary": round(dp / tp, 4),
+            "dynamic_vs_static_shadow": round(ds / ts, 4),
             "step_Mrays_s": round(2 * n / ((tp + ts) / 1e3) / 1e6, 1),
             "triangles_stored": sum(m.ntri for m in I.meshes),
             "triangles_instanced": int(sum(I.meshes[k].ntri for k in I.inst_mesh))}
@@ -772,9 +980,45 @@ def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):
         ms.append(ev[0].elapsed_time(ev[2]))
         fwd.append(ev[0].elapsed_time(ev[1]))
         bwd.append(ev[1].elapsed_time(ev[2]))
+    # the adjoint kernel alone: vsr_trace_backward between events (gradient
+    # buffers zeroed outside them), with exact counts for its byte model
+    hits = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    V.vsr_render(s, d_rays, isect, shade, img, hits, p, stream)
+    g = 2.0 * (img - target)
+    stt = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    tmp = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    V.vsr_trace_stats(s, d_rays, isect, "closest", tmp, stt, stream)
+    torch.cuda.synchronize(dev)
+    bk = []
+    for k in range(steps + 2):
+        gv.zero_()
+        gt.zero_()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        V.vsr_trace_backward(s, d_rays, isect, shade, g, gv, gt, p, stream)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 2:
+            bk.append(e0.elapsed_time(e1))
+    tb = statistics.median(bk)
+    prim = hits[:, 3].contiguous().view(torch.int32).cpu().numpy().view(np.uint32)
+    grad = (prim != 0xFFFFFFFF) & np.any(g.cpu().numpy() != 0.0, axis=1)
+    lit = np.any(img.cpu().numpy() != 0.0, axis=1)
+    nbytes, natomics = render_backward_model(n, stt.cpu().numpy().view(np.uint32), grad, lit)
+    rp = read_peaks(V, torch, dev)
+    gbs = nbytes / (tb / 1e3) / 1e9
     s.close()
     t = statistics.median(ms)
+    roof = {"kernel": "k_render_backward (re-trace + adjoint)", "bound": "l2",
+            "launch_ms": round(tb, 4), "algorithmic_bytes_per_launch": nbytes,
+            "achieved": round(gbs, 1), "unit": "GB/s", "peak": rp["l2"],
+            "frac": round(gbs / rp["l2"], 4), "atomics_per_launch": natomics,
+            "atomics_per_s": round(natomics / (tb / 1e3), 1),
+            "note": "one launch is 262,144 rays, about a quarter of a millisecond: launch-"
+                    "latency scale; the scene (65 k triangles, 4 MB texture) is L2-resident"}
     return {"value": round(n / (t / 1e3) / 1e6, 2), "unit": "Mrays/s", "ms_per_step": round(t, 4),
+            "roofline": roof,
             "forward_ms": round(statistics.median(fwd), 4),
             "backward_ms": round(statistics.median(bwd), 4),
             "workload": "displaced icosphere, 64,980 triangles, 512x512 rays, alpha-texture "
@@ -828,7 +1072,7 @@ def batch_bench(V, torch, dev, flush, stream, steps):
                   "speedup": round(tp / tb, 3), "batched_ms": round(tb, 3),
                   "per_scene_ms": round(tp, 3),
                   "tuned": {"block_size": p.block_size, "refill_threshold": p.refill_threshold,
-                            "blocks_per_sm": p.blocks_per_sm}}
+                            "blocks_per_sm": p.blocks_per_sm, "stack_regs": p.stack_regs}}
     for h in handles:
         h.close()
     return out
@@ -885,13 +1129,48 @@ def large_bench(V, torch, dev, flush, stream, steps):
     for kind in ("proc_alpha", "count"):
         out[f"ao_any/{kind}/dynamic_vs_static"] = round(
             out[f"ao_any/{kind}/static_Mrays_s"] / out[f"ao_any/{kind}/dynamic_Mrays_s"], 4)
+    # static vs dynamic at equal register budgets (both kernels compiled for
+    # 1 = no budget, 3 or 4 resident 256-thread blocks per SM), block 128
+    for kind in ("proc_alpha", "count", "default"):
+        c = cnt if kind == "count" else None
+        for cap in (1, 3, 4):
+            t = {}
+            for disp in ("static", "dynamic"):
+                isect = V.intersector(kind, disp)
+                cp = V.trace_params(block_size=128, reg_cap_blocks=cap)
+                t[disp] = timed(lambda: V.vsr_trace(s, ao, isect, "any", ao_hits, c, cp, stream),
+                                reps)
+            out[f"ao_any/equal_regs/{kind}/cap{cap}/static_ms"] = round(t["static"], 3)
+            out[f"ao_any/equal_regs/{kind}/cap{cap}/dynamic_ms"] = round(t["dynamic"], 3)
+            out[f"ao_any/equal_regs/{kind}/cap{cap}/dynamic_vs_static"] = round(
+                t["dynamic"] / t["static"], 4)
     st = torch.empty((m, 4), dtype=torch.int32, device=dev)
     V.vsr_trace_stats(s, ao, proc, "any", ao_hits, st, stream)
     torch.cuda.synchronize(dev)
-    b = trace_bytes(m, st.cpu().numpy().view(np.uint32), 16, True)
+    st_np = st.cpu().numpy().view(np.uint32)
+    b = trace_bytes(m, st_np, 0, True)  # procedural alpha reads no texel
+    ops = trace_alu_ops(m, st_np, ALU_OPS_PER_LOOKUP["proc_alpha"])
     t = out["ao_any/proc_alpha/static_ms"]
     out["ao_any/proc_alpha/static_algorithmic_bytes"] = b
     out["ao_any/proc_alpha/static_algorithmic_GBs"] = round(b / (t / 1e3) / 1e9, 1)
+    clk = 2070.0
+    alu_peak = sm_count(torch, dev) * ALU_LANES_PER_SM * clk * 1e6 / 1e12
+    out["ao_any/proc_alpha/static_alu_frac"] = round(ops / (t / 1e3) / 1e12 / alu_peak, 4)
+    ao_p = tuned_or_default(V, s, proc, "any")
+    out["ao_any/proc_alpha/static_launch"] = launch_config(ao_p)
+    kern = "trace any proc (ambient occlusion)"
+    prof_p = profile_params(V, kern)
+    levels = profiled_levels(kern, launch_config(prof_p)) if prof_p is not None else None
+    if levels is not None:
+        rp = read_peaks(V, torch, dev)
+        tp = time_launch(torch, flush, stream, lambda: V.vsr_trace(
+            s, ao, proc, "any", ao_hits, None, prof_p, stream))
+        out["ao_any/proc_alpha/static_levels"] = level_fractions(
+            levels, tp, {"l1": rp["l1"], "l2": rp["l2"], "dram": peaks()[0]})
+        out["ao_any/proc_alpha/static_levels_launch"] = {"config": launch_config(prof_p),
+                                                         "launch_ms": round(tp, 4)}
+    else:
+        out["ao_any/proc_alpha/static_levels"] = None
     # ambient-occlusion render (primary trace, occlusion count with one thread
     # per AO ray, shading) and its texel adjoint from the saved hits
     eps = scenes.shadow_eps(sc)
@@ -911,6 +1190,24 @@ def large_bench(V, torch, dev, flush, stream, steps):
     out["ao_render/bwd_ms"] = round(tb, 3)
     out["ao_render/fwd_bwd_ms"] = round(tfb, 3)
     out["ao_render/fwd_bwd_Mpixels_s"] = round(n / (tfb / 1e3) / 1e6, 1)
+    # roofline of the texel adjoint (k_ao_backward) from its byte model
+    fwd()
+    torch.cuda.synchronize(dev)
+    prim = hits[:, 3].contiguous().view(torch.int32).cpu().numpy().view(np.uint32)
+    hit = prim != 0xFFFFFFFF
+    geom = np.asarray(sc.geom_id, np.uint32)
+    textured = np.zeros_like(hit)
+    textured[hit] = geom[prim[hit]] == 0
+    visible = occ.cpu().numpy() < 1.0
+    nbytes, natomics = ao_backward_model(hit, textured, visible)
+    rp = read_peaks(V, torch, dev)
+    gbs = nbytes / (tb / 1e3) / 1e9
+    out["ao_render/bwd_roofline"] = {
+        "kernel": "k_ao_backward (texel adjoint from saved hits)", "bound": "l2",
+        "launch_ms": round(tb, 4), "algorithmic_bytes_per_launch": nbytes,
+        "achieved": round(gbs, 1), "unit": "GB/s", "peak": rp["l2"],
+        "frac": round(gbs / rp["l2"], 4), "atomics_per_launch": natomics,
+        "atomics_per_s": round(natomics / (tb / 1e3), 1)}
     s.close()
     return out
 
@@ -924,8 +1221,12 @@ def main():
     ap.add_argument("--ref-stride", type=int, default=1)
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--leg", choices=["all", "large", "batch", "fwd_bwd"], default="all",
-                    help="run one auxiliary measurement alone (profiling)")
+    ap.add_argument("--leg", choices=["all", "large", "batch", "fwd_bwd", "trace", "ao"],
+                    default="all", help="run one auxiliary measurement alone (profiling)")
+    ap.add_argument("--block", type=int, default=128,
+                    help="--leg trace/ao: block size of the profiled launches")
+    ap.add_argument("--stack-regs", type=int, default=0,
+                    help="--leg trace/ao: stack entries in registers of the profiled launches")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -934,6 +1235,54 @@ def main():
     if args.leg != "all":
         return run_leg(args)
     return run_ours(args)
+
+
+def profile_leg(V, torch, dev, flush, stream, args):
+    """Launches for an ncu capture at an explicit configuration (no tuning):
+    `trace` -- the forest's primary closest-hit and shadow any-hit passes with
+    the alpha texture on 4x8 pixel tiles, `steps` times each; `ao` -- the
+    16 M-triangle workload's ambient-occlusion any-hit pass with procedural
+    alpha (static dispatch), `steps` times.  Each launch is preceded by the
+    256 MiB L2 flush, as in the timed steps."""
+    from paper_1912_12786_gb300.inputs import scenes
+    if args.leg == "trace":
+        sc, rays = scenes.billboard_forest()
+        width = FRAME_W
+    else:
+        sc, rays = scenes.large_incoherent()
+        width = 0
+    s = V.scene_from_inputs(sc, sc.bvh())
+    n = len(rays)
+    d = torch.from_numpy(rays).to(dev)
+    hits = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    p = V.trace_params(block_size=args.block, stack_regs=args.stack_regs, image_width=width)
+    out = {"config": launch_config(p)}
+    if args.leg == "trace":
+        alpha = V.intersector("alpha_tex")
+        rs = torch.empty((n, 8), dtype=torch.float32, device=dev)
+        hs = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        V.vsr_trace(s, d, alpha, "closest", hits, None, p, stream)
+        V.vsr_make_shadow_rays(d, hits, scenes.light_dir_f32(), scenes.shadow_eps(sc), rs, stream)
+        for _ in range(args.steps):
+            flush.zero_()
+            V.vsr_trace(s, d, alpha, "closest", hits, None, p, stream)
+            flush.zero_()
+            V.vsr_trace(s, rs, alpha, "any", hs, None, p, stream)
+    else:
+        proc = V.intersector("proc_alpha")
+        m = 4 * n
+        ao = torch.empty((m, 8), dtype=torch.float32, device=dev)
+        ao_hits = torch.empty((m, 4), dtype=torch.float32, device=dev)
+        xi = torch.from_numpy(scenes.ao_random(n, 4)).to(dev)
+        V.vsr_trace(s, d, proc, "closest", hits, None, V.trace_params(image_width=FRAME_W), stream)
+        V.vsr_make_ao_rays(s, d, hits, 4, xi, 0.5, scenes.shadow_eps(sc), ao, stream)
+        for _ in range(args.steps):
+            flush.zero_()
+            V.vsr_trace(s, ao, proc, "any", ao_hits, None, p, stream)
+    torch.cuda.synchronize(dev)
+    out["device_error"] = V.vsr_get_device_error(s)
+    s.close()
+    return out
 
 
 def run_leg(args):
@@ -945,7 +1294,9 @@ def run_leg(args):
     V.lib()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    if args.leg == "large":
+    if args.leg in ("trace", "ao"):
+        res = profile_leg(V, torch, dev, flush, stream, args)
+    elif args.leg == "large":
         res = large_bench(V, torch, dev, flush, stream, args.steps)
     elif args.leg == "batch":
         res = batch_bench(V, torch, dev, flush, stream, args.steps)

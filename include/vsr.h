@@ -139,12 +139,14 @@ typedef enum vsr_query {
     VSR_ANY = 1      /* first accepted candidate in traversal order */
 } vsr_query;
 
-/* Launch configuration; pass NULL for the tuned defaults. */
+/* Launch configuration.  vsr_trace with params == NULL uses the
+ * configuration vsr_trace_tune chose for the scene, intersector and query (or
+ * tunes one on the call's own rays, see vsr_trace_tune); other entry points
+ * take NULL as the defaults {128, 0, 16, 0, 0, 0, 0, 0, 0}. */
 typedef struct vsr_trace_params {
     uint32_t block_size;       /* threads per block, multiple of 32, 32..256 */
     uint32_t persistent;       /* 0: one ray per thread; 1: persistent warps
-                                  (static dispatch; not for the procedural-
-                                  alpha any-hit query, which is refused) */
+                                  (static dispatch) */
     uint32_t refill_threshold; /* persistent: refill idle lanes when fewer
                                   than this many of 32 are still active */
     uint32_t blocks_per_sm;    /* persistent: resident blocks per SM (0=auto) */
@@ -157,6 +159,34 @@ typedef struct vsr_trace_params {
                                   keep their layout.  Results are identical;
                                   coherent (camera) rays trace faster.  Not for
                                   batched launches. */
+    uint32_t stack_regs;       /* traversal stack entries kept in registers
+                                  (the rest spill to shared memory): 0, 1, 2,
+                                  4 or 8 for vsr_trace and vsr_path_trace with
+                                  static dispatch, 0, 2 or 4 for batches; the
+                                  other queries keep the stack in shared
+                                  memory and ignore it.  Results are
+                                  identical for every value. */
+    uint32_t watchdog_iterations; /* persistent launches and batches: outer-
+                                  loop iterations a warp may run (0 = no
+                                  limit).  A warp that runs out sets
+                                  VSR_DEVERR_TIMEOUT in the scene's device
+                                  error word, writes miss records for its
+                                  rays in flight and stops: rays not yet
+                                  traced keep whatever their hit records
+                                  held. */
+    uint32_t watchdog_ms;      /* persistent launches and batches: global-timer
+                                  budget per warp, checked every 256
+                                  iterations; 0 = 60000 ms, 0xFFFFFFFF = no
+                                  limit.  Running out acts as above. */
+    uint32_t reg_cap_blocks;   /* register budget of vsr_trace's one-ray-per-
+                                  thread kernels, for measurement: 0 = each
+                                  kernel's own (static: none; dynamic: 3
+                                  blocks for closest hit, 4 for any hit);
+                                  1 = none; 3 or 4 = compiled to fit that many
+                                  256-thread blocks per SM (static: stack_regs
+                                  0, intersectors default, alpha texture,
+                                  procedural alpha and count).  Results are
+                                  identical for every value. */
 } vsr_trace_params;
 
 typedef struct vsr_scene vsr_scene;
@@ -213,7 +243,12 @@ vsr_status vsr_bvh_load(vsr_scene* scene, const void* blob, size_t bytes);
  *   hits     device, vsr_hit [n], 16-byte aligned, caller-owned, written
  *   counters device uint32 [n*2] or NULL; only for VSR_ISECT_COUNT, which
  *            writes (box tests, triangle tests) per ray (bvh_costs)
- *   params   NULL for the defaults
+ *   params   NULL: the configuration vsr_trace_tune chose for this scene,
+ *            intersector kind, dispatch and query; if there is none, the
+ *            first such call tunes one on its own rays in buffer order (as
+ *            vsr_trace_tune with image_width 0: synchronous, the hits written
+ *            several times, the last time with the result) and keeps it.  On
+ *            a stream that is being captured the defaults apply instead.
  * Traversal order is fixed (root box tested once; at an inner node both
  * children are tested and, if both are hit, the child on the side of the
  * sign of the direction along the node's split axis is visited first; LIFO
@@ -223,6 +258,31 @@ vsr_status vsr_bvh_load(vsr_scene* scene, const void* blob, size_t bytes);
 vsr_status vsr_trace(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
                      const vsr_intersector* isect, int32_t query, vsr_hit* hits,
                      uint32_t* counters, const vsr_trace_params* params, vsr_stream stream);
+
+/*
+ * Choose vsr_trace's launch configuration for (scene, intersector kind,
+ * dispatch, query) by timing candidates on the caller's rays, keep it in the
+ * scene for vsr_trace calls with params == NULL and return it in *out.
+ * Candidates: one ray per thread with block 64, 128 or 256 and 0, 1, 2, 4 or
+ * 8 stack entries in registers (static dispatch; 0 for dynamic), then, for
+ * static dispatch, the persistent launch at the fastest block and depth with
+ * refill thresholds 1, 8, 16 and 24.  Every candidate takes image_width (0:
+ * buffer order); all give the same hits, so only the time differs.
+ * Synchronous (stream synchronised per candidate); hits is written several
+ * times; counters are not written.  Not on a stream being captured
+ * (VSR_ERR_STATE).  The configuration stays with the scene (vsr_scene_update
+ * keeps it); a new call for the same key replaces it.
+ * Errors as vsr_trace; VSR_ERR_ARG also for n == 0 or out == NULL.
+ */
+vsr_status vsr_trace_tune(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
+                          const vsr_intersector* isect, int32_t query, uint32_t image_width,
+                          vsr_hit* hits, vsr_trace_params* out, vsr_stream stream);
+
+/* The configuration vsr_trace uses with params == NULL for (scene,
+ * intersector kind, dispatch, query), if one was tuned (VSR_ERR_STATE if
+ * none).  Host only. */
+vsr_status vsr_trace_tuned_params(vsr_scene* scene, const vsr_intersector* isect, int32_t query,
+                                  vsr_trace_params* out);
 
 /*
  * Multi-hit query: the first max_hits accepted hits of each ray in ascending
@@ -236,7 +296,8 @@ vsr_status vsr_trace(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
  *             nearest first, then miss records (t = +inf, u = v = 0,
  *             prim = VSR_MISS)
  *   counters  as vsr_trace (COUNT intersector only), or NULL
- *   max_hits  1..16; static dispatch; params->persistent must be 0
+ *   max_hits  1..16; static or dynamic dispatch (the callbacks as for
+ *             vsr_trace); params->persistent must be 0
  * Errors as vsr_trace.
  */
 vsr_status vsr_trace_multi(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
@@ -312,7 +373,9 @@ vsr_status vsr_instances_create(vsr_scene* const* meshes, uint32_t nmeshes,
 vsr_status vsr_instances_destroy(vsr_instances* instances);
 
 /*
- * Closest-hit or any-hit over an instance set with a static intersector: the
+ * Closest-hit or any-hit over an instance set with the intersector compiled
+ * in (static dispatch) or reached through the callback tables (dynamic
+ * dispatch; the callbacks see the mesh of the instance being traversed): the
  * top-level BVH is traversed while-while with the world-space ray (the same
  * order rule as a mesh), and at each instance the mesh's own traversal runs
  * with the object-space ray, continuing the running result.  Closest-hit
@@ -374,7 +437,10 @@ vsr_status vsr_make_shadow_rays(const vsr_ray* prim_rays, const vsr_hit* prim_hi
  * All calls share the array: calls that overlap on the GPU race and must be
  * ordered (for example on one stream).  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  n above 2^40 is rejected with VSR_ERR_ARG.
+ * before any stream capture.  The address is kept per device together with
+ * the id of the CUDA context it belongs to, and looked up again if that
+ * context was replaced (for example after cudaDeviceReset).  n above
+ * (2^31 - 2) * 32, the limit of one launch, is rejected with VSR_ERR_ARG.
  */
 vsr_status vsr_trace_persistent_noalloc(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
                                         const vsr_intersector* isect, int32_t query,
@@ -394,15 +460,15 @@ vsr_status vsr_trace_persistent_noalloc(vsr_scene* scene, const vsr_ray* rays, u
  * vsr_batch_create records the scenes (each with a loaded BVH, all on one
  * device), the device ray and hit arrays (rays[k]/hits[k]: vsr_ray/vsr_hit
  * [n[k]], 16-byte aligned, caller-owned; n[k] may be 0), the intersector
- * (static dispatch; not the clip box, and not the procedural-alpha
- * intersector with the any-hit query, which is refused as for persistent
- * vsr_trace) and the query, and builds the device tables.  With
- * params == NULL the launch configuration (block size, refill threshold,
- * blocks per SM) is chosen by timing a grid of candidates on the batch itself
- * at the first launch; results are cached per workload shape in the process
- * and, if the environment variable VSR_TUNE_CACHE names a file, there too.
- * The traversal stack depth is the deepest BVH's depth, so it needs no
- * tuning.
+ * (static dispatch; not the clip box) and the query, and builds the device
+ * tables.  With params == NULL the launch configuration (block size, refill
+ * threshold, blocks per SM, stack entries in registers) is chosen by timing
+ * candidates on the batch itself at the first launch; results are cached per
+ * workload shape in the process and, if the environment variable
+ * VSR_TUNE_CACHE names a file, there too.  The shared-memory part of the
+ * traversal stack is sized for the deepest BVH.  The persistent loop has the
+ * watchdog of vsr_trace_params (a timeout is reported to every scene with a
+ * ray in flight and to scene 0).
  *
  * vsr_batch_launch: the first call synchronises `stream`, tunes if needed,
  * runs the batch once and captures the launch (counter reset + kernel) in a
@@ -560,6 +626,20 @@ vsr_status vsr_make_ao_rays(vsr_scene* scene, const vsr_ray* prim_rays, const vs
  * VSR_ERR_CUDA if the launch fails.  Asynchronous. */
 vsr_status vsr_read_probe(const void* buf, uint64_t bytes, uint32_t reps, vsr_stream stream);
 
+/* L1 read probe, the denominator of the L1 level of the memory roofline.
+ * One launch in which every block of a full-occupancy grid (SMs x resident
+ * 512-thread blocks) reads all of `buf` `reps` times with 16-byte L1-cached
+ * loads; the buffer is small enough to stay in every SM's L1, so after the
+ * first pass the reads are L1 hits.  *bytes_read receives the bytes the
+ * launch reads (blocks x bytes x reps); the caller times the launch.
+ *   buf    device memory of the current device, 16-byte aligned (not owned);
+ *   bytes  a nonzero multiple of 16, at most 65536, within buf's allocation;
+ *   reps   passes, >= 1.
+ * Errors as vsr_read_probe; VSR_ERR_ARG also for bytes above 65536 or a null
+ * bytes_read.  Asynchronous. */
+vsr_status vsr_read_probe_l1(const void* buf, uint64_t bytes, uint32_t reps,
+                             uint64_t* bytes_read, vsr_stream stream);
+
 /* ---------------------------------------------------------------- errors */
 
 /* Message describing the last failure on the calling thread ("" if none). */
@@ -572,12 +652,21 @@ const char* vsr_last_error(void);
  *   bit 2: a render or backward kernel found a load whose address did not
  *          match its width and skipped it (vsr_last_error() names the line);
  *   bit 3: a caller-supplied hit record named a primitive out of range
- *          (skipped; vsr_make_ao_rays gives its rays inactive).
+ *          (skipped; vsr_make_ao_rays gives its rays inactive);
+ *   bit 4 (VSR_DEVERR_TIMEOUT): a persistent or batched launch ran out of
+ *          its watchdog budget (vsr_trace_params.watchdog_iterations,
+ *          watchdog_ms); the launch's results are incomplete.  A batch
+ *          reports it to every scene with a ray in flight and to scene 0.
  * Bits 0 and 1 end that ray as a miss; neither can happen with a validated
  * blob (each node is visited at most once per ray, and descent strictly
- * increases the node index).  All four checks exist so that a corrupted
- * structure or a bad address gives an error instead of a fault or an
- * endless loop. */
+ * increases the node index).  These checks exist so that a corrupted
+ * structure, a bad address or a loop that does not end gives an error
+ * instead of a fault or a hung GPU. */
+#define VSR_DEVERR_STACK 0x1u
+#define VSR_DEVERR_STEPS 0x2u
+#define VSR_DEVERR_ALIGN 0x4u
+#define VSR_DEVERR_HIT 0x8u
+#define VSR_DEVERR_TIMEOUT 0x10u
 vsr_status vsr_get_device_error(vsr_scene* scene, uint32_t* word);
 
 /* Library version, e.g. 100 for 0.1.0. */

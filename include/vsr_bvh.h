@@ -1,9 +1,9 @@
 /*
  * vsr_bvh.h — host-side BVH construction and the serialised BVH blob format.
  *
- * The paper traverses "a BVH built over some primitives" (Section 3.1) with
- * the while-while scheme of Aila and Laine (Section 3.2) but does not say how
- * the BVH is built.  This library builds it once on the host with a binned
+ * The paper's queries run over a BVH of primitives (Section 3.1), traversed
+ * with Aila and Laine's while-while scheme (Section 3.2), but it does not say
+ * how the BVH is built.  This library builds it once on the host with a binned
  * surface-area heuristic and serialises it into a self-describing blob.  The
  * blob is plain data: the GPU loader (vsr_bvh_load in vsr.h) and any other
  * consumer parse it on their own.  The builder computes only bounding boxes and

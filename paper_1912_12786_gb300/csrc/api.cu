@@ -41,6 +41,14 @@ struct vsr_scene {
     uint32_t* d_levels = nullptr;
     std::vector<uint32_t> level_offsets;
     std::vector<TexDesc> h_tex;
+    // launch configurations chosen by vsr_trace_tune, per (intersector kind,
+    // dispatch, query); read by vsr_trace with params == NULL
+    struct Tuned {
+        int32_t kind, dispatch, query;
+        vsr_trace_params p;
+    };
+    std::mutex tune_mutex;
+    std::vector<Tuned> tuned;
 };
 
 namespace {
@@ -299,6 +307,33 @@ vsr_status make_map(uint64_t n, uint32_t width, RayMap& m) {
     return VSR_OK;
 }
 
+constexpr vsr_trace_params kDefaultParams{128u, 0u, 16u, 0u, 0u, 0u, 0u, 0u, 0u};
+constexpr uint32_t kDefaultWatchdogMs = 60000u;
+
+// Watchdog of a persistent loop from the launch parameters (0 ms: the
+// default budget; 0xFFFFFFFF ms: none).
+Watchdog make_watchdog(const vsr_trace_params& p) {
+    Watchdog w{};
+    w.max_iters = p.watchdog_iterations;
+    const uint32_t ms = p.watchdog_ms == 0 ? kDefaultWatchdogMs : p.watchdog_ms;
+    w.max_ns = ms == 0xFFFFFFFFu ? 0ull : (unsigned long long)ms * 1000000ull;
+    return w;
+}
+
+// The fields of a launch that the parameters decide (validated already).
+vsr_status apply_params(LaunchArgs& a, uint64_t n, const vsr_trace_params& prm) {
+    vsr_status st = make_map(n, prm.image_width, a.map);
+    if (st != VSR_OK) return st;
+    a.block = prm.block_size;
+    a.persistent = prm.persistent;
+    a.refill = prm.refill_threshold;
+    a.blocks_per_sm = prm.blocks_per_sm;
+    a.stack_regs = prm.stack_regs;
+    a.wd = make_watchdog(prm);
+    a.reg_cap = prm.reg_cap_blocks;
+    return VSR_OK;
+}
+
 vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
                           const vsr_intersector* is, int32_t query, vsr_hit* hits,
                           const vsr_trace_params* p, LaunchArgs& a) {
@@ -306,7 +341,7 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (!s->has_bvh) return fail(VSR_ERR_STATE, "no BVH loaded into the scene");
     vsr_status st = validate_isect(is, query);
     if (st != VSR_OK) return st;
-    vsr_trace_params prm{128u, 0u, 16u, 0u, 0u};
+    vsr_trace_params prm = kDefaultParams;
     if (p) prm = *p;
     if (prm.block_size < 32 || prm.block_size > 256 || prm.block_size % 32)
         return fail(VSR_ERR_ARG, "block_size must be a multiple of 32 in 32..256");
@@ -314,13 +349,20 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (prm.refill_threshold < 1 || prm.refill_threshold > 32)
         return fail(VSR_ERR_ARG, "refill_threshold must be in 1..32");
     if (prm.blocks_per_sm > 32) return fail(VSR_ERR_ARG, "blocks_per_sm above 32");
+    if (!stack_regs_supported(prm.stack_regs))
+        return fail(VSR_ERR_ARG, "stack_regs must be 0, 1, 2, 4 or 8");
+    if (prm.reg_cap_blocks != 0 && prm.reg_cap_blocks != 1 && prm.reg_cap_blocks != 3 &&
+        prm.reg_cap_blocks != 4)
+        return fail(VSR_ERR_ARG, "reg_cap_blocks must be 0, 1, 3 or 4");
+    if ((prm.reg_cap_blocks == 3 || prm.reg_cap_blocks == 4) &&
+        is->dispatch == VSR_DISPATCH_STATIC &&
+        (prm.persistent || prm.stack_regs || is->kind < VSR_ISECT_DEFAULT ||
+         is->kind > VSR_ISECT_COUNT || prm.block_size > 256))
+        return fail(VSR_ERR_ARG,
+                    "reg_cap_blocks 3 and 4 with static dispatch: one ray per thread, stack_regs "
+                    "0, intersector default, alpha texture, procedural alpha or count");
     if (prm.persistent && is->dispatch == VSR_DISPATCH_DYNAMIC)
         return fail(VSR_ERR_ARG, "persistent launches use static dispatch only");
-    // This one instantiation stalled on the GPU twice without a cause found;
-    // it is refused until one is (the one-ray-per-thread launch serves it).
-    if (prm.persistent && is->kind == VSR_ISECT_PROC_ALPHA && query == VSR_ANY)
-        return fail(VSR_ERR_ARG,
-                    "persistent launch of the procedural-alpha any-hit query is disabled");
     if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull)
         return fail(VSR_ERR_ARG, "too many rays for one launch");
     if (n > 0) {
@@ -330,7 +372,7 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
         if (st != VSR_OK) return st;
     }
     a = LaunchArgs{};
-    st = make_map(n, prm.image_width, a.map);
+    st = apply_params(a, n, prm);
     if (st != VSR_OK) return st;
     a.sc = s->dev;
     a.ip = isect_params(is);
@@ -338,13 +380,101 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     a.n = n;
     a.hits = reinterpret_cast<float4*>(hits);
     a.query = query;
-    a.block = prm.block_size;
-    a.persistent = prm.persistent;
-    a.refill = prm.refill_threshold;
-    a.blocks_per_sm = prm.blocks_per_sm;
     a.work = s->d_work;
     a.dyn_user = s->d_user;
     return VSR_OK;
+}
+
+// Time `c` on the launch `base` describes (the caller's rays and hit
+// buffer): one warm-up launch, then the mean of two launches between CUDA
+// events on base.stream.
+cudaError_t time_params(const LaunchArgs& base, const vsr_trace_params& c, int kind,
+                        bool dynamic, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+    LaunchArgs a = base;
+    if (apply_params(a, a.n, c) != VSR_OK) return cudaErrorInvalidValue;
+    auto launch = [&]() { return dynamic ? launch_dynamic(a, kind) : launch_static(a, kind, false); };
+    cudaError_t e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, a.stream);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, a.stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    *ms *= 0.5f;
+    return e;
+}
+
+// Choose a launch configuration for (scene, intersector, query) by timing
+// candidates on the caller's rays, and remember it in the scene.  First pass:
+// one ray per thread, block 64/128/256 x register-stack depth 0/1/2/4/8
+// (depth 0 only for dynamic dispatch), starting from the default (128, 0);
+// second pass (static dispatch): the persistent launch at the best block and
+// depth with refill thresholds 1/8/16/24.  Every candidate keeps the caller's
+// image_width.
+vsr_status tune_trace(vsr_scene* s, const LaunchArgs& base, const vsr_intersector* is,
+                      int32_t query, uint32_t image_width, vsr_trace_params* out) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    VSR_CUDA(cudaStreamIsCapturing(base.stream, &cap), "capture status");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(VSR_ERR_STATE, "cannot tune while the stream is being captured");
+    const bool dynamic = is->dispatch == VSR_DISPATCH_DYNAMIC;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    VSR_CUDA(cudaEventCreate(&e0), "tune events");
+    cudaError_t e = cudaEventCreate(&e1);
+    vsr_trace_params best = kDefaultParams;
+    best.image_width = image_width;
+    float best_ms = 0.0f;
+    bool have = false;
+    // A candidate replaces the best only if it is at least 2% faster, and the
+    // default comes first, so timing noise between near-equal candidates
+    // does not change the choice from one run to the next.
+    auto consider = [&](const vsr_trace_params& c) {
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = time_params(base, c, is->kind, dynamic, e0, e1, &ms);
+        if (e == cudaSuccess && (!have || ms < 0.98f * best_ms)) {
+            best = c;
+            best_ms = ms;
+            have = true;
+        }
+    };
+    consider(vsr_trace_params{128u, 0u, 16u, 0u, image_width, 0u, 0u, 0u, 0u});
+    for (uint32_t b : {64u, 128u, 256u})
+        for (uint32_t k : {0u, 1u, 2u, 4u, 8u})
+            if ((!dynamic || k == 0) && !(b == 128u && k == 0u))
+                consider(vsr_trace_params{b, 0u, 16u, 0u, image_width, k, 0u, 0u, 0u});
+    if (!dynamic) {
+        const vsr_trace_params one = best;
+        for (uint32_t r : {1u, 8u, 16u, 24u}) {
+            vsr_trace_params c = one;
+            c.persistent = 1u;
+            c.refill_threshold = r;
+            consider(c);
+        }
+    }
+    if (e1) cudaEventDestroy(e1);
+    cudaEventDestroy(e0);
+    if (e != cudaSuccess) return cuda_fail(e, "trace tuning");
+    {
+        std::lock_guard<std::mutex> lock(s->tune_mutex);
+        bool found = false;
+        for (auto& t : s->tuned)
+            if (t.kind == is->kind && t.dispatch == is->dispatch && t.query == query) {
+                t.p = best;
+                found = true;
+            }
+        if (!found) s->tuned.push_back({is->kind, is->dispatch, query, best});
+    }
+    *out = best;
+    return VSR_OK;
+}
+
+bool tuned_params(vsr_scene* s, const vsr_intersector* is, int32_t query, vsr_trace_params* out) {
+    std::lock_guard<std::mutex> lock(s->tune_mutex);
+    for (const auto& t : s->tuned)
+        if (t.kind == is->kind && t.dispatch == is->dispatch && t.query == query) {
+            *out = t.p;
+            return true;
+        }
+    return false;
 }
 
 }  // namespace
@@ -546,6 +676,31 @@ vsr_status vsr_trace(vsr_scene* s, const vsr_ray* rays, uint64_t n, const vsr_in
     LaunchArgs a;
     vsr_status st = prepare_launch(s, rays, n, is, query, hits, p, a);
     if (st != VSR_OK) return st;
+    vsr_trace_params tp;
+    if (!p && n > 0) {
+        // the configuration tuned for this scene, intersector and query; the
+        // first such call tunes on its own rays unless the stream is being
+        // captured, in which case the defaults apply
+        bool have = tuned_params(s, is, query, &tp);
+        if (!have) {
+            a.stream = reinterpret_cast<cudaStream_t>(stream);
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(a.stream, &cap) != cudaSuccess) {
+                cudaGetLastError();
+                cap = cudaStreamCaptureStatusActive;
+            }
+            if (cap == cudaStreamCaptureStatusNone) {
+                DeviceGuard g(s->device);
+                st = tune_trace(s, a, is, query, 0u, &tp);
+                if (st != VSR_OK) return st;
+                have = true;
+            }
+        }
+        if (have) {
+            st = apply_params(a, n, tp);
+            if (st != VSR_OK) return st;
+        }
+    }
     if (counters) {
         if (is->kind != VSR_ISECT_COUNT)
             return fail(VSR_ERR_ARG, "counters are written by the COUNT intersector only");
@@ -564,13 +719,39 @@ vsr_status vsr_trace(vsr_scene* s, const vsr_ray* rays, uint64_t n, const vsr_in
     return VSR_OK;
 }
 
+vsr_status vsr_trace_tune(vsr_scene* s, const vsr_ray* rays, uint64_t n,
+                          const vsr_intersector* is, int32_t query, uint32_t image_width,
+                          vsr_hit* hits, vsr_trace_params* out, vsr_stream stream) {
+    g_err.clear();
+    if (!out) return fail(VSR_ERR_ARG, "out is null");
+    if (n == 0) return fail(VSR_ERR_ARG, "tuning needs at least one ray");
+    vsr_trace_params base = kDefaultParams;
+    base.image_width = image_width;
+    LaunchArgs a;
+    vsr_status st = prepare_launch(s, rays, n, is, query, hits, &base, a);
+    if (st != VSR_OK) return st;
+    if (is->kind == VSR_ISECT_COUNT) a.counters = nullptr;  // counters are not written
+    a.stream = reinterpret_cast<cudaStream_t>(stream);
+    DeviceGuard g(s->device);
+    return tune_trace(s, a, is, query, image_width, out);
+}
+
+vsr_status vsr_trace_tuned_params(vsr_scene* s, const vsr_intersector* is, int32_t query,
+                                  vsr_trace_params* out) {
+    g_err.clear();
+    if (!s || !out) return fail(VSR_ERR_ARG, "null argument");
+    vsr_status st = validate_isect(is, query);
+    if (st != VSR_OK) return st;
+    if (!tuned_params(s, is, query, out))
+        return fail(VSR_ERR_STATE, "no tuned configuration for this intersector and query");
+    return VSR_OK;
+}
+
 vsr_status vsr_trace_multi(vsr_scene* s, const vsr_ray* rays, uint64_t n,
                            const vsr_intersector* is, uint32_t max_hits, vsr_hit* hits,
                            uint32_t* counters, const vsr_trace_params* p, vsr_stream stream) {
     g_err.clear();
     if (max_hits < 1 || max_hits > 16) return fail(VSR_ERR_ARG, "max_hits must be in 1..16");
-    if (is && is->dispatch != VSR_DISPATCH_STATIC)
-        return fail(VSR_ERR_ARG, "the multi-hit query uses static dispatch only");
     if (p && p->persistent) return fail(VSR_ERR_ARG, "the multi-hit query uses one ray per thread");
     LaunchArgs a;
     vsr_status st = prepare_launch(s, rays, n, is, VSR_CLOSEST, hits, p, a);
@@ -591,7 +772,8 @@ vsr_status vsr_trace_multi(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (n == 0) return VSR_OK;
     a.stream = reinterpret_cast<cudaStream_t>(stream);
     DeviceGuard g(s->device);
-    cudaError_t e = launch_multi(a, is->kind, s->d_verts, s->d_idx, max_hits);
+    cudaError_t e = launch_multi(a, is->kind, s->d_verts, s->d_idx, max_hits,
+                                 is->dispatch == VSR_DISPATCH_DYNAMIC);
     if (e != cudaSuccess) return cuda_fail(e, "multi-hit launch");
     return VSR_OK;
 }
@@ -675,6 +857,24 @@ vsr_status vsr_read_probe(const void* buf, uint64_t bytes, uint32_t reps, vsr_st
     if (st != VSR_OK) return st;
     VSR_CUDA(launch_read_probe(buf, bytes, reps, reinterpret_cast<cudaStream_t>(stream)),
              "read probe launch");
+    return VSR_OK;
+}
+
+vsr_status vsr_read_probe_l1(const void* buf, uint64_t bytes, uint32_t reps,
+                             uint64_t* bytes_read, vsr_stream stream) {
+    g_err.clear();
+    if (bytes == 0 || bytes % 16 || bytes > 65536)
+        return fail(VSR_ERR_ARG, "bytes must be a nonzero multiple of 16 up to 65536");
+    if (reps == 0) return fail(VSR_ERR_ARG, "reps must be >= 1");
+    if (!bytes_read) return fail(VSR_ERR_ARG, "bytes_read is null");
+    int dev = 0;
+    VSR_CUDA(cudaGetDevice(&dev), "current device");
+    vsr_status st = check_dev(buf, dev, "buf", 16, bytes);
+    if (st != VSR_OK) return st;
+    unsigned long long total = 0;
+    VSR_CUDA(launch_read_probe_l1(buf, bytes, reps, &total, reinterpret_cast<cudaStream_t>(stream)),
+             "L1 read probe launch");
+    *bytes_read = total;
     return VSR_OK;
 }
 
@@ -946,34 +1146,77 @@ extern "C" vsr_status vsr_scene_update(vsr_scene* s, const float* verts, uint32_
 // is part of the library image: every GPU that loads the library holds these
 // 256 bytes until the process exits, and the entry point itself allocates
 // nothing.  All calls share the array, so calls that overlap on the GPU race
-// on the counter.
+// on the counter.  The counter is cleared on the caller's stream before each
+// launch.
 
 namespace {
 
 constexpr unsigned kNoallocWords = 32;  // 256 bytes
 constexpr unsigned kNoallocWordsPerCall = 1;
-constexpr uint64_t kNoallocMaxRays = 1ull << 40;
-constexpr int kNoallocMaxDevices = 64;
+// the limit of any single launch here: (2^31 - 2) * 32 rays
+constexpr uint64_t kNoallocMaxRays = (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull;
 static_assert(kNoallocWordsPerCall <= kNoallocWords, "scratch array too small");
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoallocWords];
 
-std::mutex g_noalloc_mutex;
-unsigned long long* g_noalloc_ptr[kNoallocMaxDevices] = {};
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side name of the array is only a stand-in).
+// Unique id of the calling thread's current CUDA context (ids are never
+// reused within a process), read through the driver's entry points.
+bool current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    void* ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+struct NoallocSlot {
+    unsigned long long ctx_id;
+    unsigned long long* ptr;
+};
+NoallocSlot g_noalloc[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on `device` (current).  Set up once
+// per device: the address is looked up with cudaGetSymbolAddress on the first
+// call and kept with the id of the context it belongs to.  If that context
+// was destroyed and another created (cudaDeviceReset, for example), the ids
+// differ and the address is looked up again, so a stale address is never
+// used.  The host-side name of the array is only a stand-in.
 vsr_status noalloc_scratch(int device, unsigned long long** out) {
     if (device < 0 || device >= kNoallocMaxDevices)
         return fail(VSR_ERR_ARG, "device index above the supported maximum of 64");
+    unsigned long long id = 0;
+    if (!current_context_id(&id))
+        return fail(VSR_ERR_CUDA, "cannot identify the current CUDA context");
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[device]) {
+    NoallocSlot& slot = g_noalloc[device];
+    if (!slot.ptr || slot.ctx_id != id) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-        g_noalloc_ptr[device] = static_cast<unsigned long long*>(p);
+        slot.ptr = static_cast<unsigned long long*>(p);
+        slot.ctx_id = id;
     }
-    *out = g_noalloc_ptr[device];
+    *out = slot.ptr;
     return VSR_OK;
 }
 
@@ -987,16 +1230,12 @@ extern "C" vsr_status vsr_trace_persistent_noalloc(vsr_scene* s, const vsr_ray* 
     g_err.clear();
     if (n > kNoallocMaxRays)
         return fail(VSR_ERR_ARG, "vsr_trace_persistent_noalloc: n = " + std::to_string(n) +
-                                     " exceeds the maximum of 2^40 rays");
-    if (kNoallocWordsPerCall * sizeof(unsigned long long) > sizeof(g_noalloc_scratch))
-        return fail(VSR_ERR_ARG, "vsr_trace_persistent_noalloc: scratch larger than 256 bytes");
+                                     " exceeds the maximum of (2^31 - 2) * 32 rays");
     if (is && is->dispatch != VSR_DISPATCH_STATIC)
         return fail(VSR_ERR_ARG, "vsr_trace_persistent_noalloc: static dispatch only");
-    vsr_trace_params prm{128u, 1u, 16u, 0u, 0u};
-    if (p) {
-        prm = *p;
-        prm.persistent = 1u;
-    }
+    vsr_trace_params prm = kDefaultParams;
+    if (p) prm = *p;
+    prm.persistent = 1u;
     LaunchArgs a;
     vsr_status st = prepare_launch(s, rays, n, is, query, hits, &prm, a);
     if (st != VSR_OK) return st;
@@ -1036,7 +1275,7 @@ struct vsr_batch {
     BatchItem* d_items = nullptr;
     unsigned long long* d_offsets = nullptr;
     unsigned long long* d_work = nullptr;
-    vsr_trace_params params{128u, 1u, 16u, 0u, 0u};
+    vsr_trace_params params{128u, 1u, 16u, 0u, 0u, 0u, 0u, 0u, 0u};
     bool tuned = false;
     uint64_t shape = 0;  // workload signature for the tuning cache
     cudaStream_t side = nullptr;
@@ -1069,10 +1308,15 @@ bool tune_lookup(uint64_t shape, vsr_trace_params* out) {
         g_tune_file_loaded = true;
         if (const char* f = tune_file()) {
             if (FILE* fp = std::fopen(f, "r")) {
-                unsigned long long sh;
-                unsigned b, r, bps;
-                while (std::fscanf(fp, "%llx %u %u %u", &sh, &b, &r, &bps) == 4)
-                    g_tune_cache.push_back({sh, vsr_trace_params{b, 1u, r, bps, 0u}});
+                // one line per entry: "v2 <shape hex> <block> <refill> <blocks
+                // per SM> <stack regs>"; lines in any other form are skipped
+                char line[256];
+                while (std::fgets(line, sizeof line, fp)) {
+                    unsigned long long sh;
+                    unsigned b, r, bps, k;
+                    if (std::sscanf(line, "v2 %llx %u %u %u %u", &sh, &b, &r, &bps, &k) == 5)
+                        g_tune_cache.push_back({sh, vsr_trace_params{b, 1u, r, bps, 0u, k, 0u, 0u, 0u}});
+                }
                 std::fclose(fp);
             }
         }
@@ -1090,8 +1334,8 @@ void tune_store(uint64_t shape, const vsr_trace_params& p) {
     g_tune_cache.push_back({shape, p});
     if (const char* f = tune_file()) {
         if (FILE* fp = std::fopen(f, "a")) {
-            std::fprintf(fp, "%llx %u %u %u\n", (unsigned long long)shape, p.block_size,
-                         p.refill_threshold, p.blocks_per_sm);
+            std::fprintf(fp, "v2 %llx %u %u %u %u\n", (unsigned long long)shape, p.block_size,
+                         p.refill_threshold, p.blocks_per_sm, p.stack_regs);
             std::fclose(fp);
         }
     }
@@ -1103,6 +1347,8 @@ vsr_status validate_params(const vsr_trace_params& p) {
     if (p.refill_threshold < 1 || p.refill_threshold > 32)
         return fail(VSR_ERR_ARG, "refill_threshold must be in 1..32");
     if (p.blocks_per_sm > 32) return fail(VSR_ERR_ARG, "blocks_per_sm above 32");
+    if (!batch_stack_regs_supported(p.stack_regs))
+        return fail(VSR_ERR_ARG, "batched launches take stack_regs 0, 2 or 4");
     if (p.image_width != 0)
         return fail(VSR_ERR_ARG, "batched launches take rays in buffer order (image_width 0)");
     return VSR_OK;
@@ -1120,56 +1366,74 @@ BatchLaunch batch_launch_args(const vsr_batch* b, const vsr_trace_params& p) {
     L.refill = p.refill_threshold;
     L.blocks_per_sm = p.blocks_per_sm;
     L.stack_max = b->stack_max;
+    L.stack_regs = p.stack_regs;
+    L.wd = make_watchdog(p);
     return L;
 }
 
-// Time every candidate configuration on the batch itself (two timed runs
-// after one warm-up, median of the two) and keep the fastest.
+// Time candidate configurations on the batch itself (one warm-up run, then
+// the mean of two timed runs) and keep the fastest.  First pass: block
+// 64/128/256 x refill threshold 1/8/16/24/32 x blocks per SM (occupancy or
+// 4) with the stack in shared memory; second pass: the winner with 2 and 4
+// stack entries in registers.  The caller's watchdog budget applies to every
+// run.
 vsr_status batch_tune(vsr_batch* b) {
     static const uint32_t blocks[] = {64u, 128u, 256u};
-    static const uint32_t refills[] = {8u, 16u, 24u, 32u};
-    static const uint32_t per_sm[] = {0u, 2u, 4u};
+    static const uint32_t refills[] = {1u, 8u, 16u, 24u, 32u};
+    static const uint32_t per_sm[] = {0u, 4u};
     cudaEvent_t e0, e1;
     VSR_CUDA(cudaEventCreate(&e0), "tune events");
     VSR_CUDA(cudaEventCreate(&e1), "tune events");
     float best_ms = 0.0f;
     vsr_trace_params best = b->params;
     bool have = false;
-    vsr_status st = VSR_OK;
+    cudaError_t e = cudaSuccess;
+    auto consider = [&](const vsr_trace_params& cand) {
+        if (e != cudaSuccess) return;
+        const BatchLaunch L = batch_launch_args(b, cand);
+        float ms[2] = {0.0f, 0.0f};
+        e = launch_batch(L, b->kind, b->query, b->side);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(e0, b->side);
+            if (e == cudaSuccess) e = launch_batch(L, b->kind, b->query, b->side);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->side);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[k], e0, e1);
+        }
+        if (e != cudaSuccess) return;
+        const float m = 0.5f * (ms[0] + ms[1]);
+        if (!have || m < best_ms) {
+            best_ms = m;
+            best = cand;
+            have = true;
+        }
+    };
     for (uint32_t bl : blocks) {
         if ((size_t)b->stack_max * bl * 4 > 200 * 1024) continue;
         for (uint32_t rf : refills)
             for (uint32_t ps : per_sm) {
-                const vsr_trace_params cand{bl, 1u, rf, ps, 0u};
-                const BatchLaunch L = batch_launch_args(b, cand);
-                float ms[2] = {0.0f, 0.0f};
-                cudaError_t e = launch_batch(L, b->kind, b->query, b->side);
-                for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-                    e = cudaEventRecord(e0, b->side);
-                    if (e == cudaSuccess) e = launch_batch(L, b->kind, b->query, b->side);
-                    if (e == cudaSuccess) e = cudaEventRecord(e1, b->side);
-                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[k], e0, e1);
-                }
-                if (e != cudaSuccess) {
-                    st = cuda_fail(e, "autotune");
-                    goto out;
-                }
-                const float m = 0.5f * (ms[0] + ms[1]);
-                if (!have || m < best_ms) {
-                    best_ms = m;
-                    best = cand;
-                    have = true;
-                }
+                vsr_trace_params cand = b->params;
+                cand.block_size = bl;
+                cand.persistent = 1u;
+                cand.refill_threshold = rf;
+                cand.blocks_per_sm = ps;
+                cand.stack_regs = 0u;
+                consider(cand);
             }
     }
+    const vsr_trace_params first = best;
+    for (uint32_t k : {2u, 4u}) {
+        vsr_trace_params cand = first;
+        cand.stack_regs = k;
+        consider(cand);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
     b->params = best;
     b->tuned = true;
     tune_store(b->shape, best);
-out:
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    return st;
+    return VSR_OK;
 }
 
 void batch_free(vsr_batch* b) {
@@ -1199,12 +1463,8 @@ extern "C" vsr_status vsr_batch_create(vsr_scene* const* scenes, const vsr_ray* 
         return fail(VSR_ERR_ARG, "batched launches use static dispatch only");
     if (is->kind == VSR_ISECT_CLIP)
         return fail(VSR_ERR_ARG, "the clip-box intersector is for vsr_trace and vsr_trace_multi");
-    // The procedural-alpha any-hit query stalled in persistent-warp loops three
-    // times (twice in the single-scene persistent kernel, once in this batched
-    // one) without a cause found; it stays off these kernels until one is.
-    if (is->kind == VSR_ISECT_PROC_ALPHA && query == VSR_ANY)
-        return fail(VSR_ERR_ARG, "batched procedural-alpha any-hit query is disabled");
-    vsr_trace_params prm{128u, 1u, 16u, 0u, 0u};
+    vsr_trace_params prm = kDefaultParams;
+    prm.persistent = 1u;
     if (params) {
         prm = *params;
         prm.persistent = 1u;
@@ -1522,11 +1782,9 @@ extern "C" vsr_status vsr_trace_instances(vsr_instances* x, const vsr_ray* rays,
     if (!x) return fail(VSR_ERR_ARG, "instance set is null");
     vsr_status st = validate_isect(is, query);
     if (st != VSR_OK) return st;
-    if (is->dispatch != VSR_DISPATCH_STATIC)
-        return fail(VSR_ERR_ARG, "instanced traces use static dispatch only");
     if (is->kind == VSR_ISECT_CLIP)
         return fail(VSR_ERR_ARG, "the clip-box intersector is for vsr_trace and vsr_trace_multi");
-    vsr_trace_params prm{128u, 0u, 16u, 0u, 0u};
+    vsr_trace_params prm = kDefaultParams;
     if (p) prm = *p;
     if (prm.block_size < 32 || prm.block_size > 256 || prm.block_size % 32)
         return fail(VSR_ERR_ARG, "block_size must be a multiple of 32 in 32..256");
@@ -1557,7 +1815,7 @@ extern "C" vsr_status vsr_trace_instances(vsr_instances* x, const vsr_ray* rays,
     L.stack_words = x->stack_words;
     L.stream = reinterpret_cast<cudaStream_t>(stream);
     DeviceGuard g(x->device);
-    cudaError_t e = launch_instances(L, is->kind, query);
+    cudaError_t e = launch_instances(L, is->kind, query, is->dispatch == VSR_DISPATCH_DYNAMIC);
     if (e != cudaSuccess) return cuda_fail(e, "instanced trace launch");
     return VSR_OK;
 }

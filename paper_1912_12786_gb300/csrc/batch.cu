@@ -4,11 +4,16 @@
 // The rays of all scenes form one index space [0, total) with per-scene
 // prefix offsets.  Warps claim rays from a global counter with one atomic
 // per warp and refill idle lanes when fewer than `refill` lanes are still
-// busy (the persistent scheme of k_trace_persistent).  A lane locates the
-// scene of its ray by binary search over the offsets and copies that scene's
-// descriptor, so lanes of one warp may trace different scenes.  Per-ray
-// results are identical to a per-scene vsr_trace: the traversal code is the
-// same (traverse_start / traverse_step).
+// busy (the persistent scheme of k_trace_persistent).  A claim is a run of
+// consecutive indices, so it usually lies in one scene: lane 0 finds the
+// scene of the run's first index by binary search over the offsets, and each
+// claiming lane walks forward from there to its own scene (past scenes with
+// no rays) and keeps a pointer to that scene's descriptor in the item table
+// (fields are read from L1 as the traversal needs them, instead of a
+// 128-byte copy held in registers).  Lanes of one warp may still trace
+// different scenes.  Per-ray results are identical to a per-scene
+// vsr_trace: the traversal code is the same (traverse_start /
+// traverse_step).
 #include "vsr_internal.h"
 
 namespace vsr {
@@ -27,51 +32,63 @@ __device__ __forceinline__ uint32_t scene_of(const unsigned long long* __restric
     return lo;
 }
 
-template <int Q, class H>
+// Control flow as k_trace_persistent (trace_static.cuh): converged votes at
+// the top of every iteration, one divergent traversal step closed by
+// __syncwarp, uniform exits, and the watchdog.
+template <int Q, class H, int K>
 __global__ void __launch_bounds__(256) k_trace_batch(const BatchItem* __restrict__ items,
                                                      const unsigned long long* __restrict__ offsets,
                                                      uint32_t nbatch, IsectParams ip,
                                                      unsigned long long total,
                                                      unsigned long long* __restrict__ work,
-                                                     uint32_t refill) {
+                                                     uint32_t refill, Watchdog wd) {
     extern __shared__ uint32_t s_stack[];
-    uint32_t* stack = s_stack + threadIdx.x;
-    const uint32_t stride = blockDim.x;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t lt_mask = (1u << lane) - 1u;
+    ShortStack<K> stk;
+    stk.init(s_stack + threadIdx.x, blockDim.x);
 
     bool has = false;
     bool exhausted = false;
     unsigned long long ri = 0;
     float4* hp = nullptr;
-    DevScene sc;
+    const DevScene* scp = &items[0].sc;
     Ray r;
     Best best;
     Stats st;
     H h;
-    uint32_t ref = 0, sp = 0, steps = 0;
+    uint32_t ref = 0, steps = 0;
+    uint32_t* err0 = items[0].sc.err;  // the watchdog also reports to scene 0's word
+    const unsigned long long t0 = wd.max_ns ? global_ns() : 0ull;
+    unsigned long long iters = 0;
 
     for (;;) {
-        const uint32_t busy = __ballot_sync(0xFFFFFFFFu, has);
+        const uint32_t busy = __ballot_sync(kFullMask, has);
         if (!exhausted && (uint32_t)__popc(busy) < refill) {
             const uint32_t idle = ~busy;
             const uint32_t nidle = (uint32_t)__popc(idle);
             unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(work, (unsigned long long)nidle);
-            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            uint32_t s0 = 0;
+            if (lane == 0) {
+                base = atomicAdd(work, (unsigned long long)nidle);
+                if (base < total) s0 = scene_of(offsets, nbatch, base);
+            }
+            base = __shfl_sync(kFullMask, base, 0);
+            s0 = __shfl_sync(kFullMask, s0, 0);
             if (base + nidle >= total) exhausted = true;
             if (!has) {
                 const unsigned long long g = base + (unsigned long long)__popc(idle & lt_mask);
                 if (g < total) {
-                    const uint32_t s = scene_of(offsets, nbatch, g);
+                    uint32_t s = s0;
+                    while (s + 1 < nbatch && VSR_LDG(offsets + s + 1) <= g) ++s;
                     ri = g - VSR_LDG(offsets + s);
-                    sc = items[s].sc;
+                    scp = &items[s].sc;
                     const float4* rays = items[s].rays;
                     hp = items[s].hits;
                     r = make_ray(VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
                     h = H();
                     has = true;
-                    if (!traverse_start<Q, H, false>(sc, ip, r, h, best, st, ref, sp, steps)) {
+                    if (!traverse_start<Q, H, false>(*scp, ip, r, h, best, st, ref, steps, stk)) {
                         finish_miss(best);
                         hp[ri] = hit_record(best);
                         has = false;
@@ -79,25 +96,36 @@ __global__ void __launch_bounds__(256) k_trace_batch(const BatchItem* __restrict
                 }
             }
         }
-        if (__ballot_sync(0xFFFFFFFFu, has) == 0u) {
-            if (exhausted) break;
-            continue;
+        const uint32_t live = __ballot_sync(kFullMask, has);
+        if (live == 0u && exhausted) break;
+        if (watchdog_expired(wd, ++iters, t0)) {
+            if (lane == 0) atomicOr(err0, kErrTimeout);
+            if (has) {
+                atomicOr(scp->err, kErrTimeout);
+                best.fail();
+                finish_miss(best);
+                hp[ri] = hit_record(best);
+                has = false;
+            }
+            break;
         }
-        if (!has) continue;
-        if (traverse_step<Q, H, false>(sc, ip, r, h, best, st, ref, sp, steps, stack, stride)) {
-            finish_miss(best);
-            hp[ri] = hit_record(best);
-            has = false;
+        if (has) {
+            if (traverse_step<Q, H, false>(*scp, ip, r, h, best, st, ref, steps, stk)) {
+                finish_miss(best);
+                hp[ri] = hit_record(best);
+                has = false;
+            }
         }
+        __syncwarp();
     }
 }
 
 namespace {
 
-template <int Q, class H>
+template <int Q, class H, int K>
 cudaError_t batch_one(const BatchLaunch& b, cudaStream_t stream, uint32_t* grid_out) {
-    auto k = k_trace_batch<Q, H>;
-    const size_t smem = (size_t)b.stack_max * b.block * sizeof(uint32_t);
+    auto k = k_trace_batch<Q, H, K>;
+    const size_t smem = (size_t)stack_words(b.stack_max, K) * b.block * sizeof(uint32_t);
     uint32_t grid = b.grid;
     if (grid == 0) {
         if (smem > 48 * 1024) {
@@ -121,23 +149,35 @@ cudaError_t batch_one(const BatchLaunch& b, cudaStream_t stream, uint32_t* grid_
     cudaError_t e = cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
     k<<<grid, b.block, smem, stream>>>(b.items, b.offsets, b.nbatch, b.ip, b.total, b.work,
-                                       b.refill);
+                                       b.refill, b.wd);
     return cudaGetLastError();
+}
+
+template <int Q, class H>
+cudaError_t batch_regs(const BatchLaunch& b, cudaStream_t stream, uint32_t* grid) {
+    switch (b.stack_regs) {
+        case 0: return batch_one<Q, H, 0>(b, stream, grid);
+        case 2: return batch_one<Q, H, 2>(b, stream, grid);
+        case 4: return batch_one<Q, H, 4>(b, stream, grid);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int Q>
 cudaError_t batch_kind(const BatchLaunch& b, int kind, cudaStream_t stream, uint32_t* grid) {
     switch (kind) {
-        case 0: return batch_one<Q, IsectNone>(b, stream, grid);
-        case 1: return batch_one<Q, IsectDefault>(b, stream, grid);
-        case 2: return batch_one<Q, IsectAlphaTex>(b, stream, grid);
-        case 3: return batch_one<Q, IsectProcAlpha>(b, stream, grid);
-        case 4: return batch_one<Q, IsectCount>(b, stream, grid);
+        case 0: return batch_regs<Q, IsectNone>(b, stream, grid);
+        case 1: return batch_regs<Q, IsectDefault>(b, stream, grid);
+        case 2: return batch_regs<Q, IsectAlphaTex>(b, stream, grid);
+        case 3: return batch_regs<Q, IsectProcAlpha>(b, stream, grid);
+        case 4: return batch_regs<Q, IsectCount>(b, stream, grid);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
+
+bool batch_stack_regs_supported(uint32_t k) { return k == 0 || k == 2 || k == 4; }
 
 cudaError_t launch_batch(const BatchLaunch& b, int kind, int query, cudaStream_t stream) {
     return query == kClosest ? batch_kind<kClosest>(b, kind, stream, nullptr)

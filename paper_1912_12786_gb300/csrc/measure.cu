@@ -4,6 +4,11 @@
 // this probe reaches on the same device: a buffer well inside the L2 gives
 // the L2 read peak, one far larger than the L2 the HBM read peak.
 //
+// The L1 variant: every block of a full-occupancy grid reads the same small
+// buffer (at most 64 KB, so it stays in each SM's L1) with 16-byte L1-cached
+// loads, `reps` times; the launch reads blocks x bytes x reps bytes, the
+// denominator of the L1 level of the roofline.
+//
 // Every thread of a full-occupancy grid (SMs x resident blocks) walks the
 // buffer in a grid-stride loop with four independent 16-byte loads in flight
 // (ld.global.cg: cached in L2 only, so repeated passes are not served by L1),
@@ -40,7 +45,41 @@ __global__ void __launch_bounds__(512) k_read_probe(const uint4* __restrict__ bu
     if (acc == 0x7FC00001u) g_probe_sink = acc;
 }
 
+__global__ void __launch_bounds__(512) k_read_probe_l1(const uint4* __restrict__ buf,
+                                                       uint32_t n16, uint32_t reps) {
+    uint32_t acc = 0;
+    for (uint32_t r = 0; r < reps; ++r) {
+        uint32_t i = threadIdx.x;
+        for (; i + 3 * blockDim.x < n16; i += 4 * blockDim.x) {
+            const uint4 a = __ldca(buf + i);
+            const uint4 b = __ldca(buf + i + blockDim.x);
+            const uint4 c = __ldca(buf + i + 2 * blockDim.x);
+            const uint4 d = __ldca(buf + i + 3 * blockDim.x);
+            acc ^= fold(a) ^ fold(b) ^ fold(c) ^ fold(d);
+        }
+        for (; i < n16; i += blockDim.x) acc ^= fold(__ldca(buf + i));
+        acc = acc * 0x9E3779B1u + r;
+    }
+    if (acc == 0x7FC00001u) g_probe_sink = acc;
+}
+
 }  // namespace
+
+cudaError_t launch_read_probe_l1(const void* buf, unsigned long long bytes, uint32_t reps,
+                                 unsigned long long* bytes_read, cudaStream_t stream) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_read_probe_l1, 512, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const unsigned blocks = (unsigned)(sms * per_sm);
+    *bytes_read = (unsigned long long)blocks * bytes * reps;
+    k_read_probe_l1<<<blocks, 512, 0, stream>>>(static_cast<const uint4*>(buf),
+                                                (uint32_t)(bytes / 16), reps);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_read_probe(const void* buf, unsigned long long bytes, uint32_t reps,
                               cudaStream_t stream) {

@@ -137,7 +137,9 @@ __global__ void __launch_bounds__(256) k_render(DevScene sc, IsectParams ip, Sha
     H h;
     Best best;
     Stats st;
-    traverse<kClosest, H, false>(sc, ip, r, h, best, st, s_stack + threadIdx.x, blockDim.x);
+    ShortStack<0> stk;
+    stk.init(s_stack + threadIdx.x, blockDim.x);
+    traverse<kClosest, H, false>(sc, ip, r, h, best, st, stk);
     if (hits) {
         if (reinterpret_cast<unsigned long long>(hits + i) % 16)
             atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
@@ -183,7 +185,9 @@ __global__ void __launch_bounds__(256) k_render_backward(
     H h;
     Best best;
     Stats st;
-    traverse<kClosest, H, false>(sc, ip, r, h, best, st, s_stack + threadIdx.x, blockDim.x);
+    ShortStack<0> stk;
+    stk.init(s_stack + threadIdx.x, blockDim.x);
+    traverse<kClosest, H, false>(sc, ip, r, h, best, st, stk);
     if (best.prim == kMiss) return;
     const float g[3] = {VSR_LDG(dL_dimage + 3 * i), VSR_LDG(dL_dimage + 3 * i + 1),
                         VSR_LDG(dL_dimage + 3 * i + 2)};
@@ -286,7 +290,9 @@ __global__ void __launch_bounds__(256) k_ao_occlusion(DevScene sc, IsectParams i
     H hk;
     Best best;
     Stats st;
-    traverse<kAny, H, false>(sc, ip, ar, hk, best, st, s_stack + threadIdx.x, blockDim.x);
+    ShortStack<0> stk;
+    stk.init(s_stack + threadIdx.x, blockDim.x);
+    traverse<kAny, H, false>(sc, ip, ar, hk, best, st, stk);
     if (best.prim != kMiss) atomicAdd(cnt + i, 1u);
 }
 

@@ -8,7 +8,10 @@
 //
 // One ray per thread.  The top-level while-while loop uses the bottom of the
 // thread's shared-memory stack; a mesh traversal runs on the stack above the
-// top-level entries, continuing the running result.
+// top-level entries, continuing the running result.  The intersector is
+// compiled in (static dispatch) or reached through this module's callback
+// tables (dynamic dispatch, dynamic.cuh), the callbacks seeing the mesh of
+// the instance being traversed.
 //
 // Two new kernels (the render and multi-hit kernels) raised an unexplained
 // misaligned-address fault on the first launch of their unchecked builds and
@@ -17,7 +20,7 @@
 // their address (a skipped access is reported with its line, device error
 // bit 2).
 #define VSR_CHECKED_LOADS 1
-#include "vsr_internal.h"
+#include "dynamic.cuh"
 
 namespace vsr {
 
@@ -88,6 +91,7 @@ __global__ void __launch_bounds__(256) k_trace_inst(InstDev is, IsectParams ip,
     uint32_t* stack = s_stack + threadIdx.x;
     const uint32_t stride = blockDim.x;
     H h;
+    bind_callbacks(h, ip);
     InstBest best;
     best.reset(r.tmax);
     Stats st;
@@ -141,8 +145,10 @@ __global__ void __launch_bounds__(256) k_trace_inst(InstDev is, IsectParams ip,
                             to_object(ra, rb, VSR_LDG(w), VSR_LDG(w + 1), VSR_LDG(w + 2));
                         const DevScene& msc = is.meshes[__float_as_uint(VSR_LDG(w + 3).x)];
                         best.cur = id;
-                        traverse_body<Q, H, false>(msc, ip, ro, h, best, st, stack + sp * stride,
-                                                   stride);
+                        set_callback_scene(h, &msc);
+                        ShortStack<0> stk;
+                        stk.init(stack + sp * stride, stride);
+                        traverse_body<Q, H, false>(msc, ip, ro, h, best, st, stk);
                         if (best.failed || (Q == kAny && best.prim != kMiss)) goto done;
                     }
                 }
@@ -213,7 +219,13 @@ cudaError_t instances_align_error(unsigned* line) {
     return cudaMemcpyToSymbol(g_vsr_align_line, &zero, sizeof(unsigned));
 }
 
-cudaError_t launch_instances(const InstLaunch& L, int kind, int query) {
+cudaError_t launch_instances(const InstLaunch& L, int kind, int query, bool dynamic) {
+    if (dynamic) {
+        cudaError_t e = ensure_callbacks_registered();
+        if (e != cudaSuccess) return e;
+        return query == kClosest ? inst_one<kClosest, IsectDynamic>(L)
+                                 : inst_one<kAny, IsectDynamic>(L);
+    }
     return query == kClosest ? inst_kind<kClosest>(L, kind) : inst_kind<kAny>(L, kind);
 }
 

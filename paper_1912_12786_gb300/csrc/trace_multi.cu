@@ -6,7 +6,8 @@
 // entry of a sorted buffer as its bound (MultiBest, in shared memory after
 // the traversal stack), so the intersector is consulted for exactly the
 // candidates that would enter the buffer; with n == 1 it is the closest-hit
-// query.
+// query.  The intersector is compiled in (static dispatch) or reached
+// through this module's callback tables (dynamic dispatch, dynamic.cuh).
 //
 // The first launch of the unchecked build raised a misaligned-address fault
 // that reading the code did not explain (every access here uses a cudaMalloc
@@ -15,7 +16,7 @@
 // path and the hit and counter stores check their address: a misaligned
 // access is skipped and its source line reported (device error bit 2).
 #define VSR_CHECKED_LOADS 1
-#include "vsr_internal.h"
+#include "dynamic.cuh"
 
 namespace vsr {
 
@@ -47,7 +48,8 @@ __global__ void __launch_bounds__(256) k_trace_multi(DevScene sc, IsectParams ip
                                                      const uint32_t* __restrict__ idx,
                                                      const float4* __restrict__ rays, RayMap map,
                                                      uint32_t nh, float4* __restrict__ hits,
-                                                     uint2* __restrict__ counters) {
+                                                     uint2* __restrict__ counters,
+                                                     const DevScene* __restrict__ user) {
     extern __shared__ uint32_t s_stack[];
     const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= map.threads) return;
@@ -55,6 +57,8 @@ __global__ void __launch_bounds__(256) k_trace_multi(DevScene sc, IsectParams ip
     if (i >= map.n) return;
     const Ray r = make_ray(VSR_LDG(rays + 2 * i), VSR_LDG(rays + 2 * i + 1));
     H h;
+    bind_callbacks(h, ip);
+    set_callback_scene(h, user);
     // shared memory: stack (depth x block words), then the buffer's t and
     // prim columns (nh x block words each)
     const uint32_t stride = blockDim.x;
@@ -65,7 +69,9 @@ __global__ void __launch_bounds__(256) k_trace_multi(DevScene sc, IsectParams ip
     mb.stride = stride;
     mb.n = nh;
     Stats st;
-    traverse_body<kClosest, H, false>(sc, ip, r, h, mb, st, s_stack + threadIdx.x, stride);
+    ShortStack<0> stk;
+    stk.init(s_stack + threadIdx.x, stride);
+    traverse_body<kClosest, H, false>(sc, ip, r, h, mb, st, stk);
     float4* out = hits + i * nh;
     for (uint32_t k = 0; k < nh; ++k) {
         const float4 rec = multi_record(r, verts, idx, mb.pk[k * stride]);
@@ -93,7 +99,7 @@ cudaError_t multi_one(const LaunchArgs& a, const float* verts, const uint32_t* i
     }
     const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
     k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, verts, idx, a.rays, a.map, nh,
-                                                     a.hits, a.counters);
+                                                     a.hits, a.counters, a.dyn_user);
     return cudaGetLastError();
 }
 
@@ -107,8 +113,12 @@ cudaError_t multi_align_error(unsigned* line) {
 }
 
 cudaError_t launch_multi(const LaunchArgs& a, int kind, const float* verts, const uint32_t* idx,
-                         uint32_t nh) {
+                         uint32_t nh, bool dynamic) {
     if (nh < 1 || nh > 16) return cudaErrorInvalidValue;
+    if (dynamic) {
+        cudaError_t e = ensure_callbacks_registered();
+        return e != cudaSuccess ? e : multi_one<IsectDynamic>(a, verts, idx, nh);
+    }
     switch (kind) {
         case 0: return multi_one<IsectNone>(a, verts, idx, nh);
         case 1: return multi_one<IsectDefault>(a, verts, idx, nh);

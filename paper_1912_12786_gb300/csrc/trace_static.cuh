@@ -1,0 +1,218 @@
+// Trace kernels with the intersector injected at compile time (Section 3.2:
+// the traversal receives the custom intersector as a template argument, so
+// its hooks are inlined where the box and primitive tests are), one
+// instantiation per query, intersector and register-stack depth K.
+//
+// Two launch shapes:
+//   k_trace            one ray per thread, grid over the rays;
+//   k_trace_persistent persistent warps that claim rays from a global counter
+//                      with one atomic per warp and refill idle lanes when the
+//                      number of active lanes drops below a threshold
+//                      (ballot + popc), after Aila and Laine's persistent
+//                      threads, which the paper's traversal scheme cites.
+//
+// Each translation unit trace_k<K>.cu includes this file and instantiates
+// the kernels for one K, so the instantiations compile in parallel.
+#pragma once
+
+#include "vsr_internal.h"
+
+namespace vsr {
+
+template <int Q, class H, bool STATS, int K>
+__global__ void __launch_bounds__(256) k_trace(DevScene sc, IsectParams ip,
+                                               const float4* __restrict__ rays,
+                                               RayMap map, float4* __restrict__ hits,
+                                               uint2* __restrict__ counters,
+                                               uint4* __restrict__ stats) {
+    extern __shared__ uint32_t s_stack[];
+    const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= map.threads) return;
+    const unsigned long long i = ray_of_thread(g, map);
+    if (i >= map.n) return;
+    const Ray r = make_ray(__ldg(rays + 2 * i), __ldg(rays + 2 * i + 1));
+    H h;
+    Best best;
+    Stats st;
+    ShortStack<K> stk;
+    stk.init(s_stack + threadIdx.x, blockDim.x);
+    traverse<Q, H, STATS>(sc, ip, r, h, best, st, stk);
+    hits[i] = hit_record(best);
+    if (H::kCounts && counters) counters[i] = h.counters();
+    if (STATS) stats[i] = make_uint4(st.boxes, st.tris, st.cands, st.texs);
+}
+
+// k_trace under a register budget: __launch_bounds__(256, MINB) asks the
+// compiler to fit MINB blocks of 256 threads per SM (at most 65536 /
+// (256 MINB) registers per thread).  Used to compare static injection with
+// the callback kernel at equal register budgets (trace_caps.cu); stack in
+// shared memory.
+template <int Q, class H, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_trace_cap(DevScene sc, IsectParams ip,
+                                                         const float4* __restrict__ rays,
+                                                         RayMap map, float4* __restrict__ hits,
+                                                         uint2* __restrict__ counters) {
+    extern __shared__ uint32_t s_stack[];
+    const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= map.threads) return;
+    const unsigned long long i = ray_of_thread(g, map);
+    if (i >= map.n) return;
+    const Ray r = make_ray(__ldg(rays + 2 * i), __ldg(rays + 2 * i + 1));
+    H h;
+    Best best;
+    Stats st;
+    ShortStack<0> stk;
+    stk.init(s_stack + threadIdx.x, blockDim.x);
+    traverse<Q, H, false>(sc, ip, r, h, best, st, stk);
+    hits[i] = hit_record(best);
+    if (H::kCounts && counters) counters[i] = h.counters();
+}
+
+// Persistent variant.  Per-lane traversal state lives in registers and the
+// shared-memory stack column; a lane that finishes its ray idles until the
+// warp refills.  The counter hands out thread slots of the ray map; a slot
+// past the image edge takes no ray.
+//
+// Control flow: every iteration starts with all 32 lanes converged at the
+// first vote.  The claim block runs on a warp-uniform condition; inside it
+// only the lanes without a ray take new ones, and the second vote closes that
+// divergent part.  The loop's exits (all lanes idle and the counter passed
+// the end, or the watchdog) are uniform decisions.  The traversal step is the
+// only other divergent region, a single if with one exit, and __syncwarp
+// reconverges the warp before the next iteration.  No lane ever waits on
+// another warp or block.  Each iteration claims at least one ray or advances
+// some lane's traversal (bounded per ray by the node count), so the loop
+// ends; the watchdog bounds it whatever happens.
+template <int Q, class H, bool STATS, int K>
+__global__ void __launch_bounds__(256) k_trace_persistent(
+    DevScene sc, IsectParams ip, const float4* __restrict__ rays, RayMap map,
+    float4* __restrict__ hits, uint2* __restrict__ counters, uint4* __restrict__ stats,
+    unsigned long long* __restrict__ work, uint32_t refill, Watchdog wd) {
+    extern __shared__ uint32_t s_stack[];
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    ShortStack<K> stk;
+    stk.init(s_stack + threadIdx.x, blockDim.x);
+
+    bool has = false;        // lane holds a ray in flight
+    bool exhausted = false;  // warp-uniform: the counter passed the last slot
+    unsigned long long ri = 0;
+    Ray r;
+    Best best;
+    Stats st;
+    H h;
+    uint32_t ref = 0, steps = 0;
+    const unsigned long long t0 = wd.max_ns ? global_ns() : 0ull;
+    unsigned long long iters = 0;
+
+    auto finish = [&]() {
+        finish_miss(best);
+        hits[ri] = hit_record(best);
+        if (H::kCounts && counters) counters[ri] = h.counters();
+        if (STATS) stats[ri] = make_uint4(st.boxes, st.tris, st.cands, st.texs);
+        has = false;
+    };
+
+    for (;;) {
+        const uint32_t busy = __ballot_sync(kFullMask, has);
+        if (!exhausted && (uint32_t)__popc(busy) < refill) {
+            const uint32_t idle = ~busy;
+            const uint32_t nidle = (uint32_t)__popc(idle);
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(work, (unsigned long long)nidle);
+            base = __shfl_sync(kFullMask, base, 0);
+            if (base + nidle >= map.threads) exhausted = true;
+            if (!has) {
+                const unsigned long long slot = base + (unsigned long long)__popc(idle & lt_mask);
+                ri = slot < map.threads ? ray_of_thread(slot, map) : map.n;
+                if (ri < map.n) {
+                    r = make_ray(VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
+                    h = H();
+                    st = Stats();
+                    has = true;
+                    if (!traverse_start<Q, H, STATS>(sc, ip, r, h, best, st, ref, steps, stk))
+                        finish();
+                }
+            }
+        }
+        const uint32_t live = __ballot_sync(kFullMask, has);
+        if (live == 0u && exhausted) break;
+        if (watchdog_expired(wd, ++iters, t0)) {
+            if (lane == 0) atomicOr(sc.err, kErrTimeout);
+            if (has) {
+                best.fail();
+                finish();
+            }
+            break;
+        }
+        if (has) {
+            if (traverse_step<Q, H, STATS>(sc, ip, r, h, best, st, ref, steps, stk)) finish();
+        }
+        __syncwarp();
+    }
+}
+
+namespace detail {
+
+template <class Kern>
+cudaError_t ensure_smem(Kern kernel, size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int Q, class H, bool STATS, int K>
+cudaError_t launch_one(const LaunchArgs& a) {
+    const size_t smem = (size_t)stack_words(a.sc.stack_depth, K) * a.block * sizeof(uint32_t);
+    if (!a.persistent) {
+        auto k = k_trace<Q, H, STATS, K>;
+        cudaError_t e = ensure_smem(k, smem);
+        if (e != cudaSuccess) return e;
+        const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
+        k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits,
+                                                         a.counters, a.stats);
+        return cudaGetLastError();
+    }
+    auto k = k_trace_persistent<Q, H, STATS, K>;
+    cudaError_t e = ensure_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = persistent_grid(a, reinterpret_cast<const void*>(k), smem);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), a.stream);
+    if (e != cudaSuccess) return e;
+    k<<<grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits, a.counters, a.stats,
+                                         a.work, a.refill, a.wd);
+    return cudaGetLastError();
+}
+
+template <int Q, bool STATS, int K>
+cudaError_t launch_kind(const LaunchArgs& a, int kind) {
+    switch (kind) {
+        case 0: return launch_one<Q, IsectNone, STATS, K>(a);
+        case 1: return launch_one<Q, IsectDefault, STATS, K>(a);
+        case 2: return launch_one<Q, IsectAlphaTex, STATS, K>(a);
+        case 3: return launch_one<Q, IsectProcAlpha, STATS, K>(a);
+        case 4: return launch_one<Q, IsectCount, STATS, K>(a);
+        case 5: return launch_one<Q, IsectClip, STATS, K>(a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Launchers of one K; the measurement (stats) variant is instantiated with
+// the shared-memory-only stack alone (K == 0).
+template <int K>
+cudaError_t launch_static_k(const LaunchArgs& a, int kind, bool stats) {
+    if (stats) {
+        if constexpr (K == 0) {
+            return a.query == kClosest ? launch_kind<kClosest, true, 0>(a, kind)
+                                       : launch_kind<kAny, true, 0>(a, kind);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+    return a.query == kClosest ? launch_kind<kClosest, false, K>(a, kind)
+                               : launch_kind<kAny, false, K>(a, kind);
+}
+
+}  // namespace detail
+
+}  // namespace vsr

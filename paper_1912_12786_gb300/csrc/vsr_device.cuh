@@ -48,11 +48,19 @@ constexpr int kClosest = 0;
 constexpr int kAny = 1;
 
 enum : uint32_t { kTexU8 = 0, kTexRGBA8 = 1, kTexRGBA32F = 2 };
-// Device error word bits: stack overflow and more leaf visits than nodes
+// Device error word bits: stack overflow and more node visits than nodes
 // (neither can happen for a validated blob), a misaligned load skipped, a
-// caller-supplied hit record out of range.  The checks turn a corrupted structure or input into
-// an error instead of a fault or an endless loop.
-enum : uint32_t { kErrStack = 1u, kErrSteps = 2u, kErrAlign = 4u, kErrHit = 8u };
+// caller-supplied hit record out of range, and a persistent loop that ran
+// out of its iteration or time budget (the watchdog).  The checks turn a
+// corrupted structure or input into an error instead of a fault or an
+// endless loop.
+enum : uint32_t {
+    kErrStack = 1u,
+    kErrSteps = 2u,
+    kErrAlign = 4u,
+    kErrHit = 8u,
+    kErrTimeout = 16u
+};
 
 struct TexDesc {
     uint32_t fmt, w, h, pad;
@@ -249,15 +257,41 @@ __device__ __forceinline__ bool alpha_tex_accept(const DevScene& sc, const Isect
     return a >= ip.cutoff_f;
 }
 
-// Procedural alpha: accept iff sin(f u) sin(f v) > 0 at the texture coordinate.
+// Sign of sin(x) (-1, 0 or +1) without evaluating the sine.  With
+// k = rint(x / pi) and r = x - k pi, sin(x) = (-1)^k sin(r) and |r| < pi, so
+// the sign is (-1)^k sign(r).  r is reduced with pi split in three float32
+// parts (Cody and Waite's additive reduction): kPiA has 8 significant bits,
+// so x - k kPiA is exact for |x| < 2^22, and each fused multiply-add then
+// rounds once.  Near a multiple of pi the error of r is below 2e-11 there,
+// while every float32 with |x| < 2^22 lies at least 8.4e-9 from a multiple
+// of pi (the closest is next to 161 pi), so the sign is that of the true
+// sine for every such x.  For larger |x| the result is deterministic but may
+// differ from a correctly rounded sine where |sin x| is tiny.  The parts are
+// pi rounded to 8 significant bits, then the remainder rounded to float32
+// twice over (kPiA + kPiB + kPiC = pi - 1.7e-19).
+constexpr float kInvPi = 0x1.45f306p-2f;  // float32(1 / pi)
+constexpr float kPiA = 0x1.92p+1f;        // 3.140625
+constexpr float kPiB = 0x1.fb5444p-11f;
+constexpr float kPiC = 0x1.68c234p-38f;
+
+__device__ __forceinline__ int sin_sign(float x) {
+    const float k = rintf(__fmul_rn(x, kInvPi));
+    float r = __fmaf_rn(-k, kPiA, x);
+    r = __fmaf_rn(-k, kPiB, r);
+    r = __fmaf_rn(-k, kPiC, r);
+    const int s = (r > 0.0f) - (r < 0.0f);
+    return (__float2int_rz(k) & 1) ? -s : s;
+}
+
+// Procedural alpha: accept iff sin(f u) sin(f v) > 0 at the texture
+// coordinate, decided from the signs of the two sines (their float32 product
+// differs only where it underflows, i.e. both sines below 1e-22).
 __device__ __forceinline__ bool proc_alpha_accept(const DevScene& sc, const IsectParams& ip,
                                                   uint32_t prim, float u, float v) {
     const uint32_t g = VSR_LDG(sc.geom + prim);
     if (g == kMiss) return true;
     const float2 uv = lerp_uv(sc.uvs, prim, u, v);
-    const float sa = sinf(__fmul_rn(ip.freq, uv.x));
-    const float sb = sinf(__fmul_rn(ip.freq, uv.y));
-    return __fmul_rn(sa, sb) > 0.0f;
+    return sin_sign(__fmul_rn(ip.freq, uv.x)) * sin_sign(__fmul_rn(ip.freq, uv.y)) > 0;
 }
 
 // --------------------------------------------------------------------------
@@ -431,14 +465,60 @@ struct MultiBest {
 };
 
 // --------------------------------------------------------------------------
-// The while-while traversal.  `stack` points at this thread's column of a
-// shared-memory stack with `stride` words between levels.
+// The traversal stack of node references: the top K entries in registers,
+// the rest in this thread's column of a shared-memory stack (`col`, `stride`
+// words between levels).  A push with K entries held moves the deepest one
+// to shared memory; a pop refills it from there, so a pop never waits on
+// shared memory for the node it returns.  K == 0 keeps every entry in
+// shared memory.  The order of entries is the LIFO order either way, so the
+// traversal visits nodes in the same order for every K.
+template <int K>
+struct ShortStack {
+    uint32_t top[K > 0 ? K : 1];
+    uint32_t* col;
+    uint32_t stride;
+    uint32_t n;  // entries held (registers and shared memory)
+    __device__ __forceinline__ void init(uint32_t* column, uint32_t words_apart) {
+        col = column;
+        stride = words_apart;
+        n = 0;
+    }
+    // The caller checked n against the tree depth.
+    __device__ __forceinline__ void push(uint32_t x) {
+        if (K == 0) {
+            col[n * stride] = x;
+        } else {
+            if (n >= (uint32_t)K) col[(n - K) * stride] = top[K - 1];
+#pragma unroll
+            for (int j = K - 1; j > 0; --j) top[j] = top[j - 1];
+            top[0] = x;
+        }
+        ++n;
+    }
+    // The caller checked n > 0.
+    __device__ __forceinline__ uint32_t pop() {
+        --n;
+        if (K == 0) return col[n * stride];
+        const uint32_t x = top[0];
+#pragma unroll
+        for (int j = 0; j < K - 1; ++j) top[j] = top[j + 1];
+        if (n >= (uint32_t)K) top[K - 1] = col[(n - K) * stride];
+        return x;
+    }
+};
 
-template <int Q, class H, bool STATS, class B = Best>
+// Shared-memory words per thread for a tree of `depth` levels with K
+// entries in registers.
+__host__ __device__ __forceinline__ uint32_t stack_words(uint32_t depth, uint32_t k) {
+    return depth > k ? depth - k : 1u;
+}
+
+// The while-while traversal (Section 3.2) with the intersector's hooks.
+template <int Q, class H, bool STATS, class B = Best, class S>
 __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectParams& ip,
-                                              const Ray& r, H& h, B& best, Stats& st,
-                                              uint32_t* stack, uint32_t stride) {
+                                              const Ray& r, H& h, B& best, Stats& st, S& stk) {
     best.init(r.tmax);
+    stk.n = 0;
     if (sc.nprims == 0) return;
     h.begin(r, ip);
     h.box();
@@ -446,7 +526,6 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
     if (!box_hit(r, sc.root_a, sc.root_b, h.far(best.t)) || !h.keep(ip, sc.root_a, sc.root_b))
         return;
     uint32_t ref = sc.root_ref;
-    uint32_t sp = 0;
     uint32_t steps = 0;
     for (;;) {  // while ray not terminated
         // While the node is inner.  Descent ends by construction: a loaded
@@ -466,22 +545,20 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
             const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(ra.w);
             if (hl && hr) {
                 const bool neg = (r.negmask >> (ref & 3u)) & 1u;
-                if (sp >= sc.stack_depth) {  // unreachable for a validated blob
+                if (stk.n >= sc.stack_depth) {  // unreachable for a validated blob
                     atomicOr(sc.err, kErrStack);
                     best.fail();
                     return;
                 }
-                stack[sp * stride] = neg ? rl : rr;
-                ++sp;
+                stk.push(neg ? rl : rr);
                 ref = neg ? rr : rl;
             } else if (hl) {
                 ref = rl;
             } else if (hr) {
                 ref = rr;
             } else {
-                if (sp == 0) return;
-                --sp;
-                ref = stack[sp * stride];
+                if (stk.n == 0) return;
+                ref = stk.pop();
             }
         }
         {  // found a leaf: test its primitives
@@ -515,19 +592,17 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
                 if (Q == kAny) return;
             }
         }
-        if (sp == 0) return;
-        --sp;
-        ref = stack[sp * stride];
+        if (stk.n == 0) return;
+        ref = stk.pop();
     }
 }
 
 // Full query: traversal, then every miss (root missed, empty or inactive
 // interval, nothing accepted) is reported as t = +inf, u = v = 0.
-template <int Q, class H, bool STATS>
+template <int Q, class H, bool STATS, class S>
 __device__ __forceinline__ void traverse(const DevScene& sc, const IsectParams& ip, const Ray& r,
-                                         H& h, Best& best, Stats& st, uint32_t* stack,
-                                         uint32_t stride) {
-    traverse_body<Q, H, STATS>(sc, ip, r, h, best, st, stack, stride);
+                                         H& h, Best& best, Stats& st, S& stk) {
+    traverse_body<Q, H, STATS>(sc, ip, r, h, best, st, stk);
     if (best.prim == kMiss) {
         best.t = __int_as_float(0x7f800000);
         best.u = 0.0f;
@@ -541,12 +616,12 @@ __device__ __forceinline__ void traverse(const DevScene& sc, const IsectParams& 
 // iteration of the while-while loop (descend to a leaf, test it, pop the
 // next node) and returns true when the ray has finished.  Composed, they
 // visit nodes and primitives in exactly the order of traverse_body.
-template <int Q, class H, bool STATS>
+template <int Q, class H, bool STATS, class S>
 __device__ __forceinline__ bool traverse_start(const DevScene& sc, const IsectParams& ip,
                                                const Ray& r, H& h, Best& best, Stats& st,
-                                               uint32_t& ref, uint32_t& sp, uint32_t& steps) {
+                                               uint32_t& ref, uint32_t& steps, S& stk) {
     best.init(r.tmax);
-    sp = 0;
+    stk.n = 0;
     steps = 0;
     if (sc.nprims == 0) return false;
     h.begin(r, ip);
@@ -558,11 +633,10 @@ __device__ __forceinline__ bool traverse_start(const DevScene& sc, const IsectPa
     return true;
 }
 
-template <int Q, class H, bool STATS>
+template <int Q, class H, bool STATS, class S>
 __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectParams& ip,
                                               const Ray& r, H& h, Best& best, Stats& st,
-                                              uint32_t& ref, uint32_t& sp, uint32_t& steps,
-                                              uint32_t* stack, uint32_t stride) {
+                                              uint32_t& ref, uint32_t& steps, S& stk) {
     // Descent ends by construction as in traverse_body; the persistent and
     // batched kernels that run these steps keep the per-node visit bound as
     // well, so their outer loops stay bounded whatever the node data.
@@ -574,7 +648,7 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
         }
         const float4* p = sc.nodes + 4ull * (ref >> 2);
         float4 la, lb, ra, rb;
-            load_pair(p, la, lb, ra, rb);
+        load_pair(p, la, lb, ra, rb);
         const float tfar = h.far((Q == kClosest) ? best.t : r.tmax);
         h.box();
         h.box();
@@ -584,22 +658,20 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
         const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(ra.w);
         if (hl && hr) {
             const bool neg = (r.negmask >> (ref & 3u)) & 1u;
-            if (sp >= sc.stack_depth) {
+            if (stk.n >= sc.stack_depth) {
                 atomicOr(sc.err, kErrStack);
                 best.fail();
                 return true;
             }
-            stack[sp * stride] = neg ? rl : rr;
-            ++sp;
+            stk.push(neg ? rl : rr);
             ref = neg ? rr : rl;
         } else if (hl) {
             ref = rl;
         } else if (hr) {
             ref = rr;
         } else {
-            if (sp == 0) return true;
-            --sp;
-            ref = stack[sp * stride];
+            if (stk.n == 0) return true;
+            ref = stk.pop();
         }
     }
     if (++steps > sc.max_steps) {
@@ -611,7 +683,8 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
     const uint32_t cnt = (ref & 7u) + 1u;
     const float4* tp = sc.tris + 3ull * first;
     for (uint32_t k = 0; k < cnt; ++k) {
-        const float4 a = VSR_LDG(tp + 3 * k), e1 = VSR_LDG(tp + 3 * k + 1), e2 = VSR_LDG(tp + 3 * k + 2);
+        const float4 a = VSR_LDG(tp + 3 * k), e1 = VSR_LDG(tp + 3 * k + 1),
+                     e2 = VSR_LDG(tp + 3 * k + 2);
         h.tri();
         if (STATS) st.tris++;
         float t, u, v;
@@ -630,9 +703,35 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
         best.take(t, u, v, prim);
         if (Q == kAny) return true;
     }
-    if (sp == 0) return true;
-    --sp;
-    ref = stack[sp * stride];
+    if (stk.n == 0) return true;
+    ref = stk.pop();
+    return false;
+}
+
+// Budget of a persistent loop: outer iterations per warp (0: no limit) and
+// nanoseconds of the global timer per warp (0: no limit).  When either runs
+// out the warp records kErrTimeout, marks its rays in flight as failed and
+// leaves the loop.
+struct Watchdog {
+    unsigned long long max_iters;
+    unsigned long long max_ns;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint32_t kFullMask = 0xFFFFFFFFu;
+
+// Whether a persistent warp has used up its budget.  Called by all 32 lanes
+// with the same `iters`; the result is the same on every lane.
+__device__ __forceinline__ bool watchdog_expired(const Watchdog& wd, unsigned long long iters,
+                                                 unsigned long long t0) {
+    if (wd.max_iters && iters > wd.max_iters) return true;
+    if (wd.max_ns && (iters & 255ull) == 0ull)
+        return __any_sync(kFullMask, global_ns() - t0 > wd.max_ns) != 0;
     return false;
 }
 

@@ -25,6 +25,10 @@ struct LaunchArgs {
     unsigned long long* work;  // persistent: ray counter, zeroed before launch
     const DevScene* dyn_user;  // dynamic dispatch: scene copy in device memory
     cudaStream_t stream;
+    uint32_t stack_regs;       // traversal stack entries held in registers
+    Watchdog wd;               // persistent: iteration and time budget
+    uint32_t reg_cap;          // 0: each kernel's own register budget; 1, 3, 4:
+                               // __launch_bounds__(256, reg_cap) variants
 };
 
 // Shading parameters of the differentiable render (device copy).
@@ -35,8 +39,14 @@ struct ShadeDev {
     uint32_t pad;
 };
 
-// Static injection: one instantiation per (query, intersector, stats).
+// Static injection: one instantiation per (query, intersector, stats,
+// register-stack depth).
 cudaError_t launch_static(const LaunchArgs& a, int kind, bool stats);
+// Register-stack depths the static kernels are instantiated for.
+bool stack_regs_supported(uint32_t k);
+// The static one-ray-per-thread kernel under __launch_bounds__(256, 3 or 4)
+// (trace_caps.cu): intersector kinds 1..4, stack in shared memory.
+cudaError_t launch_static_capped(const LaunchArgs& a, int kind, uint32_t min_blocks);
 // Dynamic injection: run-time checked function-pointer table.
 cudaError_t launch_dynamic(const LaunchArgs& a, int kind);
 // Resident blocks per SM for the given kernel configuration (0 on error).
@@ -45,7 +55,7 @@ int persistent_grid(const LaunchArgs& a, const void* kernel, size_t smem);
 // Multi-hit query (trace_multi.cu): the first nh (1..16) accepted hits per
 // ray in ascending (t, prim) order into a.hits [n * nh].
 cudaError_t launch_multi(const LaunchArgs& a, int kind, const float* verts, const uint32_t* idx,
-                         uint32_t nh);
+                         uint32_t nh, bool dynamic);
 // Source line of the first misaligned access the multi-hit kernels skipped
 // (0 if none), cleared after reading.
 cudaError_t multi_align_error(unsigned* line);
@@ -74,7 +84,7 @@ struct InstLaunch {
     uint32_t stack_words;  // top-level depth + deepest mesh
     cudaStream_t stream;
 };
-cudaError_t launch_instances(const InstLaunch& L, int kind, int query);
+cudaError_t launch_instances(const InstLaunch& L, int kind, int query, bool dynamic);
 // Source line of the first misaligned access the instanced kernels skipped
 // (0 if none), cleared after reading.
 cudaError_t instances_align_error(unsigned* line);
@@ -97,6 +107,8 @@ cudaError_t launch_path_bounce(const DevScene& sc, const PathDev& pd, const floa
 cudaError_t path_align_error(unsigned* line);
 cudaError_t launch_read_probe(const void* buf, unsigned long long bytes, uint32_t reps,
                               cudaStream_t stream);
+cudaError_t launch_read_probe_l1(const void* buf, unsigned long long bytes, uint32_t reps,
+                                 unsigned long long* bytes_read, cudaStream_t stream);
 
 // Closest-hit render with diffuse shading, and its adjoint (render.cu).
 cudaError_t launch_render(const LaunchArgs& a, int kind, const ShadeDev& sh, const float* verts,
@@ -122,10 +134,13 @@ struct BatchLaunch {
     unsigned long long total;
     unsigned long long* work;  // ray counter, zeroed before each launch
     uint32_t block, refill, blocks_per_sm, stack_max;
-    uint32_t grid = 0;  // non-zero: launch exactly this grid, with no set-up calls
+    uint32_t stack_regs;  // traversal stack entries held in registers
+    Watchdog wd;          // iteration and time budget of the persistent loop
+    uint32_t grid = 0;    // non-zero: launch exactly this grid, with no set-up calls
 };
 
 // Batched persistent trace over many scenes (batch.cu).
+bool batch_stack_regs_supported(uint32_t k);
 cudaError_t launch_batch(const BatchLaunch& b, int kind, int query, cudaStream_t stream);
 // Grid that launch_batch uses for b (after its shared-memory attribute is set).
 cudaError_t batch_grid(const BatchLaunch& b, int kind, int query, uint32_t* grid);

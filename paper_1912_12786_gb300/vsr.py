@@ -32,6 +32,8 @@ ISECT = {"none": 0, "default": 1, "alpha_tex": 2, "proc_alpha": 3, "count": 4, "
 DISPATCH = {"static": 0, "dynamic": 1}
 QUERY = {"closest": 0, "any": 1}
 TEX_FMT = {"u8": 0, "rgba8": 1, "rgba32f": 2}
+# device error word bits (vsr_get_device_error)
+DEVERR_STACK, DEVERR_STEPS, DEVERR_ALIGN, DEVERR_HIT, DEVERR_TIMEOUT = 1, 2, 4, 8, 16
 
 
 class VsrError(RuntimeError):
@@ -62,7 +64,9 @@ class vsr_trace_params(ctypes.Structure):
     """Launch configuration (C layout of vsr_trace_params)."""
     _fields_ = [("block_size", ctypes.c_uint32), ("persistent", ctypes.c_uint32),
                 ("refill_threshold", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
-                ("image_width", ctypes.c_uint32)]
+                ("image_width", ctypes.c_uint32), ("stack_regs", ctypes.c_uint32),
+                ("watchdog_iterations", ctypes.c_uint32), ("watchdog_ms", ctypes.c_uint32),
+                ("reg_cap_blocks", ctypes.c_uint32)]
 
 
 class vsr_path_params(ctypes.Structure):
@@ -96,6 +100,9 @@ _SIGS = {
     "vsr_scene_destroy": ([P], ctypes.c_int),
     "vsr_bvh_load": ([P, P, ctypes.c_size_t], ctypes.c_int),
     "vsr_trace": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P], ctypes.c_int),
+    "vsr_trace_tune": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, ctypes.c_uint32, P, P, P],
+                       ctypes.c_int),
+    "vsr_trace_tuned_params": ([P, P, ctypes.c_int32, P], ctypes.c_int),
     "vsr_trace_stats": ([P, P, ctypes.c_uint64, P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "vsr_trace_multi": ([P, P, ctypes.c_uint64, P, ctypes.c_uint32, P, P, P, P], ctypes.c_int),
     "vsr_instances_create": ([P, ctypes.c_uint32, P, P, ctypes.c_uint32, P, ctypes.c_size_t,
@@ -124,6 +131,8 @@ _SIGS = {
     "vsr_make_shadow_rays": ([P, P, ctypes.c_uint64, P, ctypes.c_float, P, P], ctypes.c_int),
     "vsr_get_device_error": ([P, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "vsr_read_probe": ([P, ctypes.c_uint64, ctypes.c_uint32, P], ctypes.c_int),
+    "vsr_read_probe_l1": ([P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                           P], ctypes.c_int),
     "vsr_bvh_build": ([P, ctypes.c_uint64, P, ctypes.c_uint32, P, ctypes.POINTER(P),
                        ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "vsr_bvh_free": ([P], None),
@@ -179,10 +188,20 @@ def intersector(kind="default", dispatch="static", cutoff_u8=128, cutoff_f=0.01,
 
 
 def trace_params(block_size=128, persistent=0, refill_threshold=16, blocks_per_sm=0,
-                 image_width=0):
+                 image_width=0, stack_regs=0, watchdog_iterations=0, watchdog_ms=0,
+                 reg_cap_blocks=0):
     """vsr_trace_params with the library's defaults; ``image_width`` > 0 maps
-    each warp to a 4 x 8 pixel tile of a row-major image of that width."""
-    return vsr_trace_params(block_size, persistent, refill_threshold, blocks_per_sm, image_width)
+    each warp to a 4 x 8 pixel tile of a row-major image of that width;
+    ``stack_regs`` stack entries are kept in registers; the watchdog fields
+    bound persistent loops (0 iterations: no limit; 0 ms: 60 s);
+    ``reg_cap_blocks`` selects a register budget (measurement)."""
+    return vsr_trace_params(block_size, persistent, refill_threshold, blocks_per_sm, image_width,
+                            stack_regs, watchdog_iterations, watchdog_ms, reg_cap_blocks)
+
+
+def params_dict(p: vsr_trace_params) -> dict:
+    """The fields of a vsr_trace_params as a dict."""
+    return {name: int(getattr(p, name)) for name, _ in vsr_trace_params._fields_}
 
 
 class Scene:
@@ -349,6 +368,31 @@ def vsr_trace(scene: Scene, rays, isect: vsr_intersector, query, hits, counters=
                            _stream(stream)))
 
 
+def vsr_trace_tune(scene: Scene, rays, isect: vsr_intersector, query, hits, image_width=0,
+                   stream=None) -> vsr_trace_params:
+    """Time launch configurations on ``rays`` (synchronous; ``hits`` is
+    overwritten) and keep the fastest in the scene for vsr_trace calls with
+    params None; returns it."""
+    q = QUERY[query] if isinstance(query, str) else int(query)
+    out = vsr_trace_params()
+    _check(lib().vsr_trace_tune(scene.handle, _ptr(rays), int(rays.shape[0]), ctypes.byref(isect),
+                                q, int(image_width), _ptr(hits), ctypes.byref(out),
+                                _stream(stream)))
+    return out
+
+
+def vsr_trace_tuned_params(scene: Scene, isect: vsr_intersector, query):
+    """The configuration vsr_trace uses with params None for this scene,
+    intersector and query, or None if none was tuned yet."""
+    q = QUERY[query] if isinstance(query, str) else int(query)
+    out = vsr_trace_params()
+    st = lib().vsr_trace_tuned_params(scene.handle, ctypes.byref(isect), q, ctypes.byref(out))
+    if st == VSR_ERR_STATE:
+        return None
+    _check(st)
+    return out
+
+
 def vsr_trace_persistent_noalloc(scene: Scene, rays, isect: vsr_intersector, query, hits,
                                  counters=None, params: vsr_trace_params | None = None,
                                  stream=None, n=None):
@@ -507,6 +551,16 @@ def vsr_read_probe(buf, reps: int = 1, stream=None):
     size is a multiple of 16 bytes) ``reps`` times with L2-cached loads."""
     nbytes = int(buf.numel() * buf.element_size())
     _check(lib().vsr_read_probe(_ptr(buf), nbytes, int(reps), _stream(stream)))
+
+
+def vsr_read_probe_l1(buf, reps: int = 1, stream=None) -> int:
+    """One launch in which every block reads all of ``buf`` (at most 64 KB)
+    ``reps`` times through L1; returns the bytes the launch reads."""
+    nbytes = int(buf.numel() * buf.element_size())
+    out = ctypes.c_uint64()
+    _check(lib().vsr_read_probe_l1(_ptr(buf), nbytes, int(reps), ctypes.byref(out),
+                                   _stream(stream)))
+    return int(out.value)
 
 
 def vsr_get_device_error(scene: Scene) -> int:

@@ -111,8 +111,9 @@ def test_batch_rejects_bad_arguments(batch):
     hits = _hits_like(dev_rays)
     with pytest.raises(V.VsrError, match="static dispatch"):
         V.vsr_batch_create(handles, dev_rays, hits, V.intersector("default", "dynamic"), "any")
-    with pytest.raises(V.VsrError, match="procedural-alpha any-hit query is disabled"):
-        V.vsr_batch_create(handles, dev_rays, hits, V.intersector("proc_alpha"), "any")
+    with pytest.raises(V.VsrError, match="stack_regs"):
+        V.vsr_batch_create(handles, dev_rays, hits, V.intersector("default"), "any",
+                           V.trace_params(persistent=1, stack_regs=1))
     sc = items[0][0]
     nobvh = V.vsr_scene_create_indexed(sc.verts, sc.idx, sc.uvs, sc.geom_id, sc.textures)
     with pytest.raises(V.VsrError, match="VSR_ERR_STATE"):

@@ -44,12 +44,12 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _gpu(V, X, rays, kind, query, params=None):
+def _gpu(V, X, rays, kind, query, params=None, dispatch="static"):
     n = rays.shape[0]
     hits = torch.full((n, 4), float("nan"), dtype=torch.float32, device="cuda")
     ids = torch.full((n,), 7, dtype=torch.int32, device="cuda")
     cnt = torch.full((n, 2), -1, dtype=torch.int32, device="cuda") if kind == "count" else None
-    V.vsr_trace_instances(X, rays, V.intersector(kind), query, hits, ids, cnt, params)
+    V.vsr_trace_instances(X, rays, V.intersector(kind, dispatch), query, hits, ids, cnt, params)
     torch.cuda.synchronize()
     return (hits.cpu().numpy(), ids.cpu().numpy().view(np.uint32),
             None if cnt is None else cnt.cpu().numpy().view(np.uint32))
@@ -113,8 +113,6 @@ def test_argument_checks(V, small):
     I, rays, X = small
     d = _dev(rays[:64])
     hits = torch.empty((64, 4), dtype=torch.float32, device="cuda")
-    with pytest.raises(V.VsrError, match="static dispatch"):
-        V.vsr_trace_instances(X, d, V.intersector("default", "dynamic"), "closest", hits)
     with pytest.raises(V.VsrError, match="one ray per thread"):
         V.vsr_trace_instances(X, d, V.intersector("default"), "closest", hits, None, None,
                               V.trace_params(persistent=1))
@@ -161,3 +159,22 @@ def test_instanced_forest_sample(V):
         assert V.vsr_instances_device_error(X) == 0
     finally:
         X.close()
+
+
+@pytest.mark.parametrize("query", ["closest", "any"])
+@pytest.mark.parametrize("kind", KINDS)
+def test_dynamic_dispatch_equals_static(V, small, kind, query):
+    """Callback dispatch through the instance set (the callbacks see each
+    instance's mesh) gives the same hits, instance ids and counters as the
+    compiled-in intersector, bit for bit, and so the oracle's."""
+    I, rays, X = small
+    d = _dev(rays)
+    a = _gpu(V, X, d, kind, query)
+    b = _gpu(V, X, d, kind, query, dispatch="dynamic")
+    assert np.array_equal(a[0].view(np.uint32), b[0].view(np.uint32))
+    assert np.array_equal(a[1], b[1])
+    if kind == "count":
+        assert np.array_equal(a[2], b[2])
+    c = _gpu(V, X, d, kind, query, V.trace_params(image_width=128), dispatch="dynamic")
+    assert np.array_equal(a[0].view(np.uint32), c[0].view(np.uint32))
+    assert V.vsr_instances_device_error(X) == 0

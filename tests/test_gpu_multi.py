@@ -40,11 +40,11 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _multi(V, s, rays, kind, nh, params=None, counters=False):
+def _multi(V, s, rays, kind, nh, params=None, counters=False, dispatch="static"):
     n = rays.shape[0]
     hits = torch.full((n, nh, 4), float("nan"), dtype=torch.float32, device="cuda")
     cnt = torch.full((n, 2), -1, dtype=torch.int32, device="cuda") if counters else None
-    V.vsr_trace_multi(s, rays, V.intersector(kind), nh, hits, cnt, params)
+    V.vsr_trace_multi(s, rays, V.intersector(kind, dispatch), nh, hits, cnt, params)
     torch.cuda.synchronize()
     return hits.cpu().numpy(), (cnt.cpu().numpy().view(np.uint32) if counters else None)
 
@@ -97,8 +97,6 @@ def test_argument_checks(V, small):
     for nh in (0, 17):
         with pytest.raises(V.VsrError):
             V.vsr_trace_multi(s, d, V.intersector("default"), nh, hits)
-    with pytest.raises(V.VsrError, match="static dispatch"):
-        V.vsr_trace_multi(s, d, V.intersector("default", "dynamic"), 4, hits)
     with pytest.raises(V.VsrError, match="one ray per thread"):
         V.vsr_trace_multi(s, d, V.intersector("default"), 4, hits, None,
                           V.trace_params(persistent=1))
@@ -132,3 +130,23 @@ def test_forest_full_frame_sample(V):
         assert V.vsr_get_device_error(s) == 0
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("nh", [1, 5, 16])
+@pytest.mark.parametrize("kind", KINDS)
+def test_dynamic_dispatch_equals_static(V, small, kind, nh):
+    """The intersector reached through the callback tables gives the same
+    records and counters as the compiled-in one, bit for bit (and so the
+    oracle's), including pixel tiles."""
+    sc, rays, blob, s = small
+    d = _dev(rays)
+    cnt = kind == "count"
+    for p in (None, V.trace_params(image_width=256)):
+        a, ca = _multi(V, s, d, kind, nh, p, counters=cnt)
+        b, cb = _multi(V, s, d, kind, nh, p, counters=cnt, dispatch="dynamic")
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), kind
+        if cnt:
+            assert np.array_equal(ca, cb)
+    ref, st = O.trace_multi(sc, rays, nh, kind, blob)
+    _compare(b, ref, st, f"dynamic {kind} N={nh}")
+    assert V.vsr_get_device_error(s) == 0
