@@ -254,8 +254,9 @@ def ao_backward_model(hit: np.ndarray, textured: np.ndarray, visible: np.ndarray
 
 def launch_config(p) -> str:
     """The launch configuration a profile summary is tied to."""
-    return (f"block={p.block_size} persistent={p.persistent} refill={p.refill_threshold} "
-            f"stack_regs={p.stack_regs} image_width={p.image_width}")
+    s = (f"block={p.block_size} persistent={p.persistent} refill={p.refill_threshold} "
+         f"stack_regs={p.stack_regs} image_width={p.image_width}")
+    return s + " ray_order=1" if getattr(p, "ray_order", 0) else s
 
 
 def profiled_levels(kernel: str, config: str):
@@ -1072,7 +1073,8 @@ def batch_bench(V, torch, dev, flush, stream, steps):
                   "speedup": round(tp / tb, 3), "batched_ms": round(tb, 3),
                   "per_scene_ms": round(tp, 3),
                   "tuned": {"block_size": p.block_size, "refill_threshold": p.refill_threshold,
-                            "blocks_per_sm": p.blocks_per_sm, "stack_regs": p.stack_regs}}
+                            "blocks_per_sm": p.blocks_per_sm, "stack_regs": p.stack_regs,
+                            "ray_order": p.ray_order}}
     for h in handles:
         h.close()
     return out
@@ -1221,12 +1223,19 @@ def main():
     ap.add_argument("--ref-stride", type=int, default=1)
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--leg", choices=["all", "large", "batch", "fwd_bwd", "trace", "ao"],
+    ap.add_argument("--leg", choices=["all", "large", "batch", "fwd_bwd", "trace", "ao",
+                                      "batch_profile"],
                     default="all", help="run one auxiliary measurement alone (profiling)")
     ap.add_argument("--block", type=int, default=128,
                     help="--leg trace/ao: block size of the profiled launches")
     ap.add_argument("--stack-regs", type=int, default=0,
                     help="--leg trace/ao: stack entries in registers of the profiled launches")
+    ap.add_argument("--refill", type=int, default=16,
+                    help="--leg batch_profile: refill threshold of the profiled launches")
+    ap.add_argument("--scenes", type=int, default=64,
+                    help="--leg batch_profile: scenes in the profiled batch")
+    ap.add_argument("--ray-order", type=int, default=0,
+                    help="--leg batch_profile: 1 traces the batch in coherence order")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -1242,9 +1251,32 @@ def profile_leg(V, torch, dev, flush, stream, args):
     `trace` -- the forest's primary closest-hit and shadow any-hit passes with
     the alpha texture on 4x8 pixel tiles, `steps` times each; `ao` -- the
     16 M-triangle workload's ambient-occlusion any-hit pass with procedural
-    alpha (static dispatch), `steps` times.  Each launch is preceded by the
-    256 MiB L2 flush, as in the timed steps."""
+    alpha (static dispatch), `steps` times; `batch_profile` -- a batch of the
+    first `--scenes` scenes of the batching workload, alpha-texture any hit,
+    `steps` launches (the first runs plainly, later ones replay its graph).
+    Each launch is preceded by the 256 MiB L2 flush, as in the timed steps."""
     from paper_1912_12786_gb300.inputs import scenes
+    if args.leg == "batch_profile":
+        # the first `scenes` scenes of the batching workload, alpha-texture
+        # any hit, one batch launch at the given configuration per step
+        items = scenes.batch_scenes(n_scenes=args.scenes)
+        blobs = scenes.build_bvhs([sc for sc, _ in items])
+        handles = [V.scene_from_inputs(sc, b) for (sc, _), b in zip(items, blobs)]
+        rays = [torch.from_numpy(r).to(dev) for _, r in items]
+        hits = [torch.empty((r.shape[0], 4), dtype=torch.float32, device=dev) for r in rays]
+        p = V.trace_params(block_size=args.block, persistent=1, refill_threshold=args.refill,
+                           stack_regs=args.stack_regs, ray_order=args.ray_order)
+        b = V.vsr_batch_create(handles, rays, hits, V.intersector("alpha_tex"), "any", p)
+        for _ in range(args.steps):
+            flush.zero_()
+            V.vsr_batch_launch(b, stream)
+        torch.cuda.synchronize(dev)
+        b.close()
+        out = {"config": launch_config(p), "rays": sum(int(r.shape[0]) for r in rays),
+               "device_error": max(V.vsr_get_device_error(h) for h in handles)}
+        for h in handles:
+            h.close()
+        return out
     if args.leg == "trace":
         sc, rays = scenes.billboard_forest()
         width = FRAME_W
@@ -1294,7 +1326,7 @@ def run_leg(args):
     V.lib()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    if args.leg in ("trace", "ao"):
+    if args.leg in ("trace", "ao", "batch_profile"):
         res = profile_leg(V, torch, dev, flush, stream, args)
     elif args.leg == "large":
         res = large_bench(V, torch, dev, flush, stream, args.steps)

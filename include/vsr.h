@@ -142,7 +142,7 @@ typedef enum vsr_query {
 /* Launch configuration.  vsr_trace with params == NULL uses the
  * configuration vsr_trace_tune chose for the scene, intersector and query (or
  * tunes one on the call's own rays, see vsr_trace_tune); other entry points
- * take NULL as the defaults {128, 0, 16, 0, 0, 0, 0, 0, 0}. */
+ * take NULL as the defaults {128, 0, 16, 0, 0, 0, 0, 0, 0, 0}. */
 typedef struct vsr_trace_params {
     uint32_t block_size;       /* threads per block, multiple of 32, 32..256 */
     uint32_t persistent;       /* 0: one ray per thread; 1: persistent warps
@@ -185,8 +185,20 @@ typedef struct vsr_trace_params {
                                   1 = none; 3 or 4 = compiled to fit that many
                                   256-thread blocks per SM (static: stack_regs
                                   0, intersectors default, alpha texture,
-                                  procedural alpha and count).  Results are
-                                  identical for every value. */
+                                  procedural alpha and count); 5 or 6 likewise,
+                                  static dispatch only.  Results are identical
+                                  for every value. */
+    uint32_t ray_order;        /* batches: 0 = each claim takes the next rays in
+                                  the batch's index order; 1 = coherence order:
+                                  every launch first sorts the rays by a key of
+                                  scene, origin (Morton code in the scene's
+                                  root box) and direction (octahedral code) and
+                                  claims follow the sorted order, so a warp's
+                                  lanes trace rays that start near each other
+                                  and point the same way (scratch 16 bytes per
+                                  ray plus histograms, held by the batch; up to
+                                  2^28 rays).  Results are identical; other
+                                  entry points take 0. */
 } vsr_trace_params;
 
 typedef struct vsr_scene vsr_scene;
@@ -462,8 +474,9 @@ vsr_status vsr_trace_persistent_noalloc(vsr_scene* scene, const vsr_ray* rays, u
  * [n[k]], 16-byte aligned, caller-owned; n[k] may be 0), the intersector
  * (static dispatch; not the clip box) and the query, and builds the device
  * tables.  With params == NULL the launch configuration (block size, refill
- * threshold, blocks per SM, stack entries in registers) is chosen by timing
- * candidates on the batch itself at the first launch; results are cached per
+ * threshold, blocks per SM, stack entries in registers, ray order) is chosen
+ * by timing candidates on the batch itself at the first launch (with the
+ * coherence order, the sort is part of every timed launch); results are cached per
  * workload shape in the process and, if the environment variable
  * VSR_TUNE_CACHE names a file, there too.  The shared-memory part of the
  * traversal stack is sized for the deepest BVH.  The persistent loop has the

@@ -307,7 +307,7 @@ vsr_status make_map(uint64_t n, uint32_t width, RayMap& m) {
     return VSR_OK;
 }
 
-constexpr vsr_trace_params kDefaultParams{128u, 0u, 16u, 0u, 0u, 0u, 0u, 0u, 0u};
+constexpr vsr_trace_params kDefaultParams{128u, 0u, 16u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 constexpr uint32_t kDefaultWatchdogMs = 60000u;
 
 // Watchdog of a persistent loop from the launch parameters (0 ms: the
@@ -351,15 +351,17 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (prm.blocks_per_sm > 32) return fail(VSR_ERR_ARG, "blocks_per_sm above 32");
     if (!stack_regs_supported(prm.stack_regs))
         return fail(VSR_ERR_ARG, "stack_regs must be 0, 1, 2, 4 or 8");
-    if (prm.reg_cap_blocks != 0 && prm.reg_cap_blocks != 1 && prm.reg_cap_blocks != 3 &&
-        prm.reg_cap_blocks != 4)
-        return fail(VSR_ERR_ARG, "reg_cap_blocks must be 0, 1, 3 or 4");
-    if ((prm.reg_cap_blocks == 3 || prm.reg_cap_blocks == 4) &&
-        is->dispatch == VSR_DISPATCH_STATIC &&
+    if (prm.ray_order != 0)
+        return fail(VSR_ERR_ARG, "ray_order 1 (coherence order) is for batched launches");
+    if (prm.reg_cap_blocks == 2 || prm.reg_cap_blocks > 6)
+        return fail(VSR_ERR_ARG, "reg_cap_blocks must be 0, 1, 3, 4, 5 or 6");
+    if (prm.reg_cap_blocks >= 5 && is->dispatch == VSR_DISPATCH_DYNAMIC)
+        return fail(VSR_ERR_ARG, "reg_cap_blocks 5 and 6 are for static dispatch");
+    if (prm.reg_cap_blocks >= 3 && is->dispatch == VSR_DISPATCH_STATIC &&
         (prm.persistent || prm.stack_regs || is->kind < VSR_ISECT_DEFAULT ||
-         is->kind > VSR_ISECT_COUNT || prm.block_size > 256))
+         is->kind > VSR_ISECT_COUNT))
         return fail(VSR_ERR_ARG,
-                    "reg_cap_blocks 3 and 4 with static dispatch: one ray per thread, stack_regs "
+                    "reg_cap_blocks 3 to 6 with static dispatch: one ray per thread, stack_regs "
                     "0, intersector default, alpha texture, procedural alpha or count");
     if (prm.persistent && is->dispatch == VSR_DISPATCH_DYNAMIC)
         return fail(VSR_ERR_ARG, "persistent launches use static dispatch only");
@@ -436,11 +438,11 @@ vsr_status tune_trace(vsr_scene* s, const LaunchArgs& base, const vsr_intersecto
             have = true;
         }
     };
-    consider(vsr_trace_params{128u, 0u, 16u, 0u, image_width, 0u, 0u, 0u, 0u});
+    consider(vsr_trace_params{128u, 0u, 16u, 0u, image_width, 0u, 0u, 0u, 0u, 0u});
     for (uint32_t b : {64u, 128u, 256u})
         for (uint32_t k : {0u, 1u, 2u, 4u, 8u})
             if ((!dynamic || k == 0) && !(b == 128u && k == 0u))
-                consider(vsr_trace_params{b, 0u, 16u, 0u, image_width, k, 0u, 0u, 0u});
+                consider(vsr_trace_params{b, 0u, 16u, 0u, image_width, k, 0u, 0u, 0u, 0u});
     if (!dynamic) {
         const vsr_trace_params one = best;
         for (uint32_t r : {1u, 8u, 16u, 24u}) {
@@ -1275,8 +1277,9 @@ struct vsr_batch {
     BatchItem* d_items = nullptr;
     unsigned long long* d_offsets = nullptr;
     unsigned long long* d_work = nullptr;
-    vsr_trace_params params{128u, 1u, 16u, 0u, 0u, 0u, 0u, 0u, 0u};
+    vsr_trace_params params{128u, 1u, 16u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     bool tuned = false;
+    uint32_t* d_sort = nullptr;  // coherence-order scratch (allocated when used)
     uint64_t shape = 0;  // workload signature for the tuning cache
     cudaStream_t side = nullptr;
     cudaGraph_t graph = nullptr;
@@ -1308,14 +1311,16 @@ bool tune_lookup(uint64_t shape, vsr_trace_params* out) {
         g_tune_file_loaded = true;
         if (const char* f = tune_file()) {
             if (FILE* fp = std::fopen(f, "r")) {
-                // one line per entry: "v2 <shape hex> <block> <refill> <blocks
-                // per SM> <stack regs>"; lines in any other form are skipped
+                // one line per entry: "v3 <shape hex> <block> <refill> <blocks
+                // per SM> <stack regs> <ray order>"; lines in any other form
+                // are skipped
                 char line[256];
                 while (std::fgets(line, sizeof line, fp)) {
                     unsigned long long sh;
-                    unsigned b, r, bps, k;
-                    if (std::sscanf(line, "v2 %llx %u %u %u %u", &sh, &b, &r, &bps, &k) == 5)
-                        g_tune_cache.push_back({sh, vsr_trace_params{b, 1u, r, bps, 0u, k, 0u, 0u, 0u}});
+                    unsigned b, r, bps, k, o;
+                    if (std::sscanf(line, "v3 %llx %u %u %u %u %u", &sh, &b, &r, &bps, &k, &o) == 6)
+                        g_tune_cache.push_back(
+                            {sh, vsr_trace_params{b, 1u, r, bps, 0u, k, 0u, 0u, 0u, o}});
                 }
                 std::fclose(fp);
             }
@@ -1334,8 +1339,9 @@ void tune_store(uint64_t shape, const vsr_trace_params& p) {
     g_tune_cache.push_back({shape, p});
     if (const char* f = tune_file()) {
         if (FILE* fp = std::fopen(f, "a")) {
-            std::fprintf(fp, "v2 %llx %u %u %u %u\n", (unsigned long long)shape, p.block_size,
-                         p.refill_threshold, p.blocks_per_sm, p.stack_regs);
+            std::fprintf(fp, "v3 %llx %u %u %u %u %u\n", (unsigned long long)shape,
+                         p.block_size, p.refill_threshold, p.blocks_per_sm, p.stack_regs,
+                         p.ray_order);
             std::fclose(fp);
         }
     }
@@ -1349,6 +1355,8 @@ vsr_status validate_params(const vsr_trace_params& p) {
     if (p.blocks_per_sm > 32) return fail(VSR_ERR_ARG, "blocks_per_sm above 32");
     if (!batch_stack_regs_supported(p.stack_regs))
         return fail(VSR_ERR_ARG, "batched launches take stack_regs 0, 2 or 4");
+    if (p.ray_order > 1) return fail(VSR_ERR_ARG, "ray_order must be 0 or 1");
+    if (p.reg_cap_blocks != 0) return fail(VSR_ERR_ARG, "batched launches take reg_cap_blocks 0");
     if (p.image_width != 0)
         return fail(VSR_ERR_ARG, "batched launches take rays in buffer order (image_width 0)");
     return VSR_OK;
@@ -1368,7 +1376,14 @@ BatchLaunch batch_launch_args(const vsr_batch* b, const vsr_trace_params& p) {
     L.stack_max = b->stack_max;
     L.stack_regs = p.stack_regs;
     L.wd = make_watchdog(p);
+    L.sort_scratch = p.ray_order ? b->d_sort : nullptr;
     return L;
+}
+
+// Coherence-order scratch of the batch (allocated once, when first needed).
+cudaError_t ensure_sort_scratch(vsr_batch* b) {
+    if (b->d_sort) return cudaSuccess;
+    return dmalloc(&b->d_sort, coherence_sort_words((uint32_t)b->total));
 }
 
 // Time candidate configurations on the batch itself (one warm-up run, then
@@ -1427,6 +1442,18 @@ vsr_status batch_tune(vsr_batch* b) {
         cand.stack_regs = k;
         consider(cand);
     }
+    // third pass: the winner in coherence order (the sort runs in every
+    // timed launch), if the batch is small enough for it
+    if (e == cudaSuccess && b->total > 0 && b->total <= coherence_sort_max_rays()) {
+        const bool had = b->d_sort != nullptr;
+        e = ensure_sort_scratch(b);
+        if (e == cudaSuccess) {
+            vsr_trace_params cand = best;
+            cand.ray_order = 1u;
+            consider(cand);
+            if (e == cudaSuccess && best.ray_order == 0 && !had) dfree(b->d_sort);
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(e, "autotune");
@@ -1443,6 +1470,7 @@ void batch_free(vsr_batch* b) {
     dfree(b->d_items);
     dfree(b->d_offsets);
     dfree(b->d_work);
+    dfree(b->d_sort);
     delete b;
 }
 
@@ -1542,6 +1570,11 @@ extern "C" vsr_status vsr_batch_launch(vsr_batch* b, vsr_stream stream) {
             vsr_status st = batch_tune(b);
             if (st != VSR_OK) return st;
         }
+        if (b->params.ray_order) {
+            if (b->total > coherence_sort_max_rays())
+                return fail(VSR_ERR_ARG, "too many rays in the batch for the coherence order");
+            VSR_CUDA(ensure_sort_scratch(b), "coherence-order scratch");
+        }
         BatchLaunch L = batch_launch_args(b, b->params);
         // one plain launch resolves the grid and shared-memory attribute
         VSR_CUDA(launch_batch(L, b->kind, b->query, b->side), "batch launch");
@@ -1608,9 +1641,12 @@ extern "C" vsr_status vsr_trace_batch(vsr_scene* const* scenes, const vsr_ray* c
     key = fnv_mix(fnv_mix(key, is->alpha_cutoff_u8), fbits);
     std::memcpy(&fbits, &is->proc_freq, 4);
     key = fnv_mix(key, fbits);
-    if (params)
+    if (params) {
         key = fnv_mix(fnv_mix(key, params->block_size),
                       ((uint64_t)params->refill_threshold << 32) | params->blocks_per_sm);
+        key = fnv_mix(fnv_mix(key, ((uint64_t)params->stack_regs << 32) | params->ray_order),
+                      ((uint64_t)params->watchdog_iterations << 32) | params->watchdog_ms);
+    }
     vsr_batch* b = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_batch_cache_mutex);

@@ -5,29 +5,39 @@
 // prefix offsets.  Warps claim rays from a global counter with one atomic
 // per warp and refill idle lanes when fewer than `refill` lanes are still
 // busy (the persistent scheme of k_trace_persistent).  A claim is a run of
-// consecutive indices, so it usually lies in one scene: lane 0 finds the
-// scene of the run's first index by binary search over the offsets, and each
+// consecutive indices, so it usually lies in one scene: the warp finds the
+// scene of the run's first index by a 32-way search over the offsets, and each
 // claiming lane walks forward from there to its own scene (past scenes with
 // no rays) and keeps a pointer to that scene's descriptor in the item table
 // (fields are read from L1 as the traversal needs them, instead of a
 // 128-byte copy held in registers).  Lanes of one warp may still trace
-// different scenes.  Per-ray results are identical to a per-scene
-// vsr_trace: the traversal code is the same (traverse_start /
-// traverse_step).
+// different scenes.  In coherence order (sort.cu) the claims walk the sorted
+// order instead: slot k names the ray perm[k], and scene s still owns slots
+// [offsets[s], offsets[s+1]) because the sort key is scene-major.  Per-ray
+// results are identical to a per-scene vsr_trace: the traversal code is the
+// same (traverse_start / traverse_step).
 #include "vsr_internal.h"
 
 namespace vsr {
 
-__device__ __forceinline__ uint32_t scene_of(const unsigned long long* __restrict__ offsets,
-                                             uint32_t nbatch, unsigned long long g) {
-    // largest s with offsets[s] <= g; offsets[0] = 0, offsets[nbatch] = total
-    uint32_t lo = 0, hi = nbatch;
+// Largest s with offsets[s] <= g (offsets[0] = 0, offsets[nbatch] = total),
+// found by the whole warp: each round the 32 lanes probe 32 evenly spaced
+// offsets of the remaining range at once and a ballot keeps the segment
+// that holds g, so 256 scenes take two rounds of loads (a binary search by
+// one lane takes eight dependent ones).  Called by all 32 lanes with the
+// same g; returns the same s on every lane.
+__device__ __forceinline__ uint32_t scene_of_warp(const unsigned long long* __restrict__ offsets,
+                                                  uint32_t nbatch, unsigned long long g,
+                                                  uint32_t lane) {
+    uint32_t lo = 0, hi = nbatch;  // answer in [lo, hi)
     while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (VSR_LDG(offsets + mid) <= g)
-            lo = mid;
-        else
-            hi = mid;
+        const uint32_t step = (hi - lo + 31u) / 32u;
+        const uint32_t idx = lo + lane * step;
+        const bool le = idx < hi && VSR_LDG(offsets + idx) <= g;
+        const uint32_t m = __ballot_sync(kFullMask, le);  // a prefix of the lanes (lane 0 set)
+        const uint32_t k = 31u - (uint32_t)__clz(m);
+        lo += k * step;
+        hi = min(hi, lo + step);
     }
     return lo;
 }
@@ -41,7 +51,8 @@ __global__ void __launch_bounds__(256) k_trace_batch(const BatchItem* __restrict
                                                      uint32_t nbatch, IsectParams ip,
                                                      unsigned long long total,
                                                      unsigned long long* __restrict__ work,
-                                                     uint32_t refill, Watchdog wd) {
+                                                     uint32_t refill, Watchdog wd,
+                                                     const uint32_t* __restrict__ perm) {
     extern __shared__ uint32_t s_stack[];
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -68,30 +79,37 @@ __global__ void __launch_bounds__(256) k_trace_batch(const BatchItem* __restrict
             const uint32_t idle = ~busy;
             const uint32_t nidle = (uint32_t)__popc(idle);
             unsigned long long base = 0;
-            uint32_t s0 = 0;
-            if (lane == 0) {
-                base = atomicAdd(work, (unsigned long long)nidle);
-                if (base < total) s0 = scene_of(offsets, nbatch, base);
-            }
+            if (lane == 0) base = atomicAdd(work, (unsigned long long)nidle);
             base = __shfl_sync(kFullMask, base, 0);
-            s0 = __shfl_sync(kFullMask, s0, 0);
             if (base + nidle >= total) exhausted = true;
+            const uint32_t s0 = base < total ? scene_of_warp(offsets, nbatch, base, lane) : 0u;
             if (!has) {
-                const unsigned long long g = base + (unsigned long long)__popc(idle & lt_mask);
-                if (g < total) {
+                const unsigned long long slot = base + (unsigned long long)__popc(idle & lt_mask);
+                if (slot < total) {
+                    // slots of scene s are [offsets[s], offsets[s+1]) in either order
                     uint32_t s = s0;
-                    while (s + 1 < nbatch && VSR_LDG(offsets + s + 1) <= g) ++s;
-                    ri = g - VSR_LDG(offsets + s);
+                    while (s + 1 < nbatch && VSR_LDG(offsets + s + 1) <= slot) ++s;
+                    const unsigned long long g = perm ? (unsigned long long)VSR_LDG(perm + slot)
+                                                      : slot;
+                    const unsigned long long lo_s = VSR_LDG(offsets + s);
+                    ri = g - lo_s;
                     scp = &items[s].sc;
-                    const float4* rays = items[s].rays;
-                    hp = items[s].hits;
-                    r = make_ray(VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
-                    h = H();
-                    has = true;
-                    if (!traverse_start<Q, H, false>(*scp, ip, r, h, best, st, ref, steps, stk)) {
-                        finish_miss(best);
-                        hp[ri] = hit_record(best);
-                        has = false;
+                    if (perm && (g < lo_s || g >= VSR_LDG(offsets + s + 1))) {
+                        // a sorted slot naming a ray of another scene cannot
+                        // happen with a scene-major sort; never index with it
+                        atomicOr(scp->err, kErrHit);
+                    } else {
+                        const float4* rays = items[s].rays;
+                        hp = items[s].hits;
+                        r = make_ray(VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
+                        h = H();
+                        has = true;
+                        if (!traverse_start<Q, H, false>(*scp, ip, r, h, best, st, ref, steps,
+                                                         stk)) {
+                            finish_miss(best);
+                            hp[ri] = hit_record(best);
+                            has = false;
+                        }
                     }
                 }
             }
@@ -146,10 +164,16 @@ cudaError_t batch_one(const BatchLaunch& b, cudaStream_t stream, uint32_t* grid_
         *grid_out = grid;
         return cudaSuccess;
     }
+    uint32_t* perm = nullptr;
+    if (b.sort_scratch) {
+        cudaError_t e = launch_coherence_sort(b.items, b.offsets, b.nbatch, (uint32_t)b.total,
+                                              b.sort_scratch, &perm, stream);
+        if (e != cudaSuccess) return e;
+    }
     cudaError_t e = cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
     k<<<grid, b.block, smem, stream>>>(b.items, b.offsets, b.nbatch, b.ip, b.total, b.work,
-                                       b.refill, b.wd);
+                                       b.refill, b.wd, perm);
     return cudaGetLastError();
 }
 

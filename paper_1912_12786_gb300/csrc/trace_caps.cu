@@ -2,7 +2,9 @@
 // (k_trace_cap, trace_static.cuh): 3 or 4 resident 256-thread blocks per SM,
 // the budgets of the callback kernel, so that the cost of reaching the
 // intersector through function pointers can be measured with the register
-// budget held equal.  One ray per thread, stack in shared memory.
+// budget held equal; 5 and 6 blocks (at most 51 and 42 registers) to measure
+// what occupancy buys the static kernel.  One ray per thread, stack in
+// shared memory.
 #include "trace_static.cuh"
 
 namespace vsr {
@@ -38,6 +40,10 @@ cudaError_t launch_static_capped(const LaunchArgs& a, int kind, uint32_t min_blo
         return a.query == kClosest ? cap_kind<kClosest, 3>(a, kind) : cap_kind<kAny, 3>(a, kind);
     if (min_blocks == 4)
         return a.query == kClosest ? cap_kind<kClosest, 4>(a, kind) : cap_kind<kAny, 4>(a, kind);
+    if (min_blocks == 5)
+        return a.query == kClosest ? cap_kind<kClosest, 5>(a, kind) : cap_kind<kAny, 5>(a, kind);
+    if (min_blocks == 6)
+        return a.query == kClosest ? cap_kind<kClosest, 6>(a, kind) : cap_kind<kAny, 6>(a, kind);
     return cudaErrorInvalidValue;
 }
 

@@ -27,7 +27,7 @@ struct LaunchArgs {
     cudaStream_t stream;
     uint32_t stack_regs;       // traversal stack entries held in registers
     Watchdog wd;               // persistent: iteration and time budget
-    uint32_t reg_cap;          // 0: each kernel's own register budget; 1, 3, 4:
+    uint32_t reg_cap;          // 0: each kernel's own register budget; 1, 3..6:
                                // __launch_bounds__(256, reg_cap) variants
 };
 
@@ -44,7 +44,7 @@ struct ShadeDev {
 cudaError_t launch_static(const LaunchArgs& a, int kind, bool stats);
 // Register-stack depths the static kernels are instantiated for.
 bool stack_regs_supported(uint32_t k);
-// The static one-ray-per-thread kernel under __launch_bounds__(256, 3 or 4)
+// The static one-ray-per-thread kernel under __launch_bounds__(256, 3..6)
 // (trace_caps.cu): intersector kinds 1..4, stack in shared memory.
 cudaError_t launch_static_capped(const LaunchArgs& a, int kind, uint32_t min_blocks);
 // Dynamic injection: run-time checked function-pointer table.
@@ -137,7 +137,17 @@ struct BatchLaunch {
     uint32_t stack_regs;  // traversal stack entries held in registers
     Watchdog wd;          // iteration and time budget of the persistent loop
     uint32_t grid = 0;    // non-zero: launch exactly this grid, with no set-up calls
+    uint32_t* sort_scratch = nullptr;  // non-null: trace in coherence order (sort.cu)
 };
+
+// Coherence order of a batch's rays (sort.cu): scratch words for n rays,
+// the largest n it handles, and the sort itself, which leaves in *perm
+// (inside scratch) the batch indices of the rays in sorted order.
+size_t coherence_sort_words(uint32_t n);
+uint32_t coherence_sort_max_rays();
+cudaError_t launch_coherence_sort(const BatchItem* items, const unsigned long long* offsets,
+                                  uint32_t nbatch, uint32_t n, uint32_t* scratch,
+                                  uint32_t** perm, cudaStream_t stream);
 
 // Batched persistent trace over many scenes (batch.cu).
 bool batch_stack_regs_supported(uint32_t k);

@@ -132,3 +132,38 @@ def test_batch_rejects_bad_arguments(batch):
     with pytest.raises(V.VsrError, match="device memory"):
         V.vsr_batch_create(handles[:1], [HostTensor()], hits[:1], V.intersector("default"), "any")
     del ctypes, small
+
+
+@pytest.mark.parametrize("kind,query", [("alpha_tex", "closest"), ("alpha_tex", "any"),
+                                        ("proc_alpha", "any"), ("count", "closest")])
+def test_coherence_order_equals_buffer_order(batch, kind, query):
+    """Tracing in coherence order (the rays sorted by scene, origin and
+    direction inside the launch) gives every ray the record of the buffer
+    order, bit for bit: each ray is traced exactly once.  The batch holds an
+    empty scene and a scene without rays."""
+    V, items, blobs, handles, dev_rays = batch
+    isect = V.intersector(kind)
+    outs = []
+    for order, regs in ((0, 0), (1, 0), (1, 4)):
+        hits = _hits_like(dev_rays)
+        p = V.trace_params(block_size=128, persistent=1, refill_threshold=16, stack_regs=regs,
+                           ray_order=order, watchdog_ms=10_000)
+        b = V.vsr_batch_create(handles, dev_rays, hits, isect, query, p)
+        V.vsr_batch_launch(b)
+        V.vsr_batch_launch(b)  # the graph replay sorts again
+        torch.cuda.synchronize()
+        b.close()
+        outs.append(hits)
+    for other in outs[1:]:
+        for k, (x, y) in enumerate(zip(outs[0], other)):
+            assert torch.equal(x.view(torch.int32), y.view(torch.int32)), k
+    for h in handles:
+        assert V.vsr_get_device_error(h) == 0
+
+
+def test_coherence_order_rejected_outside_batches(batch):
+    V, items, blobs, handles, dev_rays = batch
+    hits = torch.empty((dev_rays[0].shape[0], 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(V.VsrError, match="ray_order"):
+        V.vsr_trace(handles[0], dev_rays[0], V.intersector("default"), "closest", hits, None,
+                    V.trace_params(ray_order=1))
