@@ -256,7 +256,11 @@ def launch_config(p) -> str:
     """The launch configuration a profile summary is tied to."""
     s = (f"block={p.block_size} persistent={p.persistent} refill={p.refill_threshold} "
          f"stack_regs={p.stack_regs} image_width={p.image_width}")
-    return s + " ray_order=1" if getattr(p, "ray_order", 0) else s
+    if getattr(p, "ray_order", 0):
+        s += " ray_order=1"
+    if getattr(p, "lockstep", 0):
+        s += " lockstep=1"
+    return s
 
 
 def profiled_levels(kernel: str, config: str):
@@ -296,7 +300,9 @@ def profile_params(V, kernel: str):
                                       persistent=int(kv["persistent"]),
                                       refill_threshold=int(kv["refill"]),
                                       stack_regs=int(kv["stack_regs"]),
-                                      image_width=int(kv["image_width"]))
+                                      image_width=int(kv["image_width"]),
+                                      ray_order=int(kv.get("ray_order", 0)),
+                                      lockstep=int(kv.get("lockstep", 0)))
     return None
 
 
@@ -1231,11 +1237,16 @@ def main():
     ap.add_argument("--stack-regs", type=int, default=0,
                     help="--leg trace/ao: stack entries in registers of the profiled launches")
     ap.add_argument("--refill", type=int, default=16,
-                    help="--leg batch_profile: refill threshold of the profiled launches")
+                    help="--leg batch_profile (and trace/ao with --persistent 1): refill "
+                         "threshold of the profiled launches")
     ap.add_argument("--scenes", type=int, default=64,
                     help="--leg batch_profile: scenes in the profiled batch")
     ap.add_argument("--ray-order", type=int, default=0,
-                    help="--leg batch_profile: 1 traces the batch in coherence order")
+                    help="--leg trace/ao/batch_profile: 1 traces in coherence order")
+    ap.add_argument("--persistent", type=int, default=0,
+                    help="--leg trace/ao: 1 profiles the persistent launch (--refill)")
+    ap.add_argument("--lockstep", type=int, default=0,
+                    help="--leg trace/ao/batch_profile: 1 runs each warp in lock step")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -1265,7 +1276,8 @@ def profile_leg(V, torch, dev, flush, stream, args):
         rays = [torch.from_numpy(r).to(dev) for _, r in items]
         hits = [torch.empty((r.shape[0], 4), dtype=torch.float32, device=dev) for r in rays]
         p = V.trace_params(block_size=args.block, persistent=1, refill_threshold=args.refill,
-                           stack_regs=args.stack_regs, ray_order=args.ray_order)
+                           stack_regs=args.stack_regs, ray_order=args.ray_order,
+                           lockstep=args.lockstep)
         b = V.vsr_batch_create(handles, rays, hits, V.intersector("alpha_tex"), "any", p)
         for _ in range(args.steps):
             flush.zero_()
@@ -1287,7 +1299,11 @@ def profile_leg(V, torch, dev, flush, stream, args):
     n = len(rays)
     d = torch.from_numpy(rays).to(dev)
     hits = torch.empty((n, 4), dtype=torch.float32, device=dev)
-    p = V.trace_params(block_size=args.block, stack_regs=args.stack_regs, image_width=width)
+    # coherence order replaces the pixel-tile map
+    p = V.trace_params(block_size=args.block, stack_regs=args.stack_regs,
+                       image_width=0 if args.ray_order else width, ray_order=args.ray_order,
+                       persistent=args.persistent, refill_threshold=args.refill,
+                       lockstep=args.lockstep)
     out = {"config": launch_config(p)}
     if args.leg == "trace":
         alpha = V.intersector("alpha_tex")

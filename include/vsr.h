@@ -188,17 +188,34 @@ typedef struct vsr_trace_params {
                                   procedural alpha and count); 5 or 6 likewise,
                                   static dispatch only.  Results are identical
                                   for every value. */
-    uint32_t ray_order;        /* batches: 0 = each claim takes the next rays in
-                                  the batch's index order; 1 = coherence order:
-                                  every launch first sorts the rays by a key of
-                                  scene, origin (Morton code in the scene's
-                                  root box) and direction (octahedral code) and
-                                  claims follow the sorted order, so a warp's
-                                  lanes trace rays that start near each other
-                                  and point the same way (scratch 16 bytes per
-                                  ray plus histograms, held by the batch; up to
-                                  2^28 rays).  Results are identical; other
-                                  entry points take 0. */
+    uint32_t ray_order;        /* 0 = rays in the caller's order (or pixel
+                                  tiles); 1 = coherence order: every launch
+                                  first sorts the rays by a key of scene,
+                                  origin (Morton code in the scene's root box)
+                                  and direction (octahedral code), and threads
+                                  (or a batch's claims) take them in sorted
+                                  order, so a warp's lanes trace rays that
+                                  start near each other and point the same
+                                  way.  vsr_trace (image_width 0; scratch of
+                                  20 bytes per ray plus histograms from the
+                                  stream-ordered allocator) and batches (the
+                                  scratch held by the batch); up to 2^28 rays.
+                                  Results are identical; other entry points
+                                  take 0. */
+    uint32_t lockstep;         /* 1 = the warp runs the traversal in lock step:
+                                  the node loop and the primitive loop repeat
+                                  while any lane needs them and every pass ends
+                                  in a warp vote, so lanes that diverge meet
+                                  again at the next node; for the any-hit query
+                                  (intersectors without counters) a lane that
+                                  holds a leaf keeps descending toward its next
+                                  leaf while other lanes are still looking.
+                                  0 = each lane runs its own loops.  The same
+                                  nodes and leaves are visited in the same
+                                  order either way, so results are identical.
+                                  vsr_trace and vsr_path_trace (static
+                                  dispatch, reg_cap_blocks 0) and batches;
+                                  other entry points take 0. */
 } vsr_trace_params;
 
 typedef struct vsr_scene vsr_scene;
@@ -275,11 +292,15 @@ vsr_status vsr_trace(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
  * Choose vsr_trace's launch configuration for (scene, intersector kind,
  * dispatch, query) by timing candidates on the caller's rays, keep it in the
  * scene for vsr_trace calls with params == NULL and return it in *out.
- * Candidates: one ray per thread with block 64, 128 or 256 and 0, 1, 2, 4 or
- * 8 stack entries in registers (static dispatch; 0 for dynamic), then, for
- * static dispatch, the persistent launch at the fastest block and depth with
- * refill thresholds 1, 8, 16 and 24.  Every candidate takes image_width (0:
- * buffer order); all give the same hits, so only the time differs.
+ * Candidates: one ray per thread with block 64, 128 or 256, 0, 1, 2, 4 or 8
+ * stack entries in registers and per-lane loops or lock step (static
+ * dispatch; dynamic: 0 entries, per-lane loops), starting from the default;
+ * then the fastest of these in coherence order (ray_order 1, the sort timed
+ * with it); then, for static dispatch, the persistent launch at the fastest
+ * configuration with per-lane loops and in lock step, refill thresholds 1,
+ * 8, 16 and 24.  A candidate replaces the best only when at least 2%
+ * faster.  The candidates take image_width (0: buffer order), except the
+ * coherence-order one; all give the same hits, so only the time differs.
  * Synchronous (stream synchronised per candidate); hits is written several
  * times; counters are not written.  Not on a stream being captured
  * (VSR_ERR_STATE).  The configuration stays with the scene (vsr_scene_update

@@ -294,7 +294,7 @@ IsectParams isect_params(const vsr_intersector* is) {
 // whose count would not fit one launch are refused.
 vsr_status make_map(uint64_t n, uint32_t width, RayMap& m) {
     constexpr uint64_t kMaxThreads = (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull;
-    m = RayMap{n, n, 0u, 0u};
+    m = RayMap{n, n, 0u, 0u, nullptr};
     if (width == 0 || n == 0) return VSR_OK;
     if (width > n) width = (uint32_t)n;  // one partial row: the same rays
     const uint64_t rows = (n + width - 1) / width;
@@ -307,7 +307,7 @@ vsr_status make_map(uint64_t n, uint32_t width, RayMap& m) {
     return VSR_OK;
 }
 
-constexpr vsr_trace_params kDefaultParams{128u, 0u, 16u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+constexpr vsr_trace_params kDefaultParams{128u, 0u, 16u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 constexpr uint32_t kDefaultWatchdogMs = 60000u;
 
 // Watchdog of a persistent loop from the launch parameters (0 ms: the
@@ -331,6 +331,7 @@ vsr_status apply_params(LaunchArgs& a, uint64_t n, const vsr_trace_params& prm) 
     a.stack_regs = prm.stack_regs;
     a.wd = make_watchdog(prm);
     a.reg_cap = prm.reg_cap_blocks;
+    a.lockstep = prm.lockstep;
     return VSR_OK;
 }
 
@@ -352,9 +353,12 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (!stack_regs_supported(prm.stack_regs))
         return fail(VSR_ERR_ARG, "stack_regs must be 0, 1, 2, 4 or 8");
     if (prm.ray_order != 0)
-        return fail(VSR_ERR_ARG, "ray_order 1 (coherence order) is for batched launches");
+        return fail(VSR_ERR_ARG, "ray_order 1 (coherence order) is for vsr_trace and batched launches");
     if (prm.reg_cap_blocks == 2 || prm.reg_cap_blocks > 6)
         return fail(VSR_ERR_ARG, "reg_cap_blocks must be 0, 1, 3, 4, 5 or 6");
+    if (prm.lockstep > 1) return fail(VSR_ERR_ARG, "lockstep must be 0 or 1");
+    if (prm.lockstep && (is->dispatch != VSR_DISPATCH_STATIC || prm.reg_cap_blocks))
+        return fail(VSR_ERR_ARG, "lockstep 1 takes static dispatch and reg_cap_blocks 0");
     if (prm.reg_cap_blocks >= 5 && is->dispatch == VSR_DISPATCH_DYNAMIC)
         return fail(VSR_ERR_ARG, "reg_cap_blocks 5 and 6 are for static dispatch");
     if (prm.reg_cap_blocks >= 3 && is->dispatch == VSR_DISPATCH_STATIC &&
@@ -387,6 +391,27 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     return VSR_OK;
 }
 
+// Launch `a` in the rays' coherence order (vsr_trace with ray_order 1):
+// scratch from the stream-ordered allocator, the sort of the rays by origin
+// and direction, the trace through the resulting permutation, the scratch
+// freed on the stream.
+cudaError_t launch_ordered(LaunchArgs a, int kind, bool dynamic) {
+    if (a.n > coherence_sort_max_rays()) return cudaErrorInvalidValue;
+    uint32_t* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch),
+                                    coherence_sort_words((uint32_t)a.n) * sizeof(uint32_t),
+                                    a.stream);
+    if (e != cudaSuccess) return e;
+    uint32_t* perm = nullptr;
+    e = launch_coherence_sort_scene(a.sc, a.rays, (uint32_t)a.n, scratch, &perm, a.stream);
+    if (e == cudaSuccess) {
+        a.map = RayMap{a.n, a.n, 0u, 0u, perm};
+        e = dynamic ? launch_dynamic(a, kind) : launch_static(a, kind, false);
+    }
+    const cudaError_t f = cudaFreeAsync(scratch, a.stream);
+    return e != cudaSuccess ? e : f;
+}
+
 // Time `c` on the launch `base` describes (the caller's rays and hit
 // buffer): one warm-up launch, then the mean of two launches between CUDA
 // events on base.stream.
@@ -394,7 +419,10 @@ cudaError_t time_params(const LaunchArgs& base, const vsr_trace_params& c, int k
                         bool dynamic, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
     LaunchArgs a = base;
     if (apply_params(a, a.n, c) != VSR_OK) return cudaErrorInvalidValue;
-    auto launch = [&]() { return dynamic ? launch_dynamic(a, kind) : launch_static(a, kind, false); };
+    auto launch = [&]() {
+        if (c.ray_order) return launch_ordered(a, kind, dynamic);
+        return dynamic ? launch_dynamic(a, kind) : launch_static(a, kind, false);
+    };
     cudaError_t e = launch();
     if (e == cudaSuccess) e = cudaEventRecord(e0, a.stream);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch();
@@ -407,11 +435,13 @@ cudaError_t time_params(const LaunchArgs& base, const vsr_trace_params& c, int k
 
 // Choose a launch configuration for (scene, intersector, query) by timing
 // candidates on the caller's rays, and remember it in the scene.  First pass:
-// one ray per thread, block 64/128/256 x register-stack depth 0/1/2/4/8
-// (depth 0 only for dynamic dispatch), starting from the default (128, 0);
-// second pass (static dispatch): the persistent launch at the best block and
-// depth with refill thresholds 1/8/16/24.  Every candidate keeps the caller's
-// image_width.
+// one ray per thread, per-lane loops and lock step x block 64/128/256 x
+// register-stack depth 0/1/2/4/8 (static dispatch; dynamic: depth 0, per-lane
+// loops), starting from the default (128, 0, per-lane loops);
+// then the best of these in coherence order (its sort timed with it); last
+// (static dispatch): the persistent launch at the best configuration with
+// per-lane loops and in lock step, refill thresholds 1/8/16/24.  Every
+// candidate but the coherence-order one keeps the caller's image_width.
 vsr_status tune_trace(vsr_scene* s, const LaunchArgs& base, const vsr_intersector* is,
                       int32_t query, uint32_t image_width, vsr_trace_params* out) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -438,19 +468,30 @@ vsr_status tune_trace(vsr_scene* s, const LaunchArgs& base, const vsr_intersecto
             have = true;
         }
     };
-    consider(vsr_trace_params{128u, 0u, 16u, 0u, image_width, 0u, 0u, 0u, 0u, 0u});
-    for (uint32_t b : {64u, 128u, 256u})
-        for (uint32_t k : {0u, 1u, 2u, 4u, 8u})
-            if ((!dynamic || k == 0) && !(b == 128u && k == 0u))
-                consider(vsr_trace_params{b, 0u, 16u, 0u, image_width, k, 0u, 0u, 0u, 0u});
+    consider(vsr_trace_params{128u, 0u, 16u, 0u, image_width, 0u, 0u, 0u, 0u, 0u, 0u});
+    for (uint32_t ls : {0u, 1u})
+        for (uint32_t b : {64u, 128u, 256u})
+            for (uint32_t k : {0u, 1u, 2u, 4u, 8u})
+                if ((!dynamic || (k == 0 && ls == 0)) && !(b == 128u && k == 0u && ls == 0u))
+                    consider(vsr_trace_params{b, 0u, 16u, 0u, image_width, k, 0u, 0u, 0u, 0u, ls});
+    if (base.n <= coherence_sort_max_rays()) {
+        // the fastest one-ray-per-thread configuration in coherence order
+        // (the sort is part of every timed launch)
+        vsr_trace_params c = best;
+        c.image_width = 0;
+        c.ray_order = 1;
+        consider(c);
+    }
     if (!dynamic) {
         const vsr_trace_params one = best;
-        for (uint32_t r : {1u, 8u, 16u, 24u}) {
-            vsr_trace_params c = one;
-            c.persistent = 1u;
-            c.refill_threshold = r;
-            consider(c);
-        }
+        for (uint32_t ls : {0u, 1u})
+            for (uint32_t r : {1u, 8u, 16u, 24u}) {
+                vsr_trace_params c = one;
+                c.persistent = 1u;
+                c.refill_threshold = r;
+                c.lockstep = ls;
+                consider(c);
+            }
     }
     if (e1) cudaEventDestroy(e1);
     cudaEventDestroy(e0);
@@ -675,6 +716,20 @@ vsr_status vsr_trace(vsr_scene* s, const vsr_ray* rays, uint64_t n, const vsr_in
                      int32_t query, vsr_hit* hits, uint32_t* counters,
                      const vsr_trace_params* p, vsr_stream stream) {
     g_err.clear();
+    // coherence order: checked here, then the launch is prepared without it
+    vsr_trace_params given;
+    bool ordered = false;
+    if (p && p->ray_order) {
+        if (p->ray_order > 1) return fail(VSR_ERR_ARG, "ray_order must be 0 or 1");
+        if (p->image_width)
+            return fail(VSR_ERR_ARG, "ray_order 1 replaces the pixel-tile map: image_width 0");
+        if (n > coherence_sort_max_rays())
+            return fail(VSR_ERR_ARG, "too many rays for the coherence order (2^28)");
+        given = *p;
+        given.ray_order = 0;
+        p = &given;
+        ordered = true;
+    }
     LaunchArgs a;
     vsr_status st = prepare_launch(s, rays, n, is, query, hits, p, a);
     if (st != VSR_OK) return st;
@@ -701,6 +756,7 @@ vsr_status vsr_trace(vsr_scene* s, const vsr_ray* rays, uint64_t n, const vsr_in
         if (have) {
             st = apply_params(a, n, tp);
             if (st != VSR_OK) return st;
+            ordered = tp.ray_order != 0 && n <= coherence_sort_max_rays();
         }
     }
     if (counters) {
@@ -715,8 +771,10 @@ vsr_status vsr_trace(vsr_scene* s, const vsr_ray* rays, uint64_t n, const vsr_in
     if (n == 0) return VSR_OK;
     a.stream = reinterpret_cast<cudaStream_t>(stream);
     DeviceGuard g(s->device);
-    cudaError_t e = is->dispatch == VSR_DISPATCH_STATIC ? launch_static(a, is->kind, false)
-                                                        : launch_dynamic(a, is->kind);
+    const bool dynamic = is->dispatch == VSR_DISPATCH_DYNAMIC;
+    cudaError_t e = ordered    ? launch_ordered(a, is->kind, dynamic)
+                    : dynamic ? launch_dynamic(a, is->kind)
+                              : launch_static(a, is->kind, false);
     if (e != cudaSuccess) return cuda_fail(e, "trace launch");
     return VSR_OK;
 }
@@ -755,6 +813,7 @@ vsr_status vsr_trace_multi(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     g_err.clear();
     if (max_hits < 1 || max_hits > 16) return fail(VSR_ERR_ARG, "max_hits must be in 1..16");
     if (p && p->persistent) return fail(VSR_ERR_ARG, "the multi-hit query uses one ray per thread");
+    if (p && p->lockstep) return fail(VSR_ERR_ARG, "lockstep 1 is for vsr_trace, path tracing and batches");
     LaunchArgs a;
     vsr_status st = prepare_launch(s, rays, n, is, VSR_CLOSEST, hits, p, a);
     if (st != VSR_OK) return st;
@@ -945,6 +1004,7 @@ vsr_status prepare_render(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (is && is->kind == VSR_ISECT_CLIP)
         return fail(VSR_ERR_ARG, "the clip-box intersector is for vsr_trace and vsr_trace_multi");
     if (p && p->persistent) return fail(VSR_ERR_ARG, "rendering uses non-persistent launches");
+    if (p && p->lockstep) return fail(VSR_ERR_ARG, "lockstep 1 is for vsr_trace, path tracing and batches");
     // hits are checked by the callers; a placeholder keeps prepare_launch's
     // hit check out of the way when n == 0
     vsr_status st = prepare_launch(s, rays, 0, is, VSR_CLOSEST, nullptr, p, a);
@@ -1311,16 +1371,17 @@ bool tune_lookup(uint64_t shape, vsr_trace_params* out) {
         g_tune_file_loaded = true;
         if (const char* f = tune_file()) {
             if (FILE* fp = std::fopen(f, "r")) {
-                // one line per entry: "v3 <shape hex> <block> <refill> <blocks
-                // per SM> <stack regs> <ray order>"; lines in any other form
-                // are skipped
+                // one line per entry: "v4 <shape hex> <block> <refill> <blocks
+                // per SM> <stack regs> <ray order> <lockstep>"; lines in any
+                // other form are skipped
                 char line[256];
                 while (std::fgets(line, sizeof line, fp)) {
                     unsigned long long sh;
-                    unsigned b, r, bps, k, o;
-                    if (std::sscanf(line, "v3 %llx %u %u %u %u %u", &sh, &b, &r, &bps, &k, &o) == 6)
+                    unsigned b, r, bps, k, o, ls;
+                    if (std::sscanf(line, "v4 %llx %u %u %u %u %u %u", &sh, &b, &r, &bps, &k, &o,
+                                    &ls) == 7 && ls <= 1u && o <= 1u)
                         g_tune_cache.push_back(
-                            {sh, vsr_trace_params{b, 1u, r, bps, 0u, k, 0u, 0u, 0u, o}});
+                            {sh, vsr_trace_params{b, 1u, r, bps, 0u, k, 0u, 0u, 0u, o, ls}});
                 }
                 std::fclose(fp);
             }
@@ -1339,9 +1400,9 @@ void tune_store(uint64_t shape, const vsr_trace_params& p) {
     g_tune_cache.push_back({shape, p});
     if (const char* f = tune_file()) {
         if (FILE* fp = std::fopen(f, "a")) {
-            std::fprintf(fp, "v3 %llx %u %u %u %u %u\n", (unsigned long long)shape,
+            std::fprintf(fp, "v4 %llx %u %u %u %u %u %u\n", (unsigned long long)shape,
                          p.block_size, p.refill_threshold, p.blocks_per_sm, p.stack_regs,
-                         p.ray_order);
+                         p.ray_order, p.lockstep);
             std::fclose(fp);
         }
     }
@@ -1357,6 +1418,7 @@ vsr_status validate_params(const vsr_trace_params& p) {
         return fail(VSR_ERR_ARG, "batched launches take stack_regs 0, 2 or 4");
     if (p.ray_order > 1) return fail(VSR_ERR_ARG, "ray_order must be 0 or 1");
     if (p.reg_cap_blocks != 0) return fail(VSR_ERR_ARG, "batched launches take reg_cap_blocks 0");
+    if (p.lockstep > 1) return fail(VSR_ERR_ARG, "lockstep must be 0 or 1");
     if (p.image_width != 0)
         return fail(VSR_ERR_ARG, "batched launches take rays in buffer order (image_width 0)");
     return VSR_OK;
@@ -1377,6 +1439,7 @@ BatchLaunch batch_launch_args(const vsr_batch* b, const vsr_trace_params& p) {
     L.stack_regs = p.stack_regs;
     L.wd = make_watchdog(p);
     L.sort_scratch = p.ray_order ? b->d_sort : nullptr;
+    L.lockstep = p.lockstep;
     return L;
 }
 
@@ -1389,9 +1452,9 @@ cudaError_t ensure_sort_scratch(vsr_batch* b) {
 // Time candidate configurations on the batch itself (one warm-up run, then
 // the mean of two timed runs) and keep the fastest.  First pass: block
 // 64/128/256 x refill threshold 1/8/16/24/32 x blocks per SM (occupancy or
-// 4) with the stack in shared memory; second pass: the winner with 2 and 4
-// stack entries in registers.  The caller's watchdog budget applies to every
-// run.
+// 4), lock step, stack in shared memory; then the winner with 2 and 4 stack
+// entries in registers, with per-lane loops, and in coherence order.  The
+// caller's watchdog budget applies to every run.
 vsr_status batch_tune(vsr_batch* b) {
     static const uint32_t blocks[] = {64u, 128u, 256u};
     static const uint32_t refills[] = {1u, 8u, 16u, 24u, 32u};
@@ -1433,6 +1496,7 @@ vsr_status batch_tune(vsr_batch* b) {
                 cand.refill_threshold = rf;
                 cand.blocks_per_sm = ps;
                 cand.stack_regs = 0u;
+                cand.lockstep = 1u;
                 consider(cand);
             }
     }
@@ -1440,6 +1504,11 @@ vsr_status batch_tune(vsr_batch* b) {
     for (uint32_t k : {2u, 4u}) {
         vsr_trace_params cand = first;
         cand.stack_regs = k;
+        consider(cand);
+    }
+    {
+        vsr_trace_params cand = best;
+        cand.lockstep = 0u;
         consider(cand);
     }
     // third pass: the winner in coherence order (the sort runs in every
@@ -1646,6 +1715,7 @@ extern "C" vsr_status vsr_trace_batch(vsr_scene* const* scenes, const vsr_ray* c
                       ((uint64_t)params->refill_threshold << 32) | params->blocks_per_sm);
         key = fnv_mix(fnv_mix(key, ((uint64_t)params->stack_regs << 32) | params->ray_order),
                       ((uint64_t)params->watchdog_iterations << 32) | params->watchdog_ms);
+        key = fnv_mix(key, params->lockstep);
     }
     vsr_batch* b = nullptr;
     {
@@ -1825,6 +1895,7 @@ extern "C" vsr_status vsr_trace_instances(vsr_instances* x, const vsr_ray* rays,
     if (prm.block_size < 32 || prm.block_size > 256 || prm.block_size % 32)
         return fail(VSR_ERR_ARG, "block_size must be a multiple of 32 in 32..256");
     if (prm.persistent) return fail(VSR_ERR_ARG, "instanced traces use one ray per thread");
+    if (prm.lockstep) return fail(VSR_ERR_ARG, "lockstep 1 is for vsr_trace, path tracing and batches");
     if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull)
         return fail(VSR_ERR_ARG, "too many rays for one launch");
     InstLaunch L{};

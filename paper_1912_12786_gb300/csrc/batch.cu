@@ -45,7 +45,7 @@ __device__ __forceinline__ uint32_t scene_of_warp(const unsigned long long* __re
 // Control flow as k_trace_persistent (trace_static.cuh): converged votes at
 // the top of every iteration, one divergent traversal step closed by
 // __syncwarp, uniform exits, and the watchdog.
-template <int Q, class H, int K>
+template <int Q, class H, int K, bool LS>
 __global__ void __launch_bounds__(256) k_trace_batch(const BatchItem* __restrict__ items,
                                                      const unsigned long long* __restrict__ offsets,
                                                      uint32_t nbatch, IsectParams ip,
@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(256) k_trace_batch(const BatchItem* __restrict
     Best best;
     Stats st;
     H h;
-    uint32_t ref = 0, steps = 0;
+    uint32_t ref = 0, steps = 0, leaf = 0;
+    bool more = false, pend = false;
     uint32_t* err0 = items[0].sc.err;  // the watchdog also reports to scene 0's word
     const unsigned long long t0 = wd.max_ns ? global_ns() : 0ull;
     unsigned long long iters = 0;
@@ -104,6 +105,8 @@ __global__ void __launch_bounds__(256) k_trace_batch(const BatchItem* __restrict
                         r = make_ray(VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
                         h = H();
                         has = true;
+                        more = true;
+                        pend = false;
                         if (!traverse_start<Q, H, false>(*scp, ip, r, h, best, st, ref, steps,
                                                          stk)) {
                             finish_miss(best);
@@ -127,22 +130,31 @@ __global__ void __launch_bounds__(256) k_trace_batch(const BatchItem* __restrict
             }
             break;
         }
-        if (has) {
-            if (traverse_step<Q, H, false>(*scp, ip, r, h, best, st, ref, steps, stk)) {
+        if constexpr (LS) {
+            if (warp_step<Q, H, false>(*scp, ip, r, h, best, st, has, ref, more, leaf, pend,
+                                       steps, stk)) {
                 finish_miss(best);
                 hp[ri] = hit_record(best);
                 has = false;
             }
+        } else {
+            if (has) {
+                if (traverse_step<Q, H, false>(*scp, ip, r, h, best, st, ref, steps, stk)) {
+                    finish_miss(best);
+                    hp[ri] = hit_record(best);
+                    has = false;
+                }
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
 namespace {
 
-template <int Q, class H, int K>
+template <int Q, class H, int K, bool LS>
 cudaError_t batch_one(const BatchLaunch& b, cudaStream_t stream, uint32_t* grid_out) {
-    auto k = k_trace_batch<Q, H, K>;
+    auto k = k_trace_batch<Q, H, K, LS>;
     const size_t smem = (size_t)stack_words(b.stack_max, K) * b.block * sizeof(uint32_t);
     uint32_t grid = b.grid;
     if (grid == 0) {
@@ -177,14 +189,20 @@ cudaError_t batch_one(const BatchLaunch& b, cudaStream_t stream, uint32_t* grid_
     return cudaGetLastError();
 }
 
-template <int Q, class H>
-cudaError_t batch_regs(const BatchLaunch& b, cudaStream_t stream, uint32_t* grid) {
+template <int Q, class H, bool LS>
+cudaError_t batch_depth(const BatchLaunch& b, cudaStream_t stream, uint32_t* grid) {
     switch (b.stack_regs) {
-        case 0: return batch_one<Q, H, 0>(b, stream, grid);
-        case 2: return batch_one<Q, H, 2>(b, stream, grid);
-        case 4: return batch_one<Q, H, 4>(b, stream, grid);
+        case 0: return batch_one<Q, H, 0, LS>(b, stream, grid);
+        case 2: return batch_one<Q, H, 2, LS>(b, stream, grid);
+        case 4: return batch_one<Q, H, 4, LS>(b, stream, grid);
         default: return cudaErrorInvalidValue;
     }
+}
+
+template <int Q, class H>
+cudaError_t batch_regs(const BatchLaunch& b, cudaStream_t stream, uint32_t* grid) {
+    return b.lockstep ? batch_depth<Q, H, true>(b, stream, grid)
+                      : batch_depth<Q, H, false>(b, stream, grid);
 }
 
 template <int Q>

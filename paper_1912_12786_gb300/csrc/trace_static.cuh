@@ -10,6 +10,12 @@
 //                      number of active lanes drops below a threshold
 //                      (ballot + popc), after Aila and Laine's persistent
 //                      threads, which the paper's traversal scheme cites.
+// and two ways for a warp's lanes to run the traversal: each lane its own
+// while-while loop (traverse / traverse_step), or the warp in lock step
+// (k_trace_ls, and k_trace_persistent with LS: warp_step, whose loops run
+// while any lane needs them and end every pass in a warp vote; speculative
+// descent for the any-hit query).  Both visit the same nodes and leaves in
+// the same order per ray, so every result is the same.
 //
 // Each translation unit trace_k<K>.cu includes this file and instantiates
 // the kernels for one K, so the instantiations compile in parallel.
@@ -40,6 +46,48 @@ __global__ void __launch_bounds__(256) k_trace(DevScene sc, IsectParams ip,
     hits[i] = hit_record(best);
     if (H::kCounts && counters) counters[i] = h.counters();
     if (STATS) stats[i] = make_uint4(st.boxes, st.tris, st.cands, st.texs);
+}
+
+// One ray per thread, the warp in lock step (warp_step).  Every lane stays
+// in the loop to the end (lanes past the rays with busy = false), since each
+// pass ends in a full-warp vote; launches are whole warps (block a multiple
+// of 32).  Each pass finishes a ray or tests one leaf of every busy lane, so
+// the loop ends.
+template <int Q, class H, bool STATS, int K>
+__global__ void __launch_bounds__(256) k_trace_ls(DevScene sc, IsectParams ip,
+                                                  const float4* __restrict__ rays,
+                                                  RayMap map, float4* __restrict__ hits,
+                                                  uint2* __restrict__ counters,
+                                                  uint4* __restrict__ stats) {
+    extern __shared__ uint32_t s_stack[];
+    const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long i = g < map.threads ? ray_of_thread(g, map) : map.n;
+    bool busy = i < map.n;
+    Ray r;
+    H h;
+    Best best;
+    Stats st;
+    ShortStack<K> stk;
+    stk.init(s_stack + threadIdx.x, blockDim.x);
+    uint32_t ref = 0, steps = 0, leaf = 0;
+    bool more = false, pend = false;
+    auto finish = [&]() {
+        finish_miss(best);
+        hits[i] = hit_record(best);
+        if (H::kCounts && counters) counters[i] = h.counters();
+        if (STATS) stats[i] = make_uint4(st.boxes, st.tris, st.cands, st.texs);
+        busy = false;
+    };
+    if (busy) {
+        r = make_ray(__ldg(rays + 2 * i), __ldg(rays + 2 * i + 1));
+        more = traverse_start<Q, H, STATS>(sc, ip, r, h, best, st, ref, steps, stk);
+        if (!more) finish();
+    }
+    while (__any_sync(kFullMask, busy)) {
+        if (warp_step<Q, H, STATS>(sc, ip, r, h, best, st, busy, ref, more, leaf, pend, steps,
+                                   stk))
+            finish();
+    }
 }
 
 // k_trace under a register budget: __launch_bounds__(256, MINB) asks the
@@ -82,8 +130,9 @@ __global__ void __launch_bounds__(256, MINB) k_trace_cap(DevScene sc, IsectParam
 // reconverges the warp before the next iteration.  No lane ever waits on
 // another warp or block.  Each iteration claims at least one ray or advances
 // some lane's traversal (bounded per ray by the node count), so the loop
-// ends; the watchdog bounds it whatever happens.
-template <int Q, class H, bool STATS, int K>
+// ends; the watchdog bounds it whatever happens.  With LS the step is
+// warp_step, called by all 32 lanes (converged throughout).
+template <int Q, class H, bool STATS, int K, bool LS>
 __global__ void __launch_bounds__(256) k_trace_persistent(
     DevScene sc, IsectParams ip, const float4* __restrict__ rays, RayMap map,
     float4* __restrict__ hits, uint2* __restrict__ counters, uint4* __restrict__ stats,
@@ -101,7 +150,8 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
     Best best;
     Stats st;
     H h;
-    uint32_t ref = 0, steps = 0;
+    uint32_t ref = 0, steps = 0, leaf = 0;
+    bool more = false, pend = false;
     const unsigned long long t0 = wd.max_ns ? global_ns() : 0ull;
     unsigned long long iters = 0;
 
@@ -130,6 +180,8 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
                     h = H();
                     st = Stats();
                     has = true;
+                    more = true;
+                    pend = false;
                     if (!traverse_start<Q, H, STATS>(sc, ip, r, h, best, st, ref, steps, stk))
                         finish();
                 }
@@ -145,10 +197,16 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
             }
             break;
         }
-        if (has) {
-            if (traverse_step<Q, H, STATS>(sc, ip, r, h, best, st, ref, steps, stk)) finish();
+        if constexpr (LS) {
+            if (warp_step<Q, H, STATS>(sc, ip, r, h, best, st, has, ref, more, leaf, pend, steps,
+                                       stk))
+                finish();
+        } else {
+            if (has) {
+                if (traverse_step<Q, H, STATS>(sc, ip, r, h, best, st, ref, steps, stk)) finish();
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
@@ -160,11 +218,11 @@ cudaError_t ensure_smem(Kern kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <int Q, class H, bool STATS, int K>
-cudaError_t launch_one(const LaunchArgs& a) {
+template <int Q, class H, bool STATS, int K, bool LS>
+cudaError_t launch_shape(const LaunchArgs& a) {
     const size_t smem = (size_t)stack_words(a.sc.stack_depth, K) * a.block * sizeof(uint32_t);
     if (!a.persistent) {
-        auto k = k_trace<Q, H, STATS, K>;
+        auto k = LS ? k_trace_ls<Q, H, STATS, K> : k_trace<Q, H, STATS, K>;
         cudaError_t e = ensure_smem(k, smem);
         if (e != cudaSuccess) return e;
         const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
@@ -172,7 +230,7 @@ cudaError_t launch_one(const LaunchArgs& a) {
                                                          a.counters, a.stats);
         return cudaGetLastError();
     }
-    auto k = k_trace_persistent<Q, H, STATS, K>;
+    auto k = k_trace_persistent<Q, H, STATS, K, LS>;
     cudaError_t e = ensure_smem(k, smem);
     if (e != cudaSuccess) return e;
     const int grid = persistent_grid(a, reinterpret_cast<const void*>(k), smem);
@@ -182,6 +240,12 @@ cudaError_t launch_one(const LaunchArgs& a) {
     k<<<grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits, a.counters, a.stats,
                                          a.work, a.refill, a.wd);
     return cudaGetLastError();
+}
+
+template <int Q, class H, bool STATS, int K>
+cudaError_t launch_one(const LaunchArgs& a) {
+    return a.lockstep ? launch_shape<Q, H, STATS, K, true>(a)
+                      : launch_shape<Q, H, STATS, K, false>(a);
 }
 
 template <int Q, bool STATS, int K>

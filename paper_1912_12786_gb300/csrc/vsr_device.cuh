@@ -44,6 +44,7 @@ namespace vsr {
 
 constexpr uint32_t kMiss = 0xFFFFFFFFu;
 constexpr uint32_t kLeafBit = 0x80000000u;
+constexpr uint32_t kFullMask = 0xFFFFFFFFu;  // all 32 lanes of a warp
 constexpr int kClosest = 0;
 constexpr int kAny = 1;
 
@@ -88,17 +89,21 @@ struct DevScene {
 // a 4 x 8 pixel tile (tiles in row-major order, lanes row-major inside the
 // tile), so a warp's rays are neighbours in both image directions.  The
 // grid then covers `threads` = tiles_x * tiles_y * 32 threads; threads past
-// the image's right or bottom edge take no ray.  Rays and hits keep the
-// caller's layout either way.
+// the image's right or bottom edge take no ray.  perm != null (coherence
+// order, width 0): thread g takes ray perm[g], a permutation of the rays
+// sorted by origin and direction.  Rays and hits keep the caller's layout in
+// every case.
 struct RayMap {
     unsigned long long n;        // rays
     unsigned long long threads;  // threads the grid covers
     uint32_t width, tiles_x;
+    const uint32_t* perm;        // coherence order, or null
 };
 
 // Ray of thread g (< map.threads), or map.n when the thread takes none.
 __device__ __forceinline__ unsigned long long ray_of_thread(unsigned long long g,
                                                             const RayMap& m) {
+    if (m.perm) return __ldg(m.perm + g);
     if (m.width == 0) return g;
     const uint32_t tile = (uint32_t)(g >> 5), lane = (uint32_t)g & 31u;
     const uint32_t ty = tile / m.tiles_x, tx = tile - ty * m.tiles_x;
@@ -708,6 +713,149 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
     return false;
 }
 
+// The primitive loop body of the traversal for one triangle of a leaf (tp:
+// its three float4).  Returns true when the query has its answer (an
+// accepted any hit).
+template <int Q, class H, bool STATS>
+__device__ __forceinline__ bool test_prim(const DevScene& sc, const IsectParams& ip,
+                                          const Ray& r, H& h, Best& best, Stats& st,
+                                          const float4* tp) {
+    const float4 a = VSR_LDG(tp), e1 = VSR_LDG(tp + 1), e2 = VSR_LDG(tp + 2);
+    h.tri();
+    if (STATS) st.tris++;
+    float t, u, v;
+    if (!tri_test(r, a, e1, e2, t, u, v)) return false;
+    const bool geo = u >= 0.0f && v >= 0.0f && __fadd_rn(u, v) <= 1.0f;
+    if (!geo || !(t > r.tmin) || !(t < r.tmax)) return false;
+    const uint32_t prim = __float_as_uint(a.w);
+    if (Q == kClosest) {
+        if (!best.before(t, prim)) return false;
+    }
+    if (STATS) {
+        st.cands++;
+        if (H::kTexcoords && VSR_LDG(sc.geom + prim) != kMiss) st.texs++;
+    }
+    if (!h.accept(sc, ip, prim, u, v, t)) return false;
+    best.take(t, u, v, prim);
+    return Q == kAny;
+}
+
+// Speculative descent is exact for a query whose far limit never changes
+// (any hit: the ray's tmax) and an intersector whose box hooks observe
+// nothing (no counters), with no measurement counters.
+template <int Q, class H, bool STATS>
+struct Speculate {
+    static constexpr bool value = Q == kAny && !H::kCounts && !STATS;
+};
+
+// A reached leaf is held for testing and the next node taken from the stack.
+template <class S>
+__device__ __forceinline__ void hold_leaf(uint32_t& ref, bool& more, uint32_t& leaf, bool& pend,
+                                          S& stk) {
+    if (more && !pend && (ref & kLeafBit)) {
+        leaf = ref;
+        pend = true;
+        if (stk.n)
+            ref = stk.pop();
+        else
+            more = false;
+    }
+}
+
+// One outer iteration of the while-while traversal (Section 3.2) run by the
+// whole warp in lock step: all 32 lanes call it, lanes without a ray with
+// busy = false.  The node loop and the primitive loop repeat while any lane
+// needs them and every pass ends in a full-warp vote, so lanes that diverge
+// inside a pass meet again at the next one.  (With independent thread
+// scheduling a divergent loop lets the lanes of a warp drift onto different
+// iterations, each group then issuing on its own.)
+//
+// Per lane: `ref` is the next node to visit when `more`; `leaf` is a leaf
+// reached and not yet tested when `pend`.  The descent runs until every busy
+// lane holds a leaf or has run out of nodes.  When Speculate holds, a lane
+// that already holds a leaf keeps descending toward its next one while other
+// lanes are still looking (the speculative traversal of Aila and Laine,
+// 2009): its box tests use the same far limit either way, so it visits the
+// same nodes and tests the same leaves in the same order as traverse_body,
+// only earlier.  Then each lane holding a leaf tests its primitives, one per
+// pass.  Returns true on busy lanes whose ray has finished (result in best).
+template <int Q, class H, bool STATS, class S>
+__device__ __forceinline__ bool warp_step(const DevScene& sc, const IsectParams& ip,
+                                          const Ray& r, H& h, Best& best, Stats& st, bool busy,
+                                          uint32_t& ref, bool& more, uint32_t& leaf, bool& pend,
+                                          uint32_t& steps, S& stk) {
+    constexpr bool kSpec = Speculate<Q, H, STATS>::value;
+    bool done = false;
+    if (busy) hold_leaf(ref, more, leaf, pend, stk);
+    for (;;) {  // while some lane is still looking for a leaf
+        const bool seek = busy && !done && more && !pend;  // then ref is an inner node
+        if (!__any_sync(kFullMask, seek)) break;
+        if (busy && !done && more && !(ref & kLeafBit) && (kSpec || !pend)) {
+            if (++steps > sc.max_steps) {
+                atomicOr(sc.err, kErrSteps);
+                best.fail();
+                done = true;
+            } else {
+                const float4* p = sc.nodes + 4ull * (ref >> 2);
+                float4 la, lb, ra, rb;
+                load_pair(p, la, lb, ra, rb);
+                const float tfar = h.far((Q == kClosest) ? best.t : r.tmax);
+                h.box();
+                h.box();
+                if (STATS) st.boxes += 2;
+                const bool hl = box_hit(r, la, lb, tfar) && h.keep(ip, la, lb);
+                const bool hr = box_hit(r, ra, rb, tfar) && h.keep(ip, ra, rb);
+                const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(ra.w);
+                if (hl && hr) {
+                    const bool neg = (r.negmask >> (ref & 3u)) & 1u;
+                    if (stk.n >= sc.stack_depth) {
+                        atomicOr(sc.err, kErrStack);
+                        best.fail();
+                        done = true;
+                    } else {
+                        stk.push(neg ? rl : rr);
+                        ref = neg ? rr : rl;
+                    }
+                } else if (hl) {
+                    ref = rl;
+                } else if (hr) {
+                    ref = rr;
+                } else if (stk.n) {
+                    ref = stk.pop();
+                } else {
+                    more = false;
+                }
+                if (!done) hold_leaf(ref, more, leaf, pend, stk);
+            }
+        }
+    }
+    // test the held leaves, one primitive of every lane per pass
+    uint32_t cnt = 0;
+    const float4* tp = nullptr;
+    if (busy && !done && pend) {
+        if (++steps > sc.max_steps) {
+            atomicOr(sc.err, kErrSteps);
+            best.fail();
+            done = true;
+        } else {
+            cnt = (leaf & 7u) + 1u;
+            tp = sc.tris + 3ull * ((leaf >> 3) & 0x0FFFFFFFu);
+        }
+    }
+    for (uint32_t k = 0; __any_sync(kFullMask, k < cnt); ++k) {
+        if (k < cnt && test_prim<Q, H, STATS>(sc, ip, r, h, best, st, tp + 3 * k)) {
+            done = true;
+            cnt = 0;
+        }
+    }
+    if (busy && !done) {
+        pend = false;
+        hold_leaf(ref, more, leaf, pend, stk);
+        if (!pend && !more) done = true;
+    }
+    return busy && done;
+}
+
 // Budget of a persistent loop: outer iterations per warp (0: no limit) and
 // nanoseconds of the global timer per warp (0: no limit).  When either runs
 // out the warp records kErrTimeout, marks its rays in flight as failed and
@@ -722,8 +870,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-
-constexpr uint32_t kFullMask = 0xFFFFFFFFu;
 
 // Whether a persistent warp has used up its budget.  Called by all 32 lanes
 // with the same `iters`; the result is the same on every lane.

@@ -29,6 +29,7 @@ struct LaunchArgs {
     Watchdog wd;               // persistent: iteration and time budget
     uint32_t reg_cap;          // 0: each kernel's own register budget; 1, 3..6:
                                // __launch_bounds__(256, reg_cap) variants
+    uint32_t lockstep = 0;     // 1: the warp runs the traversal in lock step
 };
 
 // Shading parameters of the differentiable render (device copy).
@@ -138,6 +139,7 @@ struct BatchLaunch {
     Watchdog wd;          // iteration and time budget of the persistent loop
     uint32_t grid = 0;    // non-zero: launch exactly this grid, with no set-up calls
     uint32_t* sort_scratch = nullptr;  // non-null: trace in coherence order (sort.cu)
+    uint32_t lockstep = 0;             // 1: the warp runs the traversal in lock step
 };
 
 // Coherence order of a batch's rays (sort.cu): scratch words for n rays,
@@ -148,6 +150,9 @@ uint32_t coherence_sort_max_rays();
 cudaError_t launch_coherence_sort(const BatchItem* items, const unsigned long long* offsets,
                                   uint32_t nbatch, uint32_t n, uint32_t* scratch,
                                   uint32_t** perm, cudaStream_t stream);
+// The same for the rays of one scene (vsr_trace with ray_order 1).
+cudaError_t launch_coherence_sort_scene(const DevScene& sc, const float4* rays, uint32_t n,
+                                        uint32_t* scratch, uint32_t** perm, cudaStream_t stream);
 
 // Batched persistent trace over many scenes (batch.cu).
 bool batch_stack_regs_supported(uint32_t k);

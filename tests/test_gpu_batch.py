@@ -161,9 +161,39 @@ def test_coherence_order_equals_buffer_order(batch, kind, query):
         assert V.vsr_get_device_error(h) == 0
 
 
-def test_coherence_order_rejected_outside_batches(batch):
+@pytest.mark.parametrize("kind,query", [("alpha_tex", "closest"), ("alpha_tex", "any"),
+                                        ("proc_alpha", "any"), ("count", "closest"),
+                                        ("count", "any"), ("default", "any")])
+def test_lockstep_equals_per_lane_loops(batch, kind, query):
+    """The batched kernel with the warp in lock step (speculative any-hit
+    descent where it applies) gives the records of per-lane loops bit for
+    bit, in buffer and coherence order and with registers holding the stack
+    top."""
+    V, items, blobs, handles, dev_rays = batch
+    isect = V.intersector(kind)
+    outs = []
+    for ls, order, regs in ((0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 0, 4)):
+        hits = _hits_like(dev_rays)
+        p = V.trace_params(block_size=128, persistent=1, refill_threshold=16, stack_regs=regs,
+                           ray_order=order, lockstep=ls, watchdog_ms=10_000)
+        b = V.vsr_batch_create(handles, dev_rays, hits, isect, query, p)
+        V.vsr_batch_launch(b)
+        V.vsr_batch_launch(b)
+        torch.cuda.synchronize()
+        b.close()
+        outs.append(hits)
+    for other in outs[1:]:
+        for k, (x, y) in enumerate(zip(outs[0], other)):
+            assert torch.equal(x.view(torch.int32), y.view(torch.int32)), k
+    for h in handles:
+        assert V.vsr_get_device_error(h) == 0
+
+
+def test_coherence_order_rejected_outside_traces_and_batches(batch):
     V, items, blobs, handles, dev_rays = batch
     hits = torch.empty((dev_rays[0].shape[0], 4), dtype=torch.float32, device="cuda")
     with pytest.raises(V.VsrError, match="ray_order"):
-        V.vsr_trace(handles[0], dev_rays[0], V.intersector("default"), "closest", hits, None,
-                    V.trace_params(ray_order=1))
+        V.vsr_trace_multi(handles[0], dev_rays[0], V.intersector("default"), 2,
+                          torch.empty((dev_rays[0].shape[0], 2, 4), dtype=torch.float32,
+                                      device="cuda"),
+                          None, V.trace_params(ray_order=1))

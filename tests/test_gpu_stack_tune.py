@@ -57,6 +57,71 @@ def test_stack_depths_match_oracle(V, small, kind, query):
     assert V.vsr_get_device_error(s) == 0
 
 
+@pytest.mark.parametrize("query", ["closest", "any"])
+@pytest.mark.parametrize("kind", ["none", "default", "alpha_tex", "proc_alpha", "count", "clip"])
+def test_lockstep_matches_oracle(V, small, kind, query):
+    """The warp in lock step (speculative descent for the any-hit query with
+    intersectors that keep no counters) gives every ray the oracle's record
+    and counts: one ray per thread and persistent, pixel tiles and buffer
+    order, stack in shared memory and in registers."""
+    sc, rays, blob, s, d_rays = small
+    clip = dict(clip_lo=(0.2, 0.1, 0.0), clip_hi=(0.8, 0.7, 0.9)) if kind == "clip" else {}
+    ref, st = O.trace_bvh(sc, blob, rays, kind, query, **clip)
+    configs = [dict(block_size=128), dict(block_size=64, stack_regs=4, image_width=256),
+               dict(block_size=256, persistent=1, refill_threshold=24, watchdog_ms=10_000),
+               dict(block_size=96, persistent=1, refill_threshold=8, stack_regs=2,
+                    watchdog_ms=10_000)]
+    for c in configs:
+        p = V.trace_params(lockstep=1, **c)
+        hits, cnt = V.trace(s, d_rays, kind, query, counters=(kind == "count"), params=p, **clip)
+        _same_as_oracle(hits, ref, st, f"lockstep {kind}/{query}/{c}")
+        if kind == "count":
+            assert np.array_equal(cnt.cpu().numpy().view(np.uint32), st[:, :2])
+    assert V.vsr_get_device_error(s) == 0
+
+
+def test_lockstep_ragged_and_single_leaf(V):
+    """Ray counts that leave partly filled warps (1, 33, 4,097 rays) and a
+    scene whose BVH is one leaf (the root itself), in lock step."""
+    sc, rays = scenes.small_quads(seed=scenes.SEED_BASE + 43)
+    blob = sc.bvh()
+    s = V.scene_from_inputs(sc, blob)
+    for n in (1, 33, 4097):
+        sub = np.ascontiguousarray(rays[:n])
+        for q in ("closest", "any"):
+            ref, st = O.trace_bvh(sc, blob, sub, "alpha_tex", q)
+            for pers in (0, 1):
+                hits, _ = V.trace(s, torch.from_numpy(sub).cuda(), "alpha_tex", q,
+                                  params=V.trace_params(lockstep=1, persistent=pers,
+                                                        watchdog_ms=10_000))
+                _same_as_oracle(hits, ref, st, f"lockstep n={n} {q} persistent={pers}")
+    s.close()
+    tiny, trays = scenes.small_quads(seed=scenes.SEED_BASE + 44, n_quads=1)
+    tblob = tiny.bvh()
+    ts = V.scene_from_inputs(tiny, tblob)
+    for q in ("closest", "any"):
+        ref, st = O.trace_bvh(tiny, tblob, trays, "default", q)
+        hits, _ = V.trace(ts, torch.from_numpy(trays).cuda(), "default", q,
+                          params=V.trace_params(lockstep=1))
+        _same_as_oracle(hits, ref, st, f"lockstep one leaf {q}")
+    assert V.vsr_get_device_error(ts) == 0
+    ts.close()
+
+
+def test_lockstep_rejected_where_unsupported(V, small):
+    sc, rays, blob, s, d_rays = small
+    hits = torch.empty((len(rays), 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(V.VsrError, match="lockstep"):
+        V.vsr_trace(s, d_rays, V.intersector("default", "dynamic"), "closest", hits, None,
+                    V.trace_params(lockstep=1))
+    with pytest.raises(V.VsrError, match="lockstep"):
+        V.vsr_trace(s, d_rays, V.intersector("default"), "closest", hits, None,
+                    V.trace_params(lockstep=2))
+    with pytest.raises(V.VsrError, match="lockstep"):
+        V.vsr_trace(s, d_rays, V.intersector("default"), "closest", hits, None,
+                    V.trace_params(lockstep=1, reg_cap_blocks=4))
+
+
 def test_stack_depths_clip_box(V, small):
     sc, rays, blob, s, d_rays = small
     lo, hi = (0.2, 0.1, 0.0), (0.8, 0.7, 0.9)
@@ -65,6 +130,70 @@ def test_stack_depths_clip_box(V, small):
         p = V.trace_params(stack_regs=regs)
         hits, _ = V.trace(s, d_rays, "clip", "closest", params=p, clip_lo=lo, clip_hi=hi)
         _same_as_oracle(hits, ref, st, f"clip K={regs}")
+
+
+@pytest.mark.parametrize("kind,query,dispatch", [("none", "closest", "static"),
+                                                 ("alpha_tex", "closest", "static"),
+                                                 ("alpha_tex", "any", "static"),
+                                                 ("proc_alpha", "any", "static"),
+                                                 ("count", "closest", "static"),
+                                                 ("alpha_tex", "closest", "dynamic"),
+                                                 ("proc_alpha", "any", "dynamic")])
+def test_trace_coherence_order_matches_oracle(V, small, kind, query, dispatch):
+    """vsr_trace with ray_order 1 sorts the rays by origin and direction and
+    traces them in that order: every ray's record (and its counts) is the
+    oracle's, one ray per thread and persistent, at several stack depths."""
+    sc, rays, blob, s, d_rays = small
+    ref, st = O.trace_bvh(sc, blob, rays, kind, query)
+    configs = [dict(block_size=128), dict(block_size=64, stack_regs=2)]
+    if dispatch == "static":
+        configs += [dict(block_size=128, persistent=1, refill_threshold=16, stack_regs=4,
+                         watchdog_ms=10_000)]
+    else:
+        configs = configs[:1]
+    for c in configs:
+        p = V.trace_params(ray_order=1, **c)
+        hits, cnt = V.trace(s, d_rays, kind, query, dispatch=dispatch,
+                            counters=(kind == "count"), params=p)
+        _same_as_oracle(hits, ref, st, f"ordered {kind}/{query}/{dispatch}/{c}")
+        if kind == "count":
+            assert np.array_equal(cnt.cpu().numpy().view(np.uint32), st[:, :2])
+    assert V.vsr_get_device_error(s) == 0
+
+
+def test_trace_coherence_order_ragged_and_empty(V):
+    """Ray counts that leave ragged radix tiles (1, 33, 4,097 rays) and an
+    empty trace, in coherence order."""
+    sc, rays = scenes.small_quads(seed=scenes.SEED_BASE + 42)
+    blob = sc.bvh()
+    s = V.scene_from_inputs(sc, blob)
+    for n in (1, 33, 4097):
+        sub = np.ascontiguousarray(rays[:n])
+        ref, st = O.trace_bvh(sc, blob, sub, "alpha_tex", "closest")
+        hits, _ = V.trace(s, torch.from_numpy(sub).cuda(), "alpha_tex", "closest",
+                          params=V.trace_params(ray_order=1))
+        _same_as_oracle(hits, ref, st, f"ordered n={n}")
+    empty = torch.empty((0, 8), dtype=torch.float32, device="cuda")
+    out = torch.empty((0, 4), dtype=torch.float32, device="cuda")
+    V.vsr_trace(s, empty, V.intersector("alpha_tex"), "closest", out, None,
+                V.trace_params(ray_order=1))
+    torch.cuda.synchronize()
+    assert V.vsr_get_device_error(s) == 0
+    s.close()
+
+
+def test_trace_coherence_order_rejected_where_unsupported(V, small):
+    sc, rays, blob, s, d_rays = small
+    hits = torch.empty((len(rays), 4), dtype=torch.float32, device="cuda")
+    isect = V.intersector("default")
+    with pytest.raises(V.VsrError, match="image_width 0"):
+        V.vsr_trace(s, d_rays, isect, "closest", hits, None,
+                    V.trace_params(ray_order=1, image_width=256))
+    with pytest.raises(V.VsrError, match="ray_order"):
+        V.vsr_trace(s, d_rays, isect, "closest", hits, None, V.trace_params(ray_order=2))
+    with pytest.raises(V.VsrError, match="ray_order"):
+        V.vsr_trace_persistent_noalloc(s, d_rays, isect, "closest", hits, None,
+                                       V.trace_params(persistent=1, ray_order=1))
 
 
 def test_stack_depth_rejected_when_unsupported(V, small):
@@ -89,7 +218,9 @@ def test_null_params_use_the_tuned_configuration(V, kind, query, dispatch):
     scratch = torch.empty((len(rays), 4), dtype=torch.float32, device="cuda")
     tuned = V.vsr_trace_tune(s, d_rays, isect, query, scratch, image_width=256)
     p = V.params_dict(tuned)
-    assert p["block_size"] in (64, 128, 256) and p["image_width"] == 256
+    assert p["block_size"] in (64, 128, 256)
+    # the tiled map, or the coherence order (which replaces it)
+    assert (p["image_width"], p["ray_order"]) in ((256, 0), (0, 1))
     assert p["stack_regs"] in ((0, 1, 2, 4, 8) if dispatch == "static" else (0,))
     if dispatch == "dynamic":
         assert p["persistent"] == 0
