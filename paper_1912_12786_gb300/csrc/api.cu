@@ -398,8 +398,9 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
 cudaError_t launch_ordered(LaunchArgs a, int kind, bool dynamic) {
     if (a.n > coherence_sort_max_rays()) return cudaErrorInvalidValue;
     uint32_t* scratch = nullptr;
+    const uint32_t ntiles = (uint32_t)((a.n + kSortTileRays - 1) / kSortTileRays);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch),
-                                    coherence_sort_words((uint32_t)a.n) * sizeof(uint32_t),
+                                    coherence_sort_words((uint32_t)a.n, ntiles) * sizeof(uint32_t),
                                     a.stream);
     if (e != cudaSuccess) return e;
     uint32_t* perm = nullptr;
@@ -1340,6 +1341,10 @@ struct vsr_batch {
     vsr_trace_params params{128u, 1u, 16u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     bool tuned = false;
     uint32_t* d_sort = nullptr;  // coherence-order scratch (allocated when used)
+    SortTile* d_sort_tiles = nullptr;      // the sort's scene-aligned tiles
+    uint32_t* d_tile_scene = nullptr;
+    std::vector<SortTile> sort_tiles;      // host copy, made at creation
+    std::vector<uint32_t> tile_scene;
     uint64_t shape = 0;  // workload signature for the tuning cache
     cudaStream_t side = nullptr;
     cudaGraph_t graph = nullptr;
@@ -1439,6 +1444,9 @@ BatchLaunch batch_launch_args(const vsr_batch* b, const vsr_trace_params& p) {
     L.stack_regs = p.stack_regs;
     L.wd = make_watchdog(p);
     L.sort_scratch = p.ray_order ? b->d_sort : nullptr;
+    L.sort_tiles = b->d_sort_tiles;
+    L.tile_scene = b->d_tile_scene;
+    L.sort_ntiles = (uint32_t)b->sort_tiles.size();
     L.lockstep = p.lockstep;
     return L;
 }
@@ -1446,7 +1454,25 @@ BatchLaunch batch_launch_args(const vsr_batch* b, const vsr_trace_params& p) {
 // Coherence-order scratch of the batch (allocated once, when first needed).
 cudaError_t ensure_sort_scratch(vsr_batch* b) {
     if (b->d_sort) return cudaSuccess;
-    return dmalloc(&b->d_sort, coherence_sort_words((uint32_t)b->total));
+    const size_t nt = b->sort_tiles.size();
+    cudaError_t e = dmalloc(&b->d_sort, coherence_sort_words((uint32_t)b->total, (uint32_t)nt));
+    if (e == cudaSuccess && !b->d_sort_tiles && nt) {
+        e = dmalloc(&b->d_sort_tiles, nt);
+        if (e == cudaSuccess) e = dmalloc(&b->d_tile_scene, nt);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_sort_tiles, b->sort_tiles.data(), sizeof(SortTile) * nt,
+                           cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_tile_scene, b->tile_scene.data(), sizeof(uint32_t) * nt,
+                           cudaMemcpyHostToDevice);
+    }
+    return e;
+}
+
+// Whether the batch fits the coherence sort (ray and tile counts).
+bool sort_fits(const vsr_batch* b) {
+    return b->total > 0 && b->total <= coherence_sort_max_rays() &&
+           b->sort_tiles.size() <= coherence_sort_max_tiles();
 }
 
 // Time candidate configurations on the batch itself (one warm-up run, then
@@ -1513,7 +1539,7 @@ vsr_status batch_tune(vsr_batch* b) {
     }
     // third pass: the winner in coherence order (the sort runs in every
     // timed launch), if the batch is small enough for it
-    if (e == cudaSuccess && b->total > 0 && b->total <= coherence_sort_max_rays()) {
+    if (e == cudaSuccess && sort_fits(b)) {
         const bool had = b->d_sort != nullptr;
         e = ensure_sort_scratch(b);
         if (e == cudaSuccess) {
@@ -1540,6 +1566,8 @@ void batch_free(vsr_batch* b) {
     dfree(b->d_offsets);
     dfree(b->d_work);
     dfree(b->d_sort);
+    dfree(b->d_sort_tiles);
+    dfree(b->d_tile_scene);
     delete b;
 }
 
@@ -1610,6 +1638,7 @@ extern "C" vsr_status vsr_batch_create(vsr_scene* const* scenes, const vsr_ray* 
     b->shape = shape;
     b->params = prm;
     b->tuned = params != nullptr || tune_lookup(shape, &b->params);
+    coherence_sort_tiles(offsets.data(), nbatch, &b->sort_tiles, &b->tile_scene);
     cudaError_t e;
     if ((e = dmalloc(&b->d_items, (size_t)nbatch)) != cudaSuccess ||
         (e = dmalloc(&b->d_offsets, (size_t)nbatch + 1)) != cudaSuccess ||
@@ -1640,7 +1669,7 @@ extern "C" vsr_status vsr_batch_launch(vsr_batch* b, vsr_stream stream) {
             if (st != VSR_OK) return st;
         }
         if (b->params.ray_order) {
-            if (b->total > coherence_sort_max_rays())
+            if (!sort_fits(b))
                 return fail(VSR_ERR_ARG, "too many rays in the batch for the coherence order");
             VSR_CUDA(ensure_sort_scratch(b), "coherence-order scratch");
         }

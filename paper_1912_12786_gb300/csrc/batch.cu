@@ -178,8 +178,9 @@ cudaError_t batch_one(const BatchLaunch& b, cudaStream_t stream, uint32_t* grid_
     }
     uint32_t* perm = nullptr;
     if (b.sort_scratch) {
-        cudaError_t e = launch_coherence_sort(b.items, b.offsets, b.nbatch, (uint32_t)b.total,
-                                              b.sort_scratch, &perm, stream);
+        cudaError_t e = launch_coherence_sort(b.items, b.offsets, b.sort_tiles, b.tile_scene,
+                                              b.sort_ntiles, (uint32_t)b.total, b.sort_scratch,
+                                              &perm, stream);
         if (e != cudaSuccess) return e;
     }
     cudaError_t e = cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), stream);

@@ -1,7 +1,6 @@
-// Coherence order for batched launches: the rays of all scenes sorted by
-// scene, then by a 32-bit key of origin and direction, and the batched kernel
-// traces them in that order (claims take consecutive slots of the sorted
-// order; each slot names a ray by its index in the batch's index space).
+// Coherence order: the rays sorted by a 32-bit key of origin and direction,
+// each scene's rays among themselves, and the trace kernels take them in
+// that order (slot k of the ray map names the ray perm[k]).
 //
 // Coherence key of a ray (32 bits):
 //   high 12 bits   Morton code of the origin, quantised in its scene's root
@@ -13,19 +12,22 @@
 // the largest gain of the key widths tried; 12 + 12 half of it.)
 //
 // The sort is a least-significant-digit radix sort on 8-bit digits over
-// (key, batch index) pairs: four passes on the coherence key, then the key is
-// replaced by the ray's scene and one more pass per 8 bits of scene index
-// (none for a single scene) restores scene-major order, keeping the
-// coherence order inside each scene because every pass is stable.  Each
-// pass: per-block digit histograms, an exclusive scan of them in digit-major
-// order, and a stable scatter.  The scatter ranks a block's elements in
-// shared memory -- each warp owns a contiguous sub-tile and walks it in
-// order; lanes with the same digit find each other with __match_any_sync --
-// places them digit by digit in a shared-memory copy of the tile, and writes
-// that out so that each digit's run goes to consecutive addresses.  The
-// order is a function of the rays alone, so it is the same on every launch.
-// Results never depend on it: every ray is traced exactly as in buffer
-// order.
+// (key, ray index) pairs, four passes.  The rays are cut into tiles of up to
+// 4096 that never straddle two scenes (SortTile).  Each pass: per-tile digit
+// counts, one exclusive scan of all counts -- laid out scene by scene, each
+// scene's digit-major -- and a stable scatter.  Because a scene's counts
+// follow all earlier scenes' counts in the scan, every scene's rays are
+// sorted within the scene's own slot range, with no pass over scene indices.
+// The scatter ranks a tile in shared memory: each warp owns a contiguous
+// sub-tile, holds its 16 pairs per lane in registers and walks them in
+// order; lanes with the same digit find each other with eight ballots, one
+// per digit bit (ALU work; a match instruction per pair saturated the
+// memory-input pipe).
+// The pairs are placed digit by digit in a shared-memory copy of the tile,
+// which is written out so that each digit's run goes to consecutive
+// addresses.  The order is a function of the rays alone, so it is the same
+// on every launch.  Results never depend on it: every ray is traced exactly
+// as in buffer order.
 #include "vsr_internal.h"
 
 namespace vsr {
@@ -33,10 +35,10 @@ namespace vsr {
 namespace {
 
 constexpr uint32_t kSortThreads = 256;
-constexpr uint32_t kSortPerThread = 16;
-constexpr uint32_t kSortTile = kSortThreads * kSortPerThread;  // 4096 keys per block
+constexpr uint32_t kSortPerThread = kSortTileRays / kSortThreads;  // 16
 constexpr uint32_t kWarps = kSortThreads / 32;
-constexpr uint32_t kSubTile = kSortTile / kWarps;  // 512 keys per warp
+constexpr uint32_t kSubTile = kSortTileRays / kWarps;  // 512 pairs per warp
+constexpr uint32_t kPerLane = kSubTile / 32;           // 16 pairs per lane
 
 __device__ __forceinline__ uint32_t spread3(uint32_t x) {  // 10 bits -> every third bit
     x &= 0x3FFu;
@@ -51,20 +53,6 @@ __device__ __forceinline__ uint32_t quantise(float x, uint32_t bits) {
     const float c = fminf(fmaxf(x, 0.0f), 1.0f);
     const uint32_t n = 1u << bits;
     return min((uint32_t)(c * (float)n), n - 1u);
-}
-
-// Scene of batch index g: the largest s with offsets[s] <= g.
-__device__ __forceinline__ uint32_t scene_of_index(const unsigned long long* __restrict__ offsets,
-                                                   uint32_t nbatch, uint32_t g) {
-    uint32_t lo = 0, hi = nbatch;
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(offsets + mid) <= g)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    return lo;
 }
 
 __device__ __forceinline__ uint32_t coherence_key(float4 a, float4 b, float4 la, float4 hb) {
@@ -88,17 +76,48 @@ __device__ __forceinline__ uint32_t coherence_key(float4 a, float4 b, float4 la,
     return (morton << db) | dir;
 }
 
-__global__ void __launch_bounds__(256) k_ray_keys(const BatchItem* __restrict__ items,
-                                                  const unsigned long long* __restrict__ offsets,
-                                                  uint32_t nbatch, uint32_t n,
-                                                  uint2* __restrict__ kv) {
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
-    const uint32_t s = scene_of_index(offsets, nbatch, g);
-    const unsigned long long ri = g - __ldg(offsets + s);
+// The lanes of the warp holding a pair (`valid`) whose 8-bit digit equals
+// this lane's: the intersection, over the digit's bits, of the lanes that
+// agree on that bit.  Called by all 32 lanes.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
+    uint32_t m = __ballot_sync(kFullMask, valid);
+#pragma unroll
+    for (uint32_t b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t v = __ballot_sync(kFullMask, bit);
+        m &= bit ? v : ~v;
+    }
+    return m;
+}
+
+// Tile b: from the table, or (table null) uniform tiles of one segment.
+__device__ __forceinline__ SortTile tile_of(const SortTile* __restrict__ tiles, uint32_t b,
+                                            uint32_t n, uint32_t ntiles) {
+    if (tiles) return tiles[b];
+    SortTile t;
+    t.start = b * kSortTileRays;
+    t.count = min(kSortTileRays, n - t.start);
+    t.hist_base = b;
+    t.stride = ntiles;
+    return t;
+}
+
+// Keys of a batch: one block per tile, so the tile's scene is known.
+__global__ void __launch_bounds__(kSortThreads) k_ray_keys(
+    const BatchItem* __restrict__ items, const unsigned long long* __restrict__ offsets,
+    const SortTile* __restrict__ tiles, const uint32_t* __restrict__ tile_scene,
+    uint2* __restrict__ kv) {
+    const SortTile t = tiles[blockIdx.x];
+    const uint32_t s = tile_scene[blockIdx.x];
     const float4* rays = items[s].rays;
-    const float4 a = __ldg(rays + 2 * ri), b = __ldg(rays + 2 * ri + 1);
-    kv[g] = make_uint2(coherence_key(a, b, items[s].sc.root_a, items[s].sc.root_b), g);
+    const float4 la = items[s].sc.root_a, hb = items[s].sc.root_b;
+    const unsigned long long lo = offsets[s];
+    for (uint32_t k = threadIdx.x; k < t.count; k += kSortThreads) {
+        const uint32_t g = t.start + k;
+        const unsigned long long ri = g - lo;
+        const float4 a = __ldg(rays + 2 * ri), b = __ldg(rays + 2 * ri + 1);
+        kv[g] = make_uint2(coherence_key(a, b, la, hb), g);
+    }
 }
 
 // Coherence keys of one scene's rays (the scene by value: no device table).
@@ -110,35 +129,35 @@ __global__ void __launch_bounds__(256) k_ray_keys_scene(DevScene sc, const float
     kv[g] = make_uint2(coherence_key(a, b, sc.root_a, sc.root_b), g);
 }
 
-// Replace every key by the scene of its ray, for the scene passes.
-__global__ void __launch_bounds__(256) k_scene_keys(const unsigned long long* __restrict__ offsets,
-                                                    uint32_t nbatch, uint32_t n,
-                                                    uint2* __restrict__ kv) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    kv[i].x = scene_of_index(offsets, nbatch, kv[i].y);
-}
-
-// Per-block digit counts.  Lanes with equal digits add once per warp (keys of
-// a block often share their high digits, which would otherwise serialise the
-// shared-memory atomics on one counter).
+// Per-tile digit counts.  A lane loads all its keys first (16 independent
+// loads in flight), then counts them; lanes with equal digits add once per
+// warp (keys of a tile often share their high digits, which would otherwise
+// serialise the shared-memory atomics on one counter).  Lanes past the tile
+// hold digit 256 and take part in the ballots only.
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint2* __restrict__ kv,
-                                                              uint32_t n, uint32_t shift,
-                                                              uint32_t nblocks,
+                                                              const SortTile* __restrict__ tiles,
+                                                              uint32_t n, uint32_t ntiles,
+                                                              uint32_t shift,
                                                               uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
-    __syncthreads();
+    const SortTile t = tile_of(tiles, blockIdx.x, n, ntiles);
     const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t base = blockIdx.x * kSortTile;
+    uint32_t d[kSortPerThread];
+#pragma unroll
     for (uint32_t r = 0; r < kSortPerThread; ++r) {
-        const uint32_t i = base + r * kSortThreads + threadIdx.x;
-        const uint32_t d = i < n ? (__ldg(kv + i).x >> shift) & 0xFFu : 256u;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-        if (d < 256u && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[d], __popc(peers));
+        const uint32_t k = r * kSortThreads + threadIdx.x;
+        d[r] = k < t.count ? (__ldg(&kv[t.start + k].x) >> shift) & 0xFFu : 256u;
     }
     __syncthreads();
-    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+#pragma unroll
+    for (uint32_t r = 0; r < kSortPerThread; ++r) {
+        const bool ok = d[r] < 256u;
+        const uint32_t peers = digit_peers(d[r], ok);
+        if (ok && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[d[r]], __popc(peers));
+    }
+    __syncthreads();
+    hist[t.hist_base + threadIdx.x * t.stride] = h[threadIdx.x];
 }
 
 // Exclusive scan, three launches: each block scans 2048 values and writes
@@ -152,7 +171,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t x = v;
     for (uint32_t o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        const uint32_t y = __shfl_up_sync(kFullMask, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) s_warp[warp] = x;
@@ -161,7 +180,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
         const uint32_t nw = blockDim.x / 32u;
         uint32_t w = lane < nw ? s_warp[lane] : 0u;
         for (uint32_t o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            const uint32_t y = __shfl_up_sync(kFullMask, w, o);
             if (lane >= o) w += y;
         }
         if (lane < nw) s_warp[lane] = w;
@@ -214,82 +233,79 @@ __global__ void __launch_bounds__(256) k_scan_add(uint32_t* __restrict__ data, u
         if (base + k < n) data[base + k] += add;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
-    const uint2* __restrict__ kv_in, uint2* __restrict__ kv_out, uint32_t n, uint32_t shift,
-    uint32_t nblocks, const uint32_t* __restrict__ offsets) {
-    __shared__ uint2 tile[kSortTile];       // the block's elements, grouped by digit
+// Stable scatter of one tile.  Lane `lane` of warp w holds the pairs at tile
+// positions w * 512 + r * 32 + lane (r = 0..15) in registers from the single
+// load to the placement in shared memory.
+__global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
+    const uint2* __restrict__ kv_in, uint2* __restrict__ kv_out,
+    const SortTile* __restrict__ tiles, uint32_t n, uint32_t ntiles, uint32_t shift,
+    const uint32_t* __restrict__ offsets) {
+    __shared__ uint2 tile[kSortTileRays];   // the tile's pairs, grouped by digit
     __shared__ uint32_t wc[kWarps][256];    // per-warp digit counts, then positions
-    __shared__ uint32_t dstart[256];        // block-local start of each digit's run
+    __shared__ uint32_t dstart[256];        // tile-local start of each digit's run
     __shared__ uint32_t gbase[256];         // global start of each digit's run
     __shared__ uint32_t s_warp[32];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     for (uint32_t k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wc[0][0])[k] = 0u;
+    const SortTile t = tile_of(tiles, blockIdx.x, n, ntiles);
+    const uint32_t sub = warp * kSubTile;
+    uint2 e[kPerLane];
+#pragma unroll
+    for (uint32_t r = 0; r < kPerLane; ++r) {
+        const uint32_t k = sub + r * 32 + lane;
+        e[r] = k < t.count ? __ldg(kv_in + t.start + k) : make_uint2(0u, 0u);
+    }
     __syncthreads();
-    const uint32_t tile0 = blockIdx.x * kSortTile;
-    const uint32_t in_block = min(kSortTile, n - tile0);
-    const uint32_t sub = tile0 + warp * kSubTile;
-    // per-warp digit counts of the warp's sub-tile
-    for (uint32_t r = 0; r < kSubTile / 32; ++r) {
-        const uint32_t i = sub + r * 32 + lane;
-        const bool ok = i < n;
-        const uint32_t d = ok ? (__ldg(kv_in + i).x >> shift) & 0xFFu : 256u;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-        if (ok && lane == (uint32_t)(__ffs(peers) - 1)) wc[warp][d] += __popc(peers);
+    // per-warp digit counts of the warp's sub-tile (digit 256: no pair)
+    uint32_t peers[kPerLane];
+#pragma unroll
+    for (uint32_t r = 0; r < kPerLane; ++r) {
+        const bool ok = sub + r * 32 + lane < t.count;
+        const uint32_t d = (e[r].x >> shift) & 0xFFu;
+        peers[r] = digit_peers(d, ok);
+        if (ok && lane == (uint32_t)(__ffs(peers[r]) - 1)) wc[warp][d] += __popc(peers[r]);
         __syncwarp();
     }
     __syncthreads();
-    // block-local layout: digit runs in digit order, inside a run the warps
+    // tile-local layout: digit runs in digit order, inside a run the warps
     // in order
     {
         const uint32_t d = threadIdx.x;
         uint32_t run = 0;
         for (uint32_t w = 0; w < kWarps; ++w) {
-            const uint32_t t = wc[w][d];
+            const uint32_t c = wc[w][d];
             wc[w][d] = run;
-            run += t;
+            run += c;
         }
         uint32_t total;
         const uint32_t start = block_exclusive_scan(run, s_warp, &total);
         dstart[d] = start;
-        gbase[d] = offsets[d * nblocks + blockIdx.x];
+        gbase[d] = offsets[t.hist_base + d * t.stride];
         for (uint32_t w = 0; w < kWarps; ++w) wc[w][d] += start;
     }
     __syncthreads();
-    for (uint32_t r = 0; r < kSubTile / 32; ++r) {
-        const uint32_t i = sub + r * 32 + lane;
-        const bool ok = i < n;
-        const uint2 e = ok ? __ldg(kv_in + i) : make_uint2(0u, 0u);
-        const uint32_t d = ok ? (e.x >> shift) & 0xFFu : 256u;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+#pragma unroll
+    for (uint32_t r = 0; r < kPerLane; ++r) {
+        const bool ok = sub + r * 32 + lane < t.count;
+        const uint32_t d = (e[r].x >> shift) & 0xFFu;
         if (ok) {
-            const uint32_t pos = wc[warp][d] + __popc(peers & lt);
-            if (pos < in_block) tile[pos] = e;  // always true for consistent counts
+            const uint32_t pos = wc[warp][d] + __popc(peers[r] & lt);
+            if (pos < t.count) tile[pos] = e[r];  // always true for consistent counts
         }
         __syncwarp();
-        if (ok && lane == (uint32_t)(__ffs(peers) - 1)) wc[warp][d] += __popc(peers);
+        if (ok && lane == (uint32_t)(__ffs(peers[r]) - 1)) wc[warp][d] += __popc(peers[r]);
         __syncwarp();
     }
     __syncthreads();
     // write out: consecutive tile positions of one digit go to consecutive
     // global positions
-    for (uint32_t k = threadIdx.x; k < in_block; k += kSortThreads) {
-        const uint2 e = tile[k];
-        const uint32_t d = (e.x >> shift) & 0xFFu;
+    for (uint32_t k = threadIdx.x; k < t.count; k += kSortThreads) {
+        const uint2 x = tile[k];
+        const uint32_t d = (x.x >> shift) & 0xFFu;
         const uint32_t out = gbase[d] + (k - dstart[d]);
-        if (out < n) kv_out[out] = e;  // always true for consistent histograms
+        if (out < n) kv_out[out] = x;  // always true for consistent counts
     }
-}
-
-}  // namespace
-
-// Scratch layout (32-bit words): two (key, index) arrays of n pairs, the
-// permutation (n words), the digit histograms, the scan's block totals.
-size_t coherence_sort_words(uint32_t n) {
-    const size_t nblocks = (n + kSortTile - 1) / kSortTile;
-    const size_t hist = 256 * nblocks;
-    const size_t totals = (hist + kScanBlock - 1) / kScanBlock;
-    return 5ull * n + hist + totals;
 }
 
 __global__ void __launch_bounds__(256) k_perm(const uint2* __restrict__ kv, uint32_t n,
@@ -298,43 +314,25 @@ __global__ void __launch_bounds__(256) k_perm(const uint2* __restrict__ kv, uint
     if (i < n) perm[i] = kv[i].y;
 }
 
-uint32_t coherence_sort_max_rays() {
-    // the histograms' scan takes up to 1024 x 8 block totals of 2048 values
-    return (uint32_t)((1024ull * kScanPer * kScanBlock / 256ull) * kSortTile);
-}
-
-namespace {
-
-// Radix passes over the (key, index) pairs in kv[*cur]: four on the coherence
-// key, then, for batches, the key is replaced by the scene and one pass per
-// 8 bits of scene index follows.  Leaves the batch indices in sorted order
-// in `out`.
-cudaError_t sort_pairs(uint2* kv[2], uint32_t n, uint32_t* out, uint32_t* hist,
-                       uint32_t* totals, const unsigned long long* offsets, uint32_t nbatch,
-                       cudaStream_t stream) {
-    const uint32_t nblocks = (n + kSortTile - 1) / kSortTile;
-    const uint32_t hist_n = 256u * nblocks;
+// Four radix passes over the (key, index) pairs in kv[0]; leaves the ray
+// indices in sorted order in `out`.
+cudaError_t sort_pairs(uint2* kv[2], uint32_t n, const SortTile* tiles, uint32_t ntiles,
+                       uint32_t* out, uint32_t* hist, uint32_t* totals, cudaStream_t stream) {
+    const uint32_t hist_n = 256u * ntiles;
     const uint32_t ntot = (hist_n + kScanBlock - 1) / kScanBlock;
-    if (ntot > 1024u * kScanPer) return cudaErrorInvalidValue;
-    uint32_t scene_bits = 0;
-    while ((1ull << scene_bits) < nbatch) ++scene_bits;
+    if (ntiles > coherence_sort_max_tiles() || ntot > 1024u * kScanPer)
+        return cudaErrorInvalidValue;
     cudaError_t e = cudaGetLastError();
     int cur = 0;
-    auto pass = [&](uint32_t shift) {
-        k_radix_hist<<<nblocks, kSortThreads, 0, stream>>>(kv[cur], n, shift, nblocks, hist);
+    for (uint32_t shift = 0; shift < 32 && e == cudaSuccess; shift += 8) {
+        k_radix_hist<<<ntiles, kSortThreads, 0, stream>>>(kv[cur], tiles, n, ntiles, shift, hist);
         k_scan_blocks<<<ntot, 256, 0, stream>>>(hist, hist_n, totals);
         k_scan_totals<<<1, 1024, 0, stream>>>(totals, ntot);
         k_scan_add<<<ntot, 256, 0, stream>>>(hist, hist_n, totals);
-        k_radix_scatter<<<nblocks, kSortThreads, 0, stream>>>(kv[cur], kv[cur ^ 1], n, shift,
-                                                             nblocks, hist);
+        k_radix_scatter<<<ntiles, kSortThreads, 0, stream>>>(kv[cur], kv[cur ^ 1], tiles, n,
+                                                             ntiles, shift, hist);
         e = cudaGetLastError();
         cur ^= 1;
-    };
-    for (uint32_t shift = 0; shift < 32 && e == cudaSuccess; shift += 8) pass(shift);
-    if (scene_bits && e == cudaSuccess) {
-        k_scene_keys<<<(n + 255) / 256, 256, 0, stream>>>(offsets, nbatch, n, kv[cur]);
-        e = cudaGetLastError();
-        for (uint32_t shift = 0; shift < scene_bits && e == cudaSuccess; shift += 8) pass(shift);
     }
     if (e == cudaSuccess) {
         k_perm<<<(n + 255) / 256, 256, 0, stream>>>(kv[cur], n, out);
@@ -345,17 +343,53 @@ cudaError_t sort_pairs(uint2* kv[2], uint32_t n, uint32_t* out, uint32_t* hist,
 
 }  // namespace
 
+void coherence_sort_tiles(const unsigned long long* offsets, uint32_t nbatch,
+                          std::vector<SortTile>* tiles, std::vector<uint32_t>* tile_scene) {
+    tiles->clear();
+    tile_scene->clear();
+    uint32_t first = 0;  // index of the scene's first tile
+    for (uint32_t s = 0; s < nbatch; ++s) {
+        const unsigned long long lo = offsets[s], cnt = offsets[s + 1] - lo;
+        const uint32_t nt = (uint32_t)((cnt + kSortTileRays - 1) / kSortTileRays);
+        for (uint32_t j = 0; j < nt; ++j) {
+            const unsigned long long at = (unsigned long long)j * kSortTileRays;
+            const unsigned long long c = cnt - at < kSortTileRays ? cnt - at : kSortTileRays;
+            tiles->push_back(SortTile{(uint32_t)(lo + at), (uint32_t)c, 256u * first + j, nt});
+            tile_scene->push_back(s);
+        }
+        first += nt;
+    }
+}
+
+// Scratch layout (32-bit words): two (key, index) arrays of n pairs, the
+// permutation (n words), the digit counts (256 per tile), the scan's block
+// totals.
+size_t coherence_sort_words(uint32_t n, uint32_t ntiles) {
+    const size_t hist = 256ull * ntiles;
+    const size_t totals = (hist + kScanBlock - 1) / kScanBlock;
+    return 5ull * n + hist + totals;
+}
+
+uint32_t coherence_sort_max_tiles() {
+    // the counts' scan takes up to 1024 x 8 block totals of 2048 values
+    return (uint32_t)(1024ull * kScanPer * kScanBlock / 256ull);
+}
+
+uint32_t coherence_sort_max_rays() {
+    return (uint32_t)((unsigned long long)coherence_sort_max_tiles() * kSortTileRays);
+}
+
 cudaError_t launch_coherence_sort(const BatchItem* items, const unsigned long long* offsets,
-                                  uint32_t nbatch, uint32_t n, uint32_t* scratch,
+                                  const SortTile* tiles, const uint32_t* tile_scene,
+                                  uint32_t ntiles, uint32_t n, uint32_t* scratch,
                                   uint32_t** perm, cudaStream_t stream) {
     *perm = scratch + 4ull * n;
-    if (n == 0) return cudaSuccess;
+    if (n == 0 || ntiles == 0) return cudaSuccess;
     uint2* kv[2] = {reinterpret_cast<uint2*>(scratch),
                     reinterpret_cast<uint2*>(scratch + 2ull * n)};
-    const uint32_t nblocks = (n + kSortTile - 1) / kSortTile;
     uint32_t* hist = *perm + n;
-    k_ray_keys<<<(n + 255) / 256, 256, 0, stream>>>(items, offsets, nbatch, n, kv[0]);
-    return sort_pairs(kv, n, *perm, hist, hist + 256ull * nblocks, offsets, nbatch, stream);
+    k_ray_keys<<<ntiles, kSortThreads, 0, stream>>>(items, offsets, tiles, tile_scene, kv[0]);
+    return sort_pairs(kv, n, tiles, ntiles, *perm, hist, hist + 256ull * ntiles, stream);
 }
 
 cudaError_t launch_coherence_sort_scene(const DevScene& sc, const float4* rays, uint32_t n,
@@ -365,10 +399,10 @@ cudaError_t launch_coherence_sort_scene(const DevScene& sc, const float4* rays, 
     if (n == 0) return cudaSuccess;
     uint2* kv[2] = {reinterpret_cast<uint2*>(scratch),
                     reinterpret_cast<uint2*>(scratch + 2ull * n)};
-    const uint32_t nblocks = (n + kSortTile - 1) / kSortTile;
+    const uint32_t ntiles = (n + kSortTileRays - 1) / kSortTileRays;
     uint32_t* hist = *perm + n;
     k_ray_keys_scene<<<(n + 255) / 256, 256, 0, stream>>>(sc, rays, n, kv[0]);
-    return sort_pairs(kv, n, *perm, hist, hist + 256ull * nblocks, nullptr, 1u, stream);
+    return sort_pairs(kv, n, nullptr, ntiles, *perm, hist, hist + 256ull * ntiles, stream);
 }
 
 }  // namespace vsr

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "vsr_device.cuh"
 
 namespace vsr {
@@ -127,6 +129,17 @@ struct BatchItem {
     float4* hits;
 };
 
+// A tile of the coherence sort (sort.cu): rays [start, start + count) of
+// the index space, sorted by one block; its digit counts go to
+// hist[hist_base + digit * stride].  A batch's tiles never straddle two
+// scenes and each scene's tiles are laid out digit-major among themselves,
+// so one scan of the counts sorts every scene's rays in place: scene s keeps
+// slots [offsets[s], offsets[s+1]).
+struct SortTile {
+    uint32_t start, count, hist_base, stride;
+};
+constexpr uint32_t kSortTileRays = 4096;
+
 struct BatchLaunch {
     const BatchItem* items;             // device [nbatch]
     const unsigned long long* offsets;  // device [nbatch + 1] ray prefix offsets
@@ -139,18 +152,28 @@ struct BatchLaunch {
     Watchdog wd;          // iteration and time budget of the persistent loop
     uint32_t grid = 0;    // non-zero: launch exactly this grid, with no set-up calls
     uint32_t* sort_scratch = nullptr;  // non-null: trace in coherence order (sort.cu)
+    const SortTile* sort_tiles = nullptr;  // device [sort_ntiles]
+    const uint32_t* tile_scene = nullptr;  // device [sort_ntiles]: scene of each tile
+    uint32_t sort_ntiles = 0;
     uint32_t lockstep = 0;             // 1: the warp runs the traversal in lock step
 };
 
-// Coherence order of a batch's rays (sort.cu): scratch words for n rays,
-// the largest n it handles, and the sort itself, which leaves in *perm
-// (inside scratch) the batch indices of the rays in sorted order.
-size_t coherence_sort_words(uint32_t n);
+// Coherence order (sort.cu).  coherence_sort_tiles cuts a batch's rays into
+// scene-aligned tiles (host); coherence_sort_words is the scratch, in 32-bit
+// words, for n rays in ntiles tiles; at most coherence_sort_max_tiles tiles
+// (uniform tiles: up to 2^28 rays in one scene).  The sorts leave in *perm
+// (inside scratch) the ray indices in sorted order.
+void coherence_sort_tiles(const unsigned long long* offsets, uint32_t nbatch,
+                          std::vector<SortTile>* tiles, std::vector<uint32_t>* tile_scene);
+size_t coherence_sort_words(uint32_t n, uint32_t ntiles);
+uint32_t coherence_sort_max_tiles();
 uint32_t coherence_sort_max_rays();
 cudaError_t launch_coherence_sort(const BatchItem* items, const unsigned long long* offsets,
-                                  uint32_t nbatch, uint32_t n, uint32_t* scratch,
+                                  const SortTile* tiles, const uint32_t* tile_scene,
+                                  uint32_t ntiles, uint32_t n, uint32_t* scratch,
                                   uint32_t** perm, cudaStream_t stream);
-// The same for the rays of one scene (vsr_trace with ray_order 1).
+// The same for the rays of one scene (vsr_trace with ray_order 1), in
+// uniform tiles.
 cudaError_t launch_coherence_sort_scene(const DevScene& sc, const float4* rays, uint32_t n,
                                         uint32_t* scratch, uint32_t** perm, cudaStream_t stream);
 
