@@ -229,13 +229,14 @@ def render_backward_model(n_rays: int, stats: np.ndarray, grad: np.ndarray, lit:
     Then every ray with a hit and a nonzero image gradient (`grad`) reads
     12 B of dL/dc, 12 B of vertex indices, 36 B of vertices, 4 B geom id,
     24 B texture coordinates, 24 B texture descriptor and 48 B of the four
-    bilinear texels' colours (160 B), and adds 9 vertex gradient atomics
-    (36 B); a lit one (`lit`: nonzero shading) adds 12 texel gradient
-    atomics (48 B)."""
+    bilinear texels' colours (160 B), and adds 9 scalar vertex gradient
+    atomics (36 B); a lit one (`lit`: nonzero shading) adds the RGB
+    gradient of 4 texels (48 B) as 4 16-byte vector atomics.  Returns
+    (bytes, atomic operations)."""
     g = int(np.count_nonzero(grad))
     gl = int(np.count_nonzero(grad & lit))
     nbytes = trace_bytes(n_rays, stats, 4, True) - 16 * n_rays + 160 * g + 36 * g + 48 * gl
-    return nbytes, 9 * g + 12 * gl
+    return nbytes, 9 * g + 4 * gl
 
 
 def ao_backward_model(hit: np.ndarray, textured: np.ndarray, visible: np.ndarray):
@@ -244,12 +245,13 @@ def ao_backward_model(hit: np.ndarray, textured: np.ndarray, visible: np.ndarray
     16-byte hit record; a hit reads 4 B geom id; a hit on the gradient's
     texture also reads 24 B texture coordinates, 24 B descriptor, 48 B of
     the bilinear texels' colours and 4 B occlusion, and, if not fully
-    occluded (`visible`), adds 12 texel gradient atomics (48 B)."""
+    occluded (`visible`), adds the RGB gradient of 4 texels (48 B) as 4
+    16-byte vector atomics.  Returns (bytes, atomic operations)."""
     n = hit.size
     h = int(np.count_nonzero(hit))
     t = int(np.count_nonzero(hit & textured))
     tv = int(np.count_nonzero(hit & textured & visible))
-    return 28 * n + 4 * h + 100 * t + 48 * tv, 12 * tv
+    return 28 * n + 4 * h + 100 * t + 48 * tv, 4 * tv
 
 
 def launch_config(p) -> str:
@@ -1022,6 +1024,8 @@ def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):
             "achieved": round(gbs, 1), "unit": "GB/s", "peak": rp["l2"],
             "frac": round(gbs / rp["l2"], 4), "atomics_per_launch": natomics,
             "atomics_per_s": round(natomics / (tb / 1e3), 1),
+            "atomics_note": "9 scalar vertex-gradient atomics per ray with a gradient, 4 "
+                            "16-byte vector texel-gradient atomics per lit one",
             "note": "one launch is 262,144 rays, about a quarter of a millisecond: launch-"
                     "latency scale; the scene (65 k triangles, 4 MB texture) is L2-resident"}
     return {"value": round(n / (t / 1e3) / 1e6, 2), "unit": "Mrays/s", "ms_per_step": round(t, 4),
@@ -1215,7 +1219,8 @@ def large_bench(V, torch, dev, flush, stream, steps):
         "launch_ms": round(tb, 4), "algorithmic_bytes_per_launch": nbytes,
         "achieved": round(gbs, 1), "unit": "GB/s", "peak": rp["l2"],
         "frac": round(gbs / rp["l2"], 4), "atomics_per_launch": natomics,
-        "atomics_per_s": round(natomics / (tb / 1e3), 1)}
+        "atomics_per_s": round(natomics / (tb / 1e3), 1),
+        "atomics_note": "4 16-byte vector texel-gradient atomics per visible textured pixel"}
     s.close()
     return out
 
@@ -1230,7 +1235,7 @@ def main():
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--leg", choices=["all", "large", "batch", "fwd_bwd", "trace", "ao",
-                                      "batch_profile"],
+                                      "ao_bwd", "batch_profile"],
                     default="all", help="run one auxiliary measurement alone (profiling)")
     ap.add_argument("--block", type=int, default=128,
                     help="--leg trace/ao: block size of the profiled launches")
@@ -1264,8 +1269,10 @@ def profile_leg(V, torch, dev, flush, stream, args):
     16 M-triangle workload's ambient-occlusion any-hit pass with procedural
     alpha (static dispatch), `steps` times; `batch_profile` -- a batch of the
     first `--scenes` scenes of the batching workload, alpha-texture any hit,
-    `steps` launches (the first runs plainly, later ones replay its graph).
-    Each launch is preceded by the 256 MiB L2 flush, as in the timed steps."""
+    `steps` launches (the first runs plainly, later ones replay its graph);
+    `ao_bwd` -- the 16 M-triangle ambient-occlusion render once, then its
+    texel adjoint (k_ao_backward) `steps` times.  Each launch is preceded by
+    the 256 MiB L2 flush, as in the timed steps."""
     from paper_1912_12786_gb300.inputs import scenes
     if args.leg == "batch_profile":
         # the first `scenes` scenes of the batching workload, alpha-texture
@@ -1296,6 +1303,27 @@ def profile_leg(V, torch, dev, flush, stream, args):
         sc, rays = scenes.large_incoherent()
         width = 0
     s = V.scene_from_inputs(sc, sc.bvh())
+    if args.leg == "ao_bwd":
+        # the ambient-occlusion render once, then its texel adjoint `steps` times
+        n = len(rays)
+        d = torch.from_numpy(rays).to(dev)
+        xi = torch.from_numpy(scenes.ao_random(n, 4)).to(dev)
+        shade = V.shade_params((0.0, 0.0, 1.0), grad_tex=0)
+        img = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        hits = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        occ = torch.empty(n, dtype=torch.float32, device=dev)
+        g_img = torch.ones((n, 3), dtype=torch.float32, device=dev)
+        tx = sc.textures[0]
+        g_tex = torch.zeros((tx.h, tx.w, 4), dtype=torch.float32, device=dev)
+        V.vsr_render_ao(s, d, V.intersector("proc_alpha"), 4, xi, 0.5, scenes.shadow_eps(sc),
+                        shade, img, hits, occ, stream)
+        for _ in range(args.steps):
+            flush.zero_()
+            V.vsr_render_ao_backward(s, hits, occ, shade, g_img, g_tex, stream)
+        torch.cuda.synchronize(dev)
+        out = {"config": "k_ao_backward", "device_error": V.vsr_get_device_error(s)}
+        s.close()
+        return out
     n = len(rays)
     d = torch.from_numpy(rays).to(dev)
     hits = torch.empty((n, 4), dtype=torch.float32, device=dev)
@@ -1342,7 +1370,7 @@ def run_leg(args):
     V.lib()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    if args.leg in ("trace", "ao", "batch_profile"):
+    if args.leg in ("trace", "ao", "ao_bwd", "batch_profile"):
         res = profile_leg(V, torch, dev, flush, stream, args)
     elif args.leg == "large":
         res = large_bench(V, torch, dev, flush, stream, args.steps)

@@ -169,12 +169,27 @@ __global__ void __launch_bounds__(256) k_render(DevScene sc, IsectParams ip, Sha
 //   solve:  (t, u, v) = M^-1 (o - v0) with M = [-d, e1, e2] gives
 //           dL/dv_k = -b_k y with y = M^-T (0, dL/du, dL/dv) and
 //           b = (1 - u - v, u, v).
+// Add (a, b, c) to the RGB of texel k in a gradient array of 4 floats per
+// texel: one 16-byte vector atomic when the array is 16-byte aligned (the
+// fourth float gets +0), else three scalar atomics.  `vec` is the same for
+// the whole launch.
+__device__ __forceinline__ void add_texel_grad(float* grad, uint32_t k, float a, float b, float c,
+                                               bool vec) {
+    if (vec) {
+        atomicAdd(reinterpret_cast<float4*>(grad) + k, make_float4(a, b, c, 0.0f));
+    } else {
+        atomicAdd(grad + 4ull * k, a);
+        atomicAdd(grad + 4ull * k + 1, b);
+        atomicAdd(grad + 4ull * k + 2, c);
+    }
+}
+
 template <class H>
 __global__ void __launch_bounds__(256) k_render_backward(
     DevScene sc, IsectParams ip, ShadeDev sh, const float* __restrict__ verts,
     const uint32_t* __restrict__ idx, const float4* __restrict__ rays, RayMap map,
     const float* __restrict__ dL_dimage, float* __restrict__ grad_verts,
-    float* __restrict__ grad_texels) {
+    float* __restrict__ grad_texels, bool vec_texels) {
     extern __shared__ uint32_t s_stack[];
     const unsigned long long gi = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= map.threads) return;
@@ -207,8 +222,8 @@ __global__ void __launch_bounds__(256) k_render_backward(
         const float w[4] = {(1.0f - b.fx) * (1.0f - b.fy), b.fx * (1.0f - b.fy),
                             (1.0f - b.fx) * b.fy, b.fx * b.fy};
         for (int c = 0; c < 4; ++c)
-            for (int ch = 0; ch < 3; ++ch)
-                atomicAdd(grad_texels + 4ull * b.k[c] + ch, g[ch] * f.s * w[c]);
+            add_texel_grad(grad_texels, b.k[c], g[0] * f.s * w[c], g[1] * f.s * w[c],
+                           g[2] * f.s * w[c], vec_texels);
     }
     // through the texture coordinate
     float dL_du = 0.0f, dL_dv = 0.0f;
@@ -331,7 +346,8 @@ __global__ void __launch_bounds__(256) k_ao_backward(DevScene sc, ShadeDev sh,
                                                      const float* __restrict__ occ,
                                                      unsigned long long n,
                                                      const float* __restrict__ dL_dimage,
-                                                     float* __restrict__ grad_texels) {
+                                                     float* __restrict__ grad_texels,
+                                                     bool vec_texels) {
     const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float g[3] = {VSR_LDG(dL_dimage + 3 * i), VSR_LDG(dL_dimage + 3 * i + 1),
@@ -354,8 +370,8 @@ __global__ void __launch_bounds__(256) k_ao_backward(DevScene sc, ShadeDev sh,
     const float w[4] = {(1.0f - b.fx) * (1.0f - b.fy), b.fx * (1.0f - b.fy),
                         (1.0f - b.fx) * b.fy, b.fx * b.fy};
     for (int c = 0; c < 4; ++c)
-        for (int ch = 0; ch < 3; ++ch)
-            atomicAdd(grad_texels + 4ull * b.k[c] + ch, g[ch] * vis * w[c]);
+        add_texel_grad(grad_texels, b.k[c], g[0] * vis * w[c], g[1] * vis * w[c],
+                       g[2] * vis * w[c], vec_texels);
 }
 
 // Bottom-up refit of the node boxes after a vertex update: one launch per
@@ -430,8 +446,9 @@ cudaError_t backward_one(const LaunchArgs& a, const ShadeDev& sh, const float* v
     cudaError_t e = prep_smem(k, smem);
     if (e != cudaSuccess) return e;
     const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
+    const bool vec = (reinterpret_cast<uintptr_t>(gt) & 15u) == 0;
     k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, sh, verts, idx, a.rays, a.map, g, gv,
-                                                     gt);
+                                                     gt, vec);
     return cudaGetLastError();
 }
 
@@ -520,8 +537,9 @@ cudaError_t launch_ao_shade(const DevScene& sc, const AoArgs& ao, unsigned long 
 
 cudaError_t launch_ao_backward(const DevScene& sc, const AoArgs& ao, unsigned long long n,
                                cudaStream_t stream) {
+    const bool vec = (reinterpret_cast<uintptr_t>(ao.grad_texels) & 15u) == 0;
     k_ao_backward<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(sc, ao.sh, ao.hits, ao.occ, n,
-                                                                   ao.g, ao.grad_texels);
+                                                                   ao.g, ao.grad_texels, vec);
     return cudaGetLastError();
 }
 

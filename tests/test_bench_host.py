@@ -38,12 +38,12 @@ def test_adjoint_models_by_hand():
     nbytes, natomics = bench.render_backward_model(3, st, grad, lit)
     trace = 3 * 48 + 32 * 6 + 48 * 1 + 4 * 1 + (24 + 4) * 1 - 16 * 3
     assert nbytes == trace + 2 * (160 + 36) + 48 * 1
-    assert natomics == 2 * 9 + 12
+    assert natomics == 2 * 9 + 4  # 9 scalar vertex atomics per ray, 4 vector texel atomics
     hit = np.array([True, True, True, False])
     tex = np.array([True, True, False, False])
     vis = np.array([True, False, True, True])
     nbytes, natomics = bench.ao_backward_model(hit, tex, vis)
-    assert nbytes == 4 * 28 + 3 * 4 + 2 * 100 + 1 * 48 and natomics == 12
+    assert nbytes == 4 * 28 + 3 * 4 + 2 * 100 + 1 * 48 and natomics == 4
 
 
 def _summary(tmp_path, kernel, digest, config, levels=(11, 22, 33)):

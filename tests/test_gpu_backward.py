@@ -46,11 +46,18 @@ def sphere():
     s.close()
 
 
-def _gpu_grads(d, g):
+def _gpu_grads(d, g, misaligned=False):
+    """Vertex and texel gradients of the render; with `misaligned` the texel
+    gradient array starts 4 bytes past a 16-byte boundary (scalar atomics)."""
     V, s = d["V"], d["s"]
     rays = torch.from_numpy(d["rays"]).cuda()
     gv = torch.zeros((d["sc"].verts.shape[0], 3), dtype=torch.float32, device="cuda")
-    gt = torch.zeros(d["sc"].textures[0].texels.shape, dtype=torch.float32, device="cuda")
+    shape = d["sc"].textures[0].texels.shape
+    if misaligned:
+        gt = torch.zeros(int(np.prod(shape)) + 1, dtype=torch.float32, device="cuda")[1:].view(shape)
+        assert gt.data_ptr() % 16 == 4
+    else:
+        gt = torch.zeros(shape, dtype=torch.float32, device="cuda")
     V.vsr_trace_backward(s, rays, V.intersector("alpha_tex", cutoff_f=0.3),
                          V.shade_params(d["light"]), torch.from_numpy(g.astype(np.float32)).cuda(),
                          gv, gt)
@@ -87,6 +94,10 @@ def test_backward_matches_fp64_reference(sphere):
     err = np.abs(gv - d["gv_ref"])[big] / np.abs(d["gv_ref"])[big]
     assert np.quantile(err, 0.99) < 1e-2
     assert np.all(gt[..., 3] == 0)
+    # scalar texel atomics (misaligned array) give the same sums
+    gv2, gt2 = _gpu_grads(d, d["g"], misaligned=True)
+    assert np.allclose(gt2, gt, rtol=1e-4, atol=1e-6 * np.abs(gt).max())
+    assert np.allclose(gv2, gv, rtol=1e-4, atol=1e-6 * np.abs(gv).max())
     assert d["V"].vsr_get_device_error(d["s"]) == 0, d["V"].vsr_last_error()
 
 
@@ -203,6 +214,15 @@ def test_ao_render_autograd_and_bad_hit_records(sphere):
     _, gt_ref = fa.vjp(sc.verts, tex0, g_ref)
     assert _rel(gt, gt_ref) < 1e-3
     assert np.all(gt[..., 3] == 0)
+    # a gradient array that is 4- but not 16-byte aligned takes scalar
+    # atomics instead of one vector atomic per texel: the same sums
+    buf = torch.zeros(tex.numel() + 1, dtype=torch.float32, device="cuda")
+    gmis = buf[1:].view(tex.shape)
+    assert gmis.data_ptr() % 16 == 4
+    V.vsr_render_ao_backward(s, hits, occ, shade, g, gmis)
+    torch.cuda.synchronize()
+    assert np.allclose(gmis.cpu().numpy(), gt, rtol=1e-4, atol=1e-6 * np.abs(gt).max())
+    assert buf[0].item() == 0.0
     assert V.vsr_get_device_error(s) == 0, V.vsr_last_error()
     # hit records out of range: skipped and flagged, never dereferenced
     k = int(np.flatnonzero(gh[:, 3] != O.NONE)[0])
