@@ -46,18 +46,22 @@ __device__ __forceinline__ uint32_t scene_of_warp(const unsigned long long* __re
 // the top of every iteration, one divergent traversal step closed by
 // __syncwarp, uniform exits, and the watchdog.
 template <int Q, class H, int K, bool LS>
-__global__ void __launch_bounds__(256) k_trace_batch(const BatchItem* __restrict__ items,
+__global__ void __launch_bounds__(256, 4) k_trace_batch(const BatchItem* __restrict__ items,
                                                      const unsigned long long* __restrict__ offsets,
                                                      uint32_t nbatch, IsectParams ip,
                                                      unsigned long long total,
                                                      unsigned long long* __restrict__ work,
                                                      uint32_t refill, Watchdog wd,
-                                                     const uint32_t* __restrict__ perm) {
+                                                     const uint32_t* __restrict__ perm,
+                                                     uint32_t stack_max) {
     extern __shared__ uint32_t s_stack[];
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t lt_mask = (1u << lane) - 1u;
     ShortStack<K> stk;
     stk.init(s_stack + threadIdx.x, blockDim.x);
+    // closest-hit speculation's entry distances (lock step), after the stack
+    float* tcol =
+        reinterpret_cast<float*>(s_stack + stack_words(stack_max, K) * blockDim.x) + threadIdx.x;
 
     bool has = false;
     bool exhausted = false;
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(256) k_trace_batch(const BatchItem* __restrict
         }
         if constexpr (LS) {
             if (warp_step<Q, H, false>(*scp, ip, r, h, best, st, has, ref, more, leaf, pend,
-                                       steps, stk)) {
+                                       steps, stk, tcol)) {
                 finish_miss(best);
                 hp[ri] = hit_record(best);
                 has = false;
@@ -155,7 +159,9 @@ namespace {
 template <int Q, class H, int K, bool LS>
 cudaError_t batch_one(const BatchLaunch& b, cudaStream_t stream, uint32_t* grid_out) {
     auto k = k_trace_batch<Q, H, K, LS>;
-    const size_t smem = (size_t)stack_words(b.stack_max, K) * b.block * sizeof(uint32_t);
+    const uint32_t words =
+        stack_words(b.stack_max, K) + (LS ? spec_words<Q, H, false, K>(b.stack_max) : 0u);
+    const size_t smem = (size_t)words * b.block * sizeof(uint32_t);
     uint32_t grid = b.grid;
     if (grid == 0) {
         if (smem > 48 * 1024) {
@@ -186,7 +192,7 @@ cudaError_t batch_one(const BatchLaunch& b, cudaStream_t stream, uint32_t* grid_
     cudaError_t e = cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
     k<<<grid, b.block, smem, stream>>>(b.items, b.offsets, b.nbatch, b.ip, b.total, b.work,
-                                       b.refill, b.wd, perm);
+                                       b.refill, b.wd, perm, b.stack_max);
     return cudaGetLastError();
 }
 

@@ -69,6 +69,9 @@ __global__ void __launch_bounds__(256) k_trace_ls(DevScene sc, IsectParams ip,
     Stats st;
     ShortStack<K> stk;
     stk.init(s_stack + threadIdx.x, blockDim.x);
+    // closest-hit speculation's entry distances, after the stack columns
+    float* tcol = reinterpret_cast<float*>(s_stack + stack_words(sc.stack_depth, K) * blockDim.x) +
+                  threadIdx.x;
     uint32_t ref = 0, steps = 0, leaf = 0;
     bool more = false, pend = false;
     auto finish = [&]() {
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__(256) k_trace_ls(DevScene sc, IsectParams ip,
     }
     while (__any_sync(kFullMask, busy)) {
         if (warp_step<Q, H, STATS>(sc, ip, r, h, best, st, busy, ref, more, leaf, pend, steps,
-                                   stk))
+                                   stk, tcol))
             finish();
     }
 }
@@ -142,6 +145,9 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
     const uint32_t lt_mask = (1u << lane) - 1u;
     ShortStack<K> stk;
     stk.init(s_stack + threadIdx.x, blockDim.x);
+    // closest-hit speculation's entry distances (lock step), after the stack
+    float* tcol = reinterpret_cast<float*>(s_stack + stack_words(sc.stack_depth, K) * blockDim.x) +
+                  threadIdx.x;
 
     bool has = false;        // lane holds a ray in flight
     bool exhausted = false;  // warp-uniform: the counter passed the last slot
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
         }
         if constexpr (LS) {
             if (warp_step<Q, H, STATS>(sc, ip, r, h, best, st, has, ref, more, leaf, pend, steps,
-                                       stk))
+                                       stk, tcol))
                 finish();
         } else {
             if (has) {
@@ -220,7 +226,9 @@ cudaError_t ensure_smem(Kern kernel, size_t smem) {
 
 template <int Q, class H, bool STATS, int K, bool LS>
 cudaError_t launch_shape(const LaunchArgs& a) {
-    const size_t smem = (size_t)stack_words(a.sc.stack_depth, K) * a.block * sizeof(uint32_t);
+    const uint32_t words = stack_words(a.sc.stack_depth, K) +
+                           (LS ? spec_words<Q, H, STATS, K>(a.sc.stack_depth) : 0u);
+    const size_t smem = (size_t)words * a.block * sizeof(uint32_t);
     if (!a.persistent) {
         auto k = LS ? k_trace_ls<Q, H, STATS, K> : k_trace<Q, H, STATS, K>;
         cudaError_t e = ensure_smem(k, smem);

@@ -202,6 +202,19 @@ __device__ __forceinline__ bool box_hit(const Ray& r, float4 lo, float4 hi, floa
     return tn <= tf;
 }
 
+// box_hit that also gives the entry distance tn: the box is hit with a
+// smaller far limit t' iff it was hit and tn <= t' (the exit side of the
+// comparison does not depend on the far limit).
+__device__ __forceinline__ bool box_hit_tn(const Ray& r, float4 lo, float4 hi, float tfar,
+                                           float& tn) {
+    const float t0x = __fmaf_rn(lo.x, r.ix, r.nox), t1x = __fmaf_rn(hi.x, r.ix, r.nox);
+    const float t0y = __fmaf_rn(lo.y, r.iy, r.noy), t1y = __fmaf_rn(hi.y, r.iy, r.noy);
+    const float t0z = __fmaf_rn(lo.z, r.iz, r.noz), t1z = __fmaf_rn(hi.z, r.iz, r.noz);
+    tn = fmax3(fminf(t0x, t1x), fminf(t0y, t1y), fmaxf(fminf(t0z, t1z), r.tmin));
+    const float tf = fmin3(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fminf(fmaxf(t0z, t1z), tfar));
+    return tn <= tf;
+}
+
 // intersect(ray, basic_triangle<3,float>): Moller-Trumbore with the fixed
 // rounding order.  Returns false when det == 0 (no t, u, v) and, as a shortcut
 // that changes no decision, when u alone already rules out a geometric hit
@@ -479,6 +492,7 @@ struct MultiBest {
 // traversal visits nodes in the same order for every K.
 template <int K>
 struct ShortStack {
+    static constexpr int kRegs = K;
     uint32_t top[K > 0 ? K : 1];
     uint32_t* col;
     uint32_t stride;
@@ -740,12 +754,18 @@ __device__ __forceinline__ bool test_prim(const DevScene& sc, const IsectParams&
     return Q == kAny;
 }
 
-// Speculative descent is exact for a query whose far limit never changes
-// (any hit: the ray's tmax) and an intersector whose box hooks observe
-// nothing (no counters), with no measurement counters.
-template <int Q, class H, bool STATS>
+// Where a lane that holds a leaf may keep descending (warp_step), for an
+// intersector whose box hooks observe nothing (no counters) and no
+// measurement counters.  Any hit: the far limit is the ray's tmax, which
+// never changes, so speculation needs no bookkeeping.  Closest hit: the far
+// limit shrinks when the held leaf improves the result, so speculation
+// records entry distances (in a shared-memory column beside the stack's,
+// for the shared-memory stack, K == 0) and undoes what the new limit culls.
+template <int Q, class H, bool STATS, int K>
 struct Speculate {
-    static constexpr bool value = Q == kAny && !H::kCounts && !STATS;
+    static constexpr bool any = Q == kAny && !H::kCounts && !STATS;
+    static constexpr bool closest = Q == kClosest && !H::kCounts && !STATS && K == 0;
+    static constexpr bool value = any || closest;
 };
 
 // A reached leaf is held for testing and the next node taken from the stack.
@@ -772,21 +792,46 @@ __device__ __forceinline__ void hold_leaf(uint32_t& ref, bool& more, uint32_t& l
 //
 // Per lane: `ref` is the next node to visit when `more`; `leaf` is a leaf
 // reached and not yet tested when `pend`.  The descent runs until every busy
-// lane holds a leaf or has run out of nodes.  When Speculate holds, a lane
+// lane holds a leaf or has run out of nodes.  Where Speculate holds, a lane
 // that already holds a leaf keeps descending toward its next one while other
 // lanes are still looking (the speculative traversal of Aila and Laine,
-// 2009): its box tests use the same far limit either way, so it visits the
-// same nodes and tests the same leaves in the same order as traverse_body,
-// only earlier.  Then each lane holding a leaf tests its primitives, one per
-// pass.  Returns true on busy lanes whose ray has finished (result in best).
+// 2009).  Then each lane holding a leaf tests its primitives, one per pass.
+//
+// Speculation leaves every result and the sequence of tested leaves as in
+// traverse_body:
+//   - any hit: the far limit is the ray's tmax, so a speculating lane visits
+//     the nodes the plain order visits after the held leaf, in that order;
+//   - closest hit: a speculating lane tests boxes against the far limit of
+//     before the held leaf (tf0), which the leaf may lower (to tf).  Each
+//     entry pushed while speculating keeps, in `tcol`, the largest entry
+//     distance on the way to it (`path`: the node it was pushed from and its
+//     ancestors up to the last entry popped, itself included).  The plain
+//     order would have reached that node iff this distance is <= tf: box
+//     tests along the way passed with tf0 >= tf, and a box hit with far
+//     limit tf0 is hit with tf iff its entry distance is <= tf.  So after
+//     the leaf test, entries above `sbase` (pushed while speculating) whose
+//     distance exceeds tf are dropped, order kept, and so is `ref` when its
+//     own path distance exceeds tf; what is left is what the plain order
+//     holds at the same point, and the leaves come in its order.
+// Returns true on busy lanes whose ray has finished (result in best).
 template <int Q, class H, bool STATS, class S>
 __device__ __forceinline__ bool warp_step(const DevScene& sc, const IsectParams& ip,
                                           const Ray& r, H& h, Best& best, Stats& st, bool busy,
                                           uint32_t& ref, bool& more, uint32_t& leaf, bool& pend,
-                                          uint32_t& steps, S& stk) {
-    constexpr bool kSpec = Speculate<Q, H, STATS>::value;
+                                          uint32_t& steps, S& stk, float* tcol) {
+    using Spec = Speculate<Q, H, STATS, S::kRegs>;
+    constexpr bool kSpec = Spec::value;
+    constexpr bool kTrack = Spec::closest;
+    const float kNegInf = -__int_as_float(0x7f800000);
     bool done = false;
+    uint32_t sbase = 0;           // kTrack: entries at or above were pushed speculating
+    float path = kNegInf;         // kTrack: largest entry distance on the way to ref
+    float tf0 = 0.0f;             // kTrack: the far limit speculation used
     if (busy) hold_leaf(ref, more, leaf, pend, stk);
+    if (kTrack && busy && pend) {
+        sbase = stk.n;
+        tf0 = h.far(best.t);
+    }
     for (;;) {  // while some lane is still looking for a leaf
         const bool seek = busy && !done && more && !pend;  // then ref is an inner node
         if (!__any_sync(kFullMask, seek)) break;
@@ -803,8 +848,9 @@ __device__ __forceinline__ bool warp_step(const DevScene& sc, const IsectParams&
                 h.box();
                 h.box();
                 if (STATS) st.boxes += 2;
-                const bool hl = box_hit(r, la, lb, tfar) && h.keep(ip, la, lb);
-                const bool hr = box_hit(r, ra, rb, tfar) && h.keep(ip, ra, rb);
+                float tnl = 0.0f, tnr = 0.0f;
+                const bool hl = box_hit_tn(r, la, lb, tfar, tnl) && h.keep(ip, la, lb);
+                const bool hr = box_hit_tn(r, ra, rb, tfar, tnr) && h.keep(ip, ra, rb);
                 const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(ra.w);
                 if (hl && hr) {
                     const bool neg = (r.negmask >> (ref & 3u)) & 1u;
@@ -813,19 +859,39 @@ __device__ __forceinline__ bool warp_step(const DevScene& sc, const IsectParams&
                         best.fail();
                         done = true;
                     } else {
+                        if (kTrack) tcol[stk.n * stk.stride] = fmaxf(path, neg ? tnl : tnr);
                         stk.push(neg ? rl : rr);
                         ref = neg ? rr : rl;
+                        if (kTrack) path = fmaxf(path, neg ? tnr : tnl);
                     }
                 } else if (hl) {
                     ref = rl;
+                    if (kTrack) path = fmaxf(path, tnl);
                 } else if (hr) {
                     ref = rr;
+                    if (kTrack) path = fmaxf(path, tnr);
                 } else if (stk.n) {
                     ref = stk.pop();
+                    if (kTrack) {
+                        if (stk.n >= sbase) {
+                            path = tcol[stk.n * stk.stride];
+                        } else {  // an entry of the plain order
+                            sbase = stk.n;
+                            path = kNegInf;
+                        }
+                    }
                 } else {
                     more = false;
                 }
-                if (!done) hold_leaf(ref, more, leaf, pend, stk);
+                if (!done) {
+                    const bool held = pend;
+                    hold_leaf(ref, more, leaf, pend, stk);
+                    if (kTrack && pend && !held) {  // speculation starts here
+                        sbase = stk.n;
+                        path = kNegInf;
+                        tf0 = h.far(best.t);
+                    }
+                }
             }
         }
     }
@@ -849,11 +915,39 @@ __device__ __forceinline__ bool warp_step(const DevScene& sc, const IsectParams&
         }
     }
     if (busy && !done) {
+        if (kTrack && pend) {
+            const float tf = h.far(best.t);
+            if (tf < tf0) {  // the leaf lowered the far limit: drop what it culls
+                uint32_t j = sbase;
+                for (uint32_t i = sbase; i < stk.n; ++i) {
+                    const float tn = tcol[i * stk.stride];
+                    if (tn <= tf) {
+                        stk.col[j * stk.stride] = stk.col[i * stk.stride];
+                        tcol[j * stk.stride] = tn;
+                        ++j;
+                    }
+                }
+                stk.n = j;
+                if (more && path > tf) {
+                    if (stk.n)
+                        ref = stk.pop();
+                    else
+                        more = false;
+                }
+            }
+        }
         pend = false;
         hold_leaf(ref, more, leaf, pend, stk);
         if (!pend && !more) done = true;
     }
     return busy && done;
+}
+
+// Shared-memory words per thread of the entry-distance column that
+// closest-hit speculation keeps beside the stack (0 where it does not run).
+template <int Q, class H, bool STATS, int K>
+__host__ __device__ constexpr uint32_t spec_words(uint32_t depth) {
+    return Speculate<Q, H, STATS, K>::closest ? depth : 0u;
 }
 
 // Budget of a persistent loop: outer iterations per warp (0: no limit) and
