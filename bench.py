@@ -865,22 +865,29 @@ def path_bench(V, s, sc, d_rays, n, flush, stream, torch, steps, bounces=3):
     seg = torch.empty(n, dtype=torch.int32, device=d_rays.device)
     alpha = V.intersector("alpha_tex")
     pp = V.path_params(bounces, scenes.shadow_eps(sc), (0.7, 0.8, 1.0), (0.8, 0.75, 0.6))
-    p = default_params(V)
-    ms = []
-    for k in range(max(3, steps // 2) + 2):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        V.vsr_path_trace(s, d_rays, alpha, pp, dirs, rad, seg, p, stream)
-        e1.record(stream)
-        e1.synchronize()
-        if k >= 2:
-            ms.append(e0.elapsed_time(e1))
-    t = statistics.median(ms)
+    def frame_ms(p):
+        ms = []
+        for k in range(max(3, steps // 2) + 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            V.vsr_path_trace(s, d_rays, alpha, pp, dirs, rad, seg, p, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 2:
+                ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    t = frame_ms(default_params(V))
     segments = int(seg.sum().item())
+    # the segments in lock step, persistent warps on the same pixel tiles
+    tl = frame_ms(V.trace_params(block_size=128, image_width=FRAME_W, persistent=1,
+                                 refill_threshold=16, lockstep=1))
     return {"workload": f"{n} paths, {bounces} diffuse bounces, alpha texture, forest",
             "ms_per_frame": round(t, 4), "Mpaths_s": round(n / (t / 1e3) / 1e6, 1),
             "segments": segments, "Msegments_s": round(segments / (t / 1e3) / 1e6, 1),
+            "lockstep_persistent_ms_per_frame": round(tl, 4),
+            "lockstep_persistent_Mpaths_s": round(n / (tl / 1e3) / 1e6, 1),
             "gpu_launches_per_frame": 1 + 2 * (bounces + 1)}
 
 

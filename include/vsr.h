@@ -357,8 +357,10 @@ vsr_status vsr_trace_multi(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
  *             3 * (i * bounces + k), cosine-distributed for a diffuse surface
  *   radiance  device float32 [n * 3], written
  *   segments  device uint32 [n] or NULL: closest-hit queries path i made
- *   params    one ray per thread (persistent 0); image_width applies to every
- *             segment's launch (bounce segments stay at their pixel)
+ *   params    every segment's launch (image_width keeps bounce segments at
+ *             their pixel); persistent launches and lock step apply to each
+ *             segment depth (finished paths are inactive rays, claimed and
+ *             dropped at once); ray_order 0
  * One closest-hit launch per segment depth plus one shading launch, on
  * `stream`; scratch (n * 60 bytes) comes from the stream-ordered allocator.
  * Errors as vsr_trace.

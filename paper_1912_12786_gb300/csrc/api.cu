@@ -1990,7 +1990,6 @@ extern "C" vsr_status vsr_path_trace(vsr_scene* s, const vsr_ray* rays, uint64_t
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(pp->sky[c]) || !std::isfinite(pp->untextured[c]))
             return fail(VSR_ERR_ARG, "non-finite sky or albedo");
-    if (p && p->persistent) return fail(VSR_ERR_ARG, "path tracing uses one ray per thread");
     LaunchArgs a;
     // n == 0 keeps prepare_launch's ray and hit checks out of the way
     vsr_status st = prepare_launch(s, rays, 0, is, VSR_CLOSEST, nullptr, p, a);

@@ -73,6 +73,14 @@ def test_tiles_and_dynamic_dispatch_agree(V, small):
     c, sc_ = _gpu(V, s, rays, "alpha_tex", 3, dirs, dispatch="dynamic")
     assert np.array_equal(a.view(np.uint32), b.view(np.uint32)) and np.array_equal(sa, sb)
     assert np.array_equal(a.view(np.uint32), c.view(np.uint32)) and np.array_equal(sa, sc_)
+    # every segment in lock step (closest hit with speculative descent), one
+    # ray per thread and persistent
+    for p in (V.trace_params(lockstep=1),
+              V.trace_params(lockstep=1, persistent=1, refill_threshold=16, watchdog_ms=10_000),
+              V.trace_params(persistent=1, refill_threshold=8, image_width=256,
+                             watchdog_ms=10_000)):
+        d, sd = _gpu(V, s, rays, "alpha_tex", 3, dirs, p)
+        assert np.array_equal(a.view(np.uint32), d.view(np.uint32)) and np.array_equal(sa, sd)
 
 
 def test_ragged_sizes(V, small):
@@ -94,9 +102,9 @@ def test_argument_checks(V, small):
     isect = V.intersector("default")
     with pytest.raises(V.VsrError, match="bounces"):
         V.vsr_path_trace(s, d, isect, V.path_params(65), dirs, rad)
-    with pytest.raises(V.VsrError, match="one ray per thread"):
+    with pytest.raises(V.VsrError, match="ray_order"):
         V.vsr_path_trace(s, d, isect, V.path_params(3), dirs, rad, None,
-                         V.trace_params(persistent=1))
+                         V.trace_params(ray_order=1))
     with pytest.raises(V.VsrError, match="non-finite"):
         V.vsr_path_trace(s, d, isect, V.path_params(3, sky=(1.0, float("inf"), 1.0)), dirs, rad)
     with pytest.raises(V.VsrError, match="dirs"):
