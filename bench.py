@@ -380,14 +380,16 @@ def barrier(world):
 # CPU oracle leg
 
 
-def oracle_sample(sc, rays, blob, stride: int, min_seconds: float = 0.0, max_repeats: int = 64):
+def oracle_sample(sc, rays, blob, stride: int, min_seconds: float = 0.0, max_repeats: int = 64,
+                  threads=None):
     """Time the oracle on every `stride`-th pixel -- primary closest-hit and
-    shadow any-hit with the alpha-texture intersector, all host cores --
-    repeating the sample until at least `min_seconds` of traversal time."""
+    shadow any-hit with the alpha-texture intersector, on `threads` host
+    threads (default: all cores) -- repeating the sample until at least
+    `min_seconds` of traversal time."""
     from oracle import oracle as O
     from paper_1912_12786_gb300.inputs import scenes
     sel = rays[::stride]
-    cores = len(os.sched_getaffinity(0))
+    cores = threads or len(os.sched_getaffinity(0))
     light, eps = scenes.light_dir_f32(), scenes.shadow_eps(sc)
     elapsed, traced, reps = 0.0, 0, 0
     while reps < max_repeats and (reps == 0 or elapsed < min_seconds):
@@ -719,11 +721,18 @@ def run_ours(args):
     if world == 1 and not args.no_cpu:
         mr, cores, nsel, el, reps = oracle_sample(sc, rays, blob, args.ref_stride,
                                                   min_seconds=10.0)
+        # one thread on a smaller sample (every 16th pixel), about 2 s
+        m1, _, nsel1, el1, reps1 = oracle_sample(sc, rays, blob, 16 * args.ref_stride,
+                                                 min_seconds=2.0, threads=1)
         out["cpu_baseline"] = {"value": round(mr, 4), "unit": "Mrays/s", "cores": cores,
                                "kind": "oracle",
                                "sample": f"every {args.ref_stride}th pixel of the frame ({nsel} "
                                          f"primary + {nsel} shadow rays) x {reps} repeats, "
-                                         f"{el:.1f} s of traversal"}
+                                         f"{el:.1f} s of traversal",
+                               "single_thread_value": round(m1, 4),
+                               "single_thread_sample": f"every {16 * args.ref_stride}th pixel "
+                                                       f"({nsel1} + {nsel1} rays) x {reps1} "
+                                                       f"repeats, {el1:.1f} s"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     s.close()
