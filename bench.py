@@ -239,6 +239,21 @@ def render_backward_model(n_rays: int, stats: np.ndarray, grad: np.ndarray, lit:
     return nbytes, 9 * g + 4 * gl
 
 
+def render_backward_hits_model(hit: np.ndarray, grad: np.ndarray, lit: np.ndarray) -> int:
+    """Algorithmic bytes of one k_render_backward_hits launch (no re-trace):
+    every ray reads its 16-byte hit record; a hit reads its ray direction
+    (16 B) and its 12 B of dL/dc; a hit with a nonzero gradient (`grad`)
+    then reads 148 B more of the 160 B the re-tracing model counts
+    (indices, vertices, geom id, texture coordinates and descriptor, texel
+    colours) and adds 36 B of vertex atomics, a lit one 48 B of texel
+    atomics, as in render_backward_model."""
+    n = hit.size
+    h = int(np.count_nonzero(hit))
+    g = int(np.count_nonzero(grad))
+    gl = int(np.count_nonzero(grad & lit))
+    return 16 * n + 16 * h + 12 * h + 148 * g + 36 * g + 48 * gl
+
+
 def ao_backward_model(hit: np.ndarray, textured: np.ndarray, visible: np.ndarray):
     """Algorithmic bytes and atomics of one k_ao_backward launch (image
     gradient nonzero everywhere): every pixel reads 12 B of dL/dc and its
@@ -959,8 +974,10 @@ def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):
     """Forward render + adjoint on the displaced icosphere (64,980 triangles,
     RGBA32F 512^2 albedo with alpha cutout 0.3, 512x512 rays, alpha-texture
     closest hit, diffuse shading, L2 loss to an image rendered from perturbed
-    vertices and texels).  One step: render, loss gradient, zeroed gradient
-    buffers, backward (re-trace + adjoint).  Mrays/s counts primary rays."""
+    vertices and texels).  One step: render (keeping its hit records), loss
+    gradient, zeroed gradient buffers, the adjoint from the hit records; the
+    same step with the re-tracing adjoint is timed too.  Mrays/s counts
+    primary rays."""
     from paper_1912_12786_gb300.inputs import scenes
     sc, rays, tv, tt = scenes.displaced_icosphere()
     blob = sc.bvh()
@@ -979,34 +996,46 @@ def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):
     gv = torch.zeros((sc.verts.shape[0], 3), dtype=torch.float32, device=dev)
     gt = torch.zeros(sc.textures[0].texels.shape, dtype=torch.float32, device=dev)
 
-    def step(ev=None):
+    saved = torch.empty((n, 4), dtype=torch.float32, device=dev)
+
+    def step(ev=None, retrace=False):
+        # render (keeping the hit records), loss gradient, adjoint from the
+        # records; with `retrace` the adjoint traces every ray again instead
         if ev is not None:
             ev[0].record(stream)
-        V.vsr_render(s, d_rays, isect, shade, img, None, p, stream)
+        V.vsr_render(s, d_rays, isect, shade, img, None if retrace else saved, p, stream)
         if ev is not None:
             ev[1].record(stream)
         g = 2.0 * (img - target)
         gv.zero_()
         gt.zero_()
-        V.vsr_trace_backward(s, d_rays, isect, shade, g, gv, gt, p, stream)
+        if retrace:
+            V.vsr_trace_backward(s, d_rays, isect, shade, g, gv, gt, p, stream)
+        else:
+            V.vsr_render_backward_hits(s, d_rays, saved, shade, g, gv, gt, stream)
         if ev is not None:
             ev[2].record(stream)
 
-    for _ in range(warmup):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize(dev)
-    ms, fwd, bwd = [], [], []
-    for _ in range(steps):
-        flush.zero_()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        step(ev)
-        ev[2].synchronize()
-        ms.append(ev[0].elapsed_time(ev[2]))
-        fwd.append(ev[0].elapsed_time(ev[1]))
-        bwd.append(ev[1].elapsed_time(ev[2]))
-    # the adjoint kernel alone: vsr_trace_backward between events (gradient
-    # buffers zeroed outside them), with exact counts for its byte model
+    def run(retrace):
+        for _ in range(warmup):
+            flush.zero_()
+            step(retrace=retrace)
+        torch.cuda.synchronize(dev)
+        ms, fwd, bwd = [], [], []
+        for _ in range(steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            step(ev, retrace)
+            ev[2].synchronize()
+            ms.append(ev[0].elapsed_time(ev[2]))
+            fwd.append(ev[0].elapsed_time(ev[1]))
+            bwd.append(ev[1].elapsed_time(ev[2]))
+        return ms, fwd, bwd
+
+    ms_rt, _, bwd_rt = run(True)
+    ms, fwd, bwd = run(False)
+    # each adjoint kernel alone between events (gradient buffers zeroed outside
+    # them), with exact counts for the byte models
     hits = torch.empty((n, 4), dtype=torch.float32, device=dev)
     V.vsr_render(s, d_rays, isect, shade, img, hits, p, stream)
     g = 2.0 * (img - target)
@@ -1014,38 +1043,53 @@ def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):
     tmp = torch.empty((n, 4), dtype=torch.float32, device=dev)
     V.vsr_trace_stats(s, d_rays, isect, "closest", tmp, stt, stream)
     torch.cuda.synchronize(dev)
-    bk = []
-    for k in range(steps + 2):
-        gv.zero_()
-        gt.zero_()
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        V.vsr_trace_backward(s, d_rays, isect, shade, g, gv, gt, p, stream)
-        e1.record(stream)
-        e1.synchronize()
-        if k >= 2:
-            bk.append(e0.elapsed_time(e1))
-    tb = statistics.median(bk)
+
+    def adjoint_ms(fn):
+        bk = []
+        for k in range(steps + 2):
+            gv.zero_()
+            gt.zero_()
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 2:
+                bk.append(e0.elapsed_time(e1))
+        return statistics.median(bk)
+
+    tb_rt = adjoint_ms(lambda: V.vsr_trace_backward(s, d_rays, isect, shade, g, gv, gt, p, stream))
+    tb = adjoint_ms(lambda: V.vsr_render_backward_hits(s, d_rays, hits, shade, g, gv, gt, stream))
     prim = hits[:, 3].contiguous().view(torch.int32).cpu().numpy().view(np.uint32)
-    grad = (prim != 0xFFFFFFFF) & np.any(g.cpu().numpy() != 0.0, axis=1)
+    hit = prim != 0xFFFFFFFF
+    grad = hit & np.any(g.cpu().numpy() != 0.0, axis=1)
     lit = np.any(img.cpu().numpy() != 0.0, axis=1)
-    nbytes, natomics = render_backward_model(n, stt.cpu().numpy().view(np.uint32), grad, lit)
+    nbytes_rt, natomics = render_backward_model(n, stt.cpu().numpy().view(np.uint32), grad, lit)
+    nbytes = render_backward_hits_model(hit, grad, lit)
     rp = read_peaks(V, torch, dev)
-    gbs = nbytes / (tb / 1e3) / 1e9
     s.close()
     t = statistics.median(ms)
-    roof = {"kernel": "k_render_backward (re-trace + adjoint)", "bound": "l2",
-            "launch_ms": round(tb, 4), "algorithmic_bytes_per_launch": nbytes,
-            "achieved": round(gbs, 1), "unit": "GB/s", "peak": rp["l2"],
-            "frac": round(gbs / rp["l2"], 4), "atomics_per_launch": natomics,
-            "atomics_per_s": round(natomics / (tb / 1e3), 1),
-            "atomics_note": "9 scalar vertex-gradient atomics per ray with a gradient, 4 "
-                            "16-byte vector texel-gradient atomics per lit one",
-            "note": "one launch is 262,144 rays, about a quarter of a millisecond: launch-"
-                    "latency scale; the scene (65 k triangles, 4 MB texture) is L2-resident"}
+    note = ("9 scalar vertex-gradient atomics per ray with a gradient, 4 16-byte vector "
+            "texel-gradient atomics per lit one")
+
+    def roofline(kernel, ms_, nb):
+        gbs = nb / (ms_ / 1e3) / 1e9
+        return {"kernel": kernel, "bound": "l2", "launch_ms": round(ms_, 4),
+                "algorithmic_bytes_per_launch": nb, "achieved": round(gbs, 1), "unit": "GB/s",
+                "peak": rp["l2"], "frac": round(gbs / rp["l2"], 4),
+                "atomics_per_launch": natomics,
+                "atomics_per_s": round(natomics / (ms_ / 1e3), 1), "atomics_note": note}
+
+    roof = roofline("k_render_backward_hits (adjoint from the forward's hit records)", tb, nbytes)
+    roof["note"] = ("one launch is 262,144 rays, tens of microseconds: launch-latency scale; "
+                    "the scene (65 k triangles, 4 MB texture) is L2-resident")
+    roof_rt = roofline("k_render_backward (re-trace + adjoint)", tb_rt, nbytes_rt)
     return {"value": round(n / (t / 1e3) / 1e6, 2), "unit": "Mrays/s", "ms_per_step": round(t, 4),
-            "roofline": roof,
+            "roofline": roof, "roofline_retrace": roof_rt,
+            "retrace_value": round(n / (statistics.median(ms_rt) / 1e3) / 1e6, 2),
+            "retrace_ms_per_step": round(statistics.median(ms_rt), 4),
+            "retrace_backward_ms": round(statistics.median(bwd_rt), 4),
             "forward_ms": round(statistics.median(fwd), 4),
             "backward_ms": round(statistics.median(bwd), 4),
             "workload": "displaced icosphere, 64,980 triangles, 512x512 rays, alpha-texture "

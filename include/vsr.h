@@ -587,6 +587,24 @@ vsr_status vsr_trace_backward(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
                               const vsr_trace_params* params, vsr_stream stream);
 
 /*
+ * The same adjoint from the hit records the forward render wrote
+ * (vsr_render's `hits`): no traversal, one thread per ray.  The records are
+ * the closest hits a re-trace finds, so the gradients are vsr_trace_backward's
+ * (up to the order of the atomics).
+ *   rays        device vsr_ray [n], the forward's rays (their directions
+ *               enter the solve and the face orientation)
+ *   hits        device vsr_hit [n] from vsr_render on the same rays, scene
+ *               and intersector; a record whose primitive is out of range is
+ *               skipped and sets device error bit VSR_DEVERR_HIT
+ *   dL_dimage, grad_verts, grad_texels as vsr_trace_backward
+ * The scene must be unchanged since the forward render.  Errors as vsr_trace.
+ */
+vsr_status vsr_render_backward_hits(vsr_scene* scene, const vsr_ray* rays, const vsr_hit* hits,
+                                    uint64_t n, const vsr_shade_params* shade,
+                                    const float* dL_dimage, float* grad_verts,
+                                    float* grad_texels, vsr_stream stream);
+
+/*
  * Ambient-occlusion shading on the closest-hit query:
  *   c = albedo_rgb(uv) * (1 - occluded / spp)      (background for a miss)
  * where the spp occlusion rays of pixel i are built exactly as

@@ -1076,6 +1076,42 @@ extern "C" vsr_status vsr_trace_backward(vsr_scene* s, const vsr_ray* rays, uint
     return VSR_OK;
 }
 
+extern "C" vsr_status vsr_render_backward_hits(vsr_scene* s, const vsr_ray* rays,
+                                               const vsr_hit* hits, uint64_t n,
+                                               const vsr_shade_params* sh,
+                                               const float* dL_dimage, float* grad_verts,
+                                               float* grad_texels, vsr_stream stream) {
+    g_err.clear();
+    if (!s) return fail(VSR_ERR_ARG, "scene is null");
+    if (!s->has_bvh) return fail(VSR_ERR_STATE, "no BVH loaded into the scene");
+    ShadeDev shd;
+    vsr_status st = prepare_shade(s, sh, shd);
+    if (st != VSR_OK) return st;
+    if (grad_texels) {
+        if (shd.grad_tex == VSR_NO_TEXTURE || s->h_tex[shd.grad_tex].fmt != VSR_TEX_RGBA32F)
+            return fail(VSR_ERR_ARG, "texel gradients need an RGBA32F grad_tex");
+    }
+    if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 256ull)
+        return fail(VSR_ERR_ARG, "too many pixels for one launch");
+    if (n == 0) return VSR_OK;
+    st = check_dev(rays, s->device, "rays", 16, n * sizeof(vsr_ray));
+    if (st == VSR_OK) st = check_dev(hits, s->device, "hits", 16, n * sizeof(vsr_hit));
+    if (st == VSR_OK) st = check_dev(dL_dimage, s->device, "dL_dimage", 4, n * 12);
+    if (st == VSR_OK) st = check_dev(grad_verts, s->device, "grad_verts", 4, 12ull * s->nverts);
+    if (st == VSR_OK && grad_texels) {
+        const TexDesc& t = s->h_tex[shd.grad_tex];
+        st = check_dev(grad_texels, s->device, "grad_texels", 4, 16ull * t.w * t.h);
+    }
+    if (st != VSR_OK) return st;
+    DeviceGuard g(s->device);
+    cudaError_t e = launch_render_backward_hits(
+        s->dev, shd, s->d_verts, s->d_idx, reinterpret_cast<const float4*>(rays),
+        reinterpret_cast<const float4*>(hits), n, dL_dimage, grad_verts, grad_texels,
+        reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+    return VSR_OK;
+}
+
 namespace {
 
 vsr_status prepare_ao(vsr_scene* s, uint64_t n, uint32_t spp, const float* xi, float tmax,

@@ -160,15 +160,6 @@ __global__ void __launch_bounds__(256) k_render(DevScene sc, IsectParams ip, Sha
     image[3 * i + 2] = c[2];
 }
 
-// Adjoint of the shading at fixed visibility.  g = dL/dc for the pixel.
-//   texels: dc/dT(corner) = s * w(corner)                      (rgb channels)
-//   uv:     dc/duv.x = s * W * [(1-fy)(T01-T00) + fy(T11-T10)]   (and y)
-//   (u, v): duv/du = tc1 - tc0, duv/dv = tc2 - tc0
-//   normal: dc/dn_f = albedo * L where n_f . L > 0, n_f = flip * m/|m|,
-//           dL/dm = (dL/dn - n (n . dL/dn)) / |m|, m = e1 x e2
-//   solve:  (t, u, v) = M^-1 (o - v0) with M = [-d, e1, e2] gives
-//           dL/dv_k = -b_k y with y = M^-T (0, dL/du, dL/dv) and
-//           b = (1 - u - v, u, v).
 // Add (a, b, c) to the RGB of texel k in a gradient array of 4 floats per
 // texel: one 16-byte vector atomic when the array is 16-byte aligned (the
 // fourth float gets +0), else three scalar atomics.  `vec` is the same for
@@ -184,38 +175,38 @@ __device__ __forceinline__ void add_texel_grad(float* grad, uint32_t k, float a,
     }
 }
 
-template <class H>
-__global__ void __launch_bounds__(256) k_render_backward(
-    DevScene sc, IsectParams ip, ShadeDev sh, const float* __restrict__ verts,
-    const uint32_t* __restrict__ idx, const float4* __restrict__ rays, RayMap map,
-    const float* __restrict__ dL_dimage, float* __restrict__ grad_verts,
-    float* __restrict__ grad_texels, bool vec_texels) {
-    extern __shared__ uint32_t s_stack[];
-    const unsigned long long gi = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= map.threads) return;
-    const unsigned long long i = ray_of_thread(gi, map);
-    if (i >= map.n) return;
-    const float4 ra = VSR_LDG(rays + 2 * i), rb = VSR_LDG(rays + 2 * i + 1);
-    const Ray r = make_ray(ra, rb);
-    H h;
-    Best best;
-    Stats st;
-    ShortStack<0> stk;
-    stk.init(s_stack + threadIdx.x, blockDim.x);
-    traverse<kClosest, H, false>(sc, ip, r, h, best, st, stk);
-    if (best.prim == kMiss) return;
+// Adjoint of the shading at fixed visibility.  g = dL/dc for the pixel.
+//   texels: dc/dT(corner) = s * w(corner)                      (rgb channels)
+//   uv:     dc/duv.x = s * W * [(1-fy)(T01-T00) + fy(T11-T10)]   (and y)
+//   (u, v): duv/du = tc1 - tc0, duv/dv = tc2 - tc0
+//   normal: dc/dn_f = albedo * L where n_f . L > 0, n_f = flip * m/|m|,
+//           dL/dm = (dL/dn - n (n . dL/dn)) / |m|, m = e1 x e2
+//   solve:  (t, u, v) = M^-1 (o - v0) with M = [-d, e1, e2] gives
+//           dL/dv_k = -b_k y with y = M^-T (0, dL/du, dL/dv) and
+//           b = (1 - u - v, u, v).
+// shade_adjoint: that adjoint for pixel i, from its hit (prim, bu, bv: the
+// closest hit's primitive and barycentrics) and ray direction d; scatters
+// into grad_verts and (if not null) grad_texels.
+__device__ __forceinline__ void shade_adjoint(const DevScene& sc, const ShadeDev& sh,
+                                              const float* __restrict__ verts,
+                                              const uint32_t* __restrict__ idx,
+                                              unsigned long long i, V3 d, uint32_t prim,
+                                              float bu, float bv,
+                                              const float* __restrict__ dL_dimage,
+                                              float* __restrict__ grad_verts,
+                                              float* __restrict__ grad_texels,
+                                              bool vec_texels) {
     const float g[3] = {VSR_LDG(dL_dimage + 3 * i), VSR_LDG(dL_dimage + 3 * i + 1),
                         VSR_LDG(dL_dimage + 3 * i + 2)};
     if (g[0] == 0.0f && g[1] == 0.0f && g[2] == 0.0f) return;
-    const V3 d = v3(rb.x, rb.y, rb.z);
     const V3 L = v3(sh.light[0], sh.light[1], sh.light[2]);
     Surface f;
-    surface(verts, idx, best.prim, d, L, f);
-    const uint32_t geom = VSR_LDG(sc.geom + best.prim);
-    const float2 c0 = VSR_LDG(sc.uvs + 3ull * best.prim), c1 = VSR_LDG(sc.uvs + 3ull * best.prim + 1),
-                 c2 = VSR_LDG(sc.uvs + 3ull * best.prim + 2);
+    surface(verts, idx, prim, d, L, f);
+    const uint32_t geom = VSR_LDG(sc.geom + prim);
+    const float2 c0 = VSR_LDG(sc.uvs + 3ull * prim), c1 = VSR_LDG(sc.uvs + 3ull * prim + 1),
+                 c2 = VSR_LDG(sc.uvs + 3ull * prim + 2);
     Bilinear b;
-    albedo(sc, geom, lerp_uv(sc.uvs, best.prim, best.u, best.v), b);
+    albedo(sc, geom, lerp_uv(sc.uvs, prim, bu, bv), b);
 
     // texel gradients
     if (grad_texels && b.rgba32f && geom == sh.grad_tex && f.s > 0.0f) {
@@ -257,10 +248,10 @@ __global__ void __launch_bounds__(256) k_render_backward(
     const float det = dot(nd, f.m);
     if (det != 0.0f && (dL_du != 0.0f || dL_dv != 0.0f))
         y = (1.0f / det) * (dL_du * cross(f.e2, nd) + dL_dv * cross(nd, f.e1));
-    const float w0 = 1.0f - best.u - best.v;
+    const float w0 = 1.0f - bu - bv;
     const V3 gv0 = (-w0) * y - dL_de1 - dL_de2;
-    const V3 gv1 = (-best.u) * y + dL_de1;
-    const V3 gv2 = (-best.v) * y + dL_de2;
+    const V3 gv1 = (-bu) * y + dL_de1;
+    const V3 gv2 = (-bv) * y + dL_de2;
     const V3 gk[3] = {gv0, gv1, gv2};
     for (int k = 0; k < 3; ++k) {
         float* p = grad_verts + 3ull * f.vi[k];
@@ -268,6 +259,56 @@ __global__ void __launch_bounds__(256) k_render_backward(
         atomicAdd(p + 1, gk[k].y);
         atomicAdd(p + 2, gk[k].z);
     }
+}
+
+// The adjoint with the ray traced again (vsr_trace_backward: no forward state
+// is kept).
+template <class H>
+__global__ void __launch_bounds__(256) k_render_backward(
+    DevScene sc, IsectParams ip, ShadeDev sh, const float* __restrict__ verts,
+    const uint32_t* __restrict__ idx, const float4* __restrict__ rays, RayMap map,
+    const float* __restrict__ dL_dimage, float* __restrict__ grad_verts,
+    float* __restrict__ grad_texels, bool vec_texels) {
+    extern __shared__ uint32_t s_stack[];
+    const unsigned long long gi = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= map.threads) return;
+    const unsigned long long i = ray_of_thread(gi, map);
+    if (i >= map.n) return;
+    const float4 ra = VSR_LDG(rays + 2 * i), rb = VSR_LDG(rays + 2 * i + 1);
+    const Ray r = make_ray(ra, rb);
+    H h;
+    Best best;
+    Stats st;
+    ShortStack<0> stk;
+    stk.init(s_stack + threadIdx.x, blockDim.x);
+    traverse<kClosest, H, false>(sc, ip, r, h, best, st, stk);
+    if (best.prim == kMiss) return;
+    shade_adjoint(sc, sh, verts, idx, i, v3(rb.x, rb.y, rb.z), best.prim, best.u, best.v,
+                  dL_dimage, grad_verts, grad_texels, vec_texels);
+}
+
+// The same adjoint from the forward's saved hit records (vsr_render's
+// `hits`), one thread per pixel and no traversal: the saved (prim, u, v)
+// are the closest hit the re-trace would find, so the gradients are the
+// re-tracing kernel's.  A hit record whose primitive is out of range is
+// skipped and flagged (kErrHit).
+__global__ void __launch_bounds__(256) k_render_backward_hits(
+    DevScene sc, ShadeDev sh, const float* __restrict__ verts, const uint32_t* __restrict__ idx,
+    const float4* __restrict__ rays, const float4* __restrict__ hits, unsigned long long n,
+    const float* __restrict__ dL_dimage, float* __restrict__ grad_verts,
+    float* __restrict__ grad_texels, bool vec_texels) {
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 h = VSR_LDG(hits + i);
+    const uint32_t prim = __float_as_uint(h.w);
+    if (prim == kMiss) return;
+    if (prim >= sc.nprims) {
+        atomicOr(sc.err, kErrHit);
+        return;
+    }
+    const float4 rb = VSR_LDG(rays + 2 * i + 1);
+    shade_adjoint(sc, sh, verts, idx, i, v3(rb.x, rb.y, rb.z), prim, h.y, h.z, dL_dimage,
+                  grad_verts, grad_texels, vec_texels);
 }
 
 // Ambient-occlusion render: c = albedo_rgb(uv) * (1 - occluded / spp) for a
@@ -464,6 +505,17 @@ cudaError_t launch_render(const LaunchArgs& a, int kind, const ShadeDev& sh, con
         case 4: return render_one<IsectCount>(a, sh, verts, idx, image, hits);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_render_backward_hits(const DevScene& sc, const ShadeDev& sh,
+                                        const float* verts, const uint32_t* idx,
+                                        const float4* rays, const float4* hits,
+                                        unsigned long long n, const float* g, float* gv,
+                                        float* gt, cudaStream_t stream) {
+    const bool vec = (reinterpret_cast<uintptr_t>(gt) & 15u) == 0;
+    k_render_backward_hits<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
+        sc, sh, verts, idx, rays, hits, n, g, gv, gt, vec);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_render_backward(const LaunchArgs& a, int kind, const ShadeDev& sh,

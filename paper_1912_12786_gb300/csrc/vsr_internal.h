@@ -119,6 +119,13 @@ cudaError_t launch_render(const LaunchArgs& a, int kind, const ShadeDev& sh, con
 cudaError_t launch_render_backward(const LaunchArgs& a, int kind, const ShadeDev& sh,
                                    const float* verts, const uint32_t* idx, const float* g,
                                    float* gv, float* gt);
+// The adjoint from the forward's saved hit records (no traversal), one
+// thread per ray.
+cudaError_t launch_render_backward_hits(const DevScene& sc, const ShadeDev& sh,
+                                        const float* verts, const uint32_t* idx,
+                                        const float4* rays, const float4* hits,
+                                        unsigned long long n, const float* g, float* gv,
+                                        float* gt, cudaStream_t stream);
 // Source line of the first misaligned load a render kernel skipped (0 if
 // none), cleared after reading.
 cudaError_t render_align_error(unsigned* line);

@@ -123,6 +123,7 @@ _SIGS = {
     "vsr_trace_batch": ([P, P, P, P, ctypes.c_uint32, P, ctypes.c_int32, P, P], ctypes.c_int),
     "vsr_render": ([P, P, ctypes.c_uint64, P, P, P, P, P, P], ctypes.c_int),
     "vsr_trace_backward": ([P, P, ctypes.c_uint64, P, P, P, P, P, P, P], ctypes.c_int),
+    "vsr_render_backward_hits": ([P, P, P, ctypes.c_uint64, P, P, P, P, P], ctypes.c_int),
     "vsr_render_ao": ([P, P, ctypes.c_uint64, P, ctypes.c_uint32, P, ctypes.c_float,
                        ctypes.c_float, P, P, P, P, P], ctypes.c_int),
     "vsr_render_ao_backward": ([P, P, P, ctypes.c_uint64, P, P, P, P], ctypes.c_int),
@@ -508,6 +509,16 @@ def vsr_trace_backward(scene: Scene, rays, isect: vsr_intersector, shade: vsr_sh
                                     ctypes.byref(isect), ctypes.byref(shade), _ptr(dL_dimage),
                                     _ptr(grad_verts), _ptr(grad_texels),
                                     ctypes.byref(params) if params else None, _stream(stream)))
+
+
+def vsr_render_backward_hits(scene: Scene, rays, hits, shade: vsr_shade_params, dL_dimage,
+                             grad_verts, grad_texels=None, stream=None):
+    """The adjoint of vsr_render from its saved hit records [n,4] (no
+    re-trace): accumulates dL/dverts and dL/dtexels like vsr_trace_backward."""
+    _check(lib().vsr_render_backward_hits(scene.handle, _ptr(rays), _ptr(hits),
+                                          int(rays.shape[0]), ctypes.byref(shade),
+                                          _ptr(dL_dimage), _ptr(grad_verts), _ptr(grad_texels),
+                                          _stream(stream)))
 
 
 def vsr_render_ao(scene: Scene, rays, isect: vsr_intersector, spp: int, xi, ao_tmax: float,

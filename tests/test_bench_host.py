@@ -39,6 +39,11 @@ def test_adjoint_models_by_hand():
     trace = 3 * 48 + 32 * 6 + 48 * 1 + 4 * 1 + (24 + 4) * 1 - 16 * 3
     assert nbytes == trace + 2 * (160 + 36) + 48 * 1
     assert natomics == 2 * 9 + 4  # 9 scalar vertex atomics per ray, 4 vector texel atomics
+    # from saved hits: 16 B record per ray, 16 B direction + 12 B dL/dc per hit,
+    # 148 + 36 B per hit with a gradient, 48 B per lit one
+    hit3 = np.array([True, True, False])
+    assert bench.render_backward_hits_model(hit3, grad & hit3, lit) == \
+        3 * 16 + 2 * (16 + 12) + 2 * (148 + 36) + 48 * 1
     hit = np.array([True, True, True, False])
     tex = np.array([True, True, False, False])
     vis = np.array([True, False, True, True])

@@ -129,6 +129,62 @@ def test_backward_matches_central_differences(sphere):
     assert _rel(gt[tj, ti, tc], fdt) < 1e-3
 
 
+def test_backward_from_saved_hits(sphere):
+    """The adjoint from the forward's hit records (no re-trace) equals the
+    re-tracing adjoint up to the order of the atomics, and the FP64
+    reference; misses and out-of-range records are skipped, the latter
+    flagged (error bit 3)."""
+    d = sphere
+    V, s = d["V"], d["s"]
+    rays = torch.from_numpy(d["rays"]).cuda()
+    n = len(d["rays"])
+    isect = V.intersector("alpha_tex", cutoff_f=0.3)
+    shade = V.shade_params(d["light"])
+    img = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    hits = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    V.vsr_render(s, rays, isect, shade, img, hits)
+    g = torch.from_numpy(d["g"].astype(np.float32)).cuda()
+    gv = torch.zeros((d["sc"].verts.shape[0], 3), dtype=torch.float32, device="cuda")
+    gt = torch.zeros(d["sc"].textures[0].texels.shape, dtype=torch.float32, device="cuda")
+    V.vsr_render_backward_hits(s, rays, hits, shade, g, gv, gt)
+    torch.cuda.synchronize()
+    gv, gt = gv.cpu().numpy(), gt.cpu().numpy()
+    rv, rt = _gpu_grads(d, d["g"])
+    assert np.allclose(gv, rv, rtol=1e-4, atol=1e-6 * np.abs(rv).max())
+    assert np.allclose(gt, rt, rtol=1e-4, atol=1e-6 * np.abs(rt).max())
+    assert _rel(gv, d["gv_ref"]) < 1e-3 and _rel(gt, d["gt_ref"]) < 1e-3
+    assert np.all(gt[..., 3] == 0)
+    assert V.vsr_get_device_error(s) == 0, V.vsr_last_error()
+    # vertex gradients only (no texel array)
+    gv2 = torch.zeros((d["sc"].verts.shape[0], 3), dtype=torch.float32, device="cuda")
+    V.vsr_render_backward_hits(s, rays, hits, shade, g, gv2, None)
+    torch.cuda.synchronize()
+    assert np.allclose(gv2.cpu().numpy(), rv, rtol=1e-4, atol=1e-6 * np.abs(rv).max())
+    # a record out of range is skipped and flagged, never dereferenced
+    prim = hits[:, 3].contiguous().view(torch.int32)
+    k = int(torch.nonzero(prim != -1)[0].item())
+    bad = hits.clone()
+    bad[k, 3] = torch.tensor([d["sc"].ntri + 7], dtype=torch.int32).view(torch.float32)[0]
+    gk = torch.zeros_like(g)
+    gk[k] = 1.0
+    gv3 = torch.zeros_like(gv2)
+    V.vsr_render_backward_hits(s, rays, bad, shade, gk, gv3, None)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(gv3) == 0
+    assert V.vsr_get_device_error(s) & 8
+    assert V.vsr_get_device_error(s) == 0
+    host = np.zeros((n, 4), np.float32)
+
+    class HostTensor:  # host memory where device memory is required
+        shape = host.shape
+
+        def data_ptr(self):
+            return host.ctypes.data
+
+    with pytest.raises(V.VsrError, match="device memory"):
+        V.vsr_render_backward_hits(s, rays, HostTensor(), shade, g, gv2, None)
+
+
 def test_autograd_function_and_scene_update(sphere):
     """RenderFunction gives the same image and gradients as the direct calls;
     a vertex update refits the BVH so traces stay exact."""
@@ -146,6 +202,14 @@ def test_autograd_function_and_scene_update(sphere):
     loss.backward()
     g = 2.0 * (img.detach() - tgt)
     gv, gt = _gpu_grads(d, g.cpu().numpy())
+    assert np.allclose(verts.grad.cpu().numpy(), gv, rtol=1e-4, atol=1e-6 * np.abs(gv).max())
+    assert np.allclose(tex.grad.cpu().numpy(), gt, rtol=1e-4, atol=1e-6 * np.abs(gt).max())
+    # the re-tracing backward (no hit records kept) gives the same gradients
+    verts.grad = None
+    tex.grad = None
+    img2 = render(d["s"], rays, verts, tex, isect, shade, save_hits=False)
+    assert torch.equal(img2, img)
+    ((img2 - tgt) ** 2).sum().backward()
     assert np.allclose(verts.grad.cpu().numpy(), gv, rtol=1e-4, atol=1e-6 * np.abs(gv).max())
     assert np.allclose(tex.grad.cpu().numpy(), gt, rtol=1e-4, atol=1e-6 * np.abs(gt).max())
     # move the vertices: the refit BVH must give the same closest hits as a
