@@ -1084,7 +1084,8 @@ def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):
     roof = roofline("k_render_backward_hits (adjoint from the forward's hit records)", tb, nbytes)
     roof["note"] = ("one launch is 262,144 rays, tens of microseconds: launch-latency scale; "
                     "the scene (65 k triangles, 4 MB texture) is L2-resident")
-    roof_rt = roofline("k_render_backward (re-trace + adjoint)", tb_rt, nbytes_rt)
+    roof_rt = roofline("vsr_trace_backward (closest-hit trace + k_render_backward_hits)", tb_rt,
+                       nbytes_rt)
     return {"value": round(n / (t / 1e3) / 1e6, 2), "unit": "Mrays/s", "ms_per_step": round(t, 4),
             "roofline": roof, "roofline_retrace": roof_rt,
             "retrace_value": round(n / (statistics.median(ms_rt) / 1e3) / 1e6, 2),
@@ -1094,7 +1095,7 @@ def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):
             "backward_ms": round(statistics.median(bwd), 4),
             "workload": "displaced icosphere, 64,980 triangles, 512x512 rays, alpha-texture "
                         "closest hit, gradients for 32,492 vertices and 512^2 texels",
-            "gpu_launches_per_step": 2}
+            "gpu_launches_per_step": 3}
 
 
 def batch_bench(V, torch, dev, flush, stream, steps):

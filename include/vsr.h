@@ -557,9 +557,14 @@ typedef struct vsr_shade_params {
 } vsr_shade_params;
 
 /*
- * Closest-hit trace with `isect` (static dispatch) and the shading above.
- *   image device float32 [n*3], written; hits device vsr_hit [n] or NULL.
- *   params NULL or a non-persistent configuration.
+ * Closest-hit trace with `isect` (static dispatch) and the shading above: the
+ * trace kernels of vsr_trace write the hit records, then a shading pass reads
+ * them.
+ *   image device float32 [n*3], written; hits device vsr_hit [n] or NULL
+ *         (NULL: the records go to n * 16 bytes of scratch from the
+ *         stream-ordered allocator, freed on the stream).
+ *   params NULL (the default configuration) or any vsr_trace configuration
+ *         with ray_order 0.
  * Errors as vsr_trace.
  */
 vsr_status vsr_render(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
@@ -569,7 +574,8 @@ vsr_status vsr_render(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
 
 /*
  * Adjoint of vsr_render at fixed visibility: every ray is traced again with
- * the same traversal (the same hit; no forward state is stored) and dL/dc is
+ * the same traversal (the same hit; no forward state is kept: the records go
+ * to n * 16 bytes of stream-ordered scratch, freed on the stream) and dL/dc is
  * propagated to the vertices -- through the barycentrics u, v of the
  * Moller-Trumbore solve (dL/dv_k = -b_k M^-T (0, dL/du, dL/dv), M = [-d, e1,
  * e2], b = (1-u-v, u, v)) and through the face normal -- and to the texels of

@@ -1004,8 +1004,6 @@ vsr_status prepare_render(vsr_scene* s, const vsr_ray* rays, uint64_t n,
         return fail(VSR_ERR_ARG, "rendering uses static dispatch only");
     if (is && is->kind == VSR_ISECT_CLIP)
         return fail(VSR_ERR_ARG, "the clip-box intersector is for vsr_trace and vsr_trace_multi");
-    if (p && p->persistent) return fail(VSR_ERR_ARG, "rendering uses non-persistent launches");
-    if (p && p->lockstep) return fail(VSR_ERR_ARG, "lockstep 1 is for vsr_trace, path tracing and batches");
     // hits are checked by the callers; a placeholder keeps prepare_launch's
     // hit check out of the way when n == 0
     vsr_status st = prepare_launch(s, rays, 0, is, VSR_CLOSEST, nullptr, p, a);
@@ -1040,8 +1038,20 @@ extern "C" vsr_status vsr_render(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (st != VSR_OK) return st;
     a.stream = reinterpret_cast<cudaStream_t>(stream);
     DeviceGuard g(s->device);
-    cudaError_t e = launch_render(a, is->kind, shd, s->d_verts, s->d_idx, image,
-                                  reinterpret_cast<float4*>(hits));
+    // the closest-hit trace into `hits` (or stream-ordered scratch), then the
+    // shading pass from the records
+    float4* h = reinterpret_cast<float4*>(hits);
+    cudaError_t e = cudaSuccess;
+    if (!h) e = cudaMallocAsync(reinterpret_cast<void**>(&h), n * sizeof(float4), a.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "render scratch");
+    a.hits = h;
+    e = launch_static(a, is->kind, false);
+    if (e == cudaSuccess)
+        e = launch_shade_hits(s->dev, shd, s->d_verts, s->d_idx, a.rays, h, n, image, a.stream);
+    if (!hits) {
+        const cudaError_t f = cudaFreeAsync(h, a.stream);
+        if (e == cudaSuccess) e = f;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "render launch");
     return VSR_OK;
 }
@@ -1070,8 +1080,18 @@ extern "C" vsr_status vsr_trace_backward(vsr_scene* s, const vsr_ray* rays, uint
     if (st != VSR_OK) return st;
     a.stream = reinterpret_cast<cudaStream_t>(stream);
     DeviceGuard g(s->device);
-    cudaError_t e = launch_render_backward(a, is->kind, shd, s->d_verts, s->d_idx, dL_dimage,
-                                           grad_verts, grad_texels);
+    // the closest hits traced again into stream-ordered scratch, then the
+    // adjoint from them
+    float4* h = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&h), n * sizeof(float4), a.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "backward scratch");
+    a.hits = h;
+    e = launch_static(a, is->kind, false);
+    if (e == cudaSuccess)
+        e = launch_render_backward_hits(s->dev, shd, s->d_verts, s->d_idx, a.rays, h, n,
+                                        dL_dimage, grad_verts, grad_texels, a.stream);
+    const cudaError_t f = cudaFreeAsync(h, a.stream);
+    if (e == cudaSuccess) e = f;
     if (e != cudaSuccess) return cuda_fail(e, "backward launch");
     return VSR_OK;
 }

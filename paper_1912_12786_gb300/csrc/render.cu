@@ -6,15 +6,17 @@
 //             interpolated texture coordinate, albedo the bilinear lookup
 //             (texel centres at ((i + 0.5)/W, (j + 0.5)/H), clamp-to-edge
 //             texel indices).
-//   backward  every ray is traced again with the same traversal (the same
-//             hit, so no traversal state is stored), the shading is
-//             recomputed and its adjoint is scattered with atomics into the
-//             vertex gradients (through u, v of the Moller-Trumbore solve and
-//             through the face normal) and the texel gradients (through the
-//             bilinear weights).
+//             The render is the closest-hit trace (the trace kernels), then
+//             a shading pass over its hit records.
+//   backward  from closest-hit records -- the forward's, or those a trace
+//             writes again -- the shading is recomputed and its adjoint is
+//             scattered with atomics into the vertex gradients (through u, v
+//             of the Moller-Trumbore solve and through the face normal) and
+//             the texel gradients (through the bilinear weights).
 //
 // Also: the BVH refit used after a vertex update.
-// Render and adjoint kernels use alignment-checked loads (see VSR_LDG).
+// The shading, adjoint and occlusion kernels use alignment-checked loads
+// (see VSR_LDG).
 #define VSR_CHECKED_LOADS 1
 #include "vsr_internal.h"
 
@@ -120,39 +122,31 @@ __device__ __forceinline__ void surface(const float* __restrict__ verts,
 
 }  // namespace
 
-template <class H>
-__global__ void __launch_bounds__(256) k_render(DevScene sc, IsectParams ip, ShadeDev sh,
-                                                const float* __restrict__ verts,
-                                                const uint32_t* __restrict__ idx,
-                                                const float4* __restrict__ rays,
-                                                RayMap map, float* __restrict__ image,
-                                                float4* __restrict__ hits) {
-    extern __shared__ uint32_t s_stack[];
-    const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= map.threads) return;
-    const unsigned long long i = ray_of_thread(g, map);
-    if (i >= map.n) return;
-    const float4 ra = VSR_LDG(rays + 2 * i), rb = VSR_LDG(rays + 2 * i + 1);
-    const Ray r = make_ray(ra, rb);
-    H h;
-    Best best;
-    Stats st;
-    ShortStack<0> stk;
-    stk.init(s_stack + threadIdx.x, blockDim.x);
-    traverse<kClosest, H, false>(sc, ip, r, h, best, st, stk);
-    if (hits) {
-        if (reinterpret_cast<unsigned long long>(hits + i) % 16)
-            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
-        else
-            hits[i] = hit_record(best);
-    }
+// The forward shading from the closest hits the trace kernels wrote (the
+// render is that trace, then this pass): one thread per ray.  A hit record
+// whose primitive is out of range gives the background and is flagged
+// (kErrHit).
+__global__ void __launch_bounds__(256) k_shade_hits(DevScene sc, ShadeDev sh,
+                                                    const float* __restrict__ verts,
+                                                    const uint32_t* __restrict__ idx,
+                                                    const float4* __restrict__ rays,
+                                                    const float4* __restrict__ hits,
+                                                    unsigned long long n,
+                                                    float* __restrict__ image) {
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 h = VSR_LDG(hits + i);
+    const uint32_t prim = __float_as_uint(h.w);
     float c[3] = {sh.bg[0], sh.bg[1], sh.bg[2]};
-    if (best.prim != kMiss) {
+    if (prim != kMiss && prim >= sc.nprims) {
+        atomicOr(sc.err, kErrHit);
+    } else if (prim != kMiss) {
+        const float4 rb = VSR_LDG(rays + 2 * i + 1);
         Surface f;
-        surface(verts, idx, best.prim, v3(rb.x, rb.y, rb.z), v3(sh.light[0], sh.light[1], sh.light[2]),
+        surface(verts, idx, prim, v3(rb.x, rb.y, rb.z), v3(sh.light[0], sh.light[1], sh.light[2]),
                 f);
         Bilinear b;
-        albedo(sc, VSR_LDG(sc.geom + best.prim), lerp_uv(sc.uvs, best.prim, best.u, best.v), b);
+        albedo(sc, VSR_LDG(sc.geom + prim), lerp_uv(sc.uvs, prim, h.y, h.z), b);
         for (int ch = 0; ch < 3; ++ch) c[ch] = b.rgb[ch] * f.s;
     }
     image[3 * i] = c[0];
@@ -261,37 +255,10 @@ __device__ __forceinline__ void shade_adjoint(const DevScene& sc, const ShadeDev
     }
 }
 
-// The adjoint with the ray traced again (vsr_trace_backward: no forward state
-// is kept).
-template <class H>
-__global__ void __launch_bounds__(256) k_render_backward(
-    DevScene sc, IsectParams ip, ShadeDev sh, const float* __restrict__ verts,
-    const uint32_t* __restrict__ idx, const float4* __restrict__ rays, RayMap map,
-    const float* __restrict__ dL_dimage, float* __restrict__ grad_verts,
-    float* __restrict__ grad_texels, bool vec_texels) {
-    extern __shared__ uint32_t s_stack[];
-    const unsigned long long gi = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= map.threads) return;
-    const unsigned long long i = ray_of_thread(gi, map);
-    if (i >= map.n) return;
-    const float4 ra = VSR_LDG(rays + 2 * i), rb = VSR_LDG(rays + 2 * i + 1);
-    const Ray r = make_ray(ra, rb);
-    H h;
-    Best best;
-    Stats st;
-    ShortStack<0> stk;
-    stk.init(s_stack + threadIdx.x, blockDim.x);
-    traverse<kClosest, H, false>(sc, ip, r, h, best, st, stk);
-    if (best.prim == kMiss) return;
-    shade_adjoint(sc, sh, verts, idx, i, v3(rb.x, rb.y, rb.z), best.prim, best.u, best.v,
-                  dL_dimage, grad_verts, grad_texels, vec_texels);
-}
-
-// The same adjoint from the forward's saved hit records (vsr_render's
-// `hits`), one thread per pixel and no traversal: the saved (prim, u, v)
-// are the closest hit the re-trace would find, so the gradients are the
-// re-tracing kernel's.  A hit record whose primitive is out of range is
-// skipped and flagged (kErrHit).
+// The adjoint from closest-hit records (the forward's saved hits, or those a
+// trace writes again for vsr_trace_backward), one thread per pixel, no
+// traversal.  A hit record whose primitive is out of range is skipped and
+// flagged (kErrHit).
 __global__ void __launch_bounds__(256) k_render_backward_hits(
     DevScene sc, ShadeDev sh, const float* __restrict__ verts, const uint32_t* __restrict__ idx,
     const float4* __restrict__ rays, const float4* __restrict__ hits, unsigned long long n,
@@ -466,45 +433,14 @@ cudaError_t prep_smem(K kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <class H>
-cudaError_t render_one(const LaunchArgs& a, const ShadeDev& sh, const float* verts,
-                       const uint32_t* idx, float* image, float4* hits) {
-    const size_t smem = (size_t)a.sc.stack_depth * a.block * sizeof(uint32_t);
-    auto k = k_render<H>;
-    cudaError_t e = prep_smem(k, smem);
-    if (e != cudaSuccess) return e;
-    const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
-    k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, sh, verts, idx, a.rays, a.map, image,
-                                                     hits);
-    return cudaGetLastError();
-}
-
-template <class H>
-cudaError_t backward_one(const LaunchArgs& a, const ShadeDev& sh, const float* verts,
-                         const uint32_t* idx, const float* g, float* gv, float* gt) {
-    const size_t smem = (size_t)a.sc.stack_depth * a.block * sizeof(uint32_t);
-    auto k = k_render_backward<H>;
-    cudaError_t e = prep_smem(k, smem);
-    if (e != cudaSuccess) return e;
-    const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
-    const bool vec = (reinterpret_cast<uintptr_t>(gt) & 15u) == 0;
-    k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, sh, verts, idx, a.rays, a.map, g, gv,
-                                                     gt, vec);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
-cudaError_t launch_render(const LaunchArgs& a, int kind, const ShadeDev& sh, const float* verts,
-                          const uint32_t* idx, float* image, float4* hits) {
-    switch (kind) {
-        case 0: return render_one<IsectNone>(a, sh, verts, idx, image, hits);
-        case 1: return render_one<IsectDefault>(a, sh, verts, idx, image, hits);
-        case 2: return render_one<IsectAlphaTex>(a, sh, verts, idx, image, hits);
-        case 3: return render_one<IsectProcAlpha>(a, sh, verts, idx, image, hits);
-        case 4: return render_one<IsectCount>(a, sh, verts, idx, image, hits);
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t launch_shade_hits(const DevScene& sc, const ShadeDev& sh, const float* verts,
+                              const uint32_t* idx, const float4* rays, const float4* hits,
+                              unsigned long long n, float* image, cudaStream_t stream) {
+    k_shade_hits<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(sc, sh, verts, idx, rays, hits,
+                                                                  n, image);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_render_backward_hits(const DevScene& sc, const ShadeDev& sh,
@@ -516,19 +452,6 @@ cudaError_t launch_render_backward_hits(const DevScene& sc, const ShadeDev& sh,
     k_render_backward_hits<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
         sc, sh, verts, idx, rays, hits, n, g, gv, gt, vec);
     return cudaGetLastError();
-}
-
-cudaError_t launch_render_backward(const LaunchArgs& a, int kind, const ShadeDev& sh,
-                                   const float* verts, const uint32_t* idx, const float* g,
-                                   float* gv, float* gt) {
-    switch (kind) {
-        case 0: return backward_one<IsectNone>(a, sh, verts, idx, g, gv, gt);
-        case 1: return backward_one<IsectDefault>(a, sh, verts, idx, g, gv, gt);
-        case 2: return backward_one<IsectAlphaTex>(a, sh, verts, idx, g, gv, gt);
-        case 3: return backward_one<IsectProcAlpha>(a, sh, verts, idx, g, gv, gt);
-        case 4: return backward_one<IsectCount>(a, sh, verts, idx, g, gv, gt);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 cudaError_t render_align_error(unsigned* line) {

@@ -114,13 +114,12 @@ cudaError_t launch_read_probe_l1(const void* buf, unsigned long long bytes, uint
                                  unsigned long long* bytes_read, cudaStream_t stream);
 
 // Closest-hit render with diffuse shading, and its adjoint (render.cu).
-cudaError_t launch_render(const LaunchArgs& a, int kind, const ShadeDev& sh, const float* verts,
-                          const uint32_t* idx, float* image, float4* hits);
-cudaError_t launch_render_backward(const LaunchArgs& a, int kind, const ShadeDev& sh,
-                                   const float* verts, const uint32_t* idx, const float* g,
-                                   float* gv, float* gt);
-// The adjoint from the forward's saved hit records (no traversal), one
-// thread per ray.
+// The render's shading pass from closest-hit records (the trace kernels
+// write them first), one thread per ray.
+cudaError_t launch_shade_hits(const DevScene& sc, const ShadeDev& sh, const float* verts,
+                              const uint32_t* idx, const float4* rays, const float4* hits,
+                              unsigned long long n, float* image, cudaStream_t stream);
+// The adjoint from closest-hit records (no traversal), one thread per ray.
 cudaError_t launch_render_backward_hits(const DevScene& sc, const ShadeDev& sh,
                                         const float* verts, const uint32_t* idx,
                                         const float4* rays, const float4* hits,

@@ -129,6 +129,40 @@ def test_backward_matches_central_differences(sphere):
     assert _rel(gt[tj, ti, tc], fdt) < 1e-3
 
 
+def test_render_in_every_launch_shape(sphere):
+    """The render is the trace kernels plus a shading pass, so every launch
+    configuration of vsr_trace gives the same image and hit records; the
+    re-tracing adjoint likewise."""
+    d = sphere
+    V, s = d["V"], d["s"]
+    rays = torch.from_numpy(d["rays"]).cuda()
+    n = len(d["rays"])
+    isect = V.intersector("alpha_tex", cutoff_f=0.3)
+    shade = V.shade_params(d["light"])
+    ref_img = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    ref_hits = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    V.vsr_render(s, rays, isect, shade, ref_img, ref_hits)
+    for p in (V.trace_params(image_width=512, block_size=64),
+              V.trace_params(persistent=1, refill_threshold=16, watchdog_ms=10_000),
+              V.trace_params(persistent=1, lockstep=1, refill_threshold=24, watchdog_ms=10_000),
+              V.trace_params(lockstep=1, stack_regs=4)):
+        img = torch.full_like(ref_img, -1.0)
+        hits = torch.full_like(ref_hits, -1.0)
+        V.vsr_render(s, rays, isect, shade, img, hits, p)
+        img2 = torch.full_like(ref_img, -1.0)
+        V.vsr_render(s, rays, isect, shade, img2, None, p)
+        torch.cuda.synchronize()
+        assert torch.equal(img.view(torch.int32), ref_img.view(torch.int32))
+        assert torch.equal(img2.view(torch.int32), ref_img.view(torch.int32))
+        assert torch.equal(hits.view(torch.int32), ref_hits.view(torch.int32))
+        gv = torch.zeros((d["sc"].verts.shape[0], 3), dtype=torch.float32, device="cuda")
+        g = torch.from_numpy(d["g"].astype(np.float32)).cuda()
+        V.vsr_trace_backward(s, rays, isect, shade, g, gv, None, p)
+        torch.cuda.synchronize()
+        assert _rel(gv.cpu().numpy(), d["gv_ref"]) < 1e-3
+    assert V.vsr_get_device_error(s) == 0, V.vsr_last_error()
+
+
 def test_backward_from_saved_hits(sphere):
     """The adjoint from the forward's hit records (no re-trace) equals the
     re-tracing adjoint up to the order of the atomics, and the FP64
