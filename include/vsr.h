@@ -615,9 +615,13 @@ vsr_status vsr_render_backward_hits(vsr_scene* scene, const vsr_ray* rays, const
  *   c = albedo_rgb(uv) * (1 - occluded / spp)      (background for a miss)
  * where the spp occlusion rays of pixel i are built exactly as
  * vsr_make_ao_rays builds them from the uniforms xi[i*spp + k] and traced
- * any-hit with the same intersector (static dispatch).  Three launches on
- * `stream`: the closest-hit trace into `hits`, the occlusion count (one
- * thread per occlusion ray) and the shading.
+ * any-hit with the same intersector (static dispatch).  On `stream`: the
+ * closest-hit trace into `hits` (default configuration); the occlusion rays
+ * and their any-hit records in n * spp * 48 bytes of scratch from the
+ * stream-ordered allocator, traced at the configuration tuned for this
+ * scene, intersector and the any-hit query (vsr_trace_tune; else the
+ * default) and counted per pixel; the shading.  The counts do not depend on
+ * the configuration.
  *   image     device float32 [n*3], written
  *   hits      device vsr_hit [n], written: the primary closest hits
  *   occlusion device float32 [n], written: occluded fraction (0 for a miss)

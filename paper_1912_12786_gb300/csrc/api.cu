@@ -223,6 +223,18 @@ __global__ void k_ao_rays(const float* __restrict__ verts, const uint32_t* __res
     }
 }
 
+// Occluded rays per pixel from the ambient-occlusion rays' any-hit records
+// (pixel i's rays at i * spp .. i * spp + spp - 1), as integers, so the
+// counts do not depend on the traversal order.
+__global__ void k_ao_count(const float4* __restrict__ hits, unsigned long long n, uint32_t spp,
+                           uint32_t* __restrict__ cnt) {
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t c = 0;
+    for (uint32_t k = 0; k < spp; ++k) c += __float_as_uint(hits[i * spp + k].w) != kMiss;
+    cnt[i] = c;
+}
+
 void free_bvh(vsr_scene* s) {
     dfree(s->d_nodes);
     dfree(s->d_tris);
@@ -1170,9 +1182,42 @@ extern "C" vsr_status vsr_render_ao(vsr_scene* s, const vsr_ray* rays, uint64_t 
     DeviceGuard g(s->device);
     cudaError_t e = launch_static(a, is->kind, false);
     if (e != cudaSuccess) return cuda_fail(e, "ao primary trace launch");
-    VSR_CUDA(cudaMemsetAsync(occlusion, 0, n * 4, a.stream), "occlusion counts");
-    e = launch_ao_occlusion(a, is->kind, ao);
-    if (e != cudaSuccess) return cuda_fail(e, "ao occlusion launch");
+    // occlusion: the AO rays (as vsr_make_ao_rays makes them) and their
+    // any-hit records in stream-ordered scratch, traced by the trace kernels
+    // at the configuration tuned for this scene, intersector and the any-hit
+    // query (else the default), then counted per pixel
+    const uint64_t m = n * spp;
+    float4* ao_rays = nullptr;
+    float4* ao_hits = nullptr;
+    e = cudaMallocAsync(reinterpret_cast<void**>(&ao_rays), m * 32, a.stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ao_hits), m * 16, a.stream);
+    if (e == cudaSuccess) {
+        k_ao_rays<<<(unsigned)((n + 255) / 256), 256, 0, a.stream>>>(
+            s->d_verts, s->d_idx, a.rays, ao.hits, n, spp, ao.xi, ao_tmax, eps, s->dev.nprims,
+            s->dev.err, ao_rays);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        LaunchArgs b = a;
+        b.query = VSR_ANY;
+        b.rays = ao_rays;
+        b.n = m;
+        b.hits = ao_hits;
+        b.counters = nullptr;
+        vsr_trace_params tp;
+        if (!tuned_params(s, is, VSR_ANY, &tp) || tp.image_width) tp = kDefaultParams;
+        if (apply_params(b, m, tp) != VSR_OK) e = cudaErrorInvalidValue;
+        if (e == cudaSuccess)
+            e = tp.ray_order ? launch_ordered(b, is->kind, false) : launch_static(b, is->kind, false);
+    }
+    if (e == cudaSuccess) {
+        k_ao_count<<<(unsigned)((n + 255) / 256), 256, 0, a.stream>>>(
+            ao_hits, n, spp, reinterpret_cast<uint32_t*>(occlusion));
+        e = cudaGetLastError();
+    }
+    if (ao_hits) cudaFreeAsync(ao_hits, a.stream);
+    if (ao_rays) cudaFreeAsync(ao_rays, a.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ao occlusion");
     e = launch_ao_shade(a.sc, ao, n, a.stream);
     if (e != cudaSuccess) return cuda_fail(e, "ao shade launch");
     return VSR_OK;

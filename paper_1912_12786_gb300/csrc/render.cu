@@ -279,48 +279,12 @@ __global__ void __launch_bounds__(256) k_render_backward_hits(
 }
 
 // Ambient-occlusion render: c = albedo_rgb(uv) * (1 - occluded / spp) for a
-// primary hit, background for a miss.  Three passes over the saved primary
-// hits: the closest-hit trace (the trace kernels), the occlusion count (one
-// thread per occlusion ray) and the shading.
-
-// Occlusion ray j = i * spp + k of pixel i, built from the pixel's closest
-// hit exactly as vsr_make_ao_rays builds it and traced any-hit with the same
-// intersector; an occluded ray adds 1 to cnt[i].  The counts are integers,
-// so the totals do not depend on the order of the atomics.
-template <class H>
-__global__ void __launch_bounds__(256) k_ao_occlusion(DevScene sc, IsectParams ip,
-                                                      const float* __restrict__ verts,
-                                                      const uint32_t* __restrict__ idx,
-                                                      const float4* __restrict__ rays,
-                                                      const float4* __restrict__ hits,
-                                                      unsigned long long n, uint32_t spp,
-                                                      const float2* __restrict__ xi,
-                                                      float ao_tmax, float eps,
-                                                      uint32_t* __restrict__ cnt) {
-    extern __shared__ uint32_t s_stack[];
-    const unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n * spp) return;
-    const unsigned long long i = j / spp;
-    const float4 h = VSR_LDG(hits + i);
-    const uint32_t prim = __float_as_uint(h.w);
-    if (prim == kMiss) return;
-    const float4 rb = VSR_LDG(rays + 2 * i + 1);
-    const float4 ra = VSR_LDG(rays + 2 * i);
-    const AoFrame f = ao_frame(verts, idx, prim, rb.x, rb.y, rb.z);
-    const float4 o = make_float4(__fmaf_rn(h.x, rb.x, ra.x), __fmaf_rn(h.x, rb.y, ra.y),
-                                 __fmaf_rn(h.x, rb.z, ra.z), eps);
-    const Ray ar = make_ray(o, ao_direction(f, VSR_LDG(xi + j), ao_tmax));
-    H hk;
-    Best best;
-    Stats st;
-    ShortStack<0> stk;
-    stk.init(s_stack + threadIdx.x, blockDim.x);
-    traverse<kAny, H, false>(sc, ip, ar, hk, best, st, stk);
-    if (best.prim != kMiss) atomicAdd(cnt + i, 1u);
-}
+// primary hit, background for a miss.  The closest-hit trace, the occlusion
+// rays traced any-hit and counted (the trace kernels; api.cu), then the
+// shading of the saved hits here.
 
 // Shading of the saved hits; occ enters as the integer counts of
-// k_ao_occlusion and leaves as the occluded fraction (0 for a miss).
+// k_ao_count and leaves as the occluded fraction (0 for a miss).
 __global__ void __launch_bounds__(256) k_ao_shade(DevScene sc, ShadeDev sh,
                                                   const float4* __restrict__ hits,
                                                   unsigned long long n, uint32_t spp,
@@ -425,16 +389,6 @@ __global__ void k_refit(float4* __restrict__ nodes, const uint32_t* __restrict__
     nodes[2ull * id + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
 }
 
-namespace {
-
-template <class K>
-cudaError_t prep_smem(K kernel, size_t smem) {
-    if (smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-}  // namespace
-
 cudaError_t launch_shade_hits(const DevScene& sc, const ShadeDev& sh, const float* verts,
                               const uint32_t* idx, const float4* rays, const float4* hits,
                               unsigned long long n, float* image, cudaStream_t stream) {
@@ -473,34 +427,6 @@ cudaError_t launch_refit(float4* nodes, const uint32_t* level_nodes,
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
-}
-
-namespace {
-
-template <class H>
-cudaError_t occlusion_one(const LaunchArgs& a, const AoArgs& ao) {
-    const size_t smem = (size_t)a.sc.stack_depth * a.block * sizeof(uint32_t);
-    const unsigned long long m = a.n * ao.spp;
-    auto k = k_ao_occlusion<H>;
-    cudaError_t e = prep_smem(k, smem);
-    if (e != cudaSuccess) return e;
-    k<<<(unsigned)((m + a.block - 1) / a.block), a.block, smem, a.stream>>>(
-        a.sc, a.ip, ao.verts, ao.idx, a.rays, ao.hits, a.n, ao.spp, ao.xi, ao.tmax, ao.eps,
-        reinterpret_cast<uint32_t*>(ao.occ));
-    return cudaGetLastError();
-}
-
-}  // namespace
-
-cudaError_t launch_ao_occlusion(const LaunchArgs& a, int kind, const AoArgs& ao) {
-    switch (kind) {
-        case 0: return occlusion_one<IsectNone>(a, ao);
-        case 1: return occlusion_one<IsectDefault>(a, ao);
-        case 2: return occlusion_one<IsectAlphaTex>(a, ao);
-        case 3: return occlusion_one<IsectProcAlpha>(a, ao);
-        case 4: return occlusion_one<IsectCount>(a, ao);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 cudaError_t launch_ao_shade(const DevScene& sc, const AoArgs& ao, unsigned long long n,

@@ -203,8 +203,6 @@ struct AoArgs {
     const float* g;      // backward
     float* grad_texels;  // backward
 };
-// Occlusion counts for a.n pixels (a.rays, ao.hits) into ao.occ as uint32.
-cudaError_t launch_ao_occlusion(const LaunchArgs& a, int kind, const AoArgs& ao);
 // Image and occluded fractions from the hits and counts.
 cudaError_t launch_ao_shade(const DevScene& sc, const AoArgs& ao, unsigned long long n,
                             cudaStream_t stream);
