@@ -1244,8 +1244,12 @@ def large_bench(V, torch, dev, flush, stream, steps):
                                                          "launch_ms": round(tp, 4)}
     else:
         out["ao_any/proc_alpha/static_levels"] = None
-    # ambient-occlusion render (primary trace, occlusion count with one thread
-    # per AO ray, shading) and its texel adjoint from the saved hits
+    # ambient-occlusion render (primary trace and occlusion rays through the
+    # trace kernels at the configurations tuned for the two queries, counts,
+    # shading) and its texel adjoint from the saved hits; the primary query is
+    # tuned here on the frame's pixel tiles (the AO query was tuned above)
+    V.vsr_trace_tune(s, d_rays, proc, "closest", hits, image_width=FRAME_W, stream=stream)
+    out["ao_render/primary_launch"] = launch_config(tuned_or_default(V, s, proc, "closest"))
     eps = scenes.shadow_eps(sc)
     shade = V.shade_params((0.0, 0.0, 1.0), grad_tex=0)
     img = torch.empty((n, 3), dtype=torch.float32, device=dev)

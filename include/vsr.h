@@ -616,7 +616,9 @@ vsr_status vsr_render_backward_hits(vsr_scene* scene, const vsr_ray* rays, const
  * where the spp occlusion rays of pixel i are built exactly as
  * vsr_make_ao_rays builds them from the uniforms xi[i*spp + k] and traced
  * any-hit with the same intersector (static dispatch).  On `stream`: the
- * closest-hit trace into `hits` (default configuration); the occlusion rays
+ * closest-hit trace into `hits` (at the configuration tuned for this scene,
+ * intersector and the closest-hit query, with its pixel tiles if it has
+ * them; else the default); the occlusion rays
  * and their any-hit records in n * spp * 48 bytes of scratch from the
  * stream-ordered allocator, traced at the configuration tuned for this
  * scene, intersector and the any-hit query (vsr_trace_tune; else the

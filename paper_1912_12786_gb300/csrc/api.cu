@@ -1180,6 +1180,14 @@ extern "C" vsr_status vsr_render_ao(vsr_scene* s, const vsr_ray* rays, uint64_t 
     a.stream = reinterpret_cast<cudaStream_t>(stream);
     a.hits = ao.hits;
     DeviceGuard g(s->device);
+    // the primary trace at the configuration tuned for the closest-hit query
+    // (its pixel tiles included), else the default
+    vsr_trace_params pp;
+    if (tuned_params(s, is, VSR_CLOSEST, &pp) && pp.ray_order == 0 &&
+        apply_params(a, n, pp) != VSR_OK) {
+        st = apply_params(a, n, kDefaultParams);
+        if (st != VSR_OK) return st;
+    }
     cudaError_t e = launch_static(a, is->kind, false);
     if (e != cudaSuccess) return cuda_fail(e, "ao primary trace launch");
     // occlusion: the AO rays (as vsr_make_ao_rays makes them) and their

@@ -260,6 +260,36 @@ def test_autograd_function_and_scene_update(sphere):
     assert V.vsr_get_device_error(d["s"]) == 0
 
 
+def test_ao_render_after_tuning_the_any_hit_query(sphere):
+    """The AO render traces its occlusion rays at the configuration tuned for
+    the scene and the any-hit query; the counts, and so the image, are the
+    same whichever configuration runs."""
+    d = sphere
+    V, sc, s = d["V"], d["sc"], d["s"]
+    spp, tmax, eps = 4, 0.5, scenes.shadow_eps(sc)
+    n = len(d["rays"])
+    rays = torch.from_numpy(d["rays"]).cuda()
+    xi = torch.from_numpy(scenes.ao_random(n, spp)).cuda()
+    isect = V.intersector("alpha_tex", cutoff_f=0.3)
+    shade = V.shade_params((0.0, 0.0, 1.0), grad_tex=0)
+    out = []
+    for tune in (False, True):
+        if tune:
+            ao = torch.empty((n * spp, 8), dtype=torch.float32, device="cuda")
+            V.vsr_make_ao_rays(s, rays, out[0][1], spp, xi, tmax, eps, ao)
+            scratch = torch.empty((n * spp, 4), dtype=torch.float32, device="cuda")
+            V.vsr_trace_tune(s, ao, isect, "any", scratch)
+        img = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        hits = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        occ = torch.empty(n, dtype=torch.float32, device="cuda")
+        V.vsr_render_ao(s, rays, isect, spp, xi, tmax, eps, shade, img, hits, occ)
+        torch.cuda.synchronize()
+        out.append((img, hits, occ))
+    for x, y in zip(out[0], out[1]):
+        assert torch.equal(x.view(torch.int32), y.view(torch.int32))
+    assert V.vsr_get_device_error(s) == 0, V.vsr_last_error()
+
+
 def test_ao_render_autograd_and_bad_hit_records(sphere):
     """Ambient-occlusion render on the icosphere (4 occlusion rays per pixel,
     tmax 0.5): hits bit-exact with the oracle, occlusion equal to the oracle's
