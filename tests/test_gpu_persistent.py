@@ -98,7 +98,8 @@ def test_persistent_stack_depths_agree(V, small, kind, query, regs):
     assert V.vsr_get_device_error(s) == 0
 
 
-def test_watchdog_stops_persistent_loop(V, small):
+@pytest.mark.parametrize("lockstep", [0, 1])
+def test_watchdog_stops_persistent_loop(V, small, lockstep):
     """Default any-hit (a case that never stalled) with a budget of 3 outer
     iterations per warp: the launch returns with the timeout bit, and the next
     launch with no budget gives the full, correct result."""
@@ -110,7 +111,7 @@ def test_watchdog_stops_persistent_loop(V, small):
     torch.cuda.synchronize()
     assert V.vsr_get_device_error(s) == 0
     cut = V.trace_params(block_size=128, persistent=1, refill_threshold=16,
-                         watchdog_iterations=3)
+                         watchdog_iterations=3, lockstep=lockstep)
     hits = torch.full_like(full, -5.0)
     V.vsr_trace(s, d_rays, isect, "any", hits, None, cut)
     torch.cuda.synchronize()
@@ -128,7 +129,7 @@ def test_watchdog_stops_persistent_loop(V, small):
     again = torch.full_like(full, -5.0)
     V.vsr_trace(s, d_rays, isect, "any", again, None,
                 V.trace_params(block_size=128, persistent=1, refill_threshold=16,
-                               watchdog_ms=WD_MS))
+                               watchdog_ms=WD_MS, lockstep=lockstep))
     torch.cuda.synchronize()
     assert V.vsr_get_device_error(s) == 0
     assert torch.equal(again.view(torch.int32), full.view(torch.int32))
@@ -213,7 +214,8 @@ def test_batch_stack_depths_agree(V, batch, kind, query):
         assert V.vsr_get_device_error(h) == 0
 
 
-def test_batch_watchdog(V, batch):
+@pytest.mark.parametrize("lockstep", [0, 1])
+def test_batch_watchdog(V, batch, lockstep):
     """A batch with a budget of 3 iterations reports the timeout to scene 0;
     the GPU stays usable and a batch with no budget gives per-scene results."""
     items, blobs, handles, dev_rays = batch
@@ -221,7 +223,7 @@ def test_batch_watchdog(V, batch):
     hits = _hits(dev_rays)
     b = V.vsr_batch_create(handles, dev_rays, hits, isect, "any",
                            V.trace_params(block_size=128, persistent=1, refill_threshold=16,
-                                          watchdog_iterations=3))
+                                          watchdog_iterations=3, lockstep=lockstep))
     V.vsr_batch_launch(b)
     torch.cuda.synchronize()
     b.close()
@@ -231,7 +233,7 @@ def test_batch_watchdog(V, batch):
     hits = _hits(dev_rays)
     b = V.vsr_batch_create(handles, dev_rays, hits, isect, "any",
                            V.trace_params(block_size=128, persistent=1, refill_threshold=16,
-                                          watchdog_ms=WD_MS))
+                                          watchdog_ms=WD_MS, lockstep=lockstep))
     V.vsr_batch_launch(b)
     torch.cuda.synchronize()
     b.close()
