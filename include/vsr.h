@@ -146,11 +146,11 @@ typedef enum vsr_query {
 typedef struct vsr_trace_params {
     uint32_t block_size;       /* threads per block, multiple of 32, 32..256 */
     uint32_t persistent;       /* 0: one ray per thread; 1: persistent warps
-                                  (static dispatch).  Persistent launches on
-                                  one scene claim rays from the scene's one
-                                  counter: they must not overlap on the GPU
-                                  (issue them on one stream, or order the
-                                  streams) */
+                                  (static dispatch).  Each persistent launch
+                                  claims rays from a counter of its own (8
+                                  bytes from the stream-ordered allocator), so
+                                  launches on one scene may overlap on
+                                  different streams */
     uint32_t refill_threshold; /* persistent: refill idle lanes when fewer
                                   than this many of 32 are still active */
     uint32_t blocks_per_sm;    /* persistent: resident blocks per SM (0=auto) */

@@ -34,7 +34,6 @@ struct vsr_scene {
     DevScene dev{};
     DevScene* d_user = nullptr;
     uint32_t* d_err = nullptr;
-    unsigned long long* d_work = nullptr;
     // kept for updates: leaf order, node ids by tree level (deepest first),
     // host copies of the texture descriptors
     uint32_t* d_order = nullptr;
@@ -398,7 +397,7 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     a.n = n;
     a.hits = reinterpret_cast<float4*>(hits);
     a.query = query;
-    a.work = s->d_work;
+    a.work = nullptr;  // persistent launches take their own counter
     a.dyn_user = s->d_user;
     return VSR_OK;
 }
@@ -586,8 +585,7 @@ vsr_status vsr_scene_create_indexed(const float* verts, uint32_t nverts, const u
         (e = dmalloc(&s->d_geom, (size_t)ntri)) != cudaSuccess ||
         (e = dmalloc(&s->d_tex, (size_t)ntex)) != cudaSuccess ||
         (e = dmalloc(&s->d_texels, (size_t)texel_bytes)) != cudaSuccess ||
-        (e = dmalloc(&s->d_user, 1)) != cudaSuccess || (e = dmalloc(&s->d_err, 1)) != cudaSuccess ||
-        (e = dmalloc(&s->d_work, 1)) != cudaSuccess)
+        (e = dmalloc(&s->d_user, 1)) != cudaSuccess || (e = dmalloc(&s->d_err, 1)) != cudaSuccess)
         return bail(cuda_fail(e, "scene allocation"));
     if ((nverts && (e = cudaMemcpy(s->d_verts, verts, 12ull * nverts, cudaMemcpyHostToDevice))) ||
         (ntri && (e = cudaMemcpy(s->d_idx, idx, 12ull * ntri, cudaMemcpyHostToDevice))) ||
@@ -632,7 +630,6 @@ vsr_status vsr_scene_destroy(vsr_scene* s) {
     dfree(s->d_texels);
     dfree(s->d_user);
     dfree(s->d_err);
-    dfree(s->d_work);
     delete s;
     return VSR_OK;
 }

@@ -243,11 +243,24 @@ cudaError_t launch_shape(const LaunchArgs& a) {
     if (e != cudaSuccess) return e;
     const int grid = persistent_grid(a, reinterpret_cast<const void*>(k), smem);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
-    e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), a.stream);
-    if (e != cudaSuccess) return e;
-    k<<<grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits, a.counters, a.stats,
-                                         a.work, a.refill, a.wd);
-    return cudaGetLastError();
+    // the ray counter: the caller's, or 8 bytes of stream-ordered scratch for
+    // this launch alone, so persistent launches on one scene may overlap
+    unsigned long long* work = a.work;
+    if (!work) {
+        e = cudaMallocAsync(reinterpret_cast<void**>(&work), sizeof(unsigned long long), a.stream);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), a.stream);
+    if (e == cudaSuccess) {
+        k<<<grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits, a.counters,
+                                             a.stats, work, a.refill, a.wd);
+        e = cudaGetLastError();
+    }
+    if (!a.work) {
+        const cudaError_t f = cudaFreeAsync(work, a.stream);
+        if (e == cudaSuccess) e = f;
+    }
+    return e;
 }
 
 template <int Q, class H, bool STATS, int K>

@@ -24,7 +24,8 @@ struct LaunchArgs {
     uint32_t persistent;
     uint32_t refill;
     uint32_t blocks_per_sm;
-    unsigned long long* work;  // persistent: ray counter, zeroed before launch
+    unsigned long long* work;  // persistent: ray counter, zeroed before launch (null:
+                               // the launch takes 8 bytes of stream-ordered scratch)
     const DevScene* dyn_user;  // dynamic dispatch: scene copy in device memory
     cudaStream_t stream;
     uint32_t stack_regs;       // traversal stack entries held in registers

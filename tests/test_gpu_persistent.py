@@ -66,6 +66,27 @@ def test_persistent_proc_alpha_any_matches_oracle(V, small, block, refill, regs)
     _compare(V, hits, ref, st, f"persistent proc any {block}/{refill}/{regs}")
 
 
+def test_persistent_launches_on_two_streams(V, small):
+    """Persistent launches of one scene on two streams may overlap: each takes
+    its own ray counter, so both give the full result."""
+    sc, rays, blob, s, d_rays = small
+    isect = V.intersector("alpha_tex")
+    ref = torch.empty((len(rays), 4), dtype=torch.float32, device="cuda")
+    V.vsr_trace(s, d_rays, isect, "closest", ref, None, V.trace_params())
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [torch.full_like(ref, -3.0) for _ in range(6)]
+    torch.cuda.synchronize()  # the fills are on the current stream
+    for k, o in enumerate(outs):
+        p = V.trace_params(block_size=128, persistent=1, refill_threshold=16, lockstep=k % 2,
+                           watchdog_ms=WD_MS)
+        V.vsr_trace(s, d_rays, isect, "closest", o, None, p, streams[k % 2])
+    torch.cuda.synchronize()
+    for o in outs:
+        assert torch.equal(o.view(torch.int32), ref.view(torch.int32))
+    assert V.vsr_get_device_error(s) == 0
+
+
 def test_noalloc_proc_alpha_any_matches_persistent(V, small):
     sc, rays, blob, s, d_rays = small
     p = V.trace_params(block_size=128, persistent=1, refill_threshold=16, watchdog_ms=WD_MS)
