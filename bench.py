@@ -1145,7 +1145,7 @@ def batch_bench(V, torch, dev, flush, stream, steps):
                   "per_scene_ms": round(tp, 3),
                   "tuned": {"block_size": p.block_size, "refill_threshold": p.refill_threshold,
                             "blocks_per_sm": p.blocks_per_sm, "stack_regs": p.stack_regs,
-                            "ray_order": p.ray_order}}
+                            "ray_order": p.ray_order, "lockstep": p.lockstep}}
     for h in handles:
         h.close()
     return out
