@@ -1199,9 +1199,20 @@ def large_bench(V, torch, dev, flush, stream, steps):
             t = timed(lambda: V.vsr_trace(s, ao, isect, "any", ao_hits, c, None, stream), reps)
             out[f"ao_any/{kind}/{disp}_Mrays_s"] = round(m / (t / 1e3) / 1e6, 1)
             out[f"ao_any/{kind}/{disp}_ms"] = round(t, 3)
+            out[f"ao_any/{kind}/{disp}_tuned"] = launch_config(
+                tuned_or_default(V, s, isect, "any"))
     for kind in ("proc_alpha", "count"):
         out[f"ao_any/{kind}/dynamic_vs_static"] = round(
             out[f"ao_any/{kind}/static_Mrays_s"] / out[f"ao_any/{kind}/dynamic_Mrays_s"], 4)
+        # the dynamic kernel in the launch shape tuned for the static one
+        # (persistent and lock-step shapes take either dispatch)
+        sp = tuned_or_default(V, s, V.intersector(kind), "any")
+        dyn = V.intersector(kind, "dynamic")
+        c = cnt if kind == "count" else None
+        t = timed(lambda: V.vsr_trace(s, ao, dyn, "any", ao_hits, c, sp, stream), reps)
+        out[f"ao_any/{kind}/dynamic_at_static_shape_ms"] = round(t, 3)
+        out[f"ao_any/{kind}/dynamic_at_static_shape_vs_static"] = round(
+            t / out[f"ao_any/{kind}/static_ms"], 4)
     # static vs dynamic at equal register budgets (both kernels compiled for
     # 1 = no budget, 3 or 4 resident 256-thread blocks per SM), block 128
     for kind in ("proc_alpha", "count", "default"):

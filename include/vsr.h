@@ -146,7 +146,8 @@ typedef enum vsr_query {
 typedef struct vsr_trace_params {
     uint32_t block_size;       /* threads per block, multiple of 32, 32..256 */
     uint32_t persistent;       /* 0: one ray per thread; 1: persistent warps
-                                  (static dispatch).  Each persistent launch
+                                  (static or dynamic dispatch; dynamic:
+                                  reg_cap_blocks 0).  Each persistent launch
                                   claims rays from a counter of its own (8
                                   bytes from the stream-ordered allocator), so
                                   launches on one scene may overlap on
@@ -210,16 +211,20 @@ typedef struct vsr_trace_params {
                                   the node loop and the primitive loop repeat
                                   while any lane needs them and every pass ends
                                   in a warp vote, so lanes that diverge meet
-                                  again at the next node; for the any-hit query
-                                  (intersectors without counters) a lane that
-                                  holds a leaf keeps descending toward its next
-                                  leaf while other lanes are still looking.
+                                  again at the next node.  Intersectors
+                                  without counters (with dynamic dispatch:
+                                  kinds without a box callback): a lane that
+                                  holds a leaf keeps descending toward its
+                                  next leaf while other lanes are still
+                                  looking (any hit; closest hit with stack_regs
+                                  0, where what the held leaf's hit culls is
+                                  undone before the lane goes on).
                                   0 = each lane runs its own loops.  The same
                                   nodes and leaves are visited in the same
                                   order either way, so results are identical.
-                                  vsr_trace and vsr_path_trace (static
-                                  dispatch, reg_cap_blocks 0) and batches;
-                                  other entry points take 0. */
+                                  vsr_trace and vsr_path_trace (static or
+                                  dynamic dispatch, reg_cap_blocks 0) and
+                                  batches; other entry points take 0. */
 } vsr_trace_params;
 
 typedef struct vsr_scene vsr_scene;
@@ -297,12 +302,11 @@ vsr_status vsr_trace(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
  * dispatch, query) by timing candidates on the caller's rays, keep it in the
  * scene for vsr_trace calls with params == NULL and return it in *out.
  * Candidates: one ray per thread with block 64, 128 or 256, 0, 1, 2, 4 or 8
- * stack entries in registers and per-lane loops or lock step (static
- * dispatch; dynamic: 0 entries, per-lane loops), starting from the default;
- * then the fastest of these in coherence order (ray_order 1, the sort timed
- * with it); then, for static dispatch, the persistent launch at the fastest
- * configuration with per-lane loops and in lock step, refill thresholds 1,
- * 8, 16 and 24.  A candidate replaces the best only when at least 2%
+ * stack entries in registers (static dispatch; dynamic: 0 entries) and
+ * per-lane loops or lock step, starting from the default; then the fastest
+ * of these in coherence order (ray_order 1, the sort timed with it); then
+ * the persistent launch at the fastest configuration with per-lane loops and
+ * in lock step, refill thresholds 1, 8, 16 and 24.  A candidate replaces the best only when at least 2%
  * faster.  The candidates take image_width (0: buffer order), except the
  * coherence-order one; all give the same hits, so only the time differs.
  * Synchronous (stream synchronised per candidate); hits is written several

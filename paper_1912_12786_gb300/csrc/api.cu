@@ -368,8 +368,8 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (prm.reg_cap_blocks == 2 || prm.reg_cap_blocks > 6)
         return fail(VSR_ERR_ARG, "reg_cap_blocks must be 0, 1, 3, 4, 5 or 6");
     if (prm.lockstep > 1) return fail(VSR_ERR_ARG, "lockstep must be 0 or 1");
-    if (prm.lockstep && (is->dispatch != VSR_DISPATCH_STATIC || prm.reg_cap_blocks))
-        return fail(VSR_ERR_ARG, "lockstep 1 takes static dispatch and reg_cap_blocks 0");
+    if (prm.lockstep && prm.reg_cap_blocks)
+        return fail(VSR_ERR_ARG, "lockstep 1 takes reg_cap_blocks 0");
     if (prm.reg_cap_blocks >= 5 && is->dispatch == VSR_DISPATCH_DYNAMIC)
         return fail(VSR_ERR_ARG, "reg_cap_blocks 5 and 6 are for static dispatch");
     if (prm.reg_cap_blocks >= 3 && is->dispatch == VSR_DISPATCH_STATIC &&
@@ -378,8 +378,8 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
         return fail(VSR_ERR_ARG,
                     "reg_cap_blocks 3 to 6 with static dispatch: one ray per thread, stack_regs "
                     "0, intersector default, alpha texture, procedural alpha or count");
-    if (prm.persistent && is->dispatch == VSR_DISPATCH_DYNAMIC)
-        return fail(VSR_ERR_ARG, "persistent launches use static dispatch only");
+    if (prm.persistent && prm.reg_cap_blocks && is->dispatch == VSR_DISPATCH_DYNAMIC)
+        return fail(VSR_ERR_ARG, "persistent launches take reg_cap_blocks 0");
     if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull)
         return fail(VSR_ERR_ARG, "too many rays for one launch");
     if (n > 0) {
@@ -448,12 +448,12 @@ cudaError_t time_params(const LaunchArgs& base, const vsr_trace_params& c, int k
 // Choose a launch configuration for (scene, intersector, query) by timing
 // candidates on the caller's rays, and remember it in the scene.  First pass:
 // one ray per thread, per-lane loops and lock step x block 64/128/256 x
-// register-stack depth 0/1/2/4/8 (static dispatch; dynamic: depth 0, per-lane
-// loops), starting from the default (128, 0, per-lane loops);
-// then the best of these in coherence order (its sort timed with it); last
-// (static dispatch): the persistent launch at the best configuration with
-// per-lane loops and in lock step, refill thresholds 1/8/16/24.  Every
-// candidate but the coherence-order one keeps the caller's image_width.
+// register-stack depth 0/1/2/4/8 (static dispatch; dynamic: depth 0),
+// starting from the default (128, 0, per-lane loops); then the best of these
+// in coherence order (its sort timed with it); last, the persistent launch at
+// the best configuration with per-lane loops and in lock step, refill
+// thresholds 1/8/16/24.  Every candidate but the coherence-order one keeps
+// the caller's image_width.
 vsr_status tune_trace(vsr_scene* s, const LaunchArgs& base, const vsr_intersector* is,
                       int32_t query, uint32_t image_width, vsr_trace_params* out) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -484,7 +484,7 @@ vsr_status tune_trace(vsr_scene* s, const LaunchArgs& base, const vsr_intersecto
     for (uint32_t ls : {0u, 1u})
         for (uint32_t b : {64u, 128u, 256u})
             for (uint32_t k : {0u, 1u, 2u, 4u, 8u})
-                if ((!dynamic || (k == 0 && ls == 0)) && !(b == 128u && k == 0u && ls == 0u))
+                if ((!dynamic || k == 0) && !(b == 128u && k == 0u && ls == 0u))
                     consider(vsr_trace_params{b, 0u, 16u, 0u, image_width, k, 0u, 0u, 0u, 0u, ls});
     if (base.n <= coherence_sort_max_rays()) {
         // the fastest one-ray-per-thread configuration in coherence order
@@ -494,7 +494,7 @@ vsr_status tune_trace(vsr_scene* s, const LaunchArgs& base, const vsr_intersecto
         c.ray_order = 1;
         consider(c);
     }
-    if (!dynamic) {
+    {
         const vsr_trace_params one = best;
         for (uint32_t ls : {0u, 1u})
             for (uint32_t r : {1u, 8u, 16u, 24u}) {

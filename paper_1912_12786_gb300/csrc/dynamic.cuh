@@ -78,6 +78,9 @@ __global__ void k_dyn_register() {
 struct IsectDynamic {
     static constexpr bool kCounts = true;
     static constexpr bool kTexcoords = false;
+    // lock-step descent may speculate past a held leaf when the bound kind
+    // has no box callback (box_hooks_silent below decides for each ray)
+    static constexpr bool kMaySpeculate = true;
     AcceptFn acc = nullptr;
     CountFn on_box = nullptr, on_tri = nullptr;
     const DevScene* user = nullptr;
@@ -116,6 +119,19 @@ __device__ __forceinline__ void set_callback_scene(IsectDynamic& h, const DevSce
 }
 template <class H>
 __device__ __forceinline__ void set_callback_scene(H&, const DevScene*) {}
+
+// The box hooks observe nothing when the bound kind registered no box
+// callback (every kind but count).
+__device__ __forceinline__ bool box_hooks_silent(const IsectDynamic& h) {
+    return h.on_box == nullptr;
+}
+
+// Per-ray setup in the persistent loop: bind the callbacks and their scene.
+__device__ __forceinline__ void isect_setup(IsectDynamic& h, const IsectParams& ip,
+                                            const DevScene* user) {
+    bind_callbacks(h, ip);
+    set_callback_scene(h, user);
+}
 
 std::mutex g_dyn_reg_mutex;
 bool g_dyn_registered[64] = {};

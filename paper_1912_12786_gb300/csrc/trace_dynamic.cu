@@ -2,8 +2,11 @@
 // function pointers (dynamic.cuh), the callback approach of the libraries
 // that the paper contrasts with static injection (Sections 1 and 5).  The
 // traversal itself is the same template as the static kernels, so the two
-// variants differ only in how the intersector is reached.
+// variants differ only in how the intersector is reached.  Persistent and
+// lock-step launches take the static launch shapes (trace_static.cuh) with
+// the dynamic intersector as their template argument.
 #include "dynamic.cuh"
+#include "trace_static.cuh"
 
 namespace vsr {
 
@@ -37,10 +40,23 @@ __global__ void __launch_bounds__(256, MINB)
     if (counters) counters[i] = h.counters();
 }
 
+// Persistent warps (per-lane loops or lock step) and one ray per thread in
+// lock step, uncapped: the callbacks are bound per ray by isect_setup.
+template <int Q>
+cudaError_t launch_dynamic_shape(const LaunchArgs& a) {
+    if (a.persistent)
+        return a.lockstep ? detail::launch_persistent<Q, IsectDynamic, false, 0, true>(a)
+                          : detail::launch_persistent<Q, IsectDynamic, false, 0, false>(a);
+    return detail::launch_shape<Q, IsectDynamic, false, 0, true>(a);
+}
+
 cudaError_t launch_dynamic(const LaunchArgs& a, int kind) {
     (void)kind;
     cudaError_t e0 = ensure_callbacks_registered();
     if (e0 != cudaSuccess) return e0;
+    if (a.persistent || a.lockstep)
+        return a.query == kClosest ? launch_dynamic_shape<kClosest>(a)
+                                   : launch_dynamic_shape<kAny>(a);
     const size_t smem = (size_t)a.sc.stack_depth * a.block * sizeof(uint32_t);
     const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
     const uint32_t cap = a.reg_cap ? a.reg_cap : (a.query == kClosest ? 3u : 4u);

@@ -58,13 +58,15 @@ __global__ void __launch_bounds__(256) k_trace_ls(DevScene sc, IsectParams ip,
                                                   const float4* __restrict__ rays,
                                                   RayMap map, float4* __restrict__ hits,
                                                   uint2* __restrict__ counters,
-                                                  uint4* __restrict__ stats) {
+                                                  uint4* __restrict__ stats,
+                                                  const DevScene* __restrict__ user) {
     extern __shared__ uint32_t s_stack[];
     const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long i = g < map.threads ? ray_of_thread(g, map) : map.n;
     bool busy = i < map.n;
     Ray r;
     H h;
+    isect_setup(h, ip, user);
     Best best;
     Stats st;
     ShortStack<K> stk;
@@ -139,7 +141,8 @@ template <int Q, class H, bool STATS, int K, bool LS>
 __global__ void __launch_bounds__(256) k_trace_persistent(
     DevScene sc, IsectParams ip, const float4* __restrict__ rays, RayMap map,
     float4* __restrict__ hits, uint2* __restrict__ counters, uint4* __restrict__ stats,
-    unsigned long long* __restrict__ work, uint32_t refill, Watchdog wd) {
+    unsigned long long* __restrict__ work, uint32_t refill, Watchdog wd,
+    const DevScene* __restrict__ user) {
     extern __shared__ uint32_t s_stack[];
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -184,6 +187,7 @@ __global__ void __launch_bounds__(256) k_trace_persistent(
                 if (ri < map.n) {
                     r = make_ray(VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
                     h = H();
+                    isect_setup(h, ip, user);
                     st = Stats();
                     has = true;
                     more = true;
@@ -224,20 +228,14 @@ cudaError_t ensure_smem(Kern kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// The persistent launch (also the dynamic dispatcher's, with H =
+// IsectDynamic and a.dyn_user the scene copy its callbacks see; the static
+// intersectors ignore it).
 template <int Q, class H, bool STATS, int K, bool LS>
-cudaError_t launch_shape(const LaunchArgs& a) {
+cudaError_t launch_persistent(const LaunchArgs& a) {
     const uint32_t words = stack_words(a.sc.stack_depth, K) +
                            (LS ? spec_words<Q, H, STATS, K>(a.sc.stack_depth) : 0u);
     const size_t smem = (size_t)words * a.block * sizeof(uint32_t);
-    if (!a.persistent) {
-        auto k = LS ? k_trace_ls<Q, H, STATS, K> : k_trace<Q, H, STATS, K>;
-        cudaError_t e = ensure_smem(k, smem);
-        if (e != cudaSuccess) return e;
-        const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
-        k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits,
-                                                         a.counters, a.stats);
-        return cudaGetLastError();
-    }
     auto k = k_trace_persistent<Q, H, STATS, K, LS>;
     cudaError_t e = ensure_smem(k, smem);
     if (e != cudaSuccess) return e;
@@ -253,7 +251,7 @@ cudaError_t launch_shape(const LaunchArgs& a) {
     e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), a.stream);
     if (e == cudaSuccess) {
         k<<<grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits, a.counters,
-                                             a.stats, work, a.refill, a.wd);
+                                             a.stats, work, a.refill, a.wd, a.dyn_user);
         e = cudaGetLastError();
     }
     if (!a.work) {
@@ -261,6 +259,29 @@ cudaError_t launch_shape(const LaunchArgs& a) {
         if (e == cudaSuccess) e = f;
     }
     return e;
+}
+
+template <int Q, class H, bool STATS, int K, bool LS>
+cudaError_t launch_shape(const LaunchArgs& a) {
+    if (a.persistent) return launch_persistent<Q, H, STATS, K, LS>(a);
+    const uint32_t words = stack_words(a.sc.stack_depth, K) +
+                           (LS ? spec_words<Q, H, STATS, K>(a.sc.stack_depth) : 0u);
+    const size_t smem = (size_t)words * a.block * sizeof(uint32_t);
+    const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
+    if constexpr (LS) {
+        auto k = k_trace_ls<Q, H, STATS, K>;
+        cudaError_t e = ensure_smem(k, smem);
+        if (e != cudaSuccess) return e;
+        k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits,
+                                                         a.counters, a.stats, a.dyn_user);
+    } else {
+        auto k = k_trace<Q, H, STATS, K>;
+        cudaError_t e = ensure_smem(k, smem);
+        if (e != cudaSuccess) return e;
+        k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits,
+                                                         a.counters, a.stats);
+    }
+    return cudaGetLastError();
 }
 
 template <int Q, class H, bool STATS, int K>

@@ -324,6 +324,10 @@ __device__ __forceinline__ bool proc_alpha_accept(const DevScene& sc, const Isec
 struct IsectNone {
     static constexpr bool kCounts = false;
     static constexpr bool kTexcoords = false;  // reads geom id and texcoords
+    // box hooks that may observe nothing, so that a lane may test boxes
+    // ahead of the plain order (warp_step); whether they do for a ray is
+    // box_hooks_silent's answer
+    static constexpr bool kMaySpeculate = true;
     __device__ __forceinline__ void begin(const Ray&, const IsectParams&) {}
     __device__ __forceinline__ void box() {}
     __device__ __forceinline__ void tri() {}
@@ -358,6 +362,7 @@ struct IsectProcAlpha : IsectNone {
 // bvh_costs: ++num_boxes per box test, ++num_tris per triangle test.
 struct IsectCount : IsectNone {
     static constexpr bool kCounts = true;
+    static constexpr bool kMaySpeculate = false;  // every box test is counted
     uint32_t num_boxes = 0, num_tris = 0;
     __device__ __forceinline__ void box() { ++num_boxes; }
     __device__ __forceinline__ void tri() { ++num_tris; }
@@ -754,19 +759,33 @@ __device__ __forceinline__ bool test_prim(const DevScene& sc, const IsectParams&
     return Q == kAny;
 }
 
-// Where a lane that holds a leaf may keep descending (warp_step), for an
-// intersector whose box hooks observe nothing (no counters) and no
-// measurement counters.  Any hit: the far limit is the ray's tmax, which
+// Where a lane that holds a leaf may keep descending (warp_step): an
+// intersector whose box hooks may observe nothing, and no measurement
+// counters (box_hooks_silent then decides for the ray, at compile time for
+// the static intersectors).  Any hit: the far limit is the ray's tmax, which
 // never changes, so speculation needs no bookkeeping.  Closest hit: the far
 // limit shrinks when the held leaf improves the result, so speculation
 // records entry distances (in a shared-memory column beside the stack's,
 // for the shared-memory stack, K == 0) and undoes what the new limit culls.
 template <int Q, class H, bool STATS, int K>
 struct Speculate {
-    static constexpr bool any = Q == kAny && !H::kCounts && !STATS;
-    static constexpr bool closest = Q == kClosest && !H::kCounts && !STATS && K == 0;
+    static constexpr bool any = Q == kAny && H::kMaySpeculate && !STATS;
+    static constexpr bool closest = Q == kClosest && H::kMaySpeculate && !STATS && K == 0;
     static constexpr bool value = any || closest;
 };
+
+// Whether h's box hooks observe nothing (a static intersector: unless it
+// counts).  The dynamic intersector overloads this with a run-time answer.
+template <class H>
+__device__ __forceinline__ bool box_hooks_silent(const H&) {
+    return !H::kCounts;
+}
+
+// Per-ray setup of the intersector of a ray a persistent loop claims: none
+// for the static intersectors; the dynamic intersector overloads this to
+// bind its callbacks.
+template <class H>
+__device__ __forceinline__ void isect_setup(H&, const IsectParams&, const DevScene*) {}
 
 // A reached leaf is held for testing and the next node taken from the stack.
 template <class S>
@@ -820,22 +839,22 @@ __device__ __forceinline__ bool warp_step(const DevScene& sc, const IsectParams&
                                           uint32_t& ref, bool& more, uint32_t& leaf, bool& pend,
                                           uint32_t& steps, S& stk, float* tcol) {
     using Spec = Speculate<Q, H, STATS, S::kRegs>;
-    constexpr bool kSpec = Spec::value;
-    constexpr bool kTrack = Spec::closest;
+    const bool spec = Spec::value && box_hooks_silent(h);
+    const bool track = Spec::closest && spec;
     const float kNegInf = -__int_as_float(0x7f800000);
     bool done = false;
-    uint32_t sbase = 0;           // kTrack: entries at or above were pushed speculating
-    float path = kNegInf;         // kTrack: largest entry distance on the way to ref
-    float tf0 = 0.0f;             // kTrack: the far limit speculation used
+    uint32_t sbase = 0;           // track: entries at or above were pushed speculating
+    float path = kNegInf;         // track: largest entry distance on the way to ref
+    float tf0 = 0.0f;             // track: the far limit speculation used
     if (busy) hold_leaf(ref, more, leaf, pend, stk);
-    if (kTrack && busy && pend) {
+    if (track && busy && pend) {
         sbase = stk.n;
         tf0 = h.far(best.t);
     }
     for (;;) {  // while some lane is still looking for a leaf
         const bool seek = busy && !done && more && !pend;  // then ref is an inner node
         if (!__any_sync(kFullMask, seek)) break;
-        if (busy && !done && more && !(ref & kLeafBit) && (kSpec || !pend)) {
+        if (busy && !done && more && !(ref & kLeafBit) && (spec || !pend)) {
             if (++steps > sc.max_steps) {
                 atomicOr(sc.err, kErrSteps);
                 best.fail();
@@ -859,20 +878,20 @@ __device__ __forceinline__ bool warp_step(const DevScene& sc, const IsectParams&
                         best.fail();
                         done = true;
                     } else {
-                        if (kTrack) tcol[stk.n * stk.stride] = fmaxf(path, neg ? tnl : tnr);
+                        if (track) tcol[stk.n * stk.stride] = fmaxf(path, neg ? tnl : tnr);
                         stk.push(neg ? rl : rr);
                         ref = neg ? rr : rl;
-                        if (kTrack) path = fmaxf(path, neg ? tnr : tnl);
+                        if (track) path = fmaxf(path, neg ? tnr : tnl);
                     }
                 } else if (hl) {
                     ref = rl;
-                    if (kTrack) path = fmaxf(path, tnl);
+                    if (track) path = fmaxf(path, tnl);
                 } else if (hr) {
                     ref = rr;
-                    if (kTrack) path = fmaxf(path, tnr);
+                    if (track) path = fmaxf(path, tnr);
                 } else if (stk.n) {
                     ref = stk.pop();
-                    if (kTrack) {
+                    if (track) {
                         if (stk.n >= sbase) {
                             path = tcol[stk.n * stk.stride];
                         } else {  // an entry of the plain order
@@ -886,7 +905,7 @@ __device__ __forceinline__ bool warp_step(const DevScene& sc, const IsectParams&
                 if (!done) {
                     const bool held = pend;
                     hold_leaf(ref, more, leaf, pend, stk);
-                    if (kTrack && pend && !held) {  // speculation starts here
+                    if (track && pend && !held) {  // speculation starts here
                         sbase = stk.n;
                         path = kNegInf;
                         tf0 = h.far(best.t);
@@ -915,7 +934,7 @@ __device__ __forceinline__ bool warp_step(const DevScene& sc, const IsectParams&
         }
     }
     if (busy && !done) {
-        if (kTrack && pend) {
+        if (track && pend) {
             const float tf = h.far(best.t);
             if (tf < tf0) {  // the leaf lowered the far limit: drop what it culls
                 uint32_t j = sbase;

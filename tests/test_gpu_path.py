@@ -81,6 +81,9 @@ def test_tiles_and_dynamic_dispatch_agree(V, small):
                              watchdog_ms=10_000)):
         d, sd = _gpu(V, s, rays, "alpha_tex", 3, dirs, p)
         assert np.array_equal(a.view(np.uint32), d.view(np.uint32)) and np.array_equal(sa, sd)
+        # the same shapes with the callbacks reached through the tables
+        d, sd = _gpu(V, s, rays, "alpha_tex", 3, dirs, p, dispatch="dynamic")
+        assert np.array_equal(a.view(np.uint32), d.view(np.uint32)) and np.array_equal(sa, sd)
 
 
 def test_ragged_sizes(V, small):

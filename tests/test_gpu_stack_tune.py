@@ -80,6 +80,62 @@ def test_lockstep_matches_oracle(V, small, kind, query):
     assert V.vsr_get_device_error(s) == 0
 
 
+@pytest.mark.parametrize("query", ["closest", "any"])
+@pytest.mark.parametrize("kind", ["default", "alpha_tex", "proc_alpha", "count"])
+def test_dynamic_persistent_and_lockstep_match_oracle(V, small, kind, query):
+    """Dynamic dispatch (callbacks bound per ray through the function-pointer
+    tables) in the persistent and lock-step launch shapes: per-lane loops and
+    lock step, persistent and one ray per thread, pixel tiles and buffer
+    order.  Speculative descent runs for the kinds without a box callback;
+    count (box and triangle callbacks) keeps every lane's box tests, and its
+    counters match the oracle's."""
+    sc, rays, blob, s, d_rays = small
+    ref, st = O.trace_bvh(sc, blob, rays, kind, query)
+    configs = [dict(block_size=128, lockstep=1),
+               dict(block_size=64, lockstep=1, image_width=256),
+               dict(block_size=256, persistent=1, refill_threshold=24, watchdog_ms=10_000),
+               dict(block_size=96, persistent=1, refill_threshold=8, lockstep=1,
+                    watchdog_ms=10_000),
+               dict(block_size=128, persistent=1, refill_threshold=32, lockstep=1,
+                    image_width=256, watchdog_ms=10_000)]
+    for c in configs:
+        p = V.trace_params(**c)
+        hits, cnt = V.trace(s, d_rays, kind, query, dispatch="dynamic",
+                            counters=(kind == "count"), params=p)
+        _same_as_oracle(hits, ref, st, f"dynamic {kind}/{query}/{c}")
+        if kind == "count":
+            assert np.array_equal(cnt.cpu().numpy().view(np.uint32), st[:, :2])
+    assert V.vsr_get_device_error(s) == 0
+
+
+def test_dynamic_persistent_ragged(V):
+    """Dynamic dispatch, persistent and lock step, on ray counts that leave
+    partly filled warps, and with register budgets refused."""
+    sc, rays = scenes.small_quads(seed=scenes.SEED_BASE + 45)
+    blob = sc.bvh()
+    s = V.scene_from_inputs(sc, blob)
+    for n in (1, 33, 4097):
+        sub = np.ascontiguousarray(rays[:n])
+        for q in ("closest", "any"):
+            ref, st = O.trace_bvh(sc, blob, sub, "proc_alpha", q)
+            for pers, ls in ((1, 0), (1, 1), (0, 1)):
+                hits, _ = V.trace(s, torch.from_numpy(sub).cuda(), "proc_alpha", q,
+                                  dispatch="dynamic",
+                                  params=V.trace_params(lockstep=ls, persistent=pers,
+                                                        watchdog_ms=10_000))
+                _same_as_oracle(hits, ref, st, f"dynamic n={n} {q} pers={pers} ls={ls}")
+    hits = torch.empty((len(rays), 4), dtype=torch.float32, device="cuda")
+    d_rays = torch.from_numpy(rays).cuda()
+    with pytest.raises(V.VsrError, match="reg_cap_blocks 0"):
+        V.vsr_trace(s, d_rays, V.intersector("default", "dynamic"), "closest", hits, None,
+                    V.trace_params(persistent=1, reg_cap_blocks=3))
+    with pytest.raises(V.VsrError, match="reg_cap_blocks 0"):
+        V.vsr_trace(s, d_rays, V.intersector("default", "dynamic"), "any", hits, None,
+                    V.trace_params(lockstep=1, reg_cap_blocks=4))
+    assert V.vsr_get_device_error(s) == 0
+    s.close()
+
+
 def test_lockstep_ragged_and_single_leaf(V):
     """Ray counts that leave partly filled warps (1, 33, 4,097 rays) and a
     scene whose BVH is one leaf (the root itself), in lock step."""
@@ -111,9 +167,6 @@ def test_lockstep_ragged_and_single_leaf(V):
 def test_lockstep_rejected_where_unsupported(V, small):
     sc, rays, blob, s, d_rays = small
     hits = torch.empty((len(rays), 4), dtype=torch.float32, device="cuda")
-    with pytest.raises(V.VsrError, match="lockstep"):
-        V.vsr_trace(s, d_rays, V.intersector("default", "dynamic"), "closest", hits, None,
-                    V.trace_params(lockstep=1))
     with pytest.raises(V.VsrError, match="lockstep"):
         V.vsr_trace(s, d_rays, V.intersector("default"), "closest", hits, None,
                     V.trace_params(lockstep=2))
@@ -150,7 +203,8 @@ def test_trace_coherence_order_matches_oracle(V, small, kind, query, dispatch):
         configs += [dict(block_size=128, persistent=1, refill_threshold=16, stack_regs=4,
                          watchdog_ms=10_000)]
     else:
-        configs = configs[:1]
+        configs = configs[:1] + [dict(block_size=128, persistent=1, refill_threshold=16,
+                                      lockstep=1, watchdog_ms=10_000)]
     for c in configs:
         p = V.trace_params(ray_order=1, **c)
         hits, cnt = V.trace(s, d_rays, kind, query, dispatch=dispatch,
@@ -208,7 +262,8 @@ def test_stack_depth_rejected_when_unsupported(V, small):
                                                  ("alpha_tex", "any", "static"),
                                                  ("proc_alpha", "any", "static"),
                                                  ("count", "closest", "static"),
-                                                 ("alpha_tex", "closest", "dynamic")])
+                                                 ("alpha_tex", "closest", "dynamic"),
+                                                 ("count", "any", "dynamic")])
 def test_null_params_use_the_tuned_configuration(V, kind, query, dispatch):
     sc, rays = scenes.small_quads(seed=scenes.SEED_BASE + 40)
     blob = sc.bvh()
@@ -222,8 +277,7 @@ def test_null_params_use_the_tuned_configuration(V, kind, query, dispatch):
     # the tiled map, or the coherence order (which replaces it)
     assert (p["image_width"], p["ray_order"]) in ((256, 0), (0, 1))
     assert p["stack_regs"] in ((0, 1, 2, 4, 8) if dispatch == "static" else (0,))
-    if dispatch == "dynamic":
-        assert p["persistent"] == 0
+    assert p["reg_cap_blocks"] == 0 and p["lockstep"] in (0, 1) and p["persistent"] in (0, 1)
     a = torch.full((len(rays), 4), -3.0, dtype=torch.float32, device="cuda")
     b = torch.full_like(a, -4.0)
     V.vsr_trace(s, d_rays, isect, query, a, None, None)          # tuned (cached)
