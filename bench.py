@@ -877,6 +877,24 @@ def multi_hit(V, s, d_rays, n, flush, stream, torch, reps=5):
                 found = int((hits[:, :, 3].view(torch.int32) != -1).sum().item())
                 res[f"n{nh}_hits_per_ray"] = round(found / n, 3)
         res[f"n{nh}_dynamic_vs_static"] = round(res[f"dynamic_n{nh}_ms"] / res[f"n{nh}_ms"], 4)
+        # persistent warps, per-lane loops and lock step (static dispatch)
+        alpha = V.intersector("alpha_tex")
+        for tag, pp in (("persistent", V.trace_params(persistent=1, refill_threshold=16,
+                                                      image_width=p.image_width)),
+                        ("persistent_ls", V.trace_params(persistent=1, refill_threshold=16,
+                                                         lockstep=1,
+                                                         image_width=p.image_width))):
+            ms = []
+            for r in range(reps + 2):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                V.vsr_trace_multi(s, d_rays, alpha, nh, hits, None, pp, stream)
+                e1.record(stream)
+                e1.synchronize()
+                if r >= 2:
+                    ms.append(e0.elapsed_time(e1))
+            res[f"{tag}_n{nh}_ms"] = round(statistics.median(ms), 4)
     return res
 
 
@@ -933,7 +951,12 @@ def instanced_bench(V, torch, dev, flush, stream, steps):
     eps = float(np.float32(1e-4 * 100.0 * math.sqrt(3)))
     p = default_params(V)
     times = {}
-    for disp in ("static", "dynamic"):
+    shapes = {"static": ("static", p), "dynamic": ("dynamic", p),
+              "persistent": ("static", V.trace_params(persistent=1, refill_threshold=16,
+                                                      image_width=p.image_width)),
+              "dynamic_persistent": ("dynamic", V.trace_params(persistent=1, refill_threshold=16,
+                                                               image_width=p.image_width))}
+    for name, (disp, p) in shapes.items():
         alpha = V.intersector("alpha_tex", disp, cutoff_u8=128)
         ms_prim, ms_shad = [], []
         for k in range(max(3, steps // 2) + 2):
@@ -950,9 +973,11 @@ def instanced_bench(V, torch, dev, flush, stream, steps):
             if k >= 2:
                 ms_prim.append(ev[0].elapsed_time(ev[1]))
                 ms_shad.append(ev[2].elapsed_time(ev[3]))
-        times[disp] = (statistics.median(ms_prim), statistics.median(ms_shad))
+        times[name] = (statistics.median(ms_prim), statistics.median(ms_shad))
     tp, ts = times["static"]
     dp, ds = times["dynamic"]
+    pp_, ps_ = times["persistent"]
+    dpp, dps = times["dynamic_persistent"]
     tile = I.meshes[0]
     X.close()
     for m in ms:
@@ -965,6 +990,9 @@ def instanced_bench(V, torch, dev, flush, stream, steps):
             "dynamic_primary_ms": round(dp, 4), "dynamic_shadow_ms": round(ds, 4),
             "dynamic_vs_static_primary": round(dp / tp, 4),
             "dynamic_vs_static_shadow": round(ds / ts, 4),
+            "persistent_primary_ms": round(pp_, 4), "persistent_shadow_ms": round(ps_, 4),
+            "dynamic_persistent_primary_ms": round(dpp, 4),
+            "dynamic_persistent_shadow_ms": round(dps, 4),
             "step_Mrays_s": round(2 * n / ((tp + ts) / 1e3) / 1e6, 1),
             "triangles_stored": sum(m.ntri for m in I.meshes),
             "triangles_instanced": int(sum(I.meshes[k].ntri for k in I.inst_mesh))}
@@ -1228,6 +1256,13 @@ def large_bench(V, torch, dev, flush, stream, steps):
             out[f"ao_any/equal_regs/{kind}/cap{cap}/dynamic_ms"] = round(t["dynamic"], 3)
             out[f"ao_any/equal_regs/{kind}/cap{cap}/dynamic_vs_static"] = round(
                 t["dynamic"] / t["static"], 4)
+            # the dynamic kernel's persistent shapes under the same budget
+            dyn = V.intersector(kind, "dynamic")
+            for tag, ls in (("persistent", 0), ("persistent_ls", 1)):
+                cp = V.trace_params(block_size=128, persistent=1, refill_threshold=16,
+                                    lockstep=ls, reg_cap_blocks=cap)
+                tt = timed(lambda: V.vsr_trace(s, ao, dyn, "any", ao_hits, c, cp, stream), reps)
+                out[f"ao_any/equal_regs/{kind}/cap{cap}/dynamic_{tag}_ms"] = round(tt, 3)
     st = torch.empty((m, 4), dtype=torch.int32, device=dev)
     V.vsr_trace_stats(s, ao, proc, "any", ao_hits, st, stream)
     torch.cuda.synchronize(dev)

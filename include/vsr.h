@@ -146,8 +146,9 @@ typedef enum vsr_query {
 typedef struct vsr_trace_params {
     uint32_t block_size;       /* threads per block, multiple of 32, 32..256 */
     uint32_t persistent;       /* 0: one ray per thread; 1: persistent warps
-                                  (static or dynamic dispatch; dynamic:
-                                  reg_cap_blocks 0).  Each persistent launch
+                                  (static or dynamic dispatch; vsr_trace,
+                                  vsr_trace_multi, vsr_trace_instances,
+                                  vsr_path_trace).  Each persistent launch
                                   claims rays from a counter of its own (8
                                   bytes from the stream-ordered allocator), so
                                   launches on one scene may overlap on
@@ -183,16 +184,17 @@ typedef struct vsr_trace_params {
                                   budget per warp, checked every 256
                                   iterations; 0 = 60000 ms, 0xFFFFFFFF = no
                                   limit.  Running out acts as above. */
-    uint32_t reg_cap_blocks;   /* register budget of vsr_trace's one-ray-per-
-                                  thread kernels, for measurement: 0 = each
-                                  kernel's own (static: none; dynamic: 3
-                                  blocks for closest hit, 4 for any hit);
-                                  1 = none; 3 or 4 = compiled to fit that many
-                                  256-thread blocks per SM (static: stack_regs
-                                  0, intersectors default, alpha texture,
-                                  procedural alpha and count); 5 or 6 likewise,
-                                  static dispatch only.  Results are identical
-                                  for every value. */
+    uint32_t reg_cap_blocks;   /* register budget of vsr_trace's kernels, for
+                                  measurement: 0 = each kernel's own (static:
+                                  none; dynamic: 3 blocks for closest hit, 4
+                                  for any hit); 1 = none; 3 or 4 = compiled to
+                                  fit that many 256-thread blocks per SM
+                                  (static: one ray per thread with per-lane
+                                  loops, stack_regs 0, intersectors default,
+                                  alpha texture, procedural alpha and count;
+                                  dynamic: every launch shape); 5 or 6
+                                  likewise, static dispatch only.  Results are
+                                  identical for every value. */
     uint32_t ray_order;        /* 0 = rays in the caller's order (or pixel
                                   tiles); 1 = coherence order: every launch
                                   first sorts the rays by a key of scene,
@@ -223,8 +225,9 @@ typedef struct vsr_trace_params {
                                   nodes and leaves are visited in the same
                                   order either way, so results are identical.
                                   vsr_trace and vsr_path_trace (static or
-                                  dynamic dispatch, reg_cap_blocks 0) and
-                                  batches; other entry points take 0. */
+                                  dynamic dispatch; static: reg_cap_blocks 0),
+                                  vsr_trace_multi (persistent 1) and batches;
+                                  other entry points take 0. */
 } vsr_trace_params;
 
 typedef struct vsr_scene vsr_scene;
@@ -338,7 +341,14 @@ vsr_status vsr_trace_tuned_params(vsr_scene* scene, const vsr_intersector* isect
  *             prim = VSR_MISS)
  *   counters  as vsr_trace (COUNT intersector only), or NULL
  *   max_hits  1..16; static or dynamic dispatch (the callbacks as for
- *             vsr_trace); params->persistent must be 0
+ *             vsr_trace)
+ *   params    one ray per thread, or persistent warps (persistent 1, refill
+ *             threshold, blocks per SM, watchdog as for vsr_trace) with
+ *             per-lane loops or in lock step (lockstep 1 takes persistent
+ *             1; speculation as for the closest-hit query, the buffer's
+ *             last entry as the far limit); image_width allowed; stack in
+ *             shared memory (stack_regs ignored).  Results are identical
+ *             in every configuration.
  * Errors as vsr_trace.
  */
 vsr_status vsr_trace_multi(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
@@ -426,9 +436,13 @@ vsr_status vsr_instances_destroy(vsr_instances* instances);
  * (COUNT) include the top-level box tests.
  *   hits      device vsr_hit [n]: prim_id is the mesh's primitive id
  *   inst_ids  device uint32 [n] (VSR_MISS on a miss) or NULL
- *   params    one ray per thread (persistent 0); image_width allowed
- * Errors as vsr_trace.  Traversal errors of the top level go to the set's
- * error word (vsr_instances_device_error), those inside a mesh to the mesh's.
+ *   params    one ray per thread, or persistent warps with per-lane loops
+ *             (persistent 1, refill threshold, blocks per SM, watchdog as
+ *             for vsr_trace; lockstep and ray_order 0); image_width
+ *             allowed.  Results are identical in every configuration.
+ * Errors as vsr_trace.  Traversal errors of the top level (and the watchdog's
+ * VSR_DEVERR_TIMEOUT) go to the set's error word
+ * (vsr_instances_device_error), those inside a mesh to the mesh's.
  */
 vsr_status vsr_trace_instances(vsr_instances* instances, const vsr_ray* rays, uint64_t n,
                                const vsr_intersector* isect, int32_t query, vsr_hit* hits,
@@ -436,7 +450,7 @@ vsr_status vsr_trace_instances(vsr_instances* instances, const vsr_ray* rays, ui
                                const vsr_trace_params* params, vsr_stream stream);
 
 /* Read and clear the instance set's device error word (synchronous; bits as
- * vsr_get_device_error's 0, 1 and 2). */
+ * vsr_get_device_error's 0, 1, 2 and 4). */
 vsr_status vsr_instances_device_error(vsr_instances* instances, uint32_t* word);
 
 /*

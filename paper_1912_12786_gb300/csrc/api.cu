@@ -368,8 +368,8 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (prm.reg_cap_blocks == 2 || prm.reg_cap_blocks > 6)
         return fail(VSR_ERR_ARG, "reg_cap_blocks must be 0, 1, 3, 4, 5 or 6");
     if (prm.lockstep > 1) return fail(VSR_ERR_ARG, "lockstep must be 0 or 1");
-    if (prm.lockstep && prm.reg_cap_blocks)
-        return fail(VSR_ERR_ARG, "lockstep 1 takes reg_cap_blocks 0");
+    if (prm.lockstep && prm.reg_cap_blocks && is->dispatch == VSR_DISPATCH_STATIC)
+        return fail(VSR_ERR_ARG, "lockstep 1 with static dispatch takes reg_cap_blocks 0");
     if (prm.reg_cap_blocks >= 5 && is->dispatch == VSR_DISPATCH_DYNAMIC)
         return fail(VSR_ERR_ARG, "reg_cap_blocks 5 and 6 are for static dispatch");
     if (prm.reg_cap_blocks >= 3 && is->dispatch == VSR_DISPATCH_STATIC &&
@@ -378,8 +378,6 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
         return fail(VSR_ERR_ARG,
                     "reg_cap_blocks 3 to 6 with static dispatch: one ray per thread, stack_regs "
                     "0, intersector default, alpha texture, procedural alpha or count");
-    if (prm.persistent && prm.reg_cap_blocks && is->dispatch == VSR_DISPATCH_DYNAMIC)
-        return fail(VSR_ERR_ARG, "persistent launches take reg_cap_blocks 0");
     if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull)
         return fail(VSR_ERR_ARG, "too many rays for one launch");
     if (n > 0) {
@@ -822,8 +820,8 @@ vsr_status vsr_trace_multi(vsr_scene* s, const vsr_ray* rays, uint64_t n,
                            uint32_t* counters, const vsr_trace_params* p, vsr_stream stream) {
     g_err.clear();
     if (max_hits < 1 || max_hits > 16) return fail(VSR_ERR_ARG, "max_hits must be in 1..16");
-    if (p && p->persistent) return fail(VSR_ERR_ARG, "the multi-hit query uses one ray per thread");
-    if (p && p->lockstep) return fail(VSR_ERR_ARG, "lockstep 1 is for vsr_trace, path tracing and batches");
+    if (p && p->lockstep && !p->persistent)
+        return fail(VSR_ERR_ARG, "the multi-hit query runs lockstep 1 with persistent 1");
     LaunchArgs a;
     vsr_status st = prepare_launch(s, rays, n, is, VSR_CLOSEST, hits, p, a);
     if (st != VSR_OK) return st;
@@ -2029,8 +2027,12 @@ extern "C" vsr_status vsr_trace_instances(vsr_instances* x, const vsr_ray* rays,
     if (p) prm = *p;
     if (prm.block_size < 32 || prm.block_size > 256 || prm.block_size % 32)
         return fail(VSR_ERR_ARG, "block_size must be a multiple of 32 in 32..256");
-    if (prm.persistent) return fail(VSR_ERR_ARG, "instanced traces use one ray per thread");
-    if (prm.lockstep) return fail(VSR_ERR_ARG, "lockstep 1 is for vsr_trace, path tracing and batches");
+    if (prm.persistent > 1) return fail(VSR_ERR_ARG, "persistent must be 0 or 1");
+    if (prm.refill_threshold < 1 || prm.refill_threshold > 32)
+        return fail(VSR_ERR_ARG, "refill_threshold must be in 1..32");
+    if (prm.blocks_per_sm > 32) return fail(VSR_ERR_ARG, "blocks_per_sm above 32");
+    if (prm.lockstep) return fail(VSR_ERR_ARG, "instanced traces take lockstep 0");
+    if (prm.ray_order) return fail(VSR_ERR_ARG, "instanced traces take ray_order 0");
     if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull)
         return fail(VSR_ERR_ARG, "too many rays for one launch");
     InstLaunch L{};
@@ -2056,6 +2058,10 @@ extern "C" vsr_status vsr_trace_instances(vsr_instances* x, const vsr_ray* rays,
     L.block = prm.block_size;
     L.stack_words = x->stack_words;
     L.stream = reinterpret_cast<cudaStream_t>(stream);
+    L.persistent = prm.persistent;
+    L.refill = prm.refill_threshold;
+    L.blocks_per_sm = prm.blocks_per_sm;
+    L.wd = make_watchdog(prm);
     DeviceGuard g(x->device);
     cudaError_t e = launch_instances(L, is->kind, query, is->dispatch == VSR_DISPATCH_DYNAMIC);
     if (e != cudaSuccess) return cuda_fail(e, "instanced trace launch");

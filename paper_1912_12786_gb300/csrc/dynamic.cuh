@@ -81,6 +81,11 @@ struct IsectDynamic {
     // lock-step descent may speculate past a held leaf when the bound kind
     // has no box callback (box_hooks_silent below decides for each ray)
     static constexpr bool kMaySpeculate = true;
+    // the indirect calls take 128-160 registers uncapped: the persistent and
+    // lock-step kernels are compiled for 3 (closest hit) or 4 (any hit)
+    // resident 256-thread blocks per SM, as the one-ray-per-thread kernel
+    static constexpr int kMinBlocksClosest = 3;
+    static constexpr int kMinBlocksAny = 4;
     AcceptFn acc = nullptr;
     CountFn on_box = nullptr, on_tri = nullptr;
     const DevScene* user = nullptr;

@@ -41,13 +41,27 @@ __global__ void __launch_bounds__(256, MINB)
 }
 
 // Persistent warps (per-lane loops or lock step) and one ray per thread in
-// lock step, uncapped: the callbacks are bound per ray by isect_setup.
+// lock step, the callbacks bound per ray by isect_setup; register budget
+// MINB resident 256-thread blocks per SM (1: none).
+template <int Q, int MINB>
+cudaError_t launch_dynamic_budget(const LaunchArgs& a) {
+    if (a.persistent)
+        return a.lockstep ? detail::launch_persistent<Q, IsectDynamic, false, 0, true, MINB>(a)
+                          : detail::launch_persistent<Q, IsectDynamic, false, 0, false, MINB>(a);
+    return detail::launch_lockstep<Q, IsectDynamic, false, 0, MINB>(a);
+}
+
+// a.reg_cap 0: the intersector's budget (3 blocks closest hit, 4 any hit);
+// 1: none; 3 or 4 blocks.
 template <int Q>
 cudaError_t launch_dynamic_shape(const LaunchArgs& a) {
-    if (a.persistent)
-        return a.lockstep ? detail::launch_persistent<Q, IsectDynamic, false, 0, true>(a)
-                          : detail::launch_persistent<Q, IsectDynamic, false, 0, false>(a);
-    return detail::launch_shape<Q, IsectDynamic, false, 0, true>(a);
+    switch (a.reg_cap) {
+        case 0: return launch_dynamic_budget<Q, min_blocks<Q, IsectDynamic>()>(a);
+        case 1: return launch_dynamic_budget<Q, 1>(a);
+        case 3: return launch_dynamic_budget<Q, 3>(a);
+        case 4: return launch_dynamic_budget<Q, 4>(a);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_dynamic(const LaunchArgs& a, int kind) {

@@ -6,8 +6,9 @@
 // single mesh.  Closest-hit ties between instances go to the lower instance
 // id, then the lower primitive id.
 //
-// One ray per thread.  The top-level while-while loop uses the bottom of the
-// thread's shared-memory stack; a mesh traversal runs on the stack above the
+// One ray per thread (k_trace_inst), or persistent warps with per-lane
+// loops (k_trace_inst_persistent).  The top-level while-while loop uses the
+// bottom of the thread's shared-memory stack; a mesh traversal runs on the stack above the
 // top-level entries, continuing the running result.  The intersector is
 // compiled in (static dispatch) or reached through this module's callback
 // tables (dynamic dispatch, dynamic.cuh), the callbacks seeing the mesh of
@@ -73,6 +74,37 @@ __device__ __forceinline__ Ray to_object(const float4 ra, const float4 rb, const
         __fmaf_rn(w1.x, rb.x, __fmaf_rn(w1.y, rb.y, __fmul_rn(w1.z, rb.z))),
         __fmaf_rn(w2.x, rb.x, __fmaf_rn(w2.y, rb.y, __fmul_rn(w2.z, rb.z))), rb.w);
     return make_ray(o, d);
+}
+
+// Write ray i's record, instance id and counters with the address checks
+// (a miss as t = +inf, u = v = 0, prim and instance kMiss).
+template <class H>
+__device__ __forceinline__ void write_inst(InstBest best, const H& h, unsigned long long i,
+                                           float4* __restrict__ hits,
+                                           uint32_t* __restrict__ inst_ids,
+                                           uint2* __restrict__ counters) {
+    if (best.prim == kMiss) {
+        best.t = __int_as_float(0x7f800000);
+        best.u = 0.0f;
+        best.v = 0.0f;
+        best.inst = kMiss;
+    }
+    if (reinterpret_cast<unsigned long long>(hits + i) % 16)
+        atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
+    else
+        hits[i] = make_float4(best.t, best.u, best.v, __uint_as_float(best.prim));
+    if (inst_ids) {
+        if (reinterpret_cast<unsigned long long>(inst_ids + i) % 4)
+            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
+        else
+            inst_ids[i] = best.inst;
+    }
+    if (H::kCounts && counters) {
+        if (reinterpret_cast<unsigned long long>(counters + i) % 8)
+            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
+        else
+            counters[i] = h.counters();
+    }
 }
 
 template <int Q, class H>
@@ -159,32 +191,202 @@ __global__ void __launch_bounds__(256) k_trace_inst(InstDev is, IsectParams ip,
         }
     }
 done:
-    if (best.prim == kMiss) {
-        best.t = __int_as_float(0x7f800000);
-        best.u = 0.0f;
-        best.v = 0.0f;
-        best.inst = kMiss;
+    write_inst(best, h, i, hits, inst_ids, counters);
+}
+
+// The instanced traversal of k_trace_inst split into resumable steps for
+// the persistent kernel.  Per lane: the top-level loop's position (`tref`
+// the node to descend from when `tfresh`, `tsp` entries on the stack's
+// bottom, the current top-level leaf's instances first..first+cnt with the
+// next at k) and, while `in_mesh`, the current instance's mesh traversal
+// (traverse_start / traverse_step on the stack above the top-level entries,
+// continuing the running result).  Composed, the steps visit top-level
+// nodes, instances and mesh nodes in the order of k_trace_inst, so every
+// result and count is the same.
+template <int Q, class H>
+struct InstWalk {
+    float4 ra, rb;  // the world ray as loaded
+    Ray r, ro;      // world ray; the ray in the current instance's object space
+    InstBest best;
+    Stats st;
+    H h;
+    const DevScene* msc;
+    ShortStack<0> mstk;
+    uint32_t tref, tsp, tleaves, first, cnt, k, mref, msteps;
+    bool tfresh, in_mesh;
+
+    // Begin a ray; false when it needs no steps (no instances, root missed).
+    __device__ __forceinline__ bool start(const InstDev& is, const IsectParams& ip, float4 a,
+                                          float4 b) {
+        ra = a;
+        rb = b;
+        r = make_ray(a, b);
+        h = H();
+        bind_callbacks(h, ip);
+        best.reset(r.tmax);
+        in_mesh = false;
+        tfresh = true;
+        tsp = 0;
+        tleaves = 0;
+        cnt = 0;
+        k = 0;
+        if (is.ninst == 0) return false;
+        h.box();
+        if (!box_hit(r, is.root_a, is.root_b, Q == kClosest ? best.t : r.tmax)) return false;
+        tref = is.root_ref;
+        return true;
     }
-    if (reinterpret_cast<unsigned long long>(hits + i) % 16)
-        atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
+
+    // The next top-level leaf: descend from tref (or from the next stack
+    // entry after a leaf).  False when the top level is exhausted or failed.
+    __device__ __forceinline__ bool top_next(const InstDev& is, uint32_t* stack,
+                                             uint32_t stride) {
+        if (!tfresh) {
+            if (tsp == 0) return false;
+            --tsp;
+            tref = stack[tsp * stride];
+        }
+        tfresh = false;
+        // descent ends by construction (children follow their parent)
+        while (!(tref & kLeafBit)) {
+            const float4* p = is.nodes + 4ull * (tref >> 2);
+            const float4 la = VSR_LDG(p), lb = VSR_LDG(p + 1), qa = VSR_LDG(p + 2),
+                         qb = VSR_LDG(p + 3);
+            const float tfar = (Q == kClosest) ? best.t : r.tmax;
+            h.box();
+            h.box();
+            const bool hl = box_hit(r, la, lb, tfar);
+            const bool hr = box_hit(r, qa, qb, tfar);
+            const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(qa.w);
+            if (hl && hr) {
+                const bool neg = (r.negmask >> (tref & 3u)) & 1u;
+                if (tsp >= is.top_depth) {  // unreachable for a validated blob
+                    atomicOr(is.err, kErrStack);
+                    best.fail();
+                    return false;
+                }
+                stack[tsp * stride] = neg ? rl : rr;
+                ++tsp;
+                tref = neg ? rr : rl;
+            } else if (hl) {
+                tref = rl;
+            } else if (hr) {
+                tref = rr;
+            } else {
+                if (tsp == 0) return false;
+                --tsp;
+                tref = stack[tsp * stride];
+            }
+        }
+        if (++tleaves > is.max_leaves) {  // unreachable for a validated blob
+            atomicOr(is.err, kErrSteps);
+            best.fail();
+            return false;
+        }
+        first = (tref >> 3) & 0x0FFFFFFFu;
+        cnt = (tref & 7u) + 1u;
+        k = 0;
+        return true;
+    }
+
+    // One step: a step of the current mesh traversal, or the top level's
+    // advance to the next instance whose mesh root the ray hits.  True when
+    // the ray has finished.
+    __device__ __forceinline__ bool step(const InstDev& is, const IsectParams& ip,
+                                         uint32_t* stack, uint32_t stride) {
+        if (in_mesh) {
+            if (!traverse_step<Q, H, false>(*msc, ip, ro, h, best, st, mref, msteps, mstk))
+                return false;
+            in_mesh = false;
+            if (best.failed || (Q == kAny && best.prim != kMiss)) return true;
+        }
+        for (;;) {
+            while (k < cnt) {
+                const uint32_t id = VSR_LDG(is.order + first + k);
+                ++k;
+                const float4* w = is.inst + 4ull * id;
+                ro = to_object(ra, rb, VSR_LDG(w), VSR_LDG(w + 1), VSR_LDG(w + 2));
+                msc = is.meshes + __float_as_uint(VSR_LDG(w + 3).x);
+                best.cur = id;
+                set_callback_scene(h, msc);
+                mstk.init(stack + tsp * stride, stride);
+                if (traverse_start<Q, H, false>(*msc, ip, ro, h, best, st, mref, msteps, mstk)) {
+                    in_mesh = true;
+                    return false;
+                }
+            }
+            if (!top_next(is, stack, stride)) return true;
+        }
+    }
+};
+
+// Persistent instanced trace (persistent_rays: warps claim rays from a
+// counter and refill idle lanes), per-lane loops over InstWalk steps.
+template <int Q, class H>
+__device__ __forceinline__ void trace_inst_persistent(
+    InstDev is, IsectParams ip, const float4* __restrict__ rays, RayMap map,
+    float4* __restrict__ hits, uint32_t* __restrict__ inst_ids, uint2* __restrict__ counters,
+    unsigned long long* __restrict__ work, uint32_t refill, Watchdog wd) {
+    extern __shared__ uint32_t s_stack[];
+    uint32_t* stack = s_stack + threadIdx.x;
+    const uint32_t stride = blockDim.x;
+    InstWalk<Q, H> w;
+    persistent_rays<false>(
+        map, work, refill, wd, is.err,
+        [&](unsigned long long ri) {
+            return w.start(is, ip, VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
+        },
+        [&](bool) { return w.step(is, ip, stack, stride); },
+        [&](unsigned long long ri) { write_inst(w.best, w.h, ri, hits, inst_ids, counters); },
+        [&]() { w.best.fail(); });
+}
+
+// Kernel with the compiler's register choice (static intersectors) or the
+// intersector's budget of MINB resident blocks per SM (min_blocks).
+template <int Q, class H>
+__global__ void __launch_bounds__(256) k_trace_inst_persistent(
+    InstDev is, IsectParams ip, const float4* __restrict__ rays, RayMap map,
+    float4* __restrict__ hits, uint32_t* __restrict__ inst_ids, uint2* __restrict__ counters,
+    unsigned long long* __restrict__ work, uint32_t refill, Watchdog wd) {
+    trace_inst_persistent<Q, H>(is, ip, rays, map, hits, inst_ids, counters, work, refill, wd);
+}
+template <int Q, class H, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_trace_inst_persistent_budget(
+    InstDev is, IsectParams ip, const float4* __restrict__ rays, RayMap map,
+    float4* __restrict__ hits, uint32_t* __restrict__ inst_ids, uint2* __restrict__ counters,
+    unsigned long long* __restrict__ work, uint32_t refill, Watchdog wd) {
+    trace_inst_persistent<Q, H>(is, ip, rays, map, hits, inst_ids, counters, work, refill, wd);
+}
+template <int Q, class H>
+inline auto inst_persistent_kernel() {
+    if constexpr (min_blocks<Q, H>() > 1)
+        return k_trace_inst_persistent_budget<Q, H, min_blocks<Q, H>()>;
     else
-        hits[i] = make_float4(best.t, best.u, best.v, __uint_as_float(best.prim));
-    if (inst_ids) {
-        if (reinterpret_cast<unsigned long long>(inst_ids + i) % 4)
-            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
-        else
-            inst_ids[i] = best.inst;
+        return k_trace_inst_persistent<Q, H>;
+}
+
+template <int Q, class H>
+cudaError_t inst_persistent(const InstLaunch& L) {
+    const size_t smem = (size_t)L.stack_words * L.block * sizeof(uint32_t);
+    auto k = inst_persistent_kernel<Q, H>();
+    if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
     }
-    if (H::kCounts && counters) {
-        if (reinterpret_cast<unsigned long long>(counters + i) % 8)
-            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
-        else
-            counters[i] = h.counters();
-    }
+    const int grid =
+        persistent_grid(L.block, L.blocks_per_sm, reinterpret_cast<const void*>(k), smem);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    return with_ray_counter(nullptr, L.stream, [&](unsigned long long* work) {
+        k<<<grid, L.block, smem, L.stream>>>(L.is, L.ip, L.rays, L.map, L.hits, L.inst_ids,
+                                             L.counters, work, L.refill, L.wd);
+        return cudaGetLastError();
+    });
 }
 
 template <int Q, class H>
 cudaError_t inst_one(const InstLaunch& L) {
+    if (L.persistent) return inst_persistent<Q, H>(L);
     const size_t smem = (size_t)L.stack_words * L.block * sizeof(uint32_t);
     auto k = k_trace_inst<Q, H>;
     if (smem > 48 * 1024) {

@@ -8,6 +8,8 @@
 // candidates that would enter the buffer; with n == 1 it is the closest-hit
 // query.  The intersector is compiled in (static dispatch) or reached
 // through this module's callback tables (dynamic dispatch, dynamic.cuh).
+// Launch shapes: one ray per thread, or persistent warps with per-lane loops
+// or in lock step.
 //
 // The first launch of the unchecked build raised a misaligned-address fault
 // that reading the code did not explain (every access here uses a cudaMalloc
@@ -42,6 +44,29 @@ __device__ __forceinline__ float4 multi_record(const Ray& r, const float* __rest
     return make_float4(t, u, v, __uint_as_float(p));
 }
 
+// Write ray i's nh records (and its counters) with the address checks.
+template <class H>
+__device__ __forceinline__ void write_multi(const Ray& r, const float* __restrict__ verts,
+                                            const uint32_t* __restrict__ idx,
+                                            const MultiBest& mb, const H& h, unsigned long long i,
+                                            uint32_t nh, float4* __restrict__ hits,
+                                            uint2* __restrict__ counters) {
+    float4* out = hits + i * nh;
+    for (uint32_t k = 0; k < nh; ++k) {
+        const float4 rec = multi_record(r, verts, idx, mb.pk[k * mb.stride]);
+        if (reinterpret_cast<unsigned long long>(out + k) % 16)
+            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
+        else
+            out[k] = rec;
+    }
+    if (H::kCounts && counters) {
+        if (reinterpret_cast<unsigned long long>(counters + i) % 8)
+            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
+        else
+            counters[i] = h.counters();
+    }
+}
+
 template <class H>
 __global__ void __launch_bounds__(256) k_trace_multi(DevScene sc, IsectParams ip,
                                                      const float* __restrict__ verts,
@@ -72,24 +97,112 @@ __global__ void __launch_bounds__(256) k_trace_multi(DevScene sc, IsectParams ip
     ShortStack<0> stk;
     stk.init(s_stack + threadIdx.x, stride);
     traverse_body<kClosest, H, false>(sc, ip, r, h, mb, st, stk);
-    float4* out = hits + i * nh;
-    for (uint32_t k = 0; k < nh; ++k) {
-        const float4 rec = multi_record(r, verts, idx, mb.pk[k * stride]);
-        if (reinterpret_cast<unsigned long long>(out + k) % 16)
-            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
-        else
-            out[k] = rec;
+    write_multi(r, verts, idx, mb, h, i, nh, hits, counters);
+}
+
+// Persistent multi-hit (persistent_rays: warps claim rays from a counter and
+// refill idle lanes): each lane's traversal resumable (traverse_start /
+// traverse_step), or the warp in lock step (warp_step, whose closest-hit
+// speculation works with the buffer's last entry as the far limit).  Shared
+// memory per thread: stack, the buffer's t and prim columns, and with LS the
+// speculation's entry distances.
+template <class H, bool LS>
+__device__ __forceinline__ void trace_multi_persistent(
+    DevScene sc, IsectParams ip, const float* __restrict__ verts,
+    const uint32_t* __restrict__ idx, const float4* __restrict__ rays, RayMap map, uint32_t nh,
+    float4* __restrict__ hits, uint2* __restrict__ counters, unsigned long long* __restrict__ work,
+    uint32_t refill, Watchdog wd, const DevScene* __restrict__ user) {
+    extern __shared__ uint32_t s_stack[];
+    const uint32_t stride = blockDim.x;
+    uint32_t* buf = s_stack + sc.stack_depth * stride;
+    MultiBest mb;
+    mb.tk = reinterpret_cast<float*>(buf) + threadIdx.x;
+    mb.pk = buf + nh * stride + threadIdx.x;
+    mb.stride = stride;
+    mb.n = nh;
+    float* tcol = reinterpret_cast<float*>(buf + 2u * nh * stride) + threadIdx.x;
+    ShortStack<0> stk;
+    stk.init(s_stack + threadIdx.x, stride);
+    Ray r;
+    Stats st;
+    H h;
+    uint32_t ref = 0, steps = 0, leaf = 0;
+    bool more = false, pend = false;
+    persistent_rays<LS>(
+        map, work, refill, wd, sc.err,
+        [&](unsigned long long ri) {
+            r = make_ray(VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
+            h = H();
+            isect_setup(h, ip, user);
+            more = true;
+            pend = false;
+            return traverse_start<kClosest, H, false>(sc, ip, r, h, mb, st, ref, steps, stk);
+        },
+        [&](bool busy) {
+            if constexpr (LS)
+                return warp_step<kClosest, H, false>(sc, ip, r, h, mb, st, busy, ref, more, leaf,
+                                                     pend, steps, stk, tcol);
+            else
+                return traverse_step<kClosest, H, false>(sc, ip, r, h, mb, st, ref, steps, stk);
+        },
+        [&](unsigned long long ri) { write_multi(r, verts, idx, mb, h, ri, nh, hits, counters); },
+        [&]() { mb.fail(); });
+}
+
+// Kernel with the compiler's register choice (static intersectors) or the
+// intersector's budget of MINB resident blocks per SM (min_blocks).
+template <class H, bool LS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_trace_multi_persistent_budget(
+    DevScene sc, IsectParams ip, const float* __restrict__ verts,
+    const uint32_t* __restrict__ idx, const float4* __restrict__ rays, RayMap map, uint32_t nh,
+    float4* __restrict__ hits, uint2* __restrict__ counters, unsigned long long* __restrict__ work,
+    uint32_t refill, Watchdog wd, const DevScene* __restrict__ user) {
+    trace_multi_persistent<H, LS>(sc, ip, verts, idx, rays, map, nh, hits, counters, work, refill,
+                                  wd, user);
+}
+template <class H, bool LS>
+__global__ void __launch_bounds__(256) k_trace_multi_persistent(
+    DevScene sc, IsectParams ip, const float* __restrict__ verts,
+    const uint32_t* __restrict__ idx, const float4* __restrict__ rays, RayMap map, uint32_t nh,
+    float4* __restrict__ hits, uint2* __restrict__ counters, unsigned long long* __restrict__ work,
+    uint32_t refill, Watchdog wd, const DevScene* __restrict__ user) {
+    trace_multi_persistent<H, LS>(sc, ip, verts, idx, rays, map, nh, hits, counters, work, refill,
+                                  wd, user);
+}
+template <class H, bool LS>
+inline auto multi_persistent_kernel() {
+    if constexpr (min_blocks<kClosest, H>() > 1)
+        return k_trace_multi_persistent_budget<H, LS, min_blocks<kClosest, H>()>;
+    else
+        return k_trace_multi_persistent<H, LS>;
+}
+
+template <class H, bool LS>
+cudaError_t multi_persistent(const LaunchArgs& a, const float* verts, const uint32_t* idx,
+                             uint32_t nh) {
+    const uint32_t words = a.sc.stack_depth + 2u * nh +
+                           (LS ? spec_words<kClosest, H, false, 0>(a.sc.stack_depth) : 0u);
+    const size_t smem = (size_t)words * a.block * sizeof(uint32_t);
+    auto k = multi_persistent_kernel<H, LS>();
+    if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
     }
-    if (H::kCounts && counters) {
-        if (reinterpret_cast<unsigned long long>(counters + i) % 8)
-            atomicCAS(&g_vsr_align_line, 0u, (unsigned)__LINE__);
-        else
-            counters[i] = h.counters();
-    }
+    const int grid = persistent_grid(a, reinterpret_cast<const void*>(k), smem);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    return with_ray_counter(a.work, a.stream, [&](unsigned long long* work) {
+        k<<<grid, a.block, smem, a.stream>>>(a.sc, a.ip, verts, idx, a.rays, a.map, nh, a.hits,
+                                             a.counters, work, a.refill, a.wd, a.dyn_user);
+        return cudaGetLastError();
+    });
 }
 
 template <class H>
 cudaError_t multi_one(const LaunchArgs& a, const float* verts, const uint32_t* idx, uint32_t nh) {
+    if (a.persistent)
+        return a.lockstep ? multi_persistent<H, true>(a, verts, idx, nh)
+                          : multi_persistent<H, false>(a, verts, idx, nh);
     const size_t smem = ((size_t)a.sc.stack_depth + 2u * nh) * a.block * sizeof(uint32_t);
     auto k = k_trace_multi<H>;
     if (smem > 48 * 1024) {

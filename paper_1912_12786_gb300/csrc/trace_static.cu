@@ -28,13 +28,13 @@ cudaError_t launch_static(const LaunchArgs& a, int kind, bool stats) {
     }
 }
 
-int persistent_grid(const LaunchArgs& a, const void* kernel, size_t smem) {
+int persistent_grid(uint32_t block, uint32_t blocks_per_sm, const void* kernel, size_t smem) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (a.blocks_per_sm) {
-        per_sm = (int)a.blocks_per_sm;
-    } else if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, (int)a.block, smem) !=
+    if (blocks_per_sm) {
+        per_sm = (int)blocks_per_sm;
+    } else if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, (int)block, smem) !=
                cudaSuccess) {
         return 0;
     }

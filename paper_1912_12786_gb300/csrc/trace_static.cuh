@@ -54,12 +54,11 @@ __global__ void __launch_bounds__(256) k_trace(DevScene sc, IsectParams ip,
 // of 32).  Each pass finishes a ray or tests one leaf of every busy lane, so
 // the loop ends.
 template <int Q, class H, bool STATS, int K>
-__global__ void __launch_bounds__(256) k_trace_ls(DevScene sc, IsectParams ip,
-                                                  const float4* __restrict__ rays,
-                                                  RayMap map, float4* __restrict__ hits,
-                                                  uint2* __restrict__ counters,
-                                                  uint4* __restrict__ stats,
-                                                  const DevScene* __restrict__ user) {
+__device__ __forceinline__ void trace_ls(DevScene sc, IsectParams ip,
+                                         const float4* __restrict__ rays, RayMap map,
+                                         float4* __restrict__ hits, uint2* __restrict__ counters,
+                                         uint4* __restrict__ stats,
+                                         const DevScene* __restrict__ user) {
     extern __shared__ uint32_t s_stack[];
     const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long i = g < map.threads ? ray_of_thread(g, map) : map.n;
@@ -95,6 +94,24 @@ __global__ void __launch_bounds__(256) k_trace_ls(DevScene sc, IsectParams ip,
     }
 }
 
+// The kernels: the compiler's own register choice (the static intersectors),
+// or a budget of MINB resident 256-thread blocks per SM (min_blocks: the
+// dynamic intersector).
+template <int Q, class H, bool STATS, int K>
+__global__ void __launch_bounds__(256)
+    k_trace_ls(DevScene sc, IsectParams ip, const float4* __restrict__ rays, RayMap map,
+               float4* __restrict__ hits, uint2* __restrict__ counters,
+               uint4* __restrict__ stats, const DevScene* __restrict__ user) {
+    trace_ls<Q, H, STATS, K>(sc, ip, rays, map, hits, counters, stats, user);
+}
+template <int Q, class H, bool STATS, int K, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_trace_ls_budget(DevScene sc, IsectParams ip, const float4* __restrict__ rays, RayMap map,
+                      float4* __restrict__ hits, uint2* __restrict__ counters,
+                      uint4* __restrict__ stats, const DevScene* __restrict__ user) {
+    trace_ls<Q, H, STATS, K>(sc, ip, rays, map, hits, counters, stats, user);
+}
+
 // k_trace under a register budget: __launch_bounds__(256, MINB) asks the
 // compiler to fit MINB blocks of 256 threads per SM (at most 65536 /
 // (256 MINB) registers per thread).  Used to compare static injection with
@@ -121,106 +138,96 @@ __global__ void __launch_bounds__(256, MINB) k_trace_cap(DevScene sc, IsectParam
     if (H::kCounts && counters) counters[i] = h.counters();
 }
 
-// Persistent variant.  Per-lane traversal state lives in registers and the
-// shared-memory stack column; a lane that finishes its ray idles until the
-// warp refills.  The counter hands out thread slots of the ray map; a slot
-// past the image edge takes no ray.
-//
-// Control flow: every iteration starts with all 32 lanes converged at the
-// first vote.  The claim block runs on a warp-uniform condition; inside it
-// only the lanes without a ray take new ones, and the second vote closes that
-// divergent part.  The loop's exits (all lanes idle and the counter passed
-// the end, or the watchdog) are uniform decisions.  The traversal step is the
-// only other divergent region, a single if with one exit, and __syncwarp
-// reconverges the warp before the next iteration.  No lane ever waits on
-// another warp or block.  Each iteration claims at least one ray or advances
-// some lane's traversal (bounded per ray by the node count), so the loop
-// ends; the watchdog bounds it whatever happens.  With LS the step is
-// warp_step, called by all 32 lanes (converged throughout).
+// Persistent variant (persistent_rays: warps claim rays from a global
+// counter and refill idle lanes).  Per-lane traversal state lives in
+// registers and the shared-memory stack column; a lane that finishes its ray
+// idles until the warp refills.  A counter slot past the image edge takes no
+// ray.  Per-lane loops: the traversal step (traverse_step) is the only
+// divergent region besides the claim, and the warp reconverges after it.
+// With LS the step is warp_step, called by all 32 lanes (converged
+// throughout).
 template <int Q, class H, bool STATS, int K, bool LS>
-__global__ void __launch_bounds__(256) k_trace_persistent(
+__device__ __forceinline__ void trace_persistent(
     DevScene sc, IsectParams ip, const float4* __restrict__ rays, RayMap map,
     float4* __restrict__ hits, uint2* __restrict__ counters, uint4* __restrict__ stats,
     unsigned long long* __restrict__ work, uint32_t refill, Watchdog wd,
     const DevScene* __restrict__ user) {
     extern __shared__ uint32_t s_stack[];
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t lt_mask = (1u << lane) - 1u;
     ShortStack<K> stk;
     stk.init(s_stack + threadIdx.x, blockDim.x);
     // closest-hit speculation's entry distances (lock step), after the stack
     float* tcol = reinterpret_cast<float*>(s_stack + stack_words(sc.stack_depth, K) * blockDim.x) +
                   threadIdx.x;
-
-    bool has = false;        // lane holds a ray in flight
-    bool exhausted = false;  // warp-uniform: the counter passed the last slot
-    unsigned long long ri = 0;
     Ray r;
     Best best;
     Stats st;
     H h;
     uint32_t ref = 0, steps = 0, leaf = 0;
     bool more = false, pend = false;
-    const unsigned long long t0 = wd.max_ns ? global_ns() : 0ull;
-    unsigned long long iters = 0;
+    persistent_rays<LS>(
+        map, work, refill, wd, sc.err,
+        [&](unsigned long long ri) {
+            r = make_ray(VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
+            h = H();
+            isect_setup(h, ip, user);
+            st = Stats();
+            more = true;
+            pend = false;
+            return traverse_start<Q, H, STATS>(sc, ip, r, h, best, st, ref, steps, stk);
+        },
+        [&](bool busy) {
+            if constexpr (LS)
+                return warp_step<Q, H, STATS>(sc, ip, r, h, best, st, busy, ref, more, leaf, pend,
+                                              steps, stk, tcol);
+            else
+                return traverse_step<Q, H, STATS>(sc, ip, r, h, best, st, ref, steps, stk);
+        },
+        [&](unsigned long long ri) {
+            finish_miss(best);
+            hits[ri] = hit_record(best);
+            if (H::kCounts && counters) counters[ri] = h.counters();
+            if (STATS) stats[ri] = make_uint4(st.boxes, st.tris, st.cands, st.texs);
+        },
+        [&]() { best.fail(); });
+}
 
-    auto finish = [&]() {
-        finish_miss(best);
-        hits[ri] = hit_record(best);
-        if (H::kCounts && counters) counters[ri] = h.counters();
-        if (STATS) stats[ri] = make_uint4(st.boxes, st.tris, st.cands, st.texs);
-        has = false;
-    };
-
-    for (;;) {
-        const uint32_t busy = __ballot_sync(kFullMask, has);
-        if (!exhausted && (uint32_t)__popc(busy) < refill) {
-            const uint32_t idle = ~busy;
-            const uint32_t nidle = (uint32_t)__popc(idle);
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(work, (unsigned long long)nidle);
-            base = __shfl_sync(kFullMask, base, 0);
-            if (base + nidle >= map.threads) exhausted = true;
-            if (!has) {
-                const unsigned long long slot = base + (unsigned long long)__popc(idle & lt_mask);
-                ri = slot < map.threads ? ray_of_thread(slot, map) : map.n;
-                if (ri < map.n) {
-                    r = make_ray(VSR_LDG(rays + 2 * ri), VSR_LDG(rays + 2 * ri + 1));
-                    h = H();
-                    isect_setup(h, ip, user);
-                    st = Stats();
-                    has = true;
-                    more = true;
-                    pend = false;
-                    if (!traverse_start<Q, H, STATS>(sc, ip, r, h, best, st, ref, steps, stk))
-                        finish();
-                }
-            }
-        }
-        const uint32_t live = __ballot_sync(kFullMask, has);
-        if (live == 0u && exhausted) break;
-        if (watchdog_expired(wd, ++iters, t0)) {
-            if (lane == 0) atomicOr(sc.err, kErrTimeout);
-            if (has) {
-                best.fail();
-                finish();
-            }
-            break;
-        }
-        if constexpr (LS) {
-            if (warp_step<Q, H, STATS>(sc, ip, r, h, best, st, has, ref, more, leaf, pend, steps,
-                                       stk, tcol))
-                finish();
-        } else {
-            if (has) {
-                if (traverse_step<Q, H, STATS>(sc, ip, r, h, best, st, ref, steps, stk)) finish();
-            }
-            __syncwarp();
-        }
-    }
+template <int Q, class H, bool STATS, int K, bool LS>
+__global__ void __launch_bounds__(256) k_trace_persistent(
+    DevScene sc, IsectParams ip, const float4* __restrict__ rays, RayMap map,
+    float4* __restrict__ hits, uint2* __restrict__ counters, uint4* __restrict__ stats,
+    unsigned long long* __restrict__ work, uint32_t refill, Watchdog wd,
+    const DevScene* __restrict__ user) {
+    trace_persistent<Q, H, STATS, K, LS>(sc, ip, rays, map, hits, counters, stats, work, refill,
+                                         wd, user);
+}
+template <int Q, class H, bool STATS, int K, bool LS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_trace_persistent_budget(
+    DevScene sc, IsectParams ip, const float4* __restrict__ rays, RayMap map,
+    float4* __restrict__ hits, uint2* __restrict__ counters, uint4* __restrict__ stats,
+    unsigned long long* __restrict__ work, uint32_t refill, Watchdog wd,
+    const DevScene* __restrict__ user) {
+    trace_persistent<Q, H, STATS, K, LS>(sc, ip, rays, map, hits, counters, stats, work, refill,
+                                         wd, user);
 }
 
 namespace detail {
+
+// The kernel of each shape under a budget of MINB resident 256-thread
+// blocks per SM (MINB <= 1: the compiler's own register choice).
+template <int Q, class H, bool STATS, int K, bool LS, int MINB>
+inline auto persistent_kernel() {
+    if constexpr (MINB > 1)
+        return k_trace_persistent_budget<Q, H, STATS, K, LS, MINB>;
+    else
+        return k_trace_persistent<Q, H, STATS, K, LS>;
+}
+template <int Q, class H, bool STATS, int K, int MINB>
+inline auto lockstep_kernel() {
+    if constexpr (MINB > 1)
+        return k_trace_ls_budget<Q, H, STATS, K, MINB>;
+    else
+        return k_trace_ls<Q, H, STATS, K>;
+}
 
 template <class Kern>
 cudaError_t ensure_smem(Kern kernel, size_t smem) {
@@ -230,58 +237,55 @@ cudaError_t ensure_smem(Kern kernel, size_t smem) {
 
 // The persistent launch (also the dynamic dispatcher's, with H =
 // IsectDynamic and a.dyn_user the scene copy its callbacks see; the static
-// intersectors ignore it).
-template <int Q, class H, bool STATS, int K, bool LS>
+// intersectors ignore it), under H's register budget unless MINB says
+// otherwise.
+template <int Q, class H, bool STATS, int K, bool LS, int MINB = min_blocks<Q, H>()>
 cudaError_t launch_persistent(const LaunchArgs& a) {
     const uint32_t words = stack_words(a.sc.stack_depth, K) +
                            (LS ? spec_words<Q, H, STATS, K>(a.sc.stack_depth) : 0u);
     const size_t smem = (size_t)words * a.block * sizeof(uint32_t);
-    auto k = k_trace_persistent<Q, H, STATS, K, LS>;
+    auto k = persistent_kernel<Q, H, STATS, K, LS, MINB>();
     cudaError_t e = ensure_smem(k, smem);
     if (e != cudaSuccess) return e;
     const int grid = persistent_grid(a, reinterpret_cast<const void*>(k), smem);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
-    // the ray counter: the caller's, or 8 bytes of stream-ordered scratch for
-    // this launch alone, so persistent launches on one scene may overlap
-    unsigned long long* work = a.work;
-    if (!work) {
-        e = cudaMallocAsync(reinterpret_cast<void**>(&work), sizeof(unsigned long long), a.stream);
-        if (e != cudaSuccess) return e;
-    }
-    e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), a.stream);
-    if (e == cudaSuccess) {
+    return with_ray_counter(a.work, a.stream, [&](unsigned long long* work) {
         k<<<grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits, a.counters,
                                              a.stats, work, a.refill, a.wd, a.dyn_user);
-        e = cudaGetLastError();
-    }
-    if (!a.work) {
-        const cudaError_t f = cudaFreeAsync(work, a.stream);
-        if (e == cudaSuccess) e = f;
-    }
-    return e;
+        return cudaGetLastError();
+    });
+}
+
+// One ray per thread in lock step (budget as launch_persistent).
+template <int Q, class H, bool STATS, int K, int MINB = min_blocks<Q, H>()>
+cudaError_t launch_lockstep(const LaunchArgs& a) {
+    const uint32_t words =
+        stack_words(a.sc.stack_depth, K) + spec_words<Q, H, STATS, K>(a.sc.stack_depth);
+    const size_t smem = (size_t)words * a.block * sizeof(uint32_t);
+    const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
+    auto k = lockstep_kernel<Q, H, STATS, K, MINB>();
+    cudaError_t e = ensure_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits, a.counters,
+                                                     a.stats, a.dyn_user);
+    return cudaGetLastError();
 }
 
 template <int Q, class H, bool STATS, int K, bool LS>
 cudaError_t launch_shape(const LaunchArgs& a) {
     if (a.persistent) return launch_persistent<Q, H, STATS, K, LS>(a);
-    const uint32_t words = stack_words(a.sc.stack_depth, K) +
-                           (LS ? spec_words<Q, H, STATS, K>(a.sc.stack_depth) : 0u);
-    const size_t smem = (size_t)words * a.block * sizeof(uint32_t);
-    const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
     if constexpr (LS) {
-        auto k = k_trace_ls<Q, H, STATS, K>;
-        cudaError_t e = ensure_smem(k, smem);
-        if (e != cudaSuccess) return e;
-        k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits,
-                                                         a.counters, a.stats, a.dyn_user);
+        return launch_lockstep<Q, H, STATS, K>(a);
     } else {
+        const size_t smem = (size_t)stack_words(a.sc.stack_depth, K) * a.block * sizeof(uint32_t);
+        const unsigned long long grid = (a.map.threads + a.block - 1) / a.block;
         auto k = k_trace<Q, H, STATS, K>;
         cudaError_t e = ensure_smem(k, smem);
         if (e != cudaSuccess) return e;
         k<<<(unsigned)grid, a.block, smem, a.stream>>>(a.sc, a.ip, a.rays, a.map, a.hits,
                                                          a.counters, a.stats);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
 }
 
 template <int Q, class H, bool STATS, int K>

@@ -328,6 +328,10 @@ struct IsectNone {
     // ahead of the plain order (warp_step); whether they do for a ray is
     // box_hooks_silent's answer
     static constexpr bool kMaySpeculate = true;
+    // resident 256-thread blocks per SM the persistent and lock-step kernels
+    // are compiled for, per query (1: no register budget)
+    static constexpr int kMinBlocksClosest = 1;
+    static constexpr int kMinBlocksAny = 1;
     __device__ __forceinline__ void begin(const Ray&, const IsectParams&) {}
     __device__ __forceinline__ void box() {}
     __device__ __forceinline__ void tri() {}
@@ -639,10 +643,12 @@ __device__ __forceinline__ void traverse(const DevScene& sc, const IsectParams& 
 // returns whether the ray is still live; each traverse_step runs one outer
 // iteration of the while-while loop (descend to a leaf, test it, pop the
 // next node) and returns true when the ray has finished.  Composed, they
-// visit nodes and primitives in exactly the order of traverse_body.
-template <int Q, class H, bool STATS, class S>
+// visit nodes and primitives in exactly the order of traverse_body.  The
+// running result B is Best or one with its interface (MultiBest, the
+// instancing result).
+template <int Q, class H, bool STATS, class B, class S>
 __device__ __forceinline__ bool traverse_start(const DevScene& sc, const IsectParams& ip,
-                                               const Ray& r, H& h, Best& best, Stats& st,
+                                               const Ray& r, H& h, B& best, Stats& st,
                                                uint32_t& ref, uint32_t& steps, S& stk) {
     best.init(r.tmax);
     stk.n = 0;
@@ -657,9 +663,9 @@ __device__ __forceinline__ bool traverse_start(const DevScene& sc, const IsectPa
     return true;
 }
 
-template <int Q, class H, bool STATS, class S>
+template <int Q, class H, bool STATS, class B, class S>
 __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectParams& ip,
-                                              const Ray& r, H& h, Best& best, Stats& st,
+                                              const Ray& r, H& h, B& best, Stats& st,
                                               uint32_t& ref, uint32_t& steps, S& stk) {
     // Descent ends by construction as in traverse_body; the persistent and
     // batched kernels that run these steps keep the per-node visit bound as
@@ -735,9 +741,9 @@ __device__ __forceinline__ bool traverse_step(const DevScene& sc, const IsectPar
 // The primitive loop body of the traversal for one triangle of a leaf (tp:
 // its three float4).  Returns true when the query has its answer (an
 // accepted any hit).
-template <int Q, class H, bool STATS>
+template <int Q, class H, bool STATS, class B>
 __device__ __forceinline__ bool test_prim(const DevScene& sc, const IsectParams& ip,
-                                          const Ray& r, H& h, Best& best, Stats& st,
+                                          const Ray& r, H& h, B& best, Stats& st,
                                           const float4* tp) {
     const float4 a = VSR_LDG(tp), e1 = VSR_LDG(tp + 1), e2 = VSR_LDG(tp + 2);
     h.tri();
@@ -779,6 +785,13 @@ struct Speculate {
 template <class H>
 __device__ __forceinline__ bool box_hooks_silent(const H&) {
     return !H::kCounts;
+}
+
+// Register budget of the persistent and lock-step kernels with intersector
+// H for query Q, as resident 256-thread blocks per SM (__launch_bounds__).
+template <int Q, class H>
+__host__ __device__ constexpr int min_blocks() {
+    return Q == kClosest ? H::kMinBlocksClosest : H::kMinBlocksAny;
 }
 
 // Per-ray setup of the intersector of a ray a persistent loop claims: none
@@ -833,9 +846,9 @@ __device__ __forceinline__ void hold_leaf(uint32_t& ref, bool& more, uint32_t& l
 //     own path distance exceeds tf; what is left is what the plain order
 //     holds at the same point, and the leaves come in its order.
 // Returns true on busy lanes whose ray has finished (result in best).
-template <int Q, class H, bool STATS, class S>
+template <int Q, class H, bool STATS, class B, class S>
 __device__ __forceinline__ bool warp_step(const DevScene& sc, const IsectParams& ip,
-                                          const Ray& r, H& h, Best& best, Stats& st, bool busy,
+                                          const Ray& r, H& h, B& best, Stats& st, bool busy,
                                           uint32_t& ref, bool& more, uint32_t& leaf, bool& pend,
                                           uint32_t& steps, S& stk, float* tcol) {
     using Spec = Speculate<Q, H, STATS, S::kRegs>;
@@ -992,6 +1005,83 @@ __device__ __forceinline__ bool watchdog_expired(const Watchdog& wd, unsigned lo
     if (wd.max_ns && (iters & 255ull) == 0ull)
         return __any_sync(kFullMask, global_ns() - t0 > wd.max_ns) != 0;
     return false;
+}
+
+// The claim loop of the persistent kernels: warps that take rays from a
+// global counter (`work`, thread slots of `map`) with one atomic per warp and
+// refill idle lanes when fewer than `refill` of 32 hold a ray (ballot +
+// popc), after Aila and Laine's persistent threads.  Per ray:
+//   start(i)  begins ray i on this lane, returns whether it needs steps;
+//   step(b)   one step of the lane's ray; returns true when it has finished.
+//             With LS all 32 lanes call it (b: the lane holds a ray) and it
+//             must be a converged, warp-synchronous step; otherwise only
+//             lanes holding a ray call it (b true) and the warp reconverges
+//             after it;
+//   finish(i) writes ray i's results;
+//   fail()    marks the lane's result as failed (the watchdog ran out).
+//
+// Control flow: every iteration starts with all 32 lanes converged at the
+// first vote.  The claim block runs on a warp-uniform condition; inside it
+// only the lanes without a ray take new ones, and the second vote closes
+// that divergent part.  The loop's exits (all lanes idle and the counter
+// passed the end, or the watchdog) are uniform decisions.  No lane waits on
+// another warp or block.  Each iteration claims at least one ray or advances
+// some lane's ray (bounded per ray by the traversal's own visit bound), so
+// the loop ends; the watchdog bounds it whatever happens.
+template <bool LS, class Start, class Step, class Finish, class Fail>
+__device__ __forceinline__ void persistent_rays(const RayMap& map, unsigned long long* work,
+                                                uint32_t refill, const Watchdog& wd,
+                                                uint32_t* err, Start&& start, Step&& step,
+                                                Finish&& finish, Fail&& fail) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    bool has = false;        // lane holds a ray in flight
+    bool exhausted = false;  // warp-uniform: the counter passed the last slot
+    unsigned long long ri = 0;
+    const unsigned long long t0 = wd.max_ns ? global_ns() : 0ull;
+    unsigned long long iters = 0;
+    for (;;) {
+        const uint32_t busy = __ballot_sync(kFullMask, has);
+        if (!exhausted && (uint32_t)__popc(busy) < refill) {
+            const uint32_t idle = ~busy;
+            const uint32_t nidle = (uint32_t)__popc(idle);
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(work, (unsigned long long)nidle);
+            base = __shfl_sync(kFullMask, base, 0);
+            if (base + nidle >= map.threads) exhausted = true;
+            if (!has) {
+                const unsigned long long slot = base + (unsigned long long)__popc(idle & lt_mask);
+                ri = slot < map.threads ? ray_of_thread(slot, map) : map.n;
+                if (ri < map.n) {
+                    has = start(ri);
+                    if (!has) finish(ri);
+                }
+            }
+        }
+        const uint32_t live = __ballot_sync(kFullMask, has);
+        if (live == 0u && exhausted) break;
+        if (watchdog_expired(wd, ++iters, t0)) {
+            if (lane == 0) atomicOr(err, kErrTimeout);
+            if (has) {
+                fail();
+                finish(ri);
+                has = false;
+            }
+            break;
+        }
+        if constexpr (LS) {
+            if (step(has)) {
+                finish(ri);
+                has = false;
+            }
+        } else {
+            if (has && step(true)) {
+                finish(ri);
+                has = false;
+            }
+            __syncwarp();
+        }
+    }
 }
 
 // Ambient-occlusion sampling frame at a hit: face normal of the triangle

@@ -53,8 +53,34 @@ bool stack_regs_supported(uint32_t k);
 cudaError_t launch_static_capped(const LaunchArgs& a, int kind, uint32_t min_blocks);
 // Dynamic injection: run-time checked function-pointer table.
 cudaError_t launch_dynamic(const LaunchArgs& a, int kind);
-// Resident blocks per SM for the given kernel configuration (0 on error).
-int persistent_grid(const LaunchArgs& a, const void* kernel, size_t smem);
+// Grid of a persistent launch: SMs x resident blocks per SM (blocks_per_sm,
+// or the occupancy of `kernel` at this block size and shared memory when 0);
+// 0 on error.
+int persistent_grid(uint32_t block, uint32_t blocks_per_sm, const void* kernel, size_t smem);
+inline int persistent_grid(const LaunchArgs& a, const void* kernel, size_t smem) {
+    return persistent_grid(a.block, a.blocks_per_sm, kernel, smem);
+}
+
+// Run `launch(counter)` with a persistent launch's ray counter, zeroed on
+// `stream` first: `given` when not null, else 8 bytes of stream-ordered
+// scratch freed on the stream after the launch, so persistent launches on
+// different streams never share a counter.
+template <class Launch>
+cudaError_t with_ray_counter(unsigned long long* given, cudaStream_t stream, Launch&& launch) {
+    unsigned long long* work = given;
+    cudaError_t e = cudaSuccess;
+    if (!work) {
+        e = cudaMallocAsync(reinterpret_cast<void**>(&work), sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) e = launch(work);
+    if (!given) {
+        const cudaError_t f = cudaFreeAsync(work, stream);
+        if (e == cudaSuccess) e = f;
+    }
+    return e;
+}
 
 // Multi-hit query (trace_multi.cu): the first nh (1..16) accepted hits per
 // ray in ascending (t, prim) order into a.hits [n * nh].
@@ -87,6 +113,10 @@ struct InstLaunch {
     uint32_t block;
     uint32_t stack_words;  // top-level depth + deepest mesh
     cudaStream_t stream;
+    uint32_t persistent;     // 1: persistent warps (per-lane loops)
+    uint32_t refill;         // persistent: refill threshold
+    uint32_t blocks_per_sm;  // persistent: resident blocks per SM (0: occupancy)
+    Watchdog wd;             // persistent: iteration and time budget
 };
 cudaError_t launch_instances(const InstLaunch& L, int kind, int query, bool dynamic);
 // Source line of the first misaligned access the instanced kernels skipped

@@ -113,9 +113,12 @@ def test_argument_checks(V, small):
     I, rays, X = small
     d = _dev(rays[:64])
     hits = torch.empty((64, 4), dtype=torch.float32, device="cuda")
-    with pytest.raises(V.VsrError, match="one ray per thread"):
+    with pytest.raises(V.VsrError, match="lockstep 0"):
         V.vsr_trace_instances(X, d, V.intersector("default"), "closest", hits, None, None,
-                              V.trace_params(persistent=1))
+                              V.trace_params(persistent=1, lockstep=1))
+    with pytest.raises(V.VsrError, match="refill_threshold"):
+        V.vsr_trace_instances(X, d, V.intersector("default"), "closest", hits, None, None,
+                              V.trace_params(persistent=1, refill_threshold=0))
     ms = X.meshes
     with pytest.raises(V.VsrError, match="missing mesh"):
         V.vsr_instances_create(ms, np.full(len(I.inst_mesh), 5, np.uint32), I.w2o, I.top)
@@ -177,4 +180,65 @@ def test_dynamic_dispatch_equals_static(V, small, kind, query):
         assert np.array_equal(a[2], b[2])
     c = _gpu(V, X, d, kind, query, V.trace_params(image_width=128), dispatch="dynamic")
     assert np.array_equal(a[0].view(np.uint32), c[0].view(np.uint32))
+    assert V.vsr_instances_device_error(X) == 0
+
+
+@pytest.mark.parametrize("query", ["closest", "any"])
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("dispatch", ["static", "dynamic"])
+def test_persistent_matches_oracle(V, small, kind, query, dispatch):
+    """Persistent warps, each lane's two-level traversal resumable step by
+    step (a mesh step, or the top level's advance to the next instance whose
+    mesh root the ray hits): hits, instance ids and counters are the
+    oracle's."""
+    I, rays, X = small
+    ref, rids, st = _oracle(I, rays, kind, query)
+    d = _dev(rays)
+    for c in (dict(refill_threshold=16), dict(refill_threshold=1, block_size=64),
+              dict(refill_threshold=32, image_width=128, block_size=256)):
+        p = V.trace_params(persistent=1, watchdog_ms=10_000, **c)
+        got, ids, cnt = _gpu(V, X, d, kind, query, p, dispatch=dispatch)
+        ok = _compare(got, ids, ref, rids, st, f"{dispatch} {kind}/{query} {c}")
+        if cnt is not None:
+            assert np.array_equal(cnt[ok], st[ok, :2])
+    assert V.vsr_instances_device_error(X) == 0
+    for m in X.meshes:
+        assert V.vsr_get_device_error(m) == 0
+
+
+@pytest.mark.parametrize("n", [1, 33, 4097])
+def test_persistent_ragged(V, small, n):
+    I, rays, X = small
+    sel = np.resize(rays[::-1], (n, 8))
+    for q in ("closest", "any"):
+        ref, rids, st = _oracle(I, sel, "alpha_tex", q)
+        got, ids, _ = _gpu(V, X, _dev(sel), "alpha_tex", q,
+                           V.trace_params(persistent=1, refill_threshold=8, watchdog_ms=10_000))
+        _compare(got, ids, ref, rids, st, f"n={n} {q}")
+
+
+def test_persistent_watchdog(V, small):
+    """A watchdog of 3 outer iterations per warp runs out: the instance set's
+    error word gets the timeout bit, every record is the full result, a miss
+    written for a ray in flight or the fill value of a ray never claimed; a
+    run with the default budget afterwards is complete and clean."""
+    I, rays, X = small
+    d = _dev(rays)
+    full, fids, _ = _gpu(V, X, d, "default", "closest")
+    cut = V.trace_params(persistent=1, refill_threshold=16, watchdog_iterations=3)
+    n = rays.shape[0]
+    hits = torch.full((n, 4), -5.0, dtype=torch.float32, device="cuda")
+    V.vsr_trace_instances(X, d, V.intersector("default"), "closest", hits, None, None, cut)
+    torch.cuda.synchronize()
+    word = V.vsr_instances_device_error(X)
+    assert word & V.DEVERR_TIMEOUT, word
+    h = hits.cpu().numpy()
+    same = np.all(h.view(np.uint32) == full.view(np.uint32), axis=1)
+    miss = h[:, 3].view(np.uint32) == O.NONE
+    fill = np.all(h == -5.0, axis=1)
+    assert (same | miss | fill).all() and not same.all()
+    got, ids, _ = _gpu(V, X, d, "default", "closest",
+                       V.trace_params(persistent=1, refill_threshold=16, watchdog_ms=10_000))
+    assert np.array_equal(got.view(np.uint32), full.view(np.uint32))
+    assert np.array_equal(ids, fids)
     assert V.vsr_instances_device_error(X) == 0

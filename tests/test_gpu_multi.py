@@ -97,9 +97,9 @@ def test_argument_checks(V, small):
     for nh in (0, 17):
         with pytest.raises(V.VsrError):
             V.vsr_trace_multi(s, d, V.intersector("default"), nh, hits)
-    with pytest.raises(V.VsrError, match="one ray per thread"):
+    with pytest.raises(V.VsrError, match="persistent 1"):
         V.vsr_trace_multi(s, d, V.intersector("default"), 4, hits, None,
-                          V.trace_params(persistent=1))
+                          V.trace_params(lockstep=1))
     small_hits = torch.empty((64, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(V.VsrError, match="hits"):
         V.vsr_trace_multi(s, _dev(np.resize(rays, (1 << 16, 8))), V.intersector("default"), 16,
@@ -150,3 +150,47 @@ def test_dynamic_dispatch_equals_static(V, small, kind, nh):
     ref, st = O.trace_multi(sc, rays, nh, kind, blob)
     _compare(b, ref, st, f"dynamic {kind} N={nh}")
     assert V.vsr_get_device_error(s) == 0
+
+
+PERSISTENT = [dict(persistent=1, refill_threshold=16, watchdog_ms=10_000),
+              dict(persistent=1, refill_threshold=24, lockstep=1, watchdog_ms=10_000),
+              dict(persistent=1, refill_threshold=1, lockstep=1, image_width=256, block_size=64,
+                   watchdog_ms=10_000)]
+
+
+@pytest.mark.parametrize("nh", [1, 4, 16])
+@pytest.mark.parametrize("kind", KINDS + ["clip"])
+@pytest.mark.parametrize("dispatch", ["static", "dynamic"])
+def test_persistent_matches_oracle(V, small, kind, nh, dispatch):
+    """Persistent warps (per-lane loops and lock step, whose closest-hit
+    speculation bounds boxes by the buffer's last entry) give the oracle's
+    records and counters, with either dispatch."""
+    if dispatch == "dynamic" and kind == "clip":
+        pytest.skip("the clip box is compiled in only (static dispatch)")
+    sc, rays, blob, s = small
+    clip = dict(clip_lo=(0.2, 0.1, 0.0), clip_hi=(0.8, 0.7, 0.9)) if kind == "clip" else {}
+    ref, st = O.trace_multi(sc, rays, nh, kind, blob, **clip)
+    d = _dev(rays)
+    cnt = kind == "count"
+    for c in PERSISTENT:
+        n = rays.shape[0]
+        hits = torch.full((n, nh, 4), float("nan"), dtype=torch.float32, device="cuda")
+        cn = torch.full((n, 2), -1, dtype=torch.int32, device="cuda") if cnt else None
+        V.vsr_trace_multi(s, d, V.intersector(kind, dispatch, **clip), nh, hits, cn,
+                          V.trace_params(**c))
+        torch.cuda.synchronize()
+        _compare(hits.cpu().numpy(), ref, st, f"{dispatch} {kind} nh={nh} {c}")
+        if cnt:
+            ok = st[:, 3] == 0
+            assert np.array_equal(cn.cpu().numpy().view(np.uint32)[ok], st[ok, :2])
+    assert V.vsr_get_device_error(s) == 0
+
+
+@pytest.mark.parametrize("n", [1, 33, 4097])
+def test_persistent_ragged(V, small, n):
+    sc, rays, blob, s = small
+    sel = np.resize(rays[::-1], (n, 8))
+    ref, st = O.trace_multi(sc, sel, 6, "proc_alpha", blob)
+    for c in PERSISTENT:
+        got, _ = _multi(V, s, _dev(sel), "proc_alpha", 6, V.trace_params(**c))
+        _compare(got, ref, st, f"n={n} {c}")

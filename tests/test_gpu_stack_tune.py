@@ -110,7 +110,7 @@ def test_dynamic_persistent_and_lockstep_match_oracle(V, small, kind, query):
 
 def test_dynamic_persistent_ragged(V):
     """Dynamic dispatch, persistent and lock step, on ray counts that leave
-    partly filled warps, and with register budgets refused."""
+    partly filled warps, and at every register budget."""
     sc, rays = scenes.small_quads(seed=scenes.SEED_BASE + 45)
     blob = sc.bvh()
     s = V.scene_from_inputs(sc, blob)
@@ -124,14 +124,20 @@ def test_dynamic_persistent_ragged(V):
                                   params=V.trace_params(lockstep=ls, persistent=pers,
                                                         watchdog_ms=10_000))
                 _same_as_oracle(hits, ref, st, f"dynamic n={n} {q} pers={pers} ls={ls}")
-    hits = torch.empty((len(rays), 4), dtype=torch.float32, device="cuda")
+    # every register budget of the dynamic persistent and lock-step kernels
     d_rays = torch.from_numpy(rays).cuda()
-    with pytest.raises(V.VsrError, match="reg_cap_blocks 0"):
-        V.vsr_trace(s, d_rays, V.intersector("default", "dynamic"), "closest", hits, None,
-                    V.trace_params(persistent=1, reg_cap_blocks=3))
-    with pytest.raises(V.VsrError, match="reg_cap_blocks 0"):
+    for q in ("closest", "any"):
+        ref, st = O.trace_bvh(sc, blob, rays, "alpha_tex", q)
+        for cap in (1, 3, 4):
+            for pers, ls in ((1, 0), (1, 1), (0, 1)):
+                hits, _ = V.trace(s, d_rays, "alpha_tex", q, dispatch="dynamic",
+                                  params=V.trace_params(lockstep=ls, persistent=pers,
+                                                        reg_cap_blocks=cap, watchdog_ms=10_000))
+                _same_as_oracle(hits, ref, st, f"dynamic {q} cap={cap} pers={pers} ls={ls}")
+    hits = torch.empty((len(rays), 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(V.VsrError, match="reg_cap_blocks 5 and 6"):
         V.vsr_trace(s, d_rays, V.intersector("default", "dynamic"), "any", hits, None,
-                    V.trace_params(lockstep=1, reg_cap_blocks=4))
+                    V.trace_params(persistent=1, reg_cap_blocks=5))
     assert V.vsr_get_device_error(s) == 0
     s.close()
 
