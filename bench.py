@@ -277,6 +277,8 @@ def launch_config(p) -> str:
         s += " ray_order=1"
     if getattr(p, "lockstep", 0):
         s += " lockstep=1"
+    if getattr(p, "octant", 0):
+        s += " octant=1"
     return s
 
 
@@ -846,6 +848,30 @@ def breakdown(V, s, d_rays, rays_s, n, flush, stream, torch, reps=5):
                     if r >= 2:
                         ms.append(e0.elapsed_time(e1))
                 res[f"stack_regs/{q}/block{block}/K{k}_ms"] = round(statistics.median(ms), 4)
+    # box tests specialised to the direction octant a warp's rays share,
+    # against the generic test: every static intersector, both passes, same
+    # tiles, launches interleaved
+    for kind in ("default", "alpha_tex", "proc_alpha", "count"):
+        isect = V.intersector(kind)
+        c = cnt if kind == "count" else None
+        for q, rr in (("closest", d_rays), ("any", rays_s)):
+            ms = {0: [], 1: []}
+            for r in range(reps + 2):
+                for oc in (0, 1):
+                    p = V.trace_params(block_size=128, image_width=FRAME_W, octant=oc)
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    V.vsr_trace(s, rr, isect, q, hits, c, p, stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if r >= 2:
+                        ms[oc].append(e0.elapsed_time(e1))
+            t0, t1 = statistics.median(ms[0]), statistics.median(ms[1])
+            res[f"octant/{q}/{kind}/generic_ms"] = round(t0, 4)
+            res[f"octant/{q}/{kind}/octant_ms"] = round(t1, 4)
+            res[f"octant/{q}/{kind}/speedup"] = round(t0 / t1, 4)
     return res
 
 
@@ -1363,6 +1389,9 @@ def main():
                     help="--leg trace/ao: 1 profiles the persistent launch (--refill)")
     ap.add_argument("--lockstep", type=int, default=0,
                     help="--leg trace/ao/batch_profile: 1 runs each warp in lock step")
+    ap.add_argument("--octant", type=int, default=0,
+                    help="--leg trace/ao: 1 gives warps whose rays share a direction octant "
+                         "a box test compiled for it")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -1442,7 +1471,7 @@ def profile_leg(V, torch, dev, flush, stream, args):
     p = V.trace_params(block_size=args.block, stack_regs=args.stack_regs,
                        image_width=0 if args.ray_order else width, ray_order=args.ray_order,
                        persistent=args.persistent, refill_threshold=args.refill,
-                       lockstep=args.lockstep)
+                       lockstep=args.lockstep, octant=args.octant)
     out = {"config": launch_config(p)}
     if args.leg == "trace":
         alpha = V.intersector("alpha_tex")

@@ -142,7 +142,7 @@ typedef enum vsr_query {
 /* Launch configuration.  vsr_trace with params == NULL uses the
  * configuration vsr_trace_tune chose for the scene, intersector and query (or
  * tunes one on the call's own rays, see vsr_trace_tune); other entry points
- * take NULL as the defaults {128, 0, 16, 0, 0, 0, 0, 0, 0, 0}. */
+ * take NULL as the defaults {128, 0, 16, 0, 0, 0, 0, 0, 0, 0, 0, 0}. */
 typedef struct vsr_trace_params {
     uint32_t block_size;       /* threads per block, multiple of 32, 32..256 */
     uint32_t persistent;       /* 0: one ray per thread; 1: persistent warps
@@ -228,6 +228,24 @@ typedef struct vsr_trace_params {
                                   dynamic dispatch; static: reg_cap_blocks 0),
                                   vsr_trace_multi (persistent 1) and batches;
                                   other entry points take 0. */
+    uint32_t octant;           /* 1 = each warp first checks whether all its
+                                  rays point into the same octant (the signs
+                                  of dx, dy, dz); if so it runs a traversal
+                                  compiled for that octant, whose node box
+                                  test (Section 3.2, intersect(ray, aabb))
+                                  reads the entry and exit plane of each axis
+                                  directly instead of ordering the two planes
+                                  with min/max: five ALU instructions per box
+                                  instead of eleven.  Other warps, and scenes
+                                  whose refitted boxes are not all finite
+                                  with lo <= hi, run the generic test.  The
+                                  outcome of every box test is the same, so
+                                  results are identical.  Static dispatch,
+                                  one ray per thread, per-lane loops
+                                  (persistent 0, lockstep 0), stack_regs 0,
+                                  reg_cap_blocks 0 or 1; vsr_trace,
+                                  vsr_render and vsr_path_trace; other entry
+                                  points take 0. */
 } vsr_trace_params;
 
 typedef struct vsr_scene vsr_scene;

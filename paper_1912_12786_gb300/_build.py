@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libvsr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["api.cu", "trace_static.cu", "trace_k0.cu", "trace_k1.cu", "trace_k2.cu",
-              "trace_k4.cu", "trace_k8.cu", "trace_caps.cu", "trace_dynamic.cu", "trace_multi.cu",
+              "trace_k4.cu", "trace_k8.cu", "trace_oct.cu", "trace_caps.cu", "trace_dynamic.cu", "trace_multi.cu",
               "trace_instances.cu", "render.cu", "batch.cu", "sort.cu", "path.cu", "measure.cu"]
 CPP_SOURCES = [os.path.join(PKG, "inputs", "bvh_build.cpp")]
 _lock = threading.Lock()

@@ -33,7 +33,7 @@ struct vsr_scene {
     bool has_bvh = false;
     DevScene dev{};
     DevScene* d_user = nullptr;
-    uint32_t* d_err = nullptr;
+    uint32_t* d_err = nullptr;  // [0] device error word; [1] refit box state
     // kept for updates: leaf order, node ids by tree level (deepest first),
     // host copies of the texture descriptors
     uint32_t* d_order = nullptr;
@@ -343,6 +343,7 @@ vsr_status apply_params(LaunchArgs& a, uint64_t n, const vsr_trace_params& prm) 
     a.wd = make_watchdog(prm);
     a.reg_cap = prm.reg_cap_blocks;
     a.lockstep = prm.lockstep;
+    a.octant = prm.octant;
     return VSR_OK;
 }
 
@@ -370,6 +371,12 @@ vsr_status prepare_launch(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (prm.lockstep > 1) return fail(VSR_ERR_ARG, "lockstep must be 0 or 1");
     if (prm.lockstep && prm.reg_cap_blocks && is->dispatch == VSR_DISPATCH_STATIC)
         return fail(VSR_ERR_ARG, "lockstep 1 with static dispatch takes reg_cap_blocks 0");
+    if (prm.octant > 1) return fail(VSR_ERR_ARG, "octant must be 0 or 1");
+    if (prm.octant && (prm.persistent || prm.lockstep || prm.stack_regs ||
+                       prm.reg_cap_blocks >= 3 || is->dispatch != VSR_DISPATCH_STATIC))
+        return fail(VSR_ERR_ARG,
+                    "octant 1 takes static dispatch, persistent 0, lockstep 0, stack_regs 0 "
+                    "and reg_cap_blocks 0 or 1");
     if (prm.reg_cap_blocks >= 5 && is->dispatch == VSR_DISPATCH_DYNAMIC)
         return fail(VSR_ERR_ARG, "reg_cap_blocks 5 and 6 are for static dispatch");
     if (prm.reg_cap_blocks >= 3 && is->dispatch == VSR_DISPATCH_STATIC &&
@@ -484,6 +491,12 @@ vsr_status tune_trace(vsr_scene* s, const LaunchArgs& base, const vsr_intersecto
             for (uint32_t k : {0u, 1u, 2u, 4u, 8u})
                 if ((!dynamic || k == 0) && !(b == 128u && k == 0u && ls == 0u))
                     consider(vsr_trace_params{b, 0u, 16u, 0u, image_width, k, 0u, 0u, 0u, 0u, ls});
+    if (!dynamic)  // box tests specialised to a warp's direction octant
+        for (uint32_t b : {64u, 128u, 256u}) {
+            vsr_trace_params c{b, 0u, 16u, 0u, image_width, 0u, 0u, 0u, 0u, 0u, 0u};
+            c.octant = 1u;
+            consider(c);
+        }
     if (base.n <= coherence_sort_max_rays()) {
         // the fastest one-ray-per-thread configuration in coherence order
         // (the sort is part of every timed launch)
@@ -500,6 +513,7 @@ vsr_status tune_trace(vsr_scene* s, const LaunchArgs& base, const vsr_intersecto
                 c.persistent = 1u;
                 c.refill_threshold = r;
                 c.lockstep = ls;
+                c.octant = 0u;
                 consider(c);
             }
     }
@@ -583,7 +597,7 @@ vsr_status vsr_scene_create_indexed(const float* verts, uint32_t nverts, const u
         (e = dmalloc(&s->d_geom, (size_t)ntri)) != cudaSuccess ||
         (e = dmalloc(&s->d_tex, (size_t)ntex)) != cudaSuccess ||
         (e = dmalloc(&s->d_texels, (size_t)texel_bytes)) != cudaSuccess ||
-        (e = dmalloc(&s->d_user, 1)) != cudaSuccess || (e = dmalloc(&s->d_err, 1)) != cudaSuccess)
+        (e = dmalloc(&s->d_user, 1)) != cudaSuccess || (e = dmalloc(&s->d_err, 2)) != cudaSuccess)
         return bail(cuda_fail(e, "scene allocation"));
     if ((nverts && (e = cudaMemcpy(s->d_verts, verts, 12ull * nverts, cudaMemcpyHostToDevice))) ||
         (ntri && (e = cudaMemcpy(s->d_idx, idx, 12ull * ntri, cudaMemcpyHostToDevice))) ||
@@ -591,7 +605,7 @@ vsr_status vsr_scene_create_indexed(const float* verts, uint32_t nverts, const u
         (ntri && (e = cudaMemcpy(s->d_geom, geom_id, 4ull * ntri, cudaMemcpyHostToDevice))) ||
         (ntex && (e = cudaMemcpy(s->d_tex, td.data(), sizeof(TexDesc) * ntex,
                                  cudaMemcpyHostToDevice))) ||
-        (e = cudaMemset(s->d_err, 0, sizeof(uint32_t))))
+        (e = cudaMemset(s->d_err, 0, 2 * sizeof(uint32_t))))
         return bail(cuda_fail(e, "scene upload"));
     for (uint32_t k = 0; k < ntex; ++k) {
         const size_t b = (size_t)tex[k].w * tex[k].h * texel_size(tex[k].fmt);
@@ -710,6 +724,7 @@ vsr_status vsr_bvh_load(vsr_scene* s, const void* blob, size_t bytes) {
     d.root_ref = node_ref(nodes[0]);
     d.stack_depth = max_depth > 0 ? max_depth : 1u;
     d.max_steps = num_nodes + 2u;
+    d.boxes_ordered = 1u;  // the validator checked every box: finite, lo <= hi
     d.root_a = make_float4(nodes[0].lo[0], nodes[0].lo[1], nodes[0].lo[2], 0.0f);
     d.root_b = make_float4(nodes[0].hi[0], nodes[0].hi[1], nodes[0].hi[2], 0.0f);
     if ((e = cudaMemcpy(s->d_user, &d, sizeof(DevScene), cudaMemcpyHostToDevice)) != cudaSuccess) {
@@ -822,6 +837,8 @@ vsr_status vsr_trace_multi(vsr_scene* s, const vsr_ray* rays, uint64_t n,
     if (max_hits < 1 || max_hits > 16) return fail(VSR_ERR_ARG, "max_hits must be in 1..16");
     if (p && p->lockstep && !p->persistent)
         return fail(VSR_ERR_ARG, "the multi-hit query runs lockstep 1 with persistent 1");
+    if (p && p->octant)
+        return fail(VSR_ERR_ARG, "octant 1 is for vsr_trace, vsr_render and vsr_path_trace");
     LaunchArgs a;
     vsr_status st = prepare_launch(s, rays, n, is, VSR_CLOSEST, hits, p, a);
     if (st != VSR_OK) return st;
@@ -1282,13 +1299,16 @@ extern "C" vsr_status vsr_scene_update(vsr_scene* s, const float* verts, uint32_
                                  cs),
                  "vertex update");
         if (s->has_bvh && s->dev.nprims) {
+            // word 1 of the error allocation: set by the refit if a box comes
+            // out non-finite or inverted
+            VSR_CUDA(cudaMemsetAsync(s->d_err + 1, 0, sizeof(uint32_t), cs), "box state");
             k_build_tris<<<(s->dev.nprims + 255) / 256, 256, 0, cs>>>(s->d_verts, s->d_idx,
                                                                     s->d_order, s->dev.nprims,
                                                                     s->d_tris);
             VSR_CUDA(cudaGetLastError(), "triangle layout");
             VSR_CUDA(launch_refit(s->d_nodes, s->d_levels, s->level_offsets.data(),
                                   (uint32_t)s->level_offsets.size() - 1u, s->d_verts, s->d_idx,
-                                  s->d_order, cs),
+                                  s->d_order, s->d_err + 1, cs),
                      "refit");
         }
     }
@@ -1298,6 +1318,10 @@ extern "C" vsr_status vsr_scene_update(vsr_scene* s, const float* verts, uint32_
         VSR_CUDA(cudaMemcpy(root, s->d_nodes, sizeof(root), cudaMemcpyDeviceToHost), "root box");
         s->dev.root_a = make_float4(root[0].x, root[0].y, root[0].z, 0.0f);
         s->dev.root_b = make_float4(root[1].x, root[1].y, root[1].z, 0.0f);
+        uint32_t unordered = 0;
+        VSR_CUDA(cudaMemcpy(&unordered, s->d_err + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost),
+                 "box state");
+        s->dev.boxes_ordered = unordered ? 0u : 1u;
         VSR_CUDA(cudaMemcpy(s->d_user, &s->dev, sizeof(DevScene), cudaMemcpyHostToDevice),
                  "scene descriptor upload");
     }
@@ -1528,6 +1552,7 @@ vsr_status validate_params(const vsr_trace_params& p) {
     if (p.ray_order > 1) return fail(VSR_ERR_ARG, "ray_order must be 0 or 1");
     if (p.reg_cap_blocks != 0) return fail(VSR_ERR_ARG, "batched launches take reg_cap_blocks 0");
     if (p.lockstep > 1) return fail(VSR_ERR_ARG, "lockstep must be 0 or 1");
+    if (p.octant) return fail(VSR_ERR_ARG, "batched launches take octant 0");
     if (p.image_width != 0)
         return fail(VSR_ERR_ARG, "batched launches take rays in buffer order (image_width 0)");
     return VSR_OK;
@@ -2032,6 +2057,7 @@ extern "C" vsr_status vsr_trace_instances(vsr_instances* x, const vsr_ray* rays,
         return fail(VSR_ERR_ARG, "refill_threshold must be in 1..32");
     if (prm.blocks_per_sm > 32) return fail(VSR_ERR_ARG, "blocks_per_sm above 32");
     if (prm.lockstep) return fail(VSR_ERR_ARG, "instanced traces take lockstep 0");
+    if (prm.octant) return fail(VSR_ERR_ARG, "instanced traces take octant 0");
     if (prm.ray_order) return fail(VSR_ERR_ARG, "instanced traces take ray_order 0");
     if (n > (uint64_t)(std::numeric_limits<int>::max() - 1) * 32ull)
         return fail(VSR_ERR_ARG, "too many rays for one launch");

@@ -352,7 +352,8 @@ __global__ void __launch_bounds__(256) k_ao_backward(DevScene sc, ShadeDev sh,
 // Topology and the packed references are unchanged.
 __global__ void k_refit(float4* __restrict__ nodes, const uint32_t* __restrict__ level_nodes,
                         uint32_t count, const float* __restrict__ verts,
-                        const uint32_t* __restrict__ idx, const uint32_t* __restrict__ order) {
+                        const uint32_t* __restrict__ idx, const uint32_t* __restrict__ order,
+                        uint32_t* __restrict__ unordered) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
     const uint32_t id = level_nodes[t];
@@ -387,6 +388,11 @@ __global__ void k_refit(float4* __restrict__ nodes, const uint32_t* __restrict__
     }
     nodes[2ull * id] = make_float4(lo[0], lo[1], lo[2], a.w);
     nodes[2ull * id + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+    // the octant-specialised box test needs finite boxes with lo <= hi
+    bool ordered = true;
+    for (int c = 0; c < 3; ++c)
+        ordered = ordered && isfinite(lo[c]) && isfinite(hi[c]) && lo[c] <= hi[c];
+    if (!ordered) atomicOr(unordered, 1u);
 }
 
 cudaError_t launch_shade_hits(const DevScene& sc, const ShadeDev& sh, const float* verts,
@@ -417,12 +423,13 @@ cudaError_t render_align_error(unsigned* line) {
 
 cudaError_t launch_refit(float4* nodes, const uint32_t* level_nodes,
                          const uint32_t* level_offsets, uint32_t levels, const float* verts,
-                         const uint32_t* idx, const uint32_t* order, cudaStream_t stream) {
+                         const uint32_t* idx, const uint32_t* order, uint32_t* unordered,
+                         cudaStream_t stream) {
     for (uint32_t l = 0; l < levels; ++l) {
         const uint32_t begin = level_offsets[l], count = level_offsets[l + 1] - begin;
         if (count == 0) continue;
         k_refit<<<(count + 255) / 256, 256, 0, stream>>>(nodes, level_nodes + begin, count, verts,
-                                                         idx, order);
+                                                         idx, order, unordered);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -18,6 +18,7 @@ cudaError_t launch_static(const LaunchArgs& a, int kind, bool stats) {
     // changes neither the visiting order nor the counts
     if (stats) return launch_static_k0(a, kind, true);
     if (a.reg_cap >= 3) return launch_static_capped(a, kind, a.reg_cap);
+    if (a.octant) return launch_static_octant(a, kind);
     switch (a.stack_regs) {
         case 0: return launch_static_k0(a, kind, false);
         case 1: return launch_static_k1(a, kind, false);

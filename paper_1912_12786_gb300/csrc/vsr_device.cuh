@@ -80,7 +80,9 @@ struct DevScene {
     uint32_t* err;
     uint32_t nprims, ntex, root_ref, stack_depth;
     uint32_t max_steps;     // node visits per ray never exceed the node count
-    uint32_t pad[3];
+    uint32_t boxes_ordered; // 1: every node box is finite with lo <= hi (a
+                            // validated blob; rechecked by each refit)
+    uint32_t pad[2];
     float4 root_a, root_b;  // root box (lo, hi) in .xyz
 };
 
@@ -200,6 +202,33 @@ __device__ __forceinline__ bool box_hit(const Ray& r, float4 lo, float4 hi, floa
     const float tn = fmax3(fminf(t0x, t1x), fminf(t0y, t1y), fmaxf(fminf(t0z, t1z), r.tmin));
     const float tf = fmin3(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fminf(fmaxf(t0z, t1z), tfar));
     return tn <= tf;
+}
+
+// box_hit for rays whose direction signs are known at compile time: OCT bit
+// a is set iff d[a] has its sign bit set (Ray::negmask).  The guarded inverse
+// direction has the sign of d, so along axis a the entry plane is lo[a] for a
+// clear bit and hi[a] for a set one, and each axis needs no min/max: five
+// ALU-pipe instructions (two three-input max/min, the two limits, one
+// compare) instead of eleven.  For a box with finite lo <= hi this is box_hit
+// bit for bit: FMA rounding is monotone in the plane coordinate, so the
+// plane picked is the one min/max would pick (equal values, at most of
+// opposite zero sign, which the comparison does not see); a NaN or infinite
+// slab value comes out of both planes alike.  Inverted or non-finite boxes do
+// not occur in a validated blob; after a refit the kernels that use this test
+// check the scene's box-state word first.  OCT < 0 is box_hit.
+template <int OCT>
+__device__ __forceinline__ bool box_hit_o(const Ray& r, float4 lo, float4 hi, float tfar) {
+    if constexpr (OCT < 0) {
+        return box_hit(r, lo, hi, tfar);
+    } else {
+        const float nx = __fmaf_rn((OCT & 1) ? hi.x : lo.x, r.ix, r.nox);
+        const float fx = __fmaf_rn((OCT & 1) ? lo.x : hi.x, r.ix, r.nox);
+        const float ny = __fmaf_rn((OCT & 2) ? hi.y : lo.y, r.iy, r.noy);
+        const float fy = __fmaf_rn((OCT & 2) ? lo.y : hi.y, r.iy, r.noy);
+        const float nz = __fmaf_rn((OCT & 4) ? hi.z : lo.z, r.iz, r.noz);
+        const float fz = __fmaf_rn((OCT & 4) ? lo.z : hi.z, r.iz, r.noz);
+        return fmax3(nx, ny, fmaxf(nz, r.tmin)) <= fmin3(fx, fy, fminf(fz, tfar));
+    }
 }
 
 // box_hit that also gives the entry distance tn: the box is hit with a
@@ -542,7 +571,10 @@ __host__ __device__ __forceinline__ uint32_t stack_words(uint32_t depth, uint32_
 }
 
 // The while-while traversal (Section 3.2) with the intersector's hooks.
-template <int Q, class H, bool STATS, class B = Best, class S>
+// OCT >= 0: every node box test is box_hit_o<OCT> (the caller checked that
+// the ray's direction octant is OCT and that the scene's boxes are finite
+// and ordered), so the visits and results are those of OCT = -1.
+template <int Q, class H, bool STATS, int OCT = -1, class B = Best, class S>
 __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectParams& ip,
                                               const Ray& r, H& h, B& best, Stats& st, S& stk) {
     best.init(r.tmax);
@@ -551,7 +583,8 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
     h.begin(r, ip);
     h.box();
     if (STATS) st.boxes++;
-    if (!box_hit(r, sc.root_a, sc.root_b, h.far(best.t)) || !h.keep(ip, sc.root_a, sc.root_b))
+    if (!box_hit_o<OCT>(r, sc.root_a, sc.root_b, h.far(best.t)) ||
+        !h.keep(ip, sc.root_a, sc.root_b))
         return;
     uint32_t ref = sc.root_ref;
     uint32_t steps = 0;
@@ -568,11 +601,12 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
             h.box();
             h.box();
             if (STATS) st.boxes += 2;
-            const bool hl = box_hit(r, la, lb, tfar) && h.keep(ip, la, lb);
-            const bool hr = box_hit(r, ra, rb, tfar) && h.keep(ip, ra, rb);
+            const bool hl = box_hit_o<OCT>(r, la, lb, tfar) && h.keep(ip, la, lb);
+            const bool hr = box_hit_o<OCT>(r, ra, rb, tfar) && h.keep(ip, ra, rb);
             const uint32_t rl = __float_as_uint(la.w), rr = __float_as_uint(ra.w);
             if (hl && hr) {
-                const bool neg = (r.negmask >> (ref & 3u)) & 1u;
+                const bool neg = OCT >= 0 ? (((unsigned)OCT >> (ref & 3u)) & 1u)
+                                          : ((r.negmask >> (ref & 3u)) & 1u);
                 if (stk.n >= sc.stack_depth) {  // unreachable for a validated blob
                     atomicOr(sc.err, kErrStack);
                     best.fail();
@@ -627,10 +661,10 @@ __device__ __forceinline__ void traverse_body(const DevScene& sc, const IsectPar
 
 // Full query: traversal, then every miss (root missed, empty or inactive
 // interval, nothing accepted) is reported as t = +inf, u = v = 0.
-template <int Q, class H, bool STATS, class S>
+template <int Q, class H, bool STATS, int OCT = -1, class S>
 __device__ __forceinline__ void traverse(const DevScene& sc, const IsectParams& ip, const Ray& r,
                                          H& h, Best& best, Stats& st, S& stk) {
-    traverse_body<Q, H, STATS>(sc, ip, r, h, best, st, stk);
+    traverse_body<Q, H, STATS, OCT>(sc, ip, r, h, best, st, stk);
     if (best.prim == kMiss) {
         best.t = __int_as_float(0x7f800000);
         best.u = 0.0f;

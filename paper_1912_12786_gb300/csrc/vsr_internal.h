@@ -33,6 +33,8 @@ struct LaunchArgs {
     uint32_t reg_cap;          // 0: each kernel's own register budget; 1, 3..6:
                                // __launch_bounds__(256, reg_cap) variants
     uint32_t lockstep = 0;     // 1: the warp runs the traversal in lock step
+    uint32_t octant = 0;       // 1: box tests specialised to a warp's shared
+                               // direction octant (k_trace_oct)
 };
 
 // Shading parameters of the differentiable render (device copy).
@@ -46,6 +48,7 @@ struct ShadeDev {
 // Static injection: one instantiation per (query, intersector, stats,
 // register-stack depth).
 cudaError_t launch_static(const LaunchArgs& a, int kind, bool stats);
+cudaError_t launch_static_octant(const LaunchArgs& a, int kind);
 // Register-stack depths the static kernels are instantiated for.
 bool stack_regs_supported(uint32_t k);
 // The static one-ray-per-thread kernel under __launch_bounds__(256, 3..6)
@@ -242,9 +245,12 @@ cudaError_t launch_ao_backward(const DevScene& sc, const AoArgs& ao, unsigned lo
                                cudaStream_t stream);
 
 // Bottom-up refit over node lists grouped by level, deepest first
-// (level_offsets is a host array of levels + 1 entries).
+// (level_offsets is a host array of levels + 1 entries).  Any box that comes
+// out non-finite or with lo > hi on some axis ORs 1 into *unordered (the
+// caller zeroes it first).
 cudaError_t launch_refit(float4* nodes, const uint32_t* level_nodes,
                          const uint32_t* level_offsets, uint32_t levels, const float* verts,
-                         const uint32_t* idx, const uint32_t* order, cudaStream_t stream);
+                         const uint32_t* idx, const uint32_t* order, uint32_t* unordered,
+                         cudaStream_t stream);
 
 }  // namespace vsr

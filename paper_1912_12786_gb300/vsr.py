@@ -67,7 +67,7 @@ class vsr_trace_params(ctypes.Structure):
                 ("image_width", ctypes.c_uint32), ("stack_regs", ctypes.c_uint32),
                 ("watchdog_iterations", ctypes.c_uint32), ("watchdog_ms", ctypes.c_uint32),
                 ("reg_cap_blocks", ctypes.c_uint32), ("ray_order", ctypes.c_uint32),
-                ("lockstep", ctypes.c_uint32)]
+                ("lockstep", ctypes.c_uint32), ("octant", ctypes.c_uint32)]
 
 
 class vsr_path_params(ctypes.Structure):
@@ -191,17 +191,18 @@ def intersector(kind="default", dispatch="static", cutoff_u8=128, cutoff_f=0.01,
 
 def trace_params(block_size=128, persistent=0, refill_threshold=16, blocks_per_sm=0,
                  image_width=0, stack_regs=0, watchdog_iterations=0, watchdog_ms=0,
-                 reg_cap_blocks=0, ray_order=0, lockstep=0):
+                 reg_cap_blocks=0, ray_order=0, lockstep=0, octant=0):
     """vsr_trace_params with the library's defaults; ``image_width`` > 0 maps
     each warp to a 4 x 8 pixel tile of a row-major image of that width;
     ``stack_regs`` stack entries are kept in registers; the watchdog fields
     bound persistent loops (0 iterations: no limit; 0 ms: 60 s);
     ``reg_cap_blocks`` selects a register budget (measurement); ``ray_order``
     1 traces in coherence order; ``lockstep`` 1 runs each warp's traversal
-    in lock step."""
+    in lock step; ``octant`` 1 gives warps whose rays share a direction
+    octant a box test compiled for it."""
     return vsr_trace_params(block_size, persistent, refill_threshold, blocks_per_sm, image_width,
                             stack_regs, watchdog_iterations, watchdog_ms, reg_cap_blocks,
-                            ray_order, lockstep)
+                            ray_order, lockstep, octant)
 
 
 def params_dict(p: vsr_trace_params) -> dict:
