@@ -49,6 +49,8 @@ PROFILE_SUMMARIES = {
         ROOT, "profiles", "trace_ao_any_proc_large_incoherent.md"),
 }
 ALU_LANES_PER_SM = 64  # ALU pipe (min/max, compares, integer): 16 lanes per SMSP
+L1_RETURN_BYTES_PER_CLK = 128  # L1 -> register load-return width per SM (nominal)
+BOX_TEST_ALU_OPS = 5   # slab test with the planes picked by the direction signs
 FLUSH_BYTES = 256 << 20
 
 
@@ -65,9 +67,10 @@ def default_params(V, image_width=FRAME_W):
 
 
 # the device code of the static trace kernels (the dominant kernel): the
-# kernel templates and the traversal they inline (vsr_internal.h adds
-# host-side launch structures only; trace_k<K>.cu only instantiate)
-TRACE_SOURCES = ("trace_static.cuh", "vsr_device.cuh")
+# kernel templates and the traversal they inline, and the octant-dispatching
+# kernel (vsr_internal.h adds host-side launch structures only; trace_k<K>.cu
+# only instantiate)
+TRACE_SOURCES = ("trace_static.cuh", "vsr_device.cuh", "trace_oct.cu")
 
 
 def kernel_source_hash() -> str:
@@ -203,23 +206,34 @@ def trace_bytes(n_rays: int, stats: np.ndarray, texel_bytes: int, texcoords: boo
     return b
 
 
+def trace_load_bytes(n_rays: int, stats: np.ndarray, texel_bytes: int, texcoords: bool) -> int:
+    """Bytes the lanes of one launch load into registers: trace_bytes less
+    the 16-byte hit record each ray stores.  Every lane loads its own node
+    pairs and triangles, so these bytes pass the L1 load-return path even
+    where the lanes of a warp read the same sectors."""
+    return trace_bytes(n_rays, stats, texel_bytes, texcoords) - 16 * n_rays
+
+
 ALU_OPS_PER_LOOKUP = {"alpha_tex": 8, "proc_alpha": 11}
 
 
 def trace_alu_ops(n_rays: int, stats: np.ndarray, lookup_ops: int = 0) -> int:
     """Algorithmic work of one launch on the ALU pipe (the busiest unit), as
     the fewest ALU-pipe instructions this GPU needs for it (a three-input
-    min/max is one instruction): 11 per box test (6 per-axis min/max, 2 each
-    for the entry and exit bounds with tmin and the far limit folded in, 1
-    compare), 7 per triangle test (det == 0, u >= 0, v >= 0, u + v <= 1,
-    t > tmin, t < tmax, t < best), 1 per intersector call, 6 per ray set-up
-    (direction guards), and `lookup_ops` per textured consultation: 8 for
-    the alpha texture (clamps, index bounds, alpha compare), 11 for
-    procedural alpha (per coordinate: the two sign compares of the reduced
-    argument, the quotient's parity and the sign select; then the product's
-    sign)."""
+    min/max is one instruction): 5 per box test (the sign of the ray's
+    direction picks each axis's entry and exit plane, so no per-axis
+    min/max is needed: 2 for the entry bound with tmin folded in, 2 for the
+    exit bound with the far limit, 1 compare; the six plane distances are
+    fused multiply-adds on the FMA pipe), 7 per triangle test (det == 0,
+    u >= 0, v >= 0, u + v <= 1, t > tmin, t < tmax, t < best), 1 per
+    intersector call, 6 per ray set-up (direction guards), and `lookup_ops`
+    per textured consultation: 8 for the alpha texture (clamps, index
+    bounds, alpha compare), 11 for procedural alpha (per coordinate: the two
+    sign compares of the reduced argument, the quotient's parity and the
+    sign select; then the product's sign)."""
     s = stats.astype(np.int64).sum(axis=0)
-    return 6 * n_rays + 11 * int(s[0]) + 7 * int(s[1]) + int(s[2]) + lookup_ops * int(s[3])
+    return (6 * n_rays + BOX_TEST_ALU_OPS * int(s[0]) + 7 * int(s[1]) + int(s[2]) +
+            lookup_ops * int(s[3]))
 
 
 def render_backward_model(n_rays: int, stats: np.ndarray, grad: np.ndarray, lit: np.ndarray):
@@ -321,7 +335,8 @@ def profile_params(V, kernel: str):
                                       stack_regs=int(kv["stack_regs"]),
                                       image_width=int(kv["image_width"]),
                                       ray_order=int(kv.get("ray_order", 0)),
-                                      lockstep=int(kv.get("lockstep", 0)))
+                                      lockstep=int(kv.get("lockstep", 0)),
+                                      octant=int(kv.get("octant", 0)))
     return None
 
 
@@ -545,13 +560,13 @@ def run_ours(args):
     kernels = {
         "trace closest alpha (primary)": (statistics.mean(prim_ms), trace_bytes(n, sp_np, 4, True),
                                           trace_alu_ops(n, sp_np, ALU_OPS_PER_LOOKUP["alpha_tex"]),
-                                          tuned_p),
+                                          tuned_p, trace_load_bytes(n, sp_np, 4, True)),
         "trace any alpha (shadow)": (statistics.mean(shad_ms), trace_bytes(n, ss_np, 4, True),
                                      trace_alu_ops(n, ss_np, ALU_OPS_PER_LOOKUP["alpha_tex"]),
-                                     tuned_s),
+                                     tuned_s, trace_load_bytes(n, ss_np, 4, True)),
     }
     dom = max(kernels, key=lambda k: kernels[k][0])
-    dom_ms, dom_bytes, dom_ops, dom_p = kernels[dom]
+    dom_ms, dom_bytes, dom_ops, dom_p, dom_load = kernels[dom]
     hbm_peak, peak_src = peaks()
     clk_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     alu_peak = sm_count(torch, dev) * ALU_LANES_PER_SM * clk_mhz * 1e6 / 1e12
@@ -562,13 +577,30 @@ def run_ours(args):
     prof_p = profile_params(V, dom)
     levels = profiled_levels(dom, launch_config(prof_p)) if prof_p is not None else None
     traffic = levels["dram"] if levels and launch_config(prof_p) == launch_config(dom_p) else None
-    roofline = {"bound": "alu", "achieved": round(alu_achieved, 3), "peak": round(alu_peak, 3),
-                "unit": "Top/s", "frac": round(alu_achieved / alu_peak, 4), "traffic": traffic,
-                "kernel": dom, "algorithmic_ops_per_launch": dom_ops,
-                "peak_source": f"{sm_count(torch, dev)} SMs x {ALU_LANES_PER_SM} ALU lanes x "
-                               f"{clk_mhz:.0f} MHz",
-                "launch_ms": round(dom_ms, 4), "launch_config": launch_config(dom_p)}
     rp = read_peaks(V, torch, dev)
+    # The busiest unit of the dominant kernel (ncu: the L1 data pipe that
+    # returns load data to registers) carries the bytes every lane loads:
+    # achieved = per-lane load bytes / launch time, against the nominal
+    # load-return width of the SMs at the sampled clock; the L1 read probe's
+    # rate is given beside it.
+    l1_peak = sm_count(torch, dev) * L1_RETURN_BYTES_PER_CLK * clk_mhz * 1e6 / 1e9
+    l1_achieved = dom_load / (dom_ms / 1e3) / 1e9
+    roofline = {"bound": "l1", "achieved": round(l1_achieved, 1), "peak": round(l1_peak, 1),
+                "unit": "GB/s", "frac": round(l1_achieved / l1_peak, 4), "traffic": traffic,
+                "kernel": dom, "algorithmic_bytes_per_launch": dom_load,
+                "algorithmic_note": "bytes the lanes load into registers (rays, node pairs, "
+                                    "triangles, geometry ids, texture coordinates, texels), "
+                                    "per lane, from vsr_trace_stats counts",
+                "peak_source": f"{sm_count(torch, dev)} SMs x {L1_RETURN_BYTES_PER_CLK} B/clk "
+                               f"L1 load return x {clk_mhz:.0f} MHz (nominal)",
+                "probe_GBs": rp["l1"], "frac_of_probe": round(l1_achieved / rp["l1"], 4),
+                "launch_ms": round(dom_ms, 4), "launch_config": launch_config(dom_p)}
+    roofline_alu = {"bound": "alu", "achieved": round(alu_achieved, 3),
+                    "peak": round(alu_peak, 3), "unit": "Top/s",
+                    "frac": round(alu_achieved / alu_peak, 4), "kernel": dom,
+                    "algorithmic_ops_per_launch": dom_ops,
+                    "peak_source": f"{sm_count(torch, dev)} SMs x {ALU_LANES_PER_SM} ALU lanes x "
+                                   f"{clk_mhz:.0f} MHz"}
     level_peaks = {"l1": rp["l1"], "l2": rp["l2"], "dram": hbm_peak}
     mem = {"algorithmic_bytes_per_launch": dom_bytes,
            "algorithmic_GBs": round(dom_bytes / (dom_ms / 1e3) / 1e9, 1),
@@ -606,7 +638,8 @@ def run_ours(args):
                       "ray_order": "row-major frame; each warp traces a 4x8 pixel tile",
                       "l2": "flushed between steps (256 MiB write)",
                       "parallelism": f"replicas x{world} (each rank traces its own frame)"},
-           "roofline": roofline, "roofline_memory": mem, "gpu_launches": 3 * args.steps,
+           "roofline": roofline, "roofline_alu": roofline_alu, "roofline_memory": mem,
+           "gpu_launches": 3 * args.steps,
            "wall_s_timed_region": round(wall, 3),
            "kernel_ms": {"trace_primary": round(statistics.mean(prim_ms), 4),
                          "shadow_rays": round(statistics.mean(gen_ms), 4),
@@ -1301,6 +1334,11 @@ def large_bench(V, torch, dev, flush, stream, steps):
     clk = 2070.0
     alu_peak = sm_count(torch, dev) * ALU_LANES_PER_SM * clk * 1e6 / 1e12
     out["ao_any/proc_alpha/static_alu_frac"] = round(ops / (t / 1e3) / 1e12 / alu_peak, 4)
+    # the per-lane load bytes against the nominal L1 load-return width (the
+    # headline roofline's measure)
+    lb = trace_load_bytes(m, st_np, 0, True)
+    l1_peak = sm_count(torch, dev) * L1_RETURN_BYTES_PER_CLK * clk * 1e6 / 1e9
+    out["ao_any/proc_alpha/static_l1_load_frac"] = round(lb / (t / 1e3) / 1e9 / l1_peak, 4)
     ao_p = tuned_or_default(V, s, proc, "any")
     out["ao_any/proc_alpha/static_launch"] = launch_config(ao_p)
     kern = "trace any proc (ambient occlusion)"

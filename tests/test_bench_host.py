@@ -21,14 +21,21 @@ def test_trace_bytes_procedural_reads_no_texel():
     assert bench.trace_bytes(2, STATS, 0, True) == 96 + 160 + 48 + 4 + 24
 
 
+def test_trace_load_bytes_leave_out_the_hit_store():
+    # 2 rays x 32 ray bytes loaded; the 16-byte hit records are stores
+    assert bench.trace_load_bytes(2, STATS, 4, True) == 64 + 160 + 48 + 4 + 28
+    assert bench.trace_load_bytes(2, STATS, 0, False) == 64 + 160 + 48
+
+
 def test_trace_alu_ops_by_hand():
-    # 6 per ray, 11 per box test, 7 per triangle test, 1 per call, and the
+    # 6 per ray, 5 per box test, 7 per triangle test, 1 per call, and the
     # per-lookup work of the intersector (8 alpha texture, 11 procedural)
+    assert bench.BOX_TEST_ALU_OPS == 5
     assert bench.trace_alu_ops(2, STATS, bench.ALU_OPS_PER_LOOKUP["alpha_tex"]) == \
-        12 + 55 + 7 + 1 + 8
+        12 + 25 + 7 + 1 + 8
     assert bench.trace_alu_ops(2, STATS, bench.ALU_OPS_PER_LOOKUP["proc_alpha"]) == \
-        12 + 55 + 7 + 1 + 11
-    assert bench.trace_alu_ops(2, STATS) == 12 + 55 + 7 + 1
+        12 + 25 + 7 + 1 + 11
+    assert bench.trace_alu_ops(2, STATS) == 12 + 25 + 7 + 1
 
 
 def test_adjoint_models_by_hand():
