@@ -60,10 +60,19 @@ E2E_TRACE_STREAMS = 4  # streams the bands' traces go to, round robin
 
 
 def default_params(V, image_width=FRAME_W):
-    """Launch configuration used for the timed steps (and the full-size test):
-    one ray per thread, warps on 4x8 pixel tiles of the row-major frame."""
+    """Launch configuration of the per-intersector comparisons (and the
+    full-size test): one ray per thread, warps on 4x8 pixel tiles of the
+    row-major frame, the generic box test (either dispatch)."""
     return V.trace_params(block_size=128, persistent=0, refill_threshold=16,
                           image_width=image_width)
+
+
+def octant_params(V, image_width=FRAME_W):
+    """default_params with the box test specialised to a warp's direction
+    octant (static dispatch; what the tuner picks on coherent frames)."""
+    p = default_params(V, image_width)
+    p.octant = 1
+    return p
 
 
 # the device code of the static trace kernels (the dominant kernel): the
@@ -979,7 +988,7 @@ def path_bench(V, s, sc, d_rays, n, flush, stream, torch, steps, bounces=3):
                 ms.append(e0.elapsed_time(e1))
         return statistics.median(ms)
 
-    t = frame_ms(default_params(V))
+    t = frame_ms(octant_params(V))
     segments = int(seg.sum().item())
     # the segments in lock step, persistent warps on the same pixel tiles
     tl = frame_ms(V.trace_params(block_size=128, image_width=FRAME_W, persistent=1,
@@ -1079,7 +1088,7 @@ def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):
     V.vsr_scene_update(s, torch.from_numpy(sc.verts).to(dev), 0,
                        torch.from_numpy(sc.textures[0].texels).to(dev))
     img = torch.empty((n, 3), dtype=torch.float32, device=dev)
-    p = default_params(V, 512)
+    p = octant_params(V, 512)
     gv = torch.zeros((sc.verts.shape[0], 3), dtype=torch.float32, device=dev)
     gt = torch.zeros(sc.textures[0].texels.shape, dtype=torch.float32, device=dev)
 
@@ -1274,9 +1283,10 @@ def large_bench(V, torch, dev, flush, stream, steps):
     reps = max(3, steps // 2)
     out = {"workload": f"{sc.ntri} triangles, {n} primary + {n * spp} ambient-occlusion rays",
            "triangles": sc.ntri}
-    pp = default_params(V)
+    pp = octant_params(V)
     t = timed(lambda: V.vsr_trace(s, d_rays, proc, "closest", hits, None, pp, stream), reps)
     out["primary_closest_proc_alpha_Mrays_s"] = round(n / (t / 1e3) / 1e6, 1)
+    out["primary_launch"] = launch_config(pp)
     V.vsr_make_ao_rays(s, d_rays, hits, spp, xi, 0.5, scenes.shadow_eps(sc), ao, stream)
     m = n * spp
     for kind in ("proc_alpha", "count", "default"):

@@ -117,12 +117,60 @@ AddressRangeFn address_range_fn() {
     return fn;
 }
 
+// The driver's cuPointerGetAttributes: several attributes of a pointer in
+// one call (a pointer the driver does not know gets zeroed attributes).
+typedef int (*PointerAttrsFn)(unsigned, int*, void**, unsigned long long);
+
+PointerAttrsFn pointer_attrs_fn() {
+    static PointerAttrsFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttributes", &f, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (PointerAttrsFn) nullptr;
+        }
+        return reinterpret_cast<PointerAttrsFn>(f);
+    }();
+    return fn;
+}
+
+// Attribute codes and the device memory type of the driver API (cuda.h).
+constexpr int kAttrMemoryType = 2, kAttrIsManaged = 8, kAttrDeviceOrdinal = 9,
+              kAttrRangeStart = 11, kAttrRangeSize = 12;
+constexpr unsigned kMemoryTypeDevice = 2;
+
 // A device pointer on `device`, aligned, with `bytes` inside its allocation.
+// One driver query gives the memory type, managed flag, device and
+// allocation range; without it the runtime's attributes and the address
+// range are queried separately.
 vsr_status check_dev(const void* p, int device, const char* name, size_t align, size_t bytes) {
     if (!p) return fail(VSR_ERR_ARG, std::string(name) + " is null");
     if (reinterpret_cast<uintptr_t>(p) % align)
         return fail(VSR_ERR_ARG, std::string(name) + " is not " + std::to_string(align) +
                                      "-byte aligned");
+    if (PointerAttrsFn fn = pointer_attrs_fn()) {
+        unsigned mem_type = 0, managed = 0;
+        int ordinal = -1;
+        unsigned long long start = 0;
+        size_t size = 0;
+        int attrs[5] = {kAttrMemoryType, kAttrIsManaged, kAttrDeviceOrdinal, kAttrRangeStart,
+                        kAttrRangeSize};
+        void* data[5] = {&mem_type, &managed, &ordinal, &start, &size};
+        const unsigned long long addr = reinterpret_cast<uintptr_t>(p);
+        if (fn(5, attrs, data, addr) == 0) {
+            if (managed) return VSR_OK;
+            if (mem_type != kMemoryTypeDevice)
+                return fail(VSR_ERR_ARG, std::string(name) + " is not device memory");
+            if (ordinal != device)
+                return fail(VSR_ERR_ARG, std::string(name) + " lives on another device");
+            if (size && (addr + bytes > start + size || addr + bytes < addr))
+                return fail(VSR_ERR_ARG, std::string(name) + " is smaller than " +
+                                             std::to_string(bytes) + " bytes");
+            return VSR_OK;
+        }
+    }
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();

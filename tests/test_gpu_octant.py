@@ -220,3 +220,28 @@ def test_octant_tuned_and_rejected(V, small):
     assert V.params_dict(tp)["octant"] in (0, 1)
     got, _ = V.trace(s, d, "alpha_tex", "closest", params=tp)
     _same_as_oracle(got, ref, st, "tuned")
+
+
+def test_octant_render_and_path(V, small):
+    """The render (trace kernels + shading) and the path tracer take the
+    parameter too: images, hit records and path radiance are identical with
+    and without it."""
+    sc, rays, blob, s = small
+    d = torch.from_numpy(rays).cuda()
+    n = len(rays)
+    shade = V.shade_params(scenes.light_dir_f32())
+    out = {}
+    for oc in (0, 1):
+        p = V.trace_params(image_width=256, octant=oc)
+        img = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        hits = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        V.vsr_render(s, d, V.intersector("alpha_tex"), shade, img, hits, p)
+        dirs = torch.from_numpy(scenes.path_dirs(n, 2)).cuda()
+        rad = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        pp = V.path_params(2, scenes.shadow_eps(sc))
+        V.vsr_path_trace(s, d, V.intersector("alpha_tex"), pp, dirs, rad, None, p)
+        torch.cuda.synchronize()
+        out[oc] = (img, hits, rad)
+    for a, b in zip(out[0], out[1]):
+        assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+    assert V.vsr_get_device_error(s) == 0
