@@ -512,23 +512,31 @@ def run_ours(args):
 
     # Launch configuration: vsr_trace_tune times its candidates on the frame
     # (untimed, before the steps) and keeps the fastest in the scene for each
-    # query; the timed step then calls vsr_trace with params NULL.
-    tuned_p = V.vsr_trace_tune(s, d_rays, alpha, "closest", hits_p, FRAME_W, stream)
-    V.vsr_trace(s, d_rays, alpha, "closest", hits_p, None, None, stream)
+    # query; the timed step then calls vsr_trace with params NULL.  With
+    # --launch octant the step passes the configuration the tuner picks on
+    # this frame explicitly and nothing is tuned (for profiler runs, whose
+    # serialised launches would distort the tuner's timings).
+    if args.launch == "octant":
+        tuned_p = tuned_s = step_p = octant_params(V)
+    else:
+        tuned_p = V.vsr_trace_tune(s, d_rays, alpha, "closest", hits_p, FRAME_W, stream)
+        step_p = None
+    V.vsr_trace(s, d_rays, alpha, "closest", hits_p, None, step_p, stream)
     V.vsr_make_shadow_rays(d_rays, hits_p, light, eps, rays_s, stream)
-    tuned_s = V.vsr_trace_tune(s, rays_s, alpha, "any", hits_s, FRAME_W, stream)
+    if args.launch != "octant":
+        tuned_s = V.vsr_trace_tune(s, rays_s, alpha, "any", hits_s, FRAME_W, stream)
     torch.cuda.synchronize(dev)
 
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        V.vsr_trace(s, d_rays, alpha, "closest", hits_p, None, None, stream)
+        V.vsr_trace(s, d_rays, alpha, "closest", hits_p, None, step_p, stream)
         if ev is not None:
             ev[1].record(stream)
         V.vsr_make_shadow_rays(d_rays, hits_p, light, eps, rays_s, stream)
         if ev is not None:
             ev[2].record(stream)
-        V.vsr_trace(s, rays_s, alpha, "any", hits_s, None, None, stream)
+        V.vsr_trace(s, rays_s, alpha, "any", hits_s, None, step_p, stream)
         if ev is not None:
             ev[3].record(stream)
 
@@ -640,8 +648,11 @@ def run_ours(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "rays_per_step": rays_per_step,
                       "triangles": sc.ntri,
-                      "launch": "vsr_trace with params NULL: the configuration vsr_trace_tune "
-                                "chose on the frame (untimed, before the steps)",
+                      "launch": ("vsr_trace with params NULL: the configuration "
+                                 "vsr_trace_tune chose on the frame (untimed, before the steps)"
+                                 if args.launch == "tuned" else
+                                 "vsr_trace with the octant configuration passed explicitly "
+                                 "(--launch octant; nothing tuned)"),
                       "tuned_primary": V.params_dict(tuned_p),
                       "tuned_shadow": V.params_dict(tuned_s),
                       "ray_order": "row-major frame; each warp traces a 4x8 pixel tile",
@@ -685,10 +696,10 @@ def run_ours(args):
                 d_rays[lo:hi].copy_(h_rays[lo:hi], non_blocking=True)
             e_in.record(s_in)
             tr.wait_event(e_in)
-            V.vsr_trace(s, d_rays[lo:hi], alpha, "closest", hits_p[lo:hi], None, None, tr)
+            V.vsr_trace(s, d_rays[lo:hi], alpha, "closest", hits_p[lo:hi], None, step_p, tr)
             V.vsr_make_shadow_rays(d_rays[lo:hi], hits_p[lo:hi], light, eps, rays_s[lo:hi], tr)
             e_p.record(tr)
-            V.vsr_trace(s, rays_s[lo:hi], alpha, "any", hits_s[lo:hi], None, None, tr)
+            V.vsr_trace(s, rays_s[lo:hi], alpha, "any", hits_s[lo:hi], None, step_p, tr)
             e_s.record(tr)
             out_st.wait_event(e_p)
             with torch.cuda.stream(out_st):
@@ -1437,6 +1448,10 @@ def main():
                     help="--leg trace/ao: 1 profiles the persistent launch (--refill)")
     ap.add_argument("--lockstep", type=int, default=0,
                     help="--leg trace/ao/batch_profile: 1 runs each warp in lock step")
+    ap.add_argument("--launch", choices=["tuned", "octant"], default="tuned",
+                    help="timed step: tuned = vsr_trace_tune first, then params NULL; octant = "
+                         "the configuration the tuner picks on the frame (block 128, pixel "
+                         "tiles, octant box test), passed explicitly, nothing tuned")
     ap.add_argument("--octant", type=int, default=0,
                     help="--leg trace/ao: 1 gives warps whose rays share a direction octant "
                          "a box test compiled for it")
