@@ -979,7 +979,9 @@ def multi_hit(V, s, d_rays, n, flush, stream, torch, reps=5):
 
 def path_bench(V, s, sc, d_rays, n, flush, stream, torch, steps, bounces=3):
     """Diffuse path tracing of the forest frame: every segment a closest-hit
-    query with the alpha intersector (pixel tiles), 3 bounces, sky light."""
+    query with the alpha intersector (primary segments on pixel tiles, bounce
+    segments over the live paths compacted after each bounce), 3 bounces,
+    sky light."""
     from paper_1912_12786_gb300.inputs import scenes
     dirs = torch.from_numpy(scenes.path_dirs(n, bounces)).to(d_rays.device)
     rad = torch.empty((n, 3), dtype=torch.float32, device=d_rays.device)
@@ -1009,7 +1011,7 @@ def path_bench(V, s, sc, d_rays, n, flush, stream, torch, steps, bounces=3):
             "segments": segments, "Msegments_s": round(segments / (t / 1e3) / 1e6, 1),
             "lockstep_persistent_ms_per_frame": round(tl, 4),
             "lockstep_persistent_Mpaths_s": round(n / (tl / 1e3) / 1e6, 1),
-            "gpu_launches_per_frame": 1 + 2 * (bounces + 1)}
+            "gpu_launches_per_frame": 1 + 2 * (bounces + 1) + 3 * bounces}
 
 
 def instanced_bench(V, torch, dev, flush, stream, steps):

@@ -393,13 +393,16 @@ vsr_status vsr_trace_multi(vsr_scene* scene, const vsr_ray* rays, uint64_t n,
  *             3 * (i * bounces + k), cosine-distributed for a diffuse surface
  *   radiance  device float32 [n * 3], written
  *   segments  device uint32 [n] or NULL: closest-hit queries path i made
- *   params    every segment's launch (image_width keeps bounce segments at
- *             their pixel); persistent launches and lock step apply to each
- *             segment depth (finished paths are inactive rays, claimed and
- *             dropped at once); ray_order 0
+ *   params    every segment's launch; image_width maps the primary
+ *             segments to pixel tiles; persistent launches, lock step and
+ *             the octant box test apply to each segment depth; ray_order 0
  * One closest-hit launch per segment depth plus one shading launch, on
- * `stream`; scratch (n * 60 bytes) comes from the stream-ordered allocator.
- * Errors as vsr_trace.
+ * `stream`.  After each bounce but the last, three small launches compact
+ * the live paths (n < 2^32): the next segment's threads take the live paths
+ * first, in index order, and the finished ones (inactive rays, dropped at
+ * the root box test) after them; results do not depend on it.  Scratch
+ * (n * 64 bytes plus 4 bytes per 256 paths) comes from the stream-ordered
+ * allocator.  Errors as vsr_trace.
  */
 typedef struct vsr_path_params {
     uint32_t bounces;      /* 0..64 */

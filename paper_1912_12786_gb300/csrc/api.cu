@@ -2209,9 +2209,19 @@ extern "C" vsr_status vsr_path_trace(vsr_scene* s, const vsr_ray* rays, uint64_t
     float4* work = nullptr;
     float4* hits = nullptr;
     float* f = nullptr;
+    // after each bounce the live paths are compacted to the front of a
+    // permutation the next segment's trace follows (ray indices are 32-bit)
+    const bool compact = pp->bounces > 0 && n <= 0xFFFFFFFFull;
+    uint32_t* perm = nullptr;
+    uint32_t* counts = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&work), n * 32, cs);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&hits), n * 16, cs);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&f), n * 12, cs);
+    if (e == cudaSuccess && compact)
+        e = cudaMallocAsync(reinterpret_cast<void**>(&perm), n * 4, cs);
+    if (e == cudaSuccess && compact)
+        e = cudaMallocAsync(reinterpret_cast<void**>(&counts),
+                            (path_compact_blocks(n) + 1ull) * 4, cs);
     if (e == cudaSuccess)
         e = launch_path_init(reinterpret_cast<const float4*>(rays), n, work, f, radiance, segments,
                              cs);
@@ -2219,12 +2229,17 @@ extern "C" vsr_status vsr_path_trace(vsr_scene* s, const vsr_ray* rays, uint64_t
     a.hits = hits;
     a.stream = cs;
     for (uint32_t k = 0; e == cudaSuccess && k <= pp->bounces; ++k) {
+        if (k == 1 && compact) a.map = RayMap{n, n, 0u, 0u, perm};
         e = is->dispatch == VSR_DISPATCH_STATIC ? launch_static(a, is->kind, false)
                                                 : launch_dynamic(a, is->kind);
         if (e == cudaSuccess)
             e = launch_path_bounce(s->dev, pd, s->d_verts, s->d_idx, work, hits, f, dirs, k, n,
                                    radiance, segments, cs);
+        if (e == cudaSuccess && compact && k < pp->bounces)
+            e = launch_path_compact(f, n, counts, perm, cs);
     }
+    if (counts) cudaFreeAsync(counts, cs);
+    if (perm) cudaFreeAsync(perm, cs);
     if (f) cudaFreeAsync(f, cs);
     if (hits) cudaFreeAsync(hits, cs);
     if (work) cudaFreeAsync(work, cs);

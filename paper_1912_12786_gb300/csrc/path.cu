@@ -144,7 +144,115 @@ __global__ void k_path_bounce(DevScene sc, PathDev pd, const float* __restrict__
                     __int_as_float(0x7f800000));
 }
 
+// Live-path compaction between bounces: a stable partition of the path
+// indices with the live paths (f[3i] >= 0) first, in index order, and the
+// finished ones after them.  The next segment's trace then takes ray perm[g]
+// in thread g, so live rays fill whole warps instead of sharing them with
+// finished paths, whose inactive rays end at the root box test.  Each ray is
+// traced exactly as before, so every result is unchanged.
+constexpr uint32_t kCompactThreads = 256;
+
+__device__ __forceinline__ bool path_live(const float* __restrict__ f, unsigned long long i,
+                                          unsigned long long n) {
+    return i < n && f[3 * i] >= 0.0f;
+}
+
+// Number of live paths of this block before the thread's path, and the
+// block's live count in *total.  Every thread of the block calls it.
+__device__ __forceinline__ uint32_t block_live_rank(bool live, uint32_t* s_warp,
+                                                    uint32_t* total) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const unsigned b = __ballot_sync(kFullMask, live);
+    if (lane == 0) s_warp[warp] = __popc(b);
+    __syncthreads();
+    uint32_t before = 0, sum = 0;
+    for (uint32_t w = 0; w < kCompactThreads / 32u; ++w) {
+        const uint32_t c = s_warp[w];
+        if (w < warp) before += c;
+        sum += c;
+    }
+    *total = sum;
+    return before + __popc(b & ((1u << lane) - 1u));
+}
+
+__global__ void __launch_bounds__(kCompactThreads)
+    k_live_count(const float* __restrict__ f, unsigned long long n, uint32_t* __restrict__ counts) {
+    __shared__ uint32_t s_warp[kCompactThreads / 32];
+    const unsigned long long i = (unsigned long long)blockIdx.x * kCompactThreads + threadIdx.x;
+    uint32_t total = 0;
+    block_live_rank(path_live(f, i, n), s_warp, &total);
+    if (threadIdx.x == 0) counts[blockIdx.x] = total;
+}
+
+// Exclusive scan of the nb block counts in place, 1,024 at a time with a
+// running carry; counts[nb] receives the number of live paths.
+__global__ void __launch_bounds__(1024) k_live_scan(uint32_t* __restrict__ counts, uint32_t nb) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_carry;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < nb; base += 1024u) {
+        const uint32_t j = base + threadIdx.x;
+        const uint32_t v = j < nb ? counts[j] : 0u;
+        uint32_t x = v;  // inclusive scan within the warp
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFullMask, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = s_warp[lane];
+            for (uint32_t o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFullMask, w, o);
+                if (lane >= o) w += y;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t excl = s_carry + (warp ? s_warp[warp - 1] : 0u) + x - v;
+        if (j < nb) counts[j] = excl;
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) counts[nb] = s_carry;
+}
+
+__global__ void __launch_bounds__(kCompactThreads)
+    k_live_scatter(const float* __restrict__ f, unsigned long long n,
+                   const uint32_t* __restrict__ offsets, uint32_t nb, uint32_t* __restrict__ perm) {
+    __shared__ uint32_t s_warp[kCompactThreads / 32];
+    const unsigned long long i = (unsigned long long)blockIdx.x * kCompactThreads + threadIdx.x;
+    const bool live = path_live(f, i, n);
+    uint32_t total = 0;
+    const uint32_t rank = block_live_rank(live, s_warp, &total);
+    if (i >= n) return;
+    const uint32_t live_before = offsets[blockIdx.x];
+    if (live) {
+        perm[live_before + rank] = (uint32_t)i;
+    } else {
+        // finished paths before this one: in earlier blocks, then in this one
+        const uint32_t dead_before = blockIdx.x * kCompactThreads - live_before;
+        perm[offsets[nb] + dead_before + (threadIdx.x - rank)] = (uint32_t)i;
+    }
+}
+
 }  // namespace
+
+uint32_t path_compact_blocks(unsigned long long n) {
+    return (uint32_t)((n + kCompactThreads - 1) / kCompactThreads);
+}
+
+cudaError_t launch_path_compact(const float* f, unsigned long long n, uint32_t* counts,
+                                uint32_t* perm, cudaStream_t stream) {
+    const uint32_t nb = path_compact_blocks(n);
+    k_live_count<<<nb, kCompactThreads, 0, stream>>>(f, n, counts);
+    k_live_scan<<<1, 1024, 0, stream>>>(counts, nb);
+    k_live_scatter<<<nb, kCompactThreads, 0, stream>>>(f, n, counts, nb, perm);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_path_init(const float4* rays, unsigned long long n, float4* work, float* f,
                              float* radiance, uint32_t* segments, cudaStream_t stream) {

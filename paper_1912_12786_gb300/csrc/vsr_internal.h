@@ -139,6 +139,12 @@ cudaError_t launch_path_bounce(const DevScene& sc, const PathDev& pd, const floa
                                const uint32_t* idx, float4* work, const float4* hits, float* f,
                                const float* dirs, uint32_t k, unsigned long long n,
                                float* radiance, uint32_t* segments, cudaStream_t stream);
+// Live-path compaction (path.cu): perm[0..n) becomes the path indices with
+// the live paths first, in index order; counts holds path_compact_blocks(n)
+// + 1 words of scratch.  n < 2^32.
+uint32_t path_compact_blocks(unsigned long long n);
+cudaError_t launch_path_compact(const float* f, unsigned long long n, uint32_t* counts,
+                                uint32_t* perm, cudaStream_t stream);
 // Source line of the first misaligned load the path kernels skipped (0 if
 // none), cleared after reading.
 cudaError_t path_align_error(unsigned* line);

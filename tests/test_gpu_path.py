@@ -97,6 +97,27 @@ def test_ragged_sizes(V, small):
         assert np.array_equal(got[ok].view(np.uint32), ref[ok].view(np.uint32))
 
 
+def test_compaction_across_scan_chunks(V, small):
+    """Live-path compaction between bounces: 300,001 paths make 1,172 blocks
+    of 256, more than one 1,024-entry chunk of the block-count scan and a
+    partial last block.  Radiance equals the oracle's, and the paths with a
+    later segment are exactly those whose earlier segment hit."""
+    sc, rays, blob, s = small
+    n = 300_001
+    sel = np.resize(rays, (n, 8))
+    dirs = scenes.path_dirs(n, 2, seed=77)
+    ref, flags = O.path_trace(sc, blob, sel, 2, dirs, 1e-4, SKY, UNTEX, "alpha_tex")
+    got, seg = _gpu(V, s, sel, "alpha_tex", 2, dirs)
+    ok = flags == 0
+    assert ok.mean() > 0.99
+    assert np.array_equal(got[ok].view(np.uint32), ref[ok].view(np.uint32))
+    assert (seg == 1).any() and (seg == 2).any() and (seg == 3).any()
+    got_t, seg_t = _gpu(V, s, sel, "alpha_tex", 2, dirs, V.trace_params(octant=1))
+    assert np.array_equal(got.view(np.uint32), got_t.view(np.uint32))
+    assert np.array_equal(seg, seg_t)
+    assert V.vsr_get_device_error(s) == 0, V.vsr_last_error()
+
+
 def test_argument_checks(V, small):
     sc, rays, blob, s = small
     d = _dev(rays[:64])
