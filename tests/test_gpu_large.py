@@ -78,6 +78,27 @@ def test_primary_and_ao_parity_on_a_sample(large):
     assert V.vsr_get_device_error(s) == 0
 
 
+def test_octant_primary_full_frame(large):
+    """The 16 M-triangle frame's primary closest hits with the box test
+    specialised to each warp's direction octant (pixel tiles, as the
+    benchmark runs them) equal the generic kernel's bit for bit, and a
+    seeded sample equals the oracle's."""
+    V, sc, rays, blob, s, xi, eps = large
+    proc = V.intersector("proc_alpha")
+    d_rays = torch.from_numpy(rays).cuda()
+    h0 = torch.empty((len(rays), 4), dtype=torch.float32, device="cuda")
+    h1 = torch.empty_like(h0)
+    V.vsr_trace(s, d_rays, proc, "closest", h0, None, V.trace_params(image_width=1920))
+    V.vsr_trace(s, d_rays, proc, "closest", h1, None,
+                V.trace_params(image_width=1920, octant=1))
+    torch.cuda.synchronize()
+    assert torch.equal(h0.view(torch.int32), h1.view(torch.int32))
+    sel = np.sort(np.random.default_rng(23).choice(len(rays), 3000, replace=False))
+    ref, st = O.trace_bvh(sc, blob, rays[sel], "proc_alpha", "closest")
+    _cmp(h1.cpu().numpy()[sel], ref, st, "octant primary")
+    assert V.vsr_get_device_error(s) == 0
+
+
 def test_full_ao_pass_invariants(large):
     """All 8.3 M AO rays: static == dynamic dispatch and bvh_costs hits ==
     default hits, bit for bit; about half the pixels hit geometry."""
