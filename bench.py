@@ -68,9 +68,11 @@ def default_params(V, image_width=FRAME_W):
 
 
 def octant_params(V, image_width=FRAME_W):
-    """default_params with the box test specialised to a warp's direction
-    octant (static dispatch; what the tuner picks on coherent frames)."""
+    """One ray per thread on 4x8 pixel tiles, block 64, with the box test
+    specialised to a warp's direction octant (static dispatch; what the
+    tuner picks on the forest frame)."""
     p = default_params(V, image_width)
+    p.block_size = 64
     p.octant = 1
     return p
 
@@ -1454,7 +1456,7 @@ def main():
                     help="--leg trace/ao/batch_profile: 1 runs each warp in lock step")
     ap.add_argument("--launch", choices=["tuned", "octant"], default="tuned",
                     help="timed step: tuned = vsr_trace_tune first, then params NULL; octant = "
-                         "the configuration the tuner picks on the frame (block 128, pixel "
+                         "the configuration the tuner picks on the frame (block 64, pixel "
                          "tiles, octant box test), passed explicitly, nothing tuned")
     ap.add_argument("--octant", type=int, default=0,
                     help="--leg trace/ao: 1 gives warps whose rays share a direction octant "

@@ -503,7 +503,7 @@ cudaError_t time_params(const LaunchArgs& base, const vsr_trace_params& c, int k
 // one ray per thread, per-lane loops and lock step x block 64/128/256 x
 // register-stack depth 0/1/2/4/8 (static dispatch; dynamic: depth 0),
 // starting from the default (128, 0, per-lane loops), and with static
-// dispatch the octant-specialised box test at block 128/64/256; then the
+// dispatch the octant-specialised box test at block 64/128/256; then the
 // best of these in coherence order (its sort timed with it); last, the
 // persistent launch at
 // the best configuration with per-lane loops and in lock step, refill
@@ -542,7 +542,7 @@ vsr_status tune_trace(vsr_scene* s, const LaunchArgs& base, const vsr_intersecto
                 if ((!dynamic || k == 0) && !(b == 128u && k == 0u && ls == 0u))
                     consider(vsr_trace_params{b, 0u, 16u, 0u, image_width, k, 0u, 0u, 0u, 0u, ls});
     if (!dynamic)  // box tests specialised to a warp's direction octant
-        for (uint32_t b : {128u, 64u, 256u}) {
+        for (uint32_t b : {64u, 128u, 256u}) {
             vsr_trace_params c{b, 0u, 16u, 0u, image_width, 0u, 0u, 0u, 0u, 0u, 0u};
             c.octant = 1u;
             consider(c);
