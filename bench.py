@@ -1147,6 +1147,43 @@ def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):
 
     ms_rt, _, bwd_rt = run(True)
     ms, fwd, bwd = run(False)
+
+    # the same step (render keeping the hit records, loss gradient, zeroed
+    # buffers, adjoint) captured once in a CUDA graph and replayed, so the
+    # step's seven launches follow each other without host gaps
+    def step_on(st):
+        V.vsr_render(s, d_rays, isect, shade, img, saved, p, st)
+        gg = 2.0 * (img - target)
+        gv.zero_()
+        gt.zero_()
+        V.vsr_render_backward_hits(s, d_rays, saved, shade, gg, gv, gt, st)
+
+    graph_ms, graph_note = None, None
+    try:
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                step_on(side)
+        stream.wait_stream(side)
+        torch.cuda.synchronize(dev)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step_on(torch.cuda.current_stream())
+        gms = []
+        for k in range(steps + 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 2:
+                gms.append(e0.elapsed_time(e1))
+        graph_ms = statistics.median(gms)
+        del graph
+    except RuntimeError as exc:
+        graph_note = f"graph capture failed: {exc}"
     # each adjoint kernel alone between events (gradient buffers zeroed outside
     # them), with exact counts for the byte models
     hits = torch.empty((n, 4), dtype=torch.float32, device=dev)
@@ -1206,6 +1243,8 @@ def fwd_bwd(V, torch, dev, flush, stream, steps, warmup):
             "retrace_backward_ms": round(statistics.median(bwd_rt), 4),
             "forward_ms": round(statistics.median(fwd), 4),
             "backward_ms": round(statistics.median(bwd), 4),
+            "graph_value": (round(n / (graph_ms / 1e3) / 1e6, 2) if graph_ms else None),
+            "graph_ms_per_step": (round(graph_ms, 4) if graph_ms else graph_note),
             "workload": "displaced icosphere, 64,980 triangles, 512x512 rays, alpha-texture "
                         "closest hit, gradients for 32,492 vertices and 512^2 texels",
             "gpu_launches_per_step": 3}
