@@ -102,6 +102,24 @@ def test_octant_shadow_and_diffuse_rays(V, small):
                 assert np.array_equal(cnt.cpu().numpy().view(np.uint32), st[:, :2])
 
 
+def test_octant_in_coherence_order(V, small):
+    """Coherence order (the rays sorted by origin cell and direction inside
+    the launch) with the octant test: warps of sorted, shuffled camera rays
+    and of diffuse rays give the oracle's records."""
+    sc, rays, blob, s = small
+    shuffled = rays[np.random.default_rng(9).permutation(len(rays))]
+    diff = scenes.diffuse_rays(np.random.default_rng(12), sc, 30_000)
+    for rr in (shuffled, diff):
+        d = torch.from_numpy(np.ascontiguousarray(rr)).cuda()
+        for kind, q in (("alpha_tex", "closest"), ("count", "any")):
+            ref, st = O.trace_bvh(sc, blob, rr, kind, q)
+            hits, cnt = V.trace(s, d, kind, q, counters=(kind == "count"),
+                                params=V.trace_params(ray_order=1, octant=1))
+            _same_as_oracle(hits, ref, st, f"ordered {kind}/{q}")
+            if kind == "count":
+                assert np.array_equal(cnt.cpu().numpy().view(np.uint32), st[:, :2])
+
+
 @pytest.mark.parametrize("n", [1, 31, 33, 4097])
 def test_octant_ragged_and_clip(V, small, n):
     sc, rays, blob, s = small
@@ -190,6 +208,15 @@ def test_octant_forest_full_size(V):
         s0, _ = V.trace(s, sh, "alpha_tex", "any", params=p0)
         s1, _ = V.trace(s, sh, "alpha_tex", "any", params=p1)
         assert torch.equal(s0.view(torch.int32), s1.view(torch.int32))
+        # the other intersectors of the bench's octant comparison, both passes
+        for kind in ("default", "proc_alpha", "count"):
+            cnt = kind == "count"
+            for q, rr in (("closest", d), ("any", sh)):
+                g0, c0 = V.trace(s, rr, kind, q, counters=cnt, params=p0)
+                g1, c1 = V.trace(s, rr, kind, q, counters=cnt, params=p1)
+                assert torch.equal(g0.view(torch.int32), g1.view(torch.int32)), (kind, q)
+                if cnt:
+                    assert torch.equal(c0, c1)
         sel = np.sort(np.random.default_rng(8).choice(len(rays), 5000, replace=False))
         ref, st = O.trace_bvh(sc, blob, rays[sel], "alpha_tex", "closest")
         _same_as_oracle(h1[torch.from_numpy(sel).cuda()], ref, st, "forest sample")
