@@ -147,7 +147,69 @@ def read_peaks(V, torch, dev) -> dict:
 # clocks during the timed region
 
 
+class NvmlClockSampler:
+    """SM clock and clock-event reasons of one GPU read through NVML
+    (libnvidia-ml, read-only queries) about every millisecond from a thread,
+    so that even a region of a few milliseconds gets samples.  start()
+    returns False where NVML cannot be loaded."""
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+               "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lib = None
+        self.samples = []
+        self.max_mhz = 0
+        self.reasons = 0
+        self.thread = None
+        self.stop_flag = False
+
+    def start(self) -> bool:
+        import ctypes
+        import threading
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return False
+            dev = ctypes.c_void_p()
+            mx = ctypes.c_uint()
+            if (lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(dev)) != 0
+                    or lib.nvmlDeviceGetMaxClockInfo(dev, 1, ctypes.byref(mx)) != 0):
+                lib.nvmlShutdown()
+                return False
+        except (OSError, AttributeError):
+            return False
+        self.lib, self.dev, self.max_mhz = lib, dev, mx.value
+        clk, why = ctypes.c_uint(), ctypes.c_ulonglong()
+
+        def poll():
+            while not self.stop_flag:
+                if lib.nvmlDeviceGetClockInfo(self.dev, 1, ctypes.byref(clk)) == 0:
+                    self.samples.append(clk.value)
+                if lib.nvmlDeviceGetCurrentClocksEventReasons(self.dev, ctypes.byref(why)) == 0:
+                    self.reasons |= why.value
+                time.sleep(0.001)
+
+        self.thread = threading.Thread(target=poll, daemon=True)
+        self.thread.start()
+        return True
+
+    def stop(self):
+        if self.thread is None:
+            return None
+        self.stop_flag = True
+        self.thread.join()
+        self.lib.nvmlShutdown()
+        if not self.samples:
+            return None
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": float(self.max_mhz),
+                "reasons": sorted(k for k, bit in self.REASONS.items() if self.reasons & bit),
+                "samples": len(self.samples), "source": "NVML, about every 1 ms"}
+
+
 class ClockSampler:
+    """Clocks during a region: NVML polled from a thread where it loads,
+    else nvidia-smi every 50 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -158,8 +220,13 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.nvml = None
 
     def start(self):
+        self.nvml = NvmlClockSampler(self.gpu)
+        if self.nvml.start():
+            return
+        self.nvml = None
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -172,6 +239,8 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.nvml is not None:
+            return self.nvml.stop()
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -199,7 +268,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": f"nvidia-smi every {self.INTERVAL_MS} ms"}
 
 
 # --------------------------------------------------------------------------
